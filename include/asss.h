@@ -1,0 +1,196 @@
+/*
+ * asss.h - C ABI of a GB300 (sm_103a) implementation of the two-level iterative
+ * scheme for general sparse A x = b based on approximate shifted skew-symmetrizers
+ * (Manguoglu & Mehrmann, arXiv 2009.06954).
+ *
+ * The scheme (paper §2-§4.1):
+ *   Abar = P D_r A D_c                                   (§2, Eq. mc64)
+ *   S    = argmin ||B_u s||^2 + gamma ||B_l s - 1||^2     (§2, Eqs. eq1, eq2, regularized; App. A)
+ *   d = diag(Abar S), W = |d|^-1/2, M~_r = sign(d) - I  (§3, Eq. absfac, Fig. 1; 1x1 pivots)
+ *   J~ = W (Abar S - (Abar S)^T)/2 W                      (§3, Eq. preconditioner)
+ *   Q_k, S_k from k steps of skew-Lanczos on J~          (§3.2, Fig. 2)
+ *   P = [Q_k U_r] blkdiag(S_k, -2I) [Q_k U_r]^T + (I + J~ - Q_k S_k Q_k^T)   (§3.2, Eq. preconditioner)
+ *   outer Krylov on  W Abar S W y = W P D_r b,  x = D_c S W y                (§3 Eq. modified, §4.1)
+ *   P^-1 by SMW (Eq. smw) around inner mrs solves of the deflated shifted skew
+ *   system (§3.1, App. B).
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers may be host or device memory; the library inspects each pointer
+ *    (cudaPointerGetAttributes) and copies host data in and out itself.
+ *  - Dense vectors are float64.  Multi-vector arguments are column-major with a
+ *    leading dimension (ld >= n).
+ *  - CSR matrices are 0-based, square, column indices sorted and unique within a
+ *    row, every index in range; violations return ASSS_ERR_PATTERN.  nnz must be
+ *    below 2^31.
+ *  - The caller owns every buffer it passes; the library never keeps a caller
+ *    pointer after a call returns.  asss_setup copies A into memory owned by the
+ *    handle; asss_destroy frees it.
+ *  - All device work is enqueued on options.stream (a cudaStream_t, NULL = the
+ *    legacy default stream); each call synchronises that stream before it returns.
+ *  - Errors are reported by return code, never by abort/exit.  asss_last_error()
+ *    returns a human-readable message for the last failing call of this thread.
+ *  - Device-side waits (grid barriers of the persistent kernels) give up after
+ *    options.wait_timeout_ms and the call returns ASSS_ERR_TIMEOUT.
+ */
+#ifndef ASSS_H
+#define ASSS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ASSS_OK = 0,
+    ASSS_ERR_ARG = 1,            /* invalid argument or option                        */
+    ASSS_ERR_PATTERN = 2,        /* malformed CSR (unsorted, duplicate, out of range) */
+    ASSS_ERR_ZERO_DIAG = 3,      /* |d_i| < zero_tol * max|d|: zero pivot (§4.1 Table 4 legend) */
+    ASSS_ERR_BREAKDOWN = 4,      /* Krylov breakdown that prevented any progress      */
+    ASSS_ERR_NOT_CONVERGED = 5,  /* iteration limit reached; outputs hold the best iterate */
+    ASSS_ERR_STAGNATION = 6,     /* outer residual stopped decreasing                  */
+    ASSS_ERR_RANK = 7,           /* rank of M~_r above r_max (Eq. preconditioner2 used) - informational */
+    ASSS_ERR_TIMEOUT = 8,        /* a device-side wait exceeded wait_timeout_ms        */
+    ASSS_ERR_OOM = 9,            /* device allocation failed                           */
+    ASSS_ERR_CUDA = 10,          /* any other CUDA error                               */
+    ASSS_ERR_UNSUPPORTED = 11    /* input beyond what this build handles (text says which) */
+} asss_status;
+
+enum { ASSS_PREC_FP64 = 0, ASSS_PREC_MIXED = 1 };      /* inner solve in FP64 or FP32 */
+enum { ASSS_OUTER_TFQMR = 0, ASSS_OUTER_FGMRES = 1 };  /* §4.1: tfqmr; flexible GMRES for inexact inner solves */
+
+/* Square sparse matrix in CSR. val may be NULL where only a pattern is needed. */
+typedef struct {
+    int64_t n;
+    int64_t nnz;
+    const int64_t* row_ptr;   /* n+1 entries, row_ptr[0] = 0, row_ptr[n] = nnz */
+    const int32_t* col_idx;   /* nnz entries */
+    const double*  val;       /* nnz entries or NULL */
+} asss_csr;
+
+typedef struct {
+    double gamma;             /* weight of the diagonal constraints, Eq. regularized (paper: 1) */
+    int    k_lanczos;         /* number of skew-Lanczos vectors k (§4.3: 20)                     */
+    int    reorth;            /* 1: two classical Gram-Schmidt passes per Lanczos step; 0: Fig. 2 as printed */
+    const asss_csr* s_pattern;/* sparsity of S (values ignored); NULL: the pattern of A (§2)     */
+    const int32_t* row_perm;  /* optional row permutation P of Eq. mc64: row i of Abar is row row_perm[i] of D_r A D_c */
+    const double*  dr;        /* optional row scaling D_r (n); NULL: 1/row-max|a|               */
+    const double*  dc;        /* optional column scaling D_c (n); NULL: 1/col-max|D_r a|        */
+    double inner_tol;         /* mrs stopping tolerance on |g|/||rhs|| (App. B)                  */
+    double setup_tol;         /* tolerance of the multi-RHS mrs solve S_bar X = U_bar (§4.1); <= 0: inner_tol */
+    double outer_tol;         /* ||b - A x|| <= outer_tol ||b||                                  */
+    int    inner_maxit;       /* mrs iteration limit                                            */
+    int    outer_maxit;       /* total outer Krylov steps (§4.1: 2000)                          */
+    int    restart;           /* flexible GMRES restart length                                  */
+    int    precision;         /* ASSS_PREC_FP64 or ASSS_PREC_MIXED (inner FP32, outer FP64)      */
+    int    outer;             /* ASSS_OUTER_TFQMR or ASSS_OUTER_FGMRES                           */
+    int    r_max;             /* largest rank r of M~_r kept; above it Eq. (preconditioner2)   */
+    uint64_t seed;            /* splitmix64 seed of the Lanczos start vector                    */
+    double lls_tol;           /* normal-equation gradient tolerance of the LLS solve            */
+    int    lls_maxit;
+    double zero_tol;          /* |d_i| < zero_tol*max|d| is a zero pivot                        */
+    double wait_timeout_ms;   /* budget of each device-side wait                                */
+    void*  stream;            /* cudaStream_t                                                   */
+} asss_options;
+
+typedef struct {
+    int    status;            /* asss_status of the call                                        */
+    int    outer_its;         /* outer Krylov steps (TFQMR: full steps; FGMRES: Arnoldi steps)   */
+    int    cycles;            /* refinement cycles (true-residual restarts)                     */
+    long long inner_its_total;/* mrs iterations over all inner solves                           */
+    int    inner_solves;      /* number of inner solves (preconditioner applications)           */
+    double inner_its_avg;
+    double relres;            /* final ||b - A x|| / ||b|| in FP64 (original system)            */
+    int    r;                 /* rank of M~_r (number of negative d_i kept)                     */
+    int    k_eff;             /* Lanczos vectors kept after breakdown checks                    */
+    int    prec2;             /* 1 if Eq. (preconditioner2) was used because r > r_max          */
+    int    lls_its;           /* iterations of the LLS solve                                    */
+    double lls_relgrad;       /* final ||B^T (v - B s)|| / ||B^T v||                            */
+    long long nnz_pattern;    /* entries of pat(Abar S) + pat(Abar S)^T (LLS rows + mirror)      */
+    double t_setup_ms;
+    double t_solve_ms;
+} asss_stats;
+
+typedef struct asss_handle asss_handle;
+
+/* Fill *opt with the defaults: gamma 1, k 20, reorth 1, S on the pattern of A,
+ * identity permutation with computed scalings, inner_tol 1e-10, outer_tol 1e-8,
+ * inner_maxit 1000, outer_maxit 2000, restart 60, FP64, TFQMR, r_max 256,
+ * lls_tol 1e-13, lls_maxit 20000, zero_tol 1e-14, wait_timeout_ms 2000. */
+void asss_default_options(asss_options* opt);
+
+/* Set-up phase (§4.1, everything that does not depend on b): scaling, S, d/W/r,
+ * J~, skew-Lanczos, the SMW data for P^-1.  A is copied; *out receives a new
+ * handle (NULL on error).  st may be NULL. */
+asss_status asss_setup(const asss_csr* A, const asss_options* opt, asss_handle** out,
+                       asss_stats* st);
+
+/* Solve A x_j = b_j for nrhs right-hand sides (column-major, leading dimensions
+ * ldb, ldx >= n) with the handle's options (§4.1).  On NOT_CONVERGED/STAGNATION x
+ * holds the last iterate.  st (may be NULL) receives the statistics of the last
+ * column. */
+asss_status asss_solve(asss_handle* h, int nrhs, const double* b, int64_t ldb,
+                       double* x, int64_t ldx, asss_stats* st);
+
+/* Adjoint solve A^T lambda_j = g_j (the transposed system two-sidedly
+ * preconditioned with P^T = M~_r + I - J~, inner mrs on the transposed deflated
+ * system).  If x and dA are non-NULL, also dA[e] = -lambda_i x_j for every
+ * nonzero e = (i, j) of A (the gradient of a loss L with dL/dx = g with respect to
+ * A's values, on A's pattern); dA then has nnz(A) entries per right-hand side,
+ * column-major with leading dimension nnz(A). */
+asss_status asss_solve_adjoint(asss_handle* h, int nrhs, const double* g, int64_t ldg,
+                               double* lambda, int64_t ldl, const double* x, int64_t ldx,
+                               double* dA, asss_stats* st);
+
+/* Apply the outer operator A_cal v = W Abar S W v (transpose=0) or its transpose
+ * (transpose=1) to one vector of length n (§3 Eq. modified). */
+asss_status asss_apply_operator(asss_handle* h, int transpose, const double* v, double* out);
+
+/* Apply the preconditioner inverse P^-1 u (Eq. smw) or P^-T u, including one
+ * inner mrs solve; st->inner_its_total receives its iteration count. */
+asss_status asss_apply_preconditioner(asss_handle* h, int transpose, const double* u,
+                                      double* out, asss_stats* st);
+
+/* Copy set-up results out (any pointer may be NULL to skip it):
+ *  dr, dc, w, d: n values each; s_val: nnz(S) values of S on its pattern (CSR
+ *  order of the pattern); q: n x k_eff column-major Lanczos vectors; alpha: k_eff-1
+ *  values; neg: r indices.  k_eff and r are in asss_stats of the setup call. */
+asss_status asss_export(asss_handle* h, double* dr, double* dc, double* w, double* d,
+                        double* s_val, double* q, double* alpha, int32_t* neg);
+
+void asss_destroy(asss_handle* h);
+
+const char* asss_status_str(asss_status s);
+const char* asss_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Single steps of the path, each callable on its own.
+ * ------------------------------------------------------------------------ */
+
+/* The least-squares fit of §2 (Eq. regularized, App. A) for S on s_pattern given
+ * an already scaled matrix Abar.  s_val receives nnz(s_pattern) values in the
+ * pattern's CSR order.  Uses gamma, lls_tol, lls_maxit and stream from opt. */
+asss_status asss_skew_symmetrizer(const asss_csr* Abar, const asss_csr* s_pattern,
+                                  const asss_options* opt, double* s_val, asss_stats* st);
+
+/* k steps of skew-Lanczos (§3.2, Fig. 2) on the skew matrix J (values used as
+ * given) from start vector q1 (n values, need not be normalised).  q receives
+ * n x k_eff column-major vectors, alpha k_eff-1 values, *k_eff the number kept.
+ * reorth as in asss_options. */
+asss_status asss_skew_lanczos(const asss_csr* J, const double* q1, int k, int reorth,
+                              double* q, double* alpha, int* k_eff, void* stream);
+
+/* mrs (§3.1, App. B) on (shift I + sign*(J - Q S_k Q^T)) x = b for one right-hand
+ * side, where J is skew (not checked), Q is n x k column-major (k may be 0) and
+ * S_k the skew tridiagonal matrix with superdiagonal alpha (k-1 values).
+ * precision selects FP64 or FP32 storage and arithmetic (reductions in FP64).
+ * Stops when |g|/||b|| < tol or after maxit steps; *its and *ratio receive the
+ * step count and the final recursive residual ratio. */
+asss_status asss_mrs(const asss_csr* J, int k, const double* q, const double* alpha,
+                     double shift, double sign, const double* b, double* x, double tol,
+                     int maxit, int precision, int* its, double* ratio, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ASSS_H */

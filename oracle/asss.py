@@ -469,9 +469,10 @@ class AsssOracle:
         self.A = A
         n = A.shape[0]
         self.n = n
-        if S_pattern is None:
-            S_pattern = sp.csr_matrix((np.ones(A.nnz), A.indices, A.indptr), shape=A.shape)
         self.Abar, self.dr, self.dc, self.perm = equilibrate(A, row_perm, dr, dc)
+        if S_pattern is None:           # "having the sparsity of Abar" (§2)
+            Ab = self.Abar
+            S_pattern = sp.csr_matrix((np.ones(Ab.nnz), Ab.indices, Ab.indptr), shape=Ab.shape)
         self.S = skew_symmetrizer(self.Abar, S_pattern, gamma, lls_method)
         self.d, self.w, neg = shift_and_lowrank(self.Abar, self.S, zero_tol)
         self.prec2 = neg.size > r_max          # Eq. (preconditioner2) fallback

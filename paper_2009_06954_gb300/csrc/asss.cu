@@ -1,0 +1,1430 @@
+// C ABI of the library: set-up, solve, adjoint and single-step entry points.
+// Host code here only orders kernel launches and reads back the scalars that
+// decide control flow (convergence, breakdown); all arithmetic runs on the GPU.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+using namespace asss;
+
+namespace asss {
+
+// ---------------------------------------------------------------------------
+// small kernels used by the drivers below
+// ---------------------------------------------------------------------------
+__global__ void k_rowmax_abs(const int* rp, const double* v, int n, double* out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double m = 0.0;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) m = fmax(m, fabs(v[e]));
+    out[i] = m;
+}
+// column max of |dr_i a_ij| via atomicMax on the bit pattern (valid for x >= 0)
+__global__ void k_colmax_abs(const int* rp, const int* ci, const double* v, const double* dr, int n,
+                             unsigned long long* out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+        double a = fabs(dr[i] * v[e]);
+        atomicMax(&out[ci[e]], (unsigned long long)__double_as_longlong(a));
+    }
+}
+__global__ void k_recip_check(const double* in, int n, double* out, int* bad) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double v = in[i];
+    if (!(v > 0.0) || !isfinite(v)) {
+        atomicOr(bad, 1);
+        out[i] = 1.0;
+    } else {
+        out[i] = 1.0 / v;
+    }
+}
+// Abar row i = dr[perm[i]] * A row perm[i] * dc  (row lengths gathered first)
+__global__ void k_perm_rowlen(const int* rp, const int* perm, int n, int* len) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int r = perm ? perm[i] : i;
+    len[i] = rp[r + 1] - rp[r];
+}
+__global__ void k_perm_scale_rows(const int* rp, const int* ci, const double* v, const int* perm, const double* dr,
+                                  const double* dc, int n, const int* orp, int* oci, double* ov) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int r = perm ? perm[i] : i;
+    int o = orp[i];
+    double f = dr[r];
+    for (int e = rp[r]; e < rp[r + 1]; ++e, ++o) {
+        oci[o] = ci[e];
+        ov[o] = f * v[e] * dc[ci[e]];
+    }
+}
+__global__ void k_check_perm(const int* perm, int n, int* seen, int* bad) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int r = perm[i];
+    if (r < 0 || r >= n || atomicAdd(&seen[r], 1) != 0) atomicOr(bad, 1);
+}
+// d = C on the diagonal of P; W = |d|^-1/2; zero-pivot flag
+__global__ void k_diag_w(const double* C, const int* diagpos, int n, double* d, double* w) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double v = C[diagpos[i]];
+    d[i] = v;
+    w[i] = (v != 0.0) ? 1.0 / sqrt(fabs(v)) : 0.0;
+}
+__global__ void k_absmax(const double* a, int n, unsigned long long* out) {
+    double m = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) m = fmax(m, fabs(a[i]));
+    atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+__global__ void k_zero_pivots(const double* d, int n, double thr, int* cnt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && fabs(d[i]) < thr) atomicAdd(cnt, 1);
+}
+__global__ void k_neg_flag(const double* d, int n, int* flag) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flag[i] = d[i] < 0.0 ? 1 : 0;
+}
+__global__ void k_neg_compact(const int* flag, const int* pos, int n, int* neg) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && flag[i]) neg[pos[i]] = i;
+}
+// J~ on P: for upper k, v = (C_ij - C_ji)/2 w_i w_j at k and -v at the mirror; 0 on the diagonal
+__global__ void k_assemble_jt(int n, const int* prp, const int* pci, const int* mirror, const double* C,
+                              const double* w, double* jt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int k = prp[i]; k < prp[i + 1]; ++k) {
+        int j = pci[k];
+        if (j == i) {
+            jt[k] = 0.0;
+        } else if (j > i && mirror[k] >= 0) {
+            double v = 0.5 * (C[k] - C[mirror[k]]) * w[i] * w[j];
+            jt[k] = v;
+            jt[mirror[k]] = -v;
+        }
+    }
+}
+__global__ void k_scale_rows(const int* rp, double* v, const double* s, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) v[e] *= s[i];
+}
+__global__ void k_scale_cols(const int* rp, const int* ci, double* v, const double* s, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) v[e] *= s[ci[e]];
+}
+__global__ void k_f2d(const float* a, double* b, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (double)a[i];
+}
+__global__ void k_gather_neg(const double* z, const int* neg, int r, double* out) {
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < r) out[a] = z[neg[a]];
+}
+__global__ void k_unit(double* y, int n, int idx) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (i == idx) ? 1.0 : 0.0;
+}
+// rows k..m-1 of G = U_bar^T X are rows neg[a] of X
+__global__ void k_gram_neg_rows(const double* X, int n, int m, const int* neg, int k, int r, double* G) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= r * m) return;
+    int a = t / m, c = t % m;
+    G[(size_t)(k + a) * m + c] = X[(size_t)c * n + neg[a]];
+}
+// Sig_bar (m x m row-major) = blkdiag(S_k, -2 I_r), transposed if tr
+__global__ void k_sigma(const double* alpha, int k, int m, int tr, double* Sig) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m * m) return;
+    int a = t / m, b = t % m;
+    double v = 0.0;
+    if (a < k && b < k) {
+        if (b == a + 1) v = alpha[a];
+        if (a == b + 1) v = -alpha[b];
+    } else if (a >= k && a == b) {
+        v = -2.0;
+    }
+    if (tr) {
+        // transpose: swap the roles
+        double u = 0.0;
+        int aa = b, bb = a;
+        if (aa < k && bb < k) {
+            if (bb == aa + 1) u = alpha[aa];
+            if (aa == bb + 1) u = -alpha[bb];
+        } else if (aa >= k && aa == bb) {
+            u = -2.0;
+        }
+        v = u;
+    }
+    Sig[t] = v;
+}
+// C = (I if add_identity) + A B for m x m row-major matrices (one thread per entry)
+__global__ void k_small_mm(const double* A, const double* B, int m, int add_identity, double* C) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m * m) return;
+    int a = t / m, c = t % m;
+    double acc = (add_identity && a == c) ? 1.0 : 0.0;
+    for (int b = 0; b < m; ++b) acc += A[a * m + b] * B[b * m + c];
+    C[t] = acc;
+}
+// Y (n x m row-major) = X (n x m col-major) Z (m x m row-major)
+__global__ void k_x_times_small(const double* X, const double* Z, int n, int m, double* Y) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * m) return;
+    int i = (int)(t / m), c = (int)(t % m);
+    double acc = 0.0;
+    for (int b = 0; b < m; ++b) acc += X[(size_t)b * n + i] * Z[b * m + c];
+    Y[t] = acc;
+}
+// w -= V h (V n x p col-major)
+__global__ void k_sub_colmajor(const double* V, int ldv, int p, const double* h, int n, double* w) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double acc = 0.0;
+    for (int a = 0; a < p; ++a) acc += V[(size_t)a * ldv + i] * h[a];
+    w[i] -= acc;
+}
+__global__ void k_add(double* h, const double* h2, int p) {
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < p) h[a] += h2[a];
+}
+// refinement helpers
+__global__ void k_to_scaled_fwd(const double* r, const double* dr, const double* w, const int* perm, int n,
+                                double* out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int p = perm ? perm[i] : i;
+    out[i] = w[i] * dr[p] * r[p];
+}
+__global__ void k_from_scaled_adj(const double* dmu, const double* dr, const double* w, const int* perm, int n,
+                                  double* lam) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int p = perm ? perm[i] : i;
+    lam[p] += dr[p] * w[i] * dmu[i];
+}
+__global__ void k_axpy_mul(double* x, const double* a, const double* b, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] += a[i] * b[i];
+}
+__global__ void k_sub(const double* b, const double* t, double* r, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) r[i] = b[i] - t[i];
+}
+__global__ void k_grad_A(const int* rp, const int* ci, const double* lam, const double* x, int n, double* dA) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double l = lam[i];
+    for (int e = rp[i]; e < rp[i + 1]; ++e) dA[e] = -l * x[ci[e]];
+}
+
+// ---------------------------------------------------------------------------
+// TFQMR / FGMRES device scalar kernels
+// ---------------------------------------------------------------------------
+// scalar slots of TFQMR
+enum { TF_TAU = 0, TF_THETA, TF_ETA, TF_RHO, TF_ALPHA, TF_SIGMA, TF_WN2, TF_RHON, TF_BETA, TF_BREAK, TF_NSC };
+
+__global__ void k_tf_init(double* T, const double* rr) {
+    T[TF_TAU] = sqrt(*rr);
+    T[TF_THETA] = 0.0;
+    T[TF_ETA] = 0.0;
+    T[TF_RHO] = *rr;
+    T[TF_BREAK] = 0.0;
+}
+__global__ void k_tf_alpha(double* T) {
+    double sg = T[TF_SIGMA];
+    if (sg == 0.0 || T[TF_RHO] == 0.0) {
+        T[TF_BREAK] = 1.0;
+        T[TF_ALPHA] = 0.0;
+    } else {
+        T[TF_ALPHA] = T[TF_RHO] / sg;
+    }
+}
+// w -= alpha Bu ; d = ut + (theta^2 eta / alpha) d
+__global__ void k_tf_wd(double* w, const double* Bu, double* d, const double* ut, const double* T, int n) {
+    double a = T[TF_ALPHA];
+    double coef = (a != 0.0) ? T[TF_THETA] * T[TF_THETA] * T[TF_ETA] / a : 0.0;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    w[i] -= a * Bu[i];
+    d[i] = ut[i] + coef * d[i];
+}
+__global__ void k_tf_theta(double* T) {
+    double th = sqrt(T[TF_WN2]) / T[TF_TAU];
+    double c = 1.0 / sqrt(1.0 + th * th);
+    T[TF_THETA] = th;
+    T[TF_TAU] = T[TF_TAU] * th * c;
+    T[TF_ETA] = c * c * T[TF_ALPHA];
+}
+__global__ void k_tf_beta(double* T) {
+    double rn = T[TF_RHON];
+    if (T[TF_RHO] == 0.0) {
+        T[TF_BREAK] = 1.0;
+        T[TF_BETA] = 0.0;
+    } else {
+        T[TF_BETA] = rn / T[TF_RHO];
+    }
+    T[TF_RHO] = rn;
+}
+__global__ void k_tf_uminus(double* u, const double* v, const double* T, int n) {
+    double a = T[TF_ALPHA];
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) u[i] -= a * v[i];
+}
+__global__ void k_tf_axpy_eta(double* x, const double* d, const double* T, int n) {
+    double e = T[TF_ETA];
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] += e * d[i];
+}
+__global__ void k_tf_unew(double* u, const double* w, const double* T, int n) {
+    double b = T[TF_BETA];
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) u[i] = w[i] + b * u[i];
+}
+__global__ void k_tf_vnew(double* v, const double* Bue, const double* Buo, const double* T, int n) {
+    double b = T[TF_BETA];
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = Bue[i] + b * (Buo[i] + b * v[i]);
+}
+
+// FGMRES: H (m+1) x m column-major, cs, sn, g (m+1)
+__global__ void k_fg_init(double* g, int m, const double* rr, double* inv) {
+    double b = sqrt(*rr);
+    for (int a = 0; a <= m; ++a) g[a] = 0.0;
+    g[0] = b;
+    *inv = (b > 0.0) ? 1.0 / b : 0.0;
+}
+__global__ void k_fg_column(double* H, double* cs, double* sn, double* g, const double* h, const double* h2,
+                            const double* hn2, int j, int m, double* inv_hn) {
+    double* col = H + (size_t)j * (m + 1);
+    for (int a = 0; a <= j; ++a) col[a] = h[a] + h2[a];
+    double hn = sqrt(*hn2);
+    col[j + 1] = hn;
+    for (int a = 0; a < j; ++a) {
+        double t = cs[a] * col[a] + sn[a] * col[a + 1];
+        col[a + 1] = -sn[a] * col[a] + cs[a] * col[a + 1];
+        col[a] = t;
+    }
+    double rr = hypot(col[j], col[j + 1]);
+    double c = (rr != 0.0) ? col[j] / rr : 1.0;
+    double s = (rr != 0.0) ? col[j + 1] / rr : 0.0;
+    cs[j] = c;
+    sn[j] = s;
+    col[j] = rr;
+    col[j + 1] = 0.0;
+    g[j + 1] = -s * g[j];
+    g[j] = c * g[j];
+    *inv_hn = (hn > 0.0) ? 1.0 / hn : 0.0;
+}
+__global__ void k_fg_backsolve(const double* H, const double* g, int steps, int m, double* y) {
+    for (int a = steps - 1; a >= 0; --a) {
+        double acc = g[a];
+        for (int b = a + 1; b < steps; ++b) acc -= H[(size_t)b * (m + 1) + a] * y[b];
+        y[a] = acc / H[(size_t)a * (m + 1) + a];
+    }
+}
+__global__ void k_scale_dev(double* y, const double* x, const double* s, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (*s) * x[i];
+}
+
+}  // namespace asss
+
+// ===========================================================================
+// the handle
+// ===========================================================================
+struct SmwData {
+    bool ready = false;
+    int m = 0;
+    DBuf<double> Y;  // n x m row-major: X Sig (I + U^T X Sig)^-1
+};
+
+struct asss_handle {
+    asss_options opt;
+    Ctx ctx;
+    int n = 0;
+    DCsr A;            // original matrix (residuals)
+    DCsr AT;           // A^T (adjoint residuals), lazily
+    DCsr Abar, AbarT;
+    DCsr S;            // S with values (pattern = s_pattern)
+    DCsr ST;           // S^T with values, lazily (adjoint)
+    DCsr Aw, Sw;       // W Abar, S W (outer operator)
+    DCsr AwT, SwT;     // lazily (adjoint)
+    DCsr Jt;           // J~ on P (FP64)
+    DSell<double> J64;
+    DSell<float> J32;
+    DBuf<double> dr, dc, w, d;
+    DBuf<int> perm;
+    bool has_perm = false;
+    DBuf<int> neg;
+    int r = 0;
+    int prec2 = 0;
+    int k = 0, kp = 0;
+    DBuf<double> Qcm;   // n x k column-major
+    DBuf<double> Q64;   // n x kp row-major
+    DBuf<float> Q32;
+    DBuf<double> alpha_d;
+    std::vector<double> alpha_h;
+    SmwData smw[2];
+    MrsWork* mw = nullptr;
+    // work vectors
+    DBuf<double> t1, t2, t3, zt, wv, scal;
+    DBuf<float> z32;
+    // statistics of the current solve
+    long long inner_total = 0;
+    int inner_solves = 0;
+    asss_stats setup_stats;
+    ~asss_handle() {
+        if (mw) mrs_work_destroy(mw);
+    }
+};
+
+static void fill_defaults(asss_options* o) {
+    memset(o, 0, sizeof(*o));
+    o->gamma = 1.0;
+    o->k_lanczos = 20;
+    o->reorth = 1;
+    o->inner_tol = 1e-10;
+    o->setup_tol = 0.0;
+    o->outer_tol = 1e-8;
+    o->inner_maxit = 1000;
+    o->outer_maxit = 2000;
+    o->restart = 60;
+    o->precision = ASSS_PREC_FP64;
+    o->outer = ASSS_OUTER_TFQMR;
+    o->r_max = 256;
+    o->seed = 0x5eedull;
+    o->lls_tol = 1e-13;
+    o->lls_maxit = 20000;
+    o->zero_tol = 1e-14;
+    o->wait_timeout_ms = 2000.0;
+    o->stream = nullptr;
+}
+
+static int pick_kp(int k) {
+    const int opts[] = {0, 4, 8, 12, 16, 20, 24, 32, 48, 64};
+    for (int v : opts)
+        if (v >= k) return v;
+    return -1;
+}
+
+// ---------------------------------------------------------------------------
+// skew-Lanczos (Fig. 2) with optional two-pass classical Gram-Schmidt
+// ---------------------------------------------------------------------------
+static asss_status lanczos(const Ctx& c, const DCsr& J, const double* q1, int n, int k, int reorth,
+                           DBuf<double>& Qcm, std::vector<double>& alpha, int* k_eff) {
+    cudaStream_t s = c.stream;
+    if (k > n) k = n;
+    alpha.assign(k > 1 ? k - 1 : 0, 0.0);
+    *k_eff = 0;
+    if (k <= 0) return ASSS_OK;
+    ASSS_TRY(Qcm.alloc((int64_t)n * k));
+    DBuf<double> z, h, h2, sc;
+    ASSS_TRY(z.alloc(n));
+    ASSS_TRY(h.alloc(k));
+    ASSS_TRY(h2.alloc(k));
+    ASSS_TRY(sc.alloc(1));
+    ASSS_TRY(dot(q1, q1, n, sc.p, s));
+    double nn = 0.0;
+    ASSS_CUDA(cudaMemcpyAsync(&nn, sc.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+    ASSS_CUDA(cudaStreamSynchronize(s));
+    if (!(nn > 0.0)) {
+        set_error("Lanczos start vector is zero");
+        return ASSS_ERR_ARG;
+    }
+    ASSS_TRY(vscale(Qcm.p, q1, 1.0 / sqrt(nn), n, s));
+    int kk = 1;
+    for (int i = 1; i < k; ++i) {
+        ASSS_TRY(spmv(J, Qcm.p + (size_t)(i - 1) * n, z.p, nullptr, s));
+        if (i >= 2) ASSS_TRY(vaxpy(z.p, Qcm.p + (size_t)(i - 2) * n, -alpha[i - 2], n, s));
+        if (reorth) {
+            for (int pass = 0; pass < 2; ++pass) {
+                ASSS_TRY(gram(Qcm.p, n, i, z.p, n, 1, n, h.p, s));
+                k_sub_colmajor<<<cdiv(n, 256), 256, 0, s>>>(Qcm.p, n, i, h.p, n, z.p);
+                ASSS_CHECK_LAUNCH();
+            }
+        }
+        ASSS_TRY(dot(z.p, z.p, n, sc.p, s));
+        ASSS_CUDA(cudaMemcpyAsync(&nn, sc.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+        ASSS_CUDA(cudaStreamSynchronize(s));
+        double a = sqrt(nn);
+        if (a == 0.0 || (i >= 2 && a <= 1e-12 * alpha[0])) break;
+        alpha[i - 1] = a;
+        ASSS_TRY(vscale(Qcm.p + (size_t)i * n, z.p, -1.0 / a, n, s));
+        kk = i + 1;
+    }
+    alpha.resize(kk - 1);
+    *k_eff = kk;
+    return ASSS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// preconditioner pieces
+// ---------------------------------------------------------------------------
+static asss_status ensure_smw(asss_handle* h, int tr) {
+    SmwData& S = h->smw[tr];
+    if (S.ready) return ASSS_OK;
+    const Ctx& c = h->ctx;
+    cudaStream_t s = c.stream;
+    int n = h->n, k = h->k, r = h->r, m = k + r;
+    S.m = m;
+    if (m == 0) {
+        S.ready = true;
+        return ASSS_OK;
+    }
+    DBuf<double> X, rhs, G, Sig, K, Z;
+    ASSS_TRY(X.alloc((int64_t)n * m));
+    ASSS_TRY(rhs.alloc(n));
+    MrsOperator op;
+    op.J64 = &h->J64;
+    op.k = h->k;
+    op.kp = h->kp;
+    op.Q64 = h->Q64.p;
+    op.alpha = h->alpha_d.p;
+    double tol = h->opt.setup_tol > 0 ? h->opt.setup_tol : h->opt.inner_tol;
+    double sign = tr ? -1.0 : 1.0;
+    std::vector<int> negh(r);
+    if (r) ASSS_CUDA(cudaMemcpy(negh.data(), h->neg.p, sizeof(int) * r, cudaMemcpyDeviceToHost));
+    for (int col = 0; col < m; ++col) {
+        const double* b;
+        if (col < k) {
+            b = h->Qcm.p + (size_t)col * n;
+        } else {
+            k_unit<<<cdiv(n, 256), 256, 0, s>>>(rhs.p, n, negh[col - k]);
+            ASSS_CHECK_LAUNCH();
+            b = rhs.p;
+        }
+        MrsResult res;
+        ASSS_TRY(mrs_solve(c, h->mw, op, false, 1.0, sign, b, X.p + (size_t)col * n, nullptr, tol,
+                           h->opt.inner_maxit, &res, true));
+    }
+    ASSS_TRY(G.alloc((int64_t)m * m));
+    ASSS_TRY(Sig.alloc((int64_t)m * m));
+    ASSS_TRY(K.alloc((int64_t)m * m));
+    ASSS_TRY(Z.alloc((int64_t)m * m));
+    if (k) ASSS_TRY(gram(h->Qcm.p, n, k, X.p, n, m, n, G.p, s));
+    if (r) {
+        k_gram_neg_rows<<<cdiv(r * m, 256), 256, 0, s>>>(X.p, n, m, h->neg.p, k, r, G.p);
+        ASSS_CHECK_LAUNCH();
+    }
+    k_sigma<<<cdiv(m * m, 256), 256, 0, s>>>(h->alpha_d.p, k, m, tr, Sig.p);
+    ASSS_CHECK_LAUNCH();
+    k_small_mm<<<cdiv(m * m, 256), 256, 0, s>>>(G.p, Sig.p, m, 1, K.p);  // K = I + (U^T X) Sig
+    ASSS_CHECK_LAUNCH();
+    int singular = 0;
+    ASSS_TRY(small_inverse(K.p, m, &singular, s));
+    if (singular) {
+        set_error("the SMW matrix I + U^T S_bar^-1 U Sig is singular");
+        return ASSS_ERR_BREAKDOWN;
+    }
+    k_small_mm<<<cdiv(m * m, 256), 256, 0, s>>>(Sig.p, K.p, m, 0, Z.p);  // Z = Sig K^-1
+    ASSS_CHECK_LAUNCH();
+    ASSS_TRY(S.Y.alloc((int64_t)n * m));
+    k_x_times_small<<<cdiv((int64_t)n * m, 256), 256, 0, s>>>(X.p, Z.p, n, m, S.Y.p);
+    ASSS_CHECK_LAUNCH();
+    ASSS_CUDA(cudaStreamSynchronize(s));
+    S.ready = true;
+    return ASSS_OK;
+}
+
+// out = P^-1 u (tr = 0) or P^-T u (tr = 1): z = S_bar^-1 u by mrs, then SMW (Eq. smw)
+static asss_status apply_prec(asss_handle* h, int tr, const double* u, double* out, int* its_out) {
+    const Ctx& c = h->ctx;
+    cudaStream_t s = c.stream;
+    int n = h->n;
+    ASSS_TRY(ensure_smw(h, tr));
+    MrsOperator op;
+    op.J64 = &h->J64;
+    op.J32 = h->J32.n ? &h->J32 : nullptr;
+    op.k = h->k;
+    op.kp = h->kp;
+    op.Q64 = h->Q64.p;
+    op.Q32 = h->Q32.p;
+    op.alpha = h->alpha_d.p;
+    bool fp32 = h->opt.precision == ASSS_PREC_MIXED;
+    double sign = tr ? -1.0 : 1.0;
+    SmwData& S = h->smw[tr];
+    double* z = (S.m > 0) ? h->zt.p : out;
+    MrsResult res;
+    if (fp32) {
+        ASSS_TRY(mrs_solve(c, h->mw, op, true, 1.0, sign, u, nullptr, h->z32.p, h->opt.inner_tol, h->opt.inner_maxit,
+                           &res, true));
+        k_f2d<<<cdiv(n, 256), 256, 0, s>>>(h->z32.p, z, n);
+        ASSS_CHECK_LAUNCH();
+    } else {
+        ASSS_TRY(mrs_solve(c, h->mw, op, false, 1.0, sign, u, z, nullptr, h->opt.inner_tol, h->opt.inner_maxit, &res,
+                           true));
+    }
+    h->inner_total += res.its;
+    h->inner_solves += 1;
+    if (its_out) *its_out = res.its;
+    if (S.m > 0) {
+        if (h->k) ASSS_TRY(gram(h->Qcm.p, n, h->k, z, n, 1, n, h->wv.p, s));
+        if (h->r) {
+            k_gather_neg<<<cdiv(h->r, 128), 128, 0, s>>>(z, h->neg.p, h->r, h->wv.p + h->k);
+            ASSS_CHECK_LAUNCH();
+        }
+        ASSS_TRY(sub_rowmajor_gemv(S.Y.p, S.m, h->wv.p, z, n, out, s));
+    }
+    return ASSS_OK;
+}
+
+static asss_status ensure_adjoint_ops(asss_handle* h) {
+    cudaStream_t s = h->ctx.stream;
+    if (!h->AwT.nnz && h->Aw.nnz) ASSS_TRY(transpose_csr(h->Aw, h->AwT, nullptr, s));
+    if (!h->SwT.nnz && h->Sw.nnz) ASSS_TRY(transpose_csr(h->Sw, h->SwT, nullptr, s));
+    if (!h->ST.nnz && h->S.nnz) ASSS_TRY(transpose_csr(h->S, h->ST, nullptr, s));
+    if (!h->AT.nnz && h->A.nnz) ASSS_TRY(transpose_csr(h->A, h->AT, nullptr, s));
+    return ASSS_OK;
+}
+
+// out = A_cal v or A_cal^T v
+static asss_status apply_op(asss_handle* h, int tr, const double* v, double* out) {
+    cudaStream_t s = h->ctx.stream;
+    if (!tr) {
+        ASSS_TRY(spmv(h->Sw, v, h->t3.p, nullptr, s));
+        ASSS_TRY(spmv(h->Aw, h->t3.p, out, nullptr, s));
+    } else {
+        ASSS_TRY(ensure_adjoint_ops(h));
+        ASSS_TRY(spmv(h->AwT, v, h->t3.p, nullptr, s));
+        ASSS_TRY(spmv(h->SwT, h->t3.p, out, nullptr, s));
+    }
+    return ASSS_OK;
+}
+
+static double read_scalar(const double* d, cudaStream_t s, asss_status* st) {
+    double v = 0.0;
+    cudaError_t e = cudaMemcpyAsync(&v, d, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        set_error("scalar read-back failed: %s", cudaGetErrorString(e));
+        *st = ASSS_ERR_CUDA;
+    }
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// one TFQMR run (Freund 1993), right preconditioned, from zero: op(M^-1 u) = r
+// ---------------------------------------------------------------------------
+struct KrylovWork {
+    int n = 0, m = 0;
+    DBuf<double> w, u, ut, v, Bue, Buo, d, rstar;
+    DBuf<double> V, Z, H, cs, sn, g, hv, hv2, y;
+    DBuf<double> T;
+    asss_status init(int n_, int m_, int outer) {
+        n = n_;
+        m = m_;
+        ASSS_TRY(T.alloc(32));
+        if (outer == ASSS_OUTER_TFQMR) {
+            ASSS_TRY(w.alloc(n));
+            ASSS_TRY(u.alloc(n));
+            ASSS_TRY(ut.alloc(n));
+            ASSS_TRY(v.alloc(n));
+            ASSS_TRY(Bue.alloc(n));
+            ASSS_TRY(Buo.alloc(n));
+            ASSS_TRY(d.alloc(n));
+            ASSS_TRY(rstar.alloc(n));
+        } else {
+            ASSS_TRY(V.alloc((int64_t)n * (m + 1)));
+            ASSS_TRY(Z.alloc((int64_t)n * m));
+            ASSS_TRY(H.alloc((int64_t)(m + 1) * m));
+            ASSS_TRY(cs.alloc(m + 1));
+            ASSS_TRY(sn.alloc(m + 1));
+            ASSS_TRY(g.alloc(m + 2));
+            ASSS_TRY(hv.alloc(m + 1));
+            ASSS_TRY(hv2.alloc(m + 1));
+            ASSS_TRY(y.alloc(m + 1));
+            ASSS_TRY(w.alloc(n));
+        }
+        return ASSS_OK;
+    }
+};
+
+static asss_status tfqmr_cycle(asss_handle* h, KrylovWork& kw, int tr, const double* r, double eta, int max_steps,
+                               double* delta, int* steps_out, int* napp_out) {
+    cudaStream_t s = h->ctx.stream;
+    int n = h->n;
+    int nb = cdiv(n, 256);
+    asss_status st = ASSS_OK;
+    double* T = kw.T.p;
+    ASSS_CUDA(cudaMemsetAsync(delta, 0, sizeof(double) * n, s));
+    ASSS_TRY(dot(r, r, n, T + TF_WN2, s));
+    double rr = read_scalar(T + TF_WN2, s, &st);
+    ASSS_TRY(st);
+    *steps_out = 0;
+    *napp_out = 0;
+    if (rr == 0.0) return ASSS_OK;
+    double target = eta * sqrt(rr);
+    ASSS_TRY(vcopy(kw.w.p, r, n, s));
+    ASSS_TRY(vcopy(kw.u.p, r, n, s));
+    ASSS_TRY(vcopy(kw.rstar.p, r, n, s));
+    ASSS_CUDA(cudaMemsetAsync(kw.d.p, 0, sizeof(double) * n, s));
+    k_tf_init<<<1, 1, 0, s>>>(T, T + TF_WN2);
+    ASSS_CHECK_LAUNCH();
+    ASSS_TRY(apply_prec(h, tr, kw.u.p, kw.ut.p, nullptr));
+    *napp_out += 1;
+    ASSS_TRY(apply_op(h, tr, kw.ut.p, kw.v.p));
+    ASSS_TRY(vcopy(kw.Bue.p, kw.v.p, n, s));
+    int mcount = 0;
+    for (int step = 1; step <= max_steps; ++step) {
+        ASSS_TRY(dot(kw.rstar.p, kw.v.p, n, T + TF_SIGMA, s));
+        k_tf_alpha<<<1, 1, 0, s>>>(T);
+        ASSS_CHECK_LAUNCH();
+        for (int half = 0; half < 2; ++half) {
+            const double* Bu;
+            if (half == 0) {
+                Bu = kw.Bue.p;
+            } else {
+                k_tf_uminus<<<nb, 256, 0, s>>>(kw.u.p, kw.v.p, T, n);
+                ASSS_CHECK_LAUNCH();
+                ASSS_TRY(apply_prec(h, tr, kw.u.p, kw.ut.p, nullptr));
+                *napp_out += 1;
+                ASSS_TRY(apply_op(h, tr, kw.ut.p, kw.Buo.p));
+                Bu = kw.Buo.p;
+            }
+            k_tf_wd<<<nb, 256, 0, s>>>(kw.w.p, Bu, kw.d.p, kw.ut.p, T, n);
+            ASSS_CHECK_LAUNCH();
+            ASSS_TRY(dot(kw.w.p, kw.w.p, n, T + TF_WN2, s));
+            k_tf_theta<<<1, 1, 0, s>>>(T);
+            ASSS_CHECK_LAUNCH();
+            k_tf_axpy_eta<<<nb, 256, 0, s>>>(delta, kw.d.p, T, n);
+            ASSS_CHECK_LAUNCH();
+            ++mcount;
+            double hostT[TF_NSC];
+            ASSS_CUDA(cudaMemcpyAsync(hostT, T, sizeof(hostT), cudaMemcpyDeviceToHost, s));
+            ASSS_CUDA(cudaStreamSynchronize(s));
+            if (hostT[TF_BREAK] != 0.0) {
+                *steps_out = step - 1;
+                return ASSS_OK;
+            }
+            if (hostT[TF_TAU] * sqrt(mcount + 1.0) <= target) {
+                *steps_out = step;
+                return ASSS_OK;
+            }
+        }
+        ASSS_TRY(dot(kw.rstar.p, kw.w.p, n, T + TF_RHON, s));
+        k_tf_beta<<<1, 1, 0, s>>>(T);
+        ASSS_CHECK_LAUNCH();
+        k_tf_unew<<<nb, 256, 0, s>>>(kw.u.p, kw.w.p, T, n);
+        ASSS_CHECK_LAUNCH();
+        ASSS_TRY(apply_prec(h, tr, kw.u.p, kw.ut.p, nullptr));
+        *napp_out += 1;
+        ASSS_TRY(apply_op(h, tr, kw.ut.p, kw.Bue.p));
+        k_tf_vnew<<<nb, 256, 0, s>>>(kw.v.p, kw.Bue.p, kw.Buo.p, T, n);
+        ASSS_CHECK_LAUNCH();
+        *steps_out = step;
+    }
+    return ASSS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// one cycle of flexible GMRES(m) (Saad 1993) with two classical Gram-Schmidt passes
+// ---------------------------------------------------------------------------
+static asss_status fgmres_cycle(asss_handle* h, KrylovWork& kw, int tr, const double* r, double eta, int m,
+                                double* delta, int* steps_out, int* napp_out) {
+    cudaStream_t s = h->ctx.stream;
+    int n = h->n;
+    int M = kw.m;
+    if (m > M) m = M;
+    asss_status st = ASSS_OK;
+    double* T = kw.T.p;  // 0: rr, 1: inv, 2: hn2, 3: inv_hn
+    ASSS_TRY(dot(r, r, n, T, s));
+    k_fg_init<<<1, 1, 0, s>>>(kw.g.p, M, T, T + 1);
+    ASSS_CHECK_LAUNCH();
+    double rr = read_scalar(T, s, &st);
+    ASSS_TRY(st);
+    *steps_out = 0;
+    *napp_out = 0;
+    ASSS_CUDA(cudaMemsetAsync(delta, 0, sizeof(double) * n, s));
+    if (rr == 0.0) return ASSS_OK;
+    double beta0 = sqrt(rr);
+    k_scale_dev<<<cdiv(n, 256), 256, 0, s>>>(kw.V.p, r, T + 1, n);
+    ASSS_CHECK_LAUNCH();
+    int steps = 0;
+    for (int j = 0; j < m; ++j) {
+        double* vj = kw.V.p + (size_t)j * n;
+        double* zj = kw.Z.p + (size_t)j * n;
+        ASSS_TRY(apply_prec(h, tr, vj, zj, nullptr));
+        *napp_out += 1;
+        ASSS_TRY(apply_op(h, tr, zj, kw.w.p));
+        ASSS_TRY(gram(kw.V.p, n, j + 1, kw.w.p, n, 1, n, kw.hv.p, s));
+        k_sub_colmajor<<<cdiv(n, 256), 256, 0, s>>>(kw.V.p, n, j + 1, kw.hv.p, n, kw.w.p);
+        ASSS_CHECK_LAUNCH();
+        ASSS_TRY(gram(kw.V.p, n, j + 1, kw.w.p, n, 1, n, kw.hv2.p, s));
+        k_sub_colmajor<<<cdiv(n, 256), 256, 0, s>>>(kw.V.p, n, j + 1, kw.hv2.p, n, kw.w.p);
+        ASSS_CHECK_LAUNCH();
+        ASSS_TRY(dot(kw.w.p, kw.w.p, n, T + 2, s));
+        k_fg_column<<<1, 1, 0, s>>>(kw.H.p, kw.cs.p, kw.sn.p, kw.g.p, kw.hv.p, kw.hv2.p, T + 2, j, M, T + 3);
+        ASSS_CHECK_LAUNCH();
+        steps = j + 1;
+        double hostv[2];
+        ASSS_CUDA(cudaMemcpyAsync(&hostv[0], kw.g.p + j + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+        ASSS_CUDA(cudaMemcpyAsync(&hostv[1], T + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+        ASSS_CUDA(cudaStreamSynchronize(s));
+        if (hostv[1] == 0.0 || fabs(hostv[0]) <= eta * beta0) break;
+        k_scale_dev<<<cdiv(n, 256), 256, 0, s>>>(kw.V.p + (size_t)(j + 1) * n, kw.w.p, T + 3, n);
+        ASSS_CHECK_LAUNCH();
+    }
+    k_fg_backsolve<<<1, 1, 0, s>>>(kw.H.p, kw.g.p, steps, M, kw.y.p);
+    ASSS_CHECK_LAUNCH();
+    ASSS_TRY(colmajor_gemv(kw.Z.p, n, steps, kw.y.p, n, 0.0, delta, s));
+    *steps_out = steps;
+    return ASSS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// refinement loop on the true FP64 residual of the original system (§4.1 stop)
+// ---------------------------------------------------------------------------
+static asss_status refine(asss_handle* h, int tr, const double* rhs, double* x, asss_stats* st) {
+    cudaStream_t s = h->ctx.stream;
+    int n = h->n;
+    int nb = cdiv(n, 256);
+    const asss_options& o = h->opt;
+    asss_status es = ASSS_OK;
+    KrylovWork kw;
+    ASSS_TRY(kw.init(n, o.restart > 0 ? o.restart : 60, o.outer));
+    DBuf<double> r, rh, dy, scal;
+    ASSS_TRY(r.alloc(n));
+    ASSS_TRY(rh.alloc(n));
+    ASSS_TRY(dy.alloc(n));
+    ASSS_TRY(scal.alloc(2));
+    h->inner_total = 0;
+    h->inner_solves = 0;
+    ASSS_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    ASSS_TRY(vcopy(r.p, rhs, n, s));
+    ASSS_TRY(dot(rhs, rhs, n, scal.p, s));
+    double bn = sqrt(read_scalar(scal.p, s, &es));
+    ASSS_TRY(es);
+    st->outer_its = 0;
+    st->cycles = 0;
+    st->relres = 0.0;
+    st->status = ASSS_OK;
+    if (tr) ASSS_TRY(ensure_adjoint_ops(h));
+    if (bn == 0.0) return ASSS_OK;
+    double best = INFINITY;
+    int stall = 0;
+    int* perm = h->has_perm ? h->perm.p : nullptr;
+    while (true) {
+        ASSS_TRY(dot(r.p, r.p, n, scal.p, s));
+        double rn = sqrt(read_scalar(scal.p, s, &es));
+        ASSS_TRY(es);
+        st->relres = rn / bn;
+        if (rn / bn <= o.outer_tol) break;
+        if (!(rn == rn)) {
+            st->status = ASSS_ERR_BREAKDOWN;
+            set_error("residual became NaN");
+            break;
+        }
+        if (st->outer_its >= o.outer_maxit) {
+            st->status = ASSS_ERR_NOT_CONVERGED;
+            break;
+        }
+        if (rn < 0.999 * best) {
+            best = rn;
+            stall = 0;
+        } else if (++stall >= 5) {
+            st->status = ASSS_ERR_STAGNATION;
+            break;
+        }
+        if (!tr) {
+            k_to_scaled_fwd<<<nb, 256, 0, s>>>(r.p, h->dr.p, h->w.p, perm, n, rh.p);  // W P D_r r
+            ASSS_CHECK_LAUNCH();
+        } else {
+            ASSS_TRY(vmul(h->t1.p, h->dc.p, r.p, n, s));  // W S^T D_c r
+            ASSS_TRY(spmv(h->ST, h->t1.p, h->t2.p, nullptr, s));
+            ASSS_TRY(vmul(rh.p, h->w.p, h->t2.p, n, s));
+        }
+        double eta = fmin(0.5, 0.5 * o.outer_tol * bn / rn);
+        int budget = o.outer_maxit - st->outer_its;
+        int steps = 0, napp = 0;
+        if (o.outer == ASSS_OUTER_TFQMR) {
+            ASSS_TRY(tfqmr_cycle(h, kw, tr, rh.p, eta, budget, dy.p, &steps, &napp));
+        } else {
+            int m = o.restart < budget ? o.restart : budget;
+            ASSS_TRY(fgmres_cycle(h, kw, tr, rh.p, eta, m, dy.p, &steps, &napp));
+        }
+        st->outer_its += steps;
+        st->cycles += 1;
+        if (!tr) {
+            ASSS_TRY(vmul(h->t1.p, h->w.p, dy.p, n, s));  // x += D_c S W dy
+            ASSS_TRY(spmv(h->S, h->t1.p, h->t2.p, nullptr, s));
+            k_axpy_mul<<<nb, 256, 0, s>>>(x, h->dc.p, h->t2.p, n);
+            ASSS_CHECK_LAUNCH();
+            ASSS_TRY(spmv(h->A, x, h->t1.p, nullptr, s));
+        } else {
+            k_from_scaled_adj<<<nb, 256, 0, s>>>(dy.p, h->dr.p, h->w.p, perm, n, x);  // lambda += D_r P^T W dmu
+            ASSS_CHECK_LAUNCH();
+            ASSS_TRY(spmv(h->AT, x, h->t1.p, nullptr, s));
+        }
+        k_sub<<<nb, 256, 0, s>>>(rhs, h->t1.p, r.p, n);
+        ASSS_CHECK_LAUNCH();
+    }
+    st->inner_its_total = h->inner_total;
+    st->inner_solves = h->inner_solves;
+    st->inner_its_avg = h->inner_solves ? (double)h->inner_total / h->inner_solves : 0.0;
+    return ASSS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// set-up
+// ---------------------------------------------------------------------------
+static asss_status do_setup(asss_handle* h, const asss_csr* Ain, asss_stats* st) {
+    const asss_options& o = h->opt;
+    Ctx& c = h->ctx;
+    cudaStream_t s = c.stream;
+    if (o.k_lanczos < 0 || o.gamma <= 0 || o.inner_maxit < 1 || o.outer_maxit < 0 ||
+        (o.precision != ASSS_PREC_FP64 && o.precision != ASSS_PREC_MIXED) ||
+        (o.outer != ASSS_OUTER_TFQMR && o.outer != ASSS_OUTER_FGMRES) || (o.outer == ASSS_OUTER_FGMRES && o.restart < 1)) {
+        set_error("invalid option");
+        return ASSS_ERR_ARG;
+    }
+    ASSS_TRY(upload_csr(Ain, h->A, true, s));
+    int n = h->A.n;
+    h->n = n;
+    // scalings (Eq. mc64, reading: row max then column max unless given)
+    ASSS_TRY(h->dr.alloc(n));
+    ASSS_TRY(h->dc.alloc(n));
+    DBuf<int> flag;
+    ASSS_TRY(flag.alloc(1));
+    ASSS_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
+    DBuf<double> tmp;
+    ASSS_TRY(tmp.alloc(n));
+    if (o.dr) {
+        DBuf<double> t;
+        ASSS_TRY(to_device(t, o.dr, n, s));
+        ASSS_TRY(vcopy(h->dr.p, t.p, n, s));
+    } else {
+        k_rowmax_abs<<<cdiv(n, 256), 256, 0, s>>>(h->A.rp.p, h->A.v.p, n, tmp.p);
+        ASSS_CHECK_LAUNCH();
+        k_recip_check<<<cdiv(n, 256), 256, 0, s>>>(tmp.p, n, h->dr.p, flag.p);
+        ASSS_CHECK_LAUNCH();
+    }
+    if (o.dc) {
+        DBuf<double> t;
+        ASSS_TRY(to_device(t, o.dc, n, s));
+        ASSS_TRY(vcopy(h->dc.p, t.p, n, s));
+    } else {
+        DBuf<unsigned long long> cm;
+        ASSS_TRY(cm.alloc(n));
+        ASSS_CUDA(cudaMemsetAsync(cm.p, 0, sizeof(unsigned long long) * n, s));
+        k_colmax_abs<<<cdiv(n, 256), 256, 0, s>>>(h->A.rp.p, h->A.ci.p, h->A.v.p, h->dr.p, n, cm.p);
+        ASSS_CHECK_LAUNCH();
+        k_recip_check<<<cdiv(n, 256), 256, 0, s>>>((const double*)cm.p, n, h->dc.p, flag.p);
+        ASSS_CHECK_LAUNCH();
+    }
+    int hflag = 0;
+    ASSS_CUDA(cudaMemcpyAsync(&hflag, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ASSS_CUDA(cudaStreamSynchronize(s));
+    if (hflag) {
+        set_error("A has an empty row or column (scaling undefined)");
+        return ASSS_ERR_PATTERN;
+    }
+    if (o.row_perm) {
+        ASSS_TRY(to_device(h->perm, o.row_perm, n, s));
+        DBuf<int> seen;
+        ASSS_TRY(seen.alloc(n));
+        ASSS_CUDA(cudaMemsetAsync(seen.p, 0, sizeof(int) * n, s));
+        ASSS_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
+        k_check_perm<<<cdiv(n, 256), 256, 0, s>>>(h->perm.p, n, seen.p, flag.p);
+        ASSS_CHECK_LAUNCH();
+        ASSS_CUDA(cudaMemcpyAsync(&hflag, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        ASSS_CUDA(cudaStreamSynchronize(s));
+        if (hflag) {
+            set_error("row_perm is not a permutation of 0..n-1");
+            return ASSS_ERR_ARG;
+        }
+        h->has_perm = true;
+    }
+    {
+        DBuf<int> len;
+        ASSS_TRY(len.alloc(n));
+        k_perm_rowlen<<<cdiv(n, 256), 256, 0, s>>>(h->A.rp.p, h->has_perm ? h->perm.p : nullptr, n, len.p);
+        ASSS_CHECK_LAUNCH();
+        h->Abar.n = n;
+        h->Abar.nnz = h->A.nnz;
+        ASSS_TRY(h->Abar.rp.alloc(n + 1));
+        ASSS_TRY(exclusive_scan(len.p, h->Abar.rp.p, n, nullptr, s));
+        ASSS_TRY(h->Abar.ci.alloc(h->A.nnz));
+        ASSS_TRY(h->Abar.v.alloc(h->A.nnz));
+        k_perm_scale_rows<<<cdiv(n, 256), 256, 0, s>>>(h->A.rp.p, h->A.ci.p, h->A.v.p,
+                                                        h->has_perm ? h->perm.p : nullptr, h->dr.p, h->dc.p, n,
+                                                        h->Abar.rp.p, h->Abar.ci.p, h->Abar.v.p);
+        ASSS_CHECK_LAUNCH();
+    }
+    ASSS_TRY(transpose_csr(h->Abar, h->AbarT, nullptr, s));
+    // S pattern: given, or the pattern of Abar
+    DCsr Spat;
+    if (o.s_pattern) {
+        ASSS_TRY(upload_csr(o.s_pattern, Spat, false, s));
+        if (Spat.n != n) {
+            set_error("s_pattern has the wrong dimension");
+            return ASSS_ERR_ARG;
+        }
+        Spat.v.free();
+    } else {
+        Spat.n = n;
+        Spat.nnz = h->Abar.nnz;
+        ASSS_TRY(Spat.rp.alloc(n + 1));
+        ASSS_TRY(Spat.ci.alloc(h->Abar.nnz));
+        ASSS_CUDA(cudaMemcpyAsync(Spat.rp.p, h->Abar.rp.p, sizeof(int) * (n + 1), cudaMemcpyDeviceToDevice, s));
+        ASSS_CUDA(cudaMemcpyAsync(Spat.ci.p, h->Abar.ci.p, sizeof(int) * h->Abar.nnz, cudaMemcpyDeviceToDevice, s));
+    }
+    // the LLS (§2, App. A)
+    DCsr P;
+    DBuf<int> mirror, diagpos;
+    DBuf<double> Cval, s_val;
+    LlsResult lr;
+    ASSS_TRY(lls_fit(c, h->Abar, h->AbarT, Spat, o.gamma, o.lls_tol, o.lls_maxit, s_val, P, mirror, diagpos, Cval,
+                     &lr));
+    st->lls_its = lr.its;
+    st->lls_relgrad = lr.relgrad;
+    st->nnz_pattern = P.nnz;
+    h->S.n = n;
+    h->S.nnz = Spat.nnz;
+    h->S.rp.p = Spat.rp.p;
+    h->S.rp.n = Spat.rp.n;
+    Spat.rp.p = nullptr;
+    h->S.ci.p = Spat.ci.p;
+    h->S.ci.n = Spat.ci.n;
+    Spat.ci.p = nullptr;
+    h->S.v.p = s_val.p;
+    h->S.v.n = s_val.n;
+    s_val.p = nullptr;
+    // d, W, zero pivots, negative set (§3, reading: 1x1 pivots)
+    ASSS_TRY(h->d.alloc(n));
+    ASSS_TRY(h->w.alloc(n));
+    k_diag_w<<<cdiv(n, 256), 256, 0, s>>>(Cval.p, diagpos.p, n, h->d.p, h->w.p);
+    ASSS_CHECK_LAUNCH();
+    {
+        DBuf<unsigned long long> mx;
+        ASSS_TRY(mx.alloc(1));
+        ASSS_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(unsigned long long), s));
+        k_absmax<<<256, 256, 0, s>>>(h->d.p, n, mx.p);
+        ASSS_CHECK_LAUNCH();
+        unsigned long long bits = 0;
+        ASSS_CUDA(cudaMemcpyAsync(&bits, mx.p, sizeof(bits), cudaMemcpyDeviceToHost, s));
+        ASSS_CUDA(cudaStreamSynchronize(s));
+        double dmax;
+        memcpy(&dmax, &bits, sizeof(double));
+        ASSS_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
+        k_zero_pivots<<<cdiv(n, 256), 256, 0, s>>>(h->d.p, n, o.zero_tol * dmax, flag.p);
+        ASSS_CHECK_LAUNCH();
+        ASSS_CUDA(cudaMemcpyAsync(&hflag, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        ASSS_CUDA(cudaStreamSynchronize(s));
+        if (dmax == 0.0 || hflag) {
+            set_error("%d zero pivot(s) in diag(Abar S)", hflag);
+            return ASSS_ERR_ZERO_DIAG;
+        }
+    }
+    {
+        DBuf<int> nf, npos;
+        ASSS_TRY(nf.alloc(n));
+        ASSS_TRY(npos.alloc(n + 1));
+        k_neg_flag<<<cdiv(n, 256), 256, 0, s>>>(h->d.p, n, nf.p);
+        ASSS_CHECK_LAUNCH();
+        int64_t r = 0;
+        ASSS_TRY(exclusive_scan(nf.p, npos.p, n, &r, s));
+        if (r > o.r_max) {
+            h->prec2 = 1;  // Eq. (preconditioner2): drop M~_r
+            h->r = 0;
+        } else {
+            h->r = (int)r;
+            if (r) {
+                ASSS_TRY(h->neg.alloc(r));
+                k_neg_compact<<<cdiv(n, 256), 256, 0, s>>>(nf.p, npos.p, n, h->neg.p);
+                ASSS_CHECK_LAUNCH();
+            }
+        }
+    }
+    // J~ on P (exactly skew), SELL copies
+    h->Jt.n = n;
+    h->Jt.nnz = P.nnz;
+    h->Jt.rp.p = P.rp.p;
+    h->Jt.rp.n = P.rp.n;
+    P.rp.p = nullptr;
+    h->Jt.ci.p = P.ci.p;
+    h->Jt.ci.n = P.ci.n;
+    P.ci.p = nullptr;
+    ASSS_TRY(h->Jt.v.alloc(h->Jt.nnz));
+    k_assemble_jt<<<cdiv(n, 256), 256, 0, s>>>(n, h->Jt.rp.p, h->Jt.ci.p, mirror.p, Cval.p, h->w.p, h->Jt.v.p);
+    ASSS_CHECK_LAUNCH();
+    ASSS_TRY(build_sell<double>(h->Jt, true, h->J64, s));
+    if (o.precision == ASSS_PREC_MIXED) ASSS_TRY(build_sell<float>(h->Jt, true, h->J32, s));
+    // outer operator pieces: W Abar and S W
+    ASSS_TRY(copy_csr(h->Abar, h->Aw, s));
+    k_scale_rows<<<cdiv(n, 256), 256, 0, s>>>(h->Aw.rp.p, h->Aw.v.p, h->w.p, n);
+    ASSS_CHECK_LAUNCH();
+    ASSS_TRY(copy_csr(h->S, h->Sw, s));
+    k_scale_cols<<<cdiv(n, 256), 256, 0, s>>>(h->Sw.rp.p, h->Sw.ci.p, h->Sw.v.p, h->w.p, n);
+    ASSS_CHECK_LAUNCH();
+    // skew-Lanczos (§3.2, Fig. 2)
+    {
+        DBuf<double> q1;
+        ASSS_TRY(q1.alloc(n));
+        ASSS_TRY(splitmix64_fill(o.seed, n, q1.p, s));
+        ASSS_TRY(lanczos(c, h->Jt, q1.p, n, o.k_lanczos, o.reorth, h->Qcm, h->alpha_h, &h->k));
+    }
+    h->kp = pick_kp(h->k);
+    if (h->kp < 0) {
+        set_error("k_lanczos above 64 is not supported by this build");
+        return ASSS_ERR_UNSUPPORTED;
+    }
+    if (h->k > 1) ASSS_TRY(to_device(h->alpha_d, h->alpha_h.data(), (int64_t)h->alpha_h.size(), s));
+    else ASSS_TRY(h->alpha_d.alloc(1));
+    if (h->kp) {
+        ASSS_TRY(h->Q64.alloc((int64_t)n * h->kp));
+        ASSS_TRY(to_rowmajor(h->Qcm.p, n, h->k, n, h->kp, h->Q64.p, s));
+        if (o.precision == ASSS_PREC_MIXED) {
+            ASSS_TRY(h->Q32.alloc((int64_t)n * h->kp));
+            ASSS_TRY(to_rowmajor_f(h->Qcm.p, n, h->k, n, h->kp, h->Q32.p, s));
+        }
+    }
+    // work buffers and the mrs workspace
+    ASSS_TRY(h->t1.alloc(n));
+    ASSS_TRY(h->t2.alloc(n));
+    ASSS_TRY(h->t3.alloc(n));
+    ASSS_TRY(h->zt.alloc(n));
+    ASSS_TRY(h->wv.alloc(h->k + h->r + 1));
+    if (o.precision == ASSS_PREC_MIXED) ASSS_TRY(h->z32.alloc(n));
+    ASSS_TRY(mrs_work_create(&h->mw, n, c.sms));
+    // SMW data for P^-1 (Eq. smw; S_bar X = U_bar by mrs)
+    ASSS_TRY(ensure_smw(h, 0));
+    ASSS_CUDA(cudaStreamSynchronize(s));
+    st->r = h->r;
+    st->k_eff = h->k;
+    st->prec2 = h->prec2;
+    return ASSS_OK;
+}
+
+// ===========================================================================
+// exported functions
+// ===========================================================================
+extern "C" {
+
+void asss_default_options(asss_options* opt) {
+    if (opt) fill_defaults(opt);
+}
+
+const char* asss_status_str(asss_status s) {
+    switch (s) {
+        case ASSS_OK: return "ok";
+        case ASSS_ERR_ARG: return "invalid argument";
+        case ASSS_ERR_PATTERN: return "malformed sparsity pattern";
+        case ASSS_ERR_ZERO_DIAG: return "zero pivot in the diagonal factor";
+        case ASSS_ERR_BREAKDOWN: return "breakdown";
+        case ASSS_ERR_NOT_CONVERGED: return "not converged";
+        case ASSS_ERR_STAGNATION: return "stagnation";
+        case ASSS_ERR_RANK: return "rank above r_max";
+        case ASSS_ERR_TIMEOUT: return "device wait timed out";
+        case ASSS_ERR_OOM: return "out of device memory";
+        case ASSS_ERR_CUDA: return "CUDA error";
+        case ASSS_ERR_UNSUPPORTED: return "unsupported input";
+    }
+    return "unknown status";
+}
+
+const char* asss_last_error(void) { return get_error(); }
+
+asss_status asss_setup(const asss_csr* A, const asss_options* opt, asss_handle** out, asss_stats* st) {
+    if (!out) {
+        set_error("out is NULL");
+        return ASSS_ERR_ARG;
+    }
+    *out = nullptr;
+    set_error("");
+    auto t0 = std::chrono::steady_clock::now();
+    asss_handle* h = new asss_handle();
+    if (opt) h->opt = *opt;
+    else fill_defaults(&h->opt);
+    asss_stats lst;
+    memset(&lst, 0, sizeof(lst));
+    asss_status s = make_ctx(h->ctx, h->opt.stream, h->opt.wait_timeout_ms);
+    if (s == ASSS_OK) s = do_setup(h, A, &lst);
+    if (s != ASSS_OK) {
+        cudaStreamSynchronize(h->ctx.stream);
+        delete h;
+        lst.status = s;
+        if (st) *st = lst;
+        return s;
+    }
+    lst.t_setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    lst.status = ASSS_OK;
+    h->setup_stats = lst;
+    if (st) *st = lst;
+    *out = h;
+    return ASSS_OK;
+}
+
+void asss_destroy(asss_handle* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->ctx.stream);
+    delete h;
+}
+
+static asss_status solve_common(asss_handle* h, int tr, int nrhs, const double* b, int64_t ldb, double* x,
+                                int64_t ldx, const double* xfwd, int64_t ldxf, double* dA, asss_stats* st) {
+    if (!h || nrhs < 0 || (nrhs > 0 && (!b || !x)) || ldb < h->n || ldx < h->n) {
+        set_error("invalid solve arguments");
+        return ASSS_ERR_ARG;
+    }
+    set_error("");
+    cudaStream_t s = h->ctx.stream;
+    int n = h->n;
+    auto t0 = std::chrono::steady_clock::now();
+    bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+    DBuf<double> bb, xx, xf, dAd;
+    ASSS_TRY(bb.alloc(n));
+    ASSS_TRY(xx.alloc(n));
+    asss_stats lst = h->setup_stats;
+    asss_status worst = ASSS_OK;
+    for (int j = 0; j < nrhs; ++j) {
+        ASSS_CUDA(cudaMemcpyAsync(bb.p, b + (size_t)j * ldb, sizeof(double) * n,
+                                  bdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        double* xt = xdev ? x + (size_t)j * ldx : xx.p;
+        ASSS_TRY(refine(h, tr, bb.p, xt, &lst));
+        if (!xdev) {
+            ASSS_CUDA(cudaMemcpyAsync(x + (size_t)j * ldx, xt, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        }
+        if (tr && xfwd && dA) {
+            bool fdev = is_device_ptr(xfwd), adev = is_device_ptr(dA);
+            const double* xf_p = xfwd + (size_t)j * ldxf;
+            if (!fdev) {
+                ASSS_TRY(xf.alloc(n));
+                ASSS_CUDA(cudaMemcpyAsync(xf.p, xf_p, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+                xf_p = xf.p;
+            }
+            double* dA_p = dA + (size_t)j * h->A.nnz;
+            if (!adev) {
+                ASSS_TRY(dAd.alloc(h->A.nnz));
+                dA_p = dAd.p;
+            }
+            k_grad_A<<<cdiv(n, 256), 256, 0, s>>>(h->A.rp.p, h->A.ci.p, xt, xf_p, n, dA_p);
+            ASSS_CHECK_LAUNCH();
+            if (!adev) {
+                ASSS_CUDA(cudaMemcpyAsync(dA + (size_t)j * h->A.nnz, dA_p, sizeof(double) * h->A.nnz,
+                                          cudaMemcpyDeviceToHost, s));
+            }
+        }
+        ASSS_CUDA(cudaStreamSynchronize(s));
+        if (lst.status != ASSS_OK && worst == ASSS_OK) worst = (asss_status)lst.status;
+    }
+    lst.t_solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    lst.status = worst;
+    if (st) *st = lst;
+    if (worst != ASSS_OK) set_error("solve ended with status %d (%s)", (int)worst, asss_status_str(worst));
+    return worst;
+}
+
+asss_status asss_solve(asss_handle* h, int nrhs, const double* b, int64_t ldb, double* x, int64_t ldx,
+                       asss_stats* st) {
+    return solve_common(h, 0, nrhs, b, ldb, x, ldx, nullptr, 0, nullptr, st);
+}
+
+asss_status asss_solve_adjoint(asss_handle* h, int nrhs, const double* g, int64_t ldg, double* lambda, int64_t ldl,
+                               const double* x, int64_t ldx, double* dA, asss_stats* st) {
+    if (h && x && ldx < h->n) {
+        set_error("ldx < n");
+        return ASSS_ERR_ARG;
+    }
+    return solve_common(h, 1, nrhs, g, ldg, lambda, ldl, x, ldx, dA, st);
+}
+
+asss_status asss_apply_operator(asss_handle* h, int transpose, const double* v, double* out) {
+    if (!h || !v || !out) {
+        set_error("invalid arguments");
+        return ASSS_ERR_ARG;
+    }
+    cudaStream_t s = h->ctx.stream;
+    int n = h->n;
+    DBuf<double> vi, vo;
+    ASSS_TRY(to_device(vi, v, n, s));
+    ASSS_TRY(vo.alloc(n));
+    ASSS_TRY(apply_op(h, transpose ? 1 : 0, vi.p, vo.p));
+    ASSS_CUDA(cudaMemcpyAsync(out, vo.p, sizeof(double) * n, cudaMemcpyDefault, s));
+    ASSS_CUDA(cudaStreamSynchronize(s));
+    return ASSS_OK;
+}
+
+asss_status asss_apply_preconditioner(asss_handle* h, int transpose, const double* u, double* out, asss_stats* st) {
+    if (!h || !u || !out) {
+        set_error("invalid arguments");
+        return ASSS_ERR_ARG;
+    }
+    cudaStream_t s = h->ctx.stream;
+    int n = h->n;
+    DBuf<double> vi, vo;
+    ASSS_TRY(to_device(vi, u, n, s));
+    ASSS_TRY(vo.alloc(n));
+    int its = 0;
+    ASSS_TRY(apply_prec(h, transpose ? 1 : 0, vi.p, vo.p, &its));
+    ASSS_CUDA(cudaMemcpyAsync(out, vo.p, sizeof(double) * n, cudaMemcpyDefault, s));
+    ASSS_CUDA(cudaStreamSynchronize(s));
+    if (st) {
+        *st = h->setup_stats;
+        st->inner_its_total = its;
+        st->inner_solves = 1;
+    }
+    return ASSS_OK;
+}
+
+asss_status asss_export(asss_handle* h, double* dr, double* dc, double* w, double* d, double* s_val, double* q,
+                        double* alpha, int32_t* neg) {
+    if (!h) {
+        set_error("handle is NULL");
+        return ASSS_ERR_ARG;
+    }
+    cudaStream_t s = h->ctx.stream;
+    int n = h->n;
+    if (dr) ASSS_CUDA(cudaMemcpyAsync(dr, h->dr.p, sizeof(double) * n, cudaMemcpyDefault, s));
+    if (dc) ASSS_CUDA(cudaMemcpyAsync(dc, h->dc.p, sizeof(double) * n, cudaMemcpyDefault, s));
+    if (w) ASSS_CUDA(cudaMemcpyAsync(w, h->w.p, sizeof(double) * n, cudaMemcpyDefault, s));
+    if (d) ASSS_CUDA(cudaMemcpyAsync(d, h->d.p, sizeof(double) * n, cudaMemcpyDefault, s));
+    if (s_val) ASSS_CUDA(cudaMemcpyAsync(s_val, h->S.v.p, sizeof(double) * h->S.nnz, cudaMemcpyDefault, s));
+    if (q && h->k) ASSS_CUDA(cudaMemcpyAsync(q, h->Qcm.p, sizeof(double) * (size_t)n * h->k, cudaMemcpyDefault, s));
+    if (alpha && h->k > 1)
+        ASSS_CUDA(cudaMemcpyAsync(alpha, h->alpha_d.p, sizeof(double) * (h->k - 1), cudaMemcpyDefault, s));
+    if (neg && h->r) ASSS_CUDA(cudaMemcpyAsync(neg, h->neg.p, sizeof(int) * h->r, cudaMemcpyDefault, s));
+    ASSS_CUDA(cudaStreamSynchronize(s));
+    return ASSS_OK;
+}
+
+asss_status asss_skew_symmetrizer(const asss_csr* Abar_in, const asss_csr* s_pattern, const asss_options* opt,
+                                  double* s_val, asss_stats* st) {
+    asss_options o;
+    if (opt) o = *opt;
+    else fill_defaults(&o);
+    Ctx c;
+    ASSS_TRY(make_ctx(c, o.stream, o.wait_timeout_ms));
+    if (!s_pattern || !s_val || o.gamma <= 0) {
+        set_error("invalid arguments");
+        return ASSS_ERR_ARG;
+    }
+    DCsr Abar, AbarT, Spat, P;
+    ASSS_TRY(upload_csr(Abar_in, Abar, true, c.stream));
+    ASSS_TRY(upload_csr(s_pattern, Spat, false, c.stream));
+    Spat.v.free();
+    if (Spat.n != Abar.n) {
+        set_error("pattern dimension mismatch");
+        return ASSS_ERR_ARG;
+    }
+    ASSS_TRY(transpose_csr(Abar, AbarT, nullptr, c.stream));
+    DBuf<int> mirror, diagpos;
+    DBuf<double> Cval, sv;
+    LlsResult lr;
+    ASSS_TRY(lls_fit(c, Abar, AbarT, Spat, o.gamma, o.lls_tol, o.lls_maxit, sv, P, mirror, diagpos, Cval, &lr));
+    ASSS_CUDA(cudaMemcpyAsync(s_val, sv.p, sizeof(double) * Spat.nnz, cudaMemcpyDefault, c.stream));
+    ASSS_CUDA(cudaStreamSynchronize(c.stream));
+    if (st) {
+        memset(st, 0, sizeof(*st));
+        st->lls_its = lr.its;
+        st->lls_relgrad = lr.relgrad;
+        st->nnz_pattern = P.nnz;
+    }
+    return ASSS_OK;
+}
+
+asss_status asss_skew_lanczos(const asss_csr* J, const double* q1, int k, int reorth, double* q, double* alpha,
+                              int* k_eff, void* stream) {
+    Ctx c;
+    ASSS_TRY(make_ctx(c, stream, 2000.0));
+    if (!q1 || !q || !k_eff || k < 0) {
+        set_error("invalid arguments");
+        return ASSS_ERR_ARG;
+    }
+    DCsr Jd;
+    ASSS_TRY(upload_csr(J, Jd, true, c.stream));
+    DBuf<double> q1d, Qcm;
+    ASSS_TRY(to_device(q1d, q1, Jd.n, c.stream));
+    std::vector<double> al;
+    int ke = 0;
+    ASSS_TRY(lanczos(c, Jd, q1d.p, Jd.n, k, reorth, Qcm, al, &ke));
+    *k_eff = ke;
+    if (ke) ASSS_CUDA(cudaMemcpyAsync(q, Qcm.p, sizeof(double) * (size_t)Jd.n * ke, cudaMemcpyDefault, c.stream));
+    if (alpha && ke > 1) {
+        DBuf<double> ad;
+        ASSS_TRY(to_device(ad, al.data(), ke - 1, c.stream));
+        ASSS_CUDA(cudaMemcpyAsync(alpha, ad.p, sizeof(double) * (ke - 1), cudaMemcpyDefault, c.stream));
+        ASSS_CUDA(cudaStreamSynchronize(c.stream));
+    }
+    ASSS_CUDA(cudaStreamSynchronize(c.stream));
+    return ASSS_OK;
+}
+
+asss_status asss_mrs(const asss_csr* J, int k, const double* q, const double* alpha, double shift, double sign,
+                     const double* b, double* x, double tol, int maxit, int precision, int* its, double* ratio,
+                     void* stream) {
+    Ctx c;
+    ASSS_TRY(make_ctx(c, stream, 2000.0));
+    if (!b || !x || k < 0 || (k > 0 && !q) || (k > 1 && !alpha) || maxit < 1 || !(shift > 0.0)) {
+        set_error("invalid arguments");
+        return ASSS_ERR_ARG;
+    }
+    cudaStream_t s = c.stream;
+    DCsr Jd;
+    ASSS_TRY(upload_csr(J, Jd, true, s));
+    int n = Jd.n;
+    int kp = pick_kp(k);
+    if (kp < 0) {
+        set_error("k above 64 is not supported");
+        return ASSS_ERR_UNSUPPORTED;
+    }
+    DSell<double> J64;
+    DSell<float> J32;
+    DBuf<double> Qcm, Q64, ad, bd, xd;
+    DBuf<float> Q32, x32;
+    bool fp32 = precision == ASSS_PREC_MIXED;
+    if (fp32) ASSS_TRY(build_sell<float>(Jd, false, J32, s));
+    else ASSS_TRY(build_sell<double>(Jd, false, J64, s));
+    if (k) {
+        ASSS_TRY(to_device(Qcm, q, (int64_t)n * k, s));
+        if (fp32) {
+            ASSS_TRY(Q32.alloc((int64_t)n * kp));
+            ASSS_TRY(to_rowmajor_f(Qcm.p, n, k, n, kp, Q32.p, s));
+        } else {
+            ASSS_TRY(Q64.alloc((int64_t)n * kp));
+            ASSS_TRY(to_rowmajor(Qcm.p, n, k, n, kp, Q64.p, s));
+        }
+    }
+    if (k > 1) ASSS_TRY(to_device(ad, alpha, k - 1, s));
+    else ASSS_TRY(ad.alloc(1));
+    ASSS_TRY(to_device(bd, b, n, s));
+    ASSS_TRY(xd.alloc(n));
+    MrsWork* w = nullptr;
+    ASSS_TRY(mrs_work_create(&w, n, c.sms));
+    MrsOperator op;
+    op.J64 = fp32 ? nullptr : &J64;
+    op.J32 = fp32 ? &J32 : nullptr;
+    op.k = k;
+    op.kp = kp;
+    op.Q64 = Q64.p;
+    op.Q32 = Q32.p;
+    op.alpha = ad.p;
+    MrsResult res;
+    asss_status stt;
+    if (fp32) {
+        ASSS_TRY(x32.alloc(n));
+        stt = mrs_solve(c, w, op, true, shift, sign, bd.p, nullptr, x32.p, tol, maxit, &res, true);
+        if (stt == ASSS_OK) {
+            k_f2d<<<cdiv(n, 256), 256, 0, s>>>(x32.p, xd.p, n);
+            stt = cudaGetLastError() == cudaSuccess ? ASSS_OK : ASSS_ERR_CUDA;
+        }
+    } else {
+        stt = mrs_solve(c, w, op, false, shift, sign, bd.p, xd.p, nullptr, tol, maxit, &res, true);
+    }
+    mrs_work_destroy(w);
+    ASSS_TRY(stt);
+    ASSS_CUDA(cudaMemcpyAsync(x, xd.p, sizeof(double) * n, cudaMemcpyDefault, s));
+    ASSS_CUDA(cudaStreamSynchronize(s));
+    if (its) *its = res.its;
+    if (ratio) *ratio = res.ratio;
+    return ASSS_OK;
+}
+
+}  // extern "C"

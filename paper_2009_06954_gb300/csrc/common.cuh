@@ -1,0 +1,184 @@
+// Shared device helpers and host-side plumbing for the ASSS library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/asss.h"
+
+namespace asss {
+
+// ---------------------------------------------------------------------------
+// host-side error handling: every internal function returns asss_status and
+// records a message; nothing aborts.
+// ---------------------------------------------------------------------------
+void set_error(const char* fmt, ...);
+const char* get_error();
+
+#define ASSS_CUDA(call)                                                            \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            ::asss::set_error("%s:%d %s: %s", __FILE__, __LINE__, #call,          \
+                              cudaGetErrorString(e_));                             \
+            return e_ == cudaErrorMemoryAllocation ? ASSS_ERR_OOM : ASSS_ERR_CUDA; \
+        }                                                                          \
+    } while (0)
+
+#define ASSS_TRY(call)                     \
+    do {                                   \
+        asss_status s_ = (call);           \
+        if (s_ != ASSS_OK) return s_;      \
+    } while (0)
+
+#define ASSS_CHECK_LAUNCH() ASSS_CUDA(cudaGetLastError())
+
+inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------------------
+// device buffers owned by the library
+// ---------------------------------------------------------------------------
+template <class T>
+struct DBuf {
+    T* p = nullptr;
+    int64_t n = 0;
+    asss_status alloc(int64_t count) {
+        free();
+        if (count <= 0) return ASSS_OK;
+        cudaError_t e = cudaMalloc((void**)&p, sizeof(T) * (size_t)count);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            set_error("cudaMalloc of %lld bytes failed: %s", (long long)(sizeof(T) * count),
+                      cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? ASSS_ERR_OOM : ASSS_ERR_CUDA;
+        }
+        n = count;
+        return ASSS_OK;
+    }
+    void free() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    ~DBuf() { free(); }
+    DBuf() = default;
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+};
+
+// CSR with 32-bit row pointers (nnz < 2^31 is checked on entry).
+struct DCsr {
+    int n = 0;
+    int nnz = 0;
+    DBuf<int> rp, ci;
+    DBuf<double> v;
+};
+
+// SELL-C (C = 32) storage: slice s covers rows 32s..32s+31; entry kk of lane t
+// of slice s sits at sptr[s] + kk*32 + t.  Padding entries have value 0 and a
+// valid column (the row itself, or 0 past the last row).
+template <class T>
+struct DSell {
+    int n = 0;
+    int nslices = 0;
+    int64_t nstored = 0;
+    DBuf<int> sptr;   // nslices + 1
+    DBuf<int> col;
+    DBuf<T> val;
+};
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ int warp_sum(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier for a cooperative (co-resident) launch.  Every block calls
+// it the same number of times.  The wait is bounded: after `budget` clock cycles
+// the block records ASSS_ERR_TIMEOUT in *err and returns.
+struct GridBarrier {
+    unsigned* count;  // arrivals in the current phase
+    unsigned* gen;    // phase counter
+    int* err;         // device status word
+};
+
+__device__ __forceinline__ void grid_sync(const GridBarrier& gb, unsigned nblocks, long long budget) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned g = ld_acquire(gb.gen);
+        __threadfence();
+        unsigned ticket = atomicAdd(gb.count, 1u);
+        if (ticket == nblocks - 1) {
+            atomicExch(gb.count, 0u);
+            __threadfence();
+            atomicAdd(gb.gen, 1u);
+        } else {
+            long long t0 = clock64();
+            while (ld_acquire(gb.gen) == g) {
+                if (clock64() - t0 > budget) {
+                    atomicExch(gb.err, (int)ASSS_ERR_TIMEOUT);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// host helpers shared by the translation units
+// ---------------------------------------------------------------------------
+struct Ctx {
+    cudaStream_t stream = 0;
+    int device = 0;
+    int sms = 0;
+    int clock_khz = 0;
+    long long wait_cycles = 0;
+};
+asss_status make_ctx(Ctx& c, void* stream, double wait_timeout_ms);
+
+// pointer classification
+bool is_device_ptr(const void* p);
+
+// copy n elements from a host-or-device pointer into a device buffer
+template <class T>
+asss_status to_device(DBuf<T>& dst, const T* src, int64_t n, cudaStream_t s) {
+    ASSS_TRY(dst.alloc(n));
+    if (n == 0) return ASSS_OK;
+    ASSS_CUDA(cudaMemcpyAsync(dst.p, src, sizeof(T) * n, cudaMemcpyDefault, s));
+    return ASSS_OK;
+}
+
+// exclusive scan of int counts (n entries) into out (n+1 entries); returns total
+asss_status exclusive_scan(const int* cnt, int* out, int n, int64_t* total, cudaStream_t s);
+asss_status exclusive_scan64(const int* cnt, long long* out, int n, long long* total, cudaStream_t s);
+
+// deterministic sum reductions: out[0] = sum a[i]*b[i] (b may be null: sum a^2 if a==b flagged)
+asss_status dot(const double* a, const double* b, int n, double* d_out, cudaStream_t s);
+asss_status dot_f(const float* a, const float* b, int n, double* d_out, cudaStream_t s);
+
+}  // namespace asss

@@ -1,0 +1,85 @@
+// Internal host-side interfaces shared by the library's translation units.
+#pragma once
+
+#include "common.cuh"
+
+namespace asss {
+
+// sparse.cu
+asss_status upload_csr(const asss_csr* A, DCsr& out, bool need_values, cudaStream_t s);
+asss_status copy_csr(const DCsr& a, DCsr& out, cudaStream_t s);
+asss_status transpose_csr(const DCsr& a, DCsr& t, DBuf<int>* srcpos, cudaStream_t s);
+asss_status spmv(const DCsr& A, const double* x, double* y, const double* lscale, cudaStream_t s);
+asss_status build_pattern(const DCsr& Abar, const DCsr& AbarT, const DCsr& S, const DCsr& ST, DCsr& P,
+                          DBuf<int>& mirror, DBuf<int>& diagpos, cudaStream_t s);
+template <class T>
+asss_status build_sell(const DCsr& A, bool skip_diag, DSell<T>& out, cudaStream_t s);
+
+// dense.cu : small dense / tall-skinny / vector kernels (all FP64 unless noted)
+asss_status splitmix64_fill(uint64_t seed, int n, double* out, cudaStream_t s);
+// G (p x q, row-major) = A^T B with A n x p (col-major, lda) and B n x q (col-major, ldb)
+asss_status gram(const double* A, int lda, int p, const double* B, int ldb, int q, int n, double* G,
+                 cudaStream_t s);
+// out = z - Y w, Y n x m row-major; w on device (m)
+asss_status sub_rowmajor_gemv(const double* Y, int m, const double* w, const double* z, int n, double* out,
+                              cudaStream_t s);
+// out (n) = A (n x p col-major) c  (+ beta*out)
+asss_status colmajor_gemv(const double* A, int lda, int p, const double* c, int n, double beta, double* out,
+                          cudaStream_t s);
+// in-place inverse of an m x m row-major matrix (Gauss-Jordan, partial pivoting)
+asss_status small_inverse(double* K, int m, int* singular, cudaStream_t s);
+// col-major n x p -> row-major n x kp (zero padded), in double or float
+asss_status to_rowmajor(const double* A, int lda, int p, int n, int kp, double* out, cudaStream_t s);
+asss_status to_rowmajor_f(const double* A, int lda, int p, int n, int kp, float* out, cudaStream_t s);
+
+// vector helpers (device scalars where noted)
+asss_status vscale(double* y, const double* x, double a, int n, cudaStream_t s);                 // y = a x
+asss_status vaxpy(double* y, const double* x, double a, int n, cudaStream_t s);                  // y += a x
+asss_status vaxpy_dev(double* y, const double* x, const double* a, double sign, int n, cudaStream_t s);  // y += sign*(*a) x
+asss_status vmul(double* y, const double* a, const double* b, int n, cudaStream_t s);            // y = a .* b
+asss_status vcopy(double* y, const double* x, int n, cudaStream_t s);
+asss_status vfill(double* y, double v, int n, cudaStream_t s);
+
+// mrs.cu
+struct MrsOperator {
+    // J~ (exactly skew) in SELL-C, FP64 and/or FP32 copies
+    const DSell<double>* J64 = nullptr;
+    const DSell<float>* J32 = nullptr;
+    int k = 0, kp = 0;           // Lanczos vectors and padded row stride
+    const double* Q64 = nullptr; // n x kp row-major
+    const float* Q32 = nullptr;
+    const double* alpha = nullptr;  // device, k-1 values (S_k superdiagonal)
+};
+
+struct MrsWork;  // opaque persistent workspace (owned by a handle)
+asss_status mrs_work_create(MrsWork** w, int n, int sms);
+void mrs_work_destroy(MrsWork* w);
+
+struct MrsResult {
+    int its = 0;
+    double ratio = 0.0;
+    int status = 0;
+};
+
+// One single-RHS mrs solve (App. B) of (shift I + sign*(J~ - Q S_k Q^T)) x = rhs.
+// fp32: use the FP32 operator and vectors; rhs is FP64 in both cases, x is FP64
+// (x64) or FP32 (x32) - exactly one of them non-null.
+asss_status mrs_solve(const Ctx& c, MrsWork* w, const MrsOperator& op, bool fp32, double shift, double sign,
+                      const double* rhs, double* x64, float* x32, double tol, int maxit, MrsResult* res,
+                      bool sync_result);
+
+// lls.cu
+struct LlsResult {
+    int its = 0;
+    double relgrad = 0.0;
+};
+// S values on the pattern of Spat given Abar, AbarT (with values); also returns
+// P (symmetric pattern), mirror, diagpos, and C = Abar S on P.
+asss_status lls_fit(const Ctx& c, const DCsr& Abar, const DCsr& AbarT, const DCsr& Spat, double gamma,
+                    double tol, int maxit, DBuf<double>& s_val, DCsr& P, DBuf<int>& mirror,
+                    DBuf<int>& diagpos, DBuf<double>& Cval, LlsResult* res);
+// C = Abar S on P for given S values
+asss_status lls_product_on_pattern(const Ctx& c, const DCsr& Abar, const DCsr& ST, const int* st_src,
+                                   const double* s_val, const DCsr& P, const int* prow, double* Cval);
+
+}  // namespace asss

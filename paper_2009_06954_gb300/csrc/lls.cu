@@ -1,0 +1,316 @@
+// The least-squares problem for the shifted skew-symmetrizer S (paper §2,
+// Eqs. eq1, eq2, regularized; App. A), solved on the device without forming B.
+//
+// Unknowns: the entries of S on its pattern (CSR order).  Constraint rows: one
+// per upper entry (i < j) of the symmetric pattern P = pat(Abar S) + pat(Abar S)^T,
+// stating (Abar S)_ij + (Abar S)_ji = 0, and one per diagonal entry,
+// sqrt(gamma) (Abar S)_ii = sqrt(gamma).  With C = Abar S evaluated on P:
+//   (B s)_ij = C_ij + C_ji  (i < j),    (B s)_ii = sqrt(gamma) C_ii
+//   (B^T t)_lj = sum_i abar_il G_ij  with G symmetric on P, G_ij = t_{min,max}
+//   (off-diagonal) and G_ii = sqrt(gamma) t_ii.
+// Each output is one sorted-list intersection ("merge dot"), computed by one
+// thread, so results do not depend on scheduling.
+//
+// The normal equations B^T B s = B^T v are solved by preconditioned conjugate
+// gradients.  The preconditioner is block-Jacobi on the pairs {s_lj, s_jl}: when
+// Abar is close to I a skew perturbation of S barely changes the objective, so
+// the two entries of a pair are strongly coupled; the 2x2 Gram block of a pair is
+//   [ sum_i abar_il^2 w_ij     abar_ll abar_jj ]
+//   [ abar_ll abar_jj          sum_i abar_ij^2 w_il ]     (w = gamma on i = column)
+// and is inverted in closed form.
+#include "common.cuh"
+#include "internal.h"
+
+namespace asss {
+
+__device__ __forceinline__ double merge_dot_s(const int* __restrict__ ac, const double* __restrict__ av, int alen,
+                                              const int* __restrict__ bc, const int* __restrict__ bu, int blen,
+                                              const double* __restrict__ s) {
+    int x = 0, y = 0;
+    double acc = 0.0;
+    while (x < alen && y < blen) {
+        int ca = ac[x], cb = bc[y];
+        if (ca == cb) {
+            acc += av[x] * s[bu[y]];
+            ++x;
+            ++y;
+        } else if (ca < cb) {
+            ++x;
+        } else {
+            ++y;
+        }
+    }
+    return acc;
+}
+
+__global__ void k_row_of_entry(const int* rp, int n, int* row) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) row[e] = i;
+}
+
+// q = B s on the constraint entries of P (upper + diagonal); lower entries get 0
+__global__ void k_lls_B(int nP, const int* __restrict__ prow, const int* __restrict__ pci,
+                        const int* __restrict__ arp, const int* __restrict__ aci, const double* __restrict__ av,
+                        const int* __restrict__ strp, const int* __restrict__ stci, const int* __restrict__ stsrc,
+                        const double* __restrict__ s, double sg, double* q) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nP) return;
+    int i = prow[k], j = pci[k];
+    if (j < i) {
+        q[k] = 0.0;
+        return;
+    }
+    double cij = merge_dot_s(aci + arp[i], av + arp[i], arp[i + 1] - arp[i], stci + strp[j], stsrc + strp[j],
+                             strp[j + 1] - strp[j], s);
+    if (j == i) {
+        q[k] = sg * cij;
+        return;
+    }
+    double cji = merge_dot_s(aci + arp[j], av + arp[j], arp[j + 1] - arp[j], stci + strp[i], stsrc + strp[i],
+                             strp[i + 1] - strp[i], s);
+    q[k] = cij + cji;
+}
+
+// C = Abar S on every entry of P
+__global__ void k_lls_C(int nP, const int* __restrict__ prow, const int* __restrict__ pci,
+                        const int* __restrict__ arp, const int* __restrict__ aci, const double* __restrict__ av,
+                        const int* __restrict__ strp, const int* __restrict__ stci, const int* __restrict__ stsrc,
+                        const double* __restrict__ s, double* C) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nP) return;
+    int i = prow[k], j = pci[k];
+    C[k] = merge_dot_s(aci + arp[i], av + arp[i], arp[i + 1] - arp[i], stci + strp[j], stsrc + strp[j],
+                       strp[j + 1] - strp[j], s);
+}
+
+// g = B^T t on the unknowns
+__global__ void k_lls_BT(int nS, const int* __restrict__ srow, const int* __restrict__ sci,
+                         const int* __restrict__ atrp, const int* __restrict__ atci, const double* __restrict__ atv,
+                         const int* __restrict__ prp, const int* __restrict__ pci, const int* __restrict__ mirror,
+                         const double* __restrict__ t, double sg, double* g) {
+    int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= nS) return;
+    int l = srow[u], j = sci[u];
+    int x = atrp[l], xe = atrp[l + 1];
+    int y = prp[j], ye = prp[j + 1];
+    double acc = 0.0;
+    while (x < xe && y < ye) {
+        int ia = atci[x], ib = pci[y];
+        if (ia == ib) {
+            double G;
+            if (ia > j) G = t[y];
+            else if (ia < j) G = (mirror[y] >= 0) ? t[mirror[y]] : 0.0;
+            else G = sg * t[y];
+            acc += atv[x] * G;
+            ++x;
+            ++y;
+        } else if (ia < ib) {
+            ++x;
+        } else {
+            ++y;
+        }
+    }
+    g[u] = acc;
+}
+
+__global__ void k_diag_values(const int* rp, const int* ci, const double* v, int n, double* dv) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double d = 0.0;
+    for (int e = rp[i]; e < rp[i + 1]; ++e)
+        if (ci[e] == i) {
+            d = v[e];
+            break;
+        }
+    dv[i] = d;
+}
+
+__global__ void k_lls_prec_setup(int nS, const int* srow, const int* sci, const int* srp,
+                                 const int* atrp, const int* atci, const double* atv, const double* adiag,
+                                 double gamma, double* N, int* partner, double* cross) {
+    int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= nS) return;
+    int l = srow[u], j = sci[u];
+    double acc = 0.0;
+    for (int e = atrp[l]; e < atrp[l + 1]; ++e) {
+        double a = atv[e];
+        acc += a * a * (atci[e] == j ? gamma : 1.0);
+    }
+    N[u] = acc;
+    int p = -1;
+    if (l != j) {
+        int lo = srp[j], hi = srp[j + 1] - 1;
+        while (lo <= hi) {
+            int mid = (lo + hi) >> 1;
+            int c = sci[mid];
+            if (c == l) {
+                p = mid;
+                break;
+            }
+            if (c < l) lo = mid + 1;
+            else hi = mid - 1;
+        }
+    }
+    partner[u] = p;
+    cross[u] = (p >= 0) ? adiag[l] * adiag[j] : 0.0;
+}
+
+__global__ void k_lls_prec_apply(int nS, const double* N, const int* partner, const double* cross, const double* r,
+                                 double* z) {
+    int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= nS) return;
+    double nu = N[u];
+    if (nu <= 0.0) {
+        z[u] = 0.0;
+        return;
+    }
+    int p = partner[u];
+    if (p >= 0) {
+        double np = N[p], c = cross[u];
+        double det = nu * np - c * c;
+        if (det > 1e-12 * nu * np) {
+            z[u] = (np * r[u] - c * r[p]) / det;
+            return;
+        }
+    }
+    z[u] = r[u] / nu;
+}
+
+__global__ void k_lls_init_rho(int nP, const int* prow, const int* pci, double sg, double* rho) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nP) return;
+    rho[k] = (prow[k] == pci[k]) ? sg : 0.0;
+}
+
+__global__ void k_cg_update(double* s, const double* p, int nS, double* rho, const double* q, int nP,
+                            const double* rz, const double* qq) {
+    double a = (*qq > 0.0) ? (*rz) / (*qq) : 0.0;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < nS) s[t] += a * p[t];
+    if (t < nP) rho[t] -= a * q[t];
+}
+
+__global__ void k_cg_newp(double* p, const double* z, int nS, const double* rz_new, const double* rz_old) {
+    double b = (*rz_old != 0.0) ? (*rz_new) / (*rz_old) : 0.0;
+    int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < nS) p[u] = z[u] + b * p[u];
+}
+
+asss_status lls_product_on_pattern(const Ctx& c, const DCsr& Abar, const DCsr& ST, const int* st_src,
+                                   const double* s_val, const DCsr& P, const int* prow, double* Cval) {
+    k_lls_C<<<cdiv(P.nnz, 256), 256, 0, c.stream>>>(P.nnz, prow, P.ci.p, Abar.rp.p, Abar.ci.p, Abar.v.p, ST.rp.p,
+                                                      ST.ci.p, st_src, s_val, Cval);
+    ASSS_CHECK_LAUNCH();
+    return ASSS_OK;
+}
+
+asss_status lls_fit(const Ctx& c, const DCsr& Abar, const DCsr& AbarT, const DCsr& Spat, double gamma, double tol,
+                    int maxit, DBuf<double>& s_val, DCsr& P, DBuf<int>& mirror, DBuf<int>& diagpos,
+                    DBuf<double>& Cval, LlsResult* res) {
+    cudaStream_t s = c.stream;
+    int n = Abar.n;
+    int nS = Spat.nnz;
+    // S^T pattern with the CSR position of every entry of S
+    DCsr ST;
+    DBuf<int> st_src;
+    ASSS_TRY(transpose_csr(Spat, ST, &st_src, s));
+    ASSS_TRY(build_pattern(Abar, AbarT, Spat, ST, P, mirror, diagpos, s));
+    int nP = P.nnz;
+    DBuf<int> prow, srow;
+    ASSS_TRY(prow.alloc(nP));
+    ASSS_TRY(srow.alloc(nS));
+    k_row_of_entry<<<cdiv(n, 256), 256, 0, s>>>(P.rp.p, n, prow.p);
+    ASSS_CHECK_LAUNCH();
+    k_row_of_entry<<<cdiv(n, 256), 256, 0, s>>>(Spat.rp.p, n, srow.p);
+    ASSS_CHECK_LAUNCH();
+
+    // preconditioner
+    DBuf<double> adiag, Nn, cross;
+    DBuf<int> partner;
+    ASSS_TRY(adiag.alloc(n));
+    ASSS_TRY(Nn.alloc(nS));
+    ASSS_TRY(cross.alloc(nS));
+    ASSS_TRY(partner.alloc(nS));
+    k_diag_values<<<cdiv(n, 256), 256, 0, s>>>(Abar.rp.p, Abar.ci.p, Abar.v.p, n, adiag.p);
+    ASSS_CHECK_LAUNCH();
+    k_lls_prec_setup<<<cdiv(nS, 256), 256, 0, s>>>(nS, srow.p, Spat.ci.p, Spat.rp.p, AbarT.rp.p, AbarT.ci.p,
+                                                    AbarT.v.p, adiag.p, gamma, Nn.p, partner.p, cross.p);
+    ASSS_CHECK_LAUNCH();
+
+    const double sg = sqrt(gamma);
+    DBuf<double> rho, q, r, z, p, sc;
+    ASSS_TRY(s_val.alloc(nS));
+    ASSS_TRY(rho.alloc(nP));
+    ASSS_TRY(q.alloc(nP));
+    ASSS_TRY(r.alloc(nS));
+    ASSS_TRY(z.alloc(nS));
+    ASSS_TRY(p.alloc(nS));
+    ASSS_TRY(sc.alloc(8));  // 0: rz, 1: qq, 2: rr, 3: rz_new, 4: rr0
+    double* d_rz = sc.p;
+    double* d_qq = sc.p + 1;
+    double* d_rr = sc.p + 2;
+    double* d_rzn = sc.p + 3;
+    ASSS_CUDA(cudaMemsetAsync(s_val.p, 0, sizeof(double) * nS, s));
+    k_lls_init_rho<<<cdiv(nP, 256), 256, 0, s>>>(nP, prow.p, P.ci.p, sg, rho.p);
+    ASSS_CHECK_LAUNCH();
+    auto applyBT = [&](const double* t, double* g) -> asss_status {
+        k_lls_BT<<<cdiv(nS, 256), 256, 0, s>>>(nS, srow.p, Spat.ci.p, AbarT.rp.p, AbarT.ci.p, AbarT.v.p, P.rp.p,
+                                                P.ci.p, mirror.p, t, sg, g);
+        ASSS_CHECK_LAUNCH();
+        return ASSS_OK;
+    };
+    auto applyB = [&](const double* sv, double* out) -> asss_status {
+        k_lls_B<<<cdiv(nP, 256), 256, 0, s>>>(nP, prow.p, P.ci.p, Abar.rp.p, Abar.ci.p, Abar.v.p, ST.rp.p, ST.ci.p,
+                                               st_src.p, sv, sg, out);
+        ASSS_CHECK_LAUNCH();
+        return ASSS_OK;
+    };
+    auto precond = [&]() -> asss_status {
+        k_lls_prec_apply<<<cdiv(nS, 256), 256, 0, s>>>(nS, Nn.p, partner.p, cross.p, r.p, z.p);
+        ASSS_CHECK_LAUNCH();
+        return ASSS_OK;
+    };
+    ASSS_TRY(applyBT(rho.p, r.p));
+    ASSS_TRY(precond());
+    ASSS_TRY(vcopy(p.p, z.p, nS, s));
+    ASSS_TRY(dot(r.p, z.p, nS, d_rz, s));
+    ASSS_TRY(dot(r.p, r.p, nS, d_rr, s));
+    double rr0 = 0.0;
+    ASSS_CUDA(cudaMemcpyAsync(&rr0, d_rr, sizeof(double), cudaMemcpyDeviceToHost, s));
+    ASSS_CUDA(cudaStreamSynchronize(s));
+    int its = 0;
+    double rel = rr0 > 0 ? 1.0 : 0.0;
+    const int check_every = 8;
+    int mx = nS > nP ? nS : nP;
+    while (rr0 > 0 && its < maxit) {
+        ASSS_TRY(applyB(p.p, q.p));
+        ASSS_TRY(dot(q.p, q.p, nP, d_qq, s));
+        k_cg_update<<<cdiv(mx, 256), 256, 0, s>>>(s_val.p, p.p, nS, rho.p, q.p, nP, d_rz, d_qq);
+        ASSS_CHECK_LAUNCH();
+        ASSS_TRY(applyBT(rho.p, r.p));
+        ASSS_TRY(precond());
+        ASSS_TRY(dot(r.p, z.p, nS, d_rzn, s));
+        k_cg_newp<<<cdiv(nS, 256), 256, 0, s>>>(p.p, z.p, nS, d_rzn, d_rz);
+        ASSS_CHECK_LAUNCH();
+        ASSS_CUDA(cudaMemcpyAsync(d_rz, d_rzn, sizeof(double), cudaMemcpyDeviceToDevice, s));
+        ++its;
+        if (its % check_every == 0 || its == maxit) {
+            ASSS_TRY(dot(r.p, r.p, nS, d_rr, s));
+            double rr = 0.0;
+            ASSS_CUDA(cudaMemcpyAsync(&rr, d_rr, sizeof(double), cudaMemcpyDeviceToHost, s));
+            ASSS_CUDA(cudaStreamSynchronize(s));
+            rel = sqrt(rr / rr0);
+            if (rel <= tol) break;
+        }
+    }
+    if (res) {
+        res->its = its;
+        res->relgrad = rel;
+    }
+    ASSS_TRY(Cval.alloc(nP));
+    ASSS_TRY(lls_product_on_pattern(c, Abar, ST, st_src.p, s_val.p, P, prow.p, Cval.p));
+    return ASSS_OK;
+}
+
+}  // namespace asss

@@ -1,0 +1,428 @@
+// Persistent single-kernel mrs solve (paper §3.1, App. B) of
+//     (shift I + sign * (J~ - Q_k S_k Q_k^T)) x = b
+// with J~ exactly skew in SELL-C storage and Q_k, S_k the skew-Lanczos data of
+// §3.2 (Fig. 2).  One cooperative launch runs the whole iteration:
+//
+//   per iteration j (one pass over the rows owned by each block):
+//     y_{j+1} = sign*(nu_j J~ y_j - Q (S_k h_j)) + beta_{j-1} nu_{j-1} y_{j-1}
+//       (y_j = beta_{j-1} q_j is the unnormalised Lanczos vector, nu_j = 1/beta_{j-1},
+//        h_j = Q^T q_j)
+//     partial sums of ||y_{j+1}||^2 and Q^T y_{j+1}   -> ONE grid-wide reduction
+//     the p/x update of step j-1 (needs only scalars known before the pass)
+//   then every block computes the same Givens scalars from the reduced sums:
+//     theta_j = sqrt(theta~_j^2 + beta_j^2), c_j, s_j, delta_j = -s_{j-1} beta_j,
+//     theta~_{j+1} = c_{j-1} theta_j, x-coefficient g_j c_j, g_{j+1} = -g_j s_j.
+//
+// The norm and the k deflation dot products share the single reduction per
+// iteration, which keeps the method's one-synchronisation-per-step property (§3.1).
+// Vectors produced by other blocks are read through L2 (ld.global.cg); the grid
+// barrier has a bounded wait.
+#include "common.cuh"
+#include "internal.h"
+
+namespace asss {
+
+constexpr int MRS_THREADS = 512;
+constexpr int MRS_WARPS = MRS_THREADS / 32;
+constexpr int MRS_KPMAX = 64;
+
+struct MrsWork {
+    int n = 0;
+    int sms = 0;
+    DBuf<double> Y64, P64;
+    DBuf<float> Y32, P32;
+    DBuf<double> part;
+    DBuf<unsigned> bar;
+    DBuf<int> err;
+    DBuf<int> out_its;
+    DBuf<double> out_ratio;
+    DBuf<int> blk_slice;
+    const void* part_key = nullptr;
+    int part_nblk = 0;
+};
+
+asss_status mrs_work_create(MrsWork** w, int n, int sms) {
+    MrsWork* m = new MrsWork();
+    m->n = n;
+    m->sms = sms;
+    asss_status st = ASSS_OK;
+    int maxblk = sms * 4;
+    if ((st = m->part.alloc((int64_t)2 * (MRS_KPMAX + 1) * maxblk)) != ASSS_OK ||
+        (st = m->bar.alloc(2)) != ASSS_OK || (st = m->err.alloc(1)) != ASSS_OK ||
+        (st = m->out_its.alloc(1)) != ASSS_OK || (st = m->out_ratio.alloc(1)) != ASSS_OK ||
+        (st = m->blk_slice.alloc(maxblk + 1)) != ASSS_OK) {
+        delete m;
+        return st;
+    }
+    *w = m;
+    return ASSS_OK;
+}
+
+void mrs_work_destroy(MrsWork* w) { delete w; }
+
+template <class T>
+struct MrsParams {
+    int n;
+    const int* sptr;
+    const int* col;
+    const T* val;
+    const T* Q;
+    const double* alpha;
+    int k;
+    double shift, sign;
+    const double* rhs;
+    T* x;
+    T* Y;  // 3n ring of unnormalised Lanczos vectors
+    T* P;  // 2n ring of update directions
+    double* part;  // [2][NV][nblk]
+    GridBarrier gb;
+    const int* blk_slice;
+    double tol;
+    int maxit;
+    long long budget;
+    int* out_its;
+    double* out_ratio;
+};
+
+template <class T, int KP>
+__device__ __forceinline__ void load_qrow(const T* __restrict__ Q, int i, T (&q)[KP > 0 ? KP : 1]) {
+    if constexpr (KP > 0) {
+        const T* row = Q + (size_t)i * KP;
+        if constexpr (sizeof(T) == 4 && (KP % 4) == 0) {
+#pragma unroll
+            for (int m = 0; m < KP; m += 4) {
+                float4 v = *reinterpret_cast<const float4*>(row + m);
+                q[m] = v.x;
+                q[m + 1] = v.y;
+                q[m + 2] = v.z;
+                q[m + 3] = v.w;
+            }
+        } else if constexpr (sizeof(T) == 8 && (KP % 2) == 0) {
+#pragma unroll
+            for (int m = 0; m < KP; m += 2) {
+                double2 v = *reinterpret_cast<const double2*>(row + m);
+                q[m] = v.x;
+                q[m + 1] = v.y;
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < KP; ++m) q[m] = row[m];
+        }
+    }
+}
+
+template <class T, int KP>
+__global__ void __launch_bounds__(MRS_THREADS) k_mrs(MrsParams<T> p) {
+    constexpr int NV = KP + 1;
+    __shared__ double s_wsum[MRS_WARPS][NV];
+    __shared__ double s_red[NV];
+    __shared__ T s_u[KP > 0 ? KP : 1];
+    const int nblk = gridDim.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int s0 = p.blk_slice[blockIdx.x], s1 = p.blk_slice[blockIdx.x + 1];
+    const int n = p.n;
+    volatile int* err = p.gb.err;
+
+    auto block_partials = [&](T(&tacc)[NV], double* buf) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            double d = warp_sum((double)tacc[v]);
+            if (lane == 0) s_wsum[warp][v] = d;
+        }
+        __syncthreads();
+        for (int v = threadIdx.x; v < NV; v += MRS_THREADS) {
+            double t = 0.0;
+#pragma unroll
+            for (int w = 0; w < MRS_WARPS; ++w) t += s_wsum[w][v];
+            buf[v * nblk + blockIdx.x] = t;
+        }
+    };
+    auto reduce_all = [&](const double* buf) {
+        for (int v = warp; v < NV; v += MRS_WARPS) {
+            double t = 0.0;
+            for (int b = lane; b < nblk; b += 32) t += __ldcg(&buf[v * nblk + b]);
+            t = warp_sum(t);
+            if (lane == 0) s_red[v] = t;
+        }
+        __syncthreads();
+    };
+    // u = S_k h with h = nu * (Q^T y), S_k(m, m+1) = alpha_m, S_k(m+1, m) = -alpha_m
+    auto make_u = [&](double nu) {
+        if constexpr (KP > 0) {
+            for (int m = threadIdx.x; m < KP; m += MRS_THREADS) {
+                double u = 0.0;
+                if (m < p.k) {
+                    if (m + 1 < p.k) u += p.alpha[m] * s_red[2 + m] * nu;
+                    if (m > 0) u -= p.alpha[m - 1] * s_red[m] * nu;
+                }
+                s_u[m] = (T)u;
+            }
+        }
+        __syncthreads();
+    };
+
+    // ---- phase 0: y_1 = b, x = 0, p = 0, ||b||^2 and Q^T b ----
+    T tacc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) tacc[v] = (T)0;
+    for (int sl = s0 + warp; sl < s1; sl += MRS_WARPS) {
+        int i = sl * 32 + lane;
+        if (i < n) {
+            T b = (T)p.rhs[i];
+            p.Y[i] = b;
+            p.x[i] = (T)0;
+            p.P[i] = (T)0;
+            p.P[n + i] = (T)0;
+            tacc[0] += b * b;
+            T q[KP > 0 ? KP : 1];
+            load_qrow<T, KP>(p.Q, i, q);
+#pragma unroll
+            for (int m = 0; m < KP; ++m) tacc[1 + m] += q[m] * b;
+        }
+    }
+    block_partials(tacc, p.part);
+    grid_sync(p.gb, nblk, p.budget);
+    if (*err) return;
+    reduce_all(p.part);
+
+    const double r0 = sqrt(s_red[0]);
+    if (r0 == 0.0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            *p.out_its = 0;
+            *p.out_ratio = 0.0;
+        }
+        return;
+    }
+    double nu = 1.0 / r0, coef_old = 0.0, theta_t = p.shift, c_prev = 1.0, s_prev = 0.0, delta_prev = 0.0;
+    double G = r0;
+    double nu_p = 0.0, delta_pp = 0.0, theta_p = 1.0, xcoef_p = 0.0;
+    make_u(nu);
+
+    int its = 0;
+    double ratio = 1.0;
+    for (int j = 1; j <= p.maxit; ++j) {
+        T* Ycur = p.Y + (size_t)((j - 1) % 3) * n;
+        T* Yold = p.Y + (size_t)((j + 1) % 3) * n;
+        T* Ynew = p.Y + (size_t)(j % 3) * n;
+        T* Pj1 = p.P + (size_t)((j - 1) & 1) * n;
+        const T tnu = (T)(p.sign * nu), tsg = (T)p.sign, tco = (T)coef_old;
+        const T tnp = (T)nu_p, tdpp = (T)delta_pp, tthp = (T)(1.0 / theta_p), txp = (T)xcoef_p;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) tacc[v] = (T)0;
+        for (int sl = s0 + warp; sl < s1; sl += MRS_WARPS) {
+            const int base = __ldg(&p.sptr[sl]);
+            const int width = (__ldg(&p.sptr[sl + 1]) - base) >> 5;
+            T acc = (T)0;
+            const int* cp = p.col + base + lane;
+            const T* vp = p.val + base + lane;
+#pragma unroll 4
+            for (int kk = 0; kk < width; ++kk) acc += __ldg(vp + kk * 32) * __ldcg(&Ycur[__ldg(cp + kk * 32)]);
+            const int i = sl * 32 + lane;
+            if (i < n) {
+                T yold = (j >= 2) ? __ldcg(&Yold[i]) : (T)0;
+                T q[KP > 0 ? KP : 1];
+                load_qrow<T, KP>(p.Q, i, q);
+                T dq = (T)0;
+#pragma unroll
+                for (int m = 0; m < KP; ++m) dq += q[m] * s_u[m];
+                T ynew = tnu * acc - tsg * dq + tco * yold;
+                Ynew[i] = ynew;
+                tacc[0] += ynew * ynew;
+#pragma unroll
+                for (int m = 0; m < KP; ++m) tacc[1 + m] += q[m] * ynew;
+                if (j >= 2) {
+                    T pv = (tnp * yold - tdpp * Pj1[i]) * tthp;
+                    Pj1[i] = pv;
+                    p.x[i] += txp * pv;
+                }
+            }
+        }
+        double* buf = p.part + (size_t)(j & 1) * NV * nblk;
+        block_partials(tacc, buf);
+        grid_sync(p.gb, nblk, p.budget);
+        if (*err) break;
+        reduce_all(buf);
+
+        const double beta = sqrt(s_red[0]);
+        const double theta = sqrt(theta_t * theta_t + beta * beta);
+        const double c = theta_t / theta, s = beta / theta;
+        const double delta = -s_prev * beta;
+        const double theta_t_next = c_prev * theta;
+        const double xcoef = G * c;
+        const double Gn = -G * s;
+        ratio = fabs(Gn) / r0;
+        its = j;
+        if (ratio < p.tol || j == p.maxit) {
+            T* Pj = p.P + (size_t)(j & 1) * n;
+            const T tn = (T)nu, td = (T)delta_prev, tth = (T)(1.0 / theta), tx = (T)xcoef;
+            for (int sl = s0 + warp; sl < s1; sl += MRS_WARPS) {
+                int i = sl * 32 + lane;
+                if (i < n) {
+                    T pv = (tn * __ldcg(&Ycur[i]) - td * Pj[i]) * tth;
+                    p.x[i] += tx * pv;
+                }
+            }
+            break;
+        }
+        nu_p = nu;
+        delta_pp = delta_prev;
+        theta_p = theta;
+        xcoef_p = xcoef;
+        coef_old = beta * nu;
+        nu = (beta != 0.0) ? 1.0 / beta : 0.0;
+        s_prev = s;
+        c_prev = c;
+        delta_prev = delta;
+        theta_t = theta_t_next;
+        G = Gn;
+        make_u(nu);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *p.out_its = its;
+        *p.out_ratio = ratio;
+    }
+}
+
+// block b owns slices [blk[b], blk[b+1]), balanced by stored entries
+__global__ void k_partition(const int* sptr, int nslices, int nblk, int* blk) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > nblk) return;
+    long long total = sptr[nslices];
+    if (b == nblk) {
+        blk[b] = nslices;
+        return;
+    }
+    // slices also carry fixed per-row work (Q row, vectors): weight = stored + 32*8
+    long long wtot = total + (long long)nslices * 256;
+    long long target = wtot * b / nblk;
+    int lo = 0, hi = nslices;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        long long w = (long long)sptr[mid] + (long long)mid * 256;
+        if (w < target) lo = mid + 1;
+        else hi = mid;
+    }
+    blk[b] = lo;
+}
+
+template <class T, int KP>
+static asss_status launch_mrs(const Ctx& c, MrsWork* w, const DSell<T>& J, const T* Q, const double* alpha,
+                              int k, double shift, double sign, const double* rhs, T* x, T* Y, T* P, double tol,
+                              int maxit) {
+    int occ = 0;
+    ASSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mrs<T, KP>, MRS_THREADS, 0));
+    if (occ < 1) {
+        set_error("mrs kernel cannot be resident");
+        return ASSS_ERR_CUDA;
+    }
+    if (occ > 4) occ = 4;
+    int nblk = c.sms * occ;
+    int need = cdiv(J.nslices, MRS_WARPS);
+    if (need < 1) need = 1;
+    if (nblk > need) nblk = need;
+    if (w->part_key != (const void*)&J || w->part_nblk != nblk) {
+        k_partition<<<cdiv(nblk + 1, 128), 128, 0, c.stream>>>(J.sptr.p, J.nslices, nblk, w->blk_slice.p);
+        ASSS_CHECK_LAUNCH();
+        w->part_key = (const void*)&J;
+        w->part_nblk = nblk;
+    }
+    ASSS_CUDA(cudaMemsetAsync(w->bar.p, 0, 2 * sizeof(unsigned), c.stream));
+    ASSS_CUDA(cudaMemsetAsync(w->err.p, 0, sizeof(int), c.stream));
+    MrsParams<T> prm;
+    prm.n = J.n;
+    prm.sptr = J.sptr.p;
+    prm.col = J.col.p;
+    prm.val = J.val.p;
+    prm.Q = Q;
+    prm.alpha = alpha;
+    prm.k = k;
+    prm.shift = shift;
+    prm.sign = sign;
+    prm.rhs = rhs;
+    prm.x = x;
+    prm.Y = Y;
+    prm.P = P;
+    prm.part = w->part.p;
+    prm.gb.count = w->bar.p;
+    prm.gb.gen = w->bar.p + 1;
+    prm.gb.err = w->err.p;
+    prm.blk_slice = w->blk_slice.p;
+    prm.tol = tol;
+    prm.maxit = maxit;
+    prm.budget = c.wait_cycles;
+    prm.out_its = w->out_its.p;
+    prm.out_ratio = w->out_ratio.p;
+    void* args[] = {&prm};
+    ASSS_CUDA(cudaLaunchCooperativeKernel((const void*)k_mrs<T, KP>, dim3(nblk), dim3(MRS_THREADS), args, 0,
+                                          c.stream));
+    return ASSS_OK;
+}
+
+template <class T>
+static asss_status dispatch_mrs(const Ctx& c, MrsWork* w, const DSell<T>& J, const T* Q, const double* alpha,
+                                int k, int kp, double shift, double sign, const double* rhs, T* x, T* Y, T* P,
+                                double tol, int maxit) {
+    switch (kp) {
+#define ASSS_MRS_CASE(KPV) \
+    case KPV:              \
+        return launch_mrs<T, KPV>(c, w, J, Q, alpha, k, shift, sign, rhs, x, Y, P, tol, maxit);
+        ASSS_MRS_CASE(0)
+        ASSS_MRS_CASE(4)
+        ASSS_MRS_CASE(8)
+        ASSS_MRS_CASE(12)
+        ASSS_MRS_CASE(16)
+        ASSS_MRS_CASE(20)
+        ASSS_MRS_CASE(24)
+        ASSS_MRS_CASE(32)
+        ASSS_MRS_CASE(48)
+        ASSS_MRS_CASE(64)
+#undef ASSS_MRS_CASE
+        default:
+            set_error("unsupported padded Lanczos width %d", kp);
+            return ASSS_ERR_UNSUPPORTED;
+    }
+}
+
+asss_status mrs_solve(const Ctx& c, MrsWork* w, const MrsOperator& op, bool fp32, double shift, double sign,
+                      const double* rhs, double* x64, float* x32, double tol, int maxit, MrsResult* res,
+                      bool sync_result) {
+    int n = w->n;
+    if (fp32) {
+        if (!op.J32 || !x32) {
+            set_error("FP32 mrs needs the FP32 operator and an FP32 output");
+            return ASSS_ERR_ARG;
+        }
+        if (!w->Y32.p) {
+            ASSS_TRY(w->Y32.alloc((int64_t)3 * n));
+            ASSS_TRY(w->P32.alloc((int64_t)2 * n));
+        }
+        ASSS_TRY(dispatch_mrs<float>(c, w, *op.J32, op.Q32, op.alpha, op.k, op.kp, shift, sign, rhs, x32,
+                                     w->Y32.p, w->P32.p, tol, maxit));
+    } else {
+        if (!op.J64 || !x64) {
+            set_error("FP64 mrs needs the FP64 operator and an FP64 output");
+            return ASSS_ERR_ARG;
+        }
+        if (!w->Y64.p) {
+            ASSS_TRY(w->Y64.alloc((int64_t)3 * n));
+            ASSS_TRY(w->P64.alloc((int64_t)2 * n));
+        }
+        ASSS_TRY(dispatch_mrs<double>(c, w, *op.J64, op.Q64, op.alpha, op.k, op.kp, shift, sign, rhs, x64,
+                                      w->Y64.p, w->P64.p, tol, maxit));
+    }
+    if (sync_result && res) {
+        int herr = 0;
+        ASSS_CUDA(cudaMemcpyAsync(&res->its, w->out_its.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+        ASSS_CUDA(cudaMemcpyAsync(&res->ratio, w->out_ratio.p, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+        ASSS_CUDA(cudaMemcpyAsync(&herr, w->err.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+        ASSS_CUDA(cudaStreamSynchronize(c.stream));
+        res->status = herr;
+        if (herr) {
+            set_error("mrs: a grid barrier wait exceeded its budget");
+            return (asss_status)herr;
+        }
+    }
+    return ASSS_OK;
+}
+
+}  // namespace asss

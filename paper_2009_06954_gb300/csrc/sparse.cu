@@ -1,0 +1,600 @@
+// Sparse-matrix plumbing: CSR upload/validation, transpose, SpMV, the pattern of
+// Abar S + (Abar S)^T, SELL-C conversion, scans and deterministic dot products.
+#include <cstdarg>
+#include <cstring>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace asss {
+
+// ---------------------------------------------------------------------------
+// error text
+// ---------------------------------------------------------------------------
+static thread_local char g_err[1024] = {0};
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+const char* get_error() { return g_err; }
+
+asss_status make_ctx(Ctx& c, void* stream, double wait_timeout_ms) {
+    c.stream = (cudaStream_t)stream;
+    ASSS_CUDA(cudaGetDevice(&c.device));
+    ASSS_CUDA(cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, c.device));
+    ASSS_CUDA(cudaDeviceGetAttribute(&c.clock_khz, cudaDevAttrClockRate, c.device));
+    if (c.clock_khz <= 0) c.clock_khz = 2000000;
+    double ms = wait_timeout_ms > 0 ? wait_timeout_ms : 2000.0;
+    // clock64 counts SM cycles; use the maximum clock so the budget is an upper bound in time
+    c.wait_cycles = (long long)(ms * (double)c.clock_khz);
+    return ASSS_OK;
+}
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ---------------------------------------------------------------------------
+// scans
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long block_excl_scan_1024(long long v, long long* total) {
+    __shared__ long long ws[32];
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        long long y = (lane < (int)(blockDim.x >> 5)) ? ws[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            long long z = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += z;
+        }
+        ws[lane] = y;
+    }
+    __syncthreads();
+    long long add = warp > 0 ? ws[warp - 1] : 0;
+    *total = ws[31];
+    long long r = x + add - v;
+    __syncthreads();
+    return r;
+}
+
+template <class TO>
+__global__ void k_scan1(const int* in, TO* out, long long* bsum, int n) {
+    int i = blockIdx.x * 1024 + threadIdx.x;
+    long long v = (i < n) ? (long long)in[i] : 0;
+    long long tot;
+    long long ex = block_excl_scan_1024(v, &tot);
+    if (i < n) out[i] = (TO)ex;
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void k_scan2(long long* bsum, int nb, long long* total) {
+    long long carry = 0;
+    for (int base = 0; base < nb; base += 1024) {
+        int i = base + threadIdx.x;
+        long long v = (i < nb) ? bsum[i] : 0;
+        long long tot;
+        long long ex = block_excl_scan_1024(v, &tot);
+        if (i < nb) bsum[i] = ex + carry;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+template <class TO>
+__global__ void k_scan3(TO* out, const long long* bsum, int n, const long long* total) {
+    int i = blockIdx.x * 1024 + threadIdx.x;
+    if (i < n) out[i] += (TO)bsum[blockIdx.x];
+    if (i == 0) out[n] = (TO)(*total);
+}
+
+template <class TO>
+static asss_status scan_impl(const int* cnt, TO* out, int n, long long* total_h, cudaStream_t s) {
+    int nb = cdiv(n, 1024);
+    if (nb == 0) nb = 1;
+    DBuf<long long> bsum;
+    ASSS_TRY(bsum.alloc(nb + 1));
+    k_scan1<TO><<<nb, 1024, 0, s>>>(cnt, out, bsum.p, n);
+    ASSS_CHECK_LAUNCH();
+    k_scan2<<<1, 1024, 0, s>>>(bsum.p, nb, bsum.p + nb);
+    ASSS_CHECK_LAUNCH();
+    k_scan3<TO><<<nb, 1024, 0, s>>>(out, bsum.p, n, bsum.p + nb);
+    ASSS_CHECK_LAUNCH();
+    if (total_h) {
+        ASSS_CUDA(cudaMemcpyAsync(total_h, bsum.p + nb, sizeof(long long), cudaMemcpyDeviceToHost, s));
+        ASSS_CUDA(cudaStreamSynchronize(s));
+    }
+    return ASSS_OK;
+}
+
+asss_status exclusive_scan(const int* cnt, int* out, int n, int64_t* total, cudaStream_t s) {
+    long long t = 0;
+    ASSS_TRY(scan_impl<int>(cnt, out, n, &t, s));
+    if (t >= (1LL << 31) - 1) {
+        set_error("scan total %lld exceeds the 32-bit index range", t);
+        return ASSS_ERR_UNSUPPORTED;
+    }
+    if (total) *total = t;
+    return ASSS_OK;
+}
+
+asss_status exclusive_scan64(const int* cnt, long long* out, int n, long long* total, cudaStream_t s) {
+    return scan_impl<long long>(cnt, out, n, total, s);
+}
+
+// ---------------------------------------------------------------------------
+// deterministic dot products: fixed grid, per-block partials, ordered final sum
+// ---------------------------------------------------------------------------
+constexpr int DOT_BLOCKS = 296;
+constexpr int DOT_THREADS = 512;
+
+template <class T>
+__global__ void k_dot_partial(const T* a, const T* b, int n, double* part) {
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        acc += (double)a[i] * (double)b[i];
+    __shared__ double sw[32];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = (threadIdx.x < (blockDim.x >> 5)) ? sw[threadIdx.x] : 0.0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) part[blockIdx.x] = v;
+    }
+}
+
+__global__ void k_sum_partials(const double* part, int np, double* out) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < np; i += 32) acc += part[i];
+    acc = warp_sum(acc);
+    if (threadIdx.x == 0) *out = acc;
+}
+
+template <class T>
+static asss_status dot_impl(const T* a, const T* b, int n, double* d_out, cudaStream_t s) {
+    static thread_local DBuf<double> part;
+    if (!part.p) ASSS_TRY(part.alloc(DOT_BLOCKS));
+    k_dot_partial<T><<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(a, b, n, part.p);
+    ASSS_CHECK_LAUNCH();
+    k_sum_partials<<<1, 32, 0, s>>>(part.p, DOT_BLOCKS, d_out);
+    ASSS_CHECK_LAUNCH();
+    return ASSS_OK;
+}
+
+asss_status dot(const double* a, const double* b, int n, double* d_out, cudaStream_t s) {
+    return dot_impl<double>(a, b, n, d_out, s);
+}
+asss_status dot_f(const float* a, const float* b, int n, double* d_out, cudaStream_t s) {
+    return dot_impl<float>(a, b, n, d_out, s);
+}
+
+// ---------------------------------------------------------------------------
+// CSR upload and validation
+// ---------------------------------------------------------------------------
+__global__ void k_rowptr_check(const long long* rp64, int* rp32, int n, long long nnz, int* flag) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > n) return;
+    long long v = rp64[i];
+    if (i == 0 && v != 0) atomicOr(flag, 1);
+    if (i == n && v != nnz) atomicOr(flag, 1);
+    if (i < n && rp64[i + 1] < v) atomicOr(flag, 1);
+    rp32[i] = (int)v;
+}
+
+__global__ void k_col_check(const int* rp, const int* ci, int n, int* flag) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int prev = -1;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+        int c = ci[e];
+        if (c < 0 || c >= n || c <= prev) {
+            atomicOr(flag, 2);
+            return;
+        }
+        prev = c;
+    }
+}
+
+asss_status upload_csr(const asss_csr* A, DCsr& out, bool need_values, cudaStream_t s) {
+    if (!A || A->n <= 0 || A->nnz < 0 || !A->row_ptr || (A->nnz > 0 && !A->col_idx)) {
+        set_error("invalid CSR argument");
+        return ASSS_ERR_ARG;
+    }
+    if (A->n >= (1LL << 31) - 1 || A->nnz >= (1LL << 31) - 1) {
+        set_error("n or nnz beyond the 32-bit index range of this build");
+        return ASSS_ERR_UNSUPPORTED;
+    }
+    if (need_values && A->nnz > 0 && !A->val) {
+        set_error("CSR values required");
+        return ASSS_ERR_ARG;
+    }
+    int n = (int)A->n, nnz = (int)A->nnz;
+    out.n = n;
+    out.nnz = nnz;
+    DBuf<long long> rp64;
+    ASSS_TRY(to_device(rp64, (const long long*)A->row_ptr, n + 1, s));
+    ASSS_TRY(out.rp.alloc(n + 1));
+    ASSS_TRY(to_device(out.ci, A->col_idx, nnz, s));
+    if (A->val) ASSS_TRY(to_device(out.v, A->val, nnz, s));
+    DBuf<int> flag;
+    ASSS_TRY(flag.alloc(1));
+    ASSS_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
+    k_rowptr_check<<<cdiv(n + 1, 256), 256, 0, s>>>(rp64.p, out.rp.p, n, (long long)nnz, flag.p);
+    ASSS_CHECK_LAUNCH();
+    int hflag = 0;
+    ASSS_CUDA(cudaMemcpyAsync(&hflag, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ASSS_CUDA(cudaStreamSynchronize(s));
+    if (hflag) {
+        set_error("row_ptr is not a valid CSR row pointer");
+        return ASSS_ERR_PATTERN;
+    }
+    k_col_check<<<cdiv(n, 256), 256, 0, s>>>(out.rp.p, out.ci.p, n, flag.p);
+    ASSS_CHECK_LAUNCH();
+    ASSS_CUDA(cudaMemcpyAsync(&hflag, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ASSS_CUDA(cudaStreamSynchronize(s));
+    if (hflag) {
+        set_error("column indices out of range, unsorted or duplicated within a row");
+        return ASSS_ERR_PATTERN;
+    }
+    return ASSS_OK;
+}
+
+asss_status copy_csr(const DCsr& a, DCsr& out, cudaStream_t s) {
+    out.n = a.n;
+    out.nnz = a.nnz;
+    ASSS_TRY(out.rp.alloc(a.n + 1));
+    ASSS_TRY(out.ci.alloc(a.nnz));
+    ASSS_CUDA(cudaMemcpyAsync(out.rp.p, a.rp.p, sizeof(int) * (a.n + 1), cudaMemcpyDeviceToDevice, s));
+    ASSS_CUDA(cudaMemcpyAsync(out.ci.p, a.ci.p, sizeof(int) * a.nnz, cudaMemcpyDeviceToDevice, s));
+    if (a.v.p) {
+        ASSS_TRY(out.v.alloc(a.nnz));
+        ASSS_CUDA(cudaMemcpyAsync(out.v.p, a.v.p, sizeof(double) * a.nnz, cudaMemcpyDeviceToDevice, s));
+    }
+    return ASSS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// transpose (rows of the result sorted by column; deterministic)
+// ---------------------------------------------------------------------------
+__global__ void k_count_cols(const int* ci, int nnz, int* cnt) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < nnz) atomicAdd(&cnt[ci[e]], 1);
+}
+
+__global__ void k_scatter_t(const int* rp, const int* ci, const double* v, int n, const int* rpT,
+                            int* fill, int* ciT, double* vT, int* srcpos) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+        int c = ci[e];
+        int pos = rpT[c] + atomicAdd(&fill[c], 1);
+        ciT[pos] = i;
+        if (v) vT[pos] = v[e];
+        if (srcpos) srcpos[pos] = e;
+    }
+}
+
+__global__ void k_sort_rows(const int* rp, int n, int* ci, double* v, int* aux) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int b = rp[i], e = rp[i + 1];
+    for (int a = b + 1; a < e; ++a) {
+        int key = ci[a];
+        double kv = v ? v[a] : 0.0;
+        int ka = aux ? aux[a] : 0;
+        int t = a - 1;
+        while (t >= b && ci[t] > key) {
+            ci[t + 1] = ci[t];
+            if (v) v[t + 1] = v[t];
+            if (aux) aux[t + 1] = aux[t];
+            --t;
+        }
+        ci[t + 1] = key;
+        if (v) v[t + 1] = kv;
+        if (aux) aux[t + 1] = ka;
+    }
+}
+
+asss_status transpose_csr(const DCsr& a, DCsr& t, DBuf<int>* srcpos, cudaStream_t s) {
+    int n = a.n, nnz = a.nnz;
+    t.n = n;
+    t.nnz = nnz;
+    DBuf<int> cnt, fill;
+    ASSS_TRY(cnt.alloc(n));
+    ASSS_TRY(fill.alloc(n));
+    ASSS_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int) * n, s));
+    ASSS_CUDA(cudaMemsetAsync(fill.p, 0, sizeof(int) * n, s));
+    if (nnz) k_count_cols<<<cdiv(nnz, 256), 256, 0, s>>>(a.ci.p, nnz, cnt.p);
+    ASSS_CHECK_LAUNCH();
+    ASSS_TRY(t.rp.alloc(n + 1));
+    ASSS_TRY(exclusive_scan(cnt.p, t.rp.p, n, nullptr, s));
+    ASSS_TRY(t.ci.alloc(nnz));
+    if (a.v.p) ASSS_TRY(t.v.alloc(nnz));
+    if (srcpos) ASSS_TRY(srcpos->alloc(nnz));
+    k_scatter_t<<<cdiv(n, 256), 256, 0, s>>>(a.rp.p, a.ci.p, a.v.p, n, t.rp.p, fill.p, t.ci.p, t.v.p,
+                                              srcpos ? srcpos->p : nullptr);
+    ASSS_CHECK_LAUNCH();
+    k_sort_rows<<<cdiv(n, 128), 128, 0, s>>>(t.rp.p, n, t.ci.p, t.v.p, srcpos ? srcpos->p : nullptr);
+    ASSS_CHECK_LAUNCH();
+    return ASSS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// CSR SpMV (FP64): y = A x, LANES threads per row
+// ---------------------------------------------------------------------------
+template <int LANES>
+__global__ void k_spmv(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                       const double* __restrict__ v, const double* __restrict__ x,
+                       double* __restrict__ y, const double* __restrict__ lscale) {
+    int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    int row = gt / LANES;
+    int sub = gt % LANES;
+    if (row >= n) return;
+    double acc = 0.0;
+    for (int e = rp[row] + sub; e < rp[row + 1]; e += LANES) acc += v[e] * __ldg(&x[ci[e]]);
+#pragma unroll
+    for (int o = LANES / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, LANES);
+    if (sub == 0) y[row] = lscale ? lscale[row] * acc : acc;
+}
+
+asss_status spmv(const DCsr& A, const double* x, double* y, const double* lscale, cudaStream_t s) {
+    int n = A.n;
+    double mean = n ? (double)A.nnz / n : 0;
+    int threads = 256;
+    if (mean <= 6) {
+        k_spmv<1><<<cdiv(n, threads), threads, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, x, y, lscale);
+    } else if (mean <= 12) {
+        k_spmv<2><<<cdiv((int64_t)n * 2, threads), threads, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, x, y, lscale);
+    } else if (mean <= 24) {
+        k_spmv<4><<<cdiv((int64_t)n * 4, threads), threads, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, x, y, lscale);
+    } else if (mean <= 64) {
+        k_spmv<8><<<cdiv((int64_t)n * 8, threads), threads, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, x, y, lscale);
+    } else {
+        k_spmv<32><<<cdiv((int64_t)n * 32, threads), threads, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, x, y, lscale);
+    }
+    ASSS_CHECK_LAUNCH();
+    return ASSS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// the symmetric pattern P = pat(Abar S) + pat(Abar S)^T (+ diagonal), row by row:
+// row i of P = {i} u U_{l in Abar_i} S_l u U_{l in S^T_i} Abar^T_l
+// One warp per row gathers the candidates into shared memory, sorts them
+// (bitonic network) and keeps the distinct values.
+// ---------------------------------------------------------------------------
+__global__ void k_pattern_cand_count(int n, const int* arp, const int* aci, const int* srp,
+                                     const int* strp, const int* stci, const int* atrp, int* cnt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c = 1;
+    for (int e = arp[i]; e < arp[i + 1]; ++e) {
+        int l = aci[e];
+        c += srp[l + 1] - srp[l];
+    }
+    for (int e = strp[i]; e < strp[i + 1]; ++e) {
+        int l = stci[e];
+        c += atrp[l + 1] - atrp[l];
+    }
+    cnt[i] = c;
+}
+
+__global__ void k_max_int(const int* a, int n, int* out) {
+    int m = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) m = max(m, a[i]);
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+constexpr int PAT_WARPS = 4;
+
+__global__ void k_pattern_rows(int n, const int* arp, const int* aci, const int* srp, const int* sci,
+                               const int* strp, const int* stci, const int* atrp, const int* atci,
+                               int cap, const int* prp, int* counts, int* pci) {
+    extern __shared__ int smem[];
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int* buf = smem + warp * cap;
+    for (int i = blockIdx.x * PAT_WARPS + warp; i < n; i += gridDim.x * PAT_WARPS) {
+        int pos = 0;
+        if (lane == 0) buf[0] = i;
+        pos = 1;
+        for (int e = arp[i]; e < arp[i + 1]; ++e) {
+            int l = aci[e];
+            int b = srp[l], len = srp[l + 1] - b;
+            for (int t = lane; t < len; t += 32) buf[pos + t] = sci[b + t];
+            pos += len;
+        }
+        for (int e = strp[i]; e < strp[i + 1]; ++e) {
+            int l = stci[e];
+            int b = atrp[l], len = atrp[l + 1] - b;
+            for (int t = lane; t < len; t += 32) buf[pos + t] = atci[b + t];
+            pos += len;
+        }
+        int p2 = 32;
+        while (p2 < pos) p2 <<= 1;
+        for (int t = pos + lane; t < p2; t += 32) buf[t] = 0x7fffffff;
+        __syncwarp();
+        for (int size = 2; size <= p2; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int t = lane; t < (p2 >> 1); t += 32) {
+                    int lo = 2 * stride * (t / stride) + (t % stride);
+                    int hi = lo + stride;
+                    bool up = ((lo & size) == 0);
+                    int a = buf[lo], bb = buf[hi];
+                    if ((a > bb) == up) {
+                        buf[lo] = bb;
+                        buf[hi] = a;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        int base = prp ? prp[i] : 0;
+        int written = 0;
+        for (int t0 = 0; t0 < pos; t0 += 32) {
+            int t = t0 + lane;
+            bool u = (t < pos) && (t == 0 || buf[t] != buf[t - 1]);
+            unsigned m = __ballot_sync(0xffffffffu, u);
+            if (pci && u) pci[base + written + __popc(m & ((1u << lane) - 1u))] = buf[t];
+            written += __popc(m);
+        }
+        if (counts && lane == 0) counts[i] = written;
+        __syncwarp();
+    }
+}
+
+__global__ void k_mirror(int n, const int* prp, const int* pci, int* mirror, int* diagpos) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int k = prp[i]; k < prp[i + 1]; ++k) {
+        int j = pci[k];
+        int lo = prp[j], hi = prp[j + 1] - 1, f = -1;
+        while (lo <= hi) {
+            int mid = (lo + hi) >> 1;
+            int c = pci[mid];
+            if (c == i) {
+                f = mid;
+                break;
+            }
+            if (c < i) lo = mid + 1;
+            else hi = mid - 1;
+        }
+        mirror[k] = f;
+        if (j == i) diagpos[i] = k;
+    }
+}
+
+asss_status build_pattern(const DCsr& Abar, const DCsr& AbarT, const DCsr& S, const DCsr& ST, DCsr& P,
+                          DBuf<int>& mirror, DBuf<int>& diagpos, cudaStream_t s) {
+    int n = Abar.n;
+    DBuf<int> cnt, mx;
+    ASSS_TRY(cnt.alloc(n));
+    ASSS_TRY(mx.alloc(1));
+    k_pattern_cand_count<<<cdiv(n, 256), 256, 0, s>>>(n, Abar.rp.p, Abar.ci.p, S.rp.p, ST.rp.p, ST.ci.p,
+                                                       AbarT.rp.p, cnt.p);
+    ASSS_CHECK_LAUNCH();
+    ASSS_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(int), s));
+    k_max_int<<<256, 256, 0, s>>>(cnt.p, n, mx.p);
+    ASSS_CHECK_LAUNCH();
+    int hmax = 0;
+    ASSS_CUDA(cudaMemcpyAsync(&hmax, mx.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ASSS_CUDA(cudaStreamSynchronize(s));
+    int cap = 32;
+    while (cap < hmax) cap <<= 1;
+    size_t smem = (size_t)cap * PAT_WARPS * sizeof(int);
+    if (smem > 200 * 1024) {
+        set_error("a row of Abar*S has %d candidate entries; this build sorts at most %d per row",
+                  hmax, (200 * 1024) / (int)(PAT_WARPS * sizeof(int)));
+        return ASSS_ERR_UNSUPPORTED;
+    }
+    ASSS_CUDA(cudaFuncSetAttribute(k_pattern_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int grid = cdiv(n, PAT_WARPS);
+    if (grid > 65535 * 8) grid = 65535 * 8;
+    k_pattern_rows<<<grid, PAT_WARPS * 32, smem, s>>>(n, Abar.rp.p, Abar.ci.p, S.rp.p, S.ci.p, ST.rp.p,
+                                                      ST.ci.p, AbarT.rp.p, AbarT.ci.p, cap, nullptr,
+                                                      cnt.p, nullptr);
+    ASSS_CHECK_LAUNCH();
+    P.n = n;
+    ASSS_TRY(P.rp.alloc(n + 1));
+    int64_t tot = 0;
+    ASSS_TRY(exclusive_scan(cnt.p, P.rp.p, n, &tot, s));
+    P.nnz = (int)tot;
+    ASSS_TRY(P.ci.alloc(tot));
+    k_pattern_rows<<<grid, PAT_WARPS * 32, smem, s>>>(n, Abar.rp.p, Abar.ci.p, S.rp.p, S.ci.p, ST.rp.p,
+                                                      ST.ci.p, AbarT.rp.p, AbarT.ci.p, cap, P.rp.p,
+                                                      nullptr, P.ci.p);
+    ASSS_CHECK_LAUNCH();
+    ASSS_TRY(mirror.alloc(tot));
+    ASSS_TRY(diagpos.alloc(n));
+    k_mirror<<<cdiv(n, 256), 256, 0, s>>>(n, P.rp.p, P.ci.p, mirror.p, diagpos.p);
+    ASSS_CHECK_LAUNCH();
+    return ASSS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// SELL-C (C = 32) from CSR, optionally leaving out diagonal entries
+// ---------------------------------------------------------------------------
+__global__ void k_sell_width(int n, const int* rp, const int* ci, int skip_diag, int nslices, int* w) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nslices) return;
+    int m = 0;
+    for (int r = s * 32; r < min(n, s * 32 + 32); ++r) {
+        int len = rp[r + 1] - rp[r];
+        if (skip_diag) {
+            for (int e = rp[r]; e < rp[r + 1]; ++e)
+                if (ci[e] == r) {
+                    --len;
+                    break;
+                }
+        }
+        m = max(m, len);
+    }
+    w[s] = m * 32;
+}
+
+template <class T>
+__global__ void k_sell_fill(int n, const int* rp, const int* ci, const double* v, int skip_diag,
+                            const int* sptr, int* scol, T* sval) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    int s = r >> 5, lane = r & 31;
+    if (s * 32 >= n + 31) return;
+    int base = sptr[s], width = (sptr[s + 1] - base) >> 5;
+    int kk = 0;
+    if (r < n) {
+        for (int e = rp[r]; e < rp[r + 1]; ++e) {
+            if (skip_diag && ci[e] == r) continue;
+            scol[base + kk * 32 + lane] = ci[e];
+            sval[base + kk * 32 + lane] = (T)v[e];
+            ++kk;
+        }
+    }
+    int pad = r < n ? r : 0;
+    for (; kk < width; ++kk) {
+        scol[base + kk * 32 + lane] = pad;
+        sval[base + kk * 32 + lane] = (T)0;
+    }
+}
+
+template <class T>
+asss_status build_sell(const DCsr& A, bool skip_diag, DSell<T>& out, cudaStream_t s) {
+    int n = A.n;
+    int ns = cdiv(n, 32);
+    out.n = n;
+    out.nslices = ns;
+    DBuf<int> w;
+    ASSS_TRY(w.alloc(ns));
+    k_sell_width<<<cdiv(ns, 128), 128, 0, s>>>(n, A.rp.p, A.ci.p, skip_diag ? 1 : 0, ns, w.p);
+    ASSS_CHECK_LAUNCH();
+    ASSS_TRY(out.sptr.alloc(ns + 1));
+    int64_t tot = 0;
+    ASSS_TRY(exclusive_scan(w.p, out.sptr.p, ns, &tot, s));
+    out.nstored = tot;
+    ASSS_TRY(out.col.alloc(tot > 0 ? tot : 1));
+    ASSS_TRY(out.val.alloc(tot > 0 ? tot : 1));
+    k_sell_fill<T><<<cdiv((int64_t)ns * 32, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, skip_diag ? 1 : 0,
+                                                               out.sptr.p, out.col.p, out.val.p);
+    ASSS_CHECK_LAUNCH();
+    return ASSS_OK;
+}
+
+template asss_status build_sell<double>(const DCsr&, bool, DSell<double>&, cudaStream_t);
+template asss_status build_sell<float>(const DCsr&, bool, DSell<float>&, cudaStream_t);
+
+}  // namespace asss

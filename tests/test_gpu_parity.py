@@ -1,0 +1,247 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Every test here needs a GB300 (marked gpu).  Sizes span several 32-row slices with
+a ragged tail; the oracle computes the expected values on the same seeded inputs.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle as O
+from workloads import (convection_diffusion_2d, dissipative_hamiltonian_3d, pattern_diagonal,
+                       pattern_of, pattern_tridiagonal)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2009_06954_gb300 as p
+    return p
+
+
+def random_skew(n, per_row, seed, scale=0.1):
+    rng = np.random.default_rng(seed)
+    K = sp.random(n, n, density=per_row / (2.0 * n), random_state=rng, data_rvs=rng.standard_normal)
+    J = (K - K.T).tocsr() * scale
+    J.sum_duplicates()
+    J.sort_indices()
+    J.eliminate_zeros()
+    return J
+
+
+# ----------------------------------------------------------------------------
+# mrs (the hot kernel), same operator on both sides
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [37, 1000, 50001])
+@pytest.mark.parametrize("k", [0, 20])
+@pytest.mark.parametrize("shift,sign", [(1.0, 1.0), (1.0, -1.0), (0.5, 1.0)])
+def test_mrs_fp64_matches_oracle(pkg, n, k, shift, sign):
+    J = random_skew(n, 12, seed=n + k)
+    rng = np.random.default_rng(n)
+    b = rng.standard_normal(n)
+    Q = alpha = None
+    if k:
+        Q, alpha = O.skew_lanczos(J, rng.standard_normal(n), k)
+    kk = 0 if Q is None else Q.shape[1]
+    Sk = O.lanczos_tridiagonal(alpha) if kk else None
+
+    def apply(V):
+        out = J @ V
+        if kk:
+            out = out - Q @ (Sk @ (Q.T @ V))
+        return sign * out
+
+    xo, its_o, ratio_o, _ = O.mrs(shift, apply, b, 3000, 1e-12)
+    xg, its_g, ratio_g = pkg.mrs(J, b, Q, alpha, shift=shift, sign=sign, tol=1e-12, maxit=3000)
+    assert abs(its_g - its_o) <= 2, (its_g, its_o)
+    assert ratio_g < 1e-12
+    assert np.linalg.norm(xg - xo) <= 1e-9 * np.linalg.norm(xo)
+    true = np.linalg.norm(b - shift * xg - apply(xg)) / np.linalg.norm(b)
+    assert true <= 1e-11
+
+
+@pytest.mark.parametrize("n", [1000, 50001])
+def test_mrs_fp32(pkg, n):
+    J = random_skew(n, 12, seed=3 * n)
+    rng = np.random.default_rng(7)
+    b = rng.standard_normal(n)
+    Q, alpha = O.skew_lanczos(J, rng.standard_normal(n), 20)
+    Sk = O.lanczos_tridiagonal(alpha)
+    apply = lambda V: J @ V - Q @ (Sk @ (Q.T @ V))
+    xo, its_o, _, _ = O.mrs(1.0, apply, b, 3000, 1e-12)
+    xg, its_g, ratio_g = pkg.mrs(J, b, Q, alpha, tol=1e-5, maxit=3000, precision="mixed")
+    true = np.linalg.norm(b - xg - apply(xg)) / np.linalg.norm(b)
+    assert ratio_g < 1e-5 and true <= 5e-5
+    assert np.linalg.norm(xg - xo) <= 1e-4 * np.linalg.norm(xo)
+
+
+def test_mrs_edge_cases(pkg):
+    n = 70
+    J = random_skew(n, 6, seed=1)
+    x, its, ratio = pkg.mrs(J, np.zeros(n), tol=1e-10)
+    assert its == 0 and np.all(x == 0)
+    Z = sp.csr_matrix((np.zeros(n), np.arange(n), np.arange(n + 1)), shape=(n, n))
+    b = np.random.default_rng(2).standard_normal(n)
+    x, its, ratio = pkg.mrs(Z, b, shift=2.0, tol=1e-12)
+    assert its == 1 and np.allclose(x, b / 2.0, rtol=1e-15)
+    # 2x2 closed form: (I + J)^-1 = (I - J)/(1 + w^2)
+    w = 3.7
+    J2 = sp.csr_matrix(np.array([[0.0, w], [-w, 0.0]]))
+    b2 = np.array([0.4, -1.3])
+    x, its, ratio = pkg.mrs(J2, b2, tol=1e-15, maxit=10)
+    np.testing.assert_allclose(x, (np.eye(2) - J2.toarray()) @ b2 / (1 + w * w), rtol=1e-14)
+    assert its == 2
+
+
+# ----------------------------------------------------------------------------
+# skew-Lanczos (Fig. 2)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("reorth", [True, False])
+def test_skew_lanczos_matches_oracle(pkg, reorth):
+    n = 3001
+    J = random_skew(n, 10, seed=11)
+    q1 = np.random.default_rng(3).standard_normal(n)
+    k = 20 if reorth else 8
+    Qo, ao = O.skew_lanczos(J, q1, k, reorth=reorth)
+    Qg, ag = pkg.skew_lanczos(J, q1, k, reorth=reorth)
+    assert Qg.shape == Qo.shape
+    np.testing.assert_allclose(ag, ao, rtol=1e-10)
+    assert np.abs(Qg - Qo).max() <= 1e-9
+
+
+# ----------------------------------------------------------------------------
+# the least-squares fit of S (§2, App. A)
+# ----------------------------------------------------------------------------
+def _objective(Abar, S, gamma):
+    C = (Abar @ S).tocsr()
+    U = sp.triu(C + C.T, 1)
+    d = C.diagonal()
+    return float((U.data ** 2).sum() + gamma * ((d - 1.0) ** 2).sum())
+
+
+@pytest.mark.parametrize("case", ["cd", "dh", "dh_tri", "dh_diag"])
+def test_skew_symmetrizer_matches_oracle(pkg, case):
+    if case == "cd":
+        A, _, _ = convection_diffusion_2d(m=40)
+    else:
+        A, _, _ = dissipative_hamiltonian_3d(side=9, seed=4)
+    Abar, _, _, _ = O.equilibrate(A)
+    n = A.shape[0]
+    Sp = {"cd": pattern_of(Abar), "dh": pattern_of(Abar), "dh_tri": pattern_tridiagonal(n),
+          "dh_diag": pattern_diagonal(n)}[case]
+    So = O.skew_symmetrizer(Abar, Sp, 1.0)
+    sg, st = pkg.skew_symmetrizer(Abar, Sp, gamma=1.0)
+    Sg = sp.csr_matrix((sg, Sp.indices, Sp.indptr), shape=Sp.shape)
+    fo, fg = _objective(Abar, So, 1.0), _objective(Abar, Sg, 1.0)
+    assert fg <= fo * (1 + 1e-9) + 1e-14
+    assert np.linalg.norm(sg - So[np.repeat(np.arange(n), np.diff(Sp.indptr)), Sp.indices].A1) \
+        <= 1e-6 * np.linalg.norm(So.data)
+    assert st["lls_relgrad"] <= 1e-12
+
+
+def test_skew_symmetrizer_exact_case(pkg):
+    """Abar = (I + K) D^-1: S = D exactly on the diagonal pattern (Eqs. eq1, eq2)."""
+    rng = np.random.default_rng(3)
+    n = 500
+    K = sp.random(n, n, density=0.01, random_state=rng, data_rvs=rng.standard_normal)
+    K = sp.csr_matrix(K - K.T)
+    D = rng.uniform(0.5, 2.0, n)
+    Abar = ((sp.identity(n) + K) @ sp.diags(1.0 / D)).tocsr()
+    Abar.sort_indices()
+    sg, _ = pkg.skew_symmetrizer(Abar, pattern_diagonal(n))
+    np.testing.assert_allclose(sg, D, rtol=1e-9)
+
+
+# ----------------------------------------------------------------------------
+# whole set-up and solve
+# ----------------------------------------------------------------------------
+def test_setup_matches_oracle_cd64(pkg):
+    A, b, _ = convection_diffusion_2d(m=64)
+    o = O.AsssOracle(A, inner_tol=1e-10)
+    s = pkg.Solver(A, inner_tol=1e-10)
+    ex = s.export(A.nnz)
+    np.testing.assert_allclose(ex["dr"], o.dr, rtol=1e-15)
+    np.testing.assert_allclose(ex["dc"], o.dc, rtol=1e-15)
+    np.testing.assert_allclose(ex["d"], o.d, rtol=1e-7)
+    np.testing.assert_allclose(ex["w"], o.w, rtol=1e-7)
+    assert ex["Q"].shape == o.Q.shape
+    np.testing.assert_allclose(ex["alpha"], o.alpha, rtol=1e-6)
+    assert s.setup_stats["r"] == o.r
+
+
+@pytest.mark.parametrize("outer", ["tfqmr", "fgmres"])
+def test_solve_cd64_fp64_matches_oracle(pkg, outer):
+    A, b, xt = convection_diffusion_2d(m=64)
+    o = O.AsssOracle(A, inner_tol=1e-10)
+    xo, sto = o.solve(b, tol=1e-8, outer=outer)
+    s = pkg.Solver(A, inner_tol=1e-10, outer=outer)
+    xg, stg = s.solve(b)
+    assert stg["status"] == 0
+    res = np.linalg.norm(b - A @ xg) / np.linalg.norm(b)
+    assert res <= 1e-8
+    assert abs(stg["outer_its"] - sto["outer_its"]) <= 2, (stg["outer_its"], sto["outer_its"])
+    assert abs(stg["inner_its_avg"] - sto["inner_its_avg"]) <= 0.02 * sto["inner_its_avg"] + 2
+    assert np.linalg.norm(xg - xo) <= 1e-5 * np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solve_dh_matches_dense(pkg, precision):
+    A, b, _ = dissipative_hamiltonian_3d(side=16, seed=9)
+    s = pkg.Solver(A, precision=precision, outer="fgmres",
+                   inner_tol=1e-6 if precision == "mixed" else 1e-10)
+    x, st = s.solve(b)
+    assert st["status"] == 0
+    assert np.linalg.norm(b - A @ x) <= 1e-8 * np.linalg.norm(b)
+    xd = sp.linalg.spsolve(A.tocsc(), b)
+    assert np.linalg.norm(x - xd) <= 1e-7 * np.linalg.norm(xd)
+
+
+def test_solve_multiple_rhs_and_zero(pkg):
+    A, b, _ = dissipative_hamiltonian_3d(side=8, seed=2)
+    s = pkg.Solver(A, precision="mixed", outer="fgmres", inner_tol=1e-6)
+    B = np.column_stack([b, np.zeros_like(b), 2 * b])
+    X, st = s.solve(B)
+    assert np.all(X[:, 1] == 0)
+    np.testing.assert_allclose(X[:, 2], 2 * X[:, 0], rtol=1e-6)
+
+
+def test_adjoint_matches_dense(pkg):
+    A, b, _ = dissipative_hamiltonian_3d(side=8, seed=4)
+    n = A.shape[0]
+    s = pkg.Solver(A, precision="mixed", outer="fgmres", inner_tol=1e-6, outer_tol=1e-11)
+    x, _ = s.solve(b)
+    rng = np.random.default_rng(1)
+    xs = rng.standard_normal(n)
+    g = 2.0 * (x - xs)
+    lam, dA, st = s.solve_adjoint(g, x=x)
+    Ad = A.toarray()
+    lam_d = np.linalg.solve(Ad.T, g)
+    assert np.linalg.norm(lam - lam_d) <= 1e-9 * np.linalg.norm(lam_d)
+    rows = np.repeat(np.arange(n), np.diff(A.indptr))
+    np.testing.assert_allclose(dA, -lam[rows] * x[A.indices], rtol=1e-14)
+
+
+def test_torch_autograd(pkg):
+    import torch
+    A, b, _ = dissipative_hamiltonian_3d(side=8, seed=6)
+    n = A.shape[0]
+    s = pkg.Solver(A, precision="mixed", outer="fgmres", inner_tol=1e-6, outer_tol=1e-11)
+    bt = torch.tensor(b, device="cuda", requires_grad=True)
+    av = torch.tensor(A.data, device="cuda", requires_grad=True)
+    xs = torch.randn(n, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+    x = pkg.asss_solve(s, bt, av)
+    loss = ((x - xs) ** 2).sum()
+    loss.backward()
+    Ad = A.toarray()
+    xd = np.linalg.solve(Ad, b)
+    lam_d = np.linalg.solve(Ad.T, 2 * (xd - xs.cpu().numpy()))
+    np.testing.assert_allclose(bt.grad.cpu().numpy(), lam_d, rtol=0, atol=1e-8 * np.abs(lam_d).max())
+    rows = np.repeat(np.arange(n), np.diff(A.indptr))
+    np.testing.assert_allclose(av.grad.cpu().numpy(), -lam_d[rows] * xd[A.indices], rtol=0,
+                               atol=1e-8 * np.abs(lam_d).max() * np.abs(xd).max())
