@@ -1,0 +1,352 @@
+"""Benchmark: solves/s to a 1e-8 relative residual on the dissipative-Hamiltonian
+implicit-Euler workload (100^3 grid, n = 1e6), FP32 inner mrs / FP64 outer FGMRES.
+
+One step = one solve phase (outer Krylov + preconditioner applications + inner mrs)
+for one right-hand side, after the b-independent set-up (timed and reported
+separately, as the paper amortises it over right-hand sides).
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun each rank runs an independent replica (the single system does not
+shard in this build); value = all ranks' solves / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "solves/s to 1e-8 rel. residual"
+UNIT = "solves/s"
+WORKLOAD = ("dh3d_100: dissipative-Hamiltonian implicit-Euler step A = E + h(R - J), 100^3 grid "
+            "(n = 1,000,000, nnz = 6,940,000), S on the pattern of A, k = 20, FP32 inner mrs "
+            "(tol 1e-6) / FP64 outer FGMRES(60), outer tol 1e-8")
+SIDE = 100
+CPU_SAMPLE_SIDE = 24
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _make_rhs(A_parts, n, seed, count):
+    import numpy as np
+    out = []
+    E = A_parts["E"]
+    for c in range(count):
+        r = np.random.default_rng(seed + 1000 + c)
+        out.append(E * r.standard_normal(n) + 1e-2 * r.standard_normal(n))
+    return out
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle baseline (subprocess, one thread)
+# ----------------------------------------------------------------------------
+def cpu_worker(side, steps, warmup, budget_s):
+    import numpy as np
+
+    import oracle
+    from workloads import dissipative_hamiltonian_3d
+    A, b, parts = dissipative_hamiltonian_3d(side=side, seed=1)
+    n = A.shape[0]
+    t0 = time.perf_counter()
+    o = oracle.AsssOracle(A, inner_tol=1e-6)
+    t_setup = time.perf_counter() - t0
+    rhs = _make_rhs(parts, n, 1, 4)
+    for w in range(warmup):
+        o.solve(rhs[w % 4], tol=1e-8, outer="fgmres")
+    times = []
+    relres = []
+    t_start = time.perf_counter()
+    for s in range(steps):
+        t = time.perf_counter()
+        x, st = o.solve(rhs[s % 4], tol=1e-8, outer="fgmres")
+        times.append(time.perf_counter() - t)
+        relres.append(st["relres"])
+        if budget_s and time.perf_counter() - t_start > budget_s and s + 1 >= 1:
+            break
+    print(json.dumps({"n": n, "solves": len(times), "seconds": sum(times), "t_setup_s": t_setup,
+                      "max_relres": max(relres), "inner_avg": st["inner_its_avg"],
+                      "outer_its": st["outer_its"]}))
+
+
+def run_cpu_baseline(steps, warmup, budget_s):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[v] = "1"
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", "--steps", str(steps), "--warmup",
+           str(warmup), "--budget", str(budget_s)]
+    p = subprocess.run(cmd, capture_output=True, text=True, env=env, cwd=ROOT)
+    if p.returncode != 0:
+        raise RuntimeError("CPU baseline worker failed:\n" + p.stdout + p.stderr)
+    r = json.loads(p.stdout.strip().splitlines()[-1])
+    n_full = SIDE ** 3
+    per_s = r["solves"] / r["seconds"]
+    value = per_s * r["n"] / n_full
+    return {
+        "value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "sample": (f"FP64 numpy/scipy oracle, solve phase of the same generator at {CPU_SAMPLE_SIDE}^3 "
+                   f"(n = {r['n']}), {r['solves']} solve(s) in {r['seconds']:.2f} s "
+                   f"({per_s:.3f} solves/s, inner avg {r['inner_avg']:.1f}, outer {r['outer_its']}), scaled "
+                   f"to n = {n_full} by unknowns; set-up {r['t_setup_s']:.1f} s untimed"),
+        "max_relres": r["max_relres"],
+    }
+
+
+# ----------------------------------------------------------------------------
+# clocks
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 8:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    smax.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[4:8]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _traffic_record():
+    """ncu DRAM bytes per mrs launch, valid only for the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "mrs_traffic.json")
+    src = os.path.join(ROOT, "paper_2009_06954_gb300", "csrc", "mrs.cu")
+    try:
+        rec = json.load(open(path))
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if rec.get("mrs_cu_sha256") == h:
+            return rec
+    except Exception:
+        pass
+    return None
+
+
+# ----------------------------------------------------------------------------
+# main
+# ----------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="asss", choices=["asss", "reference"])
+    ap.add_argument("--cpu-worker", action="store_true")
+    ap.add_argument("--budget", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    if args.cpu_worker:
+        cpu_worker(CPU_SAMPLE_SIDE, args.steps, args.warmup, args.budget)
+        return
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        warm = max(0, min(args.warmup, 1))
+        cb = run_cpu_baseline(args.steps, warm, 120.0)
+        ms = 1000.0 / cb["value"]
+        line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "reference": "FP64 CPU oracle (oracle/), host cores"},
+                "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+                "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import numpy as np
+    import torch
+
+    import paper_2009_06954_gb300 as pkg
+    from paper_2009_06954_gb300.binding import kernel_launches
+    from workloads import dissipative_hamiltonian_3d
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+
+    A, b0, parts = dissipative_hamiltonian_3d(side=SIDE, seed=1)
+    n = A.shape[0]
+    t0 = time.perf_counter()
+    solver = pkg.Solver(A, precision="mixed", outer="fgmres", inner_tol=1e-6, outer_tol=1e-8, k=20,
+                        stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    rhs_h = _make_rhs(parts, n, 1 + rank, 4)
+    rhs = [torch.tensor(r, device=dev) for r in rhs_h]
+    x = torch.empty(n, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    for w in range(args.warmup):
+        solver.solve(rhs[w % 4], x)
+    torch.cuda.synchronize()
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = kernel_launches()
+    print(f"[bench] kernel launches before the timed region: {l0}", file=sys.stderr, flush=True)
+    with ClockSampler(dev.index) as clk:
+        for s in range(args.steps):
+            flush.zero_()
+            evs[s][0].record(stream)
+            _, st = solver.solve(rhs[s % 4], x)
+            evs[s][1].record(stream)
+            stats.append(st)
+        torch.cuda.synchronize()
+    launches = kernel_launches() - l0
+    if dist:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    tmax = total_ms
+    if dist:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tmax = float(t.item())
+    relres = max(s_["relres"] for s_ in stats)
+    ok = all(s_["status"] == 0 for s_ in stats) and relres <= 1e-8
+    value = world * args.steps / (tmax / 1000.0)
+
+    # end to end through the C ABI with pinned host buffers (copies in the timed region)
+    bh = [torch.tensor(r).pin_memory() for r in rhs_h]
+    xh = torch.empty(n, dtype=torch.float64).pin_memory()
+    e2e_s = 0.0
+    for s in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        solver.solve(bh[s % 4], xh)
+        e2e_s += time.perf_counter() - t
+    e2e_val = args.steps / e2e_s
+    if dist:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_val = world * args.steps / float(t.item())
+
+    inner_ms = sum(s_["t_inner_ms"] for s_ in stats)
+    inner_bytes = sum(s_["inner_bytes"] for s_ in stats)
+    inner_launches = sum(s_["inner_launches"] for s_ in stats)
+    peak, peak_kind = _peaks()
+    achieved = inner_bytes / (inner_ms / 1000.0) / 1e9 if inner_ms > 0 else 0.0
+    tr = _traffic_record()
+    traffic = None
+    if tr is not None and inner_launches:
+        traffic = tr["dram_bytes_per_iteration"] * (sum(s_["inner_its_total"] for s_ in stats) / inner_launches) \
+            if "dram_bytes_per_iteration" in tr else None
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        try:
+            cb = run_cpu_baseline(500, 1, 10.0)
+            cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        except Exception as e:  # reported, never silently substituted
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"[:300]}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32-inner/f64-outer", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "256 MB buffer written between steps (not timed); working set > L2",
+                   "setup_s": round(t_setup, 3), "lls_its": solver.setup_stats["lls_its"],
+                   "outer_its": stats[-1]["outer_its"], "inner_its_avg": round(stats[-1]["inner_its_avg"], 2),
+                   "max_relres": relres, "converged": ok, "r": solver.setup_stats["r"],
+                   "k_eff": solver.setup_stats["k_eff"]},
+        "gpu_launches": int(launches),
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
+        "roofline": {"bound": "hbm", "kernel": "k_mrs<float,20> (persistent mrs)", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak if peak else None,
+                     "peak_source": f"{peak_kind} hbm_gbs", "traffic": traffic,
+                     "algorithmic_bytes_per_launch": inner_bytes / max(inner_launches, 1),
+                     "avg_launch_ms": inner_ms / max(inner_launches, 1), "launches": inner_launches,
+                     "share_of_step": inner_ms / total_ms if total_ms else None},
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    solver.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -109,6 +109,9 @@ typedef struct {
     long long nnz_pattern;    /* entries of pat(Abar S) + pat(Abar S)^T (LLS rows + mirror)      */
     double t_setup_ms;
     double t_solve_ms;
+    double t_inner_ms;        /* device time of the mrs kernel launches (CUDA events on the stream) */
+    long long inner_bytes;    /* algorithmic bytes those launches move (matrix entries, Q_k rows, vectors) */
+    int    inner_launches;    /* mrs kernel launches counted in t_inner_ms / inner_bytes */
 } asss_stats;
 
 typedef struct asss_handle asss_handle;
@@ -162,6 +165,10 @@ void asss_destroy(asss_handle* h);
 
 const char* asss_status_str(asss_status s);
 const char* asss_last_error(void);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * devices, all handles); a monotone counter for accounting. */
+unsigned long long asss_kernel_launches(void);
 
 /* ------------------------------------------------------------------------
  * Single steps of the path, each callable on its own.

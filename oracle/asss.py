@@ -606,7 +606,7 @@ class AsssOracle:
         st["inner_its_avg"] = float(np.mean(inn)) if inn else 0.0
         return x, st
 
-    def solve(self, b, tol=1e-8, maxit=2000, outer="tfqmr", restart=30):
+    def solve(self, b, tol=1e-8, maxit=2000, outer="tfqmr", restart=60):
         """x with ||b - A x|| <= tol ||b|| (§4.1)."""
         b = np.asarray(b, dtype=np.float64)
         A = self.A
@@ -620,7 +620,7 @@ class AsssOracle:
         return self._refine(b, lambda x: A @ x, to_scaled, from_scaled, False, tol,
                             maxit, outer, restart)
 
-    def solve_adjoint(self, g, x=None, tol=1e-8, maxit=2000, outer="tfqmr", restart=30):
+    def solve_adjoint(self, g, x=None, tol=1e-8, maxit=2000, outer="tfqmr", restart=60):
         """lambda with A^T lambda = g, via A_cal^T mu = W S^T D_c g, lambda = D_r P^T W mu,
         preconditioned by P^T = M~_r + I - J~ (mrs on the transposed inner system).
         With x given, also dL/dA_ij = -lambda_i x_j on the pattern of A."""

@@ -52,7 +52,8 @@ class Stats(C.Structure):
                 ("inner_its_avg", C.c_double), ("relres", C.c_double), ("r", C.c_int),
                 ("k_eff", C.c_int), ("prec2", C.c_int), ("lls_its", C.c_int),
                 ("lls_relgrad", C.c_double), ("nnz_pattern", C.c_longlong),
-                ("t_setup_ms", C.c_double), ("t_solve_ms", C.c_double)]
+                ("t_setup_ms", C.c_double), ("t_solve_ms", C.c_double), ("t_inner_ms", C.c_double),
+                ("inner_bytes", C.c_longlong), ("inner_launches", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -61,7 +62,7 @@ class Stats(C.Structure):
 EXPORTED = ["asss_default_options", "asss_setup", "asss_solve", "asss_solve_adjoint",
             "asss_apply_operator", "asss_apply_preconditioner", "asss_export", "asss_destroy",
             "asss_status_str", "asss_last_error", "asss_skew_symmetrizer", "asss_skew_lanczos",
-            "asss_mrs"]
+            "asss_mrs", "asss_kernel_launches"]
 
 _lib = None
 
@@ -97,6 +98,8 @@ def lib():
     L.asss_skew_lanczos.argtypes = [pCSR, P, C.c_int, C.c_int, P, P, C.POINTER(C.c_int), P]
     L.asss_mrs.argtypes = [pCSR, C.c_int, P, P, C.c_double, C.c_double, P, P, C.c_double, C.c_int,
                            C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double), P]
+    L.asss_kernel_launches.argtypes = []
+    L.asss_kernel_launches.restype = C.c_ulonglong
     for f in ("asss_setup", "asss_solve", "asss_solve_adjoint", "asss_apply_operator",
               "asss_apply_preconditioner", "asss_export", "asss_skew_symmetrizer",
               "asss_skew_lanczos", "asss_mrs"):
@@ -370,3 +373,8 @@ def mrs(J, b, Q=None, alpha=None, shift=1.0, sign=1.0, tol=1e-10, maxit=1000, pr
                                       x.ctypes.data, float(tol), int(maxit), prec, C.byref(its),
                                       C.byref(ratio), None))
     return x, its.value, ratio.value
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libasss.so in this process so far."""
+    return int(lib().asss_kernel_launches())

@@ -380,6 +380,8 @@ struct asss_handle {
     // statistics of the current solve
     long long inner_total = 0;
     int inner_solves = 0;
+    double inner_ms = 0.0;
+    long long inner_bytes = 0;
     asss_stats setup_stats;
     ~asss_handle() {
         if (mw) mrs_work_destroy(mw);
@@ -564,6 +566,8 @@ static asss_status apply_prec(asss_handle* h, int tr, const double* u, double* o
     }
     h->inner_total += res.its;
     h->inner_solves += 1;
+    h->inner_ms += res.ms;
+    h->inner_bytes += res.bytes;
     if (its_out) *its_out = res.its;
     if (S.m > 0) {
         if (h->k) ASSS_TRY(gram(h->Qcm.p, n, h->k, z, n, 1, n, h->wv.p, s));
@@ -797,6 +801,8 @@ static asss_status refine(asss_handle* h, int tr, const double* rhs, double* x, 
     ASSS_TRY(scal.alloc(2));
     h->inner_total = 0;
     h->inner_solves = 0;
+    h->inner_ms = 0.0;
+    h->inner_bytes = 0;
     ASSS_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
     ASSS_TRY(vcopy(r.p, rhs, n, s));
     ASSS_TRY(dot(rhs, rhs, n, scal.p, s));
@@ -869,6 +875,9 @@ static asss_status refine(asss_handle* h, int tr, const double* rhs, double* x, 
     st->inner_its_total = h->inner_total;
     st->inner_solves = h->inner_solves;
     st->inner_its_avg = h->inner_solves ? (double)h->inner_total / h->inner_solves : 0.0;
+    st->t_inner_ms = h->inner_ms;
+    st->inner_bytes = h->inner_bytes;
+    st->inner_launches = h->inner_solves;
     return ASSS_OK;
 }
 
@@ -1132,6 +1141,8 @@ const char* asss_status_str(asss_status s) {
 
 const char* asss_last_error(void) { return get_error(); }
 
+unsigned long long asss_kernel_launches(void) { return launches(); }
+
 asss_status asss_setup(const asss_csr* A, const asss_options* opt, asss_handle** out, asss_stats* st) {
     if (!out) {
         set_error("out is NULL");
@@ -1271,6 +1282,8 @@ asss_status asss_apply_preconditioner(asss_handle* h, int transpose, const doubl
         st->inner_its_total = its;
         st->inner_solves = 1;
     }
+    h->inner_ms = 0.0;
+    h->inner_bytes = 0;
     return ASSS_OK;
 }
 

@@ -35,7 +35,12 @@ const char* get_error();
         if (s_ != ASSS_OK) return s_;      \
     } while (0)
 
-#define ASSS_CHECK_LAUNCH() ASSS_CUDA(cudaGetLastError())
+void count_launch();
+#define ASSS_CHECK_LAUNCH()            \
+    do {                               \
+        ::asss::count_launch();        \
+        ASSS_CUDA(cudaGetLastError()); \
+    } while (0)
 
 inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
@@ -85,7 +90,8 @@ template <class T>
 struct DSell {
     int n = 0;
     int nslices = 0;
-    int64_t nstored = 0;
+    int64_t nstored = 0;  // including padding
+    int64_t nnz = 0;      // stored entries that come from the matrix
     DBuf<int> sptr;   // nslices + 1
     DBuf<int> col;
     DBuf<T> val;

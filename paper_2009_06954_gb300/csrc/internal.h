@@ -59,7 +59,11 @@ struct MrsResult {
     int its = 0;
     double ratio = 0.0;
     int status = 0;
+    double ms = 0.0;          // kernel time from CUDA events around the launch
+    long long bytes = 0;      // algorithmic bytes of the launch
 };
+
+unsigned long long launches();
 
 // One single-RHS mrs solve (App. B) of (shift I + sign*(J~ - Q S_k Q^T)) x = rhs.
 // fp32: use the FP32 operator and vectors; rhs is FP64 in both cases, x is FP64

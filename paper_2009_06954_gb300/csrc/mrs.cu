@@ -39,6 +39,11 @@ struct MrsWork {
     DBuf<int> blk_slice;
     const void* part_key = nullptr;
     int part_nblk = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    ~MrsWork() {
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+    }
 };
 
 asss_status mrs_work_create(MrsWork** w, int n, int sms) {
@@ -53,6 +58,11 @@ asss_status mrs_work_create(MrsWork** w, int n, int sms) {
         (st = m->blk_slice.alloc(maxblk + 1)) != ASSS_OK) {
         delete m;
         return st;
+    }
+    if (cudaEventCreate(&m->ev0) != cudaSuccess || cudaEventCreate(&m->ev1) != cudaSuccess) {
+        delete m;
+        set_error("cudaEventCreate failed");
+        return ASSS_ERR_CUDA;
     }
     *w = m;
     return ASSS_OK;
@@ -353,8 +363,11 @@ static asss_status launch_mrs(const Ctx& c, MrsWork* w, const DSell<T>& J, const
     prm.out_its = w->out_its.p;
     prm.out_ratio = w->out_ratio.p;
     void* args[] = {&prm};
+    ASSS_CUDA(cudaEventRecord(w->ev0, c.stream));
     ASSS_CUDA(cudaLaunchCooperativeKernel((const void*)k_mrs<T, KP>, dim3(nblk), dim3(MRS_THREADS), args, 0,
                                           c.stream));
+    count_launch();
+    ASSS_CUDA(cudaEventRecord(w->ev1, c.stream));
     return ASSS_OK;
 }
 
@@ -417,6 +430,17 @@ asss_status mrs_solve(const Ctx& c, MrsWork* w, const MrsOperator& op, bool fp32
         ASSS_CUDA(cudaMemcpyAsync(&herr, w->err.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
         ASSS_CUDA(cudaStreamSynchronize(c.stream));
         res->status = herr;
+        float ms = 0.f;
+        ASSS_CUDA(cudaEventElapsedTime(&ms, w->ev0, w->ev1));
+        res->ms = ms;
+        // algorithmic bytes: set-up pass (rhs in FP64, Y/x/P written, Q row), per iteration
+        // (matrix entries value+index, Q row, gathered/own y, y_old, y_new, p r/w, x r/w),
+        // final pass (y, p, x r/w)
+        long long T = fp32 ? 4 : 8;
+        long long nn = n, kp = op.kp;
+        long long nnzJ = fp32 ? op.J32->nnz : op.J64->nnz;
+        res->bytes = nn * (8 + 4 * T + kp * T) + (long long)res->its * (nnzJ * (T + 4) + nn * (7 * T + kp * T)) +
+                     nn * 4 * T;
         if (herr) {
             set_error("mrs: a grid barrier wait exceeded its budget");
             return (asss_status)herr;

@@ -21,6 +21,10 @@ void set_error(const char* fmt, ...) {
 }
 const char* get_error() { return g_err; }
 
+static unsigned long long g_launches = 0;
+void count_launch() { __atomic_add_fetch(&g_launches, 1ull, __ATOMIC_RELAXED); }
+unsigned long long launches() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
 asss_status make_ctx(Ctx& c, void* stream, double wait_timeout_ms) {
     c.stream = (cudaStream_t)stream;
     ASSS_CUDA(cudaGetDevice(&c.device));
@@ -531,10 +535,12 @@ asss_status build_pattern(const DCsr& Abar, const DCsr& AbarT, const DCsr& S, co
 // ---------------------------------------------------------------------------
 // SELL-C (C = 32) from CSR, optionally leaving out diagonal entries
 // ---------------------------------------------------------------------------
-__global__ void k_sell_width(int n, const int* rp, const int* ci, int skip_diag, int nslices, int* w) {
+__global__ void k_sell_width(int n, const int* rp, const int* ci, int skip_diag, int nslices, int* w,
+                             unsigned long long* nnz) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nslices) return;
     int m = 0;
+    long long tot = 0;
     for (int r = s * 32; r < min(n, s * 32 + 32); ++r) {
         int len = rp[r + 1] - rp[r];
         if (skip_diag) {
@@ -545,8 +551,10 @@ __global__ void k_sell_width(int n, const int* rp, const int* ci, int skip_diag,
                 }
         }
         m = max(m, len);
+        tot += len;
     }
     w[s] = m * 32;
+    atomicAdd(nnz, (unsigned long long)tot);
 }
 
 template <class T>
@@ -579,9 +587,16 @@ asss_status build_sell(const DCsr& A, bool skip_diag, DSell<T>& out, cudaStream_
     out.n = n;
     out.nslices = ns;
     DBuf<int> w;
+    DBuf<unsigned long long> cnt;
     ASSS_TRY(w.alloc(ns));
-    k_sell_width<<<cdiv(ns, 128), 128, 0, s>>>(n, A.rp.p, A.ci.p, skip_diag ? 1 : 0, ns, w.p);
+    ASSS_TRY(cnt.alloc(1));
+    ASSS_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long), s));
+    k_sell_width<<<cdiv(ns, 128), 128, 0, s>>>(n, A.rp.p, A.ci.p, skip_diag ? 1 : 0, ns, w.p, cnt.p);
     ASSS_CHECK_LAUNCH();
+    unsigned long long hn = 0;
+    ASSS_CUDA(cudaMemcpyAsync(&hn, cnt.p, sizeof(hn), cudaMemcpyDeviceToHost, s));
+    ASSS_CUDA(cudaStreamSynchronize(s));
+    out.nnz = (int64_t)hn;
     ASSS_TRY(out.sptr.alloc(ns + 1));
     int64_t tot = 0;
     ASSS_TRY(exclusive_scan(w.p, out.sptr.p, ns, &tot, s));
