@@ -8,8 +8,11 @@ been built, importing names from here works but the first call raises
 """
 from __future__ import annotations
 
+import atexit
 import ctypes as C
 import os
+import sys
+import weakref
 
 import numpy as np
 
@@ -65,6 +68,16 @@ EXPORTED = ["asss_default_options", "asss_setup", "asss_solve", "asss_solve_adjo
             "asss_mrs", "asss_kernel_launches"]
 
 _lib = None
+_live = weakref.WeakSet()   # open handles, closed at exit while CUDA is still up
+
+
+@atexit.register
+def _close_all():
+    for s in list(_live):
+        try:
+            s.close()
+        except Exception:
+            pass
 
 
 def lib():
@@ -224,6 +237,7 @@ class Solver:
         _check("asss_setup", status)
         self._h = h
         self.setup_stats = st.as_dict()
+        _live.add(self)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -231,6 +245,10 @@ class Solver:
             self._h = None
 
     def __del__(self):
+        # during interpreter shutdown the process exit releases device memory; no
+        # CUDA call is made then
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:

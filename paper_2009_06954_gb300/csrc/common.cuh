@@ -75,6 +75,10 @@ struct DBuf {
     DBuf& operator=(const DBuf&) = delete;
 };
 
+// Reduction scratch that lives as long as the process, one buffer per device and
+// thread.  It is never freed, so no CUDA call runs during process teardown.
+asss_status process_scratch(int slot, int64_t count, double** out);
+
 // CSR with 32-bit row pointers (nnz < 2^31 is checked on entry).
 struct DCsr {
     int n = 0;

@@ -86,16 +86,15 @@ __global__ void k_gemtv_partial(const double* __restrict__ A, int lda, int p, co
 asss_status gram(const double* A, int lda, int p, const double* B, int ldb, int q, int n, double* G,
                  cudaStream_t s) {
     if (p == 0 || q == 0) return ASSS_OK;
-    static thread_local DBuf<double> part;
-    int64_t need = (int64_t)GRAM_BLOCKS * p * q;
-    if (part.n < need) ASSS_TRY(part.alloc(need));
+    double* part = nullptr;
+    ASSS_TRY(process_scratch(1, (int64_t)GRAM_BLOCKS * p * q, &part));
     if (q == 1) {
-        k_gemtv_partial<<<GRAM_BLOCKS, GRAM_THREADS, 0, s>>>(A, lda, p, B, n, part.p);
+        k_gemtv_partial<<<GRAM_BLOCKS, GRAM_THREADS, 0, s>>>(A, lda, p, B, n, part);
     } else {
-        k_gram_partial<<<GRAM_BLOCKS, GRAM_THREADS, 0, s>>>(A, lda, p, B, ldb, q, n, part.p);
+        k_gram_partial<<<GRAM_BLOCKS, GRAM_THREADS, 0, s>>>(A, lda, p, B, ldb, q, n, part);
     }
     ASSS_CHECK_LAUNCH();
-    k_gram_final<<<cdiv(p * q, 128), 128, 0, s>>>(part.p, GRAM_BLOCKS, p * q, G);
+    k_gram_final<<<cdiv(p * q, 128), 128, 0, s>>>(part, GRAM_BLOCKS, p * q, G);
     ASSS_CHECK_LAUNCH();
     return ASSS_OK;
 }

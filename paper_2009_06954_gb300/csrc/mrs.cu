@@ -25,6 +25,10 @@ namespace asss {
 constexpr int MRS_THREADS = 512;
 constexpr int MRS_WARPS = MRS_THREADS / 32;
 constexpr int MRS_KPMAX = 64;
+// resident blocks per SM the register allocation is sized for: two 512-thread
+// blocks for FP32 (more loads in flight for the gathers), one for FP64
+template <class T>
+constexpr int mrs_min_blocks() { return sizeof(T) == 4 ? 2 : 1; }
 
 struct MrsWork {
     int n = 0;
@@ -122,7 +126,7 @@ __device__ __forceinline__ void load_qrow(const T* __restrict__ Q, int i, T (&q)
 }
 
 template <class T, int KP>
-__global__ void __launch_bounds__(MRS_THREADS) k_mrs(MrsParams<T> p) {
+__global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsParams<T> p) {
     constexpr int NV = KP + 1;
     __shared__ double s_wsum[MRS_WARPS][NV];
     __shared__ double s_red[NV];
@@ -226,7 +230,7 @@ __global__ void __launch_bounds__(MRS_THREADS) k_mrs(MrsParams<T> p) {
             const int* cp = p.col + base + lane;
             const T* vp = p.val + base + lane;
 #pragma unroll 4
-            for (int kk = 0; kk < width; ++kk) acc += __ldg(vp + kk * 32) * __ldcg(&Ycur[__ldg(cp + kk * 32)]);
+            for (int kk = 0; kk < width; ++kk) acc += __ldg(vp + kk * 32) * Ycur[__ldg(cp + kk * 32)];
             const int i = sl * 32 + lane;
             if (i < n) {
                 T yold = (j >= 2) ? __ldcg(&Yold[i]) : (T)0;

@@ -25,6 +25,27 @@ static unsigned long long g_launches = 0;
 void count_launch() { __atomic_add_fetch(&g_launches, 1ull, __ATOMIC_RELAXED); }
 unsigned long long launches() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
+asss_status process_scratch(int slot, int64_t count, double** out) {
+    constexpr int MAXDEV = 64, SLOTS = 4;
+    static thread_local double* buf[MAXDEV][SLOTS] = {};
+    static thread_local int64_t cap[MAXDEV][SLOTS] = {};
+    int dev = 0;
+    ASSS_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= MAXDEV || slot < 0 || slot >= SLOTS) {
+        set_error("scratch slot out of range");
+        return ASSS_ERR_ARG;
+    }
+    if (cap[dev][slot] < count) {
+        if (buf[dev][slot]) cudaFree(buf[dev][slot]);
+        buf[dev][slot] = nullptr;
+        cap[dev][slot] = 0;
+        ASSS_CUDA(cudaMalloc((void**)&buf[dev][slot], sizeof(double) * (size_t)count));
+        cap[dev][slot] = count;
+    }
+    *out = buf[dev][slot];
+    return ASSS_OK;
+}
+
 asss_status make_ctx(Ctx& c, void* stream, double wait_timeout_ms) {
     c.stream = (cudaStream_t)stream;
     ASSS_CUDA(cudaGetDevice(&c.device));
@@ -174,11 +195,11 @@ __global__ void k_sum_partials(const double* part, int np, double* out) {
 
 template <class T>
 static asss_status dot_impl(const T* a, const T* b, int n, double* d_out, cudaStream_t s) {
-    static thread_local DBuf<double> part;
-    if (!part.p) ASSS_TRY(part.alloc(DOT_BLOCKS));
-    k_dot_partial<T><<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(a, b, n, part.p);
+    double* part = nullptr;
+    ASSS_TRY(process_scratch(0, DOT_BLOCKS, &part));
+    k_dot_partial<T><<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(a, b, n, part);
     ASSS_CHECK_LAUNCH();
-    k_sum_partials<<<1, 32, 0, s>>>(part.p, DOT_BLOCKS, d_out);
+    k_sum_partials<<<1, 32, 0, s>>>(part, DOT_BLOCKS, d_out);
     ASSS_CHECK_LAUNCH();
     return ASSS_OK;
 }
