@@ -91,7 +91,13 @@ typedef struct {
     double zero_tol;          /* |d_i| < zero_tol*max|d| is a zero pivot                        */
     double wait_timeout_ms;   /* budget of each device-side wait                                */
     void*  stream;            /* cudaStream_t                                                   */
+    int    inner_format;      /* storage of J~ for mrs: ASSS_FORMAT_AUTO (skew diagonals when J~ has
+                                 at most 64 positive offsets filling >= 50% of them, else SELL-C),
+                                 ASSS_FORMAT_SELL, ASSS_FORMAT_DIAG (fails with UNSUPPORTED if J~
+                                 does not qualify)                                              */
 } asss_options;
+
+enum { ASSS_FORMAT_AUTO = 0, ASSS_FORMAT_SELL = 1, ASSS_FORMAT_DIAG = 2 };
 
 typedef struct {
     int    status;            /* asss_status of the call                                        */
@@ -190,12 +196,14 @@ asss_status asss_skew_lanczos(const asss_csr* J, const double* q1, int k, int re
 /* mrs (§3.1, App. B) on (shift I + sign*(J - Q S_k Q^T)) x = b for one right-hand
  * side, where J is skew (not checked), Q is n x k column-major (k may be 0) and
  * S_k the skew tridiagonal matrix with superdiagonal alpha (k-1 values).
- * precision selects FP64 or FP32 storage and arithmetic (reductions in FP64).
+ * precision selects FP64 or FP32 storage and arithmetic (reductions in FP64); format
+ * selects the storage of J as in asss_options.inner_format (the skew-diagonal
+ * storage also requires J to be exactly skew, J_ij == -J_ji bit for bit).
  * Stops when |g|/||b|| < tol or after maxit steps; *its and *ratio receive the
  * step count and the final recursive residual ratio. */
 asss_status asss_mrs(const asss_csr* J, int k, const double* q, const double* alpha,
                      double shift, double sign, const double* b, double* x, double tol,
-                     int maxit, int precision, int* its, double* ratio, void* stream);
+                     int maxit, int precision, int format, int* its, double* ratio, void* stream);
 
 #ifdef __cplusplus
 }

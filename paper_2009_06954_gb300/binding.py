@@ -46,7 +46,10 @@ class Options(C.Structure):
                 ("outer_tol", C.c_double), ("inner_maxit", C.c_int), ("outer_maxit", C.c_int),
                 ("restart", C.c_int), ("precision", C.c_int), ("outer", C.c_int), ("r_max", C.c_int),
                 ("seed", C.c_uint64), ("lls_tol", C.c_double), ("lls_maxit", C.c_int),
-                ("zero_tol", C.c_double), ("wait_timeout_ms", C.c_double), ("stream", C.c_void_p)]
+                ("zero_tol", C.c_double), ("wait_timeout_ms", C.c_double), ("stream", C.c_void_p),
+                ("inner_format", C.c_int)]
+
+FORMATS = {"auto": 0, "sell": 1, "diag": 2}
 
 
 class Stats(C.Structure):
@@ -110,7 +113,7 @@ def lib():
     L.asss_skew_symmetrizer.argtypes = [pCSR, pCSR, pO, P, pS]
     L.asss_skew_lanczos.argtypes = [pCSR, P, C.c_int, C.c_int, P, P, C.POINTER(C.c_int), P]
     L.asss_mrs.argtypes = [pCSR, C.c_int, P, P, C.c_double, C.c_double, P, P, C.c_double, C.c_int,
-                           C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double), P]
+                           C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double), P]
     L.asss_kernel_launches.argtypes = []
     L.asss_kernel_launches.restype = C.c_ulonglong
     for f in ("asss_setup", "asss_solve", "asss_solve_adjoint", "asss_apply_operator",
@@ -199,6 +202,9 @@ def _options(keep, **kw):
             arr = _host(v, np.int32 if name == "row_perm" else np.float64)
             keep.append(arr)
             setattr(o, name, arr.ctypes.data)
+    fmt = kw.pop("inner_format", None)
+    if fmt is not None:
+        o.inner_format = FORMATS.get(fmt, fmt)
     stream = kw.pop("stream", None)
     if stream is not None:
         o.stream = stream if isinstance(stream, int) else stream.cuda_stream
@@ -366,7 +372,8 @@ def skew_lanczos(J, q1, k, reorth=True):
     return np.asfortranarray(Q[:, :ke]), alpha[:max(ke - 1, 0)].copy()
 
 
-def mrs(J, b, Q=None, alpha=None, shift=1.0, sign=1.0, tol=1e-10, maxit=1000, precision="fp64"):
+def mrs(J, b, Q=None, alpha=None, shift=1.0, sign=1.0, tol=1e-10, maxit=1000, precision="fp64",
+        fmt="auto"):
     """mrs (App. B) on (shift I + sign (J - Q S_k Q^T)) x = b; returns (x, its, ratio)."""
     keep = []
     a = _csr_struct(J, keep)
@@ -388,7 +395,7 @@ def mrs(J, b, Q=None, alpha=None, shift=1.0, sign=1.0, tol=1e-10, maxit=1000, pr
     ratio = C.c_double(0.0)
     prec = {"fp64": ASSS_PREC_FP64, "mixed": ASSS_PREC_MIXED, "fp32": ASSS_PREC_MIXED}[precision]
     _check("asss_mrs", lib().asss_mrs(C.byref(a), k, qp, ap, float(shift), float(sign), b.ctypes.data,
-                                      x.ctypes.data, float(tol), int(maxit), prec, C.byref(its),
+                                      x.ctypes.data, float(tol), int(maxit), prec, FORMATS[fmt], C.byref(its),
                                       C.byref(ratio), None))
     return x, its.value, ratio.value
 

@@ -360,6 +360,9 @@ struct asss_handle {
     DCsr Jt;           // J~ on P (FP64)
     DSell<double> J64;
     DSell<float> J32;
+    DSkewDia<double> D64;
+    DSkewDia<float> D32;
+    bool use_dia = false;
     DBuf<double> dr, dc, w, d;
     DBuf<int> perm;
     bool has_perm = false;
@@ -408,6 +411,7 @@ static void fill_defaults(asss_options* o) {
     o->zero_tol = 1e-14;
     o->wait_timeout_ms = 2000.0;
     o->stream = nullptr;
+    o->inner_format = ASSS_FORMAT_AUTO;
 }
 
 static int pick_kp(int k) {
@@ -485,7 +489,8 @@ static asss_status ensure_smw(asss_handle* h, int tr) {
     ASSS_TRY(X.alloc((int64_t)n * m));
     ASSS_TRY(rhs.alloc(n));
     MrsOperator op;
-    op.J64 = &h->J64;
+    op.J64 = h->use_dia ? nullptr : &h->J64;
+    op.D64 = h->use_dia ? &h->D64 : nullptr;
     op.k = h->k;
     op.kp = h->kp;
     op.Q64 = h->Q64.p;
@@ -543,8 +548,10 @@ static asss_status apply_prec(asss_handle* h, int tr, const double* u, double* o
     int n = h->n;
     ASSS_TRY(ensure_smw(h, tr));
     MrsOperator op;
-    op.J64 = &h->J64;
-    op.J32 = h->J32.n ? &h->J32 : nullptr;
+    op.J64 = h->use_dia ? nullptr : &h->J64;
+    op.J32 = (!h->use_dia && h->J32.n) ? &h->J32 : nullptr;
+    op.D64 = h->use_dia ? &h->D64 : nullptr;
+    op.D32 = (h->use_dia && h->D32.n) ? &h->D32 : nullptr;
     op.k = h->k;
     op.kp = h->kp;
     op.Q64 = h->Q64.p;
@@ -890,7 +897,8 @@ static asss_status do_setup(asss_handle* h, const asss_csr* Ain, asss_stats* st)
     cudaStream_t s = c.stream;
     if (o.k_lanczos < 0 || o.gamma <= 0 || o.inner_maxit < 1 || o.outer_maxit < 0 ||
         (o.precision != ASSS_PREC_FP64 && o.precision != ASSS_PREC_MIXED) ||
-        (o.outer != ASSS_OUTER_TFQMR && o.outer != ASSS_OUTER_FGMRES) || (o.outer == ASSS_OUTER_FGMRES && o.restart < 1)) {
+        (o.outer != ASSS_OUTER_TFQMR && o.outer != ASSS_OUTER_FGMRES) || (o.outer == ASSS_OUTER_FGMRES && o.restart < 1) ||
+        o.inner_format < ASSS_FORMAT_AUTO || o.inner_format > ASSS_FORMAT_DIAG) {
         set_error("invalid option");
         return ASSS_ERR_ARG;
     }
@@ -1064,8 +1072,20 @@ static asss_status do_setup(asss_handle* h, const asss_csr* Ain, asss_stats* st)
     ASSS_TRY(h->Jt.v.alloc(h->Jt.nnz));
     k_assemble_jt<<<cdiv(n, 256), 256, 0, s>>>(n, h->Jt.rp.p, h->Jt.ci.p, mirror.p, Cval.p, h->w.p, h->Jt.v.p);
     ASSS_CHECK_LAUNCH();
-    ASSS_TRY(build_sell<double>(h->Jt, true, h->J64, s));
-    if (o.precision == ASSS_PREC_MIXED) ASSS_TRY(build_sell<float>(h->Jt, true, h->J32, s));
+    if (o.inner_format != ASSS_FORMAT_SELL) {
+        int ok = 0;
+        ASSS_TRY(build_skew_dia<double>(h->Jt, 64, 0.5, h->D64, &ok, s));
+        if (ok && o.precision == ASSS_PREC_MIXED) ASSS_TRY(build_skew_dia<float>(h->Jt, 64, 0.5, h->D32, &ok, s));
+        h->use_dia = ok != 0;
+        if (!ok && o.inner_format == ASSS_FORMAT_DIAG) {
+            set_error("J~ does not qualify for skew diagonal storage");
+            return ASSS_ERR_UNSUPPORTED;
+        }
+    }
+    if (!h->use_dia) {
+        ASSS_TRY(build_sell<double>(h->Jt, true, h->J64, s));
+        if (o.precision == ASSS_PREC_MIXED) ASSS_TRY(build_sell<float>(h->Jt, true, h->J32, s));
+    }
     // outer operator pieces: W Abar and S W
     ASSS_TRY(copy_csr(h->Abar, h->Aw, s));
     k_scale_rows<<<cdiv(n, 256), 256, 0, s>>>(h->Aw.rp.p, h->Aw.v.p, h->w.p, n);
@@ -1371,8 +1391,8 @@ asss_status asss_skew_lanczos(const asss_csr* J, const double* q1, int k, int re
 }
 
 asss_status asss_mrs(const asss_csr* J, int k, const double* q, const double* alpha, double shift, double sign,
-                     const double* b, double* x, double tol, int maxit, int precision, int* its, double* ratio,
-                     void* stream) {
+                     const double* b, double* x, double tol, int maxit, int precision, int format, int* its,
+                     double* ratio, void* stream) {
     Ctx c;
     ASSS_TRY(make_ctx(c, stream, 2000.0));
     if (!b || !x || k < 0 || (k > 0 && !q) || (k > 1 && !alpha) || maxit < 1 || !(shift > 0.0)) {
@@ -1390,11 +1410,24 @@ asss_status asss_mrs(const asss_csr* J, int k, const double* q, const double* al
     }
     DSell<double> J64;
     DSell<float> J32;
+    DSkewDia<double> D64;
+    DSkewDia<float> D32;
     DBuf<double> Qcm, Q64, ad, bd, xd;
     DBuf<float> Q32, x32;
     bool fp32 = precision == ASSS_PREC_MIXED;
-    if (fp32) ASSS_TRY(build_sell<float>(Jd, false, J32, s));
-    else ASSS_TRY(build_sell<double>(Jd, false, J64, s));
+    int dia = 0;
+    if (format != ASSS_FORMAT_SELL) {
+        if (fp32) ASSS_TRY(build_skew_dia<float>(Jd, 64, 0.5, D32, &dia, s));
+        else ASSS_TRY(build_skew_dia<double>(Jd, 64, 0.5, D64, &dia, s));
+        if (!dia && format == ASSS_FORMAT_DIAG) {
+            set_error("J does not qualify for skew diagonal storage");
+            return ASSS_ERR_UNSUPPORTED;
+        }
+    }
+    if (!dia) {
+        if (fp32) ASSS_TRY(build_sell<float>(Jd, false, J32, s));
+        else ASSS_TRY(build_sell<double>(Jd, false, J64, s));
+    }
     if (k) {
         ASSS_TRY(to_device(Qcm, q, (int64_t)n * k, s));
         if (fp32) {
@@ -1412,8 +1445,10 @@ asss_status asss_mrs(const asss_csr* J, int k, const double* q, const double* al
     MrsWork* w = nullptr;
     ASSS_TRY(mrs_work_create(&w, n, c.sms));
     MrsOperator op;
-    op.J64 = fp32 ? nullptr : &J64;
-    op.J32 = fp32 ? &J32 : nullptr;
+    op.J64 = (fp32 || dia) ? nullptr : &J64;
+    op.J32 = (fp32 && !dia) ? &J32 : nullptr;
+    op.D64 = (!fp32 && dia) ? &D64 : nullptr;
+    op.D32 = (fp32 && dia) ? &D32 : nullptr;
     op.k = k;
     op.kp = kp;
     op.Q64 = Q64.p;

@@ -101,6 +101,19 @@ struct DSell {
     DBuf<T> val;
 };
 
+// Skew half-diagonal storage of an exactly skew matrix J whose entries lie on a
+// few diagonals (stencil-like patterns): only the diagonals with positive offset
+// are stored, U[d*n + i] = J[i, i + off[d]] (0 where absent), and the lower
+// triangle is read from the same arrays shifted: J[i, i - off[d]] = -U[d*n + i - off[d]].
+template <class T>
+struct DSkewDia {
+    int n = 0;
+    int ndiag = 0;
+    int64_t nnz = 0;          // stored upper entries that come from the matrix
+    DBuf<int> off;            // ndiag ascending positive offsets
+    DBuf<T> U;                // ndiag x n
+};
+
 // ---------------------------------------------------------------------------
 // device helpers
 // ---------------------------------------------------------------------------

@@ -50,34 +50,44 @@ __global__ void k_gram_partial(const double* __restrict__ A, int lda, int p, con
     }
 }
 
+// one warp per output, lanes stride over the block partials (fixed order)
 __global__ void k_gram_final(const double* part, int nb, int pq, double* G) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    int lane = threadIdx.x & 31;
     if (t >= pq) return;
     double acc = 0.0;
-    for (int b = 0; b < nb; ++b) acc += part[(size_t)b * pq + t];
-    G[t] = acc;
+    for (int b = lane; b < nb; b += 32) acc += part[(size_t)b * pq + t];
+    acc = warp_sum(acc);
+    if (lane == 0) G[t] = acc;
 }
 
-// Narrow case (p*q small): one warp per row chunk would waste threads, so for
-// q == 1 use all threads on rows and reduce per column of A.
+// q == 1: part[b*p + a] = sum over the rows of block b of A[r, a] x[r].  Columns are
+// taken eight at a time so each thread keeps eight independent loads in flight.
+constexpr int GEMTV_CH = 8;
 __global__ void k_gemtv_partial(const double* __restrict__ A, int lda, int p, const double* __restrict__ x, int n,
                                 double* part) {
-    // part[b*p + a] = sum over this block's rows of A[r,a] x[r]
-    __shared__ double sw[GRAM_THREADS / 32];
-    const int chunk = (n + gridDim.x - 1) / gridDim.x;
-    const int r0 = blockIdx.x * chunk;
-    const int r1 = min(n, r0 + chunk);
-    for (int a = 0; a < p; ++a) {
-        const double* pa = A + (size_t)a * lda;
-        double acc = 0.0;
-        for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) acc += pa[r] * x[r];
-        acc = warp_sum(acc);
-        if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = acc;
+    __shared__ double sw[GRAM_THREADS / 32][GEMTV_CH];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int a0 = 0; a0 < p; a0 += GEMTV_CH) {
+        double acc[GEMTV_CH];
+#pragma unroll
+        for (int t = 0; t < GEMTV_CH; ++t) acc[t] = 0.0;
+        for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+            double xr = x[r];
+#pragma unroll
+            for (int t = 0; t < GEMTV_CH; ++t)
+                if (a0 + t < p) acc[t] += A[(size_t)(a0 + t) * lda + r] * xr;
+        }
+#pragma unroll
+        for (int t = 0; t < GEMTV_CH; ++t) {
+            double v = warp_sum(acc[t]);
+            if (lane == 0) sw[warp][t] = v;
+        }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int w = 0; w < GRAM_THREADS / 32; ++w) t += sw[w];
-            part[(size_t)blockIdx.x * p + a] = t;
+        if (threadIdx.x < GEMTV_CH && a0 + threadIdx.x < p) {
+            double v = 0.0;
+            for (int w = 0; w < GRAM_THREADS / 32; ++w) v += sw[w][threadIdx.x];
+            part[(size_t)blockIdx.x * p + a0 + threadIdx.x] = v;
         }
         __syncthreads();
     }
@@ -94,7 +104,7 @@ asss_status gram(const double* A, int lda, int p, const double* B, int ldb, int 
         k_gram_partial<<<GRAM_BLOCKS, GRAM_THREADS, 0, s>>>(A, lda, p, B, ldb, q, n, part);
     }
     ASSS_CHECK_LAUNCH();
-    k_gram_final<<<cdiv(p * q, 128), 128, 0, s>>>(part, GRAM_BLOCKS, p * q, G);
+    k_gram_final<<<cdiv(p * q, 4), 128, 0, s>>>(part, GRAM_BLOCKS, p * q, G);
     ASSS_CHECK_LAUNCH();
     return ASSS_OK;
 }

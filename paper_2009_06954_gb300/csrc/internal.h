@@ -14,6 +14,12 @@ asss_status build_pattern(const DCsr& Abar, const DCsr& AbarT, const DCsr& S, co
                           DBuf<int>& mirror, DBuf<int>& diagpos, cudaStream_t s);
 template <class T>
 asss_status build_sell(const DCsr& A, bool skip_diag, DSell<T>& out, cudaStream_t s);
+// Skew half-diagonal storage of J when J is exactly skew, has at most max_diag
+// positive offsets and fills at least min_fill of the stored diagonals; *ok = 0
+// (and nothing allocated) otherwise.
+template <class T>
+asss_status build_skew_dia(const DCsr& J, int max_diag, double min_fill, DSkewDia<T>& out, int* ok,
+                           cudaStream_t s);
 
 // dense.cu : small dense / tall-skinny / vector kernels (all FP64 unless noted)
 asss_status splitmix64_fill(uint64_t seed, int n, double* out, cudaStream_t s);
@@ -45,6 +51,9 @@ struct MrsOperator {
     // J~ (exactly skew) in SELL-C, FP64 and/or FP32 copies
     const DSell<double>* J64 = nullptr;
     const DSell<float>* J32 = nullptr;
+    // skew half-diagonal copies (used instead of SELL when present)
+    const DSkewDia<double>* D64 = nullptr;
+    const DSkewDia<float>* D32 = nullptr;
     int k = 0, kp = 0;           // Lanczos vectors and padded row stride
     const double* Q64 = nullptr; // n x kp row-major
     const float* Q32 = nullptr;

@@ -25,6 +25,7 @@ namespace asss {
 constexpr int MRS_THREADS = 512;
 constexpr int MRS_WARPS = MRS_THREADS / 32;
 constexpr int MRS_KPMAX = 64;
+constexpr int MRS_MAXDIAG = 64;
 // resident blocks per SM the register allocation is sized for: two 512-thread
 // blocks for FP32 (more loads in flight for the gathers), one for FP64
 template <class T>
@@ -77,9 +78,14 @@ void mrs_work_destroy(MrsWork* w) { delete w; }
 template <class T>
 struct MrsParams {
     int n;
+    // SELL-C operator
     const int* sptr;
     const int* col;
     const T* val;
+    // skew half-diagonal operator
+    int ndiag;
+    const int* off;
+    const T* U;
     const T* Q;
     const double* alpha;
     int k;
@@ -125,12 +131,17 @@ __device__ __forceinline__ void load_qrow(const T* __restrict__ Q, int i, T (&q)
     }
 }
 
-template <class T, int KP>
+// FMT 0: SELL-C storage of J~; FMT 1: skew half-diagonal storage
+template <class T, int KP, int FMT>
 __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsParams<T> p) {
     constexpr int NV = KP + 1;
     __shared__ double s_wsum[MRS_WARPS][NV];
     __shared__ double s_red[NV];
     __shared__ T s_u[KP > 0 ? KP : 1];
+    __shared__ int s_off[FMT == 1 ? MRS_MAXDIAG : 1];
+    if constexpr (FMT == 1) {
+        for (int d = threadIdx.x; d < p.ndiag; d += MRS_THREADS) s_off[d] = p.off[d];
+    }
     const int nblk = gridDim.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int s0 = p.blk_slice[blockIdx.x], s1 = p.blk_slice[blockIdx.x + 1];
@@ -224,14 +235,27 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
 #pragma unroll
         for (int v = 0; v < NV; ++v) tacc[v] = (T)0;
         for (int sl = s0 + warp; sl < s1; sl += MRS_WARPS) {
-            const int base = __ldg(&p.sptr[sl]);
-            const int width = (__ldg(&p.sptr[sl + 1]) - base) >> 5;
-            T acc = (T)0;
-            const int* cp = p.col + base + lane;
-            const T* vp = p.val + base + lane;
-#pragma unroll 4
-            for (int kk = 0; kk < width; ++kk) acc += __ldg(vp + kk * 32) * Ycur[__ldg(cp + kk * 32)];
             const int i = sl * 32 + lane;
+            T acc = (T)0;
+            if constexpr (FMT == 0) {
+                const int base = __ldg(&p.sptr[sl]);
+                const int width = (__ldg(&p.sptr[sl + 1]) - base) >> 5;
+                const int* cp = p.col + base + lane;
+                const T* vp = p.val + base + lane;
+#pragma unroll 4
+                for (int kk = 0; kk < width; ++kk) acc += __ldg(vp + kk * 32) * Ycur[__ldg(cp + kk * 32)];
+            } else {
+                // (J~ y)_i = sum_d U_d[i] y[i + m_d] - U_d[i - m_d] y[i - m_d]
+                if (i < n) {
+                    const T* Ud = p.U;
+#pragma unroll 4
+                    for (int d = 0; d < p.ndiag; ++d, Ud += n) {
+                        const int m = s_off[d];
+                        if (i + m < n) acc += __ldg(Ud + i) * Ycur[i + m];
+                        if (i >= m) acc -= __ldg(Ud + i - m) * Ycur[i - m];
+                    }
+                }
+            }
             if (i < n) {
                 T yold = (j >= 2) ? __ldcg(&Yold[i]) : (T)0;
                 T q[KP > 0 ? KP : 1];
@@ -297,15 +321,20 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
     }
 }
 
-// block b owns slices [blk[b], blk[b+1]), balanced by stored entries
+// block b owns slices [blk[b], blk[b+1]), balanced by stored entries (SELL) or
+// uniform (diagonal storage: every row carries the same work)
 __global__ void k_partition(const int* sptr, int nslices, int nblk, int* blk) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b > nblk) return;
-    long long total = sptr[nslices];
     if (b == nblk) {
         blk[b] = nslices;
         return;
     }
+    if (!sptr) {
+        blk[b] = (int)((long long)nslices * b / nblk);
+        return;
+    }
+    long long total = sptr[nslices];
     // slices also carry fixed per-row work (Q row, vectors): weight = stored + 32*8
     long long wtot = total + (long long)nslices * 256;
     long long target = wtot * b / nblk;
@@ -319,12 +348,28 @@ __global__ void k_partition(const int* sptr, int nslices, int nblk, int* blk) {
     blk[b] = lo;
 }
 
-template <class T, int KP>
-static asss_status launch_mrs(const Ctx& c, MrsWork* w, const DSell<T>& J, const T* Q, const double* alpha,
+// what the launcher needs to know about the operator, whatever its storage
+template <class T>
+struct OpView {
+    int n = 0;
+    int fmt = 0;
+    int nslices = 0;
+    const int* sptr = nullptr;
+    const int* col = nullptr;
+    const T* val = nullptr;
+    int ndiag = 0;
+    const int* off = nullptr;
+    const T* U = nullptr;
+    const void* key = nullptr;
+    long long nnz = 0;  // matrix entries one application reads
+};
+
+template <class T, int KP, int FMT>
+static asss_status launch_mrs(const Ctx& c, MrsWork* w, const OpView<T>& J, const T* Q, const double* alpha,
                               int k, double shift, double sign, const double* rhs, T* x, T* Y, T* P, double tol,
                               int maxit) {
     int occ = 0;
-    ASSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mrs<T, KP>, MRS_THREADS, 0));
+    ASSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mrs<T, KP, FMT>, MRS_THREADS, 0));
     if (occ < 1) {
         set_error("mrs kernel cannot be resident");
         return ASSS_ERR_CUDA;
@@ -334,19 +379,23 @@ static asss_status launch_mrs(const Ctx& c, MrsWork* w, const DSell<T>& J, const
     int need = cdiv(J.nslices, MRS_WARPS);
     if (need < 1) need = 1;
     if (nblk > need) nblk = need;
-    if (w->part_key != (const void*)&J || w->part_nblk != nblk) {
-        k_partition<<<cdiv(nblk + 1, 128), 128, 0, c.stream>>>(J.sptr.p, J.nslices, nblk, w->blk_slice.p);
+    if (w->part_key != J.key || w->part_nblk != nblk) {
+        k_partition<<<cdiv(nblk + 1, 128), 128, 0, c.stream>>>(FMT == 0 ? J.sptr : nullptr, J.nslices, nblk,
+                                                               w->blk_slice.p);
         ASSS_CHECK_LAUNCH();
-        w->part_key = (const void*)&J;
+        w->part_key = J.key;
         w->part_nblk = nblk;
     }
     ASSS_CUDA(cudaMemsetAsync(w->bar.p, 0, 2 * sizeof(unsigned), c.stream));
     ASSS_CUDA(cudaMemsetAsync(w->err.p, 0, sizeof(int), c.stream));
     MrsParams<T> prm;
     prm.n = J.n;
-    prm.sptr = J.sptr.p;
-    prm.col = J.col.p;
-    prm.val = J.val.p;
+    prm.sptr = J.sptr;
+    prm.col = J.col;
+    prm.val = J.val;
+    prm.ndiag = J.ndiag;
+    prm.off = J.off;
+    prm.U = J.U;
     prm.Q = Q;
     prm.alpha = alpha;
     prm.k = k;
@@ -368,21 +417,21 @@ static asss_status launch_mrs(const Ctx& c, MrsWork* w, const DSell<T>& J, const
     prm.out_ratio = w->out_ratio.p;
     void* args[] = {&prm};
     ASSS_CUDA(cudaEventRecord(w->ev0, c.stream));
-    ASSS_CUDA(cudaLaunchCooperativeKernel((const void*)k_mrs<T, KP>, dim3(nblk), dim3(MRS_THREADS), args, 0,
+    ASSS_CUDA(cudaLaunchCooperativeKernel((const void*)k_mrs<T, KP, FMT>, dim3(nblk), dim3(MRS_THREADS), args, 0,
                                           c.stream));
     count_launch();
     ASSS_CUDA(cudaEventRecord(w->ev1, c.stream));
     return ASSS_OK;
 }
 
-template <class T>
-static asss_status dispatch_mrs(const Ctx& c, MrsWork* w, const DSell<T>& J, const T* Q, const double* alpha,
-                                int k, int kp, double shift, double sign, const double* rhs, T* x, T* Y, T* P,
-                                double tol, int maxit) {
+template <class T, int FMT>
+static asss_status dispatch_kp(const Ctx& c, MrsWork* w, const OpView<T>& J, const T* Q, const double* alpha, int k,
+                               int kp, double shift, double sign, const double* rhs, T* x, T* Y, T* P, double tol,
+                               int maxit) {
     switch (kp) {
 #define ASSS_MRS_CASE(KPV) \
     case KPV:              \
-        return launch_mrs<T, KPV>(c, w, J, Q, alpha, k, shift, sign, rhs, x, Y, P, tol, maxit);
+        return launch_mrs<T, KPV, FMT>(c, w, J, Q, alpha, k, shift, sign, rhs, x, Y, P, tol, maxit);
         ASSS_MRS_CASE(0)
         ASSS_MRS_CASE(4)
         ASSS_MRS_CASE(8)
@@ -400,12 +449,47 @@ static asss_status dispatch_mrs(const Ctx& c, MrsWork* w, const DSell<T>& J, con
     }
 }
 
+template <class T>
+static asss_status dispatch_mrs(const Ctx& c, MrsWork* w, const DSell<T>* sell, const DSkewDia<T>* dia, const T* Q,
+                                const double* alpha, int k, int kp, double shift, double sign, const double* rhs,
+                                T* x, T* Y, T* P, double tol, int maxit, long long* nnz_read) {
+    OpView<T> v;
+    if (dia && dia->ndiag > MRS_MAXDIAG) dia = nullptr;
+    if (dia) {
+        v.n = dia->n;
+        v.fmt = 1;
+        v.nslices = cdiv(dia->n, 32);
+        v.ndiag = dia->ndiag;
+        v.off = dia->off.p;
+        v.U = dia->U.p;
+        v.key = dia;
+        v.nnz = dia->nnz;
+        *nnz_read = v.nnz;
+        return dispatch_kp<T, 1>(c, w, v, Q, alpha, k, kp, shift, sign, rhs, x, Y, P, tol, maxit);
+    }
+    if (!sell) {
+        set_error("mrs: no operator storage");
+        return ASSS_ERR_ARG;
+    }
+    v.n = sell->n;
+    v.fmt = 0;
+    v.nslices = sell->nslices;
+    v.sptr = sell->sptr.p;
+    v.col = sell->col.p;
+    v.val = sell->val.p;
+    v.key = sell;
+    v.nnz = sell->nnz;
+    *nnz_read = v.nnz;
+    return dispatch_kp<T, 0>(c, w, v, Q, alpha, k, kp, shift, sign, rhs, x, Y, P, tol, maxit);
+}
+
 asss_status mrs_solve(const Ctx& c, MrsWork* w, const MrsOperator& op, bool fp32, double shift, double sign,
                       const double* rhs, double* x64, float* x32, double tol, int maxit, MrsResult* res,
                       bool sync_result) {
     int n = w->n;
+    long long nnz_read = 0;
     if (fp32) {
-        if (!op.J32 || !x32) {
+        if ((!op.J32 && !op.D32) || !x32) {
             set_error("FP32 mrs needs the FP32 operator and an FP32 output");
             return ASSS_ERR_ARG;
         }
@@ -413,10 +497,10 @@ asss_status mrs_solve(const Ctx& c, MrsWork* w, const MrsOperator& op, bool fp32
             ASSS_TRY(w->Y32.alloc((int64_t)3 * n));
             ASSS_TRY(w->P32.alloc((int64_t)2 * n));
         }
-        ASSS_TRY(dispatch_mrs<float>(c, w, *op.J32, op.Q32, op.alpha, op.k, op.kp, shift, sign, rhs, x32,
-                                     w->Y32.p, w->P32.p, tol, maxit));
+        ASSS_TRY(dispatch_mrs<float>(c, w, op.J32, op.D32, op.Q32, op.alpha, op.k, op.kp, shift, sign, rhs, x32,
+                                     w->Y32.p, w->P32.p, tol, maxit, &nnz_read));
     } else {
-        if (!op.J64 || !x64) {
+        if ((!op.J64 && !op.D64) || !x64) {
             set_error("FP64 mrs needs the FP64 operator and an FP64 output");
             return ASSS_ERR_ARG;
         }
@@ -424,8 +508,8 @@ asss_status mrs_solve(const Ctx& c, MrsWork* w, const MrsOperator& op, bool fp32
             ASSS_TRY(w->Y64.alloc((int64_t)3 * n));
             ASSS_TRY(w->P64.alloc((int64_t)2 * n));
         }
-        ASSS_TRY(dispatch_mrs<double>(c, w, *op.J64, op.Q64, op.alpha, op.k, op.kp, shift, sign, rhs, x64,
-                                      w->Y64.p, w->P64.p, tol, maxit));
+        ASSS_TRY(dispatch_mrs<double>(c, w, op.J64, op.D64, op.Q64, op.alpha, op.k, op.kp, shift, sign, rhs, x64,
+                                      w->Y64.p, w->P64.p, tol, maxit, &nnz_read));
     }
     if (sync_result && res) {
         int herr = 0;
@@ -442,9 +526,10 @@ asss_status mrs_solve(const Ctx& c, MrsWork* w, const MrsOperator& op, bool fp32
         // final pass (y, p, x r/w)
         long long T = fp32 ? 4 : 8;
         long long nn = n, kp = op.kp;
-        long long nnzJ = fp32 ? op.J32->nnz : op.J64->nnz;
-        res->bytes = nn * (8 + 4 * T + kp * T) + (long long)res->its * (nnzJ * (T + 4) + nn * (7 * T + kp * T)) +
-                     nn * 4 * T;
+        // SELL entries carry a 4-byte column index; diagonal storage reads values only
+        long long per_entry = (fp32 ? (op.D32 != nullptr) : (op.D64 != nullptr)) ? T : T + 4;
+        res->bytes = nn * (8 + 4 * T + kp * T) +
+                     (long long)res->its * (nnz_read * per_entry + nn * (7 * T + kp * T)) + nn * 4 * T;
         if (herr) {
             set_error("mrs: a grid barrier wait exceeded its budget");
             return (asss_status)herr;

@@ -634,3 +634,118 @@ template asss_status build_sell<double>(const DCsr&, bool, DSell<double>&, cudaS
 template asss_status build_sell<float>(const DCsr&, bool, DSell<float>&, cudaStream_t);
 
 }  // namespace asss
+
+namespace asss {
+
+// ---------------------------------------------------------------------------
+// skew half-diagonal storage
+// ---------------------------------------------------------------------------
+// exact skew check (J_ij == -J_ji bit for bit, zero diagonal) and the offset set
+__global__ void k_skew_offsets(int n, const int* rp, const int* ci, const double* v, unsigned* bits,
+                               unsigned long long* nup, int* bad) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    long long cnt = 0;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+        int j = ci[e];
+        if (j == i) {
+            if (v[e] != 0.0) atomicOr(bad, 1);
+            continue;
+        }
+        // mirror entry
+        int lo = rp[j], hi = rp[j + 1] - 1, f = -1;
+        while (lo <= hi) {
+            int mid = (lo + hi) >> 1;
+            int c = ci[mid];
+            if (c == i) {
+                f = mid;
+                break;
+            }
+            if (c < i) lo = mid + 1;
+            else hi = mid - 1;
+        }
+        double mv = f >= 0 ? v[f] : 0.0;
+        if (mv != -v[e]) atomicOr(bad, 1);
+        if (j > i) {
+            int off = j - i;
+            atomicOr(&bits[off >> 5], 1u << (off & 31));
+            ++cnt;
+        }
+    }
+    if (cnt) atomicAdd(nup, (unsigned long long)cnt);
+}
+
+template <class T>
+__global__ void k_fill_dia(int n, const int* rp, const int* ci, const double* v, const int* off, int ndiag, T* U) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+        int j = ci[e];
+        if (j <= i) continue;
+        int m = j - i;
+        int lo = 0, hi = ndiag - 1;
+        while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if (off[mid] < m) lo = mid + 1;
+            else hi = mid;
+        }
+        U[(size_t)lo * n + i] = (T)v[e];
+    }
+}
+
+template <class T>
+asss_status build_skew_dia(const DCsr& J, int max_diag, double min_fill, DSkewDia<T>& out, int* ok, cudaStream_t s) {
+    *ok = 0;
+    int n = J.n;
+    if (n < 2 || !J.v.p) return ASSS_OK;
+    int words = (n + 31) / 32;
+    DBuf<unsigned> bits;
+    DBuf<unsigned long long> nup;
+    DBuf<int> bad;
+    ASSS_TRY(bits.alloc(words));
+    ASSS_TRY(nup.alloc(1));
+    ASSS_TRY(bad.alloc(1));
+    ASSS_CUDA(cudaMemsetAsync(bits.p, 0, sizeof(unsigned) * words, s));
+    ASSS_CUDA(cudaMemsetAsync(nup.p, 0, sizeof(unsigned long long), s));
+    ASSS_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
+    k_skew_offsets<<<cdiv(n, 256), 256, 0, s>>>(n, J.rp.p, J.ci.p, J.v.p, bits.p, nup.p, bad.p);
+    ASSS_CHECK_LAUNCH();
+    std::vector<unsigned> hb(words);
+    unsigned long long hnup = 0;
+    int hbad = 0;
+    ASSS_CUDA(cudaMemcpyAsync(hb.data(), bits.p, sizeof(unsigned) * words, cudaMemcpyDeviceToHost, s));
+    ASSS_CUDA(cudaMemcpyAsync(&hnup, nup.p, sizeof(hnup), cudaMemcpyDeviceToHost, s));
+    ASSS_CUDA(cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ASSS_CUDA(cudaStreamSynchronize(s));
+    if (hbad) return ASSS_OK;  // not exactly skew
+    std::vector<int> off;
+    for (int w = 0; w < words; ++w) {
+        unsigned b = hb[w];
+        while (b) {
+            int t = __builtin_ctz(b);
+            off.push_back(w * 32 + t);
+            b &= b - 1;
+            if ((int)off.size() > max_diag) return ASSS_OK;
+        }
+    }
+    if (off.empty()) return ASSS_OK;
+    double stored = 0.0;
+    for (int m : off) stored += (double)(n - m);
+    if ((double)hnup < min_fill * stored) return ASSS_OK;
+    out.n = n;
+    out.ndiag = (int)off.size();
+    out.nnz = (int64_t)hnup;
+    ASSS_TRY(to_device(out.off, off.data(), (int64_t)off.size(), s));
+    ASSS_TRY(out.U.alloc((int64_t)out.ndiag * n));
+    ASSS_CUDA(cudaMemsetAsync(out.U.p, 0, sizeof(T) * (size_t)out.ndiag * n, s));
+    k_fill_dia<T><<<cdiv(n, 256), 256, 0, s>>>(n, J.rp.p, J.ci.p, J.v.p, out.off.p, out.ndiag, out.U.p);
+    ASSS_CHECK_LAUNCH();
+    ASSS_CUDA(cudaStreamSynchronize(s));
+    *ok = 1;
+    return ASSS_OK;
+}
+
+template asss_status build_skew_dia<double>(const DCsr&, int, double, DSkewDia<double>&, int*, cudaStream_t);
+template asss_status build_skew_dia<float>(const DCsr&, int, double, DSkewDia<float>&, int*, cudaStream_t);
+
+}  // namespace asss

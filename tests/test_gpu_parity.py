@@ -245,3 +245,71 @@ def test_torch_autograd(pkg):
     rows = np.repeat(np.arange(n), np.diff(A.indptr))
     np.testing.assert_allclose(av.grad.cpu().numpy(), -lam_d[rows] * xd[A.indices], rtol=0,
                                atol=1e-8 * np.abs(lam_d).max() * np.abs(xd).max())
+
+
+# ----------------------------------------------------------------------------
+# skew half-diagonal storage of J~ (same results as SELL-C and the oracle)
+# ----------------------------------------------------------------------------
+def banded_skew(n, offsets, seed, fill=0.9, scale=0.1):
+    rng = np.random.default_rng(seed)
+    rows, cols, vals = [], [], []
+    for m in offsets:
+        i = np.arange(n - m)
+        i = i[rng.random(i.size) < fill]
+        v = rng.standard_normal(i.size) * scale
+        rows += [i, i + m]
+        cols += [i + m, i]
+        vals += [v, -v]
+    J = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+    J.sort_indices()
+    return J
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_mrs_diag_storage_matches_sell_and_oracle(pkg, precision):
+    n = 40001
+    J = banded_skew(n, (1, 3, 64, 1000, 20000), seed=5)
+    rng = np.random.default_rng(6)
+    b = rng.standard_normal(n)
+    Q, alpha = O.skew_lanczos(J, rng.standard_normal(n), 20)
+    Sk = O.lanczos_tridiagonal(alpha)
+    apply = lambda V: J @ V - Q @ (Sk @ (Q.T @ V))
+    xo, its_o, _, _ = O.mrs(1.0, apply, b, 3000, 1e-12)
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    xd, its_d, rd = pkg.mrs(J, b, Q, alpha, tol=tol, maxit=3000, precision=precision, fmt="diag")
+    xs, its_s, rs = pkg.mrs(J, b, Q, alpha, tol=tol, maxit=3000, precision=precision, fmt="sell")
+    true = np.linalg.norm(b - xd - apply(xd)) / np.linalg.norm(b)
+    if precision == "fp64":
+        assert abs(its_d - its_o) <= 2 and abs(its_s - its_o) <= 2
+        assert np.linalg.norm(xd - xo) <= 1e-9 * np.linalg.norm(xo)
+        assert np.linalg.norm(xs - xo) <= 1e-9 * np.linalg.norm(xo)
+        assert true <= 1e-11
+    else:
+        assert rd < 1e-5 and true <= 5e-5
+        assert np.linalg.norm(xd - xo) <= 1e-4 * np.linalg.norm(xo)
+
+
+def test_mrs_diag_storage_rejects_non_skew(pkg):
+    n = 500
+    J = banded_skew(n, (1, 5), seed=1).tolil()
+    J[3, 4] += 1e-3   # no longer exactly skew
+    J = J.tocsr()
+    with pytest.raises(pkg.AsssError):
+        pkg.mrs(J, np.ones(n), fmt="diag")
+    x, its, ratio = pkg.mrs(J, np.ones(n), fmt="auto", tol=1e-8)   # falls back to SELL-C
+    assert ratio < 1e-8
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solver_storage_formats_agree(pkg, precision):
+    A, b, _ = dissipative_hamiltonian_3d(side=16, seed=9)
+    tol = 1e-6 if precision == "mixed" else 1e-10
+    res = {}
+    for fmt in ("sell", "diag"):
+        s = pkg.Solver(A, precision=precision, outer="fgmres", inner_tol=tol, inner_format=fmt)
+        x, st = s.solve(b)
+        assert st["status"] == 0 and np.linalg.norm(b - A @ x) <= 1e-8 * np.linalg.norm(b)
+        res[fmt] = (x, st)
+        s.close()
+    assert abs(res["sell"][1]["outer_its"] - res["diag"][1]["outer_its"]) <= 1
+    assert np.linalg.norm(res["sell"][0] - res["diag"][0]) <= 1e-7 * np.linalg.norm(res["sell"][0])
