@@ -110,8 +110,10 @@ struct DSkewDia {
     int n = 0;
     int ndiag = 0;
     int64_t nnz = 0;          // stored upper entries that come from the matrix
+    int halo = 0;             // largest offset: zero entries stored in front of each diagonal
+    int64_t ustride = 0;      // n + halo
     DBuf<int> off;            // ndiag ascending positive offsets
-    DBuf<T> U;                // ndiag x n
+    DBuf<T> U;                // diagonal d at U + d*ustride + halo, entries [-halo, n)
 };
 
 // ---------------------------------------------------------------------------

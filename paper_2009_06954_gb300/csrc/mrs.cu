@@ -44,6 +44,7 @@ struct MrsWork {
     DBuf<int> blk_slice;
     const void* part_key = nullptr;
     int part_nblk = 0;
+    int halo32 = -1, halo64 = -1;  // halo of the current Y layout (-1: not laid out)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     ~MrsWork() {
         if (ev0) cudaEventDestroy(ev0);
@@ -82,17 +83,19 @@ struct MrsParams {
     const int* sptr;
     const int* col;
     const T* val;
-    // skew half-diagonal operator
+    // skew half-diagonal operator: U points at U_0[0]; diagonal d starts ustride later
     int ndiag;
     const int* off;
     const T* U;
+    long long ustride;
+    long long ystride;  // distance between the three Y slots (n + 2 halo)
     const T* Q;
     const double* alpha;
     int k;
     double shift, sign;
     const double* rhs;
     T* x;
-    T* Y;  // 3n ring of unnormalised Lanczos vectors
+    T* Y;  // 3 slots of unnormalised Lanczos vectors, each with a zero halo on both ends
     T* P;  // 2n ring of update directions
     double* part;  // [2][NV][nblk]
     GridBarrier gb;
@@ -131,6 +134,18 @@ __device__ __forceinline__ void load_qrow(const T* __restrict__ Q, int i, T (&q)
     }
 }
 
+// Scalar state of the recurrence, kept in shared memory and advanced by one
+// thread per block (FP64 is slow on this part; every block computes the same
+// values from the same reduced sums, so all blocks agree bit for bit).
+struct MrsScalars {
+    double r0, nu, coef_old, theta_t, c_prev, s_prev, delta_prev, G;
+    double nu_p, delta_pp, theta_p, xcoef_p;
+    // final-pass coefficients when the iteration stops
+    double fin_nu, fin_delta, fin_theta, fin_xcoef;
+    double ratio;
+    int its, stop;
+};
+
 // FMT 0: SELL-C storage of J~; FMT 1: skew half-diagonal storage
 template <class T, int KP, int FMT>
 __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsParams<T> p) {
@@ -139,6 +154,7 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
     __shared__ double s_red[NV];
     __shared__ T s_u[KP > 0 ? KP : 1];
     __shared__ int s_off[FMT == 1 ? MRS_MAXDIAG : 1];
+    __shared__ MrsScalars sc;
     if constexpr (FMT == 1) {
         for (int d = threadIdx.x; d < p.ndiag; d += MRS_THREADS) s_off[d] = p.off[d];
     }
@@ -146,13 +162,15 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int s0 = p.blk_slice[blockIdx.x], s1 = p.blk_slice[blockIdx.x + 1];
     const int n = p.n;
+    const size_t ys = p.ystride;
     volatile int* err = p.gb.err;
 
+    // warp sums in T, then FP64 across warps (fixed order) into this block's partial
     auto block_partials = [&](T(&tacc)[NV], double* buf) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            double d = warp_sum((double)tacc[v]);
-            if (lane == 0) s_wsum[warp][v] = d;
+            T d = warp_sum(tacc[v]);
+            if (lane == 0) s_wsum[warp][v] = (double)d;
         }
         __syncthreads();
         for (int v = threadIdx.x; v < NV; v += MRS_THREADS) {
@@ -210,28 +228,41 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
     if (*err) return;
     reduce_all(p.part);
 
-    const double r0 = sqrt(s_red[0]);
-    if (r0 == 0.0) {
+    if (threadIdx.x == 0) {
+        double r0 = sqrt(s_red[0]);
+        sc.r0 = r0;
+        sc.nu = r0 > 0.0 ? 1.0 / r0 : 0.0;
+        sc.coef_old = 0.0;
+        sc.theta_t = p.shift;
+        sc.c_prev = 1.0;
+        sc.s_prev = 0.0;
+        sc.delta_prev = 0.0;
+        sc.G = r0;
+        sc.nu_p = 0.0;
+        sc.delta_pp = 0.0;
+        sc.theta_p = 1.0;
+        sc.xcoef_p = 0.0;
+        sc.ratio = r0 > 0.0 ? 1.0 : 0.0;
+        sc.its = 0;
+        sc.stop = r0 > 0.0 ? 0 : 1;
+    }
+    __syncthreads();
+    if (sc.stop) {  // b = 0: x = 0 already
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             *p.out_its = 0;
             *p.out_ratio = 0.0;
         }
         return;
     }
-    double nu = 1.0 / r0, coef_old = 0.0, theta_t = p.shift, c_prev = 1.0, s_prev = 0.0, delta_prev = 0.0;
-    double G = r0;
-    double nu_p = 0.0, delta_pp = 0.0, theta_p = 1.0, xcoef_p = 0.0;
-    make_u(nu);
+    make_u(sc.nu);
 
-    int its = 0;
-    double ratio = 1.0;
     for (int j = 1; j <= p.maxit; ++j) {
-        T* Ycur = p.Y + (size_t)((j - 1) % 3) * n;
-        T* Yold = p.Y + (size_t)((j + 1) % 3) * n;
-        T* Ynew = p.Y + (size_t)(j % 3) * n;
+        T* Ycur = p.Y + (size_t)((j - 1) % 3) * ys;
+        T* Yold = p.Y + (size_t)((j + 1) % 3) * ys;
+        T* Ynew = p.Y + (size_t)(j % 3) * ys;
         T* Pj1 = p.P + (size_t)((j - 1) & 1) * n;
-        const T tnu = (T)(p.sign * nu), tsg = (T)p.sign, tco = (T)coef_old;
-        const T tnp = (T)nu_p, tdpp = (T)delta_pp, tthp = (T)(1.0 / theta_p), txp = (T)xcoef_p;
+        const T tnu = (T)(p.sign * sc.nu), tsg = (T)p.sign, tco = (T)sc.coef_old;
+        const T tnp = (T)sc.nu_p, tdpp = (T)sc.delta_pp, tthp = (T)(1.0 / sc.theta_p), txp = (T)sc.xcoef_p;
 #pragma unroll
         for (int v = 0; v < NV; ++v) tacc[v] = (T)0;
         for (int sl = s0 + warp; sl < s1; sl += MRS_WARPS) {
@@ -245,19 +276,20 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
 #pragma unroll 4
                 for (int kk = 0; kk < width; ++kk) acc += __ldg(vp + kk * 32) * Ycur[__ldg(cp + kk * 32)];
             } else {
-                // (J~ y)_i = sum_d U_d[i] y[i + m_d] - U_d[i - m_d] y[i - m_d]
+                // (J~ y)_i = sum_d U_d[i] y[i + m_d] - U_d[i - m_d] y[i - m_d]; zero halos on
+                // both U (front) and y (both ends) make the loop branch-free
                 if (i < n) {
-                    const T* Ud = p.U;
+                    const T* Ud = p.U + i;
+                    const T* yi = Ycur + i;
 #pragma unroll 4
-                    for (int d = 0; d < p.ndiag; ++d, Ud += n) {
+                    for (int d = 0; d < p.ndiag; ++d, Ud += p.ustride) {
                         const int m = s_off[d];
-                        if (i + m < n) acc += __ldg(Ud + i) * Ycur[i + m];
-                        if (i >= m) acc -= __ldg(Ud + i - m) * Ycur[i - m];
+                        acc += __ldg(Ud) * yi[m] - __ldg(Ud - m) * yi[-m];
                     }
                 }
             }
             if (i < n) {
-                T yold = (j >= 2) ? __ldcg(&Yold[i]) : (T)0;
+                T yold = (j >= 2) ? Yold[i] : (T)0;
                 T q[KP > 0 ? KP : 1];
                 load_qrow<T, KP>(p.Q, i, q);
                 T dq = (T)0;
@@ -281,43 +313,55 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
         if (*err) break;
         reduce_all(buf);
 
-        const double beta = sqrt(s_red[0]);
-        const double theta = sqrt(theta_t * theta_t + beta * beta);
-        const double c = theta_t / theta, s = beta / theta;
-        const double delta = -s_prev * beta;
-        const double theta_t_next = c_prev * theta;
-        const double xcoef = G * c;
-        const double Gn = -G * s;
-        ratio = fabs(Gn) / r0;
-        its = j;
-        if (ratio < p.tol || j == p.maxit) {
+        if (threadIdx.x == 0) {
+            const double beta = sqrt(s_red[0]);
+            const double theta = sqrt(sc.theta_t * sc.theta_t + beta * beta);
+            const double c = sc.theta_t / theta, s = beta / theta;
+            const double delta = -sc.s_prev * beta;
+            const double theta_t_next = sc.c_prev * theta;
+            const double xcoef = sc.G * c;
+            const double Gn = -sc.G * s;
+            sc.ratio = fabs(Gn) / sc.r0;
+            sc.its = j;
+            if (sc.ratio < p.tol || j == p.maxit) {
+                sc.stop = 1;
+                sc.fin_nu = sc.nu;
+                sc.fin_delta = sc.delta_prev;
+                sc.fin_theta = theta;
+                sc.fin_xcoef = xcoef;
+            } else {
+                sc.nu_p = sc.nu;
+                sc.delta_pp = sc.delta_prev;
+                sc.theta_p = theta;
+                sc.xcoef_p = xcoef;
+                sc.coef_old = beta * sc.nu;
+                sc.nu = (beta != 0.0) ? 1.0 / beta : 0.0;
+                sc.s_prev = s;
+                sc.c_prev = c;
+                sc.delta_prev = delta;
+                sc.theta_t = theta_t_next;
+                sc.G = Gn;
+            }
+        }
+        __syncthreads();
+        if (sc.stop) {
             T* Pj = p.P + (size_t)(j & 1) * n;
-            const T tn = (T)nu, td = (T)delta_prev, tth = (T)(1.0 / theta), tx = (T)xcoef;
+            const T tn = (T)sc.fin_nu, td = (T)sc.fin_delta, tth = (T)(1.0 / sc.fin_theta),
+                    tx = (T)sc.fin_xcoef;
             for (int sl = s0 + warp; sl < s1; sl += MRS_WARPS) {
                 int i = sl * 32 + lane;
                 if (i < n) {
-                    T pv = (tn * __ldcg(&Ycur[i]) - td * Pj[i]) * tth;
+                    T pv = (tn * Ycur[i] - td * Pj[i]) * tth;
                     p.x[i] += tx * pv;
                 }
             }
             break;
         }
-        nu_p = nu;
-        delta_pp = delta_prev;
-        theta_p = theta;
-        xcoef_p = xcoef;
-        coef_old = beta * nu;
-        nu = (beta != 0.0) ? 1.0 / beta : 0.0;
-        s_prev = s;
-        c_prev = c;
-        delta_prev = delta;
-        theta_t = theta_t_next;
-        G = Gn;
-        make_u(nu);
+        make_u(sc.nu);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        *p.out_its = its;
-        *p.out_ratio = ratio;
+        *p.out_its = sc.its;
+        *p.out_ratio = sc.ratio;
     }
 }
 
@@ -360,14 +404,16 @@ struct OpView {
     int ndiag = 0;
     const int* off = nullptr;
     const T* U = nullptr;
+    long long ustride = 0;
+    int halo = 0;
     const void* key = nullptr;
     long long nnz = 0;  // matrix entries one application reads
 };
 
 template <class T, int KP, int FMT>
 static asss_status launch_mrs(const Ctx& c, MrsWork* w, const OpView<T>& J, const T* Q, const double* alpha,
-                              int k, double shift, double sign, const double* rhs, T* x, T* Y, T* P, double tol,
-                              int maxit) {
+                              int k, double shift, double sign, const double* rhs, T* x, T* Y, long long ystride,
+                              T* P, double tol, int maxit) {
     int occ = 0;
     ASSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mrs<T, KP, FMT>, MRS_THREADS, 0));
     if (occ < 1) {
@@ -396,6 +442,8 @@ static asss_status launch_mrs(const Ctx& c, MrsWork* w, const OpView<T>& J, cons
     prm.ndiag = J.ndiag;
     prm.off = J.off;
     prm.U = J.U;
+    prm.ustride = J.ustride;
+    prm.ystride = ystride;
     prm.Q = Q;
     prm.alpha = alpha;
     prm.k = k;
@@ -426,12 +474,12 @@ static asss_status launch_mrs(const Ctx& c, MrsWork* w, const OpView<T>& J, cons
 
 template <class T, int FMT>
 static asss_status dispatch_kp(const Ctx& c, MrsWork* w, const OpView<T>& J, const T* Q, const double* alpha, int k,
-                               int kp, double shift, double sign, const double* rhs, T* x, T* Y, T* P, double tol,
-                               int maxit) {
+                               int kp, double shift, double sign, const double* rhs, T* x, T* Y, long long ystride,
+                               T* P, double tol, int maxit) {
     switch (kp) {
 #define ASSS_MRS_CASE(KPV) \
     case KPV:              \
-        return launch_mrs<T, KPV, FMT>(c, w, J, Q, alpha, k, shift, sign, rhs, x, Y, P, tol, maxit);
+        return launch_mrs<T, KPV, FMT>(c, w, J, Q, alpha, k, shift, sign, rhs, x, Y, ystride, P, tol, maxit);
         ASSS_MRS_CASE(0)
         ASSS_MRS_CASE(4)
         ASSS_MRS_CASE(8)
@@ -449,23 +497,43 @@ static asss_status dispatch_kp(const Ctx& c, MrsWork* w, const OpView<T>& J, con
     }
 }
 
+// Y ring with zero halos of width H on both ends of each slot (re-zeroed whenever
+// the layout changes; the kernel never writes the halos)
+template <class T>
+static asss_status y_layout(MrsWork* w, DBuf<T>& Ybuf, int& cur, int H, cudaStream_t s, T** Y, long long* ystride) {
+    long long st = (long long)w->n + 2LL * H;
+    if (cur != H || Ybuf.n < 3 * st) {
+        if (Ybuf.n < 3 * st) ASSS_TRY(Ybuf.alloc(3 * st));
+        ASSS_CUDA(cudaMemsetAsync(Ybuf.p, 0, sizeof(T) * (size_t)Ybuf.n, s));
+        cur = H;
+    }
+    *Y = Ybuf.p + H;
+    *ystride = st;
+    return ASSS_OK;
+}
+
 template <class T>
 static asss_status dispatch_mrs(const Ctx& c, MrsWork* w, const DSell<T>* sell, const DSkewDia<T>* dia, const T* Q,
                                 const double* alpha, int k, int kp, double shift, double sign, const double* rhs,
-                                T* x, T* Y, T* P, double tol, int maxit, long long* nnz_read) {
+                                T* x, DBuf<T>& Ybuf, int& ylay, T* P, double tol, int maxit, long long* nnz_read) {
     OpView<T> v;
     if (dia && dia->ndiag > MRS_MAXDIAG) dia = nullptr;
+    T* Y = nullptr;
+    long long ystride = 0;
+    ASSS_TRY(y_layout<T>(w, Ybuf, ylay, dia ? dia->halo : 0, c.stream, &Y, &ystride));
     if (dia) {
         v.n = dia->n;
         v.fmt = 1;
         v.nslices = cdiv(dia->n, 32);
         v.ndiag = dia->ndiag;
         v.off = dia->off.p;
-        v.U = dia->U.p;
+        v.U = dia->U.p + dia->halo;
+        v.ustride = dia->ustride;
+        v.halo = dia->halo;
         v.key = dia;
         v.nnz = dia->nnz;
         *nnz_read = v.nnz;
-        return dispatch_kp<T, 1>(c, w, v, Q, alpha, k, kp, shift, sign, rhs, x, Y, P, tol, maxit);
+        return dispatch_kp<T, 1>(c, w, v, Q, alpha, k, kp, shift, sign, rhs, x, Y, ystride, P, tol, maxit);
     }
     if (!sell) {
         set_error("mrs: no operator storage");
@@ -480,7 +548,7 @@ static asss_status dispatch_mrs(const Ctx& c, MrsWork* w, const DSell<T>* sell, 
     v.key = sell;
     v.nnz = sell->nnz;
     *nnz_read = v.nnz;
-    return dispatch_kp<T, 0>(c, w, v, Q, alpha, k, kp, shift, sign, rhs, x, Y, P, tol, maxit);
+    return dispatch_kp<T, 0>(c, w, v, Q, alpha, k, kp, shift, sign, rhs, x, Y, ystride, P, tol, maxit);
 }
 
 asss_status mrs_solve(const Ctx& c, MrsWork* w, const MrsOperator& op, bool fp32, double shift, double sign,
@@ -493,23 +561,17 @@ asss_status mrs_solve(const Ctx& c, MrsWork* w, const MrsOperator& op, bool fp32
             set_error("FP32 mrs needs the FP32 operator and an FP32 output");
             return ASSS_ERR_ARG;
         }
-        if (!w->Y32.p) {
-            ASSS_TRY(w->Y32.alloc((int64_t)3 * n));
-            ASSS_TRY(w->P32.alloc((int64_t)2 * n));
-        }
+        if (!w->P32.p) ASSS_TRY(w->P32.alloc((int64_t)2 * n));
         ASSS_TRY(dispatch_mrs<float>(c, w, op.J32, op.D32, op.Q32, op.alpha, op.k, op.kp, shift, sign, rhs, x32,
-                                     w->Y32.p, w->P32.p, tol, maxit, &nnz_read));
+                                     w->Y32, w->halo32, w->P32.p, tol, maxit, &nnz_read));
     } else {
         if ((!op.J64 && !op.D64) || !x64) {
             set_error("FP64 mrs needs the FP64 operator and an FP64 output");
             return ASSS_ERR_ARG;
         }
-        if (!w->Y64.p) {
-            ASSS_TRY(w->Y64.alloc((int64_t)3 * n));
-            ASSS_TRY(w->P64.alloc((int64_t)2 * n));
-        }
+        if (!w->P64.p) ASSS_TRY(w->P64.alloc((int64_t)2 * n));
         ASSS_TRY(dispatch_mrs<double>(c, w, op.J64, op.D64, op.Q64, op.alpha, op.k, op.kp, shift, sign, rhs, x64,
-                                      w->Y64.p, w->P64.p, tol, maxit, &nnz_read));
+                                      w->Y64, w->halo64, w->P64.p, tol, maxit, &nnz_read));
     }
     if (sync_result && res) {
         int herr = 0;

@@ -676,7 +676,8 @@ __global__ void k_skew_offsets(int n, const int* rp, const int* ci, const double
 }
 
 template <class T>
-__global__ void k_fill_dia(int n, const int* rp, const int* ci, const double* v, const int* off, int ndiag, T* U) {
+__global__ void k_fill_dia(int n, const int* rp, const int* ci, const double* v, const int* off, int ndiag,
+                           int64_t ustride, T* U) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     for (int e = rp[i]; e < rp[i + 1]; ++e) {
@@ -689,7 +690,7 @@ __global__ void k_fill_dia(int n, const int* rp, const int* ci, const double* v,
             if (off[mid] < m) lo = mid + 1;
             else hi = mid;
         }
-        U[(size_t)lo * n + i] = (T)v[e];
+        U[(size_t)lo * ustride + i] = (T)v[e];
     }
 }
 
@@ -735,10 +736,13 @@ asss_status build_skew_dia(const DCsr& J, int max_diag, double min_fill, DSkewDi
     out.n = n;
     out.ndiag = (int)off.size();
     out.nnz = (int64_t)hnup;
+    out.halo = off.back();
+    out.ustride = (int64_t)n + out.halo;
     ASSS_TRY(to_device(out.off, off.data(), (int64_t)off.size(), s));
-    ASSS_TRY(out.U.alloc((int64_t)out.ndiag * n));
-    ASSS_CUDA(cudaMemsetAsync(out.U.p, 0, sizeof(T) * (size_t)out.ndiag * n, s));
-    k_fill_dia<T><<<cdiv(n, 256), 256, 0, s>>>(n, J.rp.p, J.ci.p, J.v.p, out.off.p, out.ndiag, out.U.p);
+    ASSS_TRY(out.U.alloc((int64_t)out.ndiag * out.ustride));
+    ASSS_CUDA(cudaMemsetAsync(out.U.p, 0, sizeof(T) * (size_t)out.ndiag * out.ustride, s));
+    k_fill_dia<T><<<cdiv(n, 256), 256, 0, s>>>(n, J.rp.p, J.ci.p, J.v.p, out.off.p, out.ndiag, out.ustride,
+                                               out.U.p + out.halo);
     ASSS_CHECK_LAUNCH();
     ASSS_CUDA(cudaStreamSynchronize(s));
     *ok = 1;
