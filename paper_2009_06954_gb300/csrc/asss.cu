@@ -124,6 +124,31 @@ __global__ void k_f2d(const float* a, double* b, int n) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) b[i] = (double)a[i];
 }
+__global__ void k_gather_neg_f(const float* z, const int* neg, int r, double* out) {
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < r) out[a] = (double)z[neg[a]];
+}
+__global__ void k_d2f(const double* a, int64_t n, float* b) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+// out = z - Y w for the mixed-precision path: z and Y in FP32, w and out in FP64
+__global__ void k_smw_apply_f32(const float* __restrict__ z, const float* __restrict__ Y, int m,
+                                const double* __restrict__ w, int n, double* out) {
+    extern __shared__ double sw_f[];
+    for (int t = threadIdx.x; t < m; t += blockDim.x) sw_f[t] = w[t];
+    __syncthreads();
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double acc = 0.0;
+    if (m > 0) {
+        const float* row = Y + (size_t)i * m;
+        float a = 0.f;
+        for (int c = 0; c < m; ++c) a += row[c] * (float)sw_f[c];
+        acc = a;
+    }
+    out[i] = (double)z[i] - acc;
+}
 __global__ void k_gather_neg(const double* z, const int* neg, int r, double* out) {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a < r) out[a] = z[neg[a]];
@@ -343,7 +368,8 @@ __global__ void k_scale_dev(double* y, const double* x, const double* s, int n) 
 struct SmwData {
     bool ready = false;
     int m = 0;
-    DBuf<double> Y;  // n x m row-major: X Sig (I + U^T X Sig)^-1
+    DBuf<double> Y;    // n x m row-major: X Sig (I + U^T X Sig)^-1
+    DBuf<float> Y32;   // FP32 copy for the mixed-precision preconditioner
 };
 
 struct asss_handle {
@@ -508,9 +534,8 @@ static asss_status ensure_smw(asss_handle* h, int tr) {
             ASSS_CHECK_LAUNCH();
             b = rhs.p;
         }
-        MrsResult res;
         ASSS_TRY(mrs_solve(c, h->mw, op, false, 1.0, sign, b, X.p + (size_t)col * n, nullptr, tol,
-                           h->opt.inner_maxit, &res, true));
+                           h->opt.inner_maxit, nullptr, nullptr, false));
     }
     ASSS_TRY(G.alloc((int64_t)m * m));
     ASSS_TRY(Sig.alloc((int64_t)m * m));
@@ -533,16 +558,26 @@ static asss_status ensure_smw(asss_handle* h, int tr) {
     }
     k_small_mm<<<cdiv(m * m, 256), 256, 0, s>>>(Sig.p, K.p, m, 0, Z.p);  // Z = Sig K^-1
     ASSS_CHECK_LAUNCH();
+    ASSS_TRY(mrs_collect(c, h->mw, nullptr));
+    mrs_take_totals(h->mw);
     ASSS_TRY(S.Y.alloc((int64_t)n * m));
     k_x_times_small<<<cdiv((int64_t)n * m, 256), 256, 0, s>>>(X.p, Z.p, n, m, S.Y.p);
     ASSS_CHECK_LAUNCH();
+    if (h->opt.precision == ASSS_PREC_MIXED) {
+        ASSS_TRY(S.Y32.alloc((int64_t)n * m));
+        k_d2f<<<cdiv((int64_t)n * m, 256), 256, 0, s>>>(S.Y.p, (int64_t)n * m, S.Y32.p);
+        ASSS_CHECK_LAUNCH();
+    }
     ASSS_CUDA(cudaStreamSynchronize(s));
     S.ready = true;
     return ASSS_OK;
 }
 
 // out = P^-1 u (tr = 0) or P^-T u (tr = 1): z = S_bar^-1 u by mrs, then SMW (Eq. smw)
-static asss_status apply_prec(asss_handle* h, int tr, const double* u, double* out, int* its_out) {
+//   P^-1 u = z - Y (U_bar^T z),  U_bar^T z = [Q_k^T z ; z(neg)]
+// Q_k^T z comes out of the mrs kernel's final pass.  Step counts and timings stay
+// on the device until the solve collects them.
+static asss_status apply_prec(asss_handle* h, int tr, const double* u, double* out) {
     const Ctx& c = h->ctx;
     cudaStream_t s = c.stream;
     int n = h->n;
@@ -560,30 +595,30 @@ static asss_status apply_prec(asss_handle* h, int tr, const double* u, double* o
     bool fp32 = h->opt.precision == ASSS_PREC_MIXED;
     double sign = tr ? -1.0 : 1.0;
     SmwData& S = h->smw[tr];
-    double* z = (S.m > 0) ? h->zt.p : out;
-    MrsResult res;
+    double* qtz = (S.m > 0 && h->k > 0) ? h->wv.p : nullptr;
     if (fp32) {
-        ASSS_TRY(mrs_solve(c, h->mw, op, true, 1.0, sign, u, nullptr, h->z32.p, h->opt.inner_tol, h->opt.inner_maxit,
-                           &res, true));
-        k_f2d<<<cdiv(n, 256), 256, 0, s>>>(h->z32.p, z, n);
-        ASSS_CHECK_LAUNCH();
-    } else {
-        ASSS_TRY(mrs_solve(c, h->mw, op, false, 1.0, sign, u, z, nullptr, h->opt.inner_tol, h->opt.inner_maxit, &res,
-                           true));
-    }
-    h->inner_total += res.its;
-    h->inner_solves += 1;
-    h->inner_ms += res.ms;
-    h->inner_bytes += res.bytes;
-    if (its_out) *its_out = res.its;
-    if (S.m > 0) {
-        if (h->k) ASSS_TRY(gram(h->Qcm.p, n, h->k, z, n, 1, n, h->wv.p, s));
-        if (h->r) {
-            k_gather_neg<<<cdiv(h->r, 128), 128, 0, s>>>(z, h->neg.p, h->r, h->wv.p + h->k);
+        ASSS_TRY(mrs_solve(c, h->mw, op, true, 1.0, sign, u, nullptr, h->z32.p, h->opt.inner_tol,
+                           h->opt.inner_maxit, qtz, nullptr, false));
+        if (h->r && S.m > 0) {
+            k_gather_neg_f<<<cdiv(h->r, 128), 128, 0, s>>>(h->z32.p, h->neg.p, h->r, h->wv.p + h->k);
             ASSS_CHECK_LAUNCH();
         }
-        ASSS_TRY(sub_rowmajor_gemv(S.Y.p, S.m, h->wv.p, z, n, out, s));
+        k_smw_apply_f32<<<cdiv(n, 256), 256, sizeof(double) * (S.m > 0 ? S.m : 1), s>>>(
+            h->z32.p, S.m > 0 ? S.Y32.p : nullptr, S.m, h->wv.p, n, out);
+        ASSS_CHECK_LAUNCH();
+    } else {
+        double* z = (S.m > 0) ? h->zt.p : out;
+        ASSS_TRY(mrs_solve(c, h->mw, op, false, 1.0, sign, u, z, nullptr, h->opt.inner_tol, h->opt.inner_maxit,
+                           qtz, nullptr, false));
+        if (S.m > 0) {
+            if (h->r) {
+                k_gather_neg<<<cdiv(h->r, 128), 128, 0, s>>>(z, h->neg.p, h->r, h->wv.p + h->k);
+                ASSS_CHECK_LAUNCH();
+            }
+            ASSS_TRY(sub_rowmajor_gemv(S.Y.p, S.m, h->wv.p, z, n, out, s));
+        }
     }
+    h->inner_solves += 1;
     return ASSS_OK;
 }
 
@@ -679,7 +714,7 @@ static asss_status tfqmr_cycle(asss_handle* h, KrylovWork& kw, int tr, const dou
     ASSS_CUDA(cudaMemsetAsync(kw.d.p, 0, sizeof(double) * n, s));
     k_tf_init<<<1, 1, 0, s>>>(T, T + TF_WN2);
     ASSS_CHECK_LAUNCH();
-    ASSS_TRY(apply_prec(h, tr, kw.u.p, kw.ut.p, nullptr));
+    ASSS_TRY(apply_prec(h, tr, kw.u.p, kw.ut.p));
     *napp_out += 1;
     ASSS_TRY(apply_op(h, tr, kw.ut.p, kw.v.p));
     ASSS_TRY(vcopy(kw.Bue.p, kw.v.p, n, s));
@@ -695,7 +730,7 @@ static asss_status tfqmr_cycle(asss_handle* h, KrylovWork& kw, int tr, const dou
             } else {
                 k_tf_uminus<<<nb, 256, 0, s>>>(kw.u.p, kw.v.p, T, n);
                 ASSS_CHECK_LAUNCH();
-                ASSS_TRY(apply_prec(h, tr, kw.u.p, kw.ut.p, nullptr));
+                ASSS_TRY(apply_prec(h, tr, kw.u.p, kw.ut.p));
                 *napp_out += 1;
                 ASSS_TRY(apply_op(h, tr, kw.ut.p, kw.Buo.p));
                 Bu = kw.Buo.p;
@@ -725,7 +760,7 @@ static asss_status tfqmr_cycle(asss_handle* h, KrylovWork& kw, int tr, const dou
         ASSS_CHECK_LAUNCH();
         k_tf_unew<<<nb, 256, 0, s>>>(kw.u.p, kw.w.p, T, n);
         ASSS_CHECK_LAUNCH();
-        ASSS_TRY(apply_prec(h, tr, kw.u.p, kw.ut.p, nullptr));
+        ASSS_TRY(apply_prec(h, tr, kw.u.p, kw.ut.p));
         *napp_out += 1;
         ASSS_TRY(apply_op(h, tr, kw.ut.p, kw.Bue.p));
         k_tf_vnew<<<nb, 256, 0, s>>>(kw.v.p, kw.Bue.p, kw.Buo.p, T, n);
@@ -762,7 +797,7 @@ static asss_status fgmres_cycle(asss_handle* h, KrylovWork& kw, int tr, const do
     for (int j = 0; j < m; ++j) {
         double* vj = kw.V.p + (size_t)j * n;
         double* zj = kw.Z.p + (size_t)j * n;
-        ASSS_TRY(apply_prec(h, tr, vj, zj, nullptr));
+        ASSS_TRY(apply_prec(h, tr, vj, zj));
         *napp_out += 1;
         ASSS_TRY(apply_op(h, tr, zj, kw.w.p));
         ASSS_TRY(gram(kw.V.p, n, j + 1, kw.w.p, n, 1, n, kw.hv.p, s));
@@ -806,10 +841,9 @@ static asss_status refine(asss_handle* h, int tr, const double* rhs, double* x, 
     ASSS_TRY(rh.alloc(n));
     ASSS_TRY(dy.alloc(n));
     ASSS_TRY(scal.alloc(2));
-    h->inner_total = 0;
     h->inner_solves = 0;
-    h->inner_ms = 0.0;
-    h->inner_bytes = 0;
+    ASSS_TRY(mrs_collect(h->ctx, h->mw, nullptr));
+    mrs_take_totals(h->mw);
     ASSS_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
     ASSS_TRY(vcopy(r.p, rhs, n, s));
     ASSS_TRY(dot(rhs, rhs, n, scal.p, s));
@@ -879,12 +913,14 @@ static asss_status refine(asss_handle* h, int tr, const double* rhs, double* x, 
         k_sub<<<nb, 256, 0, s>>>(rhs, h->t1.p, r.p, n);
         ASSS_CHECK_LAUNCH();
     }
-    st->inner_its_total = h->inner_total;
-    st->inner_solves = h->inner_solves;
-    st->inner_its_avg = h->inner_solves ? (double)h->inner_total / h->inner_solves : 0.0;
-    st->t_inner_ms = h->inner_ms;
-    st->inner_bytes = h->inner_bytes;
-    st->inner_launches = h->inner_solves;
+    ASSS_TRY(mrs_collect(h->ctx, h->mw, nullptr));
+    MrsTotals t = mrs_take_totals(h->mw);
+    st->inner_its_total = t.its;
+    st->inner_solves = t.launches;
+    st->inner_its_avg = t.launches ? (double)t.its / t.launches : 0.0;
+    st->t_inner_ms = t.ms;
+    st->inner_bytes = t.bytes;
+    st->inner_launches = t.launches;
     return ASSS_OK;
 }
 
@@ -1293,17 +1329,21 @@ asss_status asss_apply_preconditioner(asss_handle* h, int transpose, const doubl
     DBuf<double> vi, vo;
     ASSS_TRY(to_device(vi, u, n, s));
     ASSS_TRY(vo.alloc(n));
-    int its = 0;
-    ASSS_TRY(apply_prec(h, transpose ? 1 : 0, vi.p, vo.p, &its));
+    ASSS_TRY(mrs_collect(h->ctx, h->mw, nullptr));
+    mrs_take_totals(h->mw);
+    ASSS_TRY(apply_prec(h, transpose ? 1 : 0, vi.p, vo.p));
     ASSS_CUDA(cudaMemcpyAsync(out, vo.p, sizeof(double) * n, cudaMemcpyDefault, s));
-    ASSS_CUDA(cudaStreamSynchronize(s));
+    ASSS_TRY(mrs_collect(h->ctx, h->mw, nullptr));
+    MrsTotals t = mrs_take_totals(h->mw);
     if (st) {
         *st = h->setup_stats;
-        st->inner_its_total = its;
-        st->inner_solves = 1;
+        st->inner_its_total = t.its;
+        st->inner_solves = t.launches;
+        st->inner_its_avg = (double)t.its;
+        st->t_inner_ms = t.ms;
+        st->inner_bytes = t.bytes;
+        st->inner_launches = t.launches;
     }
-    h->inner_ms = 0.0;
-    h->inner_bytes = 0;
     return ASSS_OK;
 }
 
@@ -1458,13 +1498,13 @@ asss_status asss_mrs(const asss_csr* J, int k, const double* q, const double* al
     asss_status stt;
     if (fp32) {
         ASSS_TRY(x32.alloc(n));
-        stt = mrs_solve(c, w, op, true, shift, sign, bd.p, nullptr, x32.p, tol, maxit, &res, true);
+        stt = mrs_solve(c, w, op, true, shift, sign, bd.p, nullptr, x32.p, tol, maxit, nullptr, &res, true);
         if (stt == ASSS_OK) {
             k_f2d<<<cdiv(n, 256), 256, 0, s>>>(x32.p, xd.p, n);
             stt = cudaGetLastError() == cudaSuccess ? ASSS_OK : ASSS_ERR_CUDA;
         }
     } else {
-        stt = mrs_solve(c, w, op, false, shift, sign, bd.p, xd.p, nullptr, tol, maxit, &res, true);
+        stt = mrs_solve(c, w, op, false, shift, sign, bd.p, xd.p, nullptr, tol, maxit, nullptr, &res, true);
     }
     mrs_work_destroy(w);
     ASSS_TRY(stt);

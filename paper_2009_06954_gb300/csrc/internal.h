@@ -1,6 +1,8 @@
 // Internal host-side interfaces shared by the library's translation units.
 #pragma once
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace asss {
@@ -60,6 +62,13 @@ struct MrsOperator {
     const double* alpha = nullptr;  // device, k-1 values (S_k superdiagonal)
 };
 
+struct MrsTotals {
+    long long its = 0;     // mrs steps summed over the launches
+    int launches = 0;
+    double ms = 0.0;       // kernel time from CUDA events around each launch
+    long long bytes = 0;   // algorithmic bytes of those launches
+};
+
 struct MrsWork;  // opaque persistent workspace (owned by a handle)
 asss_status mrs_work_create(MrsWork** w, int n, int sms);
 void mrs_work_destroy(MrsWork* w);
@@ -77,9 +86,16 @@ unsigned long long launches();
 // One single-RHS mrs solve (App. B) of (shift I + sign*(J~ - Q S_k Q^T)) x = rhs.
 // fp32: use the FP32 operator and vectors; rhs is FP64 in both cases, x is FP64
 // (x64) or FP32 (x32) - exactly one of them non-null.
+// qtz (optional, k values): Q^T x of the final iterate, reduced inside the kernel.
+// With sync_result false the step count and timing stay on the device until
+// mrs_collect; with true they are read back into *res before returning.
 asss_status mrs_solve(const Ctx& c, MrsWork* w, const MrsOperator& op, bool fp32, double shift, double sign,
-                      const double* rhs, double* x64, float* x32, double tol, int maxit, MrsResult* res,
-                      bool sync_result);
+                      const double* rhs, double* x64, float* x32, double tol, int maxit, double* qtz,
+                      MrsResult* res, bool sync_result);
+// Synchronise the stream, fold every logged launch into the totals and report a
+// timed-out device wait.
+asss_status mrs_collect(const Ctx& c, MrsWork* w, std::vector<MrsResult>* out);
+MrsTotals mrs_take_totals(MrsWork* w);
 
 // lls.cu
 struct LlsResult {

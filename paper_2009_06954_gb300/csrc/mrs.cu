@@ -17,6 +17,8 @@
 // iteration, which keeps the method's one-synchronisation-per-step property (§3.1).
 // Vectors produced by other blocks are read through L2 (ld.global.cg); the grid
 // barrier has a bounded wait.
+#include <vector>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -46,9 +48,21 @@ struct MrsWork {
     int part_nblk = 0;
     int halo32 = -1, halo64 = -1;  // halo of the current Y layout (-1: not laid out)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // deferred statistics: each launch writes its step count and ratio into a log
+    // slot and is bracketed by its own event pair; mrs_collect reads them all at once
+    static constexpr int LOG_CAP = 1024;
+    DBuf<int> its_log;
+    DBuf<double> ratio_log;
+    std::vector<cudaEvent_t> evs;
+    std::vector<long long> log_nnz, log_per_row;  // bytes model per launch
+    int log_n = 0;
+    MrsTotals tot;
+    DBuf<double> qtz_part;   // [KPMAX][maxblk] partials of the fused Q^T x
+    DBuf<unsigned> qtz_done; // last-block counter
     ~MrsWork() {
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
+        for (cudaEvent_t e : evs) cudaEventDestroy(e);
     }
 };
 
@@ -68,6 +82,18 @@ asss_status mrs_work_create(MrsWork** w, int n, int sms) {
     if (cudaEventCreate(&m->ev0) != cudaSuccess || cudaEventCreate(&m->ev1) != cudaSuccess) {
         delete m;
         set_error("cudaEventCreate failed");
+        return ASSS_ERR_CUDA;
+    }
+    if ((st = m->its_log.alloc(MrsWork::LOG_CAP)) != ASSS_OK ||
+        (st = m->ratio_log.alloc(MrsWork::LOG_CAP)) != ASSS_OK ||
+        (st = m->qtz_part.alloc((int64_t)MRS_KPMAX * maxblk)) != ASSS_OK || (st = m->qtz_done.alloc(1)) != ASSS_OK) {
+        delete m;
+        return st;
+    }
+    if (cudaMemset(m->qtz_done.p, 0, sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(m->err.p, 0, sizeof(int)) != cudaSuccess) {
+        delete m;
+        set_error("cudaMemset failed");
         return ASSS_ERR_CUDA;
     }
     *w = m;
@@ -105,6 +131,9 @@ struct MrsParams {
     long long budget;
     int* out_its;
     double* out_ratio;
+    double* qtz;         // optional: Q^T x (k values) computed in the final pass
+    double* qtz_part;    // [KP][nblk] block partials for it
+    unsigned* qtz_done;  // last-block counter (left at 0)
 };
 
 template <class T, int KP>
@@ -145,6 +174,44 @@ struct MrsScalars {
     double ratio;
     int its, stop;
 };
+
+// Q^T x of the final iterate: block partials, then the last block to finish adds
+// them in block order and writes p.qtz (no block waits for another).
+template <class T, int KP>
+__device__ __forceinline__ void qtz_reduce(const MrsParams<T>& p, T (&tacc)[KP + 1], double (&s_wsum)[MRS_WARPS][KP + 1],
+                                           int warp, int lane) {
+    __shared__ int s_last;
+    const int nblk = gridDim.x;
+#pragma unroll
+    for (int v = 1; v <= KP; ++v) {
+        T d = warp_sum(tacc[v]);
+        if (lane == 0) s_wsum[warp][v] = (double)d;
+    }
+    __syncthreads();
+    for (int v = threadIdx.x; v < p.k; v += MRS_THREADS) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < MRS_WARPS; ++w) t += s_wsum[w][1 + v];
+        p.qtz_part[v * nblk + blockIdx.x] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned t = atomicAdd(p.qtz_done, 1u);
+        s_last = (t == (unsigned)nblk - 1);
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        for (int v = warp; v < p.k; v += MRS_WARPS) {
+            double t = 0.0;
+            for (int b = lane; b < nblk; b += 32) t += __ldcg(&p.qtz_part[v * nblk + b]);
+            t = warp_sum(t);
+            if (lane == 0) p.qtz[v] = t;
+        }
+        if (threadIdx.x == 0) atomicExch(p.qtz_done, 0u);
+    }
+}
 
 // FMT 0: SELL-C storage of J~; FMT 1: skew half-diagonal storage
 template <class T, int KP, int FMT>
@@ -248,9 +315,13 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
     }
     __syncthreads();
     if (sc.stop) {  // b = 0: x = 0 already
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            *p.out_its = 0;
-            *p.out_ratio = 0.0;
+        if (blockIdx.x == 0) {
+            if (threadIdx.x == 0) {
+                *p.out_its = 0;
+                *p.out_ratio = 0.0;
+            }
+            if (p.qtz)
+                for (int v = threadIdx.x; v < p.k; v += MRS_THREADS) p.qtz[v] = 0.0;
         }
         return;
     }
@@ -348,12 +419,26 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
             T* Pj = p.P + (size_t)(j & 1) * n;
             const T tn = (T)sc.fin_nu, td = (T)sc.fin_delta, tth = (T)(1.0 / sc.fin_theta),
                     tx = (T)sc.fin_xcoef;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) tacc[v] = (T)0;
             for (int sl = s0 + warp; sl < s1; sl += MRS_WARPS) {
                 int i = sl * 32 + lane;
                 if (i < n) {
                     T pv = (tn * Ycur[i] - td * Pj[i]) * tth;
-                    p.x[i] += tx * pv;
+                    T xi = p.x[i] + tx * pv;
+                    p.x[i] = xi;
+                    if constexpr (KP > 0) {
+                        if (p.qtz) {
+                            T q[KP];
+                            load_qrow<T, KP>(p.Q, i, q);
+#pragma unroll
+                            for (int m = 0; m < KP; ++m) tacc[1 + m] += q[m] * xi;
+                        }
+                    }
                 }
+            }
+            if constexpr (KP > 0) {
+                if (p.qtz) qtz_reduce<T, KP>(p, tacc, s_wsum, warp, lane);
             }
             break;
         }
@@ -410,10 +495,15 @@ struct OpView {
     long long nnz = 0;  // matrix entries one application reads
 };
 
+struct LaunchOut {
+    int slot;
+    double* qtz;
+};
+
 template <class T, int KP, int FMT>
 static asss_status launch_mrs(const Ctx& c, MrsWork* w, const OpView<T>& J, const T* Q, const double* alpha,
                               int k, double shift, double sign, const double* rhs, T* x, T* Y, long long ystride,
-                              T* P, double tol, int maxit) {
+                              T* P, double tol, int maxit, LaunchOut lo) {
     int occ = 0;
     ASSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mrs<T, KP, FMT>, MRS_THREADS, 0));
     if (occ < 1) {
@@ -433,7 +523,6 @@ static asss_status launch_mrs(const Ctx& c, MrsWork* w, const OpView<T>& J, cons
         w->part_nblk = nblk;
     }
     ASSS_CUDA(cudaMemsetAsync(w->bar.p, 0, 2 * sizeof(unsigned), c.stream));
-    ASSS_CUDA(cudaMemsetAsync(w->err.p, 0, sizeof(int), c.stream));
     MrsParams<T> prm;
     prm.n = J.n;
     prm.sptr = J.sptr;
@@ -461,25 +550,28 @@ static asss_status launch_mrs(const Ctx& c, MrsWork* w, const OpView<T>& J, cons
     prm.tol = tol;
     prm.maxit = maxit;
     prm.budget = c.wait_cycles;
-    prm.out_its = w->out_its.p;
-    prm.out_ratio = w->out_ratio.p;
+    prm.out_its = w->its_log.p + lo.slot;
+    prm.out_ratio = w->ratio_log.p + lo.slot;
+    prm.qtz = (KP > 0 && k > 0) ? lo.qtz : nullptr;
+    prm.qtz_part = w->qtz_part.p;
+    prm.qtz_done = w->qtz_done.p;
     void* args[] = {&prm};
-    ASSS_CUDA(cudaEventRecord(w->ev0, c.stream));
+    ASSS_CUDA(cudaEventRecord(w->evs[2 * lo.slot], c.stream));
     ASSS_CUDA(cudaLaunchCooperativeKernel((const void*)k_mrs<T, KP, FMT>, dim3(nblk), dim3(MRS_THREADS), args, 0,
                                           c.stream));
     count_launch();
-    ASSS_CUDA(cudaEventRecord(w->ev1, c.stream));
+    ASSS_CUDA(cudaEventRecord(w->evs[2 * lo.slot + 1], c.stream));
     return ASSS_OK;
 }
 
 template <class T, int FMT>
 static asss_status dispatch_kp(const Ctx& c, MrsWork* w, const OpView<T>& J, const T* Q, const double* alpha, int k,
                                int kp, double shift, double sign, const double* rhs, T* x, T* Y, long long ystride,
-                               T* P, double tol, int maxit) {
+                               T* P, double tol, int maxit, LaunchOut lo) {
     switch (kp) {
 #define ASSS_MRS_CASE(KPV) \
     case KPV:              \
-        return launch_mrs<T, KPV, FMT>(c, w, J, Q, alpha, k, shift, sign, rhs, x, Y, ystride, P, tol, maxit);
+        return launch_mrs<T, KPV, FMT>(c, w, J, Q, alpha, k, shift, sign, rhs, x, Y, ystride, P, tol, maxit, lo);
         ASSS_MRS_CASE(0)
         ASSS_MRS_CASE(4)
         ASSS_MRS_CASE(8)
@@ -515,7 +607,8 @@ static asss_status y_layout(MrsWork* w, DBuf<T>& Ybuf, int& cur, int H, cudaStre
 template <class T>
 static asss_status dispatch_mrs(const Ctx& c, MrsWork* w, const DSell<T>* sell, const DSkewDia<T>* dia, const T* Q,
                                 const double* alpha, int k, int kp, double shift, double sign, const double* rhs,
-                                T* x, DBuf<T>& Ybuf, int& ylay, T* P, double tol, int maxit, long long* nnz_read) {
+                                T* x, DBuf<T>& Ybuf, int& ylay, T* P, double tol, int maxit, long long* nnz_read,
+                                LaunchOut lo) {
     OpView<T> v;
     if (dia && dia->ndiag > MRS_MAXDIAG) dia = nullptr;
     T* Y = nullptr;
@@ -533,7 +626,7 @@ static asss_status dispatch_mrs(const Ctx& c, MrsWork* w, const DSell<T>* sell, 
         v.key = dia;
         v.nnz = dia->nnz;
         *nnz_read = v.nnz;
-        return dispatch_kp<T, 1>(c, w, v, Q, alpha, k, kp, shift, sign, rhs, x, Y, ystride, P, tol, maxit);
+        return dispatch_kp<T, 1>(c, w, v, Q, alpha, k, kp, shift, sign, rhs, x, Y, ystride, P, tol, maxit, lo);
     }
     if (!sell) {
         set_error("mrs: no operator storage");
@@ -548,13 +641,20 @@ static asss_status dispatch_mrs(const Ctx& c, MrsWork* w, const DSell<T>* sell, 
     v.key = sell;
     v.nnz = sell->nnz;
     *nnz_read = v.nnz;
-    return dispatch_kp<T, 0>(c, w, v, Q, alpha, k, kp, shift, sign, rhs, x, Y, ystride, P, tol, maxit);
+    return dispatch_kp<T, 0>(c, w, v, Q, alpha, k, kp, shift, sign, rhs, x, Y, ystride, P, tol, maxit, lo);
 }
 
 asss_status mrs_solve(const Ctx& c, MrsWork* w, const MrsOperator& op, bool fp32, double shift, double sign,
-                      const double* rhs, double* x64, float* x32, double tol, int maxit, MrsResult* res,
+                      const double* rhs, double* x64, float* x32, double tol, int maxit, double* qtz, MrsResult* res,
                       bool sync_result) {
     int n = w->n;
+    if (w->log_n == MrsWork::LOG_CAP) ASSS_TRY(mrs_collect(c, w, nullptr));
+    LaunchOut lo{w->log_n, qtz};
+    while ((int)w->evs.size() < 2 * (lo.slot + 1)) {
+        cudaEvent_t e;
+        ASSS_CUDA(cudaEventCreate(&e));
+        w->evs.push_back(e);
+    }
     long long nnz_read = 0;
     if (fp32) {
         if ((!op.J32 && !op.D32) || !x32) {
@@ -563,7 +663,7 @@ asss_status mrs_solve(const Ctx& c, MrsWork* w, const MrsOperator& op, bool fp32
         }
         if (!w->P32.p) ASSS_TRY(w->P32.alloc((int64_t)2 * n));
         ASSS_TRY(dispatch_mrs<float>(c, w, op.J32, op.D32, op.Q32, op.alpha, op.k, op.kp, shift, sign, rhs, x32,
-                                     w->Y32, w->halo32, w->P32.p, tol, maxit, &nnz_read));
+                                     w->Y32, w->halo32, w->P32.p, tol, maxit, &nnz_read, lo));
     } else {
         if ((!op.J64 && !op.D64) || !x64) {
             set_error("FP64 mrs needs the FP64 operator and an FP64 output");
@@ -571,33 +671,68 @@ asss_status mrs_solve(const Ctx& c, MrsWork* w, const MrsOperator& op, bool fp32
         }
         if (!w->P64.p) ASSS_TRY(w->P64.alloc((int64_t)2 * n));
         ASSS_TRY(dispatch_mrs<double>(c, w, op.J64, op.D64, op.Q64, op.alpha, op.k, op.kp, shift, sign, rhs, x64,
-                                      w->Y64, w->halo64, w->P64.p, tol, maxit, &nnz_read));
+                                      w->Y64, w->halo64, w->P64.p, tol, maxit, &nnz_read, lo));
     }
-    if (sync_result && res) {
-        int herr = 0;
-        ASSS_CUDA(cudaMemcpyAsync(&res->its, w->out_its.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
-        ASSS_CUDA(cudaMemcpyAsync(&res->ratio, w->out_ratio.p, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
-        ASSS_CUDA(cudaMemcpyAsync(&herr, w->err.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
-        ASSS_CUDA(cudaStreamSynchronize(c.stream));
-        res->status = herr;
-        float ms = 0.f;
-        ASSS_CUDA(cudaEventElapsedTime(&ms, w->ev0, w->ev1));
-        res->ms = ms;
-        // algorithmic bytes: set-up pass (rhs in FP64, Y/x/P written, Q row), per iteration
-        // (matrix entries value+index, Q row, gathered/own y, y_old, y_new, p r/w, x r/w),
-        // final pass (y, p, x r/w)
-        long long T = fp32 ? 4 : 8;
-        long long nn = n, kp = op.kp;
-        // SELL entries carry a 4-byte column index; diagonal storage reads values only
-        long long per_entry = (fp32 ? (op.D32 != nullptr) : (op.D64 != nullptr)) ? T : T + 4;
-        res->bytes = nn * (8 + 4 * T + kp * T) +
-                     (long long)res->its * (nnz_read * per_entry + nn * (7 * T + kp * T)) + nn * 4 * T;
-        if (herr) {
-            set_error("mrs: a grid barrier wait exceeded its budget");
-            return (asss_status)herr;
-        }
+    // algorithmic bytes: set-up pass (rhs in FP64, Y/x/P written, Q row), per step
+    // (matrix entries - SELL ones with a 4-byte index -, Q row, gathered/own y,
+    // y_old, y_new, p r/w, x r/w), final pass (y, p, x r/w, and the Q row for Q^T x)
+    long long T = fp32 ? 4 : 8;
+    long long nn = n, kp = op.kp;
+    long long per_entry = (fp32 ? (op.D32 != nullptr) : (op.D64 != nullptr)) ? T : T + 4;
+    if ((int)w->log_nnz.size() <= lo.slot) {
+        w->log_nnz.resize(lo.slot + 1);
+        w->log_per_row.resize(lo.slot + 1);
+    }
+    w->log_nnz[lo.slot] = nn * (8 + 4 * T + kp * T) + nn * 4 * T + ((qtz && op.k) ? nn * kp * T : 0);
+    w->log_per_row[lo.slot] = nnz_read * per_entry + nn * (7 * T + kp * T);
+    w->log_n++;
+    if (sync_result) {
+        std::vector<MrsResult> v;
+        ASSS_TRY(mrs_collect(c, w, &v));
+        if (res) *res = v.back();
     }
     return ASSS_OK;
+}
+
+asss_status mrs_collect(const Ctx& c, MrsWork* w, std::vector<MrsResult>* out) {
+    int nl = w->log_n;
+    if (nl == 0) return ASSS_OK;
+    std::vector<int> its(nl);
+    std::vector<double> ratio(nl);
+    int herr = 0;
+    ASSS_CUDA(cudaMemcpyAsync(its.data(), w->its_log.p, sizeof(int) * nl, cudaMemcpyDeviceToHost, c.stream));
+    ASSS_CUDA(cudaMemcpyAsync(ratio.data(), w->ratio_log.p, sizeof(double) * nl, cudaMemcpyDeviceToHost, c.stream));
+    ASSS_CUDA(cudaMemcpyAsync(&herr, w->err.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    ASSS_CUDA(cudaStreamSynchronize(c.stream));
+    w->log_n = 0;
+    for (int i = 0; i < nl; ++i) {
+        float ms = 0.f;
+        ASSS_CUDA(cudaEventElapsedTime(&ms, w->evs[2 * i], w->evs[2 * i + 1]));
+        MrsResult r;
+        r.its = its[i];
+        r.ratio = ratio[i];
+        r.status = herr;
+        r.ms = ms;
+        r.bytes = w->log_nnz[i] + (long long)its[i] * w->log_per_row[i];
+        w->tot.its += r.its;
+        w->tot.launches += 1;
+        w->tot.ms += r.ms;
+        w->tot.bytes += r.bytes;
+        if (out) out->push_back(r);
+    }
+    if (herr) {
+        // the status word is sticky until read here: later launches exit at once
+        ASSS_CUDA(cudaMemsetAsync(w->err.p, 0, sizeof(int), c.stream));
+        set_error("mrs: a grid barrier wait exceeded its budget");
+        return (asss_status)herr;
+    }
+    return ASSS_OK;
+}
+
+MrsTotals mrs_take_totals(MrsWork* w) {
+    MrsTotals t = w->tot;
+    w->tot = MrsTotals();
+    return t;
 }
 
 }  // namespace asss
