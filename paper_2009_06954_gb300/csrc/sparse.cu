@@ -372,12 +372,14 @@ __global__ void k_spmv(int n, const int* __restrict__ rp, const int* __restrict_
     int gt = blockIdx.x * blockDim.x + threadIdx.x;
     int row = gt / LANES;
     int sub = gt % LANES;
-    if (row >= n) return;
+    // no early exit: every lane of the warp takes part in the shuffles below
+    const bool live = row < n;
     double acc = 0.0;
-    for (int e = rp[row] + sub; e < rp[row + 1]; e += LANES) acc += v[e] * __ldg(&x[ci[e]]);
+    if (live)
+        for (int e = rp[row] + sub; e < rp[row + 1]; e += LANES) acc += v[e] * __ldg(&x[ci[e]]);
 #pragma unroll
     for (int o = LANES / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, LANES);
-    if (sub == 0) y[row] = lscale ? lscale[row] * acc : acc;
+    if (live && sub == 0) y[row] = lscale ? lscale[row] * acc : acc;
 }
 
 asss_status spmv(const DCsr& A, const double* x, double* y, const double* lscale, cudaStream_t s) {
@@ -579,11 +581,11 @@ __global__ void k_sell_width(int n, const int* rp, const int* ci, int skip_diag,
 }
 
 template <class T>
-__global__ void k_sell_fill(int n, const int* rp, const int* ci, const double* v, int skip_diag,
+__global__ void k_sell_fill(int n, int nslices, const int* rp, const int* ci, const double* v, int skip_diag,
                             const int* sptr, int* scol, T* sval) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     int s = r >> 5, lane = r & 31;
-    if (s * 32 >= n + 31) return;
+    if (s >= nslices) return;
     int base = sptr[s], width = (sptr[s + 1] - base) >> 5;
     int kk = 0;
     if (r < n) {
@@ -624,7 +626,7 @@ asss_status build_sell(const DCsr& A, bool skip_diag, DSell<T>& out, cudaStream_
     out.nstored = tot;
     ASSS_TRY(out.col.alloc(tot > 0 ? tot : 1));
     ASSS_TRY(out.val.alloc(tot > 0 ? tot : 1));
-    k_sell_fill<T><<<cdiv((int64_t)ns * 32, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, skip_diag ? 1 : 0,
+    k_sell_fill<T><<<cdiv((int64_t)ns * 32, 256), 256, 0, s>>>(n, ns, A.rp.p, A.ci.p, A.v.p, skip_diag ? 1 : 0,
                                                                out.sptr.p, out.col.p, out.val.p);
     ASSS_CHECK_LAUNCH();
     return ASSS_OK;
