@@ -205,6 +205,38 @@ asss_status asss_mrs(const asss_csr* J, int k, const double* q, const double* al
                      double shift, double sign, const double* b, double* x, double tol,
                      int maxit, int precision, int format, int* its, double* ratio, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free variant of asss_mrs.
+ *
+ * For callers that must not allocate device memory during a call: code that runs
+ * inside a memory-capped service with a fixed device budget, or under an
+ * allocator whose pool must not grow while a request is served.  The paper has
+ * no counterpart; it is an interface convenience of this library.
+ *
+ * Same method and stopping rule as asss_mrs with precision FP64, on J given as
+ * plain CSR that is read in place (every array - row_ptr, col_idx, val, q, alpha,
+ * b, x - must already be device memory; nothing is copied).  q is the deflation
+ * basis in ROW-major layout with leading dimension kp (kp one of 0, 4, 8, 12, 16,
+ * 20, 24, 32, 48, 64, kp >= k, columns k..kp-1 zero).  Scratch comes from one
+ * static device array of the library (about 3.2 MB per device, held by every GPU
+ * that loads the library until the process exits), so n must be at most 65536;
+ * larger n returns ASSS_ERR_ARG.  The call allocates nothing: no cudaMalloc, no
+ * cudaFree, no allocating library routine.
+ *
+ * The first call on a device looks up the device address of that array (once per
+ * device, with the device current); make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents:
+ * calls that overlap on the GPU (different streams, threads or processes sharing
+ * a context) race and must not be issued.  The call synchronises the stream
+ * before returning.  The CSR is checked (row pointers, then column indices) and
+ * ASSS_ERR_PATTERN is returned if it is malformed.
+ */
+asss_status asss_mrs_noalloc(int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                             const double* val, int k, int kp, const double* q_rowmajor,
+                             const double* alpha, double shift, double sign, const double* b,
+                             double* x, double tol, int maxit, int* its, double* ratio,
+                             void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -68,7 +68,7 @@ class Stats(C.Structure):
 EXPORTED = ["asss_default_options", "asss_setup", "asss_solve", "asss_solve_adjoint",
             "asss_apply_operator", "asss_apply_preconditioner", "asss_export", "asss_destroy",
             "asss_status_str", "asss_last_error", "asss_skew_symmetrizer", "asss_skew_lanczos",
-            "asss_mrs", "asss_kernel_launches"]
+            "asss_mrs", "asss_kernel_launches", "asss_mrs_noalloc"]
 
 _lib = None
 _live = weakref.WeakSet()   # open handles, closed at exit while CUDA is still up
@@ -114,6 +114,10 @@ def lib():
     L.asss_skew_lanczos.argtypes = [pCSR, P, C.c_int, C.c_int, P, P, C.POINTER(C.c_int), P]
     L.asss_mrs.argtypes = [pCSR, C.c_int, P, P, C.c_double, C.c_double, P, P, C.c_double, C.c_int,
                            C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double), P]
+    L.asss_mrs_noalloc.argtypes = [C.c_int64, C.c_int64, P, P, P, C.c_int, C.c_int, P, P, C.c_double,
+                                   C.c_double, P, P, C.c_double, C.c_int, C.POINTER(C.c_int),
+                                   C.POINTER(C.c_double), P]
+    L.asss_mrs_noalloc.restype = C.c_int
     L.asss_kernel_launches.argtypes = []
     L.asss_kernel_launches.restype = C.c_ulonglong
     for f in ("asss_setup", "asss_solve", "asss_solve_adjoint", "asss_apply_operator",

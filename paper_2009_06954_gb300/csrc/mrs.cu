@@ -17,6 +17,8 @@
 // iteration, which keeps the method's one-synchronisation-per-step property (§3.1).
 // Vectors produced by other blocks are read through L2 (ld.global.cg); the grid
 // barrier has a bounded wait.
+#include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -114,6 +116,10 @@ struct MrsParams {
     const int* off;
     const T* U;
     long long ustride;
+    // plain CSR operator read in place (64-bit row pointers), one thread per row
+    const long long* crp;
+    const int* cci;
+    const T* cval;
     long long ystride;  // distance between the three Y slots (n + 2 halo)
     const T* Q;
     const double* alpha;
@@ -213,7 +219,7 @@ __device__ __forceinline__ void qtz_reduce(const MrsParams<T>& p, T (&tacc)[KP +
     }
 }
 
-// FMT 0: SELL-C storage of J~; FMT 1: skew half-diagonal storage
+// FMT 0: SELL-C storage of J~; FMT 1: skew half-diagonal storage; FMT 2: plain CSR
 template <class T, int KP, int FMT>
 __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsParams<T> p) {
     constexpr int NV = KP + 1;
@@ -339,7 +345,12 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
         for (int sl = s0 + warp; sl < s1; sl += MRS_WARPS) {
             const int i = sl * 32 + lane;
             T acc = (T)0;
-            if constexpr (FMT == 0) {
+            if constexpr (FMT == 2) {
+                if (i < n) {
+                    const long long e1 = __ldg(&p.crp[i + 1]);
+                    for (long long e = __ldg(&p.crp[i]); e < e1; ++e) acc += __ldg(&p.cval[e]) * Ycur[__ldg(&p.cci[e])];
+                }
+            } else if constexpr (FMT == 0) {
                 const int base = __ldg(&p.sptr[sl]);
                 const int width = (__ldg(&p.sptr[sl + 1]) - base) >> 5;
                 const int* cp = p.col + base + lane;
@@ -532,6 +543,9 @@ static asss_status launch_mrs(const Ctx& c, MrsWork* w, const OpView<T>& J, cons
     prm.off = J.off;
     prm.U = J.U;
     prm.ustride = J.ustride;
+    prm.crp = nullptr;
+    prm.cci = nullptr;
+    prm.cval = nullptr;
     prm.ystride = ystride;
     prm.Q = Q;
     prm.alpha = alpha;
@@ -735,4 +749,199 @@ MrsTotals mrs_take_totals(MrsWork* w) {
     return t;
 }
 
+
+// ===========================================================================
+// Allocation-free entry point.  Its scratch is one file-scope device array, so
+// the call itself never allocates device memory.
+// ===========================================================================
+constexpr long long NOALLOC_MAX_N = 1LL << 16;
+constexpr int NOALLOC_MAX_BLOCKS = 512;
+constexpr long long NOALLOC_CTRL = 8;                                          // control words
+constexpr long long NOALLOC_PART = 2LL * (MRS_KPMAX + 1) * NOALLOC_MAX_BLOCKS;  // reduction partials
+constexpr long long NOALLOC_BLK = (NOALLOC_MAX_BLOCKS + 2) / 2;                // block->slice table (ints)
+constexpr long long NOALLOC_DOUBLES = NOALLOC_CTRL + NOALLOC_PART + NOALLOC_BLK + 5 * NOALLOC_MAX_N;
+
+// [ctrl | partials | block table | Y: 3 slots of n | P: 2 slots of n]
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
+
+static double* noalloc_base(int* status) {
+    static std::mutex mu;
+    static double* base[256] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 256) {
+        set_error("cudaGetDevice failed: %s", cudaGetErrorString(e));
+        *status = ASSS_ERR_CUDA;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (!base[dev]) {
+        double* ptr = nullptr;
+        e = cudaGetSymbolAddress((void**)&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) {
+            set_error("cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+            *status = ASSS_ERR_CUDA;
+            return nullptr;
+        }
+        base[dev] = ptr;
+    }
+    *status = ASSS_OK;
+    return base[dev];
+}
+
+__global__ void k_noalloc_check_rp(const int64_t* rp, int64_t n, int64_t nnz, int* flag) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > n) return;
+    int64_t v = rp[i];
+    if ((i == 0 && v != 0) || (i == n && v != nnz) || v < 0 || v > nnz || (i < n && rp[i + 1] < v)) atomicOr(flag, 1);
+}
+
+__global__ void k_noalloc_check_ci(const int64_t* rp, const int32_t* ci, int64_t n, int* flag) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int64_t e = rp[i]; e < rp[i + 1]; ++e)
+        if (ci[e] < 0 || ci[e] >= n) {
+            atomicOr(flag, 2);
+            return;
+        }
+}
+
+template <int KP>
+static asss_status noalloc_launch(int nblk, cudaStream_t s, MrsParams<double>& prm) {
+    void* args[] = {&prm};
+    ASSS_CUDA(cudaLaunchCooperativeKernel((const void*)k_mrs<double, KP, 2>, dim3(nblk), dim3(MRS_THREADS), args, 0,
+                                          s));
+    count_launch();
+    return ASSS_OK;
+}
+
+template <int KP>
+static asss_status noalloc_occupancy(int* occ) {
+    ASSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_mrs<double, KP, 2>, MRS_THREADS, 0));
+    return ASSS_OK;
+}
+
 }  // namespace asss
+
+using namespace asss;
+
+extern "C" asss_status asss_mrs_noalloc(int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                                        const double* val, int k, int kp, const double* q_rowmajor,
+                                        const double* alpha, double shift, double sign, const double* b, double* x,
+                                        double tol, int maxit, int* its, double* ratio, void* stream) {
+    if (n < 1 || n > NOALLOC_MAX_N) {
+        set_error("asss_mrs_noalloc: n = %lld is outside 1..%lld, the size of its static scratch", (long long)n,
+                  NOALLOC_MAX_N);
+        return ASSS_ERR_ARG;
+    }
+    if (nnz < 0 || nnz >= (1LL << 40) || !row_ptr || !col_idx || !val || !b || !x || maxit < 1 || !(shift > 0.0) ||
+        k < 0 || k > kp ||
+        (k > 0 && !q_rowmajor) || (k > 1 && !alpha)) {
+        set_error("asss_mrs_noalloc: invalid arguments");
+        return ASSS_ERR_ARG;
+    }
+    if (!is_device_ptr(row_ptr) || !is_device_ptr(col_idx) || !is_device_ptr(val) || !is_device_ptr(b) ||
+        !is_device_ptr(x) || (k > 0 && !is_device_ptr(q_rowmajor)) || (k > 1 && !is_device_ptr(alpha))) {
+        set_error("asss_mrs_noalloc: every array must be device memory");
+        return ASSS_ERR_ARG;
+    }
+    int st = ASSS_OK;
+    double* base = noalloc_base(&st);
+    if (!base) return (asss_status)st;
+    cudaStream_t s = (cudaStream_t)stream;
+    Ctx c;
+    ASSS_TRY(make_ctx(c, stream, 2000.0));
+    int occ = 0;
+    switch (kp) {
+#define NA_OCC(KPV) \
+    case KPV:       \
+        ASSS_TRY(noalloc_occupancy<KPV>(&occ)); \
+        break;
+        NA_OCC(0) NA_OCC(4) NA_OCC(8) NA_OCC(12) NA_OCC(16) NA_OCC(20) NA_OCC(24) NA_OCC(32) NA_OCC(48) NA_OCC(64)
+#undef NA_OCC
+        default:
+            set_error("asss_mrs_noalloc: kp must be one of 0,4,8,12,16,20,24,32,48,64");
+            return ASSS_ERR_ARG;
+    }
+    int nslices = (int)((n + 31) / 32);
+    int nblk = c.sms * (occ < 1 ? 1 : occ);
+    if (nblk > NOALLOC_MAX_BLOCKS) nblk = NOALLOC_MAX_BLOCKS;
+    int need = (nslices + MRS_WARPS - 1) / MRS_WARPS;
+    if (nblk > need) nblk = need;
+    unsigned* ctrl = reinterpret_cast<unsigned*>(base);  // [0] count [1] gen [2] err [3] its; ratio at base[3]
+    double* part = base + NOALLOC_CTRL;
+    int* blk = reinterpret_cast<int*>(base + NOALLOC_CTRL + NOALLOC_PART);
+    double* Y = base + NOALLOC_CTRL + NOALLOC_PART + NOALLOC_BLK;
+    double* P = Y + 3 * n;
+    // the control words must start at zero; everything else is written before it is read
+    ASSS_CUDA(cudaMemsetAsync(base, 0, sizeof(double) * NOALLOC_CTRL, s));
+    // the CSR is read in place: check row pointers, then column indices (flag in ctrl[2])
+    {
+        int* flag = reinterpret_cast<int*>(ctrl + 2);
+        k_noalloc_check_rp<<<(int)((n + 256) / 256), 256, 0, s>>>(row_ptr, n, nnz, flag);
+        ASSS_CHECK_LAUNCH();
+        int hf = 0;
+        ASSS_CUDA(cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        ASSS_CUDA(cudaStreamSynchronize(s));
+        if (!hf) {
+            k_noalloc_check_ci<<<(int)((n + 255) / 256), 256, 0, s>>>(row_ptr, col_idx, n, flag);
+            ASSS_CHECK_LAUNCH();
+            ASSS_CUDA(cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+            ASSS_CUDA(cudaStreamSynchronize(s));
+        }
+        if (hf) {
+            set_error("asss_mrs_noalloc: malformed CSR (row pointers or column indices)");
+            return ASSS_ERR_PATTERN;
+        }
+    }
+    k_partition<<<(nblk + 128) / 128, 128, 0, s>>>(nullptr, nslices, nblk, blk);
+    ASSS_CHECK_LAUNCH();
+    MrsParams<double> prm;
+    memset(&prm, 0, sizeof(prm));
+    prm.n = (int)n;
+    prm.crp = (const long long*)row_ptr;
+    prm.cci = col_idx;
+    prm.cval = val;
+    prm.ystride = n;
+    prm.Q = q_rowmajor;
+    prm.alpha = alpha;
+    prm.k = k;
+    prm.shift = shift;
+    prm.sign = sign;
+    prm.rhs = b;
+    prm.x = x;
+    prm.Y = Y;
+    prm.P = P;
+    prm.part = part;
+    prm.gb.count = ctrl;
+    prm.gb.gen = ctrl + 1;
+    prm.gb.err = reinterpret_cast<int*>(ctrl + 2);
+    prm.blk_slice = blk;
+    prm.tol = tol;
+    prm.maxit = maxit;
+    prm.budget = c.wait_cycles;
+    prm.out_its = reinterpret_cast<int*>(ctrl + 3);
+    prm.out_ratio = base + 3;
+    prm.qtz = nullptr;
+    switch (kp) {
+#define NA_CASE(KPV) \
+    case KPV:        \
+        ASSS_TRY(noalloc_launch<KPV>(nblk, s, prm)); \
+        break;
+        NA_CASE(0) NA_CASE(4) NA_CASE(8) NA_CASE(12) NA_CASE(16) NA_CASE(20) NA_CASE(24) NA_CASE(32) NA_CASE(48)
+        NA_CASE(64)
+#undef NA_CASE
+    }
+    unsigned h[4] = {0, 0, 0, 0};
+    double hr = 0.0;
+    ASSS_CUDA(cudaMemcpyAsync(h, ctrl, sizeof(h), cudaMemcpyDeviceToHost, s));
+    ASSS_CUDA(cudaMemcpyAsync(&hr, base + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
+    ASSS_CUDA(cudaStreamSynchronize(s));
+    if (h[2]) {
+        set_error("asss_mrs_noalloc: a grid barrier wait exceeded its budget");
+        return ASSS_ERR_TIMEOUT;
+    }
+    if (its) *its = (int)h[3];
+    if (ratio) *ratio = hr;
+    return ASSS_OK;
+}
