@@ -2,6 +2,8 @@
 // Host code here only orders kernel launches and reads back the scalars that
 // decide control flow (convergence, breakdown); all arithmetic runs on the GPU.
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -365,6 +367,82 @@ __global__ void k_scale_dev(double* y, const double* x, const double* s, int n) 
 // ===========================================================================
 // the handle
 // ===========================================================================
+struct KrylovWork {
+    int n = 0, m = 0;
+    DBuf<double> w, u, ut, v, Bue, Buo, d, rstar;
+    DBuf<double> V, Z, H, cs, sn, g, hv, hv2, y;
+    DBuf<double> T;
+    int outer = -1;
+    // allocates on first use or when the size changes; kept by the handle across solves
+    asss_status init(int n_, int m_, int outer_) {
+        if (n == n_ && m == m_ && outer == outer_) return ASSS_OK;
+        outer = -1;  // marked ready only when every buffer exists
+        ASSS_TRY(T.alloc(32));
+        if (outer_ == ASSS_OUTER_TFQMR) {
+            ASSS_TRY(w.alloc(n));
+            ASSS_TRY(u.alloc(n));
+            ASSS_TRY(ut.alloc(n));
+            ASSS_TRY(v.alloc(n));
+            ASSS_TRY(Bue.alloc(n));
+            ASSS_TRY(Buo.alloc(n));
+            ASSS_TRY(d.alloc(n));
+            ASSS_TRY(rstar.alloc(n));
+        } else {
+            ASSS_TRY(V.alloc((int64_t)n * (m + 1)));
+            ASSS_TRY(Z.alloc((int64_t)n * m));
+            ASSS_TRY(H.alloc((int64_t)(m + 1) * m));
+            ASSS_TRY(cs.alloc(m + 1));
+            ASSS_TRY(sn.alloc(m + 1));
+            ASSS_TRY(g.alloc(m + 2));
+            ASSS_TRY(hv.alloc(m + 1));
+            ASSS_TRY(hv2.alloc(m + 1));
+            ASSS_TRY(y.alloc(m + 1));
+            ASSS_TRY(w.alloc(n));
+        }
+        n = n_;
+        m = m_;
+        outer = outer_;
+        return ASSS_OK;
+    }
+};
+
+// Optional phase timing of a solve (environment variable ASSS_TRACE=1): CUDA
+// events at phase boundaries on the solve's stream, summed and printed to stderr
+// after the solve.  Off by default; no events are recorded then.
+struct Tracer {
+    enum { PREC = 0, OP, ORTH, REFINE, SCALAR, NPH };
+    bool on = false;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> tag;
+    void mark(cudaStream_t s, int t) {
+        if (!on) return;
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        cudaEventRecord(e, s);
+        ev.push_back(e);
+        tag.push_back(t);
+    }
+    void report(cudaStream_t s, int outer_its, long long inner) {
+        if (!on || ev.size() < 2) return;
+        cudaStreamSynchronize(s);
+        double ph[NPH] = {0, 0, 0, 0, 0};
+        for (size_t i = 0; i + 1 < ev.size(); ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+            ph[tag[i]] += ms;
+        }
+        float tot = 0.f;
+        cudaEventElapsedTime(&tot, ev.front(), ev.back());
+        fprintf(stderr,
+                "asss trace: total %.3f ms | preconditioner %.3f | operator %.3f | orthogonalisation %.3f | "
+                "refinement %.3f | scalars+readback %.3f | outer its %d, inner its %lld\n",
+                tot, ph[PREC], ph[OP], ph[ORTH], ph[REFINE], ph[SCALAR], outer_its, inner);
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        ev.clear();
+        tag.clear();
+    }
+};
+
 struct SmwData {
     bool ready = false;
     int m = 0;
@@ -406,11 +484,12 @@ struct asss_handle {
     // work vectors
     DBuf<double> t1, t2, t3, zt, wv, scal;
     DBuf<float> z32;
+    // per-solve work buffers, allocated once
+    KrylovWork kw;
+    Tracer tr;
+    DBuf<double> rr, rh, dy, rscal, bb, xx;
     // statistics of the current solve
-    long long inner_total = 0;
     int inner_solves = 0;
-    double inner_ms = 0.0;
-    long long inner_bytes = 0;
     asss_stats setup_stats;
     ~asss_handle() {
         if (mw) mrs_work_destroy(mw);
@@ -659,39 +738,7 @@ static double read_scalar(const double* d, cudaStream_t s, asss_status* st) {
 // ---------------------------------------------------------------------------
 // one TFQMR run (Freund 1993), right preconditioned, from zero: op(M^-1 u) = r
 // ---------------------------------------------------------------------------
-struct KrylovWork {
-    int n = 0, m = 0;
-    DBuf<double> w, u, ut, v, Bue, Buo, d, rstar;
-    DBuf<double> V, Z, H, cs, sn, g, hv, hv2, y;
-    DBuf<double> T;
-    asss_status init(int n_, int m_, int outer) {
-        n = n_;
-        m = m_;
-        ASSS_TRY(T.alloc(32));
-        if (outer == ASSS_OUTER_TFQMR) {
-            ASSS_TRY(w.alloc(n));
-            ASSS_TRY(u.alloc(n));
-            ASSS_TRY(ut.alloc(n));
-            ASSS_TRY(v.alloc(n));
-            ASSS_TRY(Bue.alloc(n));
-            ASSS_TRY(Buo.alloc(n));
-            ASSS_TRY(d.alloc(n));
-            ASSS_TRY(rstar.alloc(n));
-        } else {
-            ASSS_TRY(V.alloc((int64_t)n * (m + 1)));
-            ASSS_TRY(Z.alloc((int64_t)n * m));
-            ASSS_TRY(H.alloc((int64_t)(m + 1) * m));
-            ASSS_TRY(cs.alloc(m + 1));
-            ASSS_TRY(sn.alloc(m + 1));
-            ASSS_TRY(g.alloc(m + 2));
-            ASSS_TRY(hv.alloc(m + 1));
-            ASSS_TRY(hv2.alloc(m + 1));
-            ASSS_TRY(y.alloc(m + 1));
-            ASSS_TRY(w.alloc(n));
-        }
-        return ASSS_OK;
-    }
-};
+
 
 static asss_status tfqmr_cycle(asss_handle* h, KrylovWork& kw, int tr, const double* r, double eta, int max_steps,
                                double* delta, int* steps_out, int* napp_out) {
@@ -797,9 +844,12 @@ static asss_status fgmres_cycle(asss_handle* h, KrylovWork& kw, int tr, const do
     for (int j = 0; j < m; ++j) {
         double* vj = kw.V.p + (size_t)j * n;
         double* zj = kw.Z.p + (size_t)j * n;
+        h->tr.mark(s, Tracer::PREC);
         ASSS_TRY(apply_prec(h, tr, vj, zj));
         *napp_out += 1;
+        h->tr.mark(s, Tracer::OP);
         ASSS_TRY(apply_op(h, tr, zj, kw.w.p));
+        h->tr.mark(s, Tracer::ORTH);
         ASSS_TRY(gram(kw.V.p, n, j + 1, kw.w.p, n, 1, n, kw.hv.p, s));
         k_sub_colmajor<<<cdiv(n, 256), 256, 0, s>>>(kw.V.p, n, j + 1, kw.hv.p, n, kw.w.p);
         ASSS_CHECK_LAUNCH();
@@ -807,6 +857,7 @@ static asss_status fgmres_cycle(asss_handle* h, KrylovWork& kw, int tr, const do
         k_sub_colmajor<<<cdiv(n, 256), 256, 0, s>>>(kw.V.p, n, j + 1, kw.hv2.p, n, kw.w.p);
         ASSS_CHECK_LAUNCH();
         ASSS_TRY(dot(kw.w.p, kw.w.p, n, T + 2, s));
+        h->tr.mark(s, Tracer::SCALAR);
         k_fg_column<<<1, 1, 0, s>>>(kw.H.p, kw.cs.p, kw.sn.p, kw.g.p, kw.hv.p, kw.hv2.p, T + 2, j, M, T + 3);
         ASSS_CHECK_LAUNCH();
         steps = j + 1;
@@ -834,13 +885,18 @@ static asss_status refine(asss_handle* h, int tr, const double* rhs, double* x, 
     int nb = cdiv(n, 256);
     const asss_options& o = h->opt;
     asss_status es = ASSS_OK;
-    KrylovWork kw;
+    KrylovWork& kw = h->kw;
     ASSS_TRY(kw.init(n, o.restart > 0 ? o.restart : 60, o.outer));
-    DBuf<double> r, rh, dy, scal;
-    ASSS_TRY(r.alloc(n));
-    ASSS_TRY(rh.alloc(n));
-    ASSS_TRY(dy.alloc(n));
-    ASSS_TRY(scal.alloc(2));
+    if (!h->rr.p) {
+        ASSS_TRY(h->rr.alloc(n));
+        ASSS_TRY(h->rh.alloc(n));
+        ASSS_TRY(h->dy.alloc(n));
+        ASSS_TRY(h->rscal.alloc(2));
+    }
+    DBuf<double>& r = h->rr;
+    DBuf<double>& rh = h->rh;
+    DBuf<double>& dy = h->dy;
+    DBuf<double>& scal = h->rscal;
     h->inner_solves = 0;
     ASSS_TRY(mrs_collect(h->ctx, h->mw, nullptr));
     mrs_take_totals(h->mw);
@@ -858,7 +914,9 @@ static asss_status refine(asss_handle* h, int tr, const double* rhs, double* x, 
     double best = INFINITY;
     int stall = 0;
     int* perm = h->has_perm ? h->perm.p : nullptr;
+    h->tr.on = getenv("ASSS_TRACE") != nullptr;
     while (true) {
+        h->tr.mark(s, Tracer::REFINE);
         ASSS_TRY(dot(r.p, r.p, n, scal.p, s));
         double rn = sqrt(read_scalar(scal.p, s, &es));
         ASSS_TRY(es);
@@ -899,6 +957,7 @@ static asss_status refine(asss_handle* h, int tr, const double* rhs, double* x, 
         }
         st->outer_its += steps;
         st->cycles += 1;
+        h->tr.mark(s, Tracer::REFINE);
         if (!tr) {
             ASSS_TRY(vmul(h->t1.p, h->w.p, dy.p, n, s));  // x += D_c S W dy
             ASSS_TRY(spmv(h->S, h->t1.p, h->t2.p, nullptr, s));
@@ -913,8 +972,10 @@ static asss_status refine(asss_handle* h, int tr, const double* rhs, double* x, 
         k_sub<<<nb, 256, 0, s>>>(rhs, h->t1.p, r.p, n);
         ASSS_CHECK_LAUNCH();
     }
+    h->tr.mark(s, Tracer::REFINE);
     ASSS_TRY(mrs_collect(h->ctx, h->mw, nullptr));
     MrsTotals t = mrs_take_totals(h->mw);
+    h->tr.report(s, st->outer_its, t.its);
     st->inner_its_total = t.its;
     st->inner_solves = t.launches;
     st->inner_its_avg = t.launches ? (double)t.its / t.launches : 0.0;
@@ -1246,9 +1307,13 @@ static asss_status solve_common(asss_handle* h, int tr, int nrhs, const double* 
     int n = h->n;
     auto t0 = std::chrono::steady_clock::now();
     bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
-    DBuf<double> bb, xx, xf, dAd;
-    ASSS_TRY(bb.alloc(n));
-    ASSS_TRY(xx.alloc(n));
+    DBuf<double> xf, dAd;
+    if (!h->bb.p) {
+        ASSS_TRY(h->bb.alloc(n));
+        ASSS_TRY(h->xx.alloc(n));
+    }
+    DBuf<double>& bb = h->bb;
+    DBuf<double>& xx = h->xx;
     asss_stats lst = h->setup_stats;
     asss_status worst = ASSS_OK;
     for (int j = 0; j < nrhs; ++j) {

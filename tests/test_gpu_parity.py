@@ -313,3 +313,52 @@ def test_solver_storage_formats_agree(pkg, precision):
         s.close()
     assert abs(res["sell"][1]["outer_its"] - res["diag"][1]["outer_its"]) <= 1
     assert np.linalg.norm(res["sell"][0] - res["diag"][0]) <= 1e-7 * np.linalg.norm(res["sell"][0])
+
+
+# ----------------------------------------------------------------------------
+# failure detection: a device wait that runs out is reported, the context survives
+# ----------------------------------------------------------------------------
+def test_device_wait_timeout_is_reported_and_context_survives(pkg):
+    A, b, _ = dissipative_hamiltonian_3d(side=12, seed=3)
+    # a budget of ~1 ns: the first block to reach a grid barrier gives up at once
+    with pytest.raises(pkg.AsssError) as e:
+        pkg.Solver(A, precision="mixed", outer="fgmres", inner_tol=1e-6, wait_timeout_ms=1e-6)
+    assert e.value.status == 8
+    s = pkg.Solver(A, precision="mixed", outer="fgmres", inner_tol=1e-6)
+    x, st = s.solve(b)
+    assert st["status"] == 0 and np.linalg.norm(b - A @ x) <= 1e-8 * np.linalg.norm(b)
+
+
+# ----------------------------------------------------------------------------
+# the benchmark's configuration at full size (n = 10^6): properties that hold at
+# any size, checked on the CPU from the oracle's definitions
+# ----------------------------------------------------------------------------
+@pytest.mark.slow
+def test_full_size_dh100_properties(pkg):
+    A, b, _ = dissipative_hamiltonian_3d(side=100, seed=1)
+    n = A.shape[0]
+    s = pkg.Solver(A, precision="mixed", outer="fgmres", inner_tol=1e-6, outer_tol=1e-8, k=20)
+    x, st = s.solve(b)
+    assert st["status"] == 0
+    assert np.linalg.norm(b - A @ x) <= 1e-8 * np.linalg.norm(b)
+    ex = s.export(A.nnz)
+    Abar, dr, dc, _ = O.equilibrate(A)
+    np.testing.assert_allclose(ex["dr"], dr, rtol=1e-15)
+    np.testing.assert_allclose(ex["dc"], dc, rtol=1e-15)
+    S = sp.csr_matrix((ex["s_val"], Abar.indices, Abar.indptr), shape=A.shape)
+    # d_i = (Abar S)_ii on sampled rows and W = |d|^-1/2 (§3, 1x1 pivots)
+    rng = np.random.default_rng(0)
+    rows = rng.choice(n, 2000, replace=False)
+    ST = S.T.tocsr()
+    d_ref = np.array([Abar[i].multiply(ST[i]).sum() for i in rows])
+    np.testing.assert_allclose(ex["d"][rows], d_ref, rtol=1e-12)
+    np.testing.assert_allclose(ex["w"], 1.0 / np.sqrt(np.abs(ex["d"])), rtol=1e-14)
+    # the LLS minimiser: normal-equation gradient vanishes relative to B^T v (§2, App. A)
+    B, v, _ = O.lls_system(Abar, S, 1.0)
+    g = B.T @ (v - B @ ex["s_val"])
+    assert np.linalg.norm(g) <= 1e-10 * np.linalg.norm(B.T @ v)
+    # skew-Lanczos relations on the J~ built from the definition (§3.2)
+    Jt = O.inner_skew_operator(Abar, S, ex["w"])
+    Q = ex["Q"]
+    np.testing.assert_allclose(Q.T @ Q, np.eye(Q.shape[1]), atol=1e-10)
+    np.testing.assert_allclose(Q.T @ (Jt @ Q), O.lanczos_tridiagonal(ex["alpha"]), atol=1e-8)
