@@ -379,25 +379,25 @@ struct KrylovWork {
         outer = -1;  // marked ready only when every buffer exists
         ASSS_TRY(T.alloc(32));
         if (outer_ == ASSS_OUTER_TFQMR) {
-            ASSS_TRY(w.alloc(n));
-            ASSS_TRY(u.alloc(n));
-            ASSS_TRY(ut.alloc(n));
-            ASSS_TRY(v.alloc(n));
-            ASSS_TRY(Bue.alloc(n));
-            ASSS_TRY(Buo.alloc(n));
-            ASSS_TRY(d.alloc(n));
-            ASSS_TRY(rstar.alloc(n));
+            ASSS_TRY(w.alloc(n_));
+            ASSS_TRY(u.alloc(n_));
+            ASSS_TRY(ut.alloc(n_));
+            ASSS_TRY(v.alloc(n_));
+            ASSS_TRY(Bue.alloc(n_));
+            ASSS_TRY(Buo.alloc(n_));
+            ASSS_TRY(d.alloc(n_));
+            ASSS_TRY(rstar.alloc(n_));
         } else {
-            ASSS_TRY(V.alloc((int64_t)n * (m + 1)));
-            ASSS_TRY(Z.alloc((int64_t)n * m));
-            ASSS_TRY(H.alloc((int64_t)(m + 1) * m));
-            ASSS_TRY(cs.alloc(m + 1));
-            ASSS_TRY(sn.alloc(m + 1));
-            ASSS_TRY(g.alloc(m + 2));
-            ASSS_TRY(hv.alloc(m + 1));
-            ASSS_TRY(hv2.alloc(m + 1));
-            ASSS_TRY(y.alloc(m + 1));
-            ASSS_TRY(w.alloc(n));
+            ASSS_TRY(V.alloc((int64_t)n_ * (m_ + 1)));
+            ASSS_TRY(Z.alloc((int64_t)n_ * m_));
+            ASSS_TRY(H.alloc((int64_t)(m_ + 1) * m_));
+            ASSS_TRY(cs.alloc(m_ + 1));
+            ASSS_TRY(sn.alloc(m_ + 1));
+            ASSS_TRY(g.alloc(m_ + 2));
+            ASSS_TRY(hv.alloc(m_ + 1));
+            ASSS_TRY(hv2.alloc(m_ + 1));
+            ASSS_TRY(y.alloc(m_ + 1));
+            ASSS_TRY(w.alloc(n_));
         }
         n = n_;
         m = m_;
@@ -887,6 +887,10 @@ static asss_status refine(asss_handle* h, int tr, const double* rhs, double* x, 
     asss_status es = ASSS_OK;
     KrylovWork& kw = h->kw;
     ASSS_TRY(kw.init(n, o.restart > 0 ? o.restart : 60, o.outer));
+    if (kw.n != n || kw.outer != o.outer || !kw.w.p) {
+        set_error("internal: Krylov workspace not allocated");
+        return ASSS_ERR_CUDA;
+    }
     if (!h->rr.p) {
         ASSS_TRY(h->rr.alloc(n));
         ASSS_TRY(h->rh.alloc(n));
