@@ -303,10 +303,7 @@ def main():
     peak, peak_kind = _peaks()
     achieved = inner_bytes / (inner_ms / 1000.0) / 1e9 if inner_ms > 0 else 0.0
     tr = _traffic_record()
-    traffic = None
-    if tr is not None and inner_launches:
-        traffic = tr["dram_bytes_per_iteration"] * (sum(s_["inner_its_total"] for s_ in stats) / inner_launches) \
-            if "dram_bytes_per_iteration" in tr else None
+    traffic = tr.get("dram_bytes_per_launch") if tr is not None else None
 
     if rank != 0:
         if dist:
