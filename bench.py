@@ -194,6 +194,8 @@ def main():
     ap.add_argument("--cpu-worker", action="store_true")
     ap.add_argument("--budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--q-storage", default="f32", choices=["f32", "bf16"],
+                    help="storage of the Lanczos basis read by the FP32 inner solve")
     args = ap.parse_args()
 
     if args.cpu_worker:
@@ -240,7 +242,7 @@ def main():
     n = A.shape[0]
     t0 = time.perf_counter()
     solver = pkg.Solver(A, precision="mixed", outer="fgmres", inner_tol=1e-6, outer_tol=1e-8, k=20,
-                        stream=stream.cuda_stream)
+                        q_bf16=args.q_storage == "bf16", stream=stream.cuda_stream)
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
     rhs_h = _make_rhs(parts, n, 1 + rank, 4)
@@ -327,7 +329,7 @@ def main():
                    "setup_s": round(t_setup, 3), "lls_its": solver.setup_stats["lls_its"],
                    "outer_its": stats[-1]["outer_its"], "inner_its_avg": round(stats[-1]["inner_its_avg"], 2),
                    "max_relres": relres, "converged": ok, "r": solver.setup_stats["r"],
-                   "k_eff": solver.setup_stats["k_eff"]},
+                   "k_eff": solver.setup_stats["k_eff"], "q_storage": args.q_storage},
         "gpu_launches": int(launches),
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
         "roofline": {"bound": "hbm", "kernel": "k_mrs<float,20> (persistent mrs)", "achieved": achieved,

@@ -95,6 +95,10 @@ typedef struct {
                                  at most 64 positive offsets filling >= 50% of them, else SELL-C),
                                  ASSS_FORMAT_SELL, ASSS_FORMAT_DIAG (fails with UNSUPPORTED if J~
                                  does not qualify)                                              */
+    int    q_bf16;            /* mixed precision only: round the Lanczos basis Q_k to BF16 values
+                                 and use those rounded values everywhere (set-up SMW data and the
+                                 FP32 inner solve, which then reads Q_k in BF16); P is unchanged,
+                                 the deflation slightly less sharp                              */
 } asss_options;
 
 enum { ASSS_FORMAT_AUTO = 0, ASSS_FORMAT_SELL = 1, ASSS_FORMAT_DIAG = 2 };

@@ -47,7 +47,7 @@ class Options(C.Structure):
                 ("restart", C.c_int), ("precision", C.c_int), ("outer", C.c_int), ("r_max", C.c_int),
                 ("seed", C.c_uint64), ("lls_tol", C.c_double), ("lls_maxit", C.c_int),
                 ("zero_tol", C.c_double), ("wait_timeout_ms", C.c_double), ("stream", C.c_void_p),
-                ("inner_format", C.c_int)]
+                ("inner_format", C.c_int), ("q_bf16", C.c_int)]
 
 FORMATS = {"auto": 0, "sell": 1, "diag": 2}
 
@@ -217,7 +217,7 @@ def _options(keep, **kw):
     for key, val in kw.items():
         if val is None:
             continue
-        if key == "reorth":
+        if key in ("reorth", "q_bf16"):
             val = int(bool(val))
         setattr(o, key, val)
     return o

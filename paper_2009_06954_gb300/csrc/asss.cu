@@ -8,6 +8,8 @@
 #include <cstring>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -125,6 +127,18 @@ __global__ void k_scale_cols(const int* rp, const int* ci, double* v, const doub
 __global__ void k_f2d(const float* a, double* b, int n) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) b[i] = (double)a[i];
+}
+// round to the nearest BF16 value, kept in FP64 (the rounded basis is used everywhere)
+__global__ void k_round_bf16(double* a, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = (double)__bfloat162float(__double2bfloat16(a[i]));
+}
+// col-major FP64 n x p -> row-major BF16 n x kp (zero padded)
+__global__ void k_to_rowmajor_bf16(const double* A, int lda, int p, int n, int kp, __nv_bfloat16* out) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * kp) return;
+    int i = (int)(t / kp), a = (int)(t % kp);
+    out[t] = __double2bfloat16(a < p ? A[(size_t)a * lda + i] : 0.0);
 }
 __global__ void k_gather_neg_f(const float* z, const int* neg, int r, double* out) {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
@@ -477,6 +491,8 @@ struct asss_handle {
     DBuf<double> Qcm;   // n x k column-major
     DBuf<double> Q64;   // n x kp row-major
     DBuf<float> Q32;
+    DBuf<__nv_bfloat16> Q16;  // n x kp16 row-major (q_bf16)
+    int kp16 = 0;
     DBuf<double> alpha_d;
     std::vector<double> alpha_h;
     SmwData smw[2];
@@ -517,6 +533,7 @@ static void fill_defaults(asss_options* o) {
     o->wait_timeout_ms = 2000.0;
     o->stream = nullptr;
     o->inner_format = ASSS_FORMAT_AUTO;
+    o->q_bf16 = 0;
 }
 
 static int pick_kp(int k) {
@@ -670,6 +687,8 @@ static asss_status apply_prec(asss_handle* h, int tr, const double* u, double* o
     op.kp = h->kp;
     op.Q64 = h->Q64.p;
     op.Q32 = h->Q32.p;
+    op.Q16 = h->Q16.p;
+    op.kp16 = h->kp16;
     op.alpha = h->alpha_d.p;
     bool fp32 = h->opt.precision == ASSS_PREC_MIXED;
     double sign = tr ? -1.0 : 1.0;
@@ -1208,10 +1227,21 @@ static asss_status do_setup(asss_handle* h, const asss_csr* Ain, asss_stats* st)
     }
     if (h->k > 1) ASSS_TRY(to_device(h->alpha_d, h->alpha_h.data(), (int64_t)h->alpha_h.size(), s));
     else ASSS_TRY(h->alpha_d.alloc(1));
+    bool qb = o.q_bf16 && o.precision == ASSS_PREC_MIXED && h->k > 0;
+    if (qb) {
+        // Q' = bf16(Q): every later use (SMW set-up in FP64, U^T z, the inner kernel) sees Q'
+        k_round_bf16<<<cdiv((int64_t)n * h->k, 256), 256, 0, s>>>(h->Qcm.p, (int64_t)n * h->k);
+        ASSS_CHECK_LAUNCH();
+        h->kp16 = (h->k + 7) / 8 * 8;
+        if (h->kp16 == 40 || h->kp16 == 56) h->kp16 += 8;
+        ASSS_TRY(h->Q16.alloc((int64_t)n * h->kp16));
+        k_to_rowmajor_bf16<<<cdiv((int64_t)n * h->kp16, 256), 256, 0, s>>>(h->Qcm.p, n, h->k, n, h->kp16, h->Q16.p);
+        ASSS_CHECK_LAUNCH();
+    }
     if (h->kp) {
         ASSS_TRY(h->Q64.alloc((int64_t)n * h->kp));
         ASSS_TRY(to_rowmajor(h->Qcm.p, n, h->k, n, h->kp, h->Q64.p, s));
-        if (o.precision == ASSS_PREC_MIXED) {
+        if (o.precision == ASSS_PREC_MIXED && !qb) {
             ASSS_TRY(h->Q32.alloc((int64_t)n * h->kp));
             ASSS_TRY(to_rowmajor_f(h->Qcm.p, n, h->k, n, h->kp, h->Q32.p, s));
         }

@@ -59,6 +59,8 @@ struct MrsOperator {
     int k = 0, kp = 0;           // Lanczos vectors and padded row stride
     const double* Q64 = nullptr; // n x kp row-major
     const float* Q32 = nullptr;
+    const void* Q16 = nullptr;   // BF16 n x kp16 row-major (FP32 solve only); used instead of Q32 when set
+    int kp16 = 0;
     const double* alpha = nullptr;  // device, k-1 values (S_k superdiagonal)
 };
 

@@ -21,6 +21,8 @@
 #include <mutex>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -122,6 +124,7 @@ struct MrsParams {
     const T* cval;
     long long ystride;  // distance between the three Y slots (n + 2 halo)
     const T* Q;
+    const __nv_bfloat16* Q16;  // BF16 copy of Q (row stride KP) when the kernel reads Q in BF16
     const double* alpha;
     int k;
     double shift, sign;
@@ -141,6 +144,25 @@ struct MrsParams {
     double* qtz_part;    // [KP][nblk] block partials for it
     unsigned* qtz_done;  // last-block counter (left at 0)
 };
+
+// BF16 rows: KP a multiple of 8, 16-byte aligned, converted to T on load
+template <class T, int KP>
+__device__ __forceinline__ void load_qrow16(const __nv_bfloat16* __restrict__ Q, int i, T (&q)[KP > 0 ? KP : 1]) {
+    if constexpr (KP > 0) {
+        const __nv_bfloat16* row = Q + (size_t)i * KP;
+#pragma unroll
+        for (int m = 0; m < KP; m += 8) {
+            uint4 v = *reinterpret_cast<const uint4*>(row + m);
+            const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                float2 f = __bfloat1622float2(h[t]);
+                q[m + 2 * t] = (T)f.x;
+                q[m + 2 * t + 1] = (T)f.y;
+            }
+        }
+    }
+}
 
 template <class T, int KP>
 __device__ __forceinline__ void load_qrow(const T* __restrict__ Q, int i, T (&q)[KP > 0 ? KP : 1]) {
@@ -167,6 +189,19 @@ __device__ __forceinline__ void load_qrow(const T* __restrict__ Q, int i, T (&q)
             for (int m = 0; m < KP; ++m) q[m] = row[m];
         }
     }
+}
+
+// Error-free FP32 pair ("double-float") addition: TwoSum of the leading parts, the
+// trailing parts added to the error, renormalised.  About 44 significant bits, so
+// the FP32 solve's cross-block sums stay accurate without the (slow) FP64 pipe.
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+    float s = a.x + b.x;
+    float bb = s - a.x;
+    float e = (a.x - (s - bb)) + (b.x - bb);
+    e += a.y + b.y;
+    float hi = s + e;
+    float lo = e - (hi - s);
+    return make_float2(hi, lo);
 }
 
 // Scalar state of the recurrence, kept in shared memory and advanced by one
@@ -220,7 +255,7 @@ __device__ __forceinline__ void qtz_reduce(const MrsParams<T>& p, T (&tacc)[KP +
 }
 
 // FMT 0: SELL-C storage of J~; FMT 1: skew half-diagonal storage; FMT 2: plain CSR
-template <class T, int KP, int FMT>
+template <class T, int KP, int FMT, bool QB = false>
 __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsParams<T> p) {
     constexpr int NV = KP + 1;
     __shared__ double s_wsum[MRS_WARPS][NV];
@@ -250,15 +285,36 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
             double t = 0.0;
 #pragma unroll
             for (int w = 0; w < MRS_WARPS; ++w) t += s_wsum[w][v];
-            buf[v * nblk + blockIdx.x] = t;
+            if constexpr (sizeof(T) == 4) {
+                // block partial as a float pair (hi, lo) in the same 8 bytes
+                float hi = (float)t;
+                float lo = (float)(t - (double)hi);
+                reinterpret_cast<float2*>(buf)[v * nblk + blockIdx.x] = make_float2(hi, lo);
+            } else {
+                buf[v * nblk + blockIdx.x] = t;
+            }
         }
     };
     auto reduce_all = [&](const double* buf) {
         for (int v = warp; v < NV; v += MRS_WARPS) {
-            double t = 0.0;
-            for (int b = lane; b < nblk; b += 32) t += __ldcg(&buf[v * nblk + b]);
-            t = warp_sum(t);
-            if (lane == 0) s_red[v] = t;
+            if constexpr (sizeof(T) == 4) {
+                const float2* b2 = reinterpret_cast<const float2*>(buf) + (size_t)v * nblk;
+                float2 acc = make_float2(0.f, 0.f);
+                for (int b = lane; b < nblk; b += 32) acc = df_add(acc, __ldcg(&b2[b]));
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    float2 other;
+                    other.x = __shfl_xor_sync(0xffffffffu, acc.x, o);
+                    other.y = __shfl_xor_sync(0xffffffffu, acc.y, o);
+                    acc = df_add(acc, other);
+                }
+                if (lane == 0) s_red[v] = (double)acc.x + (double)acc.y;
+            } else {
+                double t = 0.0;
+                for (int b = lane; b < nblk; b += 32) t += __ldcg(&buf[v * nblk + b]);
+                t = warp_sum(t);
+                if (lane == 0) s_red[v] = t;
+            }
         }
         __syncthreads();
     };
@@ -291,7 +347,8 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
             p.P[n + i] = (T)0;
             tacc[0] += b * b;
             T q[KP > 0 ? KP : 1];
-            load_qrow<T, KP>(p.Q, i, q);
+            if constexpr (QB) load_qrow16<T, KP>(p.Q16, i, q);
+            else load_qrow<T, KP>(p.Q, i, q);
 #pragma unroll
             for (int m = 0; m < KP; ++m) tacc[1 + m] += q[m] * b;
         }
@@ -373,7 +430,8 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
             if (i < n) {
                 T yold = (j >= 2) ? Yold[i] : (T)0;
                 T q[KP > 0 ? KP : 1];
-                load_qrow<T, KP>(p.Q, i, q);
+                if constexpr (QB) load_qrow16<T, KP>(p.Q16, i, q);
+                else load_qrow<T, KP>(p.Q, i, q);
                 T dq = (T)0;
 #pragma unroll
                 for (int m = 0; m < KP; ++m) dq += q[m] * s_u[m];
@@ -441,7 +499,8 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
                     if constexpr (KP > 0) {
                         if (p.qtz) {
                             T q[KP];
-                            load_qrow<T, KP>(p.Q, i, q);
+                            if constexpr (QB) load_qrow16<T, KP>(p.Q16, i, q);
+                            else load_qrow<T, KP>(p.Q, i, q);
 #pragma unroll
                             for (int m = 0; m < KP; ++m) tacc[1 + m] += q[m] * xi;
                         }
@@ -511,12 +570,12 @@ struct LaunchOut {
     double* qtz;
 };
 
-template <class T, int KP, int FMT>
+template <class T, int KP, int FMT, bool QB = false>
 static asss_status launch_mrs(const Ctx& c, MrsWork* w, const OpView<T>& J, const T* Q, const double* alpha,
                               int k, double shift, double sign, const double* rhs, T* x, T* Y, long long ystride,
-                              T* P, double tol, int maxit, LaunchOut lo) {
+                              T* P, double tol, int maxit, LaunchOut lo, const __nv_bfloat16* Q16 = nullptr) {
     int occ = 0;
-    ASSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mrs<T, KP, FMT>, MRS_THREADS, 0));
+    ASSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mrs<T, KP, FMT, QB>, MRS_THREADS, 0));
     if (occ < 1) {
         set_error("mrs kernel cannot be resident");
         return ASSS_ERR_CUDA;
@@ -548,6 +607,7 @@ static asss_status launch_mrs(const Ctx& c, MrsWork* w, const OpView<T>& J, cons
     prm.cval = nullptr;
     prm.ystride = ystride;
     prm.Q = Q;
+    prm.Q16 = Q16;
     prm.alpha = alpha;
     prm.k = k;
     prm.shift = shift;
@@ -571,8 +631,8 @@ static asss_status launch_mrs(const Ctx& c, MrsWork* w, const OpView<T>& J, cons
     prm.qtz_done = w->qtz_done.p;
     void* args[] = {&prm};
     ASSS_CUDA(cudaEventRecord(w->evs[2 * lo.slot], c.stream));
-    ASSS_CUDA(cudaLaunchCooperativeKernel((const void*)k_mrs<T, KP, FMT>, dim3(nblk), dim3(MRS_THREADS), args, 0,
-                                          c.stream));
+    ASSS_CUDA(cudaLaunchCooperativeKernel((const void*)k_mrs<T, KP, FMT, QB>, dim3(nblk), dim3(MRS_THREADS), args,
+                                          0, c.stream));
     count_launch();
     ASSS_CUDA(cudaEventRecord(w->evs[2 * lo.slot + 1], c.stream));
     return ASSS_OK;
@@ -618,11 +678,35 @@ static asss_status y_layout(MrsWork* w, DBuf<T>& Ybuf, int& cur, int H, cudaStre
     return ASSS_OK;
 }
 
+// FP32 solve reading Q in BF16: row strides that keep 16-byte aligned rows
+template <int FMT>
+static asss_status dispatch_kp16(const Ctx& c, MrsWork* w, const OpView<float>& J, const __nv_bfloat16* Q16,
+                                 const double* alpha, int k, int kp, double shift, double sign, const double* rhs,
+                                 float* x, float* Y, long long ystride, float* P, double tol, int maxit,
+                                 LaunchOut lo) {
+    switch (kp) {
+#define ASSS_MRS16_CASE(KPV) \
+    case KPV:                \
+        return launch_mrs<float, KPV, FMT, true>(c, w, J, nullptr, alpha, k, shift, sign, rhs, x, Y, ystride, P, tol, \
+                                                 maxit, lo, Q16);
+        ASSS_MRS16_CASE(8)
+        ASSS_MRS16_CASE(16)
+        ASSS_MRS16_CASE(24)
+        ASSS_MRS16_CASE(32)
+        ASSS_MRS16_CASE(48)
+        ASSS_MRS16_CASE(64)
+#undef ASSS_MRS16_CASE
+        default:
+            set_error("unsupported BF16 Lanczos width %d", kp);
+            return ASSS_ERR_UNSUPPORTED;
+    }
+}
+
 template <class T>
 static asss_status dispatch_mrs(const Ctx& c, MrsWork* w, const DSell<T>* sell, const DSkewDia<T>* dia, const T* Q,
                                 const double* alpha, int k, int kp, double shift, double sign, const double* rhs,
                                 T* x, DBuf<T>& Ybuf, int& ylay, T* P, double tol, int maxit, long long* nnz_read,
-                                LaunchOut lo) {
+                                LaunchOut lo, const __nv_bfloat16* Q16 = nullptr, int kp16 = 0) {
     OpView<T> v;
     if (dia && dia->ndiag > MRS_MAXDIAG) dia = nullptr;
     T* Y = nullptr;
@@ -640,6 +724,10 @@ static asss_status dispatch_mrs(const Ctx& c, MrsWork* w, const DSell<T>* sell, 
         v.key = dia;
         v.nnz = dia->nnz;
         *nnz_read = v.nnz;
+        if constexpr (sizeof(T) == 4) {
+            if (Q16) return dispatch_kp16<1>(c, w, v, Q16, alpha, k, kp16, shift, sign, rhs, x, Y, ystride, P, tol,
+                                             maxit, lo);
+        }
         return dispatch_kp<T, 1>(c, w, v, Q, alpha, k, kp, shift, sign, rhs, x, Y, ystride, P, tol, maxit, lo);
     }
     if (!sell) {
@@ -655,6 +743,10 @@ static asss_status dispatch_mrs(const Ctx& c, MrsWork* w, const DSell<T>* sell, 
     v.key = sell;
     v.nnz = sell->nnz;
     *nnz_read = v.nnz;
+    if constexpr (sizeof(T) == 4) {
+        if (Q16) return dispatch_kp16<0>(c, w, v, Q16, alpha, k, kp16, shift, sign, rhs, x, Y, ystride, P, tol, maxit,
+                                         lo);
+    }
     return dispatch_kp<T, 0>(c, w, v, Q, alpha, k, kp, shift, sign, rhs, x, Y, ystride, P, tol, maxit, lo);
 }
 
@@ -677,7 +769,8 @@ asss_status mrs_solve(const Ctx& c, MrsWork* w, const MrsOperator& op, bool fp32
         }
         if (!w->P32.p) ASSS_TRY(w->P32.alloc((int64_t)2 * n));
         ASSS_TRY(dispatch_mrs<float>(c, w, op.J32, op.D32, op.Q32, op.alpha, op.k, op.kp, shift, sign, rhs, x32,
-                                     w->Y32, w->halo32, w->P32.p, tol, maxit, &nnz_read, lo));
+                                     w->Y32, w->halo32, w->P32.p, tol, maxit, &nnz_read, lo,
+                                     (const __nv_bfloat16*)op.Q16, op.kp16));
     } else {
         if ((!op.J64 && !op.D64) || !x64) {
             set_error("FP64 mrs needs the FP64 operator and an FP64 output");
@@ -692,13 +785,14 @@ asss_status mrs_solve(const Ctx& c, MrsWork* w, const MrsOperator& op, bool fp32
     // y_old, y_new, p r/w, x r/w), final pass (y, p, x r/w, and the Q row for Q^T x)
     long long T = fp32 ? 4 : 8;
     long long nn = n, kp = op.kp;
+    long long qrow = (fp32 && op.Q16) ? 2LL * op.kp16 : kp * T;  // bytes of one Q row as read
     long long per_entry = (fp32 ? (op.D32 != nullptr) : (op.D64 != nullptr)) ? T : T + 4;
     if ((int)w->log_nnz.size() <= lo.slot) {
         w->log_nnz.resize(lo.slot + 1);
         w->log_per_row.resize(lo.slot + 1);
     }
-    w->log_nnz[lo.slot] = nn * (8 + 4 * T + kp * T) + nn * 4 * T + ((qtz && op.k) ? nn * kp * T : 0);
-    w->log_per_row[lo.slot] = nnz_read * per_entry + nn * (7 * T + kp * T);
+    w->log_nnz[lo.slot] = nn * (8 + 4 * T + qrow) + nn * 4 * T + ((qtz && op.k) ? nn * qrow : 0);
+    w->log_per_row[lo.slot] = nnz_read * per_entry + nn * (7 * T + qrow);
     w->log_n++;
     if (sync_result) {
         std::vector<MrsResult> v;

@@ -362,3 +362,18 @@ def test_full_size_dh100_properties(pkg):
     Q = ex["Q"]
     np.testing.assert_allclose(Q.T @ Q, np.eye(Q.shape[1]), atol=1e-10)
     np.testing.assert_allclose(Q.T @ (Jt @ Q), O.lanczos_tridiagonal(ex["alpha"]), atol=1e-8)
+
+
+def test_solver_bf16_deflation_basis(pkg):
+    """Mixed precision with Q_k rounded to BF16 everywhere: P is unchanged, so the
+    solve reaches the same residual and solution."""
+    A, b, _ = dissipative_hamiltonian_3d(side=16, seed=9)
+    res = {}
+    for qb in (False, True):
+        s = pkg.Solver(A, precision="mixed", outer="fgmres", inner_tol=1e-6, q_bf16=qb)
+        x, st = s.solve(b)
+        assert st["status"] == 0 and np.linalg.norm(b - A @ x) <= 1e-8 * np.linalg.norm(b)
+        res[qb] = (x, st)
+        s.close()
+    assert abs(res[True][1]["outer_its"] - res[False][1]["outer_its"]) <= 1
+    assert np.linalg.norm(res[True][0] - res[False][0]) <= 1e-7 * np.linalg.norm(res[False][0])
