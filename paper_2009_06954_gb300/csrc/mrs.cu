@@ -263,9 +263,30 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
     __shared__ T s_u[KP > 0 ? KP : 1];
     __shared__ int s_off[FMT == 1 ? MRS_MAXDIAG : 1];
     __shared__ MrsScalars sc;
+    __shared__ double s_alpha[MRS_KPMAX];
+    // per-step coefficients in T, set by thread 0 (so no thread converts or divides in FP64):
+    // 0 sign*nu, 1 sign, 2 beta_{j-1} nu_{j-1}, 3 nu_p, 4 delta_pp, 5 1/theta_p, 6 xcoef_p,
+    // 7..10 the final pass: nu, delta, 1/theta, xcoef
+    __shared__ T s_cf[12];
     if constexpr (FMT == 1) {
         for (int d = threadIdx.x; d < p.ndiag; d += MRS_THREADS) s_off[d] = p.off[d];
     }
+    for (int m = threadIdx.x; m + 1 < p.k && m < MRS_KPMAX; m += MRS_THREADS) s_alpha[m] = p.alpha[m];
+    auto set_coefs = [&]() {  // thread 0 only
+        s_cf[0] = (T)(p.sign * sc.nu);
+        s_cf[1] = (T)p.sign;
+        s_cf[2] = (T)sc.coef_old;
+        s_cf[3] = (T)sc.nu_p;
+        s_cf[4] = (T)sc.delta_pp;
+        s_cf[5] = (T)(1.0 / sc.theta_p);
+        s_cf[6] = (T)sc.xcoef_p;
+        if (sc.stop) {
+            s_cf[7] = (T)sc.fin_nu;
+            s_cf[8] = (T)sc.fin_delta;
+            s_cf[9] = (T)(1.0 / sc.fin_theta);
+            s_cf[10] = (T)sc.fin_xcoef;
+        }
+    };
     const int nblk = gridDim.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int s0 = p.blk_slice[blockIdx.x], s1 = p.blk_slice[blockIdx.x + 1];
@@ -277,8 +298,22 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
     auto block_partials = [&](T(&tacc)[NV], double* buf) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            T d = warp_sum(tacc[v]);
-            if (lane == 0) s_wsum[warp][v] = (double)d;
+            if constexpr (sizeof(T) == 4) {
+                T d = warp_sum(tacc[v]);
+                if (lane == 0) s_wsum[warp][v] = (double)d;
+            } else {
+                // FP64 partials: the warp tree runs on float pairs (the FP64 pipe is slow)
+                float hi = (float)tacc[v];
+                float2 a = make_float2(hi, (float)((double)tacc[v] - (double)hi));
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    float2 b;
+                    b.x = __shfl_xor_sync(0xffffffffu, a.x, o);
+                    b.y = __shfl_xor_sync(0xffffffffu, a.y, o);
+                    a = df_add(a, b);
+                }
+                if (lane == 0) s_wsum[warp][v] = (double)a.x + (double)a.y;
+            }
         }
         __syncthreads();
         for (int v = threadIdx.x; v < NV; v += MRS_THREADS) {
@@ -324,8 +359,8 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
             for (int m = threadIdx.x; m < KP; m += MRS_THREADS) {
                 double u = 0.0;
                 if (m < p.k) {
-                    if (m + 1 < p.k) u += p.alpha[m] * s_red[2 + m] * nu;
-                    if (m > 0) u -= p.alpha[m - 1] * s_red[m] * nu;
+                    if (m + 1 < p.k) u += s_alpha[m] * s_red[2 + m] * nu;
+                    if (m > 0) u -= s_alpha[m - 1] * s_red[m] * nu;
                 }
                 s_u[m] = (T)u;
             }
@@ -375,6 +410,7 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
         sc.ratio = r0 > 0.0 ? 1.0 : 0.0;
         sc.its = 0;
         sc.stop = r0 > 0.0 ? 0 : 1;
+        set_coefs();
     }
     __syncthreads();
     if (sc.stop) {  // b = 0: x = 0 already
@@ -395,12 +431,24 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
         T* Yold = p.Y + (size_t)((j + 1) % 3) * ys;
         T* Ynew = p.Y + (size_t)(j % 3) * ys;
         T* Pj1 = p.P + (size_t)((j - 1) & 1) * n;
-        const T tnu = (T)(p.sign * sc.nu), tsg = (T)p.sign, tco = (T)sc.coef_old;
-        const T tnp = (T)sc.nu_p, tdpp = (T)sc.delta_pp, tthp = (T)(1.0 / sc.theta_p), txp = (T)sc.xcoef_p;
+        const T tnu = s_cf[0], tsg = s_cf[1], tco = s_cf[2];
+        const T tnp = s_cf[3], tdpp = s_cf[4], tthp = s_cf[5], txp = s_cf[6];
 #pragma unroll
         for (int v = 0; v < NV; ++v) tacc[v] = (T)0;
         for (int sl = s0 + warp; sl < s1; sl += MRS_WARPS) {
             const int i = sl * 32 + lane;
+            const bool live = i < n;
+            // this row's own data first (independent of the operator loop below)
+            const T yold = (live && j >= 2) ? Yold[i] : (T)0;
+            const T pold = (live && j >= 2) ? Pj1[i] : (T)0;
+            uint4 qraw[(QB && KP > 0) ? KP / 8 : 1];
+            if constexpr (QB && KP > 0) {
+                if (live) {
+                    const uint4* qr = reinterpret_cast<const uint4*>(p.Q16 + (size_t)i * KP);
+#pragma unroll
+                    for (int t = 0; t < KP / 8; ++t) qraw[t] = __ldg(qr + t);
+                }
+            }
             T acc = (T)0;
             if constexpr (FMT == 2) {
                 if (i < n) {
@@ -427,11 +475,22 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
                     }
                 }
             }
-            if (i < n) {
-                T yold = (j >= 2) ? Yold[i] : (T)0;
+            if (live) {
                 T q[KP > 0 ? KP : 1];
-                if constexpr (QB) load_qrow16<T, KP>(p.Q16, i, q);
-                else load_qrow<T, KP>(p.Q, i, q);
+                if constexpr (QB && KP > 0) {
+#pragma unroll
+                    for (int t = 0; t < KP / 8; ++t) {
+                        const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&qraw[t]);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            float2 f = __bfloat1622float2(h2[e]);
+                            q[8 * t + 2 * e] = (T)f.x;
+                            q[8 * t + 2 * e + 1] = (T)f.y;
+                        }
+                    }
+                } else {
+                    load_qrow<T, KP>(p.Q, i, q);
+                }
                 T dq = (T)0;
 #pragma unroll
                 for (int m = 0; m < KP; ++m) dq += q[m] * s_u[m];
@@ -441,7 +500,7 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
 #pragma unroll
                 for (int m = 0; m < KP; ++m) tacc[1 + m] += q[m] * ynew;
                 if (j >= 2) {
-                    T pv = (tnp * yold - tdpp * Pj1[i]) * tthp;
+                    T pv = (tnp * yold - tdpp * pold) * tthp;
                     Pj1[i] = pv;
                     p.x[i] += txp * pv;
                 }
@@ -482,12 +541,12 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
                 sc.theta_t = theta_t_next;
                 sc.G = Gn;
             }
+            set_coefs();
         }
         __syncthreads();
         if (sc.stop) {
             T* Pj = p.P + (size_t)(j & 1) * n;
-            const T tn = (T)sc.fin_nu, td = (T)sc.fin_delta, tth = (T)(1.0 / sc.fin_theta),
-                    tx = (T)sc.fin_xcoef;
+            const T tn = s_cf[7], td = s_cf[8], tth = s_cf[9], tx = s_cf[10];
 #pragma unroll
             for (int v = 0; v < NV; ++v) tacc[v] = (T)0;
             for (int sl = s0 + warp; sl < s1; sl += MRS_WARPS) {
