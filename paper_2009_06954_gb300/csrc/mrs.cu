@@ -17,6 +17,8 @@
 // iteration, which keeps the method's one-synchronisation-per-step property (§3.1).
 // Vectors produced by other blocks are read through L2 (ld.global.cg); the grid
 // barrier has a bounded wait.
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -32,6 +34,8 @@ constexpr int MRS_THREADS = 512;
 constexpr int MRS_WARPS = MRS_THREADS / 32;
 constexpr int MRS_KPMAX = 64;
 constexpr int MRS_MAXDIAG = 64;
+constexpr int MRS_TRACE_STEPS = 16;
+constexpr int MRS_TRACE_SLOTS = 4 + 5 * MRS_TRACE_STEPS;
 // resident blocks per SM the register allocation is sized for: two 512-thread
 // blocks for FP32 (more loads in flight for the gathers), one for FP64
 template <class T>
@@ -63,6 +67,7 @@ struct MrsWork {
     MrsTotals tot;
     DBuf<double> qtz_part;   // [KPMAX][maxblk] partials of the fused Q^T x
     DBuf<unsigned> qtz_done; // last-block counter
+    DBuf<unsigned long long> trace;  // ASSS_TRACE_MRS=1: timeline of block 0
     ~MrsWork() {
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
@@ -87,6 +92,10 @@ asss_status mrs_work_create(MrsWork** w, int n, int sms) {
         delete m;
         set_error("cudaEventCreate failed");
         return ASSS_ERR_CUDA;
+    }
+    if (getenv("ASSS_TRACE_MRS") && (st = m->trace.alloc(MRS_TRACE_SLOTS)) != ASSS_OK) {
+        delete m;
+        return st;
     }
     if ((st = m->its_log.alloc(MrsWork::LOG_CAP)) != ASSS_OK ||
         (st = m->ratio_log.alloc(MrsWork::LOG_CAP)) != ASSS_OK ||
@@ -140,6 +149,7 @@ struct MrsParams {
     long long budget;
     int* out_its;
     double* out_ratio;
+    unsigned long long* trace;  // optional timeline (block 0): %globaltimer at phase boundaries
     double* qtz;         // optional: Q^T x (k values) computed in the final pass
     double* qtz_part;    // [KP][nblk] block partials for it
     unsigned* qtz_done;  // last-block counter (left at 0)
@@ -189,6 +199,12 @@ __device__ __forceinline__ void load_qrow(const T* __restrict__ Q, int i, T (&q)
             for (int m = 0; m < KP; ++m) q[m] = row[m];
         }
     }
+}
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
 }
 
 // Error-free FP32 pair ("double-float") addition: TwoSum of the leading parts, the
@@ -293,6 +309,13 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
     const int n = p.n;
     const size_t ys = p.ystride;
     volatile int* err = p.gb.err;
+    // timeline slots: 0 start, 1 phase-0 pass, 2 phase-0 barrier, 3 set-up scalars; then per
+    // step j (1-based, first MRS_TRACE_STEPS): 4+5(j-1)+{0 pass, 1 partials, 2 barrier, 3 reduce, 4 scalars+u}
+    const bool tr = p.trace && blockIdx.x == 0 && threadIdx.x == 0;
+    auto stamp = [&](int slot) {
+        if (tr && slot < MRS_TRACE_SLOTS) p.trace[slot] = gtimer();
+    };
+    stamp(0);
 
     // warp sums in T, then FP64 across warps (fixed order) into this block's partial
     auto block_partials = [&](T(&tacc)[NV], double* buf) {
@@ -388,8 +411,10 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
             for (int m = 0; m < KP; ++m) tacc[1 + m] += q[m] * b;
         }
     }
+    stamp(1);
     block_partials(tacc, p.part);
     grid_sync(p.gb, nblk, p.budget);
+    stamp(2);
     if (*err) return;
     reduce_all(p.part);
 
@@ -425,8 +450,10 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
         return;
     }
     make_u(sc.nu);
+    stamp(3);
 
     for (int j = 1; j <= p.maxit; ++j) {
+        const int tb = 4 + 5 * (j - 1);
         T* Ycur = p.Y + (size_t)((j - 1) % 3) * ys;
         T* Yold = p.Y + (size_t)((j + 1) % 3) * ys;
         T* Ynew = p.Y + (size_t)(j % 3) * ys;
@@ -507,10 +534,14 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
             }
         }
         double* buf = p.part + (size_t)(j & 1) * NV * nblk;
+        stamp(tb);
         block_partials(tacc, buf);
+        stamp(tb + 1);
         grid_sync(p.gb, nblk, p.budget);
+        stamp(tb + 2);
         if (*err) break;
         reduce_all(buf);
+        stamp(tb + 3);
 
         if (threadIdx.x == 0) {
             const double beta = sqrt(s_red[0]);
@@ -572,6 +603,7 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
             break;
         }
         make_u(sc.nu);
+        stamp(tb + 4);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         *p.out_its = sc.its;
@@ -686,6 +718,7 @@ static asss_status launch_mrs(const Ctx& c, MrsWork* w, const OpView<T>& J, cons
     prm.out_its = w->its_log.p + lo.slot;
     prm.out_ratio = w->ratio_log.p + lo.slot;
     prm.qtz = (KP > 0 && k > 0) ? lo.qtz : nullptr;
+    prm.trace = w->trace.p;
     prm.qtz_part = w->qtz_part.p;
     prm.qtz_done = w->qtz_done.p;
     void* args[] = {&prm};
@@ -870,8 +903,25 @@ asss_status mrs_collect(const Ctx& c, MrsWork* w, std::vector<MrsResult>* out) {
     ASSS_CUDA(cudaMemcpyAsync(its.data(), w->its_log.p, sizeof(int) * nl, cudaMemcpyDeviceToHost, c.stream));
     ASSS_CUDA(cudaMemcpyAsync(ratio.data(), w->ratio_log.p, sizeof(double) * nl, cudaMemcpyDeviceToHost, c.stream));
     ASSS_CUDA(cudaMemcpyAsync(&herr, w->err.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    std::vector<unsigned long long> tl(w->trace.p ? MRS_TRACE_SLOTS : 0);
+    if (w->trace.p)
+        ASSS_CUDA(cudaMemcpyAsync(tl.data(), w->trace.p, sizeof(unsigned long long) * MRS_TRACE_SLOTS,
+                                  cudaMemcpyDeviceToHost, c.stream));
     ASSS_CUDA(cudaStreamSynchronize(c.stream));
     w->log_n = 0;
+    if (w->trace.p) {
+        // last launch: phase durations in ns (block 0)
+        fprintf(stderr, "mrs timeline (block 0, ns): phase0-pass %llu barrier %llu setup %llu |",
+                tl[1] - tl[0], tl[2] - tl[1], tl[3] - tl[2]);
+        int steps = its[nl - 1] < MRS_TRACE_STEPS ? its[nl - 1] : MRS_TRACE_STEPS;
+        for (int j = 1; j < steps; ++j) {
+            int tb = 4 + 5 * (j - 1);
+            unsigned long long prev = (j == 1) ? tl[3] : tl[tb - 1];
+            fprintf(stderr, " [pass %llu part %llu bar %llu red %llu sc+u %llu]", tl[tb] - prev,
+                    tl[tb + 1] - tl[tb], tl[tb + 2] - tl[tb + 1], tl[tb + 3] - tl[tb + 2], tl[tb + 4] - tl[tb + 3]);
+        }
+        fprintf(stderr, "\n");
+    }
     for (int i = 0; i < nl; ++i) {
         float ms = 0.f;
         ASSS_CUDA(cudaEventElapsedTime(&ms, w->evs[2 * i], w->evs[2 * i + 1]));
