@@ -183,6 +183,30 @@ def _traffic_record():
 
 
 # ----------------------------------------------------------------------------
+# multi-rank helpers (replicas: one independent solve stream per GPU)
+# ----------------------------------------------------------------------------
+def rank_env():
+    """(world, rank, local_rank) from the torchrun environment."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def reduce_max(value, dist=None, device=None):
+    """Largest value over the ranks (the slowest rank's time); identity without a group."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(world, steps, max_seconds):
+    """Whole-job rate: every rank processed `steps` units; the job ends with the slowest."""
+    return world * steps / max_seconds
+
+
+# ----------------------------------------------------------------------------
 # main
 # ----------------------------------------------------------------------------
 def main():
@@ -202,9 +226,7 @@ def main():
         cpu_worker(CPU_SAMPLE_SIDE, args.steps, args.warmup, args.budget)
         return
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
 
     if args.impl == "reference":
         if rank != 0:
@@ -274,14 +296,10 @@ def main():
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = sum(step_ms)
-    tmax = total_ms
-    if dist:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tmax = float(t.item())
+    tmax = reduce_max(total_ms, dist, dev)
     relres = max(s_["relres"] for s_ in stats)
     ok = all(s_["status"] == 0 for s_ in stats) and relres <= 1e-8
-    value = world * args.steps / (tmax / 1000.0)
+    value = aggregate_rate(world, args.steps, tmax / 1000.0)
 
     # end to end through the C ABI with pinned host buffers (copies in the timed region)
     bh = [torch.tensor(r).pin_memory() for r in rhs_h]
@@ -293,11 +311,7 @@ def main():
         t = time.perf_counter()
         solver.solve(bh[s % 4], xh)
         e2e_s += time.perf_counter() - t
-    e2e_val = args.steps / e2e_s
-    if dist:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_val = world * args.steps / float(t.item())
+    e2e_val = aggregate_rate(world, args.steps, reduce_max(e2e_s, dist, dev))
 
     inner_ms = sum(s_["t_inner_ms"] for s_ in stats)
     inner_bytes = sum(s_["inner_bytes"] for s_ in stats)

@@ -377,3 +377,66 @@ def test_solver_bf16_deflation_basis(pkg):
         s.close()
     assert abs(res[True][1]["outer_its"] - res[False][1]["outer_its"]) <= 1
     assert np.linalg.norm(res[True][0] - res[False][0]) <= 1e-7 * np.linalg.norm(res[False][0])
+
+
+# ----------------------------------------------------------------------------
+# differentiation at the 64^3 size: adjoint vs finite differences on 64 seeded entries
+# ----------------------------------------------------------------------------
+@pytest.mark.slow
+def test_adjoint_finite_differences_dh64(pkg):
+    """L = ||x - x*||^2 on the 64^3 dissipative-Hamiltonian step (n = 262 144),
+    FP32 inner / FP64 outer.  32 entries of b and 32 nonzeros of A, seeded.
+
+    b: L is quadratic in b, so the central difference with any step h is exact:
+       [L(b+h e_i) - L(b-h e_i)] / 2h = (x+ - x-).(x+ + x- - 2x*) / 2h with
+       x+ - x- = A^-1 (2h e_i) and x+ + x- = 2x  (one forward solve per entry).
+    A: central differences with h = 1e-3 |a_e| and one Richardson step
+       (4 D(h) - D(2h)) / 3, each D from two perturbed set-ups and solves, in the
+       cancellation-free form (x+ - x-).(x+ + x- - 2x*) / 2h."""
+    A, b, _ = dissipative_hamiltonian_3d(side=64, seed=4)
+    n = A.shape[0]
+    rng = np.random.default_rng(44)
+    xs = rng.standard_normal(n)
+    opts = dict(precision="mixed", outer="fgmres", inner_tol=1e-6, outer_tol=1e-13)
+    s = pkg.Solver(A, **opts)
+    x, st = s.solve(b)
+    assert st["status"] == 0
+    g = 2.0 * (x - xs)
+    lam, dA, st2 = s.solve_adjoint(g, x=x)
+    assert st2["status"] == 0
+    scale_b = np.abs(lam).max()
+    h = 1e-6
+    errs = []
+    for i in rng.choice(n, 32, replace=False):
+        e = np.zeros(n)
+        e[i] = 2.0 * h
+        dx, _ = s.solve(e)
+        fd = np.dot(dx, 2.0 * x - 2.0 * xs) / (2.0 * h)
+        errs.append(abs(fd - lam[i]) / max(abs(fd), 1e-3 * scale_b))
+    assert max(errs) <= 1e-6, max(errs)
+    s.close()
+
+    rows = np.repeat(np.arange(n), np.diff(A.indptr))
+    scale_a = np.abs(dA).max()
+
+    def central(e_idx, hh):
+        out = []
+        for sgn in (1.0, -1.0):
+            Ap = A.copy()
+            Ap.data[e_idx] += sgn * hh
+            sp_ = pkg.Solver(Ap, **opts)
+            xp, stp = sp_.solve(b)
+            assert stp["status"] == 0
+            out.append(xp)
+            sp_.close()
+        xp, xm = out
+        return np.dot(xp - xm, xp + xm - 2.0 * xs) / (2.0 * hh)
+
+    errs = []
+    for e_idx in rng.choice(A.nnz, 32, replace=False):
+        hh = 1e-3 * abs(A.data[e_idx])
+        d1 = central(e_idx, hh)
+        d2 = central(e_idx, 2.0 * hh)
+        fd = (4.0 * d1 - d2) / 3.0
+        errs.append(abs(fd - dA[e_idx]) / max(abs(fd), 1e-3 * scale_a))
+    assert max(errs) <= 1e-6, max(errs)
