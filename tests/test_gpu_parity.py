@@ -385,15 +385,16 @@ def test_solver_bf16_deflation_basis(pkg):
 @pytest.mark.slow
 def test_adjoint_finite_differences_dh64(pkg):
     """L = ||x - x*||^2 on the 64^3 dissipative-Hamiltonian step (n = 262 144),
-    FP32 inner / FP64 outer.  32 entries of b and 32 nonzeros of A, seeded.
+    FP32 inner / FP64 outer; central differences with step h = 1e-6 on 32 entries
+    of b and 32 nonzeros of A (seeded), evaluated without cancellation:
 
-    b: L is quadratic in b, so the central difference with any step h is exact:
-       [L(b+h e_i) - L(b-h e_i)] / 2h = (x+ - x-).(x+ + x- - 2x*) / 2h with
-       x+ - x- = A^-1 (2h e_i) and x+ + x- = 2x  (one forward solve per entry).
-    A: central differences with the absolute step h = 1e-3 and one Richardson step
-       (4 D(h) - D(2h)) / 3 (truncation O(h^4)), each D from two perturbed set-ups and
-       solves, in the cancellation-free form (x+ - x-).(x+ + x- - 2x*) / 2h.  A step of
-       1e-6 would leave x+ - x- below the round-off of a 262 144-unknown solve."""
+      [L(+) - L(-)] / 2h = (x+ - x-) . (x+ + x- - 2x*) / 2h      (exact identity)
+
+    b: L is quadratic in b, x+ - x- = A^-1 (2h e_i) and x+ + x- = 2x.
+    A (entry e = (i, j), E = e_i e_j^T): (A +- hE) x+- = b gives
+       A (x+ - x-) = -h E (x+ + x-), i.e. x+ - x- = -h (x+_j + x-_j) A^-1 e_i,
+    so the difference of two nearly equal solves is never formed; x+ and x- come from
+    their own set-ups and solves, A^-1 e_i from one more forward solve."""
     A, b, _ = dissipative_hamiltonian_3d(side=64, seed=4)
     n = A.shape[0]
     rng = np.random.default_rng(44)
@@ -405,8 +406,8 @@ def test_adjoint_finite_differences_dh64(pkg):
     g = 2.0 * (x - xs)
     lam, dA, st2 = s.solve_adjoint(g, x=x)
     assert st2["status"] == 0
-    scale_b = np.abs(lam).max()
     h = 1e-6
+    scale_b = np.abs(lam).max()
     errs = []
     for i in rng.choice(n, 32, replace=False):
         e = np.zeros(n)
@@ -415,28 +416,27 @@ def test_adjoint_finite_differences_dh64(pkg):
         fd = np.dot(dx, 2.0 * x - 2.0 * xs) / (2.0 * h)
         errs.append(abs(fd - lam[i]) / max(abs(fd), 1e-3 * scale_b))
     assert max(errs) <= 1e-6, max(errs)
-    s.close()
 
+    rows = np.repeat(np.arange(n), np.diff(A.indptr))
     scale_a = np.abs(dA).max()
-
-    def central(e_idx, hh):
-        out = []
-        for sgn in (1.0, -1.0):
-            Ap = A.copy()
-            Ap.data[e_idx] += sgn * hh
-            sp_ = pkg.Solver(Ap, **opts)
-            xp, stp = sp_.solve(b)
-            assert stp["status"] == 0
-            out.append(xp)
-            sp_.close()
-        xp, xm = out
-        return np.dot(xp - xm, xp + xm - 2.0 * xs) / (2.0 * hh)
-
     errs = []
     for e_idx in rng.choice(A.nnz, 32, replace=False):
-        hh = 1e-3
-        d1 = central(e_idx, hh)
-        d2 = central(e_idx, 2.0 * hh)
-        fd = (4.0 * d1 - d2) / 3.0
+        i, j = rows[e_idx], A.indices[e_idx]
+        xpm = []
+        for sgn in (1.0, -1.0):
+            Ap = A.copy()
+            Ap.data[e_idx] += sgn * h
+            sp_ = pkg.Solver(Ap, **opts)
+            xp_, stp = sp_.solve(b)
+            assert stp["status"] == 0
+            xpm.append(xp_)
+            sp_.close()
+        xp, xm = xpm
+        ei = np.zeros(n)
+        ei[i] = 1.0
+        ai, _ = s.solve(ei)
+        dxpm = -h * (xp[j] + xm[j]) * ai
+        fd = np.dot(dxpm, xp + xm - 2.0 * xs) / (2.0 * h)
         errs.append(abs(fd - dA[e_idx]) / max(abs(fd), 1e-3 * scale_a))
     assert max(errs) <= 1e-6, max(errs)
+    s.close()
