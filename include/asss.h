@@ -173,6 +173,39 @@ asss_status asss_export(asss_handle* h, double* dr, double* dc, double* w, doubl
 
 void asss_destroy(asss_handle* h);
 
+/* ------------------------------------------------------------------------
+ * Batched solves: many matrices of uneven size, each with its own set-up, and
+ * many right-hand sides, solved by one persistent launch (§4.1 solve phase per
+ * system: refinement on the FP64 residual, flexible GMRES outer, P^-1 by
+ * Eq. smw around FP32 mrs, App. B).  Each CTA takes (matrix, right-hand side)
+ * items from a global counter, largest matrices first, and runs the whole solve
+ * of one item in block scope.  The launch is captured once into a CUDA graph
+ * and replayed while b, x and nrhs stay the same.
+ * ------------------------------------------------------------------------ */
+typedef struct asss_batch asss_batch;
+
+/* Set up nmat systems A[0..nmat) with one option set.  Forces the mixed-precision
+ * path, flexible GMRES and skew-diagonal storage of J~ (UNSUPPORTED if a J~ does
+ * not fit it, if the matrices end with different Lanczos widths, or if k > 32,
+ * k + r > 320 or J~ has more than 64 diagonals).  The restart length is
+ * min(opt->restart, 24).  A tuner runs one synthetic batch (b = A 1) at 256, 512
+ * and 1024 threads per CTA and keeps the fastest.  st (may be NULL): t_setup_ms,
+ * k_eff of matrix 0, and inner_launches = the chosen CTA size. */
+asss_status asss_setup_batched(int nmat, const asss_csr* const* A, const asss_options* opt,
+                               asss_batch** out, asss_stats* st);
+
+/* Solve every system for nrhs right-hand sides.  b and x (host or device) hold
+ * the systems one after the other: system m occupies entries
+ * [off_m * nrhs, (off_m + n_m) * nrhs) with off_m = n_0 + ... + n_{m-1}, column-major
+ * n_m x nrhs inside.  x is overwritten.  st (may be NULL): outer_its = the largest
+ * over items, inner_its_total and cycles summed, relres = the largest, inner_solves
+ * = number of items, t_inner_ms = device time of the batched launch.  Returns the
+ * first non-OK item status (x then holds every item's last iterate). */
+asss_status asss_solve_batched(asss_batch* b, int nrhs, const double* rhs, double* x,
+                               asss_stats* st);
+
+void asss_destroy_batched(asss_batch* b);
+
 const char* asss_status_str(asss_status s);
 const char* asss_last_error(void);
 

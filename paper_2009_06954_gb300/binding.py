@@ -68,7 +68,8 @@ class Stats(C.Structure):
 EXPORTED = ["asss_default_options", "asss_setup", "asss_solve", "asss_solve_adjoint",
             "asss_apply_operator", "asss_apply_preconditioner", "asss_export", "asss_destroy",
             "asss_status_str", "asss_last_error", "asss_skew_symmetrizer", "asss_skew_lanczos",
-            "asss_mrs", "asss_kernel_launches", "asss_mrs_noalloc"]
+            "asss_mrs", "asss_kernel_launches", "asss_mrs_noalloc", "asss_setup_batched",
+            "asss_solve_batched", "asss_destroy_batched"]
 
 _lib = None
 _live = weakref.WeakSet()   # open handles, closed at exit while CUDA is still up
@@ -118,11 +119,15 @@ def lib():
                                    C.c_double, P, P, C.c_double, C.c_int, C.POINTER(C.c_int),
                                    C.POINTER(C.c_double), P]
     L.asss_mrs_noalloc.restype = C.c_int
+    L.asss_setup_batched.argtypes = [C.c_int, C.POINTER(pCSR), pO, C.POINTER(P), pS]
+    L.asss_solve_batched.argtypes = [P, C.c_int, P, P, pS]
+    L.asss_destroy_batched.argtypes = [P]
+    L.asss_destroy_batched.restype = None
     L.asss_kernel_launches.argtypes = []
     L.asss_kernel_launches.restype = C.c_ulonglong
     for f in ("asss_setup", "asss_solve", "asss_solve_adjoint", "asss_apply_operator",
               "asss_apply_preconditioner", "asss_export", "asss_skew_symmetrizer",
-              "asss_skew_lanczos", "asss_mrs"):
+              "asss_skew_lanczos", "asss_mrs", "asss_setup_batched", "asss_solve_batched"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -331,6 +336,77 @@ class Solver:
         _check("asss_export", lib().asss_export(
             self._h, *[_ptr_f(out[key], keep) for key in ("dr", "dc", "w", "d", "s_val", "Q", "alpha", "neg")]))
         return out
+
+
+class BatchSolver:
+    """Many systems of uneven size, each set up once, solved together by one
+    persistent launch (replayed CUDA graph) for nrhs right-hand sides each.
+
+    mats: list of scipy.sparse matrices.  Options as for ``Solver``; precision,
+    outer method and J~ storage are fixed (mixed, flexible GMRES, skew-diagonal),
+    restart is capped at 24.  ``solve`` takes b as one concatenated vector: system m
+    occupies [off_m * nrhs, (off_m + n_m) * nrhs), column-major n_m x nrhs, with
+    off_m the sum of the sizes before it (``offsets``).
+    """
+
+    def __init__(self, mats, **opts):
+        self._keep = []
+        self.sizes = [int(A.shape[0]) for A in mats]
+        self.offsets = np.concatenate([[0], np.cumsum(self.sizes)]).astype(np.int64)
+        self.total = int(self.offsets[-1])
+        structs = [_csr_struct(A, self._keep) for A in mats]
+        arr = (C.POINTER(CSR) * len(structs))(*[C.pointer(c) for c in structs])
+        self._keep.append(arr)
+        self._opts = _options(self._keep, **opts)
+        h = C.c_void_p()
+        st = Stats()
+        status = lib().asss_setup_batched(len(structs), arr, C.byref(self._opts), C.byref(h), C.byref(st))
+        _check("asss_setup_batched", status)
+        self._h = h
+        self.setup_stats = st.as_dict()
+        self.cta_threads = int(st.inner_launches)
+        _live.add(self)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().asss_destroy_batched(self._h)
+            self._h = None
+
+    def __del__(self):
+        if sys.is_finalizing():
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def pack(self, blocks):
+        """List of n_m x nrhs (or n_m) arrays -> concatenated numpy vector."""
+        return np.concatenate([np.asarray(b, dtype=np.float64).reshape(len(b), -1).ravel(order="F")
+                               for b in blocks])
+
+    def unpack(self, v, nrhs):
+        v = np.asarray(v)
+        return [v[o * nrhs:(o + n) * nrhs].reshape((n, nrhs), order="F")
+                for o, n in zip(self.offsets[:-1], self.sizes)]
+
+    def solve(self, b, nrhs=1, x=None):
+        """x for every (system, column); b host or device, length total * nrhs."""
+        keep = []
+        if not _is_torch(b):
+            b = np.ascontiguousarray(b, dtype=np.float64)
+        if b.shape[0] != self.total * nrhs:
+            raise ValueError(f"b must have {self.total * nrhs} entries")
+        if x is None:
+            if _is_torch(b):
+                import torch
+                x = torch.empty_like(b)
+            else:
+                x = np.empty_like(b)
+        st = Stats()
+        status = lib().asss_solve_batched(self._h, int(nrhs), _ptr_f(b, keep), _ptr_f(x, keep), C.byref(st))
+        _check("asss_solve_batched", status, soft_ok=True)
+        return x, st.as_dict()
 
 
 def _ptr_f(a, keep):

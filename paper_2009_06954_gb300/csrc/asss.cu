@@ -1,6 +1,7 @@
 // C ABI of the library: set-up, solve, adjoint and single-step entry points.
 // Host code here only orders kernel launches and reads back the scalars that
 // decide control flow (convergence, breakdown); all arithmetic runs on the GPU.
+#include <algorithm>
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
@@ -1612,6 +1613,356 @@ asss_status asss_mrs(const asss_csr* J, int k, const double* q, const double* al
     if (its) *its = res.its;
     if (ratio) *ratio = res.ratio;
     return ASSS_OK;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// batched solves: many matrices (own set-up each) x many right-hand sides,
+// one persistent launch captured in a CUDA graph
+// ===========================================================================
+struct asss_batch {
+    asss_options opt;
+    Ctx ctx;
+    cudaStream_t own = nullptr;      // the batch's stream (graphs cannot capture the legacy stream)
+    cudaEvent_t ev_in = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
+    std::vector<asss_handle*> hs;
+    std::vector<int> n_of;
+    std::vector<long long> off_h;
+    long long total_rows = 0;
+    int n_max = 0, halo_max = 0, kp = 0, qbf16 = 0, restart = 20;
+    DBuf<BatchMat> mats;
+    DBuf<long long> row_off;
+    DBuf<double> work;
+    long long work_stride = 0;
+    int nblk = 0, nthreads = 512;
+    DBuf<unsigned> counter;
+    DBuf<BatchItemStat> stats;
+    DBuf<int2> items;
+    int items_nrhs = -1;
+    DBuf<double> bdev, xdev;
+    cudaGraphExec_t gexec = nullptr;
+    const void* g_b = nullptr;
+    const void* g_x = nullptr;
+    int g_nrhs = -1, g_nt = -1;
+    ~asss_batch() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        for (asss_handle* h : hs) delete h;
+        if (ev_in) cudaEventDestroy(ev_in);
+        if (ev_t0) cudaEventDestroy(ev_t0);
+        if (ev_t1) cudaEventDestroy(ev_t1);
+        if (own) cudaStreamDestroy(own);
+    }
+};
+
+static asss_status batch_view(asss_handle* h, BatchMat* v) {
+    if (!h->use_dia || !h->D32.n || h->opt.precision != ASSS_PREC_MIXED) {
+        set_error("batched solves need the mixed-precision path and skew-diagonal storage of J~");
+        return ASSS_ERR_UNSUPPORTED;
+    }
+    SmwData& S = h->smw[0];
+    if (!S.ready || (S.m > 0 && !S.Y32.p) || S.m > 320 || h->k > 32 || h->D32.ndiag > 64) {
+        set_error("batched solves support k <= 32, k + r <= 320 and at most 64 diagonals");
+        return ASSS_ERR_UNSUPPORTED;
+    }
+    memset(v, 0, sizeof(*v));
+    v->n = h->n;
+    v->k = h->k;
+    v->m = S.m;
+    v->r = h->r;
+    v->ndiag = h->D32.ndiag;
+    v->halo = h->D32.halo;
+    v->ustride = h->D32.ustride;
+    v->off = h->D32.off.p;
+    v->U = h->D32.U.p + h->D32.halo;
+    v->Q32 = h->Q32.p;
+    v->Q16 = h->Q16.p;
+    v->alpha = h->alpha_d.p;
+    v->Y32 = S.Y32.p;
+    v->neg = h->neg.p;
+    v->arp = h->A.rp.p;
+    v->aci = h->A.ci.p;
+    v->av = h->A.v.p;
+    v->awrp = h->Aw.rp.p;
+    v->awci = h->Aw.ci.p;
+    v->awv = h->Aw.v.p;
+    v->swrp = h->Sw.rp.p;
+    v->swci = h->Sw.ci.p;
+    v->swv = h->Sw.v.p;
+    v->srp = h->S.rp.p;
+    v->sci = h->S.ci.p;
+    v->sv = h->S.v.p;
+    v->dr = h->dr.p;
+    v->dc = h->dc.p;
+    v->w = h->w.p;
+    v->perm = h->has_perm ? h->perm.p : nullptr;
+    return ASSS_OK;
+}
+
+// work items (matrix, column), largest matrices first so the tail of the launch is short
+static asss_status batch_items(asss_batch* B, int nrhs) {
+    if (B->items_nrhs == nrhs) return ASSS_OK;
+    int nm = (int)B->hs.size();
+    std::vector<int> order(nm);
+    for (int i = 0; i < nm; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return B->n_of[a] > B->n_of[b]; });
+    std::vector<int2> it;
+    it.reserve((size_t)nm * nrhs);
+    for (int m : order)
+        for (int c = 0; c < nrhs; ++c) it.push_back(make_int2(m, c));
+    ASSS_TRY(to_device(B->items, it.data(), (int64_t)it.size(), B->own));
+    ASSS_TRY(B->stats.alloc((int64_t)it.size()));
+    B->items_nrhs = nrhs;
+    if (B->gexec) {
+        cudaGraphExecDestroy(B->gexec);
+        B->gexec = nullptr;
+    }
+    return ASSS_OK;
+}
+
+static asss_status batch_run(asss_batch* B, int nrhs, const double* bd, double* xd, int nthreads, bool use_graph,
+                             float* ms) {
+    ASSS_TRY(batch_items(B, nrhs));
+    BatchLaunch L;
+    L.mats = B->mats.p;
+    L.items = B->items.p;
+    L.nitems = (int)B->items.n;
+    L.nrhs = nrhs;
+    L.row_off = B->row_off.p;
+    L.b = bd;
+    L.x = xd;
+    L.work = B->work.p;
+    L.work_stride = B->work_stride;
+    L.n_max = B->n_max;
+    L.halo_max = B->halo_max;
+    L.kp = B->kp;
+    L.qbf16 = B->qbf16;
+    L.restart = B->restart;
+    L.outer_tol = B->opt.outer_tol;
+    L.outer_maxit = B->opt.outer_maxit;
+    L.inner_tol = B->opt.inner_tol;
+    L.inner_maxit = B->opt.inner_maxit;
+    L.next_item = B->counter.p;
+    L.stats = B->stats.p;
+    int nblk = B->nblk < L.nitems ? B->nblk : L.nitems;
+    if (nblk < 1) nblk = 1;
+    cudaStream_t s = B->own;
+    if (use_graph) {
+        if (!B->gexec || B->g_b != bd || B->g_x != xd || B->g_nrhs != nrhs || B->g_nt != nthreads) {
+            if (B->gexec) {
+                cudaGraphExecDestroy(B->gexec);
+                B->gexec = nullptr;
+            }
+            cudaGraph_t g;
+            ASSS_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            asss_status st = ASSS_OK;
+            if (cudaMemsetAsync(B->counter.p, 0, sizeof(unsigned), s) != cudaSuccess) st = ASSS_ERR_CUDA;
+            if (st == ASSS_OK) st = batch_launch(L, nthreads, nblk, s);
+            cudaError_t e = cudaStreamEndCapture(s, &g);
+            if (st != ASSS_OK) return st;
+            if (e != cudaSuccess) {
+                set_error("graph capture failed: %s", cudaGetErrorString(e));
+                return ASSS_ERR_CUDA;
+            }
+            e = cudaGraphInstantiate(&B->gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                set_error("graph instantiate failed: %s", cudaGetErrorString(e));
+                return ASSS_ERR_CUDA;
+            }
+            B->g_b = bd;
+            B->g_x = xd;
+            B->g_nrhs = nrhs;
+            B->g_nt = nthreads;
+        }
+        ASSS_CUDA(cudaEventRecord(B->ev_t0, s));
+        ASSS_CUDA(cudaGraphLaunch(B->gexec, s));
+        count_launch();
+        ASSS_CUDA(cudaEventRecord(B->ev_t1, s));
+    } else {
+        ASSS_CUDA(cudaEventRecord(B->ev_t0, s));
+        ASSS_CUDA(cudaMemsetAsync(B->counter.p, 0, sizeof(unsigned), s));
+        ASSS_TRY(batch_launch(L, nthreads, nblk, s));
+        ASSS_CUDA(cudaEventRecord(B->ev_t1, s));
+    }
+    ASSS_CUDA(cudaStreamSynchronize(s));
+    if (ms) ASSS_CUDA(cudaEventElapsedTime(ms, B->ev_t0, B->ev_t1));
+    return ASSS_OK;
+}
+
+extern "C" {
+
+asss_status asss_setup_batched(int nmat, const asss_csr* const* A, const asss_options* opt, asss_batch** out,
+                               asss_stats* st) {
+    if (!out || nmat < 1 || !A) {
+        set_error("invalid arguments");
+        return ASSS_ERR_ARG;
+    }
+    *out = nullptr;
+    auto t0 = std::chrono::steady_clock::now();
+    asss_batch* B = new asss_batch();
+    if (opt) B->opt = *opt;
+    else fill_defaults(&B->opt);
+    B->opt.precision = ASSS_PREC_MIXED;
+    B->opt.outer = ASSS_OUTER_FGMRES;
+    if (B->opt.inner_format == ASSS_FORMAT_SELL) {
+        delete B;
+        set_error("batched solves use the skew-diagonal storage");
+        return ASSS_ERR_UNSUPPORTED;
+    }
+    B->opt.inner_format = ASSS_FORMAT_DIAG;
+    B->restart = B->opt.restart > 0 ? (B->opt.restart < BATCH_RMAX ? B->opt.restart : BATCH_RMAX) : 20;
+    asss_status s = make_ctx(B->ctx, B->opt.stream, B->opt.wait_timeout_ms);
+    if (s == ASSS_OK && cudaStreamCreateWithFlags(&B->own, cudaStreamNonBlocking) != cudaSuccess) s = ASSS_ERR_CUDA;
+    if (s == ASSS_OK && (cudaEventCreate(&B->ev_in) != cudaSuccess || cudaEventCreate(&B->ev_t0) != cudaSuccess ||
+                         cudaEventCreate(&B->ev_t1) != cudaSuccess))
+        s = ASSS_ERR_CUDA;
+    asss_options o = B->opt;
+    o.stream = B->own;
+    std::vector<BatchMat> views(nmat);
+    long long rows = 0;
+    for (int m = 0; m < nmat && s == ASSS_OK; ++m) {
+        asss_handle* h = nullptr;
+        asss_stats hs;
+        s = asss_setup(A[m], &o, &h, &hs);
+        if (s != ASSS_OK) break;
+        B->hs.push_back(h);
+        s = batch_view(h, &views[m]);
+        if (s != ASSS_OK) break;
+        int kpm = h->Q16.p ? h->kp16 : h->kp;
+        if (m == 0) {
+            B->kp = kpm;
+            B->qbf16 = h->Q16.p ? 1 : 0;
+        } else if (kpm != B->kp || (h->Q16.p ? 1 : 0) != B->qbf16) {
+            set_error("matrices of a batch must keep the same number of Lanczos vectors");
+            s = ASSS_ERR_UNSUPPORTED;
+            break;
+        }
+        B->n_of.push_back(h->n);
+        B->off_h.push_back(rows);
+        rows += h->n;
+        if (h->n > B->n_max) B->n_max = h->n;
+        if (h->D32.halo > B->halo_max) B->halo_max = h->D32.halo;
+    }
+    if (s == ASSS_OK) {
+        B->total_rows = rows;
+        s = to_device(B->mats, views.data(), nmat, B->own);
+        if (s == ASSS_OK) s = to_device(B->row_off, B->off_h.data(), nmat, B->own);
+        if (s == ASSS_OK) s = B->counter.alloc(1);
+    }
+    // CTA size: pick the fastest of 256 / 512 / 1024 threads on a synthetic batch
+    // (b = A 1 for every matrix, one column), timed with CUDA events
+    if (s == ASSS_OK) {
+        B->work_stride = batch_work_doubles(B->n_max, B->halo_max, B->restart);
+        int best_nt = 0;
+        float best_ms = 0.f;
+        DBuf<double> bt, xt, ones;
+        if ((s = bt.alloc(rows)) == ASSS_OK && (s = xt.alloc(rows)) == ASSS_OK && (s = ones.alloc(B->n_max)) == ASSS_OK)
+            s = vfill(ones.p, 1.0, B->n_max, B->own);
+        for (int m = 0; m < nmat && s == ASSS_OK; ++m) s = spmv(B->hs[m]->A, ones.p, bt.p + B->off_h[m], nullptr, B->own);
+        const int cand[3] = {256, 512, 1024};
+        for (int c = 0; c < 3 && s == ASSS_OK; ++c) {
+            int occ = 0;
+            s = batch_occupancy(B->kp, B->qbf16, cand[c], &occ);
+            if (s != ASSS_OK || occ < 1) continue;
+            int nb = B->ctx.sms * (occ < 2 ? occ : 2);
+            if (nb > B->nblk) {
+                B->nblk = nb;
+                s = B->work.alloc(B->work_stride * (long long)nb);
+                if (s != ASSS_OK) break;
+            }
+            int keep = B->nblk;
+            B->nblk = nb;
+            float ms = 0.f;
+            s = batch_run(B, 1, bt.p, xt.p, cand[c], false, &ms);
+            B->nblk = keep;
+            if (s != ASSS_OK) break;
+            if (!best_nt || ms < best_ms) {
+                best_nt = cand[c];
+                best_ms = ms;
+            }
+        }
+        if (s == ASSS_OK) {
+            int occ = 0;
+            s = batch_occupancy(B->kp, B->qbf16, best_nt, &occ);
+            B->nthreads = best_nt;
+            B->nblk = B->ctx.sms * (occ < 2 ? occ : 2);
+        }
+    }
+    if (s != ASSS_OK) {
+        if (B->own) cudaStreamSynchronize(B->own);
+        delete B;
+        if (st) {
+            memset(st, 0, sizeof(*st));
+            st->status = s;
+        }
+        return s;
+    }
+    if (st) {
+        memset(st, 0, sizeof(*st));
+        st->k_eff = B->hs[0]->k;
+        st->t_setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        st->inner_launches = B->nthreads;  // CTA size chosen by the tuner
+    }
+    *out = B;
+    return ASSS_OK;
+}
+
+asss_status asss_solve_batched(asss_batch* B, int nrhs, const double* b, double* x, asss_stats* st) {
+    if (!B || nrhs < 1 || !b || !x) {
+        set_error("invalid arguments");
+        return ASSS_ERR_ARG;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    long long total = B->total_rows * nrhs;
+    bool bdv = is_device_ptr(b), xdv = is_device_ptr(x);
+    // order after the caller's stream
+    ASSS_CUDA(cudaEventRecord(B->ev_in, (cudaStream_t)B->opt.stream));
+    ASSS_CUDA(cudaStreamWaitEvent(B->own, B->ev_in, 0));
+    const double* bd = b;
+    double* xd = x;
+    if (!bdv) {
+        if (B->bdev.n < total) ASSS_TRY(B->bdev.alloc(total));
+        ASSS_CUDA(cudaMemcpyAsync(B->bdev.p, b, sizeof(double) * total, cudaMemcpyHostToDevice, B->own));
+        bd = B->bdev.p;
+    }
+    if (!xdv) {
+        if (B->xdev.n < total) ASSS_TRY(B->xdev.alloc(total));
+        xd = B->xdev.p;
+    }
+    float ms = 0.f;
+    ASSS_TRY(batch_run(B, nrhs, bd, xd, B->nthreads, true, &ms));
+    if (!xdv) ASSS_CUDA(cudaMemcpyAsync(x, xd, sizeof(double) * total, cudaMemcpyDeviceToHost, B->own));
+    std::vector<BatchItemStat> hs(B->items.n);
+    ASSS_CUDA(cudaMemcpyAsync(hs.data(), B->stats.p, sizeof(BatchItemStat) * hs.size(), cudaMemcpyDeviceToHost,
+                              B->own));
+    ASSS_CUDA(cudaStreamSynchronize(B->own));
+    asss_stats a;
+    memset(&a, 0, sizeof(a));
+    int worst = ASSS_OK;
+    for (const BatchItemStat& t : hs) {
+        if (t.outer_its > a.outer_its) a.outer_its = t.outer_its;
+        a.inner_its_total += t.inner_its;
+        a.cycles += t.cycles;
+        if (t.relres > a.relres) a.relres = t.relres;
+        if (t.status != ASSS_OK && worst == ASSS_OK) worst = t.status;
+    }
+    a.inner_solves = (int)hs.size();
+    a.inner_its_avg = hs.empty() ? 0.0 : (double)a.inner_its_total / hs.size();
+    a.status = worst;
+    a.t_inner_ms = ms;   // device time of the batched launch
+    a.inner_launches = 1;
+    a.t_solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    a.k_eff = B->hs[0]->k;
+    if (st) *st = a;
+    if (worst != ASSS_OK) set_error("batched solve: an item ended with status %d", worst);
+    return (asss_status)worst;
+}
+
+void asss_destroy_batched(asss_batch* B) {
+    if (!B) return;
+    if (B->own) cudaStreamSynchronize(B->own);
+    delete B;
 }
 
 }  // extern "C"

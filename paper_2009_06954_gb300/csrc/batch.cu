@@ -1,0 +1,558 @@
+// Batched solves (many matrices of uneven size, many right-hand sides): one
+// persistent launch in which every CTA takes (matrix, right-hand side) work items
+// from a global counter and runs the whole solve of that item in block scope:
+//   the refinement loop on the true FP64 residual and flexible GMRES (outer, FP64,
+//   §4.1), P^-1 by SMW (Eq. smw) around the mrs iteration of App. B on the
+//   deflated shifted skew system (FP32, skew-diagonal storage of J~, §3.1-3.2).
+// The algorithms are those of the single-system path (asss.cu, mrs.cu); what
+// changes is the scope: block reductions and __syncthreads instead of grid
+// barriers and kernel launches, so small systems do not pay a launch or a grid
+// synchronisation per step.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace asss {
+
+constexpr int BMAX_WARPS = 32;
+constexpr int BKPMAX = 32;   // largest padded Lanczos width handled by the batched kernel
+constexpr int BMMAX = 320;   // largest SMW rank k + r
+
+long long batch_work_doubles(int n_max, int halo_max, int restart) {
+    long long nd = (long long)(5 + 2 * restart + 1) * n_max;                  // r, rh, dy, t1, t2, V, Z
+    long long nf = 3LL * ((long long)n_max + 2LL * halo_max) + 3LL * n_max;   // Y ring, P, z32 (floats)
+    return nd + (nf + 1) / 2 + 64;
+}
+
+struct BScalars {
+    double r0, nu, coef_old, theta_t, c_prev, s_prev, delta_prev, G;
+    double nu_p, delta_pp, theta_p, xcoef_p;
+    double fin_nu, fin_delta, fin_theta, fin_xcoef;
+    double ratio;
+    int its, stop;
+};
+
+struct BatchShared {
+    BatchMat M;
+    double red[BKPMAX + 1];
+    double wsum[BMAX_WARPS][BKPMAX + 1];
+    double tmp[BMAX_WARPS + 1];
+    float u[BKPMAX];
+    float cf[12];
+    double alpha[BKPMAX];
+    int off[64];
+    double H[(BATCH_RMAX + 1) * BATCH_RMAX];
+    double cs[BATCH_RMAX + 1], sn[BATCH_RMAX + 1], g[BATCH_RMAX + 2], hv[BATCH_RMAX + 1], hv2[BATCH_RMAX + 1],
+        yv[BATCH_RMAX + 1];
+    double wv[BMMAX];
+    BScalars sc;
+    int item;
+    int steps;
+    int brk;
+};
+
+// sum over the block of one double per thread; every thread gets the result
+__device__ __forceinline__ double bsum(double v, BatchShared& sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh.tmp[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        double t = lane < nw ? sh.tmp[lane] : 0.0;
+        t = warp_sum(t);
+        if (lane == 0) sh.tmp[BMAX_WARPS] = t;
+    }
+    __syncthreads();
+    return sh.tmp[BMAX_WARPS];
+}
+
+__device__ __forceinline__ double bdot(const double* a, const double* b, int n, BatchShared& sh) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += a[i] * b[i];
+    return bsum(acc, sh);
+}
+
+// y = A x for a CSR matrix, one row per thread (rows strided over the block)
+__device__ __forceinline__ void bspmv(const int* rp, const int* ci, const double* v, const double* x, double* y,
+                                      int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double s = 0.0;
+        for (int e = rp[i]; e < rp[i + 1]; ++e) s += v[e] * x[ci[e]];
+        y[i] = s;
+    }
+    __syncthreads();
+}
+
+template <int KP, bool QB>
+__device__ __forceinline__ void bq_row(const BatchMat& M, int i, float (&q)[KP > 0 ? KP : 1]) {
+    if constexpr (KP > 0) {
+        if constexpr (QB) {
+            const uint4* row = reinterpret_cast<const uint4*>(reinterpret_cast<const __nv_bfloat16*>(M.Q16) +
+                                                             (size_t)i * KP);
+#pragma unroll
+            for (int t = 0; t < KP / 8; ++t) {
+                uint4 v = __ldg(row + t);
+                const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    float2 f = __bfloat1622float2(h2[e]);
+                    q[8 * t + 2 * e] = f.x;
+                    q[8 * t + 2 * e + 1] = f.y;
+                }
+            }
+        } else {
+            const float4* row = reinterpret_cast<const float4*>(M.Q32 + (size_t)i * KP);
+#pragma unroll
+            for (int t = 0; t < KP / 4; ++t) {
+                float4 v = __ldg(row + t);
+                q[4 * t] = v.x;
+                q[4 * t + 1] = v.y;
+                q[4 * t + 2] = v.z;
+                q[4 * t + 3] = v.w;
+            }
+        }
+    }
+}
+
+// block reduction of the KP+1 per-thread sums of an mrs step into sh.red (FP64)
+template <int KP>
+__device__ __forceinline__ void bred(float (&tacc)[KP + 1], BatchShared& sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int v = 0; v <= KP; ++v) {
+        float d = warp_sum(tacc[v]);
+        if (lane == 0) sh.wsum[warp][v] = (double)d;
+    }
+    __syncthreads();
+    for (int v = threadIdx.x; v <= KP; v += blockDim.x) {
+        double t = 0.0;
+        for (int w = 0; w < nw; ++w) t += sh.wsum[w][v];
+        sh.red[v] = t;
+    }
+    __syncthreads();
+}
+
+template <int KP>
+__device__ __forceinline__ void bmake_u(const BatchMat& M, BatchShared& sh) {
+    for (int m = threadIdx.x; m < KP; m += blockDim.x) {
+        double u = 0.0;
+        if (m < M.k) {
+            if (m + 1 < M.k) u += sh.alpha[m] * sh.red[2 + m] * sh.sc.nu;
+            if (m > 0) u -= sh.alpha[m - 1] * sh.red[m] * sh.sc.nu;
+        }
+        sh.u[m] = (float)u;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void bset_coefs(BatchShared& sh) {
+    BScalars& c = sh.sc;
+    sh.cf[0] = (float)c.nu;
+    sh.cf[2] = (float)c.coef_old;
+    sh.cf[3] = (float)c.nu_p;
+    sh.cf[4] = (float)c.delta_pp;
+    sh.cf[5] = (float)(1.0 / c.theta_p);
+    sh.cf[6] = (float)c.xcoef_p;
+    if (c.stop) {
+        sh.cf[7] = (float)c.fin_nu;
+        sh.cf[8] = (float)c.fin_delta;
+        sh.cf[9] = (float)(1.0 / c.fin_theta);
+        sh.cf[10] = (float)c.fin_xcoef;
+    }
+}
+
+// mrs (App. B) in block scope on (I + J_bar) z = u, J_bar = J~ - Q S_k Q^T, FP32 vectors;
+// z in FP32, Q^T z of the final iterate into sh.wv[0..k); returns the step count.
+template <int KP, bool QB>
+__device__ int bmrs(const double* u, float* z, float* Y, long long ys, float* P, double tol, int maxit,
+                    BatchShared& sh) {
+    const BatchMat& M = sh.M;
+    const int n = M.n;
+    const int h = M.halo;
+    // zero this matrix's halo band of every slot (the workspace is shared by items)
+    for (int t = threadIdx.x; t < 6 * h; t += blockDim.x) {
+        int slot = t / (2 * h), e = t % (2 * h);
+        int idx = e < h ? -h + e : n + (e - h);
+        Y[slot * ys + idx] = 0.f;
+    }
+    float tacc[KP + 1];
+#pragma unroll
+    for (int v = 0; v <= KP; ++v) tacc[v] = 0.f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        float b = (float)u[i];
+        Y[i] = b;
+        z[i] = 0.f;
+        P[i] = 0.f;
+        P[n + i] = 0.f;
+        tacc[0] += b * b;
+        float q[KP > 0 ? KP : 1];
+        bq_row<KP, QB>(M, i, q);
+#pragma unroll
+        for (int m = 0; m < KP; ++m) tacc[1 + m] += q[m] * b;
+    }
+    bred<KP>(tacc, sh);
+    if (threadIdx.x == 0) {
+        BScalars& c = sh.sc;
+        double r0 = sqrt(sh.red[0]);
+        c.r0 = r0;
+        c.nu = r0 > 0.0 ? 1.0 / r0 : 0.0;
+        c.coef_old = 0.0;
+        c.theta_t = 1.0;
+        c.c_prev = 1.0;
+        c.s_prev = 0.0;
+        c.delta_prev = 0.0;
+        c.G = r0;
+        c.nu_p = 0.0;
+        c.delta_pp = 0.0;
+        c.theta_p = 1.0;
+        c.xcoef_p = 0.0;
+        c.ratio = 0.0;
+        c.its = 0;
+        c.stop = r0 > 0.0 ? 0 : 1;
+        bset_coefs(sh);
+    }
+    __syncthreads();
+    if (sh.sc.stop) {
+        for (int v = threadIdx.x; v < M.k; v += blockDim.x) sh.wv[v] = 0.0;
+        __syncthreads();
+        return 0;
+    }
+    bmake_u<KP>(M, sh);
+    for (int j = 1; j <= maxit; ++j) {
+        float* Ycur = Y + (size_t)((j - 1) % 3) * ys;
+        float* Yold = Y + (size_t)((j + 1) % 3) * ys;
+        float* Ynew = Y + (size_t)(j % 3) * ys;
+        float* Pj1 = P + (size_t)((j - 1) & 1) * n;
+        const float tnu = sh.cf[0], tco = sh.cf[2], tnp = sh.cf[3], tdpp = sh.cf[4], tthp = sh.cf[5],
+                    txp = sh.cf[6];
+#pragma unroll
+        for (int v = 0; v <= KP; ++v) tacc[v] = 0.f;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const float yold = j >= 2 ? Yold[i] : 0.f;
+            const float pold = j >= 2 ? Pj1[i] : 0.f;
+            float acc = 0.f;
+            const float* Ud = M.U + i;
+            const float* yi = Ycur + i;
+            for (int d = 0; d < M.ndiag; ++d, Ud += M.ustride) {
+                const int m = sh.off[d];
+                acc += __ldg(Ud) * yi[m] - __ldg(Ud - m) * yi[-m];
+            }
+            float q[KP > 0 ? KP : 1];
+            bq_row<KP, QB>(M, i, q);
+            float dq = 0.f;
+#pragma unroll
+            for (int m = 0; m < KP; ++m) dq += q[m] * sh.u[m];
+            const float ynew = tnu * acc - dq + tco * yold;
+            Ynew[i] = ynew;
+            tacc[0] += ynew * ynew;
+#pragma unroll
+            for (int m = 0; m < KP; ++m) tacc[1 + m] += q[m] * ynew;
+            if (j >= 2) {
+                float pv = (tnp * yold - tdpp * pold) * tthp;
+                Pj1[i] = pv;
+                z[i] += txp * pv;
+            }
+        }
+        bred<KP>(tacc, sh);
+        if (threadIdx.x == 0) {
+            BScalars& c = sh.sc;
+            const double beta = sqrt(sh.red[0]);
+            const double theta = sqrt(c.theta_t * c.theta_t + beta * beta);
+            const double cc = c.theta_t / theta, s = beta / theta;
+            const double delta = -c.s_prev * beta;
+            const double theta_t_next = c.c_prev * theta;
+            const double xcoef = c.G * cc;
+            const double Gn = -c.G * s;
+            c.ratio = fabs(Gn) / c.r0;
+            c.its = j;
+            if (c.ratio < tol || j == maxit) {
+                c.stop = 1;
+                c.fin_nu = c.nu;
+                c.fin_delta = c.delta_prev;
+                c.fin_theta = theta;
+                c.fin_xcoef = xcoef;
+            } else {
+                c.nu_p = c.nu;
+                c.delta_pp = c.delta_prev;
+                c.theta_p = theta;
+                c.xcoef_p = xcoef;
+                c.coef_old = beta * c.nu;
+                c.nu = (beta != 0.0) ? 1.0 / beta : 0.0;
+                c.s_prev = s;
+                c.c_prev = cc;
+                c.delta_prev = delta;
+                c.theta_t = theta_t_next;
+                c.G = Gn;
+            }
+            bset_coefs(sh);
+        }
+        __syncthreads();
+        if (sh.sc.stop) {
+            float* Pj = P + (size_t)(j & 1) * n;
+            const float tn = sh.cf[7], td = sh.cf[8], tth = sh.cf[9], tx = sh.cf[10];
+#pragma unroll
+            for (int v = 0; v <= KP; ++v) tacc[v] = 0.f;
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                float pv = (tn * Ycur[i] - td * Pj[i]) * tth;
+                float xi = z[i] + tx * pv;
+                z[i] = xi;
+                float q[KP > 0 ? KP : 1];
+                bq_row<KP, QB>(M, i, q);
+#pragma unroll
+                for (int m = 0; m < KP; ++m) tacc[1 + m] += q[m] * xi;
+            }
+            bred<KP>(tacc, sh);
+            for (int v = threadIdx.x; v < M.k; v += blockDim.x) sh.wv[v] = sh.red[1 + v];
+            __syncthreads();
+            return sh.sc.its;
+        }
+        bmake_u<KP>(M, sh);
+    }
+    return sh.sc.its;
+}
+
+template <int KP, bool QB, int NT>
+__global__ void __launch_bounds__(NT, 1) k_batch(BatchLaunch L) {
+    __shared__ BatchShared sh;
+    const int R = L.restart;
+    const long long nm = L.n_max;
+    double* base = L.work + (size_t)blockIdx.x * (size_t)L.work_stride;
+    double* r = base;
+    double* rh = r + nm;
+    double* dy = rh + nm;
+    double* t1 = dy + nm;
+    double* t2 = t1 + nm;
+    double* V = t2 + nm;              // R+1 vectors
+    double* Z = V + (R + 1) * nm;     // R vectors
+    float* fb = reinterpret_cast<float*>(Z + R * nm);
+    const long long ys = nm + 2LL * L.halo_max;
+    float* Y = fb + L.halo_max;
+    float* P = fb + 3 * ys;
+    float* z32 = P + 2 * nm;
+
+    while (true) {
+        if (threadIdx.x == 0) sh.item = (int)atomicAdd(L.next_item, 1u);
+        __syncthreads();
+        const int it = sh.item;
+        if (it >= L.nitems) break;
+        const int2 mc = L.items[it];
+        if (threadIdx.x == 0) sh.M = L.mats[mc.x];
+        __syncthreads();
+        const BatchMat& M = sh.M;
+        const int n = M.n;
+        for (int d = threadIdx.x; d < M.ndiag && d < 64; d += blockDim.x) sh.off[d] = M.off[d];
+        for (int a = threadIdx.x; a + 1 < M.k && a < BKPMAX; a += blockDim.x) sh.alpha[a] = M.alpha[a];
+        const double* bcol = L.b + L.row_off[mc.x] * L.nrhs + (long long)mc.y * n;
+        double* xcol = L.x + L.row_off[mc.x] * L.nrhs + (long long)mc.y * n;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            xcol[i] = 0.0;
+            r[i] = bcol[i];
+        }
+        __syncthreads();
+        const double bn = sqrt(bdot(bcol, bcol, n, sh));
+        int outer = 0, inner = 0, cycles = 0, status = ASSS_OK, stall = 0;
+        double best = INFINITY, relres = 0.0;
+        while (bn > 0.0) {
+            const double rn = sqrt(bdot(r, r, n, sh));
+            relres = rn / bn;
+            if (relres <= L.outer_tol) break;
+            if (!(rn == rn)) {
+                status = ASSS_ERR_BREAKDOWN;
+                break;
+            }
+            if (outer >= L.outer_maxit) {
+                status = ASSS_ERR_NOT_CONVERGED;
+                break;
+            }
+            if (rn < 0.999 * best) {
+                best = rn;
+                stall = 0;
+            } else if (++stall >= 5) {
+                status = ASSS_ERR_STAGNATION;
+                break;
+            }
+            // r^ = W P D_r r
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                int p = M.perm ? M.perm[i] : i;
+                rh[i] = M.w[i] * M.dr[p] * r[p];
+            }
+            __syncthreads();
+            const double eta = fmin(0.5, 0.5 * L.outer_tol * bn / rn);
+            int mcyc = R < L.outer_maxit - outer ? R : L.outer_maxit - outer;
+            // ---- one flexible GMRES cycle on A_cal dy = r^ ----
+            const double beta0 = sqrt(bdot(rh, rh, n, sh));
+            if (!(beta0 > 0.0)) {
+                status = ASSS_ERR_BREAKDOWN;
+                break;
+            }
+            for (int i = threadIdx.x; i < n; i += blockDim.x) V[i] = rh[i] / beta0;
+            if (threadIdx.x == 0) {
+                for (int a = 0; a <= R + 1; ++a) sh.g[a] = 0.0;
+                sh.g[0] = beta0;
+                sh.steps = 0;
+            }
+            __syncthreads();
+            for (int j = 0; j < mcyc; ++j) {
+                double* vj = V + j * nm;
+                double* zj = Z + j * nm;
+                // z_j = P^-1 v_j: mrs, then z - Y (U^T z)
+                inner += bmrs<KP, QB>(vj, z32, Y, ys, P, L.inner_tol, L.inner_maxit, sh);
+                for (int a = threadIdx.x; a < M.r; a += blockDim.x) sh.wv[M.k + a] = (double)z32[M.neg[a]];
+                __syncthreads();
+                for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                    double acc = 0.0;
+                    const float* yr = M.Y32 + (size_t)i * M.m;
+                    for (int c = 0; c < M.m; ++c) acc += (double)yr[c] * sh.wv[c];
+                    zj[i] = (double)z32[i] - acc;
+                }
+                __syncthreads();
+                // w = A_cal z_j = (W Abar) (S W) z_j, into t2
+                bspmv(M.swrp, M.swci, M.swv, zj, t1, n);
+                bspmv(M.awrp, M.awci, M.awv, t1, t2, n);
+                // two classical Gram-Schmidt passes
+                for (int pass = 0; pass < 2; ++pass) {
+                    for (int a = 0; a <= j; ++a) {
+                        double hva = bdot(V + a * nm, t2, n, sh);
+                        if (threadIdx.x == 0) (pass == 0 ? sh.hv : sh.hv2)[a] = hva;
+                    }
+                    __syncthreads();
+                    const double* hh = pass == 0 ? sh.hv : sh.hv2;
+                    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                        double acc = 0.0;
+                        for (int a = 0; a <= j; ++a) acc += V[a * nm + i] * hh[a];
+                        t2[i] -= acc;
+                    }
+                    __syncthreads();
+                }
+                const double hn = sqrt(bdot(t2, t2, n, sh));
+                if (threadIdx.x == 0) {
+                    double* col = sh.H + j * (R + 1);
+                    for (int a = 0; a <= j; ++a) col[a] = sh.hv[a] + sh.hv2[a];
+                    col[j + 1] = hn;
+                    for (int a = 0; a < j; ++a) {
+                        double tq = sh.cs[a] * col[a] + sh.sn[a] * col[a + 1];
+                        col[a + 1] = -sh.sn[a] * col[a] + sh.cs[a] * col[a + 1];
+                        col[a] = tq;
+                    }
+                    double rr = hypot(col[j], col[j + 1]);
+                    double c = rr != 0.0 ? col[j] / rr : 1.0;
+                    double s = rr != 0.0 ? col[j + 1] / rr : 0.0;
+                    sh.cs[j] = c;
+                    sh.sn[j] = s;
+                    col[j] = rr;
+                    col[j + 1] = 0.0;
+                    sh.g[j + 1] = -s * sh.g[j];
+                    sh.g[j] = c * sh.g[j];
+                    sh.steps = j + 1;
+                    sh.brk = (hn == 0.0 || fabs(sh.g[j + 1]) <= eta * beta0) ? 1 : 0;
+                }
+                __syncthreads();
+                if (sh.brk) break;
+                for (int i = threadIdx.x; i < n; i += blockDim.x) V[(j + 1) * nm + i] = t2[i] / hn;
+                __syncthreads();
+            }
+            const int steps = sh.steps;
+            if (threadIdx.x == 0) {
+                for (int a = steps - 1; a >= 0; --a) {
+                    double acc = sh.g[a];
+                    for (int bq = a + 1; bq < steps; ++bq) acc -= sh.H[bq * (R + 1) + a] * sh.yv[bq];
+                    sh.yv[a] = acc / sh.H[a * (R + 1) + a];
+                }
+            }
+            __syncthreads();
+            // x += D_c S W dy,  dy = Z y
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                double acc = 0.0;
+                for (int a = 0; a < steps; ++a) acc += Z[a * nm + i] * sh.yv[a];
+                dy[i] = acc;
+                t1[i] = M.w[i] * acc;
+            }
+            __syncthreads();
+            bspmv(M.srp, M.sci, M.sv, t1, t2, n);
+            for (int i = threadIdx.x; i < n; i += blockDim.x) xcol[i] += M.dc[i] * t2[i];
+            __syncthreads();
+            bspmv(M.arp, M.aci, M.av, xcol, t1, n);
+            for (int i = threadIdx.x; i < n; i += blockDim.x) r[i] = bcol[i] - t1[i];
+            __syncthreads();
+            outer += steps;
+            ++cycles;
+        }
+        if (threadIdx.x == 0) {
+            BatchItemStat st;
+            st.outer_its = outer;
+            st.inner_its = inner;
+            st.status = status;
+            st.cycles = cycles;
+            st.relres = relres;
+            L.stats[it] = st;
+        }
+        __syncthreads();
+    }
+}
+
+template <int KP, bool QB>
+static asss_status launch_nt(const BatchLaunch& L, int nthreads, int nblk, cudaStream_t s) {
+    switch (nthreads) {
+        case 256:
+            k_batch<KP, QB, 256><<<nblk, 256, 0, s>>>(L);
+            break;
+        case 512:
+            k_batch<KP, QB, 512><<<nblk, 512, 0, s>>>(L);
+            break;
+        case 1024:
+            k_batch<KP, QB, 1024><<<nblk, 1024, 0, s>>>(L);
+            break;
+        default:
+            set_error("batched solver: unsupported CTA size %d", nthreads);
+            return ASSS_ERR_ARG;
+    }
+    ASSS_CHECK_LAUNCH();
+    return ASSS_OK;
+}
+
+template <int KP, bool QB>
+static asss_status occ_nt(int nthreads, int* occ) {
+    switch (nthreads) {
+        case 256:
+            ASSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_batch<KP, QB, 256>, 256, 0));
+            return ASSS_OK;
+        case 512:
+            ASSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_batch<KP, QB, 512>, 512, 0));
+            return ASSS_OK;
+        case 1024:
+            ASSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_batch<KP, QB, 1024>, 1024, 0));
+            return ASSS_OK;
+    }
+    set_error("batched solver: unsupported CTA size %d", nthreads);
+    return ASSS_ERR_ARG;
+}
+
+#define ASSS_BATCH_DISPATCH(FN, ...)                                                     \
+    switch (kp * 2 + (qbf16 ? 1 : 0)) {                                                  \
+        case 0 * 2: return FN<0, false>(__VA_ARGS__);                                    \
+        case 8 * 2: return FN<8, false>(__VA_ARGS__);                                    \
+        case 16 * 2: return FN<16, false>(__VA_ARGS__);                                  \
+        case 20 * 2: return FN<20, false>(__VA_ARGS__);                                  \
+        case 24 * 2: return FN<24, false>(__VA_ARGS__);                                  \
+        case 32 * 2: return FN<32, false>(__VA_ARGS__);                                  \
+        case 8 * 2 + 1: return FN<8, true>(__VA_ARGS__);                                 \
+        case 16 * 2 + 1: return FN<16, true>(__VA_ARGS__);                               \
+        case 24 * 2 + 1: return FN<24, true>(__VA_ARGS__);                               \
+        case 32 * 2 + 1: return FN<32, true>(__VA_ARGS__);                               \
+        default:                                                                         \
+            set_error("batched solver: unsupported Lanczos width %d (bf16 %d)", kp, qbf16); \
+            return ASSS_ERR_UNSUPPORTED;                                                 \
+    }
+
+asss_status batch_launch(const BatchLaunch& L, int nthreads, int nblk, cudaStream_t s) {
+    const int kp = L.kp, qbf16 = L.qbf16;
+    ASSS_BATCH_DISPATCH(launch_nt, L, nthreads, nblk, s)
+}
+
+asss_status batch_occupancy(int kp, int qbf16, int nthreads, int* occ) {
+    ASSS_BATCH_DISPATCH(occ_nt, nthreads, occ)
+}
+
+}  // namespace asss

@@ -113,4 +113,68 @@ asss_status lls_fit(const Ctx& c, const DCsr& Abar, const DCsr& AbarT, const DCs
 asss_status lls_product_on_pattern(const Ctx& c, const DCsr& Abar, const DCsr& ST, const int* st_src,
                                    const double* s_val, const DCsr& P, const int* prow, double* Cval);
 
+// batch.cu: one matrix of a batched solve, as device pointers into its handle
+struct BatchMat {
+    int n;
+    int k;           // Lanczos vectors
+    int m;           // k + r (SMW rank)
+    int r;
+    int ndiag;       // skew diagonals of J~
+    int halo;        // largest diagonal offset
+    long long ustride;
+    const int* off;  // ndiag offsets
+    const float* U;  // J~ diagonals (FP32), diagonal d at U + d*ustride, entries [-halo, n)
+    const float* Q32;               // n x kp row-major (or null)
+    const void* Q16;                // BF16 n x kp row-major (or null)
+    const double* alpha;            // k-1
+    const float* Y32;               // SMW data, n x m row-major
+    const int* neg;                 // r indices
+    const int *arp, *aci;           // A (original) for the residual
+    const double* av;
+    const int *awrp, *awci;         // W Abar
+    const double* awv;
+    const int *swrp, *swci;         // S W
+    const double* swv;
+    const int *srp, *sci;           // S
+    const double* sv;
+    const double *dr, *dc, *w;
+    const int* perm;                // row permutation or null
+};
+
+struct BatchItemStat {
+    int outer_its;
+    int inner_its;
+    int status;
+    int cycles;
+    double relres;
+};
+
+struct BatchLaunch {
+    const BatchMat* mats;
+    const int2* items;          // (matrix, column), largest matrices first
+    int nitems;
+    int nrhs;
+    const long long* row_off;   // first row of each matrix in the concatenated vectors
+    const double* b;            // concatenated right-hand sides, matrix m at row_off[m]*nrhs, n_m x nrhs
+    double* x;
+    double* work;               // per-CTA workspace
+    long long work_stride;      // doubles per CTA
+    int n_max, halo_max;
+    int kp, qbf16;              // common padded Lanczos width and Q storage of the batch
+    int restart;
+    double outer_tol;
+    int outer_maxit;
+    double inner_tol;
+    int inner_maxit;
+    unsigned* next_item;
+    BatchItemStat* stats;
+};
+
+// launches the persistent batched solver on stream s with nthreads per CTA and nblk CTAs
+asss_status batch_launch(const BatchLaunch& L, int nthreads, int nblk, cudaStream_t s);
+// resident CTAs per SM of the batched solver for a CTA size
+asss_status batch_occupancy(int kp, int qbf16, int nthreads, int* occ);
+constexpr int BATCH_RMAX = 24;    // restart length bound of the batched FGMRES
+long long batch_work_doubles(int n_max, int halo_max, int restart);
+
 }  // namespace asss
