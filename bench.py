@@ -33,6 +33,10 @@ WORKLOAD = ("dh3d_100: dissipative-Hamiltonian implicit-Euler step A = E + h(R -
             "(tol 1e-6) / FP64 outer FGMRES(60), outer tol 1e-8")
 SIDE = 100
 CPU_SAMPLE_SIDE = 24
+BATCH = {"count": 256, "side_lo": 10, "side_hi": 40, "nrhs": 32, "seed": 3}
+BATCH_WORKLOAD = ("batched_dh: 256 dissipative-Hamiltonian systems, 3D grids of sides 10..40 (n = 1e3..6.4e4, "
+                  "seeded), 32 right-hand sides ~ N(0,1) each (8192 solves per step), one persistent launch "
+                  "replayed from a CUDA graph, FP32 inner mrs (tol 1e-6) / FP64 outer FGMRES(24), outer tol 1e-8")
 
 
 def _peaks():
@@ -57,6 +61,64 @@ def _make_rhs(A_parts, n, seed, count):
 # ----------------------------------------------------------------------------
 # CPU oracle baseline (subprocess, one thread)
 # ----------------------------------------------------------------------------
+def batched_worker(budget_s):
+    """Oracle solves of a bounded sample of the batched workload's items."""
+    import numpy as np
+
+    import oracle
+    from workloads import batched_dissipative_hamiltonian
+    batch = batched_dissipative_hamiltonian(**BATCH)
+    order = np.argsort([A.shape[0] for A, _ in batch])
+    solves, secs, rows, t_setup, relres = 0, 0.0, 0, 0.0, 0.0
+    t_start = time.perf_counter()
+    for m in order[::max(1, len(order) // 16)]:
+        A, B = batch[m]
+        t0 = time.perf_counter()
+        o = oracle.AsssOracle(A, inner_tol=1e-6)
+        t_setup += time.perf_counter() - t0
+        for c in range(2):
+            t = time.perf_counter()
+            _, st = o.solve(B[:, c], tol=1e-8, outer="fgmres")
+            secs += time.perf_counter() - t
+            solves += 1
+            rows += A.shape[0]
+            relres = max(relres, st["relres"])
+        if time.perf_counter() - t_start > budget_s:
+            break
+    print(json.dumps({"solves": solves, "seconds": secs, "rows": rows, "t_setup_s": t_setup,
+                      "max_relres": relres}))
+
+
+def batch_mean_n():
+    """Mean system size of the batched workload (its sides drawn as the generator does)."""
+    import numpy as np
+    rng = np.random.default_rng(BATCH["seed"])
+    sides = rng.integers(BATCH["side_lo"], BATCH["side_hi"] + 1, size=BATCH["count"])
+    return float(np.mean(sides.astype(np.float64) ** 3))
+
+
+def run_batched_cpu_baseline(budget_s, mean_n):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[v] = "1"
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", "--workload", "batched_dh", "--budget",
+           str(budget_s)]
+    p = subprocess.run(cmd, capture_output=True, text=True, env=env, cwd=ROOT)
+    if p.returncode != 0:
+        raise RuntimeError("CPU baseline worker failed:\n" + p.stdout + p.stderr)
+    r = json.loads(p.stdout.strip().splitlines()[-1])
+    per_s = r["solves"] / r["seconds"]
+    sample_n = r["rows"] / r["solves"]
+    return {
+        "value": per_s * sample_n / mean_n, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "sample": (f"FP64 numpy/scipy oracle, {r['solves']} solves (2 columns each of every 16th matrix of the "
+                   f"batch by size, mean n = {sample_n:.0f}) in {r['seconds']:.2f} s ({per_s:.3f} solves/s), "
+                   f"scaled to the batch's mean n = {mean_n:.0f} by unknowns; set-up {r['t_setup_s']:.1f} s "
+                   f"untimed"),
+        "max_relres": r["max_relres"],
+    }
+
+
 def cpu_worker(side, steps, warmup, budget_s):
     import numpy as np
 
@@ -207,6 +269,121 @@ def aggregate_rate(world, steps, max_seconds):
 
 
 # ----------------------------------------------------------------------------
+# batched workload
+# ----------------------------------------------------------------------------
+def main_batched(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_2009_06954_gb300 as pkg
+    from paper_2009_06954_gb300.binding import kernel_launches
+    from workloads import batched_dissipative_hamiltonian
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    batch = batched_dissipative_hamiltonian(**dict(BATCH, seed=BATCH["seed"] + rank))
+    nrhs = BATCH["nrhs"]
+    t0 = time.perf_counter()
+    bs = pkg.BatchSolver([A for A, _ in batch], inner_tol=1e-6, outer_tol=1e-8, k=20, restart=24,
+                         q_bf16=args.q_storage == "bf16", stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    bh = bs.pack([B for _, B in batch])
+    items = len(batch) * nrhs
+    bd = torch.tensor(bh, device=dev)
+    xd = torch.empty_like(bd)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    for _ in range(args.warmup):
+        bs.solve(bd, nrhs=nrhs, x=xd)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = kernel_launches()
+    stats = []
+    with ClockSampler(dev.index) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            _, st = bs.solve(bd, nrhs=nrhs, x=xd)   # device time of the launch in t_inner_ms
+            stats.append(st)
+        torch.cuda.synchronize()
+    launches = kernel_launches() - l0
+    if dist:
+        dist.barrier()
+    total_ms = sum(s_["t_inner_ms"] for s_ in stats)
+    tmax = reduce_max(total_ms, dist, dev)
+    relres = max(s_["relres"] for s_ in stats)
+    ok = all(s_["status"] == 0 for s_ in stats) and relres <= 1e-8
+    value = world * items * args.steps / (tmax / 1000.0)
+
+    # end to end: pinned host b and x, copies inside the timed region
+    bp = torch.from_numpy(bh).pin_memory()
+    xp = torch.empty_like(bp).pin_memory()
+    e2e_s = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        bs.solve(bp, nrhs=nrhs, x=xp)
+        e2e_s += time.perf_counter() - t
+    e2e_val = world * items * args.steps / reduce_max(e2e_s, dist, dev)
+    # the result is checked on the host for one step: every item's true residual
+    X = bs.unpack(xd.cpu().numpy(), nrhs)
+    worst = 0.0
+    for (A, B), x in zip(batch, X):
+        worst = max(worst, float(np.max(np.linalg.norm(B - A @ x, axis=0) / np.linalg.norm(B, axis=0))))
+    peak, peak_kind = _peaks()
+    inner_bytes = sum(s_["inner_bytes"] for s_ in stats)
+    achieved = inner_bytes / (total_ms / 1000.0) / 1e9 if total_ms > 0 else 0.0
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    mean_n = bs.total / len(batch)
+    cpu = None
+    if not args.no_cpu_baseline:
+        try:
+            cb = run_batched_cpu_baseline(15.0, mean_n)
+            cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        except Exception as e:
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"[:300]}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32-inner/f64-outer", "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "256 MB buffer written between steps (not timed); working set > L2",
+                   "setup_s": round(t_setup, 3), "cta_threads": bs.cta_threads, "items_per_step": items,
+                   "total_rows": bs.total, "max_relres": relres, "host_checked_max_relres": worst,
+                   "converged": ok and worst <= 1e-8, "outer_its_max": stats[-1]["outer_its"],
+                   "inner_its_total": stats[-1]["inner_its_total"], "q_storage": args.q_storage},
+        "gpu_launches": int(launches),
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 8 * bs.total * nrhs,
+                "d2h_bytes_per_step": 8 * bs.total * nrhs},
+        "roofline": {"bound": "hbm", "kernel": "k_batch (persistent batched solve)", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak if peak else None,
+                     "peak_source": f"{peak_kind} hbm_gbs", "traffic": None,
+                     "algorithmic_bytes_per_launch": inner_bytes / max(len(stats), 1),
+                     "bytes_model": "inner mrs steps only (a lower bound on the launch's bytes)",
+                     "avg_launch_ms": total_ms / max(len(stats), 1), "launches": len(stats)},
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    bs.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------
 # main
 # ----------------------------------------------------------------------------
 def main():
@@ -220,24 +397,36 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--q-storage", default="f32", choices=["f32", "bf16"],
                     help="storage of the Lanczos basis read by the FP32 inner solve")
+    ap.add_argument("--workload", default="dh3d_100", choices=["dh3d_100", "batched_dh"],
+                    help="dh3d_100: one 1e6-unknown system; batched_dh: 256 systems x 32 right-hand sides")
     args = ap.parse_args()
 
     if args.cpu_worker:
-        cpu_worker(CPU_SAMPLE_SIDE, args.steps, args.warmup, args.budget)
+        if args.workload == "batched_dh":
+            batched_worker(args.budget)
+        else:
+            cpu_worker(CPU_SAMPLE_SIDE, args.steps, args.warmup, args.budget)
         return
 
     world, rank, local = rank_env()
+    if args.workload == "batched_dh" and args.impl != "reference":
+        main_batched(args, world, rank, local)
+        return
 
     if args.impl == "reference":
         if rank != 0:
             return
         warm = max(0, min(args.warmup, 1))
-        cb = run_cpu_baseline(args.steps, warm, 120.0)
+        if args.workload == "batched_dh":
+            cb = run_batched_cpu_baseline(120.0, batch_mean_n())
+        else:
+            cb = run_cpu_baseline(args.steps, warm, 120.0)
         ms = 1000.0 / cb["value"]
         line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "reference": "FP64 CPU oracle (oracle/), host cores"},
+                "config": {"workload": BATCH_WORKLOAD if args.workload == "batched_dh" else WORKLOAD,
+                           "reference": "FP64 CPU oracle (oracle/), host cores"},
                 "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
                 "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)

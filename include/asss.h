@@ -199,7 +199,9 @@ asss_status asss_setup_batched(int nmat, const asss_csr* const* A, const asss_op
  * [off_m * nrhs, (off_m + n_m) * nrhs) with off_m = n_0 + ... + n_{m-1}, column-major
  * n_m x nrhs inside.  x is overwritten.  st (may be NULL): outer_its = the largest
  * over items, inner_its_total and cycles summed, relres = the largest, inner_solves
- * = number of items, t_inner_ms = device time of the batched launch.  Returns the
+ * = number of items, t_inner_ms = device time of the batched launch, inner_bytes =
+ * the algorithmic bytes of the inner mrs steps (the one-system byte model summed
+ * over items).  Returns the
  * first non-OK item status (x then holds every item's last iterate). */
 asss_status asss_solve_batched(asss_batch* b, int nrhs, const double* rhs, double* x,
                                asss_stats* st);

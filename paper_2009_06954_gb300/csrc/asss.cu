@@ -1639,6 +1639,8 @@ struct asss_batch {
     DBuf<unsigned> counter;
     DBuf<BatchItemStat> stats;
     DBuf<int2> items;
+    std::vector<int2> items_h;
+    std::vector<double> step_bytes, call_bytes;   // mrs byte model per matrix
     int items_nrhs = -1;
     DBuf<double> bdev, xdev;
     cudaGraphExec_t gexec = nullptr;
@@ -1711,6 +1713,7 @@ static asss_status batch_items(asss_batch* B, int nrhs) {
     for (int m : order)
         for (int c = 0; c < nrhs; ++c) it.push_back(make_int2(m, c));
     ASSS_TRY(to_device(B->items, it.data(), (int64_t)it.size(), B->own));
+    B->items_h = it;
     ASSS_TRY(B->stats.alloc((int64_t)it.size()));
     B->items_nrhs = nrhs;
     if (B->gexec) {
@@ -1838,6 +1841,14 @@ asss_status asss_setup_batched(int nmat, const asss_csr* const* A, const asss_op
             s = ASSS_ERR_UNSUPPORTED;
             break;
         }
+        // algorithmic bytes of the inner solve (same model as the one-system mrs):
+        // per step the stored diagonal entries once, the Q row, y (own, old, new),
+        // p and z read and written; per call the set-up and final passes
+        {
+            double nn = h->n, qrow = h->Q16.p ? 2.0 * h->kp16 : 4.0 * h->kp;
+            B->step_bytes.push_back(4.0 * (double)h->D32.nnz + nn * (28.0 + qrow));
+            B->call_bytes.push_back(nn * (8.0 + 16.0 + qrow) + nn * 16.0 + (h->k ? nn * qrow : 0.0));
+        }
         B->n_of.push_back(h->n);
         B->off_h.push_back(rows);
         rows += h->n;
@@ -1940,7 +1951,11 @@ asss_status asss_solve_batched(asss_batch* B, int nrhs, const double* b, double*
     asss_stats a;
     memset(&a, 0, sizeof(a));
     int worst = ASSS_OK;
-    for (const BatchItemStat& t : hs) {
+    double bytes = 0.0;
+    for (size_t q = 0; q < hs.size(); ++q) {
+        const BatchItemStat& t = hs[q];
+        const int m = B->items_h[q].x;
+        bytes += t.inner_its * B->step_bytes[m] + t.outer_its * B->call_bytes[m];
         if (t.outer_its > a.outer_its) a.outer_its = t.outer_its;
         a.inner_its_total += t.inner_its;
         a.cycles += t.cycles;
@@ -1952,6 +1967,7 @@ asss_status asss_solve_batched(asss_batch* B, int nrhs, const double* b, double*
     a.status = worst;
     a.t_inner_ms = ms;   // device time of the batched launch
     a.inner_launches = 1;
+    a.inner_bytes = (long long)bytes;
     a.t_solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     a.k_eff = B->hs[0]->k;
     if (st) *st = a;
