@@ -188,9 +188,9 @@ typedef struct asss_batch asss_batch;
  * path, flexible GMRES and skew-diagonal storage of J~ (UNSUPPORTED if a J~ does
  * not fit it, if the matrices end with different Lanczos widths, or if k > 32,
  * k + r > 320 or J~ has more than 64 diagonals).  The restart length is
- * min(opt->restart, 24).  A tuner runs one synthetic batch (b = A 1) at 256, 512
- * and 1024 threads per CTA and keeps the fastest.  st (may be NULL): t_setup_ms,
- * k_eff of matrix 0, and inner_launches = the chosen CTA size. */
+ * min(opt->restart, 24).  Device scratch: (6 + 2 restart) FP64 and about 6 FP32
+ * vectors of the largest system per resident CTA.  st (may be NULL): t_setup_ms
+ * and k_eff of matrix 0. */
 asss_status asss_setup_batched(int nmat, const asss_csr* const* A, const asss_options* opt,
                                asss_batch** out, asss_stats* st);
 
@@ -202,9 +202,16 @@ asss_status asss_setup_batched(int nmat, const asss_csr* const* A, const asss_op
  * = number of items, t_inner_ms = device time of the batched launch, inner_bytes =
  * the algorithmic bytes of the inner mrs steps (the one-system byte model summed
  * over items).  Returns the
- * first non-OK item status (x then holds every item's last iterate). */
+ * first non-OK item status (x then holds every item's last iterate).  The first
+ * call for a given nrhs tunes the CTA size: it solves the batch once at each of
+ * 128, 256, 512 and 1024 threads per CTA (64 registers a thread, as many CTAs
+ * per SM as fit, at most one CTA per item) and keeps the fastest for later calls;
+ * that call takes about five times as long. */
 asss_status asss_solve_batched(asss_batch* b, int nrhs, const double* rhs, double* x,
                                asss_stats* st);
+
+/* CTA size chosen by the tuner (0 before the first solve). */
+int asss_batch_cta_threads(const asss_batch* b);
 
 void asss_destroy_batched(asss_batch* b);
 

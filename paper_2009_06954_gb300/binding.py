@@ -69,7 +69,7 @@ EXPORTED = ["asss_default_options", "asss_setup", "asss_solve", "asss_solve_adjo
             "asss_apply_operator", "asss_apply_preconditioner", "asss_export", "asss_destroy",
             "asss_status_str", "asss_last_error", "asss_skew_symmetrizer", "asss_skew_lanczos",
             "asss_mrs", "asss_kernel_launches", "asss_mrs_noalloc", "asss_setup_batched",
-            "asss_solve_batched", "asss_destroy_batched"]
+            "asss_solve_batched", "asss_destroy_batched", "asss_batch_cta_threads"]
 
 _lib = None
 _live = weakref.WeakSet()   # open handles, closed at exit while CUDA is still up
@@ -123,6 +123,8 @@ def lib():
     L.asss_solve_batched.argtypes = [P, C.c_int, P, P, pS]
     L.asss_destroy_batched.argtypes = [P]
     L.asss_destroy_batched.restype = None
+    L.asss_batch_cta_threads.argtypes = [P]
+    L.asss_batch_cta_threads.restype = C.c_int
     L.asss_kernel_launches.argtypes = []
     L.asss_kernel_launches.restype = C.c_ulonglong
     for f in ("asss_setup", "asss_solve", "asss_solve_adjoint", "asss_apply_operator",
@@ -364,8 +366,12 @@ class BatchSolver:
         _check("asss_setup_batched", status)
         self._h = h
         self.setup_stats = st.as_dict()
-        self.cta_threads = int(st.inner_launches)
         _live.add(self)
+
+    @property
+    def cta_threads(self):
+        """CTA size picked by the tuner on the first solve (0 before it)."""
+        return int(lib().asss_batch_cta_threads(self._h)) if getattr(self, "_h", None) else 0
 
     def close(self):
         if getattr(self, "_h", None):

@@ -1635,7 +1635,7 @@ struct asss_batch {
     DBuf<long long> row_off;
     DBuf<double> work;
     long long work_stride = 0;
-    int nblk = 0, nthreads = 512;
+    int nblk = 0, nthreads = 0, tuned_nrhs = -1;
     DBuf<unsigned> counter;
     DBuf<BatchItemStat> stats;
     DBuf<int2> items;
@@ -1793,6 +1793,40 @@ static asss_status batch_run(asss_batch* B, int nrhs, const double* bd, double* 
     return ASSS_OK;
 }
 
+// CTA size for a number of right-hand sides: each candidate (128 / 256 / 512 /
+// 1024 threads, as many CTAs as fit on the GPU, at most one per item) solves the
+// caller's batch once, timed with CUDA events; the fastest is kept for later calls
+static asss_status batch_tune(asss_batch* B, int nrhs, const double* bd, double* xd) {
+    const int cand[4] = {128, 256, 512, 1024};
+    const long long nitems = (long long)B->hs.size() * nrhs;
+    int best_nt = 0, best_nb = 0;
+    float best_ms = 0.f;
+    for (int c = 0; c < 4; ++c) {
+        int occ = 0;
+        ASSS_TRY(batch_occupancy(B->kp, B->qbf16, cand[c], &occ));
+        if (occ < 1) continue;
+        long long nb = (long long)B->ctx.sms * occ;
+        if (nb > nitems) nb = nitems;
+        if (B->work.n < B->work_stride * nb) ASSS_TRY(B->work.alloc(B->work_stride * nb));
+        B->nblk = (int)nb;
+        float ms = 0.f;
+        ASSS_TRY(batch_run(B, nrhs, bd, xd, cand[c], false, &ms));
+        if (!best_nt || ms < best_ms) {
+            best_nt = cand[c];
+            best_nb = (int)nb;
+            best_ms = ms;
+        }
+    }
+    if (!best_nt) {
+        set_error("batched solver: no CTA size fits on this device");
+        return ASSS_ERR_UNSUPPORTED;
+    }
+    B->nthreads = best_nt;
+    B->nblk = best_nb;
+    B->tuned_nrhs = nrhs;
+    return ASSS_OK;
+}
+
 extern "C" {
 
 asss_status asss_setup_batched(int nmat, const asss_csr* const* A, const asss_options* opt, asss_batch** out,
@@ -1861,45 +1895,7 @@ asss_status asss_setup_batched(int nmat, const asss_csr* const* A, const asss_op
         if (s == ASSS_OK) s = to_device(B->row_off, B->off_h.data(), nmat, B->own);
         if (s == ASSS_OK) s = B->counter.alloc(1);
     }
-    // CTA size: pick the fastest of 256 / 512 / 1024 threads on a synthetic batch
-    // (b = A 1 for every matrix, one column), timed with CUDA events
-    if (s == ASSS_OK) {
-        B->work_stride = batch_work_doubles(B->n_max, B->halo_max, B->restart);
-        int best_nt = 0;
-        float best_ms = 0.f;
-        DBuf<double> bt, xt, ones;
-        if ((s = bt.alloc(rows)) == ASSS_OK && (s = xt.alloc(rows)) == ASSS_OK && (s = ones.alloc(B->n_max)) == ASSS_OK)
-            s = vfill(ones.p, 1.0, B->n_max, B->own);
-        for (int m = 0; m < nmat && s == ASSS_OK; ++m) s = spmv(B->hs[m]->A, ones.p, bt.p + B->off_h[m], nullptr, B->own);
-        const int cand[3] = {256, 512, 1024};
-        for (int c = 0; c < 3 && s == ASSS_OK; ++c) {
-            int occ = 0;
-            s = batch_occupancy(B->kp, B->qbf16, cand[c], &occ);
-            if (s != ASSS_OK || occ < 1) continue;
-            int nb = B->ctx.sms * (occ < 2 ? occ : 2);
-            if (nb > B->nblk) {
-                B->nblk = nb;
-                s = B->work.alloc(B->work_stride * (long long)nb);
-                if (s != ASSS_OK) break;
-            }
-            int keep = B->nblk;
-            B->nblk = nb;
-            float ms = 0.f;
-            s = batch_run(B, 1, bt.p, xt.p, cand[c], false, &ms);
-            B->nblk = keep;
-            if (s != ASSS_OK) break;
-            if (!best_nt || ms < best_ms) {
-                best_nt = cand[c];
-                best_ms = ms;
-            }
-        }
-        if (s == ASSS_OK) {
-            int occ = 0;
-            s = batch_occupancy(B->kp, B->qbf16, best_nt, &occ);
-            B->nthreads = best_nt;
-            B->nblk = B->ctx.sms * (occ < 2 ? occ : 2);
-        }
-    }
+    if (s == ASSS_OK) B->work_stride = batch_work_doubles(B->n_max, B->halo_max, B->restart);
     if (s != ASSS_OK) {
         if (B->own) cudaStreamSynchronize(B->own);
         delete B;
@@ -1913,7 +1909,6 @@ asss_status asss_setup_batched(int nmat, const asss_csr* const* A, const asss_op
         memset(st, 0, sizeof(*st));
         st->k_eff = B->hs[0]->k;
         st->t_setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-        st->inner_launches = B->nthreads;  // CTA size chosen by the tuner
     }
     *out = B;
     return ASSS_OK;
@@ -1941,6 +1936,7 @@ asss_status asss_solve_batched(asss_batch* B, int nrhs, const double* b, double*
         if (B->xdev.n < total) ASSS_TRY(B->xdev.alloc(total));
         xd = B->xdev.p;
     }
+    if (B->tuned_nrhs != nrhs) ASSS_TRY(batch_tune(B, nrhs, bd, xd));
     float ms = 0.f;
     ASSS_TRY(batch_run(B, nrhs, bd, xd, B->nthreads, true, &ms));
     if (!xdv) ASSS_CUDA(cudaMemcpyAsync(x, xd, sizeof(double) * total, cudaMemcpyDeviceToHost, B->own));
@@ -1974,6 +1970,8 @@ asss_status asss_solve_batched(asss_batch* B, int nrhs, const double* b, double*
     if (worst != ASSS_OK) set_error("batched solve: an item ended with status %d", worst);
     return (asss_status)worst;
 }
+
+int asss_batch_cta_threads(const asss_batch* B) { return B ? B->nthreads : 0; }
 
 void asss_destroy_batched(asss_batch* B) {
     if (!B) return;

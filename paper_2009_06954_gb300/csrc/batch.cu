@@ -313,8 +313,11 @@ __device__ int bmrs(const double* u, float* z, float* Y, long long ys, float* P,
     return sh.sc.its;
 }
 
+// 64 registers a thread at every CTA size: 1024 threads per SM in 1024 / NT
+// resident CTAs, so that while one CTA waits in a block reduction the others
+// keep loads in flight
 template <int KP, bool QB, int NT>
-__global__ void __launch_bounds__(NT, 1) k_batch(BatchLaunch L) {
+__global__ void __launch_bounds__(NT, 1024 / NT) k_batch(BatchLaunch L) {
     __shared__ BatchShared sh;
     const int R = L.restart;
     const long long nm = L.n_max;
@@ -495,6 +498,9 @@ __global__ void __launch_bounds__(NT, 1) k_batch(BatchLaunch L) {
 template <int KP, bool QB>
 static asss_status launch_nt(const BatchLaunch& L, int nthreads, int nblk, cudaStream_t s) {
     switch (nthreads) {
+        case 128:
+            k_batch<KP, QB, 128><<<nblk, 128, 0, s>>>(L);
+            break;
         case 256:
             k_batch<KP, QB, 256><<<nblk, 256, 0, s>>>(L);
             break;
@@ -515,6 +521,9 @@ static asss_status launch_nt(const BatchLaunch& L, int nthreads, int nblk, cudaS
 template <int KP, bool QB>
 static asss_status occ_nt(int nthreads, int* occ) {
     switch (nthreads) {
+        case 128:
+            ASSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_batch<KP, QB, 128>, 128, 0));
+            return ASSS_OK;
         case 256:
             ASSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_batch<KP, QB, 256>, 256, 0));
             return ASSS_OK;
