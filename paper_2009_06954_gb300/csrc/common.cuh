@@ -174,6 +174,31 @@ __device__ __forceinline__ void grid_sync(const GridBarrier& gb, unsigned nblock
     __syncthreads();
 }
 
+// Grid barrier on a counter that only grows during a launch (set to 0 before it):
+// barrier number `phase` (0-based) is complete once the counter reaches
+// (phase + 1) * nblocks.  One atomic per block and no reset on the critical path;
+// the last block to arrive does not wait.  Waits are bounded like grid_sync.
+__device__ __forceinline__ void grid_sync_phase(const GridBarrier& gb, unsigned nblocks, unsigned phase,
+                                                long long budget) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned target = (phase + 1u) * nblocks;
+        __threadfence();
+        const unsigned arrived = atomicAdd(gb.count, 1u) + 1u;
+        if (arrived != target) {
+            long long t0 = clock64();
+            while ((int)(ld_acquire(gb.count) - target) < 0) {
+                if (clock64() - t0 > budget) {
+                    atomicExch(gb.err, (int)ASSS_ERR_TIMEOUT);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // host helpers shared by the translation units
 // ---------------------------------------------------------------------------

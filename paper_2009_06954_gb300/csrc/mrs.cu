@@ -224,10 +224,10 @@ __device__ __forceinline__ float2 df_add(float2 a, float2 b) {
 // thread per block (FP64 is slow on this part; every block computes the same
 // values from the same reduced sums, so all blocks agree bit for bit).
 struct MrsScalars {
-    double r0, nu, coef_old, theta_t, c_prev, s_prev, delta_prev, G;
-    double nu_p, delta_pp, theta_p, xcoef_p;
+    double r0, rr0, nu, coef_old, theta_t, c_prev, s_prev, delta_prev, G;
+    double nu_p, delta_pp, rtheta_p, xcoef_p;   // rtheta_p = 1 / theta of the previous step
     // final-pass coefficients when the iteration stops
-    double fin_nu, fin_delta, fin_theta, fin_xcoef;
+    double fin_nu, fin_delta, fin_rtheta, fin_xcoef;
     double ratio;
     int its, stop;
 };
@@ -294,12 +294,12 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
         s_cf[2] = (T)sc.coef_old;
         s_cf[3] = (T)sc.nu_p;
         s_cf[4] = (T)sc.delta_pp;
-        s_cf[5] = (T)(1.0 / sc.theta_p);
+        s_cf[5] = (T)sc.rtheta_p;
         s_cf[6] = (T)sc.xcoef_p;
         if (sc.stop) {
             s_cf[7] = (T)sc.fin_nu;
             s_cf[8] = (T)sc.fin_delta;
-            s_cf[9] = (T)(1.0 / sc.fin_theta);
+            s_cf[9] = (T)sc.fin_rtheta;
             s_cf[10] = (T)sc.fin_xcoef;
         }
     };
@@ -353,12 +353,24 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
             }
         }
     };
+    // every block adds the block partials in the same fixed order; each lane issues
+    // its loads (RCHUNK at a time) before adding, so the L2 latencies overlap
+    constexpr int RCHUNK = 10;
     auto reduce_all = [&](const double* buf) {
         for (int v = warp; v < NV; v += MRS_WARPS) {
             if constexpr (sizeof(T) == 4) {
                 const float2* b2 = reinterpret_cast<const float2*>(buf) + (size_t)v * nblk;
                 float2 acc = make_float2(0.f, 0.f);
-                for (int b = lane; b < nblk; b += 32) acc = df_add(acc, __ldcg(&b2[b]));
+                for (int b0 = 0; b0 < nblk; b0 += 32 * RCHUNK) {
+                    float2 ld[RCHUNK];
+#pragma unroll
+                    for (int t = 0; t < RCHUNK; ++t) {
+                        const int b = b0 + lane + 32 * t;
+                        ld[t] = b < nblk ? __ldcg(&b2[b]) : make_float2(0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int t = 0; t < RCHUNK; ++t) acc = df_add(acc, ld[t]);
+                }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
                     float2 other;
@@ -369,17 +381,27 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
                 if (lane == 0) s_red[v] = (double)acc.x + (double)acc.y;
             } else {
                 double t = 0.0;
-                for (int b = lane; b < nblk; b += 32) t += __ldcg(&buf[v * nblk + b]);
+                for (int b0 = 0; b0 < nblk; b0 += 32 * RCHUNK) {
+                    double ld[RCHUNK];
+#pragma unroll
+                    for (int q = 0; q < RCHUNK; ++q) {
+                        const int b = b0 + lane + 32 * q;
+                        ld[q] = b < nblk ? __ldcg(&buf[v * nblk + b]) : 0.0;
+                    }
+#pragma unroll
+                    for (int q = 0; q < RCHUNK; ++q) t += ld[q];
+                }
                 t = warp_sum(t);
                 if (lane == 0) s_red[v] = t;
             }
         }
         __syncthreads();
     };
-    // u = S_k h with h = nu * (Q^T y), S_k(m, m+1) = alpha_m, S_k(m+1, m) = -alpha_m
-    auto make_u = [&](double nu) {
+    // u = S_k h with h = nu * (Q^T y), S_k(m, m+1) = alpha_m, S_k(m+1, m) = -alpha_m;
+    // computed by the lanes of warp 0 (the caller synchronises the block afterwards)
+    auto make_u_warp0 = [&](double nu) {
         if constexpr (KP > 0) {
-            for (int m = threadIdx.x; m < KP; m += MRS_THREADS) {
+            for (int m = lane; m < KP; m += 32) {
                 double u = 0.0;
                 if (m < p.k) {
                     if (m + 1 < p.k) u += s_alpha[m] * s_red[2 + m] * nu;
@@ -388,8 +410,8 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
                 s_u[m] = (T)u;
             }
         }
-        __syncthreads();
     };
+    unsigned phase = 0;  // grid barriers passed in this launch
 
     // ---- phase 0: y_1 = b, x = 0, p = 0, ||b||^2 and Q^T b ----
     T tacc[NV];
@@ -413,29 +435,34 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
     }
     stamp(1);
     block_partials(tacc, p.part);
-    grid_sync(p.gb, nblk, p.budget);
+    grid_sync_phase(p.gb, nblk, phase++, p.budget);
     stamp(2);
     if (*err) return;
     reduce_all(p.part);
 
-    if (threadIdx.x == 0) {
-        double r0 = sqrt(s_red[0]);
-        sc.r0 = r0;
-        sc.nu = r0 > 0.0 ? 1.0 / r0 : 0.0;
-        sc.coef_old = 0.0;
-        sc.theta_t = p.shift;
-        sc.c_prev = 1.0;
-        sc.s_prev = 0.0;
-        sc.delta_prev = 0.0;
-        sc.G = r0;
-        sc.nu_p = 0.0;
-        sc.delta_pp = 0.0;
-        sc.theta_p = 1.0;
-        sc.xcoef_p = 0.0;
-        sc.ratio = r0 > 0.0 ? 1.0 : 0.0;
-        sc.its = 0;
-        sc.stop = r0 > 0.0 ? 0 : 1;
-        set_coefs();
+    if (warp == 0) {
+        if (lane == 0) {
+            double r0 = sqrt(s_red[0]);
+            sc.r0 = r0;
+            sc.rr0 = r0 > 0.0 ? 1.0 / r0 : 0.0;
+            sc.nu = sc.rr0;
+            sc.coef_old = 0.0;
+            sc.theta_t = p.shift;
+            sc.c_prev = 1.0;
+            sc.s_prev = 0.0;
+            sc.delta_prev = 0.0;
+            sc.G = r0;
+            sc.nu_p = 0.0;
+            sc.delta_pp = 0.0;
+            sc.rtheta_p = 1.0;
+            sc.xcoef_p = 0.0;
+            sc.ratio = r0 > 0.0 ? 1.0 : 0.0;
+            sc.its = 0;
+            sc.stop = r0 > 0.0 ? 0 : 1;
+            set_coefs();
+        }
+        __syncwarp();
+        if (!sc.stop) make_u_warp0(sc.nu);
     }
     __syncthreads();
     if (sc.stop) {  // b = 0: x = 0 already
@@ -449,7 +476,6 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
         }
         return;
     }
-    make_u(sc.nu);
     stamp(3);
 
     for (int j = 1; j <= p.maxit; ++j) {
@@ -537,42 +563,47 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
         stamp(tb);
         block_partials(tacc, buf);
         stamp(tb + 1);
-        grid_sync(p.gb, nblk, p.budget);
+        grid_sync_phase(p.gb, nblk, phase++, p.budget);
         stamp(tb + 2);
         if (*err) break;
         reduce_all(buf);
         stamp(tb + 3);
 
-        if (threadIdx.x == 0) {
-            const double beta = sqrt(s_red[0]);
-            const double theta = sqrt(sc.theta_t * sc.theta_t + beta * beta);
-            const double c = sc.theta_t / theta, s = beta / theta;
-            const double delta = -sc.s_prev * beta;
-            const double theta_t_next = sc.c_prev * theta;
-            const double xcoef = sc.G * c;
-            const double Gn = -sc.G * s;
-            sc.ratio = fabs(Gn) / sc.r0;
-            sc.its = j;
-            if (sc.ratio < p.tol || j == p.maxit) {
-                sc.stop = 1;
-                sc.fin_nu = sc.nu;
-                sc.fin_delta = sc.delta_prev;
-                sc.fin_theta = theta;
-                sc.fin_xcoef = xcoef;
-            } else {
-                sc.nu_p = sc.nu;
-                sc.delta_pp = sc.delta_prev;
-                sc.theta_p = theta;
-                sc.xcoef_p = xcoef;
-                sc.coef_old = beta * sc.nu;
-                sc.nu = (beta != 0.0) ? 1.0 / beta : 0.0;
-                sc.s_prev = s;
-                sc.c_prev = c;
-                sc.delta_prev = delta;
-                sc.theta_t = theta_t_next;
-                sc.G = Gn;
+        if (warp == 0) {
+            if (lane == 0) {
+                const double beta = sqrt(s_red[0]);
+                const double theta = sqrt(sc.theta_t * sc.theta_t + beta * beta);
+                const double rth = 1.0 / theta;
+                const double c = sc.theta_t * rth, s = beta * rth;
+                const double delta = -sc.s_prev * beta;
+                const double theta_t_next = sc.c_prev * theta;
+                const double xcoef = sc.G * c;
+                const double Gn = -sc.G * s;
+                sc.ratio = fabs(Gn) * sc.rr0;
+                sc.its = j;
+                if (sc.ratio < p.tol || j == p.maxit) {
+                    sc.stop = 1;
+                    sc.fin_nu = sc.nu;
+                    sc.fin_delta = sc.delta_prev;
+                    sc.fin_rtheta = rth;
+                    sc.fin_xcoef = xcoef;
+                } else {
+                    sc.nu_p = sc.nu;
+                    sc.delta_pp = sc.delta_prev;
+                    sc.rtheta_p = rth;
+                    sc.xcoef_p = xcoef;
+                    sc.coef_old = beta * sc.nu;
+                    sc.nu = (beta != 0.0) ? 1.0 / beta : 0.0;
+                    sc.s_prev = s;
+                    sc.c_prev = c;
+                    sc.delta_prev = delta;
+                    sc.theta_t = theta_t_next;
+                    sc.G = Gn;
+                }
+                set_coefs();
             }
-            set_coefs();
+            __syncwarp();
+            if (!sc.stop) make_u_warp0(sc.nu);
         }
         __syncthreads();
         if (sc.stop) {
@@ -602,7 +633,6 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
             }
             break;
         }
-        make_u(sc.nu);
         stamp(tb + 4);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
