@@ -387,6 +387,7 @@ struct KrylovWork {
     DBuf<double> w, u, ut, v, Bue, Buo, d, rstar;
     DBuf<double> V, Z, H, cs, sn, g, hv, hv2, y;
     DBuf<double> T;
+    ArnoldiWork ao;   // fused Arnoldi step (FGMRES)
     int outer = -1;
     // allocates on first use or when the size changes; kept by the handle across solves
     asss_status init(int n_, int m_, int outer_) {
@@ -727,6 +728,9 @@ static asss_status ensure_adjoint_ops(asss_handle* h) {
     if (!h->SwT.nnz && h->Sw.nnz) ASSS_TRY(transpose_csr(h->Sw, h->SwT, nullptr, s));
     if (!h->ST.nnz && h->S.nnz) ASSS_TRY(transpose_csr(h->S, h->ST, nullptr, s));
     if (!h->AT.nnz && h->A.nnz) ASSS_TRY(transpose_csr(h->A, h->AT, nullptr, s));
+    int ok = 0;
+    for (DCsr* M : {&h->AwT, &h->SwT, &h->ST, &h->AT})
+        if (M->nnz) ASSS_TRY(attach_dia(*M, 16, 0.5, &ok, s));
     return ASSS_OK;
 }
 
@@ -870,24 +874,41 @@ static asss_status fgmres_cycle(asss_handle* h, KrylovWork& kw, int tr, const do
         h->tr.mark(s, Tracer::OP);
         ASSS_TRY(apply_op(h, tr, zj, kw.w.p));
         h->tr.mark(s, Tracer::ORTH);
-        ASSS_TRY(gram(kw.V.p, n, j + 1, kw.w.p, n, 1, n, kw.hv.p, s));
-        k_sub_colmajor<<<cdiv(n, 256), 256, 0, s>>>(kw.V.p, n, j + 1, kw.hv.p, n, kw.w.p);
-        ASSS_CHECK_LAUNCH();
-        ASSS_TRY(gram(kw.V.p, n, j + 1, kw.w.p, n, 1, n, kw.hv2.p, s));
-        k_sub_colmajor<<<cdiv(n, 256), 256, 0, s>>>(kw.V.p, n, j + 1, kw.hv2.p, n, kw.w.p);
-        ASSS_CHECK_LAUNCH();
-        ASSS_TRY(dot(kw.w.p, kw.w.p, n, T + 2, s));
-        h->tr.mark(s, Tracer::SCALAR);
-        k_fg_column<<<1, 1, 0, s>>>(kw.H.p, kw.cs.p, kw.sn.p, kw.g.p, kw.hv.p, kw.hv2.p, T + 2, j, M, T + 3);
-        ASSS_CHECK_LAUNCH();
+        const bool fused = j + 1 <= AO_MAXV;
+        if (fused) {
+            // CGS2, ||w||, the Givens update and v_{j+1} in one launch
+            ASSS_TRY(arnoldi_orth(h->ctx, kw.ao, kw.V.p, kw.w.p, n, j, M, kw.H.p, kw.cs.p, kw.sn.p, kw.g.p,
+                                  kw.hv.p, kw.hv2.p, T + 2, T + 3));
+            h->tr.mark(s, Tracer::SCALAR);
+        } else {
+            ASSS_TRY(gram(kw.V.p, n, j + 1, kw.w.p, n, 1, n, kw.hv.p, s));
+            k_sub_colmajor<<<cdiv(n, 256), 256, 0, s>>>(kw.V.p, n, j + 1, kw.hv.p, n, kw.w.p);
+            ASSS_CHECK_LAUNCH();
+            ASSS_TRY(gram(kw.V.p, n, j + 1, kw.w.p, n, 1, n, kw.hv2.p, s));
+            k_sub_colmajor<<<cdiv(n, 256), 256, 0, s>>>(kw.V.p, n, j + 1, kw.hv2.p, n, kw.w.p);
+            ASSS_CHECK_LAUNCH();
+            ASSS_TRY(dot(kw.w.p, kw.w.p, n, T + 2, s));
+            h->tr.mark(s, Tracer::SCALAR);
+            k_fg_column<<<1, 1, 0, s>>>(kw.H.p, kw.cs.p, kw.sn.p, kw.g.p, kw.hv.p, kw.hv2.p, T + 2, j, M, T + 3);
+            ASSS_CHECK_LAUNCH();
+        }
         steps = j + 1;
         double hostv[2];
+        int aerr = 0;
         ASSS_CUDA(cudaMemcpyAsync(&hostv[0], kw.g.p + j + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
         ASSS_CUDA(cudaMemcpyAsync(&hostv[1], T + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+        if (fused) ASSS_CUDA(cudaMemcpyAsync(&aerr, kw.ao.err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
         ASSS_CUDA(cudaStreamSynchronize(s));
+        if (aerr) {
+            kw.ao.n = 0;  // the barrier counter is re-initialised on the next launch
+            set_error("a device wait in the Arnoldi step ran out (status %d)", aerr);
+            return (asss_status)aerr;
+        }
         if (hostv[1] == 0.0 || fabs(hostv[0]) <= eta * beta0) break;
-        k_scale_dev<<<cdiv(n, 256), 256, 0, s>>>(kw.V.p + (size_t)(j + 1) * n, kw.w.p, T + 3, n);
-        ASSS_CHECK_LAUNCH();
+        if (!fused) {
+            k_scale_dev<<<cdiv(n, 256), 256, 0, s>>>(kw.V.p + (size_t)(j + 1) * n, kw.w.p, T + 3, n);
+            ASSS_CHECK_LAUNCH();
+        }
     }
     k_fg_backsolve<<<1, 1, 0, s>>>(kw.H.p, kw.g.p, steps, M, kw.y.p);
     ASSS_CHECK_LAUNCH();
@@ -1214,6 +1235,11 @@ static asss_status do_setup(asss_handle* h, const asss_csr* Ain, asss_stats* st)
     ASSS_TRY(copy_csr(h->S, h->Sw, s));
     k_scale_cols<<<cdiv(n, 256), 256, 0, s>>>(h->Sw.rp.p, h->Sw.ci.p, h->Sw.v.p, h->w.p, n);
     ASSS_CHECK_LAUNCH();
+    // stencil-like matrices also get a diagonal copy for the solve-phase products
+    {
+        int ok = 0;
+        for (DCsr* M : {&h->Aw, &h->Sw, &h->A, &h->S}) ASSS_TRY(attach_dia(*M, 16, 0.5, &ok, s));
+    }
     // skew-Lanczos (§3.2, Fig. 2)
     {
         DBuf<double> q1;

@@ -80,11 +80,21 @@ struct DBuf {
 asss_status process_scratch(int slot, int64_t count, double** out);
 
 // CSR with 32-bit row pointers (nnz < 2^31 is checked on entry).
+// Optional diagonal copy of a CSR matrix whose entries sit on a few diagonals
+// (stencils): val[d*n + i] = A(i, i + off[d]), 0 where absent or outside the matrix.
+struct DDia {
+    bool tried = false;  // attach_dia ran on this matrix (attached or not)
+    int ndiag = 0;
+    DBuf<int> off;       // ascending signed offsets
+    DBuf<double> val;
+};
+
 struct DCsr {
     int n = 0;
     int nnz = 0;
     DBuf<int> rp, ci;
     DBuf<double> v;
+    DDia dia;            // used by spmv when present
 };
 
 // SELL-C (C = 32) storage: slice s covers rows 32s..32s+31; entry kk of lane t

@@ -12,6 +12,9 @@ asss_status upload_csr(const asss_csr* A, DCsr& out, bool need_values, cudaStrea
 asss_status copy_csr(const DCsr& a, DCsr& out, cudaStream_t s);
 asss_status transpose_csr(const DCsr& a, DCsr& t, DBuf<int>* srcpos, cudaStream_t s);
 asss_status spmv(const DCsr& A, const double* x, double* y, const double* lscale, cudaStream_t s);
+// attach a diagonal copy (DDia) when A's entries lie on at most max_diag diagonals
+// that are at least min_fill full; *ok tells whether it was attached
+asss_status attach_dia(DCsr& A, int max_diag, double min_fill, int* ok, cudaStream_t s);
 asss_status build_pattern(const DCsr& Abar, const DCsr& AbarT, const DCsr& S, const DCsr& ST, DCsr& P,
                           DBuf<int>& mirror, DBuf<int>& diagpos, cudaStream_t s);
 template <class T>
@@ -174,7 +177,19 @@ struct BatchLaunch {
 asss_status batch_launch(const BatchLaunch& L, int nthreads, int nblk, cudaStream_t s);
 // resident CTAs per SM of the batched solver for a CTA size
 asss_status batch_occupancy(int kp, int qbf16, int nthreads, int* occ);
-constexpr int BATCH_RMAX = 24;    // restart length bound of the batched FGMRES
+constexpr int BATCH_RMAX = 24;
+
+// fused Arnoldi step of FGMRES (arnoldi.cu): CGS2 + norm + Givens + next basis vector
+constexpr int AO_MAXV = 64;
+struct ArnoldiWork {
+    int n = 0, nblk = 0;
+    unsigned phase = 0;  // grid barriers completed on bar[0]
+    DBuf<double> part;
+    DBuf<unsigned> bar;
+    DBuf<int> err;
+};
+asss_status arnoldi_orth(const Ctx& c, ArnoldiWork& aw, const double* V, double* w, int n, int j, int m, double* H,
+                         double* cs, double* sn, double* g, double* hv, double* hv2, double* hn2, double* inv_hn);    // restart length bound of the batched FGMRES
 long long batch_work_doubles(int n_max, int halo_max, int restart);
 
 }  // namespace asss

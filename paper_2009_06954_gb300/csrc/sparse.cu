@@ -382,8 +382,98 @@ __global__ void k_spmv(int n, const int* __restrict__ rp, const int* __restrict_
     if (live && sub == 0) y[row] = lscale ? lscale[row] * acc : acc;
 }
 
+// ---------------------------------------------------------------------------
+// diagonal storage for stencil-like FP64 matrices: one thread per row, the
+// diagonals read with unit stride (no column indices), offsets in shared memory
+// ---------------------------------------------------------------------------
+constexpr int DIA_MAX = 16;
+
+__global__ void k_dia_spmv(int n, int ndiag, const int* __restrict__ off, const double* __restrict__ val,
+                           const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ lscale) {
+    __shared__ int s_off[DIA_MAX];
+    if (threadIdx.x < ndiag) s_off[threadIdx.x] = off[threadIdx.x];
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double acc = 0.0;
+    for (int d = 0; d < ndiag; ++d) {
+        const int j = i + s_off[d];
+        if (j >= 0 && j < n) acc += __ldg(&val[(size_t)d * n + i]) * __ldg(&x[j]);
+    }
+    y[i] = lscale ? lscale[i] * acc : acc;
+}
+
+__global__ void k_dia_offsets(int n, const int* rp, const int* ci, unsigned* bits) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+        const unsigned b = (unsigned)(ci[e] - i + n - 1);  // 0 .. 2n-2
+        atomicOr(&bits[b >> 5], 1u << (b & 31));
+    }
+}
+
+__global__ void k_dia_fill(int n, const int* rp, const int* ci, const double* v, const int* off, int ndiag,
+                           double* val) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+        const int o = ci[e] - i;
+        int lo = 0, hi = ndiag - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (off[mid] < o) lo = mid + 1;
+            else hi = mid;
+        }
+        val[(size_t)lo * n + i] = v[e];  // every offset of A is in the list
+    }
+}
+
+asss_status attach_dia(DCsr& A, int max_diag, double min_fill, int* ok, cudaStream_t s) {
+    *ok = A.dia.ndiag > 0;
+    if (A.dia.tried) return ASSS_OK;
+    A.dia.tried = true;
+    const int n = A.n;
+    if (n < 1 || !A.v.p || A.nnz < 1 || max_diag > DIA_MAX) return ASSS_OK;
+    const long long nbits = 2LL * n - 1;
+    const int words = (int)((nbits + 31) / 32);
+    DBuf<unsigned> bits;
+    ASSS_TRY(bits.alloc(words));
+    ASSS_CUDA(cudaMemsetAsync(bits.p, 0, sizeof(unsigned) * words, s));
+    k_dia_offsets<<<cdiv(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, bits.p);
+    ASSS_CHECK_LAUNCH();
+    std::vector<unsigned> hb(words);
+    ASSS_CUDA(cudaMemcpyAsync(hb.data(), bits.p, sizeof(unsigned) * words, cudaMemcpyDeviceToHost, s));
+    ASSS_CUDA(cudaStreamSynchronize(s));
+    std::vector<int> off;
+    for (int w = 0; w < words; ++w) {
+        unsigned b = hb[w];
+        while (b) {
+            const int t = __builtin_ctz(b);
+            off.push_back(w * 32 + t - (n - 1));
+            b &= b - 1;
+            if ((int)off.size() > max_diag) return ASSS_OK;
+        }
+    }
+    double stored = 0.0;
+    for (int o : off) stored += (double)(n - (o < 0 ? -o : o));
+    if ((double)A.nnz < min_fill * stored) return ASSS_OK;
+    ASSS_TRY(to_device(A.dia.off, off.data(), (int64_t)off.size(), s));
+    ASSS_TRY(A.dia.val.alloc((int64_t)off.size() * n));
+    ASSS_CUDA(cudaMemsetAsync(A.dia.val.p, 0, sizeof(double) * off.size() * (size_t)n, s));
+    k_dia_fill<<<cdiv(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, A.dia.off.p, (int)off.size(), A.dia.val.p);
+    ASSS_CHECK_LAUNCH();
+    A.dia.ndiag = (int)off.size();
+    *ok = 1;
+    return ASSS_OK;
+}
+
 asss_status spmv(const DCsr& A, const double* x, double* y, const double* lscale, cudaStream_t s) {
     int n = A.n;
+    if (A.dia.ndiag > 0) {
+        k_dia_spmv<<<cdiv(n, 256), 256, 0, s>>>(n, A.dia.ndiag, A.dia.off.p, A.dia.val.p, x, y, lscale);
+        ASSS_CHECK_LAUNCH();
+        return ASSS_OK;
+    }
     double mean = n ? (double)A.nnz / n : 0;
     int threads = 256;
     if (mean <= 6) {
