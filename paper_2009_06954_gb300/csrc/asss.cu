@@ -150,21 +150,30 @@ __global__ void k_d2f(const double* a, int64_t n, float* b) {
     if (i < n) b[i] = (float)a[i];
 }
 // out = z - Y w for the mixed-precision path: z and Y in FP32, w and out in FP64
+// (w is converted to FP32 once per block: per-row conversions would run on the
+// FP64 pipe, which is narrow on this part; rows of Y are read as float4 when m
+// is a multiple of 4)
 __global__ void k_smw_apply_f32(const float* __restrict__ z, const float* __restrict__ Y, int m,
                                 const double* __restrict__ w, int n, double* out) {
-    extern __shared__ double sw_f[];
-    for (int t = threadIdx.x; t < m; t += blockDim.x) sw_f[t] = w[t];
+    extern __shared__ float sw_f[];
+    for (int t = threadIdx.x; t < m; t += blockDim.x) sw_f[t] = (float)w[t];
     __syncthreads();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double acc = 0.0;
+    float a = 0.f;
     if (m > 0) {
         const float* row = Y + (size_t)i * m;
-        float a = 0.f;
-        for (int c = 0; c < m; ++c) a += row[c] * (float)sw_f[c];
-        acc = a;
+        if ((m & 3) == 0) {
+            const float4* r4 = reinterpret_cast<const float4*>(row);
+            for (int c = 0; c < (m >> 2); ++c) {
+                const float4 v = __ldg(r4 + c);
+                a += v.x * sw_f[4 * c] + v.y * sw_f[4 * c + 1] + v.z * sw_f[4 * c + 2] + v.w * sw_f[4 * c + 3];
+            }
+        } else {
+            for (int c = 0; c < m; ++c) a += row[c] * sw_f[c];
+        }
     }
-    out[i] = (double)z[i] - acc;
+    out[i] = (double)(z[i] - a);
 }
 __global__ void k_gather_neg(const double* z, const int* neg, int r, double* out) {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
@@ -703,7 +712,7 @@ static asss_status apply_prec(asss_handle* h, int tr, const double* u, double* o
             k_gather_neg_f<<<cdiv(h->r, 128), 128, 0, s>>>(h->z32.p, h->neg.p, h->r, h->wv.p + h->k);
             ASSS_CHECK_LAUNCH();
         }
-        k_smw_apply_f32<<<cdiv(n, 256), 256, sizeof(double) * (S.m > 0 ? S.m : 1), s>>>(
+        k_smw_apply_f32<<<cdiv(n, 256), 256, sizeof(float) * (S.m > 0 ? S.m : 1), s>>>(
             h->z32.p, S.m > 0 ? S.Y32.p : nullptr, S.m, h->wv.p, n, out);
         ASSS_CHECK_LAUNCH();
     } else {

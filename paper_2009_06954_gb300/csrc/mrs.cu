@@ -36,10 +36,12 @@ constexpr int MRS_KPMAX = 64;
 constexpr int MRS_MAXDIAG = 64;
 constexpr int MRS_TRACE_STEPS = 16;
 constexpr int MRS_TRACE_SLOTS = 4 + 5 * MRS_TRACE_STEPS;
-// resident blocks per SM the register allocation is sized for: two 512-thread
-// blocks for FP32 (more loads in flight for the gathers), one for FP64
+// resident blocks per SM the register allocation is sized for: one 512-thread
+// block, so a thread has up to 128 registers and can keep the loads of a whole
+// row (all diagonals unrolled) in flight; more resident warps with half the
+// registers measured slower (the pass is bound by memory latency per row)
 template <class T>
-constexpr int mrs_min_blocks() { return sizeof(T) == 4 ? 2 : 1; }
+constexpr int mrs_min_blocks() { return 1; }
 
 struct MrsWork {
     int n = 0;
@@ -521,7 +523,7 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
                 if (i < n) {
                     const T* Ud = p.U + i;
                     const T* yi = Ycur + i;
-#pragma unroll 4
+#pragma unroll 12
                     for (int d = 0; d < p.ndiag; ++d, Ud += p.ustride) {
                         const int m = s_off[d];
                         acc += __ldg(Ud) * yi[m] - __ldg(Ud - m) * yi[-m];
