@@ -30,6 +30,8 @@ struct AoParams {
     double* hn2;      // ||w||^2 after both passes
     double* inv_hn;   // 1 / ||w|| (0 when w = 0)
     double* part;     // 2 x [AO_MAXV][nblk] block partials (consecutive passes alternate halves)
+    double thr;       // the cycle stops when |g[j+1]| <= thr
+    int* stop;
     GridBarrier gb;
     unsigned phase0;  // barriers completed on gb.count before this launch
     long long budget;
@@ -58,6 +60,7 @@ __device__ void ao_fg_column(const AoParams& p, const double* h1, const double* 
     p.g[j] = c * p.g[j];
     *p.hn2 = hn2;
     *p.inv_hn = (hn > 0.0) ? 1.0 / hn : 0.0;
+    *p.stop = (hn2 == 0.0 || fabs(p.g[j + 1]) <= p.thr) ? 1 : 0;
 }
 
 __global__ void __launch_bounds__(AO_THREADS, 2) k_arnoldi_orth(AoParams p) {
@@ -201,7 +204,8 @@ __global__ void __launch_bounds__(AO_THREADS, 2) k_arnoldi_orth(AoParams p) {
 }
 
 asss_status arnoldi_orth(const Ctx& c, ArnoldiWork& aw, const double* V, double* w, int n, int j, int m, double* H,
-                         double* cs, double* sn, double* g, double* hv, double* hv2, double* hn2, double* inv_hn) {
+                         double* cs, double* sn, double* g, double* hv, double* hv2, double* hn2, double* inv_hn,
+                         double thr, int* stop) {
     if (j + 1 > AO_MAXV) {
         set_error("Arnoldi step %d exceeds the fused kernel's %d vectors", j, AO_MAXV);
         return ASSS_ERR_UNSUPPORTED;
@@ -243,6 +247,8 @@ asss_status arnoldi_orth(const Ctx& c, ArnoldiWork& aw, const double* V, double*
     p.hn2 = hn2;
     p.inv_hn = inv_hn;
     p.part = aw.part.p;
+    p.thr = thr;
+    p.stop = stop;
     p.gb.count = aw.bar.p;
     p.gb.gen = aw.bar.p + 1;
     p.gb.err = aw.err.p;

@@ -397,12 +397,22 @@ struct KrylovWork {
     DBuf<double> V, Z, H, cs, sn, g, hv, hv2, y;
     DBuf<double> T;
     ArnoldiWork ao;   // fused Arnoldi step (FGMRES)
+    DBuf<int> stop;   // set by the fused step when the cycle ends
+    double* hpin = nullptr;        // pinned read-back slots
+    cudaEvent_t ev_rb = nullptr;   // marks the read-back in the stream
     int outer = -1;
+    ~KrylovWork() {
+        if (hpin) cudaFreeHost(hpin);
+        if (ev_rb) cudaEventDestroy(ev_rb);
+    }
     // allocates on first use or when the size changes; kept by the handle across solves
     asss_status init(int n_, int m_, int outer_) {
         if (n == n_ && m == m_ && outer == outer_) return ASSS_OK;
         outer = -1;  // marked ready only when every buffer exists
         ASSS_TRY(T.alloc(32));
+        if (!hpin) ASSS_CUDA(cudaMallocHost((void**)&hpin, 8 * sizeof(double)));
+        if (!ev_rb) ASSS_CUDA(cudaEventCreateWithFlags(&ev_rb, cudaEventDisableTiming));
+        if (!stop.p) ASSS_TRY(stop.alloc(1));
         if (outer_ == ASSS_OUTER_TFQMR) {
             ASSS_TRY(w.alloc(n_));
             ASSS_TRY(u.alloc(n_));
@@ -859,35 +869,46 @@ static asss_status fgmres_cycle(asss_handle* h, KrylovWork& kw, int tr, const do
     int n = h->n;
     int M = kw.m;
     if (m > M) m = M;
-    asss_status st = ASSS_OK;
     double* T = kw.T.p;  // 0: rr, 1: inv, 2: hn2, 3: inv_hn
+    double* hp = kw.hpin;
+    *steps_out = 0;
+    *napp_out = 0;
+    // v_0 = r / ||r||, and P^-1 v_0 enqueued before ||r|| reaches the host
     ASSS_TRY(dot(r, r, n, T, s));
     k_fg_init<<<1, 1, 0, s>>>(kw.g.p, M, T, T + 1);
     ASSS_CHECK_LAUNCH();
-    double rr = read_scalar(T, s, &st);
-    ASSS_TRY(st);
-    *steps_out = 0;
-    *napp_out = 0;
+    ASSS_CUDA(cudaMemcpyAsync(hp, T, sizeof(double), cudaMemcpyDeviceToHost, s));
+    ASSS_CUDA(cudaEventRecord(kw.ev_rb, s));
     ASSS_CUDA(cudaMemsetAsync(delta, 0, sizeof(double) * n, s));
-    if (rr == 0.0) return ASSS_OK;
-    double beta0 = sqrt(rr);
     k_scale_dev<<<cdiv(n, 256), 256, 0, s>>>(kw.V.p, r, T + 1, n);
     ASSS_CHECK_LAUNCH();
+    h->tr.mark(s, Tracer::PREC);
+    ASSS_TRY(apply_prec(h, tr, kw.V.p, kw.Z.p));
+    bool have_z = true;  // Z[:, j] is already enqueued
+    ASSS_CUDA(cudaEventSynchronize(kw.ev_rb));
+    const double rr = hp[0];
+    if (rr == 0.0) return ASSS_OK;
+    *napp_out = 1;
+    const double beta0 = sqrt(rr);
+    const double thr = eta * beta0;
     int steps = 0;
     for (int j = 0; j < m; ++j) {
         double* vj = kw.V.p + (size_t)j * n;
         double* zj = kw.Z.p + (size_t)j * n;
-        h->tr.mark(s, Tracer::PREC);
-        ASSS_TRY(apply_prec(h, tr, vj, zj));
-        *napp_out += 1;
+        if (!have_z) {
+            h->tr.mark(s, Tracer::PREC);
+            ASSS_TRY(apply_prec(h, tr, vj, zj));
+            *napp_out += 1;
+        }
+        have_z = false;
         h->tr.mark(s, Tracer::OP);
         ASSS_TRY(apply_op(h, tr, zj, kw.w.p));
         h->tr.mark(s, Tracer::ORTH);
         const bool fused = j + 1 <= AO_MAXV;
         if (fused) {
-            // CGS2, ||w||, the Givens update and v_{j+1} in one launch
+            // CGS2, ||w||, the Givens update, v_{j+1} and the stop test in one launch
             ASSS_TRY(arnoldi_orth(h->ctx, kw.ao, kw.V.p, kw.w.p, n, j, M, kw.H.p, kw.cs.p, kw.sn.p, kw.g.p,
-                                  kw.hv.p, kw.hv2.p, T + 2, T + 3));
+                                  kw.hv.p, kw.hv2.p, T + 2, T + 3, thr, kw.stop.p));
             h->tr.mark(s, Tracer::SCALAR);
         } else {
             ASSS_TRY(gram(kw.V.p, n, j + 1, kw.w.p, n, 1, n, kw.hv.p, s));
@@ -902,18 +923,36 @@ static asss_status fgmres_cycle(asss_handle* h, KrylovWork& kw, int tr, const do
             ASSS_CHECK_LAUNCH();
         }
         steps = j + 1;
-        double hostv[2];
-        int aerr = 0;
-        ASSS_CUDA(cudaMemcpyAsync(&hostv[0], kw.g.p + j + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
-        ASSS_CUDA(cudaMemcpyAsync(&hostv[1], T + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
-        if (fused) ASSS_CUDA(cudaMemcpyAsync(&aerr, kw.ao.err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-        ASSS_CUDA(cudaStreamSynchronize(s));
-        if (aerr) {
-            kw.ao.n = 0;  // the barrier counter is re-initialised on the next launch
-            set_error("a device wait in the Arnoldi step ran out (status %d)", aerr);
-            return (asss_status)aerr;
+        // read-back slots: 0 g[j+1], 1 ||w||^2, 2 (int) device wait status, 3 (int) stop flag
+        int* hi = reinterpret_cast<int*>(hp + 2);
+        hi[0] = 0;
+        hi[2] = 0;
+        ASSS_CUDA(cudaMemcpyAsync(hp, kw.g.p + j + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+        ASSS_CUDA(cudaMemcpyAsync(hp + 1, T + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+        if (fused) {
+            ASSS_CUDA(cudaMemcpyAsync(hi, kw.ao.err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+            ASSS_CUDA(cudaMemcpyAsync(hi + 2, kw.stop.p, sizeof(int), cudaMemcpyDeviceToHost, s));
         }
-        if (hostv[1] == 0.0 || fabs(hostv[0]) <= eta * beta0) break;
+        ASSS_CUDA(cudaEventRecord(kw.ev_rb, s));
+        // while the host waits for the stop test, P^-1 v_{j+1} runs; if the cycle
+        // ends here the mrs launch finds the device stop flag set and does nothing
+        if (fused && j + 1 < m) {
+            h->tr.mark(s, Tracer::PREC);
+            mrs_set_skip(h->mw, kw.stop.p);
+            asss_status ps = apply_prec(h, tr, kw.V.p + (size_t)(j + 1) * n, kw.Z.p + (size_t)(j + 1) * n);
+            mrs_set_skip(h->mw, nullptr);
+            ASSS_TRY(ps);
+            have_z = true;
+        }
+        ASSS_CUDA(cudaEventSynchronize(kw.ev_rb));
+        if (hi[0]) {
+            kw.ao.n = 0;  // the barrier counter is re-initialised on the next launch
+            set_error("a device wait in the Arnoldi step ran out (status %d)", hi[0]);
+            return (asss_status)hi[0];
+        }
+        const bool stop = fused ? (hi[2] != 0) : (hp[1] == 0.0 || fabs(hp[0]) <= thr);
+        if (stop) break;
+        if (have_z) *napp_out += 1;
         if (!fused) {
             k_scale_dev<<<cdiv(n, 256), 256, 0, s>>>(kw.V.p + (size_t)(j + 1) * n, kw.w.p, T + 3, n);
             ASSS_CHECK_LAUNCH();
@@ -969,11 +1008,16 @@ static asss_status refine(asss_handle* h, int tr, const double* rhs, double* x, 
     int stall = 0;
     int* perm = h->has_perm ? h->perm.p : nullptr;
     h->tr.on = getenv("ASSS_TRACE") != nullptr;
+    bool first = true;  // r = b (x = 0) on the first pass: ||r|| = ||b|| is known
     while (true) {
         h->tr.mark(s, Tracer::REFINE);
-        ASSS_TRY(dot(r.p, r.p, n, scal.p, s));
-        double rn = sqrt(read_scalar(scal.p, s, &es));
-        ASSS_TRY(es);
+        double rn = bn;
+        if (!first) {
+            ASSS_TRY(dot(r.p, r.p, n, scal.p, s));
+            rn = sqrt(read_scalar(scal.p, s, &es));
+            ASSS_TRY(es);
+        }
+        first = false;
         st->relres = rn / bn;
         if (rn / bn <= o.outer_tol) break;
         if (!(rn == rn)) {

@@ -101,6 +101,9 @@ asss_status mrs_solve(const Ctx& c, MrsWork* w, const MrsOperator& op, bool fp32
 // timed-out device wait.
 asss_status mrs_collect(const Ctx& c, MrsWork* w, std::vector<MrsResult>* out);
 MrsTotals mrs_take_totals(MrsWork* w);
+// launches enqueued while flag is set (non-null) read *flag on the device first and
+// do nothing if it is non-zero (speculative work enqueued ahead of a host decision)
+void mrs_set_skip(MrsWork* w, const int* flag);
 
 // lls.cu
 struct LlsResult {
@@ -188,8 +191,10 @@ struct ArnoldiWork {
     DBuf<unsigned> bar;
     DBuf<int> err;
 };
+// *stop receives 1 when the cycle ends at this step (||w|| = 0 or |g[j+1]| <= thr)
 asss_status arnoldi_orth(const Ctx& c, ArnoldiWork& aw, const double* V, double* w, int n, int j, int m, double* H,
-                         double* cs, double* sn, double* g, double* hv, double* hv2, double* hn2, double* inv_hn);    // restart length bound of the batched FGMRES
+                         double* cs, double* sn, double* g, double* hv, double* hv2, double* hn2, double* inv_hn,
+                         double thr, int* stop);    // restart length bound of the batched FGMRES
 long long batch_work_doubles(int n_max, int halo_max, int restart);
 
 }  // namespace asss

@@ -45,6 +45,7 @@ constexpr int mrs_min_blocks() { return 1; }
 
 struct MrsWork {
     int n = 0;
+    const int* skip = nullptr;  // device flag read by the next launches (see mrs_set_skip)
     int sms = 0;
     DBuf<double> Y64, P64;
     DBuf<float> Y32, P32;
@@ -152,6 +153,7 @@ struct MrsParams {
     int* out_its;
     double* out_ratio;
     unsigned long long* trace;  // optional timeline (block 0): %globaltimer at phase boundaries
+    const int* skip;     // optional: when *skip != 0 at launch the kernel only logs its = -1
     double* qtz;         // optional: Q^T x (k values) computed in the final pass
     double* qtz_part;    // [KP][nblk] block partials for it
     unsigned* qtz_done;  // last-block counter (left at 0)
@@ -276,6 +278,13 @@ __device__ __forceinline__ void qtz_reduce(const MrsParams<T>& p, T (&tacc)[KP +
 template <class T, int KP, int FMT, bool QB = false>
 __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsParams<T> p) {
     constexpr int NV = KP + 1;
+    if (p.skip && *p.skip) {  // enqueued ahead of a decision that went the other way
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            *p.out_its = -1;
+            *p.out_ratio = 0.0;
+        }
+        return;
+    }
     __shared__ double s_wsum[MRS_WARPS][NV];
     __shared__ double s_red[NV];
     __shared__ T s_u[KP > 0 ? KP : 1];
@@ -751,6 +760,7 @@ static asss_status launch_mrs(const Ctx& c, MrsWork* w, const OpView<T>& J, cons
     prm.out_ratio = w->ratio_log.p + lo.slot;
     prm.qtz = (KP > 0 && k > 0) ? lo.qtz : nullptr;
     prm.trace = w->trace.p;
+    prm.skip = w->skip;
     prm.qtz_part = w->qtz_part.p;
     prm.qtz_done = w->qtz_done.p;
     void* args[] = {&prm};
@@ -955,6 +965,7 @@ asss_status mrs_collect(const Ctx& c, MrsWork* w, std::vector<MrsResult>* out) {
         fprintf(stderr, "\n");
     }
     for (int i = 0; i < nl; ++i) {
+        if (its[i] < 0) continue;  // a launch that found its skip flag set did no work
         float ms = 0.f;
         ASSS_CUDA(cudaEventElapsedTime(&ms, w->evs[2 * i], w->evs[2 * i + 1]));
         MrsResult r;
@@ -977,6 +988,8 @@ asss_status mrs_collect(const Ctx& c, MrsWork* w, std::vector<MrsResult>* out) {
     }
     return ASSS_OK;
 }
+
+void mrs_set_skip(MrsWork* w, const int* flag) { w->skip = flag; }
 
 MrsTotals mrs_take_totals(MrsWork* w) {
     MrsTotals t = w->tot;
