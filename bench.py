@@ -34,8 +34,8 @@ WORKLOAD = ("dh3d_100: dissipative-Hamiltonian implicit-Euler step A = E + h(R -
 SIDE = 100
 CPU_SAMPLE_SIDE = 24
 BATCH = {"count": 256, "side_lo": 10, "side_hi": 40, "nrhs": 32, "seed": 3}
-BATCH_WORKLOAD = ("batched_dh: 256 dissipative-Hamiltonian systems, 3D grids of sides 10..40 (n = 1e3..6.4e4, "
-                  "seeded), 32 right-hand sides ~ N(0,1) each (8192 solves per step), one persistent launch "
+BATCH_WORKLOAD = ("batched_dh: {count} dissipative-Hamiltonian systems, 3D grids of sides 10..40 (n = 1e3..6.4e4, "
+                  "seeded), 32 right-hand sides ~ N(0,1) each ({items} solves per step), one persistent launch "
                   "replayed from a CUDA graph, FP32 inner mrs (tol 1e-6) / FP64 outer FGMRES(24), outer tol 1e-8")
 
 
@@ -102,7 +102,7 @@ def run_batched_cpu_baseline(budget_s, mean_n):
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[v] = "1"
     cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", "--workload", "batched_dh", "--budget",
-           str(budget_s)]
+           str(budget_s), "--batch-count", str(BATCH["count"])]
     p = subprocess.run(cmd, capture_output=True, text=True, env=env, cwd=ROOT)
     if p.returncode != 0:
         raise RuntimeError("CPU baseline worker failed:\n" + p.stdout + p.stderr)
@@ -359,7 +359,8 @@ def main_batched(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32-inner/f64-outer", "data": "synthetic",
-        "config": {"workload": BATCH_WORKLOAD, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+        "config": {"workload": BATCH_WORKLOAD.format(count=len(batch), items=items),
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "256 MB buffer written between steps (not timed); working set > L2",
                    "setup_s": round(t_setup, 3), "cta_threads": bs.cta_threads, "items_per_step": items,
                    "total_rows": bs.total, "max_relres": relres, "host_checked_max_relres": worst,
@@ -399,7 +400,10 @@ def main():
                     help="storage of the Lanczos basis read by the FP32 inner solve")
     ap.add_argument("--workload", default="dh3d_100", choices=["dh3d_100", "batched_dh"],
                     help="dh3d_100: one 1e6-unknown system; batched_dh: 256 systems x 32 right-hand sides")
+    ap.add_argument("--batch-count", type=int, default=BATCH["count"],
+                    help="systems in the batched workload (smaller counts for profiling captures)")
     args = ap.parse_args()
+    BATCH["count"] = args.batch_count
 
     if args.cpu_worker:
         if args.workload == "batched_dh":
@@ -425,7 +429,8 @@ def main():
         line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": BATCH_WORKLOAD if args.workload == "batched_dh" else WORKLOAD,
+                "config": {"workload": (BATCH_WORKLOAD.format(count=BATCH["count"], items=BATCH["count"] * BATCH["nrhs"])
+                                        if args.workload == "batched_dh" else WORKLOAD),
                            "reference": "FP64 CPU oracle (oracle/), host cores"},
                 "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
                 "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
