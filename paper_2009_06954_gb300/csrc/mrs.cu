@@ -225,34 +225,45 @@ __device__ __forceinline__ float2 df_add(float2 a, float2 b) {
 }
 
 // Scalar state of the recurrence, kept in shared memory and advanced by one
-// thread per block (FP64 is slow on this part; every block computes the same
-// values from the same reduced sums, so all blocks agree bit for bit).
+// thread per block in the precision of the vectors (the FP32 solve keeps its
+// whole synchronisation chain off the narrow FP64 pipe of this part; every block
+// computes the same values from the same reduced sums, so all blocks agree bit
+// for bit).
+template <class S>
 struct MrsScalars {
-    double r0, rr0, nu, coef_old, theta_t, c_prev, s_prev, delta_prev, G;
-    double nu_p, delta_pp, rtheta_p, xcoef_p;   // rtheta_p = 1 / theta of the previous step
+    S r0, rr0, nu, coef_old, theta_t, c_prev, s_prev, delta_prev, G;
+    S nu_p, delta_pp, rtheta_p, xcoef_p;   // rtheta_p = 1 / theta of the previous step
     // final-pass coefficients when the iteration stops
-    double fin_nu, fin_delta, fin_rtheta, fin_xcoef;
-    double ratio;
+    S fin_nu, fin_delta, fin_rtheta, fin_xcoef;
+    S ratio;
     int its, stop;
 };
 
 // Q^T x of the final iterate: block partials, then the last block to finish adds
 // them in block order and writes p.qtz (no block waits for another).
 template <class T, int KP>
-__device__ __forceinline__ void qtz_reduce(const MrsParams<T>& p, T (&tacc)[KP + 1], double (&s_wsum)[MRS_WARPS][KP + 1],
+__device__ __forceinline__ void qtz_reduce(const MrsParams<T>& p, T (&tacc)[KP + 1], T (&s_wsum)[MRS_WARPS][KP + 1],
                                            int warp, int lane) {
     __shared__ int s_last;
     const int nblk = gridDim.x;
 #pragma unroll
     for (int v = 1; v <= KP; ++v) {
         T d = warp_sum(tacc[v]);
-        if (lane == 0) s_wsum[warp][v] = (double)d;
+        if (lane == 0) s_wsum[warp][v] = d;
     }
     __syncthreads();
     for (int v = threadIdx.x; v < p.k; v += MRS_THREADS) {
-        double t = 0.0;
+        double t;
+        if constexpr (sizeof(T) == 4) {
+            float2 a = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int w = 0; w < MRS_WARPS; ++w) t += s_wsum[w][1 + v];
+            for (int w = 0; w < MRS_WARPS; ++w) a = df_add(a, make_float2(s_wsum[w][1 + v], 0.f));
+            t = (double)a.x + (double)a.y;
+        } else {
+            t = 0.0;
+#pragma unroll
+            for (int w = 0; w < MRS_WARPS; ++w) t += s_wsum[w][1 + v];
+        }
         p.qtz_part[v * nblk + blockIdx.x] = t;
     }
     __syncthreads();
@@ -285,12 +296,12 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
         }
         return;
     }
-    __shared__ double s_wsum[MRS_WARPS][NV];
-    __shared__ double s_red[NV];
+    __shared__ T s_wsum[MRS_WARPS][NV];
+    __shared__ T s_red[NV];
     __shared__ T s_u[KP > 0 ? KP : 1];
     __shared__ int s_off[FMT == 1 ? MRS_MAXDIAG : 1];
-    __shared__ MrsScalars sc;
-    __shared__ double s_alpha[MRS_KPMAX];
+    __shared__ MrsScalars<T> sc;
+    __shared__ T s_alpha[MRS_KPMAX];
     // per-step coefficients in T, set by thread 0 (so no thread converts or divides in FP64):
     // 0 sign*nu, 1 sign, 2 beta_{j-1} nu_{j-1}, 3 nu_p, 4 delta_pp, 5 1/theta_p, 6 xcoef_p,
     // 7..10 the final pass: nu, delta, 1/theta, xcoef
@@ -298,9 +309,9 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
     if constexpr (FMT == 1) {
         for (int d = threadIdx.x; d < p.ndiag; d += MRS_THREADS) s_off[d] = p.off[d];
     }
-    for (int m = threadIdx.x; m + 1 < p.k && m < MRS_KPMAX; m += MRS_THREADS) s_alpha[m] = p.alpha[m];
+    for (int m = threadIdx.x; m + 1 < p.k && m < MRS_KPMAX; m += MRS_THREADS) s_alpha[m] = (T)p.alpha[m];
     auto set_coefs = [&]() {  // thread 0 only
-        s_cf[0] = (T)(p.sign * sc.nu);
+        s_cf[0] = (T)p.sign * sc.nu;
         s_cf[1] = (T)p.sign;
         s_cf[2] = (T)sc.coef_old;
         s_cf[3] = (T)sc.nu_p;
@@ -334,7 +345,7 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
         for (int v = 0; v < NV; ++v) {
             if constexpr (sizeof(T) == 4) {
                 T d = warp_sum(tacc[v]);
-                if (lane == 0) s_wsum[warp][v] = (double)d;
+                if (lane == 0) s_wsum[warp][v] = d;
             } else {
                 // FP64 partials: the warp tree runs on float pairs (the FP64 pipe is slow)
                 float hi = (float)tacc[v];
@@ -351,15 +362,17 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
         }
         __syncthreads();
         for (int v = threadIdx.x; v < NV; v += MRS_THREADS) {
-            double t = 0.0;
-#pragma unroll
-            for (int w = 0; w < MRS_WARPS; ++w) t += s_wsum[w][v];
             if constexpr (sizeof(T) == 4) {
-                // block partial as a float pair (hi, lo) in the same 8 bytes
-                float hi = (float)t;
-                float lo = (float)(t - (double)hi);
-                reinterpret_cast<float2*>(buf)[v * nblk + blockIdx.x] = make_float2(hi, lo);
+                // block partial as a float pair (hi, lo) in the same 8 bytes, summed over
+                // the warps in float-pair arithmetic
+                float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int w = 0; w < MRS_WARPS; ++w) a = df_add(a, make_float2(s_wsum[w][v], 0.f));
+                reinterpret_cast<float2*>(buf)[v * nblk + blockIdx.x] = a;
             } else {
+                double t = 0.0;
+#pragma unroll
+                for (int w = 0; w < MRS_WARPS; ++w) t += s_wsum[w][v];
                 buf[v * nblk + blockIdx.x] = t;
             }
         }
@@ -389,7 +402,7 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
                     other.y = __shfl_xor_sync(0xffffffffu, acc.y, o);
                     acc = df_add(acc, other);
                 }
-                if (lane == 0) s_red[v] = (double)acc.x + (double)acc.y;
+                if (lane == 0) s_red[v] = acc.x + acc.y;
             } else {
                 double t = 0.0;
                 for (int b0 = 0; b0 < nblk; b0 += 32 * RCHUNK) {
@@ -410,15 +423,15 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
     };
     // u = S_k h with h = nu * (Q^T y), S_k(m, m+1) = alpha_m, S_k(m+1, m) = -alpha_m;
     // computed by the lanes of warp 0 (the caller synchronises the block afterwards)
-    auto make_u_warp0 = [&](double nu) {
+    auto make_u_warp0 = [&](T nu) {
         if constexpr (KP > 0) {
             for (int m = lane; m < KP; m += 32) {
-                double u = 0.0;
+                T u = (T)0;
                 if (m < p.k) {
                     if (m + 1 < p.k) u += s_alpha[m] * s_red[2 + m] * nu;
                     if (m > 0) u -= s_alpha[m - 1] * s_red[m] * nu;
                 }
-                s_u[m] = (T)u;
+                s_u[m] = u;
             }
         }
     };
@@ -453,23 +466,24 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
 
     if (warp == 0) {
         if (lane == 0) {
-            double r0 = sqrt(s_red[0]);
+            const T r0 = sqrt(s_red[0]);
+            const T zero = (T)0, one = (T)1;
             sc.r0 = r0;
-            sc.rr0 = r0 > 0.0 ? 1.0 / r0 : 0.0;
+            sc.rr0 = r0 > zero ? one / r0 : zero;
             sc.nu = sc.rr0;
-            sc.coef_old = 0.0;
-            sc.theta_t = p.shift;
-            sc.c_prev = 1.0;
-            sc.s_prev = 0.0;
-            sc.delta_prev = 0.0;
+            sc.coef_old = zero;
+            sc.theta_t = (T)p.shift;
+            sc.c_prev = one;
+            sc.s_prev = zero;
+            sc.delta_prev = zero;
             sc.G = r0;
-            sc.nu_p = 0.0;
-            sc.delta_pp = 0.0;
-            sc.rtheta_p = 1.0;
-            sc.xcoef_p = 0.0;
-            sc.ratio = r0 > 0.0 ? 1.0 : 0.0;
+            sc.nu_p = zero;
+            sc.delta_pp = zero;
+            sc.rtheta_p = one;
+            sc.xcoef_p = zero;
+            sc.ratio = r0 > zero ? one : zero;
             sc.its = 0;
-            sc.stop = r0 > 0.0 ? 0 : 1;
+            sc.stop = r0 > zero ? 0 : 1;
             set_coefs();
         }
         __syncwarp();
@@ -582,14 +596,14 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
 
         if (warp == 0) {
             if (lane == 0) {
-                const double beta = sqrt(s_red[0]);
-                const double theta = sqrt(sc.theta_t * sc.theta_t + beta * beta);
-                const double rth = 1.0 / theta;
-                const double c = sc.theta_t * rth, s = beta * rth;
-                const double delta = -sc.s_prev * beta;
-                const double theta_t_next = sc.c_prev * theta;
-                const double xcoef = sc.G * c;
-                const double Gn = -sc.G * s;
+                const T beta = sqrt(s_red[0]);
+                const T theta = sqrt(sc.theta_t * sc.theta_t + beta * beta);
+                const T rth = (T)1 / theta;
+                const T c = sc.theta_t * rth, s = beta * rth;
+                const T delta = -sc.s_prev * beta;
+                const T theta_t_next = sc.c_prev * theta;
+                const T xcoef = sc.G * c;
+                const T Gn = -sc.G * s;
                 sc.ratio = fabs(Gn) * sc.rr0;
                 sc.its = j;
                 if (sc.ratio < p.tol || j == p.maxit) {
@@ -604,7 +618,7 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
                     sc.rtheta_p = rth;
                     sc.xcoef_p = xcoef;
                     sc.coef_old = beta * sc.nu;
-                    sc.nu = (beta != 0.0) ? 1.0 / beta : 0.0;
+                    sc.nu = (beta != (T)0) ? (T)1 / beta : (T)0;
                     sc.s_prev = s;
                     sc.c_prev = c;
                     sc.delta_prev = delta;
@@ -648,7 +662,7 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         *p.out_its = sc.its;
-        *p.out_ratio = sc.ratio;
+        *p.out_ratio = (double)sc.ratio;
     }
 }
 
