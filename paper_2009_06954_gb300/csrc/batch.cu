@@ -25,27 +25,29 @@ long long batch_work_doubles(int n_max, int halo_max, int restart) {
     return nd + (nf + 1) / 2 + 64;
 }
 
+// scalar state of the FP32 inner recurrence (kept in FP32 like its vectors: the
+// FP64 pipe of this part is narrow and sits on the critical path of every step)
 struct BScalars {
-    double r0, nu, coef_old, theta_t, c_prev, s_prev, delta_prev, G;
-    double nu_p, delta_pp, theta_p, xcoef_p;
-    double fin_nu, fin_delta, fin_theta, fin_xcoef;
-    double ratio;
+    float r0, rr0, nu, coef_old, theta_t, c_prev, s_prev, delta_prev, G;
+    float nu_p, delta_pp, rtheta_p, xcoef_p;
+    float fin_nu, fin_delta, fin_rtheta, fin_xcoef;
+    float ratio;
     int its, stop;
 };
 
 struct BatchShared {
     BatchMat M;
-    double red[BKPMAX + 1];
-    double wsum[BMAX_WARPS][BKPMAX + 1];
+    float red[BKPMAX + 1];
+    float wsum[BMAX_WARPS][BKPMAX + 1];
     double tmp[BMAX_WARPS + 1];
     float u[BKPMAX];
     float cf[12];
-    double alpha[BKPMAX];
+    float alpha[BKPMAX];
     int off[64];
     double H[(BATCH_RMAX + 1) * BATCH_RMAX];
     double cs[BATCH_RMAX + 1], sn[BATCH_RMAX + 1], g[BATCH_RMAX + 2], hv[BATCH_RMAX + 1], hv2[BATCH_RMAX + 1],
         yv[BATCH_RMAX + 1];
-    double wv[BMMAX];
+    float wv[BMMAX];  // U^T z for the SMW correction (FP32, like the inner solve)
     BScalars sc;
     int item;
     int steps;
@@ -116,20 +118,32 @@ __device__ __forceinline__ void bq_row(const BatchMat& M, int i, float (&q)[KP >
     }
 }
 
-// block reduction of the KP+1 per-thread sums of an mrs step into sh.red (FP64)
+// float-pair (TwoSum) addition, about 44 significant bits without the FP64 pipe
+__device__ __forceinline__ float2 bdf_add(float2 a, float2 b) {
+    float s = a.x + b.x;
+    float bb = s - a.x;
+    float e = (a.x - (s - bb)) + (b.x - bb);
+    e += a.y + b.y;
+    float hi = s + e;
+    float lo = e - (hi - s);
+    return make_float2(hi, lo);
+}
+
+// block reduction of the KP+1 per-thread sums of an mrs step into sh.red: warp sums
+// in FP32, then the warps added in a fixed order in float pairs
 template <int KP>
 __device__ __forceinline__ void bred(float (&tacc)[KP + 1], BatchShared& sh) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int v = 0; v <= KP; ++v) {
         float d = warp_sum(tacc[v]);
-        if (lane == 0) sh.wsum[warp][v] = (double)d;
+        if (lane == 0) sh.wsum[warp][v] = d;
     }
     __syncthreads();
     for (int v = threadIdx.x; v <= KP; v += blockDim.x) {
-        double t = 0.0;
-        for (int w = 0; w < nw; ++w) t += sh.wsum[w][v];
-        sh.red[v] = t;
+        float2 t = make_float2(0.f, 0.f);
+        for (int w = 0; w < nw; ++w) t = bdf_add(t, make_float2(sh.wsum[w][v], 0.f));
+        sh.red[v] = t.x + t.y;
     }
     __syncthreads();
 }
@@ -137,29 +151,29 @@ __device__ __forceinline__ void bred(float (&tacc)[KP + 1], BatchShared& sh) {
 template <int KP>
 __device__ __forceinline__ void bmake_u(const BatchMat& M, BatchShared& sh) {
     for (int m = threadIdx.x; m < KP; m += blockDim.x) {
-        double u = 0.0;
+        float u = 0.f;
         if (m < M.k) {
             if (m + 1 < M.k) u += sh.alpha[m] * sh.red[2 + m] * sh.sc.nu;
             if (m > 0) u -= sh.alpha[m - 1] * sh.red[m] * sh.sc.nu;
         }
-        sh.u[m] = (float)u;
+        sh.u[m] = u;
     }
     __syncthreads();
 }
 
 __device__ __forceinline__ void bset_coefs(BatchShared& sh) {
     BScalars& c = sh.sc;
-    sh.cf[0] = (float)c.nu;
-    sh.cf[2] = (float)c.coef_old;
-    sh.cf[3] = (float)c.nu_p;
-    sh.cf[4] = (float)c.delta_pp;
-    sh.cf[5] = (float)(1.0 / c.theta_p);
-    sh.cf[6] = (float)c.xcoef_p;
+    sh.cf[0] = c.nu;
+    sh.cf[2] = c.coef_old;
+    sh.cf[3] = c.nu_p;
+    sh.cf[4] = c.delta_pp;
+    sh.cf[5] = c.rtheta_p;
+    sh.cf[6] = c.xcoef_p;
     if (c.stop) {
-        sh.cf[7] = (float)c.fin_nu;
-        sh.cf[8] = (float)c.fin_delta;
-        sh.cf[9] = (float)(1.0 / c.fin_theta);
-        sh.cf[10] = (float)c.fin_xcoef;
+        sh.cf[7] = c.fin_nu;
+        sh.cf[8] = c.fin_delta;
+        sh.cf[9] = c.fin_rtheta;
+        sh.cf[10] = c.fin_xcoef;
     }
 }
 
@@ -195,27 +209,28 @@ __device__ int bmrs(const double* u, float* z, float* Y, long long ys, float* P,
     bred<KP>(tacc, sh);
     if (threadIdx.x == 0) {
         BScalars& c = sh.sc;
-        double r0 = sqrt(sh.red[0]);
+        const float r0 = sqrtf(sh.red[0]);
         c.r0 = r0;
-        c.nu = r0 > 0.0 ? 1.0 / r0 : 0.0;
-        c.coef_old = 0.0;
-        c.theta_t = 1.0;
-        c.c_prev = 1.0;
-        c.s_prev = 0.0;
-        c.delta_prev = 0.0;
+        c.rr0 = r0 > 0.f ? 1.f / r0 : 0.f;
+        c.nu = c.rr0;
+        c.coef_old = 0.f;
+        c.theta_t = 1.f;
+        c.c_prev = 1.f;
+        c.s_prev = 0.f;
+        c.delta_prev = 0.f;
         c.G = r0;
-        c.nu_p = 0.0;
-        c.delta_pp = 0.0;
-        c.theta_p = 1.0;
-        c.xcoef_p = 0.0;
-        c.ratio = 0.0;
+        c.nu_p = 0.f;
+        c.delta_pp = 0.f;
+        c.rtheta_p = 1.f;
+        c.xcoef_p = 0.f;
+        c.ratio = 0.f;
         c.its = 0;
-        c.stop = r0 > 0.0 ? 0 : 1;
+        c.stop = r0 > 0.f ? 0 : 1;
         bset_coefs(sh);
     }
     __syncthreads();
     if (sh.sc.stop) {
-        for (int v = threadIdx.x; v < M.k; v += blockDim.x) sh.wv[v] = 0.0;
+        for (int v = threadIdx.x; v < M.k; v += blockDim.x) sh.wv[v] = 0.f;
         __syncthreads();
         return 0;
     }
@@ -258,28 +273,29 @@ __device__ int bmrs(const double* u, float* z, float* Y, long long ys, float* P,
         bred<KP>(tacc, sh);
         if (threadIdx.x == 0) {
             BScalars& c = sh.sc;
-            const double beta = sqrt(sh.red[0]);
-            const double theta = sqrt(c.theta_t * c.theta_t + beta * beta);
-            const double cc = c.theta_t / theta, s = beta / theta;
-            const double delta = -c.s_prev * beta;
-            const double theta_t_next = c.c_prev * theta;
-            const double xcoef = c.G * cc;
-            const double Gn = -c.G * s;
-            c.ratio = fabs(Gn) / c.r0;
+            const float beta = sqrtf(sh.red[0]);
+            const float theta = sqrtf(c.theta_t * c.theta_t + beta * beta);
+            const float rth = 1.f / theta;
+            const float cc = c.theta_t * rth, s = beta * rth;
+            const float delta = -c.s_prev * beta;
+            const float theta_t_next = c.c_prev * theta;
+            const float xcoef = c.G * cc;
+            const float Gn = -c.G * s;
+            c.ratio = fabsf(Gn) * c.rr0;
             c.its = j;
             if (c.ratio < tol || j == maxit) {
                 c.stop = 1;
                 c.fin_nu = c.nu;
                 c.fin_delta = c.delta_prev;
-                c.fin_theta = theta;
+                c.fin_rtheta = rth;
                 c.fin_xcoef = xcoef;
             } else {
                 c.nu_p = c.nu;
                 c.delta_pp = c.delta_prev;
-                c.theta_p = theta;
+                c.rtheta_p = rth;
                 c.xcoef_p = xcoef;
                 c.coef_old = beta * c.nu;
-                c.nu = (beta != 0.0) ? 1.0 / beta : 0.0;
+                c.nu = (beta != 0.f) ? 1.f / beta : 0.f;
                 c.s_prev = s;
                 c.c_prev = cc;
                 c.delta_prev = delta;
@@ -346,7 +362,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_batch(BatchLaunch L) {
         const BatchMat& M = sh.M;
         const int n = M.n;
         for (int d = threadIdx.x; d < M.ndiag && d < 64; d += blockDim.x) sh.off[d] = M.off[d];
-        for (int a = threadIdx.x; a + 1 < M.k && a < BKPMAX; a += blockDim.x) sh.alpha[a] = M.alpha[a];
+        for (int a = threadIdx.x; a + 1 < M.k && a < BKPMAX; a += blockDim.x) sh.alpha[a] = (float)M.alpha[a];
         const double* bcol = L.b + L.row_off[mc.x] * L.nrhs + (long long)mc.y * n;
         double* xcol = L.x + L.row_off[mc.x] * L.nrhs + (long long)mc.y * n;
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -402,13 +418,23 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_batch(BatchLaunch L) {
                 double* zj = Z + j * nm;
                 // z_j = P^-1 v_j: mrs, then z - Y (U^T z)
                 inner += bmrs<KP, QB>(vj, z32, Y, ys, P, L.inner_tol, L.inner_maxit, sh);
-                for (int a = threadIdx.x; a < M.r; a += blockDim.x) sh.wv[M.k + a] = (double)z32[M.neg[a]];
+                for (int a = threadIdx.x; a < M.r; a += blockDim.x) sh.wv[M.k + a] = z32[M.neg[a]];
                 __syncthreads();
+                // FP32 correction (no per-row FP64 operation); rows of Y as float4 when possible
                 for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                    double acc = 0.0;
+                    float acc = 0.f;
                     const float* yr = M.Y32 + (size_t)i * M.m;
-                    for (int c = 0; c < M.m; ++c) acc += (double)yr[c] * sh.wv[c];
-                    zj[i] = (double)z32[i] - acc;
+                    if ((M.m & 3) == 0) {
+                        const float4* y4 = reinterpret_cast<const float4*>(yr);
+                        for (int c = 0; c < (M.m >> 2); ++c) {
+                            const float4 v = __ldg(y4 + c);
+                            acc += v.x * sh.wv[4 * c] + v.y * sh.wv[4 * c + 1] + v.z * sh.wv[4 * c + 2] +
+                                   v.w * sh.wv[4 * c + 3];
+                        }
+                    } else {
+                        for (int c = 0; c < M.m; ++c) acc += yr[c] * sh.wv[c];
+                    }
+                    zj[i] = (double)(z32[i] - acc);
                 }
                 __syncthreads();
                 // w = A_cal z_j = (W Abar) (S W) z_j, into t2
