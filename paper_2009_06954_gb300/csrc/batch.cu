@@ -40,6 +40,7 @@ struct BatchShared {
     float red[BKPMAX + 1];
     float wsum[BMAX_WARPS][BKPMAX + 1];
     double tmp[BMAX_WARPS + 1];
+    double wd[BMAX_WARPS][4];
     float u[BKPMAX];
     float cf[12];
     float alpha[BKPMAX];
@@ -76,7 +77,37 @@ __device__ __forceinline__ double bdot(const double* a, const double* b, int n, 
     return bsum(acc, sh);
 }
 
-// y = A x for a CSR matrix, one row per thread (rows strided over the block)
+// out[a] = V_a^T x for a < cnt (V column-major with leading dimension ld): four dot
+// products per sweep and one block reduction per sweep (warps added in order)
+__device__ __forceinline__ void bdots(const double* V, long long ld, int cnt, const double* x, int n,
+                                      double* out, double (&wd)[BMAX_WARPS][4]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int c0 = 0; c0 < cnt; c0 += 4) {
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const double xi = x[i];
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (c0 + t < cnt) acc[t] += V[(size_t)(c0 + t) * ld + i] * xi;
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const double v = warp_sum(acc[t]);
+            if (lane == 0) wd[warp][t] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 4 && c0 + (int)threadIdx.x < cnt) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += wd[w][threadIdx.x];
+            out[c0 + threadIdx.x] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// y = A x for a CSR matrix, one row per thread (rows strided over the block); the
+// diagonal copies of the one-system path measured slower here, where a CTA's rows are
+// few and the gathers hit L1
 __device__ __forceinline__ void bspmv(const int* rp, const int* ci, const double* v, const double* x, double* y,
                                       int n) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -442,11 +473,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_batch(BatchLaunch L) {
                 bspmv(M.awrp, M.awci, M.awv, t1, t2, n);
                 // two classical Gram-Schmidt passes
                 for (int pass = 0; pass < 2; ++pass) {
-                    for (int a = 0; a <= j; ++a) {
-                        double hva = bdot(V + a * nm, t2, n, sh);
-                        if (threadIdx.x == 0) (pass == 0 ? sh.hv : sh.hv2)[a] = hva;
-                    }
-                    __syncthreads();
+                    bdots(V, nm, j + 1, t2, n, pass == 0 ? sh.hv : sh.hv2, sh.wd);
                     const double* hh = pass == 0 ? sh.hv : sh.hv2;
                     for (int i = threadIdx.x; i < n; i += blockDim.x) {
                         double acc = 0.0;
