@@ -179,9 +179,32 @@ __device__ __forceinline__ void bred(float (&tacc)[KP + 1], BatchShared& sh) {
     __syncthreads();
 }
 
+// as bred, but only warp 0 adds the warps' sums and holds sh.red afterwards (the
+// scalar update that reads it runs in warp 0 too, so one block barrier is saved)
 template <int KP>
-__device__ __forceinline__ void bmake_u(const BatchMat& M, BatchShared& sh) {
-    for (int m = threadIdx.x; m < KP; m += blockDim.x) {
+__device__ __forceinline__ void bred_w0(float (&tacc)[KP + 1], BatchShared& sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int v = 0; v <= KP; ++v) {
+        float d = warp_sum(tacc[v]);
+        if (lane == 0) sh.wsum[warp][v] = d;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        for (int v = lane; v <= KP; v += 32) {
+            float2 t = make_float2(0.f, 0.f);
+            for (int w = 0; w < nw; ++w) t = bdf_add(t, make_float2(sh.wsum[w][v], 0.f));
+            sh.red[v] = t.x + t.y;
+        }
+        __syncwarp();
+    }
+}
+
+// u = nu S_k (Q^T y) by the lanes of warp 0 (after its lane 0 set nu)
+template <int KP>
+__device__ __forceinline__ void bmake_u_w0(const BatchMat& M, BatchShared& sh) {
+    const int lane = threadIdx.x & 31;
+    for (int m = lane; m < KP; m += 32) {
         float u = 0.f;
         if (m < M.k) {
             if (m + 1 < M.k) u += sh.alpha[m] * sh.red[2 + m] * sh.sc.nu;
@@ -189,7 +212,6 @@ __device__ __forceinline__ void bmake_u(const BatchMat& M, BatchShared& sh) {
         }
         sh.u[m] = u;
     }
-    __syncthreads();
 }
 
 __device__ __forceinline__ void bset_coefs(BatchShared& sh) {
@@ -237,8 +259,9 @@ __device__ int bmrs(const double* u, float* z, float* Y, long long ys, float* P,
 #pragma unroll
         for (int m = 0; m < KP; ++m) tacc[1 + m] += q[m] * b;
     }
-    bred<KP>(tacc, sh);
-    if (threadIdx.x == 0) {
+    bred_w0<KP>(tacc, sh);
+    const int lane0 = threadIdx.x & 31, warp0 = threadIdx.x >> 5;
+    if (warp0 == 0 && lane0 == 0) {
         BScalars& c = sh.sc;
         const float r0 = sqrtf(sh.red[0]);
         c.r0 = r0;
@@ -259,13 +282,16 @@ __device__ int bmrs(const double* u, float* z, float* Y, long long ys, float* P,
         c.stop = r0 > 0.f ? 0 : 1;
         bset_coefs(sh);
     }
+    if (warp0 == 0) {
+        __syncwarp();
+        if (!sh.sc.stop) bmake_u_w0<KP>(M, sh);
+    }
     __syncthreads();
     if (sh.sc.stop) {
         for (int v = threadIdx.x; v < M.k; v += blockDim.x) sh.wv[v] = 0.f;
         __syncthreads();
         return 0;
     }
-    bmake_u<KP>(M, sh);
     for (int j = 1; j <= maxit; ++j) {
         float* Ycur = Y + (size_t)((j - 1) % 3) * ys;
         float* Yold = Y + (size_t)((j + 1) % 3) * ys;
@@ -301,8 +327,8 @@ __device__ int bmrs(const double* u, float* z, float* Y, long long ys, float* P,
                 z[i] += txp * pv;
             }
         }
-        bred<KP>(tacc, sh);
-        if (threadIdx.x == 0) {
+        bred_w0<KP>(tacc, sh);
+        if (warp0 == 0 && lane0 == 0) {
             BScalars& c = sh.sc;
             const float beta = sqrtf(sh.red[0]);
             const float theta = sqrtf(c.theta_t * c.theta_t + beta * beta);
@@ -335,6 +361,10 @@ __device__ int bmrs(const double* u, float* z, float* Y, long long ys, float* P,
             }
             bset_coefs(sh);
         }
+        if (warp0 == 0) {
+            __syncwarp();
+            if (!sh.sc.stop) bmake_u_w0<KP>(M, sh);
+        }
         __syncthreads();
         if (sh.sc.stop) {
             float* Pj = P + (size_t)(j & 1) * n;
@@ -355,7 +385,6 @@ __device__ int bmrs(const double* u, float* z, float* Y, long long ys, float* P,
             __syncthreads();
             return sh.sc.its;
         }
-        bmake_u<KP>(M, sh);
     }
     return sh.sc.its;
 }
