@@ -440,3 +440,55 @@ def test_adjoint_finite_differences_dh64(pkg):
         errs.append(abs(fd - dA[e_idx]) / max(abs(fd), 1e-3 * scale_a))
     assert max(errs) <= 1e-6, max(errs)
     s.close()
+
+
+# ----------------------------------------------------------------------------
+# the outer operator and the preconditioner, checked against the oracle's own
+# building blocks evaluated on the set-up the GPU exported (so the comparison
+# isolates the products: diagonal storage for stencils, CSR otherwise)
+# ----------------------------------------------------------------------------
+def _general_sparse(n, seed):
+    rng = np.random.default_rng(seed)
+    K = sp.random(n, n, density=6.0 / n, random_state=rng, data_rvs=rng.standard_normal)
+    A = (K + sp.diags(4.0 + rng.random(n))).tocsr()
+    A.sum_duplicates()
+    A.sort_indices()
+    return A
+
+
+@pytest.mark.parametrize("case", ["stencil", "general"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_operator_and_preconditioner_match_oracle_blocks(pkg, case, precision):
+    if case == "stencil":
+        A, _, _ = dissipative_hamiltonian_3d(side=13, seed=5)
+    else:
+        A = _general_sparse(3001, seed=7)
+    tol_in = 1e-10 if precision == "fp64" else 1e-6
+    s = pkg.Solver(A, precision=precision, inner_tol=tol_in)
+    ex = s.export(A.nnz)
+    Abar, dr, dc, _ = O.equilibrate(A)
+    np.testing.assert_allclose(ex["dr"], dr, rtol=1e-15)
+    np.testing.assert_allclose(ex["dc"], dc, rtol=1e-15)
+    S = sp.csr_matrix((ex["s_val"], Abar.indices.copy(), Abar.indptr.copy()), shape=A.shape)
+    Pat = pattern_of(A)
+    assert np.array_equal(Pat.indptr, Abar.indptr) and np.array_equal(Pat.indices, Abar.indices)
+    w = ex["w"]
+    W = sp.diags(w)
+    Acal = (W @ Abar @ S @ W).tocsr()
+    rng = np.random.default_rng(11)
+    v = rng.standard_normal(A.shape[0])
+    for tr in (False, True):
+        ref = (Acal.T if tr else Acal) @ v
+        got = s.apply_operator(v, transpose=tr)
+        assert np.linalg.norm(got - ref) <= 1e-13 * np.linalg.norm(ref)
+    # P = M~_r + I + J~ = diag(sign d) + J~ (reading R5), J~ from the oracle
+    Jt = O.inner_skew_operator(Abar, S, w)
+    P = (sp.diags(np.sign(ex["d"])) + Jt).tocsr()
+    u = rng.standard_normal(A.shape[0])
+    bound = 1e-8 if precision == "fp64" else 1e-4
+    for tr in (False, True):
+        z, its = s.apply_preconditioner(u, transpose=tr)
+        r = ((P.T if tr else P) @ z) - u
+        assert its > 0
+        assert np.linalg.norm(r) <= bound * np.linalg.norm(u), (tr, np.linalg.norm(r) / np.linalg.norm(u))
+    s.close()
