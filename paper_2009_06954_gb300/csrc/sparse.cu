@@ -524,11 +524,12 @@ constexpr int PAT_WARPS = 4;
 
 __global__ void k_pattern_rows(int n, const int* arp, const int* aci, const int* srp, const int* sci,
                                const int* strp, const int* stci, const int* atrp, const int* atci,
-                               int cap, const int* prp, int* counts, int* pci) {
+                               int cap, const int* cand, const int* prp, int* counts, int* pci) {
     extern __shared__ int smem[];
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int* buf = smem + warp * cap;
     for (int i = blockIdx.x * PAT_WARPS + warp; i < n; i += gridDim.x * PAT_WARPS) {
+        if (cand[i] > cap) continue;  // a heavy row: k_pattern_heavy handles it
         int pos = 0;
         if (lane == 0) buf[0] = i;
         pos = 1;
@@ -577,6 +578,77 @@ __global__ void k_pattern_rows(int n, const int* arp, const int* aci, const int*
     }
 }
 
+// Rows whose candidates do not fit the shared-memory sort: one block per row marks
+// the candidate columns in a bitmap of n bits (global scratch, one per block), then
+// counts them or writes them in ascending order (a block prefix sum over words).
+constexpr int PATH_THREADS = 512;
+
+__global__ void __launch_bounds__(PATH_THREADS) k_pattern_heavy(
+    int n, const int* heavy, int nheavy, const int* arp, const int* aci, const int* srp, const int* sci,
+    const int* strp, const int* stci, const int* atrp, const int* atci, unsigned* bitmaps, int words,
+    const int* prp, int* counts, int* pci) {
+    __shared__ int s_warp[PATH_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = PATH_THREADS / 32;
+    unsigned* bm = bitmaps + (size_t)blockIdx.x * words;
+    const int per = (words + PATH_THREADS - 1) / PATH_THREADS;
+    const int w0 = min(words, (int)threadIdx.x * per), w1 = min(words, w0 + per);
+    for (int h = blockIdx.x; h < nheavy; h += gridDim.x) {
+        const int i = heavy[h];
+        for (int w = threadIdx.x; w < words; w += PATH_THREADS) bm[w] = 0u;
+        __syncthreads();
+        if (threadIdx.x == 0) atomicOr(&bm[i >> 5], 1u << (i & 31));
+        for (int e = arp[i] + warp; e < arp[i + 1]; e += nw) {
+            const int l = aci[e];
+            for (int t = srp[l] + lane; t < srp[l + 1]; t += 32) {
+                const int c = sci[t];
+                atomicOr(&bm[c >> 5], 1u << (c & 31));
+            }
+        }
+        for (int e = strp[i] + warp; e < strp[i + 1]; e += nw) {
+            const int l = stci[e];
+            for (int t = atrp[l] + lane; t < atrp[l + 1]; t += 32) {
+                const int c = atci[t];
+                atomicOr(&bm[c >> 5], 1u << (c & 31));
+            }
+        }
+        __syncthreads();
+        int cnt = 0;
+        for (int w = w0; w < w1; ++w) cnt += __popc(bm[w]);
+        // exclusive prefix of cnt over the block (threads own consecutive word ranges)
+        int incl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int v = lane < nw ? s_warp[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += u;
+            }
+            if (lane < nw) s_warp[lane] = v;  // inclusive totals per warp
+        }
+        __syncthreads();
+        const int before = (warp > 0 ? s_warp[warp - 1] : 0) + incl - cnt;
+        if (counts) {
+            if (threadIdx.x == PATH_THREADS - 1) counts[i] = before + cnt;
+        } else {
+            int pos = prp[i] + before;
+            for (int w = w0; w < w1; ++w) {
+                unsigned bits = bm[w];
+                while (bits) {
+                    const int t = __ffs(bits) - 1;
+                    pci[pos++] = w * 32 + t;
+                    bits &= bits - 1u;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void k_mirror(int n, const int* prp, const int* pci, int* mirror, int* diagpos) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -613,31 +685,64 @@ asss_status build_pattern(const DCsr& Abar, const DCsr& AbarT, const DCsr& S, co
     int hmax = 0;
     ASSS_CUDA(cudaMemcpyAsync(&hmax, mx.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     ASSS_CUDA(cudaStreamSynchronize(s));
+    // rows with at most PAT_LIGHT candidates are sorted in shared memory by one warp;
+    // the rest (power-law rows) go through a bitmap per block
+    constexpr int PAT_LIGHT = 8192;
     int cap = 32;
-    while (cap < hmax) cap <<= 1;
-    size_t smem = (size_t)cap * PAT_WARPS * sizeof(int);
-    if (smem > 200 * 1024) {
-        set_error("a row of Abar*S has %d candidate entries; this build sorts at most %d per row",
-                  hmax, (200 * 1024) / (int)(PAT_WARPS * sizeof(int)));
-        return ASSS_ERR_UNSUPPORTED;
+    while (cap < hmax && cap < PAT_LIGHT) cap <<= 1;
+    std::vector<int> heavy;
+    if (hmax > cap) {
+        std::vector<int> hc(n);
+        ASSS_CUDA(cudaMemcpyAsync(hc.data(), cnt.p, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
+        ASSS_CUDA(cudaStreamSynchronize(s));
+        for (int i = 0; i < n; ++i)
+            if (hc[i] > cap) heavy.push_back(i);
     }
+    DBuf<int> cand, hrows;
+    DBuf<unsigned> bitmaps;
+    const int words = (n + 31) / 32;
+    int hblk = 0;
+    ASSS_TRY(cand.alloc(n));
+    ASSS_CUDA(cudaMemcpyAsync(cand.p, cnt.p, sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
+    if (!heavy.empty()) {
+        ASSS_TRY(to_device(hrows, heavy.data(), (int64_t)heavy.size(), s));
+        hblk = (int)heavy.size() < 256 ? (int)heavy.size() : 256;
+        ASSS_TRY(bitmaps.alloc((int64_t)hblk * words));
+    }
+    size_t smem = (size_t)cap * PAT_WARPS * sizeof(int);
     ASSS_CUDA(cudaFuncSetAttribute(k_pattern_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int grid = cdiv(n, PAT_WARPS);
     if (grid > 65535 * 8) grid = 65535 * 8;
     k_pattern_rows<<<grid, PAT_WARPS * 32, smem, s>>>(n, Abar.rp.p, Abar.ci.p, S.rp.p, S.ci.p, ST.rp.p,
-                                                      ST.ci.p, AbarT.rp.p, AbarT.ci.p, cap, nullptr,
+                                                      ST.ci.p, AbarT.rp.p, AbarT.ci.p, cap, cand.p, nullptr,
                                                       cnt.p, nullptr);
     ASSS_CHECK_LAUNCH();
+    if (hblk) {
+        k_pattern_heavy<<<hblk, PATH_THREADS, 0, s>>>(n, hrows.p, (int)heavy.size(), Abar.rp.p, Abar.ci.p, S.rp.p,
+                                                      S.ci.p, ST.rp.p, ST.ci.p, AbarT.rp.p, AbarT.ci.p, bitmaps.p,
+                                                      words, nullptr, cnt.p, nullptr);
+        ASSS_CHECK_LAUNCH();
+    }
     P.n = n;
     ASSS_TRY(P.rp.alloc(n + 1));
     int64_t tot = 0;
     ASSS_TRY(exclusive_scan(cnt.p, P.rp.p, n, &tot, s));
+    if (tot > 0x7fffffffLL) {
+        set_error("the pattern of Abar*S has %lld entries; this build indexes at most 2^31 - 1", (long long)tot);
+        return ASSS_ERR_UNSUPPORTED;
+    }
     P.nnz = (int)tot;
     ASSS_TRY(P.ci.alloc(tot));
     k_pattern_rows<<<grid, PAT_WARPS * 32, smem, s>>>(n, Abar.rp.p, Abar.ci.p, S.rp.p, S.ci.p, ST.rp.p,
-                                                      ST.ci.p, AbarT.rp.p, AbarT.ci.p, cap, P.rp.p,
+                                                      ST.ci.p, AbarT.rp.p, AbarT.ci.p, cap, cand.p, P.rp.p,
                                                       nullptr, P.ci.p);
     ASSS_CHECK_LAUNCH();
+    if (hblk) {
+        k_pattern_heavy<<<hblk, PATH_THREADS, 0, s>>>(n, hrows.p, (int)heavy.size(), Abar.rp.p, Abar.ci.p, S.rp.p,
+                                                      S.ci.p, ST.rp.p, ST.ci.p, AbarT.rp.p, AbarT.ci.p, bitmaps.p,
+                                                      words, P.rp.p, nullptr, P.ci.p);
+        ASSS_CHECK_LAUNCH();
+    }
     ASSS_TRY(mirror.alloc(tot));
     ASSS_TRY(diagpos.alloc(n));
     k_mirror<<<cdiv(n, 256), 256, 0, s>>>(n, P.rp.p, P.ci.p, mirror.p, diagpos.p);
