@@ -695,6 +695,7 @@ static asss_status ensure_smw(asss_handle* h, int tr) {
 // Q_k^T z comes out of the mrs kernel's final pass.  Step counts and timings stay
 // on the device until the solve collects them.
 static asss_status apply_prec(asss_handle* h, int tr, const double* u, double* out) {
+    NvtxRange nv_("asss:preconditioner");
     const Ctx& c = h->ctx;
     cudaStream_t s = c.stream;
     int n = h->n;
@@ -865,6 +866,7 @@ static asss_status tfqmr_cycle(asss_handle* h, KrylovWork& kw, int tr, const dou
 // ---------------------------------------------------------------------------
 static asss_status fgmres_cycle(asss_handle* h, KrylovWork& kw, int tr, const double* r, double eta, int m,
                                 double* delta, int* steps_out, int* napp_out) {
+    NvtxRange nv_("asss:fgmres-cycle");
     cudaStream_t s = h->ctx.stream;
     int n = h->n;
     int M = kw.m;
@@ -969,6 +971,7 @@ static asss_status fgmres_cycle(asss_handle* h, KrylovWork& kw, int tr, const do
 // refinement loop on the true FP64 residual of the original system (§4.1 stop)
 // ---------------------------------------------------------------------------
 static asss_status refine(asss_handle* h, int tr, const double* rhs, double* x, asss_stats* st) {
+    NvtxRange nv_(tr ? "asss:adjoint-solve" : "asss:solve");
     cudaStream_t s = h->ctx.stream;
     int n = h->n;
     int nb = cdiv(n, 256);
@@ -1087,6 +1090,7 @@ static asss_status refine(asss_handle* h, int tr, const double* rhs, double* x, 
 // set-up
 // ---------------------------------------------------------------------------
 static asss_status do_setup(asss_handle* h, const asss_csr* Ain, asss_stats* st) {
+    NvtxRange nv_("asss:setup");
     const asss_options& o = h->opt;
     Ctx& c = h->ctx;
     cudaStream_t s = c.stream;
@@ -1994,6 +1998,7 @@ asss_status asss_setup_batched(int nmat, const asss_csr* const* A, const asss_op
 }
 
 asss_status asss_solve_batched(asss_batch* B, int nrhs, const double* b, double* x, asss_stats* st) {
+    NvtxRange nv_("asss:batched-solve");
     if (!B || nrhs < 1 || !b || !x) {
         set_error("invalid arguments");
         return ASSS_ERR_ARG;

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <cstdio>
@@ -208,6 +209,17 @@ __device__ __forceinline__ void grid_sync_phase(const GridBarrier& gb, unsigned 
     }
     __syncthreads();
 }
+
+// ---------------------------------------------------------------------------
+// NVTX ranges (header-only NVTX 3: no library to link; a profiler that injects
+// itself, e.g. ncu --nvtx, sees them, otherwise they cost a branch)
+// ---------------------------------------------------------------------------
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ---------------------------------------------------------------------------
 // host helpers shared by the translation units

@@ -901,6 +901,7 @@ static asss_status dispatch_mrs(const Ctx& c, MrsWork* w, const DSell<T>* sell, 
 asss_status mrs_solve(const Ctx& c, MrsWork* w, const MrsOperator& op, bool fp32, double shift, double sign,
                       const double* rhs, double* x64, float* x32, double tol, int maxit, double* qtz, MrsResult* res,
                       bool sync_result) {
+    NvtxRange nv_("asss:mrs");
     int n = w->n;
     if (w->log_n == MrsWork::LOG_CAP) ASSS_TRY(mrs_collect(c, w, nullptr));
     LaunchOut lo{w->log_n, qtz};
