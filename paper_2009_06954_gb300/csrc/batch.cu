@@ -292,11 +292,18 @@ __device__ int bmrs(const double* u, float* z, float* Y, long long ys, float* P,
         __syncthreads();
         return 0;
     }
+    // loop invariants in registers, and the vectors of a step marked as not aliasing one
+    // another, so loads of later rows may be scheduled ahead of this row's stores
+    const float* __restrict__ Ubase = M.U;
+    const long long ust = M.ustride;
+    const int nd = M.ndiag;
+    const int* __restrict__ soff = sh.off;
     for (int j = 1; j <= maxit; ++j) {
-        float* Ycur = Y + (size_t)((j - 1) % 3) * ys;
-        float* Yold = Y + (size_t)((j + 1) % 3) * ys;
-        float* Ynew = Y + (size_t)(j % 3) * ys;
-        float* Pj1 = P + (size_t)((j - 1) & 1) * n;
+        const float* __restrict__ Ycur = Y + (size_t)((j - 1) % 3) * ys;
+        const float* __restrict__ Yold = Y + (size_t)((j + 1) % 3) * ys;
+        float* __restrict__ Ynew = Y + (size_t)(j % 3) * ys;
+        float* __restrict__ Pj1 = P + (size_t)((j - 1) & 1) * n;
+        float* __restrict__ zz = z;
         const float tnu = sh.cf[0], tco = sh.cf[2], tnp = sh.cf[3], tdpp = sh.cf[4], tthp = sh.cf[5],
                     txp = sh.cf[6];
 #pragma unroll
@@ -305,10 +312,10 @@ __device__ int bmrs(const double* u, float* z, float* Y, long long ys, float* P,
             const float yold = j >= 2 ? Yold[i] : 0.f;
             const float pold = j >= 2 ? Pj1[i] : 0.f;
             float acc = 0.f;
-            const float* Ud = M.U + i;
+            const float* Ud = Ubase + i;
             const float* yi = Ycur + i;
-            for (int d = 0; d < M.ndiag; ++d, Ud += M.ustride) {
-                const int m = sh.off[d];
+            for (int d = 0; d < nd; ++d, Ud += ust) {
+                const int m = soff[d];
                 acc += __ldg(Ud) * yi[m] - __ldg(Ud - m) * yi[-m];
             }
             float q[KP > 0 ? KP : 1];
@@ -324,7 +331,7 @@ __device__ int bmrs(const double* u, float* z, float* Y, long long ys, float* P,
             if (j >= 2) {
                 float pv = (tnp * yold - tdpp * pold) * tthp;
                 Pj1[i] = pv;
-                z[i] += txp * pv;
+                zz[i] += txp * pv;
             }
         }
         bred_w0<KP>(tacc, sh);
