@@ -505,10 +505,15 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
 
     for (int j = 1; j <= p.maxit; ++j) {
         const int tb = 4 + 5 * (j - 1);
-        T* Ycur = p.Y + (size_t)((j - 1) % 3) * ys;
-        T* Yold = p.Y + (size_t)((j + 1) % 3) * ys;
-        T* Ynew = p.Y + (size_t)(j % 3) * ys;
-        T* Pj1 = p.P + (size_t)((j - 1) & 1) * n;
+        // the step's vectors do not overlap: restrict lets later rows' loads be scheduled
+        // ahead of this row's stores
+        const T* __restrict__ Ycur = p.Y + (size_t)((j - 1) % 3) * ys;
+        const T* __restrict__ Yold = p.Y + (size_t)((j + 1) % 3) * ys;
+        T* __restrict__ Ynew = p.Y + (size_t)(j % 3) * ys;
+        T* __restrict__ Pj1 = p.P + (size_t)((j - 1) & 1) * n;
+        T* __restrict__ xv = p.x;
+        const T* __restrict__ Ub = p.U;
+        const T* __restrict__ Qr = p.Q;
         const T tnu = s_cf[0], tsg = s_cf[1], tco = s_cf[2];
         const T tnp = s_cf[3], tdpp = s_cf[4], tthp = s_cf[5], txp = s_cf[6];
 #pragma unroll
@@ -544,7 +549,7 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
                 // (J~ y)_i = sum_d U_d[i] y[i + m_d] - U_d[i - m_d] y[i - m_d]; zero halos on
                 // both U (front) and y (both ends) make the loop branch-free
                 if (i < n) {
-                    const T* Ud = p.U + i;
+                    const T* Ud = Ub + i;
                     const T* yi = Ycur + i;
 #pragma unroll 12
                     for (int d = 0; d < p.ndiag; ++d, Ud += p.ustride) {
@@ -567,7 +572,7 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
                         }
                     }
                 } else {
-                    load_qrow<T, KP>(p.Q, i, q);
+                    load_qrow<T, KP>(Qr, i, q);
                 }
                 T dq = (T)0;
 #pragma unroll
@@ -580,7 +585,7 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
                 if (j >= 2) {
                     T pv = (tnp * yold - tdpp * pold) * tthp;
                     Pj1[i] = pv;
-                    p.x[i] += txp * pv;
+                    xv[i] += txp * pv;
                 }
             }
         }
