@@ -71,7 +71,8 @@ __device__ __forceinline__ double bsum(double v, BatchShared& sh) {
     return sh.tmp[BMAX_WARPS];
 }
 
-__device__ __forceinline__ double bdot(const double* a, const double* b, int n, BatchShared& sh) {
+__device__ __forceinline__ double bdot(const double* __restrict__ a, const double* __restrict__ b, int n,
+                                       BatchShared& sh) {
     double acc = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) acc += a[i] * b[i];
     return bsum(acc, sh);
@@ -79,8 +80,9 @@ __device__ __forceinline__ double bdot(const double* a, const double* b, int n, 
 
 // out[a] = V_a^T x for a < cnt (V column-major with leading dimension ld): four dot
 // products per sweep and one block reduction per sweep (warps added in order)
-__device__ __forceinline__ void bdots(const double* V, long long ld, int cnt, const double* x, int n,
-                                      double* out, double (&wd)[BMAX_WARPS][4]) {
+__device__ __forceinline__ void bdots(const double* __restrict__ V, long long ld, int cnt,
+                                      const double* __restrict__ x, int n, double* out,
+                                      double (&wd)[BMAX_WARPS][4]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int c0 = 0; c0 < cnt; c0 += 4) {
         double acc[4] = {0.0, 0.0, 0.0, 0.0};
@@ -108,8 +110,9 @@ __device__ __forceinline__ void bdots(const double* V, long long ld, int cnt, co
 // y = A x for a CSR matrix, one row per thread (rows strided over the block); the
 // diagonal copies of the one-system path measured slower here, where a CTA's rows are
 // few and the gathers hit L1
-__device__ __forceinline__ void bspmv(const int* rp, const int* ci, const double* v, const double* x, double* y,
-                                      int n) {
+__device__ __forceinline__ void bspmv(const int* __restrict__ rp, const int* __restrict__ ci,
+                                      const double* __restrict__ v, const double* __restrict__ x,
+                                      double* __restrict__ y, int n) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         double s = 0.0;
         for (int e = rp[i]; e < rp[i + 1]; ++e) s += v[e] * x[ci[e]];
@@ -247,17 +250,24 @@ __device__ int bmrs(const double* u, float* z, float* Y, long long ys, float* P,
     float tacc[KP + 1];
 #pragma unroll
     for (int v = 0; v <= KP; ++v) tacc[v] = 0.f;
+    {
+    const double* __restrict__ ur = u;
+    float* __restrict__ Y0 = Y;
+    float* __restrict__ zr = z;
+    float* __restrict__ P0 = P;
+    float* __restrict__ P1 = P + n;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        float b = (float)u[i];
-        Y[i] = b;
-        z[i] = 0.f;
-        P[i] = 0.f;
-        P[n + i] = 0.f;
+        float b = (float)ur[i];
+        Y0[i] = b;
+        zr[i] = 0.f;
+        P0[i] = 0.f;
+        P1[i] = 0.f;
         tacc[0] += b * b;
         float q[KP > 0 ? KP : 1];
         bq_row<KP, QB>(M, i, q);
 #pragma unroll
         for (int m = 0; m < KP; ++m) tacc[1 + m] += q[m] * b;
+    }
     }
     bred_w0<KP>(tacc, sh);
     const int lane0 = threadIdx.x & 31, warp0 = threadIdx.x >> 5;
@@ -374,14 +384,14 @@ __device__ int bmrs(const double* u, float* z, float* Y, long long ys, float* P,
         }
         __syncthreads();
         if (sh.sc.stop) {
-            float* Pj = P + (size_t)(j & 1) * n;
+            const float* __restrict__ Pj = P + (size_t)(j & 1) * n;
             const float tn = sh.cf[7], td = sh.cf[8], tth = sh.cf[9], tx = sh.cf[10];
 #pragma unroll
             for (int v = 0; v <= KP; ++v) tacc[v] = 0.f;
             for (int i = threadIdx.x; i < n; i += blockDim.x) {
                 float pv = (tn * Ycur[i] - td * Pj[i]) * tth;
-                float xi = z[i] + tx * pv;
-                z[i] = xi;
+                float xi = zz[i] + tx * pv;
+                zz[i] = xi;
                 float q[KP > 0 ? KP : 1];
                 bq_row<KP, QB>(M, i, q);
 #pragma unroll
@@ -488,20 +498,24 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_batch(BatchLaunch L) {
                 for (int a = threadIdx.x; a < M.r; a += blockDim.x) sh.wv[M.k + a] = z32[M.neg[a]];
                 __syncthreads();
                 // FP32 correction (no per-row FP64 operation); rows of Y as float4 when possible
+                const float* __restrict__ Y32 = M.Y32;
+                const int mm = M.m;
+                const float* __restrict__ z32r = z32;
+                double* __restrict__ zjr = zj;
                 for (int i = threadIdx.x; i < n; i += blockDim.x) {
                     float acc = 0.f;
-                    const float* yr = M.Y32 + (size_t)i * M.m;
-                    if ((M.m & 3) == 0) {
+                    const float* yr = Y32 + (size_t)i * mm;
+                    if ((mm & 3) == 0) {
                         const float4* y4 = reinterpret_cast<const float4*>(yr);
-                        for (int c = 0; c < (M.m >> 2); ++c) {
+                        for (int c = 0; c < (mm >> 2); ++c) {
                             const float4 v = __ldg(y4 + c);
                             acc += v.x * sh.wv[4 * c] + v.y * sh.wv[4 * c + 1] + v.z * sh.wv[4 * c + 2] +
                                    v.w * sh.wv[4 * c + 3];
                         }
                     } else {
-                        for (int c = 0; c < M.m; ++c) acc += yr[c] * sh.wv[c];
+                        for (int c = 0; c < mm; ++c) acc += yr[c] * sh.wv[c];
                     }
-                    zj[i] = (double)(z32[i] - acc);
+                    zjr[i] = (double)(z32r[i] - acc);
                 }
                 __syncthreads();
                 // w = A_cal z_j = (W Abar) (S W) z_j, into t2
@@ -511,10 +525,12 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_batch(BatchLaunch L) {
                 for (int pass = 0; pass < 2; ++pass) {
                     bdots(V, nm, j + 1, t2, n, pass == 0 ? sh.hv : sh.hv2, sh.wd);
                     const double* hh = pass == 0 ? sh.hv : sh.hv2;
+                    const double* __restrict__ Vr = V;
+                    double* __restrict__ t2r = t2;
                     for (int i = threadIdx.x; i < n; i += blockDim.x) {
                         double acc = 0.0;
-                        for (int a = 0; a <= j; ++a) acc += V[a * nm + i] * hh[a];
-                        t2[i] -= acc;
+                        for (int a = 0; a <= j; ++a) acc += Vr[a * nm + i] * hh[a];
+                        t2r[i] -= acc;
                     }
                     __syncthreads();
                 }
