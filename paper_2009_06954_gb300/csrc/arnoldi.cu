@@ -73,8 +73,8 @@ __global__ void __launch_bounds__(AO_THREADS, 2) k_arnoldi_orth(AoParams p) {
     const long long n = p.n;
     const long long r0 = n * blockIdx.x / nblk, r1 = n * (blockIdx.x + 1) / nblk;
     const int nv = p.nv;
-    const double* V = p.V;
-    double* w = p.w;
+    const double* __restrict__ V = p.V;  // v_0..v_j (read) and v_{j+1} (written) do not overlap w
+    double* __restrict__ w = p.w;
     volatile int* err = p.gb.err;
     // a block may still be adding the previous pass's partials while a faster one
     // writes the next pass's, so consecutive passes use the two halves of p.part

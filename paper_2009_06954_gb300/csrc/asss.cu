@@ -154,7 +154,7 @@ __global__ void k_d2f(const double* a, int64_t n, float* b) {
 // FP64 pipe, which is narrow on this part; rows of Y are read as float4 when m
 // is a multiple of 4)
 __global__ void k_smw_apply_f32(const float* __restrict__ z, const float* __restrict__ Y, int m,
-                                const double* __restrict__ w, int n, double* out) {
+                                const double* __restrict__ w, int n, double* __restrict__ out) {
     extern __shared__ float sw_f[];
     for (int t = threadIdx.x; t < m; t += blockDim.x) sw_f[t] = (float)w[t];
     __syncthreads();
