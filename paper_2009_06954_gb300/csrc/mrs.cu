@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
     __shared__ int s_off[FMT == 1 ? MRS_MAXDIAG : 1];
     __shared__ MrsScalars<T> sc;
     __shared__ T s_alpha[MRS_KPMAX];
-    // per-step coefficients in T, set by thread 0 (so no thread converts or divides in FP64):
+    // per-step coefficients in T, set by one thread (the others only read them):
     // 0 sign*nu, 1 sign, 2 beta_{j-1} nu_{j-1}, 3 nu_p, 4 delta_pp, 5 1/theta_p, 6 xcoef_p,
     // 7..10 the final pass: nu, delta, 1/theta, xcoef
     __shared__ T s_cf[12];
@@ -339,7 +339,8 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
     };
     stamp(0);
 
-    // warp sums in T, then FP64 across warps (fixed order) into this block's partial
+    // warp sums in T, then across warps in a fixed order (float pairs for the FP32 solve,
+    // FP64 for the FP64 solve) into this block's partial
     auto block_partials = [&](T(&tacc)[NV], double* buf) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
