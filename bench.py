@@ -34,6 +34,10 @@ WORKLOAD = ("dh3d_100: dissipative-Hamiltonian implicit-Euler step A = E + h(R -
 SIDE = 100
 CPU_SAMPLE_SIDE = 24
 BATCH = {"count": 256, "side_lo": 10, "side_hi": 40, "nrhs": 32, "seed": 3}
+ADJ_SIDE = 64
+ADJ_WORKLOAD = ("adjoint_dh64: gradient of L = ||x - x*||^2 for the dissipative-Hamiltonian step on a 64^3 grid "
+                "(n = 262,144), x* ~ N(0,1): dL/db = lambda from A^T lambda = 2 (x - x*) and dL/dA = -lambda_i x_j "
+                "on A's nonzeros, FP32 inner mrs (tol 1e-6) / FP64 outer FGMRES(60), outer tol 1e-8")
 BATCH_WORKLOAD = ("batched_dh: {count} dissipative-Hamiltonian systems, 3D grids of sides 10..40 (n = 1e3..6.4e4, "
                   "seeded), 32 right-hand sides ~ N(0,1) each ({items} solves per step), one persistent launch "
                   "replayed from a CUDA graph, FP32 inner mrs (tol 1e-6) / FP64 outer FGMRES(24), outer tol 1e-8")
@@ -87,6 +91,51 @@ def batched_worker(budget_s):
             break
     print(json.dumps({"solves": solves, "seconds": secs, "rows": rows, "t_setup_s": t_setup,
                       "max_relres": relres}))
+
+
+def adjoint_worker(budget_s):
+    """Oracle gradients (forward solve untimed, adjoint solve timed) at 24^3."""
+    import numpy as np
+
+    import oracle
+    from workloads import dissipative_hamiltonian_3d
+    A, b, _ = dissipative_hamiltonian_3d(side=CPU_SAMPLE_SIDE, seed=4)
+    n = A.shape[0]
+    t0 = time.perf_counter()
+    o = oracle.AsssOracle(A, inner_tol=1e-6)
+    t_setup = time.perf_counter() - t0
+    x, _ = o.solve(b, tol=1e-8, outer="fgmres")
+    xs = np.random.default_rng(44).standard_normal(n)
+    g = 2.0 * (x - xs)
+    times = []
+    t_start = time.perf_counter()
+    while True:
+        t = time.perf_counter()
+        lam, dA, st = o.solve_adjoint(g, x, tol=1e-8, outer="fgmres")
+        times.append(time.perf_counter() - t)
+        if time.perf_counter() - t_start > budget_s or len(times) >= 50:
+            break
+    print(json.dumps({"n": n, "solves": len(times), "seconds": sum(times), "t_setup_s": t_setup}))
+
+
+def run_adjoint_cpu_baseline(budget_s):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[v] = "1"
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", "--workload", "adjoint_dh64", "--budget",
+           str(budget_s)]
+    p = subprocess.run(cmd, capture_output=True, text=True, env=env, cwd=ROOT)
+    if p.returncode != 0:
+        raise RuntimeError("CPU baseline worker failed:\n" + p.stdout + p.stderr)
+    r = json.loads(p.stdout.strip().splitlines()[-1])
+    n_full = ADJ_SIDE ** 3
+    per_s = r["solves"] / r["seconds"]
+    return {
+        "value": per_s * r["n"] / n_full, "unit": "gradients/s", "cores": 1, "kind": "oracle",
+        "sample": (f"FP64 numpy/scipy oracle, adjoint solve + dL/dA at {CPU_SAMPLE_SIDE}^3 (n = {r['n']}), "
+                   f"{r['solves']} in {r['seconds']:.2f} s ({per_s:.3f}/s), scaled to n = {n_full} by unknowns; "
+                   f"set-up and the forward solve untimed"),
+    }
 
 
 def batch_mean_n():
@@ -385,6 +434,119 @@ def main_batched(args, world, rank, local):
 
 
 # ----------------------------------------------------------------------------
+# gradients through the adjoint solve
+# ----------------------------------------------------------------------------
+def main_adjoint(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_2009_06954_gb300 as pkg
+    from paper_2009_06954_gb300.binding import kernel_launches
+    from workloads import dissipative_hamiltonian_3d
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    A, b, _ = dissipative_hamiltonian_3d(side=ADJ_SIDE, seed=4 + rank)
+    n = A.shape[0]
+    t0 = time.perf_counter()
+    s = pkg.Solver(A, precision="mixed", outer="fgmres", inner_tol=1e-6, outer_tol=1e-8, k=20,
+                   stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    x, stf = s.solve(torch.tensor(b, device=dev))
+    xs = torch.tensor(np.random.default_rng(44 + rank).standard_normal(n), device=dev)
+    g = 2.0 * (x - xs)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        s.solve_adjoint(g, x)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    l0 = kernel_launches()
+    with ClockSampler(dev.index) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            lam, dA, st = s.solve_adjoint(g, x)
+            evs[k][1].record(stream)
+            stats.append(st)
+        torch.cuda.synchronize()
+    launches = kernel_launches() - l0
+    if dist:
+        dist.barrier()
+    total_ms = sum(a.elapsed_time(c) for a, c in evs)
+    tmax = reduce_max(total_ms, dist, dev)
+    # the gradient is checked once on the host: A^T lambda = g to the outer tolerance
+    lam_h = lam.cpu().numpy()
+    g_h = g.cpu().numpy()
+    adj_relres = float(np.linalg.norm(g_h - A.T @ lam_h) / np.linalg.norm(g_h))
+    ok = all(st_["status"] == 0 for st_ in stats) and adj_relres <= 1e-8
+    value = aggregate_rate(world, args.steps, tmax / 1000.0)
+    # end to end from pinned host buffers (g and x in, lambda and dA out)
+    gp = g.cpu().pin_memory()
+    xp = x.cpu().pin_memory()
+    e2e_s = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        s.solve_adjoint(gp, xp)
+        e2e_s += time.perf_counter() - t
+    e2e_val = aggregate_rate(world, args.steps, reduce_max(e2e_s, dist, dev))
+    inner_ms = sum(st_["t_inner_ms"] for st_ in stats)
+    inner_bytes = sum(st_["inner_bytes"] for st_ in stats)
+    inner_launches = sum(st_["inner_launches"] for st_ in stats)
+    peak, peak_kind = _peaks()
+    achieved = inner_bytes / (inner_ms / 1000.0) / 1e9 if inner_ms > 0 else 0.0
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline:
+        try:
+            cb = run_adjoint_cpu_baseline(10.0)
+            cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        except Exception as e:
+            cpu = {"value": None, "unit": "gradients/s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"[:300]}
+    line = {
+        "metric": "gradients/s (adjoint solve + dL/dA) to 1e-8 rel. residual", "value": value,
+        "unit": "gradients/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32-inner/f64-outer", "data": "synthetic",
+        "config": {"workload": ADJ_WORKLOAD, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "256 MB buffer written between steps (not timed)", "setup_s": round(t_setup, 3),
+                   "forward_outer_its": stf["outer_its"], "adjoint_outer_its": stats[-1]["outer_its"],
+                   "adjoint_inner_its_avg": round(stats[-1]["inner_its_avg"], 2),
+                   "host_checked_adjoint_relres": adj_relres, "converged": ok},
+        "gpu_launches": int(launches),
+        "e2e": {"value": e2e_val, "unit": "gradients/s", "h2d_bytes_per_step": 16 * n,
+                "d2h_bytes_per_step": 8 * n + 8 * A.nnz},
+        "roofline": {"bound": "hbm", "kernel": "k_mrs<float,20> (persistent mrs, transposed operator)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak if peak else None,
+                     "peak_source": f"{peak_kind} hbm_gbs", "traffic": None,
+                     "algorithmic_bytes_per_launch": inner_bytes / max(inner_launches, 1),
+                     "avg_launch_ms": inner_ms / max(inner_launches, 1), "launches": inner_launches},
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    s.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------
 # main
 # ----------------------------------------------------------------------------
 def main():
@@ -398,8 +560,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--q-storage", default="f32", choices=["f32", "bf16"],
                     help="storage of the Lanczos basis read by the FP32 inner solve")
-    ap.add_argument("--workload", default="dh3d_100", choices=["dh3d_100", "batched_dh"],
-                    help="dh3d_100: one 1e6-unknown system; batched_dh: 256 systems x 32 right-hand sides")
+    ap.add_argument("--workload", default="dh3d_100", choices=["dh3d_100", "batched_dh", "adjoint_dh64"],
+                    help="dh3d_100: one 1e6-unknown system; batched_dh: 256 systems x 32 right-hand sides; "
+                         "adjoint_dh64: gradients through the adjoint solve")
     ap.add_argument("--batch-count", type=int, default=BATCH["count"],
                     help="systems in the batched workload (smaller counts for profiling captures)")
     args = ap.parse_args()
@@ -408,6 +571,8 @@ def main():
     if args.cpu_worker:
         if args.workload == "batched_dh":
             batched_worker(args.budget)
+        elif args.workload == "adjoint_dh64":
+            adjoint_worker(args.budget)
         else:
             cpu_worker(CPU_SAMPLE_SIDE, args.steps, args.warmup, args.budget)
         return
@@ -416,6 +581,9 @@ def main():
     if args.workload == "batched_dh" and args.impl != "reference":
         main_batched(args, world, rank, local)
         return
+    if args.workload == "adjoint_dh64" and args.impl != "reference":
+        main_adjoint(args, world, rank, local)
+        return
 
     if args.impl == "reference":
         if rank != 0:
@@ -423,17 +591,23 @@ def main():
         warm = max(0, min(args.warmup, 1))
         if args.workload == "batched_dh":
             cb = run_batched_cpu_baseline(120.0, batch_mean_n())
+        elif args.workload == "adjoint_dh64":
+            cb = run_adjoint_cpu_baseline(120.0)
         else:
             cb = run_cpu_baseline(args.steps, warm, 120.0)
         ms = 1000.0 / cb["value"]
-        line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
+        adj = args.workload == "adjoint_dh64"
+        metric = "gradients/s (adjoint solve + dL/dA) to 1e-8 rel. residual" if adj else METRIC
+        unit = "gradients/s" if adj else UNIT
+        line = {"impl": "reference", "metric": metric, "value": cb["value"], "unit": unit, "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": (BATCH_WORKLOAD.format(count=BATCH["count"], items=BATCH["count"] * BATCH["nrhs"])
-                                        if args.workload == "batched_dh" else WORKLOAD),
+                                        if args.workload == "batched_dh" else
+                                        ADJ_WORKLOAD if args.workload == "adjoint_dh64" else WORKLOAD),
                            "reference": "FP64 CPU oracle (oracle/), host cores"},
                 "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
-                "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+                "e2e": {"value": cb["value"], "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
 
