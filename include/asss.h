@@ -99,6 +99,11 @@ typedef struct {
                                  and use those rounded values everywhere (set-up SMW data and the
                                  FP32 inner solve, which then reads Q_k in BF16); P is unchanged,
                                  the deflation slightly less sharp                              */
+    const double* s_values;   /* optional (host or device): values of S on s_pattern, in its CSR order,
+                                 e.g. from asss_export of an earlier set-up of the same matrix and
+                                 options. The least-squares fit of §2 starts from them and stops at
+                                 once when they already meet lls_tol, so a saved S resumes a set-up
+                                 without refitting; NULL: start from S = 0                       */
 } asss_options;
 
 enum { ASSS_FORMAT_AUTO = 0, ASSS_FORMAT_SELL = 1, ASSS_FORMAT_DIAG = 2 };

@@ -47,7 +47,7 @@ class Options(C.Structure):
                 ("restart", C.c_int), ("precision", C.c_int), ("outer", C.c_int), ("r_max", C.c_int),
                 ("seed", C.c_uint64), ("lls_tol", C.c_double), ("lls_maxit", C.c_int),
                 ("zero_tol", C.c_double), ("wait_timeout_ms", C.c_double), ("stream", C.c_void_p),
-                ("inner_format", C.c_int), ("q_bf16", C.c_int)]
+                ("inner_format", C.c_int), ("q_bf16", C.c_int), ("s_values", C.c_void_p)]
 
 FORMATS = {"auto": 0, "sell": 1, "diag": 2}
 
@@ -207,7 +207,7 @@ def _options(keep, **kw):
     if sp_ is not None:
         s = _csr_struct(sp_, keep, values=False)
         o.s_pattern = C.pointer(s)
-    for name in ("row_perm", "dr", "dc"):
+    for name in ("row_perm", "dr", "dc", "s_values"):
         v = kw.pop(name, None)
         if v is not None:
             arr = _host(v, np.int32 if name == "row_perm" else np.float64)
@@ -239,7 +239,9 @@ class Solver:
     A: scipy.sparse matrix (host).  Options follow ``asss_options``: precision
     ('fp64' | 'mixed'), outer ('tfqmr' | 'fgmres'), gamma, k, reorth, s_pattern,
     inner_tol, setup_tol, outer_tol, inner_maxit, outer_maxit, restart, r_max,
-    seed, lls_tol, lls_maxit, zero_tol, wait_timeout_ms, row_perm, dr, dc, stream.
+    seed, lls_tol, lls_maxit, zero_tol, wait_timeout_ms, row_perm, dr, dc, stream, s_values
+    (saved S values to resume the set-up from, e.g. ``export(nnz)["s_val"]`` of an
+    earlier solver for the same matrix).
     """
 
     def __init__(self, A, **opts):

@@ -555,6 +555,7 @@ static void fill_defaults(asss_options* o) {
     o->stream = nullptr;
     o->inner_format = ASSS_FORMAT_AUTO;
     o->q_bf16 = 0;
+    o->s_values = nullptr;
 }
 
 static int pick_kp(int k) {
@@ -1197,8 +1198,10 @@ static asss_status do_setup(asss_handle* h, const asss_csr* Ain, asss_stats* st)
     DBuf<int> mirror, diagpos;
     DBuf<double> Cval, s_val;
     LlsResult lr;
+    DBuf<double> s_start;  // saved S values to resume from (options.s_values)
+    if (o.s_values) ASSS_TRY(to_device(s_start, o.s_values, Spat.nnz, s));
     ASSS_TRY(lls_fit(c, h->Abar, h->AbarT, Spat, o.gamma, o.lls_tol, o.lls_maxit, s_val, P, mirror, diagpos, Cval,
-                     &lr));
+                     &lr, o.s_values ? s_start.p : nullptr));
     st->lls_its = lr.its;
     st->lls_relgrad = lr.relgrad;
     st->nnz_pattern = P.nnz;

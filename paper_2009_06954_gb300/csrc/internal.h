@@ -114,7 +114,7 @@ struct LlsResult {
 // P (symmetric pattern), mirror, diagpos, and C = Abar S on P.
 asss_status lls_fit(const Ctx& c, const DCsr& Abar, const DCsr& AbarT, const DCsr& Spat, double gamma,
                     double tol, int maxit, DBuf<double>& s_val, DCsr& P, DBuf<int>& mirror,
-                    DBuf<int>& diagpos, DBuf<double>& Cval, LlsResult* res);
+                    DBuf<int>& diagpos, DBuf<double>& Cval, LlsResult* res, const double* s0 = nullptr);
 // C = Abar S on P for given S values
 asss_status lls_product_on_pattern(const Ctx& c, const DCsr& Abar, const DCsr& ST, const int* st_src,
                                    const double* s_val, const DCsr& P, const int* prow, double* Cval);

@@ -207,7 +207,7 @@ asss_status lls_product_on_pattern(const Ctx& c, const DCsr& Abar, const DCsr& S
 
 asss_status lls_fit(const Ctx& c, const DCsr& Abar, const DCsr& AbarT, const DCsr& Spat, double gamma, double tol,
                     int maxit, DBuf<double>& s_val, DCsr& P, DBuf<int>& mirror, DBuf<int>& diagpos,
-                    DBuf<double>& Cval, LlsResult* res) {
+                    DBuf<double>& Cval, LlsResult* res, const double* s0) {
     cudaStream_t s = c.stream;
     int n = Abar.n;
     int nS = Spat.nnz;
@@ -271,19 +271,32 @@ asss_status lls_fit(const Ctx& c, const DCsr& Abar, const DCsr& AbarT, const DCs
         ASSS_CHECK_LAUNCH();
         return ASSS_OK;
     };
+    // the tolerance is relative to ||B^T v|| (the gradient at s = 0), also when the
+    // iteration starts from given values s0 (a set-up resumed from saved S values)
     ASSS_TRY(applyBT(rho.p, r.p));
-    ASSS_TRY(precond());
-    ASSS_TRY(vcopy(p.p, z.p, nS, s));
-    ASSS_TRY(dot(r.p, z.p, nS, d_rz, s));
     ASSS_TRY(dot(r.p, r.p, nS, d_rr, s));
     double rr0 = 0.0;
     ASSS_CUDA(cudaMemcpyAsync(&rr0, d_rr, sizeof(double), cudaMemcpyDeviceToHost, s));
     ASSS_CUDA(cudaStreamSynchronize(s));
-    int its = 0;
     double rel = rr0 > 0 ? 1.0 : 0.0;
+    if (s0 && rr0 > 0) {
+        ASSS_CUDA(cudaMemcpyAsync(s_val.p, s0, sizeof(double) * nS, cudaMemcpyDeviceToDevice, s));
+        ASSS_TRY(applyB(s_val.p, q.p));
+        ASSS_TRY(vaxpy(rho.p, q.p, -1.0, nP, s));  // rho = v - B s0
+        ASSS_TRY(applyBT(rho.p, r.p));
+        ASSS_TRY(dot(r.p, r.p, nS, d_rr, s));
+        double rr = 0.0;
+        ASSS_CUDA(cudaMemcpyAsync(&rr, d_rr, sizeof(double), cudaMemcpyDeviceToHost, s));
+        ASSS_CUDA(cudaStreamSynchronize(s));
+        rel = sqrt(rr / rr0);
+    }
+    ASSS_TRY(precond());
+    ASSS_TRY(vcopy(p.p, z.p, nS, s));
+    ASSS_TRY(dot(r.p, z.p, nS, d_rz, s));
+    int its = 0;
     const int check_every = 8;
     int mx = nS > nP ? nS : nP;
-    while (rr0 > 0 && its < maxit) {
+    while (rr0 > 0 && rel > tol && its < maxit) {
         ASSS_TRY(applyB(p.p, q.p));
         ASSS_TRY(dot(q.p, q.p, nP, d_qq, s));
         k_cg_update<<<cdiv(mx, 256), 256, 0, s>>>(s_val.p, p.p, nS, rho.p, q.p, nP, d_rz, d_qq);

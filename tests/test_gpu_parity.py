@@ -522,3 +522,28 @@ def test_powerlaw_rows_pattern_and_fit(pkg):
     assert st["status"] in (0, 5, 6)  # converged, not converged or stagnated: no failure
     assert np.all(np.isfinite(x))
     s.close()
+
+
+# ----------------------------------------------------------------------------
+# resuming a set-up from saved S values (options.s_values)
+# ----------------------------------------------------------------------------
+def test_setup_resumes_from_saved_s_values(pkg):
+    A, b, _ = dissipative_hamiltonian_3d(side=20, seed=6)
+    s1 = pkg.Solver(A, precision="mixed", outer="fgmres", inner_tol=1e-6)
+    assert s1.setup_stats["lls_its"] > 8
+    saved = s1.export(A.nnz)["s_val"].copy()
+    x1, st1 = s1.solve(b)
+    s1.close()
+    s2 = pkg.Solver(A, precision="mixed", outer="fgmres", inner_tol=1e-6, s_values=saved)
+    assert s2.setup_stats["lls_its"] == 0
+    assert s2.setup_stats["lls_relgrad"] <= 1e-13
+    np.testing.assert_array_equal(s2.export(A.nnz)["s_val"], saved)
+    x2, st2 = s2.solve(b)
+    assert st2["status"] == 0 and st2["outer_its"] == st1["outer_its"]
+    assert np.linalg.norm(x2 - x1) <= 1e-12 * np.linalg.norm(x1)
+    # a perturbed start converges back to the fit
+    s3 = pkg.Solver(A, precision="mixed", outer="fgmres", inner_tol=1e-6, s_values=saved * (1 + 1e-3))
+    assert 0 < s3.setup_stats["lls_its"]
+    assert np.linalg.norm(s3.export(A.nnz)["s_val"] - saved) <= 1e-9 * np.linalg.norm(saved)
+    s3.close()
+    s2.close()

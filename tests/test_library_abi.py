@@ -43,3 +43,37 @@ def test_status_strings():
     L = pkg.lib()
     assert L.asss_status_str(0) == b"ok"
     assert L.asss_status_str(8) == b"device wait timed out"
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of asss_csr, asss_options and asss_stats have the C sizes and
+    field offsets (compiled from include/asss.h with the host C compiler)."""
+    import ctypes as C
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    from paper_2009_06954_gb300 import binding as B
+    structs = {"asss_csr": B.CSR, "asss_options": B.Options, "asss_stats": B.Stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "asss.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        if ln:
+            a, b, c = ln.split()
+            got[(a, b)] = int(c)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == C.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
