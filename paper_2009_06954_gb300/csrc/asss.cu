@@ -166,7 +166,7 @@ __global__ void k_smw_apply_f32(const float* __restrict__ z, const float* __rest
         if ((m & 3) == 0) {
             const float4* r4 = reinterpret_cast<const float4*>(row);
             for (int c = 0; c < (m >> 2); ++c) {
-                const float4 v = __ldg(r4 + c);
+                const float4 v = __ldcs(r4 + c);  // Y is streamed once per application: evict-first
                 a += v.x * sw_f[4 * c] + v.y * sw_f[4 * c + 1] + v.z * sw_f[4 * c + 2] + v.w * sw_f[4 * c + 3];
             }
         } else {

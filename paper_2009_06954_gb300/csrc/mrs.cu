@@ -185,7 +185,8 @@ __device__ __forceinline__ void load_qrow(const T* __restrict__ Q, int i, T (&q)
         if constexpr (sizeof(T) == 4 && (KP % 4) == 0) {
 #pragma unroll
             for (int m = 0; m < KP; m += 4) {
-                float4 v = *reinterpret_cast<const float4*>(row + m);
+                // Q is streamed once per step: evict-first keeps the reused vectors in L2
+                float4 v = __ldcs(reinterpret_cast<const float4*>(row + m));
                 q[m] = v.x;
                 q[m + 1] = v.y;
                 q[m + 2] = v.z;
@@ -530,7 +531,7 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
                 if (live) {
                     const uint4* qr = reinterpret_cast<const uint4*>(p.Q16 + (size_t)i * KP);
 #pragma unroll
-                    for (int t = 0; t < KP / 8; ++t) qraw[t] = __ldg(qr + t);
+                    for (int t = 0; t < KP / 8; ++t) qraw[t] = __ldcs(qr + t);  // evict-first, as above
                 }
             }
             T acc = (T)0;

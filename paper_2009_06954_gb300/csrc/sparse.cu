@@ -398,7 +398,7 @@ __global__ void k_dia_spmv(int n, int ndiag, const int* __restrict__ off, const 
     double acc = 0.0;
     for (int d = 0; d < ndiag; ++d) {
         const int j = i + s_off[d];
-        if (j >= 0 && j < n) acc += __ldg(&val[(size_t)d * n + i]) * __ldg(&x[j]);
+        if (j >= 0 && j < n) acc += __ldcs(&val[(size_t)d * n + i]) * __ldg(&x[j]);  // values: evict-first
     }
     y[i] = lscale ? lscale[i] * acc : acc;
 }
