@@ -154,7 +154,7 @@ __global__ void k_d2f(const double* a, int64_t n, float* b) {
 // FP64 pipe, which is narrow on this part; rows of Y are read as float4 when m
 // is a multiple of 4)
 __global__ void k_smw_apply_f32(const float* __restrict__ z, const float* __restrict__ Y, int m,
-                                const double* __restrict__ w, int n, double* __restrict__ out) {
+                                const double* __restrict__ w, int n, double* __restrict__ out, int evict_first) {
     extern __shared__ float sw_f[];
     for (int t = threadIdx.x; t < m; t += blockDim.x) sw_f[t] = (float)w[t];
     __syncthreads();
@@ -166,7 +166,7 @@ __global__ void k_smw_apply_f32(const float* __restrict__ z, const float* __rest
         if ((m & 3) == 0) {
             const float4* r4 = reinterpret_cast<const float4*>(row);
             for (int c = 0; c < (m >> 2); ++c) {
-                const float4 v = __ldcs(r4 + c);  // Y is streamed once per application: evict-first
+                const float4 v = evict_first ? __ldcs(r4 + c) : __ldg(r4 + c);  // Y: read once per application
                 a += v.x * sw_f[4 * c] + v.y * sw_f[4 * c + 1] + v.z * sw_f[4 * c + 2] + v.w * sw_f[4 * c + 3];
             }
         } else {
@@ -725,7 +725,8 @@ static asss_status apply_prec(asss_handle* h, int tr, const double* u, double* o
             ASSS_CHECK_LAUNCH();
         }
         k_smw_apply_f32<<<cdiv(n, 256), 256, sizeof(float) * (S.m > 0 ? S.m : 1), s>>>(
-            h->z32.p, S.m > 0 ? S.Y32.p : nullptr, S.m, h->wv.p, n, out);
+            h->z32.p, S.m > 0 ? S.Y32.p : nullptr, S.m, h->wv.p, n, out,
+            stream_evict_first(c, (long long)n * (4LL * h->kp + 28) + 4LL * h->D32.nnz) ? 1 : 0);
         ASSS_CHECK_LAUNCH();
     } else {
         double* z = (S.m > 0) ? h->zt.p : out;

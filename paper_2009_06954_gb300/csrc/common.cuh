@@ -85,6 +85,7 @@ asss_status process_scratch(int slot, int64_t count, double** out);
 // (stencils): val[d*n + i] = A(i, i + off[d]), 0 where absent or outside the matrix.
 struct DDia {
     bool tried = false;  // attach_dia ran on this matrix (attached or not)
+    bool stream = false; // values loaded evict-first (two products' values exceed L2)
     int ndiag = 0;
     DBuf<int> off;       // ascending signed offsets
     DBuf<double> val;
@@ -230,7 +231,15 @@ struct Ctx {
     int sms = 0;
     int clock_khz = 0;
     long long wait_cycles = 0;
+    long long l2_bytes = 0;
 };
+
+// Data read once per pass is loaded evict-first only when the pass's working set is
+// larger than L2: then it would only push out the vectors that the next pass reuses;
+// when everything fits, normal loads keep the streamed data in L2 for the next pass.
+inline bool stream_evict_first(const Ctx& c, long long pass_bytes) {
+    return c.l2_bytes > 0 && pass_bytes > c.l2_bytes * 3 / 4;
+}
 asss_status make_ctx(Ctx& c, void* stream, double wait_timeout_ms);
 
 // pointer classification

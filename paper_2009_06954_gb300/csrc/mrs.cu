@@ -154,6 +154,7 @@ struct MrsParams {
     double* out_ratio;
     unsigned long long* trace;  // optional timeline (block 0): %globaltimer at phase boundaries
     const int* skip;     // optional: when *skip != 0 at launch the kernel only logs its = -1
+    int qcs;             // load Q rows evict-first (the step's data exceed L2)
     double* qtz;         // optional: Q^T x (k values) computed in the final pass
     double* qtz_part;    // [KP][nblk] block partials for it
     unsigned* qtz_done;  // last-block counter (left at 0)
@@ -178,15 +179,18 @@ __device__ __forceinline__ void load_qrow16(const __nv_bfloat16* __restrict__ Q,
     }
 }
 
+// cs: Q is streamed once per step and the step's data exceed L2, so its rows are
+// loaded evict-first to keep the reused vectors in L2 (see stream_evict_first)
 template <class T, int KP>
-__device__ __forceinline__ void load_qrow(const T* __restrict__ Q, int i, T (&q)[KP > 0 ? KP : 1]) {
+__device__ __forceinline__ void load_qrow(const T* __restrict__ Q, int i, T (&q)[KP > 0 ? KP : 1],
+                                          bool cs = false) {
     if constexpr (KP > 0) {
         const T* row = Q + (size_t)i * KP;
         if constexpr (sizeof(T) == 4 && (KP % 4) == 0) {
 #pragma unroll
             for (int m = 0; m < KP; m += 4) {
-                // Q is streamed once per step: evict-first keeps the reused vectors in L2
-                float4 v = __ldcs(reinterpret_cast<const float4*>(row + m));
+                const float4* a = reinterpret_cast<const float4*>(row + m);
+                float4 v = cs ? __ldcs(a) : __ldg(a);
                 q[m] = v.x;
                 q[m + 1] = v.y;
                 q[m + 2] = v.z;
@@ -454,7 +458,7 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
             tacc[0] += b * b;
             T q[KP > 0 ? KP : 1];
             if constexpr (QB) load_qrow16<T, KP>(p.Q16, i, q);
-            else load_qrow<T, KP>(p.Q, i, q);
+            else load_qrow<T, KP>(p.Q, i, q, p.qcs != 0);
 #pragma unroll
             for (int m = 0; m < KP; ++m) tacc[1 + m] += q[m] * b;
         }
@@ -531,7 +535,7 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
                 if (live) {
                     const uint4* qr = reinterpret_cast<const uint4*>(p.Q16 + (size_t)i * KP);
 #pragma unroll
-                    for (int t = 0; t < KP / 8; ++t) qraw[t] = __ldcs(qr + t);  // evict-first, as above
+                    for (int t = 0; t < KP / 8; ++t) qraw[t] = p.qcs ? __ldcs(qr + t) : __ldg(qr + t);
                 }
             }
             T acc = (T)0;
@@ -574,7 +578,7 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
                         }
                     }
                 } else {
-                    load_qrow<T, KP>(Qr, i, q);
+                    load_qrow<T, KP>(Qr, i, q, p.qcs != 0);
                 }
                 T dq = (T)0;
 #pragma unroll
@@ -653,7 +657,7 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
                         if (p.qtz) {
                             T q[KP];
                             if constexpr (QB) load_qrow16<T, KP>(p.Q16, i, q);
-                            else load_qrow<T, KP>(p.Q, i, q);
+                            else load_qrow<T, KP>(p.Q, i, q, p.qcs != 0);
 #pragma unroll
                             for (int m = 0; m < KP; ++m) tacc[1 + m] += q[m] * xi;
                         }
@@ -782,6 +786,10 @@ static asss_status launch_mrs(const Ctx& c, MrsWork* w, const OpView<T>& J, cons
     prm.qtz = (KP > 0 && k > 0) ? lo.qtz : nullptr;
     prm.trace = w->trace.p;
     prm.skip = w->skip;
+    {
+        const long long qrow = QB ? 2LL * KP : (long long)sizeof(T) * KP;
+        prm.qcs = stream_evict_first(c, J.nnz * (long long)sizeof(T) + (long long)J.n * (7LL * sizeof(T) + qrow)) ? 1 : 0;
+    }
     prm.qtz_part = w->qtz_part.p;
     prm.qtz_done = w->qtz_done.p;
     void* args[] = {&prm};

@@ -55,6 +55,9 @@ asss_status make_ctx(Ctx& c, void* stream, double wait_timeout_ms) {
     double ms = wait_timeout_ms > 0 ? wait_timeout_ms : 2000.0;
     // clock64 counts SM cycles; use the maximum clock so the budget is an upper bound in time
     c.wait_cycles = (long long)(ms * (double)c.clock_khz);
+    int l2 = 0;
+    ASSS_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c.device));
+    c.l2_bytes = l2;
     return ASSS_OK;
 }
 
@@ -389,7 +392,8 @@ __global__ void k_spmv(int n, const int* __restrict__ rp, const int* __restrict_
 constexpr int DIA_MAX = 16;
 
 __global__ void k_dia_spmv(int n, int ndiag, const int* __restrict__ off, const double* __restrict__ val,
-                           const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ lscale) {
+                           const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ lscale,
+                           int evict_first) {
     __shared__ int s_off[DIA_MAX];
     if (threadIdx.x < ndiag) s_off[threadIdx.x] = off[threadIdx.x];
     __syncthreads();
@@ -398,7 +402,10 @@ __global__ void k_dia_spmv(int n, int ndiag, const int* __restrict__ off, const 
     double acc = 0.0;
     for (int d = 0; d < ndiag; ++d) {
         const int j = i + s_off[d];
-        if (j >= 0 && j < n) acc += __ldcs(&val[(size_t)d * n + i]) * __ldg(&x[j]);  // values: evict-first
+        if (j >= 0 && j < n) {
+            const double v = evict_first ? __ldcs(&val[(size_t)d * n + i]) : __ldg(&val[(size_t)d * n + i]);
+            acc += v * __ldg(&x[j]);
+        }
     }
     y[i] = lscale ? lscale[i] * acc : acc;
 }
@@ -463,6 +470,11 @@ asss_status attach_dia(DCsr& A, int max_diag, double min_fill, int* ok, cudaStre
     k_dia_fill<<<cdiv(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, A.v.p, A.dia.off.p, (int)off.size(), A.dia.val.p);
     ASSS_CHECK_LAUNCH();
     A.dia.ndiag = (int)off.size();
+    // the outer operator applies two such products back to back
+    int dev = 0, l2 = 0;
+    ASSS_CUDA(cudaGetDevice(&dev));
+    ASSS_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+    A.dia.stream = 2LL * (long long)off.size() * n * (long long)sizeof(double) > (long long)l2 * 3 / 4;
     *ok = 1;
     return ASSS_OK;
 }
@@ -470,7 +482,8 @@ asss_status attach_dia(DCsr& A, int max_diag, double min_fill, int* ok, cudaStre
 asss_status spmv(const DCsr& A, const double* x, double* y, const double* lscale, cudaStream_t s) {
     int n = A.n;
     if (A.dia.ndiag > 0) {
-        k_dia_spmv<<<cdiv(n, 256), 256, 0, s>>>(n, A.dia.ndiag, A.dia.off.p, A.dia.val.p, x, y, lscale);
+        k_dia_spmv<<<cdiv(n, 256), 256, 0, s>>>(n, A.dia.ndiag, A.dia.off.p, A.dia.val.p, x, y, lscale,
+                                                 A.dia.stream ? 1 : 0);
         ASSS_CHECK_LAUNCH();
         return ASSS_OK;
     }
