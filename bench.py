@@ -398,7 +398,7 @@ def main_batched(args, world, rank, local):
         return
     mean_n = bs.total / len(batch)
     cpu = None
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:  # the oracle baseline is timed at N = 1 only
         try:
             cb = run_batched_cpu_baseline(15.0, mean_n)
             cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
@@ -513,7 +513,7 @@ def main_adjoint(args, world, rank, local):
             dist.destroy_process_group()
         return
     cpu = None
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:  # the oracle baseline is timed at N = 1 only
         try:
             cb = run_adjoint_cpu_baseline(10.0)
             cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
@@ -695,7 +695,7 @@ def main():
         return
 
     cpu = None
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:  # the oracle baseline is timed at N = 1 only
         try:
             cb = run_cpu_baseline(500, 1, 10.0)
             cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
