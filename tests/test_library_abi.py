@@ -77,3 +77,24 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "size")] == C.sizeof(py), cname
         for fname, _ in py._fields_:
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def test_batched_packing_follows_the_abi_layout():
+    """System m occupies [off_m * nrhs, (off_m + n_m) * nrhs) of the concatenated vector,
+    column-major n_m x nrhs inside (the layout asss_solve_batched documents)."""
+    import numpy as np
+    from paper_2009_06954_gb300.binding import BatchSolver
+    bs = object.__new__(BatchSolver)  # the packing needs only the sizes
+    bs.sizes = [3, 5, 2]
+    bs.offsets = np.concatenate([[0], np.cumsum(bs.sizes)]).astype(np.int64)
+    bs.total = int(bs.offsets[-1])
+    nrhs = 4
+    rng = np.random.default_rng(0)
+    blocks = [rng.standard_normal((n, nrhs)) for n in bs.sizes]
+    v = bs.pack(blocks)
+    assert v.shape == (bs.total * nrhs,)
+    for m, (o, n) in enumerate(zip(bs.offsets[:-1], bs.sizes)):
+        for c in range(nrhs):
+            np.testing.assert_array_equal(v[o * nrhs + c * n: o * nrhs + (c + 1) * n], blocks[m][:, c])
+    for a, b in zip(bs.unpack(v, nrhs), blocks):
+        np.testing.assert_array_equal(a, b)
