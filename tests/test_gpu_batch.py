@@ -110,3 +110,27 @@ def test_batched_rejects_wrong_lengths(pkg):
     with pytest.raises(ValueError):
         bs.solve(np.zeros(A.shape[0]), nrhs=1)
     bs.close()
+
+
+@pytest.mark.slow
+def test_batched_full_size_workload(pkg):
+    """The 256-system x 32-column workload of the batched benchmark, in the launch
+    configuration the benchmark times: every item meets the tolerance on the host, and
+    sampled items (the smallest systems, one column each) agree with the FP64 oracle."""
+    import oracle as O
+    batch = batched_dissipative_hamiltonian(count=256, side_lo=10, side_hi=40, nrhs=32, seed=3)
+    As = [A for A, _ in batch]
+    Bs = [B for _, B in batch]
+    bs = pkg.BatchSolver(As, inner_tol=1e-6, outer_tol=1e-8, k=20, restart=24)
+    x, st = bs.solve(bs.pack(Bs), nrhs=32)
+    assert st["status"] == 0 and st["inner_solves"] == 256 * 32
+    X = bs.unpack(x, 32)
+    worst = max(float(np.max(np.linalg.norm(B - A @ Xm, axis=0) / np.linalg.norm(B, axis=0)))
+                for (A, B), Xm in zip(batch, X))
+    assert worst <= 1e-8
+    order = np.argsort([A.shape[0] for A in As])[:3]
+    for m in order:
+        o = O.AsssOracle(As[m], inner_tol=1e-6)
+        xo, sto = o.solve(Bs[m][:, 5], tol=1e-8, outer="fgmres")
+        assert np.linalg.norm(X[m][:, 5] - xo) <= 1e-6 * np.linalg.norm(xo)
+    bs.close()
