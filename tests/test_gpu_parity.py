@@ -547,3 +547,43 @@ def test_setup_resumes_from_saved_s_values(pkg):
     assert np.linalg.norm(s3.export(A.nnz)["s_val"] - saved) <= 1e-9 * np.linalg.norm(saved)
     s3.close()
     s2.close()
+
+
+# ----------------------------------------------------------------------------
+# an indefinite matrix: diag(Abar S) has negative entries, so M~_r has rank r > 0 and
+# the SMW correction carries U_r next to the Lanczos vectors (§3, Fig. 1; Eq. smw)
+# ----------------------------------------------------------------------------
+def _indefinite(n, seed, sym, skew):
+    rng = np.random.default_rng(seed)
+    K = sp.random(n, n, density=5.0 / n, random_state=rng, data_rvs=rng.standard_normal)
+    D = sp.diags(rng.choice([-1.0, 1.0], size=n) * (1.0 + rng.random(n)))
+    A = (D + 0.5 * (K + K.T) * sym + 0.5 * (K - K.T) * skew).tocsr()
+    A.sum_duplicates()
+    A.sort_indices()
+    return A
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_negative_pivots_low_rank_part(pkg, precision):
+    A = _indefinite(600, 4, 0.6, 1.0)
+    Sd = pattern_diagonal(A.shape[0])
+    o = O.AsssOracle(A, S_pattern=Sd, gamma=0.1, inner_tol=1e-10)
+    assert o.r > 0
+    tol_in = 1e-10 if precision == "fp64" else 1e-6
+    s = pkg.Solver(A, s_pattern=Sd, gamma=0.1, precision=precision, inner_tol=tol_in)
+    assert s.setup_stats["r"] == o.r
+    ex = s.export(Sd.nnz)
+    np.testing.assert_array_equal(np.sort(ex["neg"]), np.sort(np.flatnonzero(o.d < 0)))
+    np.testing.assert_allclose(ex["d"], o.d, rtol=1e-8, atol=1e-12 * np.abs(o.d).max())
+    # P z = u with P = diag(sign d) + J~ built by the oracle from the exported S
+    Abar, _, _, _ = O.equilibrate(A)
+    S = sp.csr_matrix((ex["s_val"], Sd.indices.copy(), Sd.indptr.copy()), shape=A.shape)
+    Jt = O.inner_skew_operator(Abar, S, ex["w"])
+    P = (sp.diags(np.sign(ex["d"])) + Jt).tocsr()
+    u = np.random.default_rng(12).standard_normal(A.shape[0])
+    bound = 1e-8 if precision == "fp64" else 1e-4
+    for tr in (False, True):
+        z, _ = s.apply_preconditioner(u, transpose=tr)
+        r = ((P.T if tr else P) @ z) - u
+        assert np.linalg.norm(r) <= bound * np.linalg.norm(u), (tr, np.linalg.norm(r) / np.linalg.norm(u))
+    s.close()
