@@ -99,6 +99,21 @@ def test_mrs_edge_cases(pkg):
     assert its == 2
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_mrs_stops_at_maxit_with_the_oracle_iterate(pkg, precision):
+    """An iteration limit below convergence: its = maxit, the ratio above tol, and x is
+    the oracle's iterate after the same number of steps (App. B, reading R9)."""
+    n = 2000
+    J = random_skew(n, 10, seed=31)
+    b = np.random.default_rng(32).standard_normal(n)
+    xo, its_o, ratio_o, _ = O.mrs(1.0, lambda V: J @ V, b, 3, 1e-14)
+    x, its, ratio = pkg.mrs(J, b, tol=1e-14, maxit=3, precision=precision)
+    assert its == 3 and its_o == 3
+    rtol = 1e-12 if precision == "fp64" else 2e-5
+    assert abs(ratio - ratio_o) <= rtol * ratio_o
+    assert np.linalg.norm(x - xo) <= rtol * np.linalg.norm(xo)
+
+
 # ----------------------------------------------------------------------------
 # skew-Lanczos (Fig. 2)
 # ----------------------------------------------------------------------------
@@ -113,6 +128,28 @@ def test_skew_lanczos_matches_oracle(pkg, reorth):
     assert Qg.shape == Qo.shape
     np.testing.assert_allclose(ag, ao, rtol=1e-10)
     assert np.abs(Qg - Qo).max() <= 1e-9
+
+
+def test_skew_lanczos_breakdown_matches_oracle(pkg):
+    """q1 inside an invariant subspace of dimension 4 (two 2x2 rotation blocks of a
+    block-diagonal skew J): the process stops with k_eff = 4 (Fig. 2 breakdown)."""
+    nb = 40
+    rng = np.random.default_rng(21)
+    w = 0.5 + rng.random(nb)
+    rows, cols, vals = [], [], []
+    for b, wb in enumerate(w):
+        i = 2 * b
+        rows += [i, i + 1]
+        cols += [i + 1, i]
+        vals += [wb, -wb]
+    J = sp.csr_matrix((vals, (rows, cols)), shape=(2 * nb, 2 * nb))
+    q1 = np.zeros(2 * nb)
+    q1[[4, 5, 10, 11]] = rng.standard_normal(4)
+    Qo, ao = O.skew_lanczos(J, q1, 10)
+    Qg, ag = pkg.skew_lanczos(J, q1, 10)
+    assert Qo.shape[1] == 4 and Qg.shape[1] == 4
+    np.testing.assert_allclose(ag, ao, rtol=1e-12)
+    assert np.abs(Qg - Qo).max() <= 1e-12
 
 
 # ----------------------------------------------------------------------------
