@@ -134,3 +134,25 @@ def test_batched_full_size_workload(pkg):
         xo, sto = o.solve(Bs[m][:, 5], tol=1e-8, outer="fgmres")
         assert np.linalg.norm(X[m][:, 5] - xo) <= 1e-6 * np.linalg.norm(xo)
     bs.close()
+
+
+def test_batched_bf16_basis_and_a_tiny_system(pkg, batch):
+    # the BF16 deflation basis (the kernel reads Q in BF16): same tolerance, nearly the
+    # same solutions as the FP32 basis
+    As = [A for A, _ in batch[:5]]
+    Bs = [B[:, :2] for _, B in batch[:5]]
+    x32, st32 = pkg.BatchSolver(As, inner_tol=1e-6).solve(np.concatenate(
+        [b.ravel(order="F") for b in Bs]), nrhs=2)
+    b16 = pkg.BatchSolver(As, inner_tol=1e-6, q_bf16=True)
+    x16, st16 = b16.solve(b16.pack(Bs), nrhs=2)
+    assert st16["status"] == 0 and st16["relres"] <= 1e-8
+    _check_columns(list(zip(As, Bs)), b16.unpack(x16, 2), Bs)
+    assert np.linalg.norm(x16 - x32) <= 1e-6 * np.linalg.norm(x32)
+    b16.close()
+    # a 27-row system (smaller than one 32-row slice, fewer Lanczos vectors than asked)
+    A, b, _ = dissipative_hamiltonian_3d(side=3, seed=8)
+    bs = pkg.BatchSolver([A], inner_tol=1e-6)
+    x, st = bs.solve(b, nrhs=1)
+    assert st["status"] == 0
+    assert np.linalg.norm(b - A @ x) <= 1e-8 * np.linalg.norm(b)
+    bs.close()
