@@ -32,7 +32,8 @@ WORKLOAD = ("dh3d_100: dissipative-Hamiltonian implicit-Euler step A = E + h(R -
             "(n = 1,000,000, nnz = 6,940,000), S on the pattern of A, k = 20, FP32 inner mrs "
             "(tol 1e-6) / FP64 outer FGMRES(60), outer tol 1e-8")
 SIDE = 100
-CPU_SAMPLE_SIDE = 24
+CPU_SAMPLE_SIDE = 40
+ADJ_CPU_SIDE = 24
 BATCH = {"count": 256, "side_lo": 10, "side_hi": 40, "nrhs": 32, "seed": 3}
 ADJ_SIDE = 64
 ADJ_WORKLOAD = ("adjoint_dh64: gradient of L = ||x - x*||^2 for the dissipative-Hamiltonian step on a 64^3 grid "
@@ -79,6 +80,7 @@ def batched_worker(budget_s):
         A, B = batch[m]
         t0 = time.perf_counter()
         o = oracle.AsssOracle(A, inner_tol=1e-6)
+        o._smw(False)   # the SMW data the oracle would otherwise build inside the first solve
         t_setup += time.perf_counter() - t0
         for c in range(2):
             t = time.perf_counter()
@@ -99,12 +101,13 @@ def adjoint_worker(budget_s):
 
     import oracle
     from workloads import dissipative_hamiltonian_3d
-    A, b, _ = dissipative_hamiltonian_3d(side=CPU_SAMPLE_SIDE, seed=4)
+    A, b, _ = dissipative_hamiltonian_3d(side=ADJ_CPU_SIDE, seed=4)
     n = A.shape[0]
     t0 = time.perf_counter()
     o = oracle.AsssOracle(A, inner_tol=1e-6)
     t_setup = time.perf_counter() - t0
     x, _ = o.solve(b, tol=1e-8, outer="fgmres")
+    o._smw(True)        # the transposed SMW data (set-up of the adjoint), outside the timed solves
     xs = np.random.default_rng(44).standard_normal(n)
     g = 2.0 * (x - xs)
     times = []
@@ -132,9 +135,10 @@ def run_adjoint_cpu_baseline(budget_s):
     per_s = r["solves"] / r["seconds"]
     return {
         "value": per_s * r["n"] / n_full, "unit": "gradients/s", "cores": 1, "kind": "oracle",
-        "sample": (f"FP64 numpy/scipy oracle, adjoint solve + dL/dA at {CPU_SAMPLE_SIDE}^3 (n = {r['n']}), "
+        "sample": (f"FP64 numpy/scipy oracle, adjoint solve + dL/dA at {ADJ_CPU_SIDE}^3 (n = {r['n']}), "
                    f"{r['solves']} in {r['seconds']:.2f} s ({per_s:.3f}/s), scaled to n = {n_full} by unknowns; "
                    f"set-up and the forward solve untimed"),
+        "solves": r["solves"], "seconds": r["seconds"],
     }
 
 
@@ -164,11 +168,32 @@ def run_batched_cpu_baseline(budget_s, mean_n):
                    f"batch by size, mean n = {sample_n:.0f}) in {r['seconds']:.2f} s ({per_s:.3f} solves/s), "
                    f"scaled to the batch's mean n = {mean_n:.0f} by unknowns; set-up {r['t_setup_s']:.1f} s "
                    f"untimed"),
-        "max_relres": r["max_relres"],
+        "max_relres": r["max_relres"], "solves": r["solves"], "seconds": r["seconds"],
     }
 
 
-def cpu_worker(side, steps, warmup, budget_s):
+_ORACLE = {}
+
+
+def _oracle_solve(i):
+    """One oracle solve of right-hand side i in a forked pool process (CPU only)."""
+    o, rhs = _ORACLE["o"], _ORACLE["rhs"]
+    t = time.perf_counter()
+    _, st = o.solve(rhs[i % len(rhs)], tol=1e-8, outer="fgmres")
+    return time.perf_counter() - t, st["relres"], st["inner_its_avg"], st["outer_its"]
+
+
+def cpu_worker(side, steps, warmup, budget_s, procs, xout):
+    """The FP64 oracle's solve phase on the side^3 instance of the bench's generator.
+
+    Set-up once (untimed), then: one solve alone (the one-thread rate; its x is
+    written to xout for the relative-error check of the GPU legs), then `warmup`
+    untimed and up to `steps` timed rounds of `procs` concurrent solves, one per
+    forked process (all host cores, BLAS pinned to one thread each), stopping
+    early once `budget_s` of timed rounds have run.  This process never touches
+    the GPU, so forking after the set-up is safe."""
+    import multiprocessing as mp
+
     import numpy as np
 
     import oracle
@@ -177,45 +202,74 @@ def cpu_worker(side, steps, warmup, budget_s):
     n = A.shape[0]
     t0 = time.perf_counter()
     o = oracle.AsssOracle(A, inner_tol=1e-6)
+    rhs = _make_rhs(parts, n, 1, 8)
+    o.solve(rhs[0], tol=1e-8, outer="fgmres")   # the oracle builds its SMW data on first use: set-up
     t_setup = time.perf_counter() - t0
-    rhs = _make_rhs(parts, n, 1, 4)
-    for w in range(warmup):
-        o.solve(rhs[w % 4], tol=1e-8, outer="fgmres")
-    times = []
-    relres = []
-    t_start = time.perf_counter()
-    for s in range(steps):
-        t = time.perf_counter()
-        x, st = o.solve(rhs[s % 4], tol=1e-8, outer="fgmres")
-        times.append(time.perf_counter() - t)
-        relres.append(st["relres"])
-        if budget_s and time.perf_counter() - t_start > budget_s and s + 1 >= 1:
-            break
-    print(json.dumps({"n": n, "solves": len(times), "seconds": sum(times), "t_setup_s": t_setup,
-                      "max_relres": max(relres), "inner_avg": st["inner_its_avg"],
-                      "outer_its": st["outer_its"]}))
+    _ORACLE["o"], _ORACLE["rhs"] = o, rhs
+    t = time.perf_counter()
+    x0, st0 = o.solve(rhs[0], tol=1e-8, outer="fgmres")
+    t_one = time.perf_counter() - t
+    if xout:
+        np.save(xout, x0)
+    rounds, relres, inner, outer = [], [st0["relres"]], [st0["inner_its_avg"]], [st0["outer_its"]]
+    with mp.get_context("fork").Pool(procs) as pool:
+        for w in range(warmup):
+            pool.map(_oracle_solve, range(procs))
+        t_start = time.perf_counter()
+        for s in range(steps):
+            t = time.perf_counter()
+            res = pool.map(_oracle_solve, [s * procs + i for i in range(procs)])
+            rounds.append(time.perf_counter() - t)
+            relres += [r[1] for r in res]
+            inner += [r[2] for r in res]
+            outer += [r[3] for r in res]
+            if budget_s and time.perf_counter() - t_start > budget_s:
+                break
+    print(json.dumps({"n": n, "side": side, "procs": procs, "rounds": rounds, "warmup": warmup,
+                      "t_one": t_one, "t_setup_s": t_setup, "max_relres": max(relres),
+                      "inner_avg": float(np.mean(inner)), "outer_its": int(max(outer))}))
 
 
-def run_cpu_baseline(steps, warmup, budget_s):
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_cpu_baseline(steps, warmup, budget_s, xout=None):
+    """Oracle solve rate on the CPU_SAMPLE_SIDE^3 instance, on all host cores, in the
+    bench's unit: each sample solve counts as n_sample / n_full of a 100^3 solve (the
+    solve phase of this generator is linear in n: the same outer count and nearly the
+    same inner count at every grid size, reported in the sample line)."""
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[v] = "1"
+    procs = host_cores()
     cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", "--steps", str(steps), "--warmup",
-           str(warmup), "--budget", str(budget_s)]
+           str(warmup), "--budget", str(budget_s), "--procs", str(procs)]
+    if xout:
+        cmd += ["--xout", xout]
     p = subprocess.run(cmd, capture_output=True, text=True, env=env, cwd=ROOT)
     if p.returncode != 0:
         raise RuntimeError("CPU baseline worker failed:\n" + p.stdout + p.stderr)
     r = json.loads(p.stdout.strip().splitlines()[-1])
     n_full = SIDE ** 3
-    per_s = r["solves"] / r["seconds"]
-    value = per_s * r["n"] / n_full
+    scale = r["n"] / n_full
+    wall = sum(r["rounds"])
+    per_s = r["procs"] * len(r["rounds"]) / wall          # sample solves / s, all cores
+    one_s = 1.0 / r["t_one"]                               # sample solves / s, one thread
     return {
-        "value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-        "sample": (f"FP64 numpy/scipy oracle, solve phase of the same generator at {CPU_SAMPLE_SIDE}^3 "
-                   f"(n = {r['n']}), {r['solves']} solve(s) in {r['seconds']:.2f} s "
-                   f"({per_s:.3f} solves/s, inner avg {r['inner_avg']:.1f}, outer {r['outer_its']}), scaled "
-                   f"to n = {n_full} by unknowns; set-up {r['t_setup_s']:.1f} s untimed"),
-        "max_relres": r["max_relres"],
+        "value": per_s * scale, "unit": UNIT, "cores": r["procs"], "kind": "oracle",
+        "sample": (f"FP64 numpy/scipy oracle, solve phase of the same generator and options at "
+                   f"{r['side']}^3 (n = {r['n']}): {len(r['rounds'])} timed rounds of {r['procs']} concurrent "
+                   f"solves (one process per host core, BLAS 1 thread) in {wall:.2f} s = {per_s:.2f} sample "
+                   f"solves/s; one thread alone {one_s:.3f} sample solves/s ({one_s * scale:.4f} in the unit); "
+                   f"each sample solve counted as n_sample/n = {scale:.4f} of a 100^3 solve; outer its "
+                   f"{r['outer_its']}, inner avg {r['inner_avg']:.2f}; set-up {r['t_setup_s']:.1f} s untimed"),
+        "one_thread_value": one_s * scale,
+        "rounds": r["rounds"], "procs": r["procs"], "warmup": r["warmup"], "n_sample": r["n"],
+        "max_relres": r["max_relres"], "t_setup_s": r["t_setup_s"],
     }
 
 
@@ -547,6 +601,70 @@ def main_adjoint(args, world, rank, local):
 
 
 # ----------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle, timed as it stands on the host cores
+# ----------------------------------------------------------------------------
+def main_reference(args):
+    """The oracle on a bounded sample of the workload.  The printed steps, warmup
+    and ms_per_step are the ones that ran: for dh3d_100 a step is one round of
+    concurrent sample solves (one per host core); for the batched and adjoint
+    workloads a step is one sample solve (one thread)."""
+    adj = args.workload == "adjoint_dh64"
+    metric = "gradients/s (adjoint solve + dL/dA) to 1e-8 rel. residual" if adj else METRIC
+    unit = "gradients/s" if adj else UNIT
+    if args.workload == "batched_dh":
+        cb = run_batched_cpu_baseline(120.0, batch_mean_n())
+        workload = BATCH_WORKLOAD.format(count=BATCH["count"], items=BATCH["count"] * BATCH["nrhs"])
+        steps, warm, ms = cb["solves"], 0, 1000.0 * cb["seconds"] / max(cb["solves"], 1)
+        per_step = "one oracle solve of a sampled (matrix, column) item, counted as n_item / mean n of an item"
+    elif adj:
+        cb = run_adjoint_cpu_baseline(120.0)
+        workload = ADJ_WORKLOAD
+        steps, warm, ms = cb["solves"], 0, 1000.0 * cb["seconds"] / max(cb["solves"], 1)
+        per_step = f"one oracle adjoint solve + dL/dA at {ADJ_CPU_SIDE}^3, counted as n_sample / n of a gradient"
+    else:
+        cb = run_cpu_baseline(args.steps, max(0, min(args.warmup, 1)), 120.0)
+        workload = WORKLOAD
+        steps, warm = len(cb["rounds"]), cb["warmup"]
+        ms = 1000.0 * sum(cb["rounds"]) / max(steps, 1)
+        per_step = (f"{cb['procs']} concurrent oracle solves at {CPU_SAMPLE_SIDE}^3 (n = {cb['n_sample']}), each "
+                    f"counted as n_sample / n of a 100^3 solve")
+    line = {"impl": "reference", "metric": metric, "value": cb["value"], "unit": unit, "n_gpus": args.gpus,
+            "steps": steps, "warmup": warm, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload, "reference": "FP64 CPU oracle (oracle/) as it stands, host cores",
+                       "step": per_step, "requested_steps": args.steps, "requested_warmup": args.warmup},
+            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": cb["value"], "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    if "one_thread_value" in cb:
+        line["cpu_baseline"]["one_thread_value"] = cb["one_thread_value"]
+    print(json.dumps(line), flush=True)
+
+
+def rel_error_legs(pkg, dev, stream, xo_path, legs):
+    """Relative error ||x - x_oracle|| / ||x_oracle|| of each GPU leg on the instance the
+    oracle solved (the CPU_SAMPLE_SIDE^3 step of the same generator, first rhs)."""
+    import numpy as np
+    import torch
+
+    from workloads import dissipative_hamiltonian_3d
+    xo = np.load(xo_path)
+    A, _, parts = dissipative_hamiltonian_3d(side=CPU_SAMPLE_SIDE, seed=1)
+    b = _make_rhs(parts, A.shape[0], 1, 1)[0]
+    out = {}
+    for name, prec in legs:
+        s = pkg.Solver(A, precision=prec, outer="fgmres", inner_tol=1e-6, outer_tol=1e-8, k=20,
+                       stream=stream.cuda_stream)
+        x, st = s.solve(torch.tensor(b, device=dev))
+        xh = x.cpu().numpy()
+        out[name] = {"rel_error": float(np.linalg.norm(xh - xo) / np.linalg.norm(xo)),
+                     "relres": float(np.linalg.norm(b - A @ xh) / np.linalg.norm(b)),
+                     "outer_its": st["outer_its"]}
+        s.close()
+    out["instance"] = f"{CPU_SAMPLE_SIDE}^3 (n = {A.shape[0]}), the oracle's x for the same b"
+    return out
+
+
+# ----------------------------------------------------------------------------
 # main
 # ----------------------------------------------------------------------------
 def main():
@@ -563,6 +681,9 @@ def main():
     ap.add_argument("--workload", default="dh3d_100", choices=["dh3d_100", "batched_dh", "adjoint_dh64"],
                     help="dh3d_100: one 1e6-unknown system; batched_dh: 256 systems x 32 right-hand sides; "
                          "adjoint_dh64: gradients through the adjoint solve")
+    ap.add_argument("--procs", type=int, default=0, help="(CPU worker) processes of the oracle pool")
+    ap.add_argument("--xout", default="", help="(CPU worker) where to save the oracle's x of the first rhs")
+    ap.add_argument("--no-fp64-leg", action="store_true", help="skip the FP64-GPU comparison solve")
     ap.add_argument("--batch-count", type=int, default=BATCH["count"],
                     help="systems in the batched workload (smaller counts for profiling captures)")
     args = ap.parse_args()
@@ -574,7 +695,7 @@ def main():
         elif args.workload == "adjoint_dh64":
             adjoint_worker(args.budget)
         else:
-            cpu_worker(CPU_SAMPLE_SIDE, args.steps, args.warmup, args.budget)
+            cpu_worker(CPU_SAMPLE_SIDE, args.steps, args.warmup, args.budget, max(1, args.procs), args.xout)
         return
 
     world, rank, local = rank_env()
@@ -588,27 +709,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        warm = max(0, min(args.warmup, 1))
-        if args.workload == "batched_dh":
-            cb = run_batched_cpu_baseline(120.0, batch_mean_n())
-        elif args.workload == "adjoint_dh64":
-            cb = run_adjoint_cpu_baseline(120.0)
-        else:
-            cb = run_cpu_baseline(args.steps, warm, 120.0)
-        ms = 1000.0 / cb["value"]
-        adj = args.workload == "adjoint_dh64"
-        metric = "gradients/s (adjoint solve + dL/dA) to 1e-8 rel. residual" if adj else METRIC
-        unit = "gradients/s" if adj else UNIT
-        line = {"impl": "reference", "metric": metric, "value": cb["value"], "unit": unit, "n_gpus": args.gpus,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": (BATCH_WORKLOAD.format(count=BATCH["count"], items=BATCH["count"] * BATCH["nrhs"])
-                                        if args.workload == "batched_dh" else
-                                        ADJ_WORKLOAD if args.workload == "adjoint_dh64" else WORKLOAD),
-                           "reference": "FP64 CPU oracle (oracle/), host cores"},
-                "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
-                "e2e": {"value": cb["value"], "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-        print(json.dumps(line), flush=True)
+        main_reference(args)
         return
 
     import numpy as np
@@ -681,6 +782,40 @@ def main():
         e2e_s += time.perf_counter() - t
     e2e_val = aggregate_rate(world, args.steps, reduce_max(e2e_s, dist, dev))
 
+    # the same solves in FP64 throughout (inner mrs in FP64 too), same options and
+    # stopping rule, timed the same way: the precision form's comparison
+    fp64 = None
+    if not args.no_fp64_leg:
+        solver.close()   # frees the mixed handle's device memory first
+        t0 = time.perf_counter()
+        s64 = pkg.Solver(A, precision="fp64", outer="fgmres", inner_tol=1e-6, outer_tol=1e-8, k=20,
+                         stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        t_setup64 = time.perf_counter() - t0
+        for w in range(args.warmup):
+            s64.solve(rhs[w % 4], x)
+        torch.cuda.synchronize()
+        evs64 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                 for _ in range(args.steps)]
+        st64 = []
+        for s in range(args.steps):
+            flush.zero_()
+            evs64[s][0].record(stream)
+            _, st = s64.solve(rhs[s % 4], x)
+            evs64[s][1].record(stream)
+            st64.append(st)
+        torch.cuda.synchronize()
+        ms64 = reduce_max(sum(a.elapsed_time(b) for a, b in evs64), dist, dev)
+        fp64 = {"value": aggregate_rate(world, args.steps, ms64 / 1000.0), "unit": UNIT,
+                "ms_per_step": ms64 / args.steps,
+                "inner_its_per_s": world * sum(s_["inner_its_total"] for s_ in st64) / (ms64 / 1000.0),
+                "outer_its": st64[-1]["outer_its"], "inner_its_avg": round(st64[-1]["inner_its_avg"], 2),
+                "max_relres": max(s_["relres"] for s_ in st64),
+                "converged": all(s_["status"] == 0 for s_ in st64) and max(s_["relres"] for s_ in st64) <= 1e-8,
+                "setup_s": round(t_setup64, 3),
+                "mrs_avg_launch_ms": sum(s_["t_inner_ms"] for s_ in st64) / max(sum(s_["inner_launches"] for s_ in st64), 1)}
+        s64.close()
+
     inner_ms = sum(s_["t_inner_ms"] for s_ in stats)
     inner_bytes = sum(s_["inner_bytes"] for s_ in stats)
     inner_launches = sum(s_["inner_launches"] for s_ in stats)
@@ -695,12 +830,18 @@ def main():
         return
 
     cpu = None
+    rel_err = None
     if not args.no_cpu_baseline and world == 1:  # the oracle baseline is timed at N = 1 only
+        xo_path = os.path.join(tempfile.mkdtemp(prefix="asss_bench_"), "x_oracle.npy")
         try:
-            cb = run_cpu_baseline(500, 1, 10.0)
-            cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+            cb = run_cpu_baseline(500, 1, 15.0, xout=xo_path)
+            cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "one_thread_value")}
         except Exception as e:  # reported, never silently substituted
-            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"[:300]}
+            cpu = {"value": None, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+                   "sample": f"failed: {e}"[:300]}
+        if os.path.exists(xo_path):
+            legs = [("mixed", "mixed")] + ([] if args.no_fp64_leg else [("fp64", "fp64")])
+            rel_err = rel_error_legs(pkg, dev, stream, xo_path, legs)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -711,7 +852,9 @@ def main():
                    "setup_s": round(t_setup, 3), "lls_its": solver.setup_stats["lls_its"],
                    "outer_its": stats[-1]["outer_its"], "inner_its_avg": round(stats[-1]["inner_its_avg"], 2),
                    "max_relres": relres, "converged": ok, "r": solver.setup_stats["r"],
-                   "k_eff": solver.setup_stats["k_eff"], "q_storage": args.q_storage},
+                   "k_eff": solver.setup_stats["k_eff"], "q_storage": args.q_storage,
+                   "inner_its_per_s": world * sum(s_["inner_its_total"] for s_ in stats) / (tmax / 1000.0),
+                   "fp64_gpu": fp64, "rel_error_vs_oracle": rel_err},
         "gpu_launches": int(launches),
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
         "roofline": {"bound": "hbm", "kernel": "k_mrs<float,20> (persistent mrs)", "achieved": achieved,

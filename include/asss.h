@@ -247,7 +247,8 @@ asss_status asss_skew_lanczos(const asss_csr* J, const double* q1, int k, int re
 /* mrs (§3.1, App. B) on (shift I + sign*(J - Q S_k Q^T)) x = b for one right-hand
  * side, where J is skew (not checked), Q is n x k column-major (k may be 0) and
  * S_k the skew tridiagonal matrix with superdiagonal alpha (k-1 values).
- * precision selects FP64 or FP32 storage and arithmetic (reductions in FP64); format
+ * precision selects FP64 or FP32 storage and arithmetic (the FP32 solve sums in FP32
+ * within a warp and in float pairs, about 44 bits, across warps and blocks); format
  * selects the storage of J as in asss_options.inner_format (the skew-diagonal
  * storage also requires J to be exactly skew, J_ij == -J_ji bit for bit).
  * Stops when |g|/||b|| < tol or after maxit steps; *its and *ratio receive the
@@ -266,9 +267,12 @@ asss_status asss_mrs(const asss_csr* J, int k, const double* q, const double* al
  *
  * Same method and stopping rule as asss_mrs with precision FP64, on J given as
  * plain CSR that is read in place (every array - row_ptr, col_idx, val, q, alpha,
- * b, x - must already be device memory; nothing is copied).  q is the deflation
- * basis in ROW-major layout with leading dimension kp (kp one of 0, 4, 8, 12, 16,
- * 20, 24, 32, 48, 64, kp >= k, columns k..kp-1 zero).  Scratch comes from one
+ * b, x - must already be memory of the current device (or managed memory);
+ * nothing is copied).  Each array must be aligned to its element size, and q to
+ * 16 bytes: other pointers are rejected with ASSS_ERR_ARG before any launch.  q is
+ * the deflation basis in ROW-major layout with leading dimension kp (kp one of 0, 4,
+ * 8, 12, 16, 20, 24, 32, 48, 64, kp >= k); its columns k..kp-1 must be zero
+ * (checked: ASSS_ERR_ARG otherwise).  sign must be +1 or -1.  Scratch comes from one
  * static device array of the library (about 3.2 MB per device, held by every GPU
  * that loads the library until the process exits), so n must be at most 65536;
  * larger n returns ASSS_ERR_ARG.  The call allocates nothing: no cudaMalloc, no
@@ -276,7 +280,10 @@ asss_status asss_mrs(const asss_csr* J, int k, const double* q, const double* al
  *
  * The first call on a device looks up the device address of that array (once per
  * device, with the device current); make that first call before any stream
- * capture.  All calls share the array and it keeps the last call's contents:
+ * capture.  The address is cached for the life of the process: after a
+ * cudaDeviceReset (or any teardown of the device's primary context) this entry
+ * point must not be called again in that process.  All calls share the array and
+ * it keeps the last call's contents:
  * calls that overlap on the GPU (different streams, threads or processes sharing
  * a context) race and must not be issued.  The call synchronises the stream
  * before returning.  The CSR is checked (row pointers, then column indices) and

@@ -232,13 +232,17 @@ struct Ctx {
     int clock_khz = 0;
     long long wait_cycles = 0;
     long long l2_bytes = 0;
+    bool force_stream = false;  // ASSS_FORCE_EVICT_FIRST=1: take the evict-first loads at any size
 };
 
 // Data read once per pass is loaded evict-first only when the pass's working set is
 // larger than L2: then it would only push out the vectors that the next pass reuses;
 // when everything fits, normal loads keep the streamed data in L2 for the next pass.
+// The environment variable ASSS_FORCE_EVICT_FIRST=1 (read when a context is made)
+// selects the evict-first loads at every size, so that small inputs exercise the code
+// path that large ones take.
 inline bool stream_evict_first(const Ctx& c, long long pass_bytes) {
-    return c.l2_bytes > 0 && pass_bytes > c.l2_bytes * 3 / 4;
+    return c.force_stream || (c.l2_bytes > 0 && pass_bytes > c.l2_bytes * 3 / 4);
 }
 asss_status make_ctx(Ctx& c, void* stream, double wait_timeout_ms);
 

@@ -1,6 +1,7 @@
 // Persistent single-kernel mrs solve (paper §3.1, App. B) of
 //     (shift I + sign * (J~ - Q_k S_k Q_k^T)) x = b
-// with J~ exactly skew in SELL-C storage and Q_k, S_k the skew-Lanczos data of
+// with J~ exactly skew - stored as skew half-diagonals (stencil-like patterns), in
+// SELL-C, or read in place as CSR - and Q_k, S_k the skew-Lanczos data of
 // §3.2 (Fig. 2).  One cooperative launch runs the whole iteration:
 //
 //   per iteration j (one pass over the rows owned by each block):
@@ -1042,6 +1043,17 @@ constexpr long long NOALLOC_DOUBLES = NOALLOC_CTRL + NOALLOC_PART + NOALLOC_BLK 
 // [ctrl | partials | block table | Y: 3 slots of n | P: 2 slots of n]
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
 
+// device (or managed) memory that belongs to device dev
+static bool noalloc_on_device(const void* p, int dev) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
 static double* noalloc_base(int* status) {
     static std::mutex mu;
     static double* base[256] = {};
@@ -1084,6 +1096,17 @@ __global__ void k_noalloc_check_ci(const int64_t* rp, const int32_t* ci, int64_t
         }
 }
 
+// columns k..kp-1 of the row-major q must be zero: they enter x through q[m] * u[m]
+// with u[m] = 0, so a NaN or Inf there would turn x into NaN
+__global__ void k_noalloc_check_qpad(const double* q, int64_t n, int k, int kp, int* flag) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int w = kp - k;
+    if (w <= 0 || t >= n * w) return;
+    const int64_t i = t / w;
+    const int m = k + (int)(t % w);
+    if (q[i * kp + m] != 0.0) atomicOr(flag, 4);
+}
+
 template <int KP>
 static asss_status noalloc_launch(int nblk, cudaStream_t s, MrsParams<double>& prm) {
     void* args[] = {&prm};
@@ -1118,10 +1141,33 @@ extern "C" asss_status asss_mrs_noalloc(int64_t n, int64_t nnz, const int64_t* r
         set_error("asss_mrs_noalloc: invalid arguments");
         return ASSS_ERR_ARG;
     }
-    if (!is_device_ptr(row_ptr) || !is_device_ptr(col_idx) || !is_device_ptr(val) || !is_device_ptr(b) ||
-        !is_device_ptr(x) || (k > 0 && !is_device_ptr(q_rowmajor)) || (k > 1 && !is_device_ptr(alpha))) {
-        set_error("asss_mrs_noalloc: every array must be device memory");
+    if (sign != 1.0 && sign != -1.0) {
+        set_error("asss_mrs_noalloc: sign must be +1 or -1");
         return ASSS_ERR_ARG;
+    }
+    int cur_dev = 0;
+    ASSS_CUDA(cudaGetDevice(&cur_dev));
+    // every array is read in place by the kernel: it must be memory of the current
+    // device (another GPU's memory would be read without peer access) and aligned for
+    // the kernel's vector loads (q rows are read 16 bytes at a time)
+    struct Arr {
+        const void* p;
+        size_t align;
+        const char* name;
+    };
+    const Arr arrs[] = {{row_ptr, 8, "row_ptr"}, {col_idx, 4, "col_idx"}, {val, 8, "val"},
+                        {b, 8, "b"},             {x, 8, "x"},             {k > 0 ? q_rowmajor : nullptr, 16, "q"},
+                        {k > 1 ? alpha : nullptr, 8, "alpha"}};
+    for (const Arr& a : arrs) {
+        if (!a.p) continue;
+        if (!noalloc_on_device(a.p, cur_dev)) {
+            set_error("asss_mrs_noalloc: %s must be device memory of the current device %d", a.name, cur_dev);
+            return ASSS_ERR_ARG;
+        }
+        if (((uintptr_t)a.p) % a.align != 0) {
+            set_error("asss_mrs_noalloc: %s must be aligned to %zu bytes", a.name, a.align);
+            return ASSS_ERR_ARG;
+        }
     }
     int st = ASSS_OK;
     double* base = noalloc_base(&st);
@@ -1141,8 +1187,13 @@ extern "C" asss_status asss_mrs_noalloc(int64_t n, int64_t nnz, const int64_t* r
             set_error("asss_mrs_noalloc: kp must be one of 0,4,8,12,16,20,24,32,48,64");
             return ASSS_ERR_ARG;
     }
+    if (occ < 1) {
+        set_error("mrs kernel cannot be resident");
+        return ASSS_ERR_CUDA;
+    }
+    if (occ > 4) occ = 4;
     int nslices = (int)((n + 31) / 32);
-    int nblk = c.sms * (occ < 1 ? 1 : occ);
+    int nblk = c.sms * occ;
     if (nblk > NOALLOC_MAX_BLOCKS) nblk = NOALLOC_MAX_BLOCKS;
     int need = (nslices + MRS_WARPS - 1) / MRS_WARPS;
     if (nblk > need) nblk = need;
@@ -1164,12 +1215,21 @@ extern "C" asss_status asss_mrs_noalloc(int64_t n, int64_t nnz, const int64_t* r
         if (!hf) {
             k_noalloc_check_ci<<<(int)((n + 255) / 256), 256, 0, s>>>(row_ptr, col_idx, n, flag);
             ASSS_CHECK_LAUNCH();
+            if (k > 0 && kp > k) {
+                const int64_t cnt = n * (int64_t)(kp - k);
+                k_noalloc_check_qpad<<<(int)((cnt + 255) / 256), 256, 0, s>>>(q_rowmajor, n, k, kp, flag);
+                ASSS_CHECK_LAUNCH();
+            }
             ASSS_CUDA(cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
             ASSS_CUDA(cudaStreamSynchronize(s));
         }
-        if (hf) {
+        if (hf & 3) {
             set_error("asss_mrs_noalloc: malformed CSR (row pointers or column indices)");
             return ASSS_ERR_PATTERN;
+        }
+        if (hf) {
+            set_error("asss_mrs_noalloc: columns k..kp-1 of q must be zero");
+            return ASSS_ERR_ARG;
         }
     }
     k_partition<<<(nblk + 128) / 128, 128, 0, s>>>(nullptr, nslices, nblk, blk);

@@ -1,6 +1,7 @@
 // Sparse-matrix plumbing: CSR upload/validation, transpose, SpMV, the pattern of
 // Abar S + (Abar S)^T, SELL-C conversion, scans and deterministic dot products.
 #include <cstdarg>
+#include <cstdlib>
 #include <cstring>
 
 #include "common.cuh"
@@ -58,6 +59,8 @@ asss_status make_ctx(Ctx& c, void* stream, double wait_timeout_ms) {
     int l2 = 0;
     ASSS_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c.device));
     c.l2_bytes = l2;
+    const char* fe = getenv("ASSS_FORCE_EVICT_FIRST");
+    c.force_stream = fe && fe[0] == '1';
     return ASSS_OK;
 }
 
@@ -474,7 +477,8 @@ asss_status attach_dia(DCsr& A, int max_diag, double min_fill, int* ok, cudaStre
     int dev = 0, l2 = 0;
     ASSS_CUDA(cudaGetDevice(&dev));
     ASSS_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
-    A.dia.stream = 2LL * (long long)off.size() * n * (long long)sizeof(double) > (long long)l2 * 3 / 4;
+    const char* fe = getenv("ASSS_FORCE_EVICT_FIRST");
+    A.dia.stream = (fe && fe[0] == '1') || 2LL * (long long)off.size() * n * (long long)sizeof(double) > (long long)l2 * 3 / 4;
     *ok = 1;
     return ASSS_OK;
 }

@@ -59,5 +59,9 @@ def test_reference_arm_prints_the_contract_line():
                 "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert key in line, key
     assert line["impl"] == "reference" and line["value"] > 0
-    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    # the oracle runs on every host core, and the line reports the steps that ran
+    cores = len(os.sched_getaffinity(0))
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == cores
+    assert line["steps"] == 1 and line["warmup"] == 0 and line["ms_per_step"] > 0
+    assert line["cpu_baseline"]["one_thread_value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["unit"] == line["unit"]
