@@ -257,6 +257,17 @@ asss_status asss_mrs(const asss_csr* J, int k, const double* q, const double* al
                      double shift, double sign, const double* b, double* x, double tol,
                      int maxit, int precision, int format, int* its, double* ratio, void* stream);
 
+/* mrs for nrhs right-hand sides at once: App. B's simultaneous iterations on
+ * (shift I + sign*(J - Q S_k Q^T)) X = B, B and X n x nrhs column-major with leading
+ * dimensions ldb, ldx >= n (host or device).  Every column runs its own recurrence
+ * and freezes once its |g|/||b_j|| < tol (the result equals nrhs separate asss_mrs
+ * calls); the columns share each pass over J and Q (up to 8 columns per launch, the
+ * SpMM form of the product).  k at most 32.  its and ratio (may be NULL) receive
+ * nrhs values each.  Other arguments as for asss_mrs. */
+asss_status asss_mrs_multi(const asss_csr* J, int k, const double* q, const double* alpha, double shift,
+                           double sign, int nrhs, const double* B, int64_t ldb, double* X, int64_t ldx, double tol,
+                           int maxit, int precision, int format, int* its, double* ratio, void* stream);
+
 /* ------------------------------------------------------------------------
  * Allocation-free variant of asss_mrs.
  *

@@ -68,7 +68,7 @@ class Stats(C.Structure):
 EXPORTED = ["asss_default_options", "asss_setup", "asss_solve", "asss_solve_adjoint",
             "asss_apply_operator", "asss_apply_preconditioner", "asss_export", "asss_destroy",
             "asss_status_str", "asss_last_error", "asss_skew_symmetrizer", "asss_skew_lanczos",
-            "asss_mrs", "asss_kernel_launches", "asss_mrs_noalloc", "asss_setup_batched",
+            "asss_mrs", "asss_mrs_multi", "asss_kernel_launches", "asss_mrs_noalloc", "asss_setup_batched",
             "asss_solve_batched", "asss_destroy_batched", "asss_batch_cta_threads"]
 
 _lib = None
@@ -115,6 +115,8 @@ def lib():
     L.asss_skew_lanczos.argtypes = [pCSR, P, C.c_int, C.c_int, P, P, C.POINTER(C.c_int), P]
     L.asss_mrs.argtypes = [pCSR, C.c_int, P, P, C.c_double, C.c_double, P, P, C.c_double, C.c_int,
                            C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double), P]
+    L.asss_mrs_multi.argtypes = [pCSR, C.c_int, P, P, C.c_double, C.c_double, C.c_int, P, C.c_int64, P, C.c_int64,
+                                 C.c_double, C.c_int, C.c_int, C.c_int, P, P, P]
     L.asss_mrs_noalloc.argtypes = [C.c_int64, C.c_int64, P, P, P, C.c_int, C.c_int, P, P, C.c_double,
                                    C.c_double, P, P, C.c_double, C.c_int, C.POINTER(C.c_int),
                                    C.POINTER(C.c_double), P]
@@ -129,7 +131,7 @@ def lib():
     L.asss_kernel_launches.restype = C.c_ulonglong
     for f in ("asss_setup", "asss_solve", "asss_solve_adjoint", "asss_apply_operator",
               "asss_apply_preconditioner", "asss_export", "asss_skew_symmetrizer",
-              "asss_skew_lanczos", "asss_mrs", "asss_setup_batched", "asss_solve_batched"):
+              "asss_skew_lanczos", "asss_mrs", "asss_mrs_multi", "asss_setup_batched", "asss_solve_batched"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -486,6 +488,35 @@ def mrs(J, b, Q=None, alpha=None, shift=1.0, sign=1.0, tol=1e-10, maxit=1000, pr
                                       x.ctypes.data, float(tol), int(maxit), prec, FORMATS[fmt], C.byref(its),
                                       C.byref(ratio), None))
     return x, its.value, ratio.value
+
+
+def mrs_multi(J, B, Q=None, alpha=None, shift=1.0, sign=1.0, tol=1e-10, maxit=1000, precision="fp64",
+              fmt="auto"):
+    """App. B's simultaneous mrs iterations for the columns of B (n x nrhs); returns
+    (X, its[nrhs], ratio[nrhs])."""
+    keep = []
+    a = _csr_struct(J, keep)
+    n = int(a.n)
+    k = 0 if Q is None else Q.shape[1]
+    qp = ap = None
+    if k:
+        Qf = np.asfortranarray(Q, dtype=np.float64)
+        keep.append(Qf)
+        qp = Qf.ctypes.data
+        if k > 1:
+            al = np.ascontiguousarray(alpha, dtype=np.float64)
+            keep.append(al)
+            ap = al.ctypes.data
+    B = np.asfortranarray(np.asarray(B, dtype=np.float64).reshape(n, -1))
+    nrhs = B.shape[1]
+    X = np.empty((n, nrhs), order="F")
+    its = np.zeros(nrhs, dtype=np.int32)
+    ratio = np.zeros(nrhs)
+    prec = {"fp64": ASSS_PREC_FP64, "mixed": ASSS_PREC_MIXED, "fp32": ASSS_PREC_MIXED}[precision]
+    _check("asss_mrs_multi", lib().asss_mrs_multi(C.byref(a), k, qp, ap, float(shift), float(sign), nrhs,
+                                                  B.ctypes.data, n, X.ctypes.data, n, float(tol), int(maxit), prec,
+                                                  FORMATS[fmt], its.ctypes.data, ratio.ctypes.data, None))
+    return X, its, ratio
 
 
 def kernel_launches() -> int:

@@ -643,17 +643,31 @@ static asss_status ensure_smw(asss_handle* h, int tr) {
     double sign = tr ? -1.0 : 1.0;
     std::vector<int> negh(r);
     if (r) ASSS_CUDA(cudaMemcpy(negh.data(), h->neg.p, sizeof(int) * r, cudaMemcpyDeviceToHost));
-    for (int col = 0; col < m; ++col) {
-        const double* b;
-        if (col < k) {
-            b = h->Qcm.p + (size_t)col * n;
-        } else {
-            k_unit<<<cdiv(n, 256), 256, 0, s>>>(rhs.p, n, negh[col - k]);
+    if (h->kp <= MRS_MULTI_KPMAX) {
+        // S_bar X = U_bar as App. B's simultaneous iterations: the k + r columns share
+        // every pass over J~ and Q_k (groups of up to 8 per launch)
+        DBuf<double> Ub;
+        ASSS_TRY(Ub.alloc((int64_t)n * m));
+        if (k) ASSS_CUDA(cudaMemcpyAsync(Ub.p, h->Qcm.p, sizeof(double) * (size_t)n * k, cudaMemcpyDeviceToDevice, s));
+        for (int t = 0; t < r; ++t) {
+            k_unit<<<cdiv(n, 256), 256, 0, s>>>(Ub.p + (size_t)(k + t) * n, n, negh[t]);
             ASSS_CHECK_LAUNCH();
-            b = rhs.p;
         }
-        ASSS_TRY(mrs_solve(c, h->mw, op, false, 1.0, sign, b, X.p + (size_t)col * n, nullptr, tol,
-                           h->opt.inner_maxit, nullptr, nullptr, false));
+        ASSS_TRY(mrs_multi_solve(c, op, false, 1.0, sign, m, Ub.p, n, X.p, nullptr, n, tol, h->opt.inner_maxit,
+                                 nullptr, nullptr));
+    } else {
+        for (int col = 0; col < m; ++col) {
+            const double* b;
+            if (col < k) {
+                b = h->Qcm.p + (size_t)col * n;
+            } else {
+                k_unit<<<cdiv(n, 256), 256, 0, s>>>(rhs.p, n, negh[col - k]);
+                ASSS_CHECK_LAUNCH();
+                b = rhs.p;
+            }
+            ASSS_TRY(mrs_solve(c, h->mw, op, false, 1.0, sign, b, X.p + (size_t)col * n, nullptr, tol,
+                               h->opt.inner_maxit, nullptr, nullptr, false));
+        }
     }
     ASSS_TRY(G.alloc((int64_t)m * m));
     ASSS_TRY(Sig.alloc((int64_t)m * m));
@@ -1614,6 +1628,86 @@ asss_status asss_skew_lanczos(const asss_csr* J, const double* q1, int k, int re
         ASSS_CUDA(cudaStreamSynchronize(c.stream));
     }
     ASSS_CUDA(cudaStreamSynchronize(c.stream));
+    return ASSS_OK;
+}
+
+asss_status asss_mrs_multi(const asss_csr* J, int k, const double* q, const double* alpha, double shift,
+                           double sign, int nrhs, const double* B, int64_t ldb, double* X, int64_t ldx, double tol,
+                           int maxit, int precision, int format, int* its, double* ratio, void* stream) {
+    Ctx c;
+    ASSS_TRY(make_ctx(c, stream, 2000.0));
+    if (!J || !B || !X || nrhs < 0 || k < 0 || (k > 0 && !q) || (k > 1 && !alpha) || maxit < 1 || !(shift > 0.0) ||
+        ldb < J->n || ldx < J->n) {
+        set_error("invalid arguments");
+        return ASSS_ERR_ARG;
+    }
+    if (nrhs == 0) return ASSS_OK;
+    cudaStream_t s = c.stream;
+    DCsr Jd;
+    ASSS_TRY(upload_csr(J, Jd, true, s));
+    const int n = Jd.n;
+    const int kp = pick_kp(k);
+    if (kp < 0 || kp > MRS_MULTI_KPMAX) {
+        set_error("k above %d is not supported by the multi-column mrs", MRS_MULTI_KPMAX);
+        return ASSS_ERR_UNSUPPORTED;
+    }
+    DSell<double> J64;
+    DSell<float> J32;
+    DSkewDia<double> D64;
+    DSkewDia<float> D32;
+    DBuf<double> Qcm, Q64, ad, bd, xd;
+    DBuf<float> Q32, x32;
+    const bool fp32 = precision == ASSS_PREC_MIXED;
+    int dia = 0;
+    if (format != ASSS_FORMAT_SELL) {
+        if (fp32) ASSS_TRY(build_skew_dia<float>(Jd, 64, 0.5, D32, &dia, s));
+        else ASSS_TRY(build_skew_dia<double>(Jd, 64, 0.5, D64, &dia, s));
+        if (!dia && format == ASSS_FORMAT_DIAG) {
+            set_error("J does not qualify for skew diagonal storage");
+            return ASSS_ERR_UNSUPPORTED;
+        }
+    }
+    if (!dia) {
+        if (fp32) ASSS_TRY(build_sell<float>(Jd, false, J32, s));
+        else ASSS_TRY(build_sell<double>(Jd, false, J64, s));
+    }
+    if (k) {
+        ASSS_TRY(to_device(Qcm, q, (int64_t)n * k, s));
+        if (fp32) {
+            ASSS_TRY(Q32.alloc((int64_t)n * kp));
+            ASSS_TRY(to_rowmajor_f(Qcm.p, n, k, n, kp, Q32.p, s));
+        } else {
+            ASSS_TRY(Q64.alloc((int64_t)n * kp));
+            ASSS_TRY(to_rowmajor(Qcm.p, n, k, n, kp, Q64.p, s));
+        }
+    }
+    if (k > 1) ASSS_TRY(to_device(ad, alpha, k - 1, s));
+    else ASSS_TRY(ad.alloc(1));
+    ASSS_TRY(bd.alloc((int64_t)n * nrhs));
+    ASSS_CUDA(cudaMemcpy2DAsync(bd.p, sizeof(double) * n, B, sizeof(double) * ldb, sizeof(double) * n, nrhs,
+                                cudaMemcpyDefault, s));
+    ASSS_TRY(xd.alloc((int64_t)n * nrhs));
+    MrsOperator op;
+    op.J64 = (fp32 || dia) ? nullptr : &J64;
+    op.J32 = (fp32 && !dia) ? &J32 : nullptr;
+    op.D64 = (!fp32 && dia) ? &D64 : nullptr;
+    op.D32 = (fp32 && dia) ? &D32 : nullptr;
+    op.k = k;
+    op.kp = kp;
+    op.Q64 = Q64.p;
+    op.Q32 = Q32.p;
+    op.alpha = ad.p;
+    if (fp32) {
+        ASSS_TRY(x32.alloc((int64_t)n * nrhs));
+        ASSS_TRY(mrs_multi_solve(c, op, true, shift, sign, nrhs, bd.p, n, nullptr, x32.p, n, tol, maxit, its, ratio));
+        k_f2d<<<cdiv((int64_t)n * nrhs, 256), 256, 0, s>>>(x32.p, xd.p, n * nrhs);
+        ASSS_CHECK_LAUNCH();
+    } else {
+        ASSS_TRY(mrs_multi_solve(c, op, false, shift, sign, nrhs, bd.p, n, xd.p, nullptr, n, tol, maxit, its, ratio));
+    }
+    ASSS_CUDA(cudaMemcpy2DAsync(X, sizeof(double) * ldx, xd.p, sizeof(double) * n, sizeof(double) * n, nrhs,
+                                cudaMemcpyDefault, s));
+    ASSS_CUDA(cudaStreamSynchronize(s));
     return ASSS_OK;
 }
 

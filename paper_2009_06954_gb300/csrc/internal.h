@@ -105,6 +105,16 @@ MrsTotals mrs_take_totals(MrsWork* w);
 // do nothing if it is non-zero (speculative work enqueued ahead of a host decision)
 void mrs_set_skip(MrsWork* w, const int* flag);
 
+// mrs_multi.cu: App. B's simultaneous iterations for ncol right-hand sides (B, X
+// column-major with leading dimensions ldb, ldx; X in FP64 or FP32 as fp32 says), in
+// launches of up to 8 columns that share every pass over J~ and Q_k; per-column
+// freezing.  its / ratio: host arrays of ncol entries (may be null).  Supports padded
+// Lanczos widths up to MRS_MULTI_KPMAX.
+constexpr int MRS_MULTI_KPMAX = 32;
+asss_status mrs_multi_solve(const Ctx& c, const MrsOperator& op, bool fp32, double shift, double sign, int ncol,
+                            const double* B, long long ldb, double* X64, float* X32, long long ldx, double tol,
+                            int maxit, int* its, double* ratio);
+
 // lls.cu
 struct LlsResult {
     int its = 0;

@@ -52,7 +52,8 @@ def skew_measures(Abar, S):
     return frac, float(np.linalg.norm(d - 1.0) / np.sqrt(len(d)))
 
 
-def run_case(A, b, pattern_name, S_pat, gamma, k, precision, outer, inner_tol):
+def measure_case(A, b, S_pat, gamma, k, precision, outer, inner_tol):
+    """Set up and solve once with one choice; returns the study's measures as a dict."""
     s = Solver(A, s_pattern=S_pat, gamma=gamma, k=k, precision=precision, outer=outer,
                inner_tol=inner_tol)
     st0 = s.setup_stats
@@ -62,9 +63,16 @@ def run_case(A, b, pattern_name, S_pat, gamma, k, precision, outer, inner_tol):
     x, st = s.solve(b)
     s.close()
     relres = float(np.linalg.norm(b - A @ x) / np.linalg.norm(b))
-    return (f"| {pattern_name} | {gamma:g} | {k} | {st0['lls_its']} | {frac:.4f} | {ddev:.2e} | "
-            f"{st0['r']} | {st['outer_its']} | {st['inner_its_avg']:.1f} | {st['t_solve_ms']:.1f} | "
-            f"{relres:.1e} |")
+    return {"lls_its": st0["lls_its"], "skew_fraction": frac, "diag_dev": ddev, "r": st0["r"],
+            "outer_its": st["outer_its"], "inner_its_avg": st["inner_its_avg"], "solve_ms": st["t_solve_ms"],
+            "relres": relres, "status": st["status"]}
+
+
+def run_case(A, b, pattern_name, S_pat, gamma, k, precision, outer, inner_tol):
+    m = measure_case(A, b, S_pat, gamma, k, precision, outer, inner_tol)
+    return (f"| {pattern_name} | {gamma:g} | {k} | {m['lls_its']} | {m['skew_fraction']:.4f} | "
+            f"{m['diag_dev']:.2e} | {m['r']} | {m['outer_its']} | {m['inner_its_avg']:.1f} | "
+            f"{m['solve_ms']:.1f} | {m['relres']:.1e} |")
 
 
 def main(argv=None):

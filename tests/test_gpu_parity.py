@@ -649,3 +649,58 @@ def test_negative_pivots_low_rank_part(pkg, precision):
         r = ((P.T if tr else P) @ z) - u
         assert np.linalg.norm(r) <= bound * np.linalg.norm(u), (tr, np.linalg.norm(r) / np.linalg.norm(u))
     s.close()
+
+
+# ----------------------------------------------------------------------------
+# App. B's simultaneous iterations: several right-hand sides in one launch (the
+# columns share the passes over J~ and Q_k), per-column freezing (reading R9)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("storage", ["sell", "diag"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+def test_mrs_multi_matches_oracle_freeze(pkg, storage, precision, sign, loads):
+    n = 20001
+    J = random_skew(n, 12, seed=41) if storage == "sell" else banded_skew(n, (1, 3, 64, 1000), seed=42)
+    rng = np.random.default_rng(43)
+    Q, alpha = O.skew_lanczos(J, rng.standard_normal(n), 20)
+    Sk = O.lanczos_tridiagonal(alpha)
+    apply = lambda V: sign * (J @ V - Q @ (Sk @ (Q.T @ V)))
+    B = rng.standard_normal((n, 11))       # two launches: 8 + 3 columns
+    B[:, 3] = 0.0                          # a zero column gives x = 0 and its = 0
+    B[:, 5] *= 1e3                         # scale does not change the per-column stop
+    B[:, 9] = 0.0
+    B[7, 9] = 1.0                          # a unit vector, as in the SMW set-up
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    Xo, its_o, ratio_o, _ = O.mrs(1.0, apply, B, 3000, 1e-12 if precision == "fp64" else 1e-7, freeze=True)
+    Xg, its_g, ratio_g = pkg.mrs_multi(J, B, Q, alpha, sign=sign, tol=tol, maxit=3000, precision=precision,
+                                       fmt=storage)
+    assert its_g[3] == 0 and np.all(Xg[:, 3] == 0)
+    for c in range(B.shape[1]):
+        if c == 3:
+            continue
+        xo = Xo[:, c]
+        if precision == "fp64":
+            assert abs(int(its_g[c]) - int(its_o[c])) <= 2, (c, its_g[c], its_o[c])
+            assert ratio_g[c] < 1e-12
+            np.testing.assert_allclose(Xg[:, c], xo, rtol=0, atol=1e-9 * np.abs(xo).max())
+        else:
+            assert ratio_g[c] < 1e-5
+            np.testing.assert_allclose(Xg[:, c], xo, rtol=0, atol=1e-4 * np.abs(xo).max())
+    # the same as separate single-column solves
+    for c in (0, 5, 10):
+        x1, its1, _ = pkg.mrs(J, B[:, c], Q, alpha, sign=sign, tol=tol, maxit=3000, precision=precision, fmt=storage)
+        assert abs(int(its_g[c]) - its1) <= 2
+        atol = (1e-9 if precision == "fp64" else 1e-4) * np.abs(x1).max()
+        np.testing.assert_allclose(Xg[:, c], x1, rtol=0, atol=atol)
+
+
+def test_mrs_multi_stops_at_maxit_with_the_oracle_iterates(pkg):
+    """Every column at its iteration limit: its = maxit, X equals the oracle's iterates."""
+    n = 3001
+    J = random_skew(n, 10, seed=44)
+    B = np.random.default_rng(45).standard_normal((n, 5))
+    Xo, its_o, ratio_o, _ = O.mrs(1.0, lambda V: J @ V, B, 4, 1e-14, freeze=True)
+    Xg, its_g, ratio_g = pkg.mrs_multi(J, B, tol=1e-14, maxit=4)
+    assert np.all(its_g == 4) and np.all(its_o == 4)
+    np.testing.assert_allclose(ratio_g, ratio_o, rtol=1e-12)
+    np.testing.assert_allclose(Xg, Xo, rtol=0, atol=1e-12 * np.abs(Xo).max())
