@@ -99,9 +99,14 @@ struct DCsr {
     DDia dia;            // used by spmv when present
 };
 
-// SELL-C (C = 32) storage: slice s covers rows 32s..32s+31; entry kk of lane t
-// of slice s sits at sptr[s] + kk*32 + t.  Padding entries have value 0 and a
-// valid column (the row itself, or 0 past the last row).
+// SELL-C (C = 32) storage: slot 32s + t (lane t of slice s) holds row rowmap[32s + t]
+// (row 32s + t when rowmap is empty); entry kk of that lane sits at sptr[s] + kk*32 + t.
+// With SELL-C-sigma the rows of each window of SELL_SIGMA consecutive rows are sorted
+// by length (longest first) before they are cut into slices, so a slice holds rows
+// of similar length and heavy-tailed row lengths do not pad every slice to its
+// longest row.  Padding entries have value 0 and a valid column; slots past the
+// last row map to row n (no row).
+constexpr int SELL_SIGMA = 1024;
 template <class T>
 struct DSell {
     int n = 0;
@@ -111,6 +116,8 @@ struct DSell {
     DBuf<int> sptr;   // nslices + 1
     DBuf<int> col;
     DBuf<T> val;
+    DBuf<int> rowmap; // 32 * nslices slots -> row (empty: identity)
+    DBuf<int> rowpos; // n rows -> slot (empty: identity)
 };
 
 // Skew half-diagonal storage of an exactly skew matrix J whose entries lie on a

@@ -119,10 +119,11 @@ void mrs_work_destroy(MrsWork* w) { delete w; }
 template <class T>
 struct MrsParams {
     int n;
-    // SELL-C operator
+    // SELL-C operator (rowmap: slot -> row for SELL-C-sigma, null for the identity)
     const int* sptr;
     const int* col;
     const T* val;
+    const int* rowmap;
     // skew half-diagonal operator: U points at U_0[0]; diagonal d starts ustride later
     int ndiag;
     const int* off;
@@ -361,8 +362,15 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
     T tacc[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) tacc[v] = (T)0;
+    // the row held by lane `lane` of slice sl (SELL-C-sigma permutes rows within windows)
+    auto row_of = [&](int sl) -> int {
+        if constexpr (FMT == 0) {
+            if (p.rowmap) return __ldg(&p.rowmap[sl * 32 + lane]);
+        }
+        return sl * 32 + lane;
+    };
     for (int sl = s0 + warp; sl < s1; sl += MRS_WARPS) {
-        int i = sl * 32 + lane;
+        int i = row_of(sl);
         if (i < n) {
             T b = (T)p.rhs[i];
             p.Y[i] = b;
@@ -439,7 +447,7 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
 #pragma unroll
         for (int v = 0; v < NV; ++v) tacc[v] = (T)0;
         for (int sl = s0 + warp; sl < s1; sl += MRS_WARPS) {
-            const int i = sl * 32 + lane;
+            const int i = row_of(sl);
             const bool live = i < n;
             // this row's own data first (independent of the operator loop below)
             const T yold = (live && j >= 2) ? Yold[i] : (T)0;
@@ -562,7 +570,7 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
 #pragma unroll
             for (int v = 0; v < NV; ++v) tacc[v] = (T)0;
             for (int sl = s0 + warp; sl < s1; sl += MRS_WARPS) {
-                int i = sl * 32 + lane;
+                int i = row_of(sl);
                 if (i < n) {
                     T pv = (tn * Ycur[i] - td * Pj[i]) * tth;
                     T xi = p.x[i] + tx * pv;
@@ -600,6 +608,7 @@ struct OpView {
     const int* sptr = nullptr;
     const int* col = nullptr;
     const T* val = nullptr;
+    const int* rowmap = nullptr;
     int ndiag = 0;
     const int* off = nullptr;
     const T* U = nullptr;
@@ -642,6 +651,7 @@ static asss_status launch_mrs(const Ctx& c, MrsWork* w, const OpView<T>& J, cons
     prm.sptr = J.sptr;
     prm.col = J.col;
     prm.val = J.val;
+    prm.rowmap = J.rowmap;
     prm.ndiag = J.ndiag;
     prm.off = J.off;
     prm.U = J.U;
@@ -790,6 +800,7 @@ static asss_status dispatch_mrs(const Ctx& c, MrsWork* w, const DSell<T>* sell, 
     v.sptr = sell->sptr.p;
     v.col = sell->col.p;
     v.val = sell->val.p;
+    v.rowmap = sell->rowmap.p;
     v.key = sell;
     v.nnz = sell->nnz;
     *nnz_read = v.nnz;

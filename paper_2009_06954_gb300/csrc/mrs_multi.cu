@@ -33,10 +33,11 @@ constexpr int MM_RPW = 32 / MM_R;       // rows per warp and pass iteration
 template <class T>
 struct MultiParams {
     int n, ncol;
-    // SELL-C operator
+    // SELL-C operator (rowpos: row -> slot for SELL-C-sigma, null for the identity)
     const int* sptr;
     const int* col;
     const T* val;
+    const int* rowpos;
     // skew half-diagonal operator (U points at U_0[0], diagonal d starts ustride later)
     int ndiag;
     const int* off;
@@ -254,7 +255,8 @@ __global__ void __launch_bounds__(MRS_THREADS, 1) k_mrs_multi(MultiParams<T> p) 
             if (lv) {
                 T acc = (T)0;
                 if constexpr (FMT == 0) {
-                    const int sl = i >> 5, t = i & 31;
+                    const int slot = p.rowpos ? __ldg(&p.rowpos[i]) : i;
+                    const int sl = slot >> 5, t = slot & 31;
                     const int sb = __ldg(&p.sptr[sl]);
                     const int width = (__ldg(&p.sptr[sl + 1]) - sb) >> 5;
                     const int* cp = p.col + sb + t;
@@ -445,6 +447,7 @@ static asss_status multi_typed(const Ctx& c, const DSell<T>* sell, const DSkewDi
         prm.sptr = sell->sptr.p;
         prm.col = sell->col.p;
         prm.val = sell->val.p;
+        prm.rowpos = sell->rowpos.p;
     }
     prm.halo = H;
     prm.yslot = yslot;

@@ -770,23 +770,67 @@ asss_status build_pattern(const DCsr& Abar, const DCsr& AbarT, const DCsr& S, co
 // ---------------------------------------------------------------------------
 // SELL-C (C = 32) from CSR, optionally leaving out diagonal entries
 // ---------------------------------------------------------------------------
-__global__ void k_sell_width(int n, const int* rp, const int* ci, int skip_diag, int nslices, int* w,
-                             unsigned long long* nnz) {
+// length of each row as stored (the diagonal left out when skip_diag)
+__global__ void k_sell_rowlen(int n, const int* rp, const int* ci, int skip_diag, int* len) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    int l = rp[r + 1] - rp[r];
+    if (skip_diag) {
+        for (int e = rp[r]; e < rp[r + 1]; ++e)
+            if (ci[e] == r) {
+                --l;
+                break;
+            }
+    }
+    len[r] = l;
+}
+
+// SELL-C-sigma: one block per window of SELL_SIGMA rows sorts (length desc, row asc)
+// with a bitonic network in shared memory and writes slot -> row and row -> slot;
+// slots past the last row map to row n
+__global__ void __launch_bounds__(SELL_SIGMA) k_sell_sort_window(int n, int nslots, const int* len, int* rowmap,
+                                                                   int* rowpos) {
+    __shared__ long long key[SELL_SIGMA];
+    const int w0 = blockIdx.x * SELL_SIGMA;
+    const int t = threadIdx.x;
+    const int r = w0 + t;
+    // key: length in the high word (complemented for descending order), row in the low word
+    key[t] = r < n ? ((long long)(0x7fffffff - len[r]) << 32) | (unsigned)r : ((long long)0x7fffffff << 32) | 0x7fffffffu;
+    __syncthreads();
+    for (int k = 2; k <= SELL_SIGMA; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const int ixj = t ^ j;
+            if (ixj > t) {
+                const long long a = key[t], b = key[ixj];
+                const bool up = (t & k) == 0;
+                if ((a > b) == up) {
+                    key[t] = b;
+                    key[ixj] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    const int slot = w0 + t;
+    if (slot < nslots) {
+        const int row = (int)(key[t] & 0xffffffffLL);
+        const bool real = row < n;   // the padding key's row word is 0x7fffffff >= n
+        rowmap[slot] = real ? row : n;
+        if (real) rowpos[row] = slot;
+    }
+}
+
+__global__ void k_sell_width(int n, const int* len, const int* rowmap, int nslices, int* w, unsigned long long* nnz) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nslices) return;
     int m = 0;
     long long tot = 0;
-    for (int r = s * 32; r < min(n, s * 32 + 32); ++r) {
-        int len = rp[r + 1] - rp[r];
-        if (skip_diag) {
-            for (int e = rp[r]; e < rp[r + 1]; ++e)
-                if (ci[e] == r) {
-                    --len;
-                    break;
-                }
-        }
-        m = max(m, len);
-        tot += len;
+    for (int slot = s * 32; slot < s * 32 + 32; ++slot) {
+        const int r = rowmap ? rowmap[slot] : slot;
+        if (r >= n) continue;
+        const int l = len[r];
+        m = max(m, l);
+        tot += l;
     }
     w[s] = m * 32;
     atomicAdd(nnz, (unsigned long long)tot);
@@ -794,10 +838,11 @@ __global__ void k_sell_width(int n, const int* rp, const int* ci, int skip_diag,
 
 template <class T>
 __global__ void k_sell_fill(int n, int nslices, const int* rp, const int* ci, const double* v, int skip_diag,
-                            const int* sptr, int* scol, T* sval) {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    int s = r >> 5, lane = r & 31;
+                            const int* rowmap, const int* sptr, int* scol, T* sval) {
+    int slot = blockIdx.x * blockDim.x + threadIdx.x;
+    int s = slot >> 5, lane = slot & 31;
     if (s >= nslices) return;
+    const int r = rowmap ? rowmap[slot] : slot;
     int base = sptr[s], width = (sptr[s + 1] - base) >> 5;
     int kk = 0;
     if (r < n) {
@@ -815,31 +860,53 @@ __global__ void k_sell_fill(int n, int nslices, const int* rp, const int* ci, co
     }
 }
 
+// Slices of 32 rows in natural order; when that pads the stored entries by more than
+// a fifth over the matrix's own (heavy-tailed row lengths), SELL-C-sigma instead.
 template <class T>
 asss_status build_sell(const DCsr& A, bool skip_diag, DSell<T>& out, cudaStream_t s) {
     int n = A.n;
     int ns = cdiv(n, 32);
     out.n = n;
     out.nslices = ns;
-    DBuf<int> w;
+    DBuf<int> w, len;
     DBuf<unsigned long long> cnt;
     ASSS_TRY(w.alloc(ns));
+    ASSS_TRY(len.alloc(n > 0 ? n : 1));
     ASSS_TRY(cnt.alloc(1));
-    ASSS_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long), s));
-    k_sell_width<<<cdiv(ns, 128), 128, 0, s>>>(n, A.rp.p, A.ci.p, skip_diag ? 1 : 0, ns, w.p, cnt.p);
+    k_sell_rowlen<<<cdiv(n, 256), 256, 0, s>>>(n, A.rp.p, A.ci.p, skip_diag ? 1 : 0, len.p);
     ASSS_CHECK_LAUNCH();
+    long long tot = 0;
     unsigned long long hn = 0;
-    ASSS_CUDA(cudaMemcpyAsync(&hn, cnt.p, sizeof(hn), cudaMemcpyDeviceToHost, s));
-    ASSS_CUDA(cudaStreamSynchronize(s));
+    DBuf<long long> off64;
+    ASSS_TRY(off64.alloc(ns + 1));
+    for (int pass = 0; pass < 2; ++pass) {
+        const int* rmap = pass ? out.rowmap.p : nullptr;
+        ASSS_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long), s));
+        k_sell_width<<<cdiv(ns, 128), 128, 0, s>>>(n, len.p, rmap, ns, w.p, cnt.p);
+        ASSS_CHECK_LAUNCH();
+        ASSS_CUDA(cudaMemcpyAsync(&hn, cnt.p, sizeof(hn), cudaMemcpyDeviceToHost, s));
+        ASSS_TRY(exclusive_scan64(w.p, off64.p, ns, &tot, s));   // 64-bit total (synchronises)
+        if (pass == 1 || (double)tot <= 1.2 * (double)hn) break;
+        // heavy-tailed rows: sort each window of SELL_SIGMA rows by length
+        const int nslots = ns * 32;
+        ASSS_TRY(out.rowmap.alloc(nslots));
+        ASSS_TRY(out.rowpos.alloc(n));
+        k_sell_sort_window<<<cdiv(nslots, SELL_SIGMA), SELL_SIGMA, 0, s>>>(n, nslots, len.p, out.rowmap.p,
+                                                                           out.rowpos.p);
+        ASSS_CHECK_LAUNCH();
+    }
     out.nnz = (int64_t)hn;
-    ASSS_TRY(out.sptr.alloc(ns + 1));
-    int64_t tot = 0;
-    ASSS_TRY(exclusive_scan(w.p, out.sptr.p, ns, &tot, s));
     out.nstored = tot;
+    if (tot >= (1LL << 31) - 1) {
+        set_error("SELL-C storage of %lld entries exceeds 32-bit slice offsets", tot);
+        return ASSS_ERR_UNSUPPORTED;
+    }
+    ASSS_TRY(out.sptr.alloc(ns + 1));
+    ASSS_TRY(exclusive_scan(w.p, out.sptr.p, ns, nullptr, s));
     ASSS_TRY(out.col.alloc(tot > 0 ? tot : 1));
     ASSS_TRY(out.val.alloc(tot > 0 ? tot : 1));
     k_sell_fill<T><<<cdiv((int64_t)ns * 32, 256), 256, 0, s>>>(n, ns, A.rp.p, A.ci.p, A.v.p, skip_diag ? 1 : 0,
-                                                               out.sptr.p, out.col.p, out.val.p);
+                                                               out.rowmap.p, out.sptr.p, out.col.p, out.val.p);
     ASSS_CHECK_LAUNCH();
     return ASSS_OK;
 }

@@ -704,3 +704,43 @@ def test_mrs_multi_stops_at_maxit_with_the_oracle_iterates(pkg):
     assert np.all(its_g == 4) and np.all(its_o == 4)
     np.testing.assert_allclose(ratio_g, ratio_o, rtol=1e-12)
     np.testing.assert_allclose(Xg, Xo, rtol=0, atol=1e-12 * np.abs(Xo).max())
+
+
+# ----------------------------------------------------------------------------
+# the general power-law recipe (heavy-tailed rows: SELL-C-sigma storage of J~)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_powerlaw_inner_operator_mrs_steps_match_oracle(pkg, precision):
+    """J~ of the power-law recipe built by the oracle from the GPU's exported S and w
+    (§3, Eq. preconditioner): five App. B steps with k = 20 deflation vectors agree
+    element by element with the oracle's; the heavy-tailed rows make the SELL-C
+    storage sort rows within windows (SELL-C-sigma)."""
+    from workloads import pattern_symmetrized, random_powerlaw
+    A, b = random_powerlaw(n=20000, seed=2, band=1000)
+    A = sp.csr_matrix(A)
+    Sp = pattern_symmetrized(A)
+    s = pkg.Solver(A, s_pattern=Sp, precision="mixed", outer="fgmres", inner_tol=1e-6, lls_maxit=400)
+    ex = s.export(Sp.nnz)
+    s.close()
+    Abar, _, _, _ = O.equilibrate(A)
+    S = sp.csr_matrix((ex["s_val"], Sp.indices.copy(), Sp.indptr.copy()), shape=A.shape)
+    Jt = O.inner_skew_operator(Abar, S, ex["w"])
+    lens = np.diff(Jt.indptr)
+    assert lens.max() > 8 * lens.mean()          # heavy tail: unsorted slices would pad heavily
+    rng = np.random.default_rng(51)
+    Q, alpha = O.skew_lanczos(Jt, rng.standard_normal(Jt.shape[0]), 20)
+    Sk = O.lanczos_tridiagonal(alpha)
+    u = rng.standard_normal(Jt.shape[0])
+    apply = lambda V: Jt @ V - Q @ (Sk @ (Q.T @ V))
+    xo, its_o, ratio_o, _ = O.mrs(1.0, apply, u, 5, 1e-14)
+    xg, its_g, ratio_g = pkg.mrs(Jt, u, Q, alpha, tol=1e-14, maxit=5, precision=precision, fmt="sell")
+    assert its_g == 5 and its_o == 5
+    rtol = 1e-11 if precision == "fp64" else 2e-5
+    assert abs(ratio_g - ratio_o) <= rtol * ratio_o
+    np.testing.assert_allclose(xg, xo, rtol=0, atol=rtol * np.abs(xo).max())
+    # the multi-column kernel on the same storage
+    B = np.column_stack([u, rng.standard_normal(u.size)])
+    Xo, _, _, _ = O.mrs(1.0, apply, B, 5, 1e-14, freeze=True)
+    Xg, its_m, _ = pkg.mrs_multi(Jt, B, Q, alpha, tol=1e-14, maxit=5, precision=precision, fmt="sell")
+    assert np.all(its_m == 5)
+    np.testing.assert_allclose(Xg, Xo, rtol=0, atol=rtol * np.abs(Xo).max())
