@@ -104,7 +104,14 @@ typedef struct {
                                  options. The least-squares fit of §2 starts from them and stops at
                                  once when they already meet lls_tol, so a saved S resumes a set-up
                                  without refitting; NULL: start from S = 0                       */
+    int    scaling;           /* how Eq. mc64's P, D_r, D_c are found when row_perm, dr and dc are
+                                 all NULL: ASSS_SCALING_MAXES (identity P, row then column maxima)
+                                 or ASSS_SCALING_MATCHING (maximum-product matching and its dual
+                                 scalings, the role of MC64 in §2: |diag| = 1, other entries
+                                 <= 1 up to a relative 1e-9)                                    */
 } asss_options;
+
+enum { ASSS_SCALING_MAXES = 0, ASSS_SCALING_MATCHING = 1 };
 
 enum { ASSS_FORMAT_AUTO = 0, ASSS_FORMAT_SELL = 1, ASSS_FORMAT_DIAG = 2 };
 
@@ -176,6 +183,10 @@ asss_status asss_apply_preconditioner(asss_handle* h, int transpose, const doubl
 asss_status asss_export(asss_handle* h, double* dr, double* dc, double* w, double* d,
                         double* s_val, double* q, double* alpha, int32_t* neg);
 
+/* The row permutation of Eq. mc64 used by the handle: row i of Abar is row
+ * row_perm[i] of D_r A D_c (n entries; the identity unless given or matched). */
+asss_status asss_export_permutation(asss_handle* h, int32_t* row_perm);
+
 void asss_destroy(asss_handle* h);
 
 /* ------------------------------------------------------------------------
@@ -236,6 +247,18 @@ unsigned long long asss_kernel_launches(void);
  * pattern's CSR order.  Uses gamma, lls_tol, lls_maxit and stream from opt. */
 asss_status asss_skew_symmetrizer(const asss_csr* Abar, const asss_csr* s_pattern,
                                   const asss_options* opt, double* s_val, asss_stats* st);
+
+/* Maximum-product matching and scaling of a square A (§2, Eq. mc64, the role MC64
+ * plays in the paper): costs c_ij = log(max_k |a_kj|) - log|a_ij| on A's nonzeros, a
+ * perfect matching of minimum total cost (maximum product of matched |a_ij|) by an
+ * auction algorithm with epsilon-scaling, within n * 1e-9 * max(1, max c) of the
+ * optimum, and scalings from its dual variables.  row_perm (n), dr (n), dc (n), host
+ * or device, receive P, D_r, D_c with row i of P D_r A D_c equal to row row_perm[i] of
+ * D_r A D_c, |diagonal| = 1 and every other entry <= 1 + 1e-9 in modulus.  Explicit
+ * zeros of A are not matched.  ASSS_ERR_PATTERN when A has no perfect matching
+ * (structurally singular) or an empty column.  *rounds (may be NULL): auction rounds. */
+asss_status asss_matching_scaling(const asss_csr* A, int32_t* row_perm, double* dr, double* dc, int* rounds,
+                                  void* stream);
 
 /* k steps of skew-Lanczos (§3.2, Fig. 2) on the skew matrix J (values used as
  * given) from start vector q1 (n values, need not be normalised).  q receives

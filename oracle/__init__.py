@@ -27,3 +27,4 @@ from .asss import (  # noqa: F401
     tfqmr_cycle,
     fgmres_cycle,
 )
+from .matching import matching_costs, matching_scaling, max_product_matching  # noqa: F401

@@ -6,8 +6,8 @@ this package only marshals arguments.  ``Solver`` wraps set-up/solve/adjoint,
 ``skew_symmetrizer``, ``skew_lanczos`` and ``mrs`` expose single steps, and
 ``asss_solve`` is the differentiable PyTorch entry (adjoint in the backward pass).
 """
-from .binding import (EXPORTED, LIB_PATH, AsssError, BatchSolver, Solver, lib, mrs, mrs_multi,  # noqa: F401
-                      skew_lanczos, skew_symmetrizer)
+from .binding import (EXPORTED, LIB_PATH, AsssError, BatchSolver, Solver, lib, matching_scaling, mrs,  # noqa: F401
+                      mrs_multi, skew_lanczos, skew_symmetrizer)
 
 
 def asss_solve(solver, b, a_values):

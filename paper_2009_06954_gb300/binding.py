@@ -47,9 +47,11 @@ class Options(C.Structure):
                 ("restart", C.c_int), ("precision", C.c_int), ("outer", C.c_int), ("r_max", C.c_int),
                 ("seed", C.c_uint64), ("lls_tol", C.c_double), ("lls_maxit", C.c_int),
                 ("zero_tol", C.c_double), ("wait_timeout_ms", C.c_double), ("stream", C.c_void_p),
-                ("inner_format", C.c_int), ("q_bf16", C.c_int), ("s_values", C.c_void_p)]
+                ("inner_format", C.c_int), ("q_bf16", C.c_int), ("s_values", C.c_void_p),
+                ("scaling", C.c_int)]
 
 FORMATS = {"auto": 0, "sell": 1, "diag": 2}
+SCALINGS = {"maxes": 0, "matching": 1}
 
 
 class Stats(C.Structure):
@@ -68,7 +70,8 @@ class Stats(C.Structure):
 EXPORTED = ["asss_default_options", "asss_setup", "asss_solve", "asss_solve_adjoint",
             "asss_apply_operator", "asss_apply_preconditioner", "asss_export", "asss_destroy",
             "asss_status_str", "asss_last_error", "asss_skew_symmetrizer", "asss_skew_lanczos",
-            "asss_mrs", "asss_mrs_multi", "asss_kernel_launches", "asss_mrs_noalloc", "asss_setup_batched",
+            "asss_mrs", "asss_mrs_multi", "asss_kernel_launches", "asss_mrs_noalloc", "asss_export_permutation",
+            "asss_matching_scaling", "asss_setup_batched",
             "asss_solve_batched", "asss_destroy_batched", "asss_batch_cta_threads"]
 
 _lib = None
@@ -115,6 +118,8 @@ def lib():
     L.asss_skew_lanczos.argtypes = [pCSR, P, C.c_int, C.c_int, P, P, C.POINTER(C.c_int), P]
     L.asss_mrs.argtypes = [pCSR, C.c_int, P, P, C.c_double, C.c_double, P, P, C.c_double, C.c_int,
                            C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double), P]
+    L.asss_export_permutation.argtypes = [P, P]
+    L.asss_matching_scaling.argtypes = [pCSR, P, P, P, C.POINTER(C.c_int), P]
     L.asss_mrs_multi.argtypes = [pCSR, C.c_int, P, P, C.c_double, C.c_double, C.c_int, P, C.c_int64, P, C.c_int64,
                                  C.c_double, C.c_int, C.c_int, C.c_int, P, P, P]
     L.asss_mrs_noalloc.argtypes = [C.c_int64, C.c_int64, P, P, P, C.c_int, C.c_int, P, P, C.c_double,
@@ -131,7 +136,8 @@ def lib():
     L.asss_kernel_launches.restype = C.c_ulonglong
     for f in ("asss_setup", "asss_solve", "asss_solve_adjoint", "asss_apply_operator",
               "asss_apply_preconditioner", "asss_export", "asss_skew_symmetrizer",
-              "asss_skew_lanczos", "asss_mrs", "asss_mrs_multi", "asss_setup_batched", "asss_solve_batched"):
+              "asss_skew_lanczos", "asss_mrs", "asss_mrs_multi", "asss_setup_batched", "asss_solve_batched",
+              "asss_export_permutation", "asss_matching_scaling"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -218,6 +224,9 @@ def _options(keep, **kw):
     fmt = kw.pop("inner_format", None)
     if fmt is not None:
         o.inner_format = FORMATS.get(fmt, fmt)
+    scl = kw.pop("scaling", None)
+    if scl is not None:
+        o.scaling = SCALINGS.get(scl, scl)
     stream = kw.pop("stream", None)
     if stream is not None:
         o.stream = stream if isinstance(stream, int) else stream.cuda_stream
@@ -241,7 +250,8 @@ class Solver:
     A: scipy.sparse matrix (host).  Options follow ``asss_options``: precision
     ('fp64' | 'mixed'), outer ('tfqmr' | 'fgmres'), gamma, k, reorth, s_pattern,
     inner_tol, setup_tol, outer_tol, inner_maxit, outer_maxit, restart, r_max,
-    seed, lls_tol, lls_maxit, zero_tol, wait_timeout_ms, row_perm, dr, dc, stream, s_values
+    seed, lls_tol, lls_maxit, zero_tol, wait_timeout_ms, row_perm, dr, dc, stream, s_values,
+    scaling ('maxes' | 'matching': how Eq. mc64's P, D_r, D_c are found when none is given)
     (saved S values to resume the set-up from, e.g. ``export(nnz)["s_val"]`` of an
     earlier solver for the same matrix).
     """
@@ -330,6 +340,12 @@ class Solver:
                lib().asss_apply_preconditioner(self._h, int(transpose), _ptr_f(u, keep),
                                                _ptr_f(out, keep), C.byref(st)))
         return out, int(st.inner_its_total)
+
+    def export_permutation(self):
+        """Row permutation of Eq. mc64: row i of Abar is row perm[i] of D_r A D_c."""
+        out = np.empty(self.n, dtype=np.int32)
+        _check("asss_export_permutation", lib().asss_export_permutation(self._h, out.ctypes.data))
+        return out
 
     def export(self, s_nnz):
         n = self.n
@@ -488,6 +504,20 @@ def mrs(J, b, Q=None, alpha=None, shift=1.0, sign=1.0, tol=1e-10, maxit=1000, pr
                                       x.ctypes.data, float(tol), int(maxit), prec, FORMATS[fmt], C.byref(its),
                                       C.byref(ratio), None))
     return x, its.value, ratio.value
+
+
+def matching_scaling(A):
+    """(row_perm, dr, dc, rounds): maximum-product matching and dual scalings (Eq. mc64)."""
+    keep = []
+    a = _csr_struct(A, keep)
+    n = int(a.n)
+    perm = np.empty(n, dtype=np.int32)
+    dr = np.empty(n)
+    dc = np.empty(n)
+    rounds = C.c_int(0)
+    _check("asss_matching_scaling", lib().asss_matching_scaling(C.byref(a), perm.ctypes.data, dr.ctypes.data,
+                                                                dc.ctypes.data, C.byref(rounds), None))
+    return perm, dr, dc, rounds.value
 
 
 def mrs_multi(J, B, Q=None, alpha=None, shift=1.0, sign=1.0, tol=1e-10, maxit=1000, precision="fp64",

@@ -556,6 +556,7 @@ static void fill_defaults(asss_options* o) {
     o->inner_format = ASSS_FORMAT_AUTO;
     o->q_bf16 = 0;
     o->s_values = nullptr;
+    o->scaling = ASSS_SCALING_MAXES;
 }
 
 static int pick_kp(int k) {
@@ -1113,13 +1114,16 @@ static asss_status do_setup(asss_handle* h, const asss_csr* Ain, asss_stats* st)
     if (o.k_lanczos < 0 || o.gamma <= 0 || o.inner_maxit < 1 || o.outer_maxit < 0 ||
         (o.precision != ASSS_PREC_FP64 && o.precision != ASSS_PREC_MIXED) ||
         (o.outer != ASSS_OUTER_TFQMR && o.outer != ASSS_OUTER_FGMRES) || (o.outer == ASSS_OUTER_FGMRES && o.restart < 1) ||
-        o.inner_format < ASSS_FORMAT_AUTO || o.inner_format > ASSS_FORMAT_DIAG) {
+        o.inner_format < ASSS_FORMAT_AUTO || o.inner_format > ASSS_FORMAT_DIAG ||
+        (o.scaling != ASSS_SCALING_MAXES && o.scaling != ASSS_SCALING_MATCHING)) {
         set_error("invalid option");
         return ASSS_ERR_ARG;
     }
     ASSS_TRY(upload_csr(Ain, h->A, true, s));
     int n = h->A.n;
     h->n = n;
+    // Eq. mc64 by the maximum-product matching (the role of MC64) when nothing is given
+    const bool match = o.scaling == ASSS_SCALING_MATCHING && !o.row_perm && !o.dr && !o.dc;
     // scalings (Eq. mc64, reading: row max then column max unless given)
     ASSS_TRY(h->dr.alloc(n));
     ASSS_TRY(h->dc.alloc(n));
@@ -1128,7 +1132,11 @@ static asss_status do_setup(asss_handle* h, const asss_csr* Ain, asss_stats* st)
     ASSS_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
     DBuf<double> tmp;
     ASSS_TRY(tmp.alloc(n));
-    if (o.dr) {
+    if (match) {
+        ASSS_TRY(h->perm.alloc(n));
+        ASSS_TRY(matching_scaling(c, h->A, h->perm.p, h->dr.p, h->dc.p, nullptr, nullptr));
+        h->has_perm = true;
+    } else if (o.dr) {
         DBuf<double> t;
         ASSS_TRY(to_device(t, o.dr, n, s));
         ASSS_TRY(vcopy(h->dr.p, t.p, n, s));
@@ -1138,7 +1146,9 @@ static asss_status do_setup(asss_handle* h, const asss_csr* Ain, asss_stats* st)
         k_recip_check<<<cdiv(n, 256), 256, 0, s>>>(tmp.p, n, h->dr.p, flag.p);
         ASSS_CHECK_LAUNCH();
     }
-    if (o.dc) {
+    if (match) {
+        // dc came with the matching
+    } else if (o.dc) {
         DBuf<double> t;
         ASSS_TRY(to_device(t, o.dc, n, s));
         ASSS_TRY(vcopy(h->dc.p, t.p, n, s));
@@ -1628,6 +1638,48 @@ asss_status asss_skew_lanczos(const asss_csr* J, const double* q1, int k, int re
         ASSS_CUDA(cudaStreamSynchronize(c.stream));
     }
     ASSS_CUDA(cudaStreamSynchronize(c.stream));
+    return ASSS_OK;
+}
+
+asss_status asss_export_permutation(asss_handle* h, int32_t* row_perm) {
+    if (!h || !row_perm) {
+        set_error("invalid arguments");
+        return ASSS_ERR_ARG;
+    }
+    cudaStream_t s = h->ctx.stream;
+    if (h->has_perm) {
+        ASSS_CUDA(cudaMemcpyAsync(row_perm, h->perm.p, sizeof(int) * h->n, cudaMemcpyDefault, s));
+        ASSS_CUDA(cudaStreamSynchronize(s));
+    } else {
+        std::vector<int32_t> id(h->n);
+        for (int i = 0; i < h->n; ++i) id[i] = i;
+        ASSS_CUDA(cudaMemcpy(row_perm, id.data(), sizeof(int32_t) * h->n, cudaMemcpyDefault));
+    }
+    return ASSS_OK;
+}
+
+asss_status asss_matching_scaling(const asss_csr* A, int32_t* row_perm, double* dr, double* dc, int* rounds,
+                                  void* stream) {
+    Ctx c;
+    ASSS_TRY(make_ctx(c, stream, 2000.0));
+    if (!A || !row_perm || !dr || !dc) {
+        set_error("invalid arguments");
+        return ASSS_ERR_ARG;
+    }
+    cudaStream_t s = c.stream;
+    DCsr Ad;
+    ASSS_TRY(upload_csr(A, Ad, true, s));
+    const int n = Ad.n;
+    DBuf<int> perm;
+    DBuf<double> r, cc;
+    ASSS_TRY(perm.alloc(n));
+    ASSS_TRY(r.alloc(n));
+    ASSS_TRY(cc.alloc(n));
+    ASSS_TRY(matching_scaling(c, Ad, perm.p, r.p, cc.p, rounds, nullptr));
+    ASSS_CUDA(cudaMemcpyAsync(row_perm, perm.p, sizeof(int) * n, cudaMemcpyDefault, s));
+    ASSS_CUDA(cudaMemcpyAsync(dr, r.p, sizeof(double) * n, cudaMemcpyDefault, s));
+    ASSS_CUDA(cudaMemcpyAsync(dc, cc.p, sizeof(double) * n, cudaMemcpyDefault, s));
+    ASSS_CUDA(cudaStreamSynchronize(s));
     return ASSS_OK;
 }
 

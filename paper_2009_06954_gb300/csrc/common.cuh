@@ -106,7 +106,7 @@ struct DCsr {
 // of similar length and heavy-tailed row lengths do not pad every slice to its
 // longest row.  Padding entries have value 0 and a valid column; slots past the
 // last row map to row n (no row).
-constexpr int SELL_SIGMA = 1024;
+constexpr int SELL_SIGMA = 4096;
 template <class T>
 struct DSell {
     int n = 0;

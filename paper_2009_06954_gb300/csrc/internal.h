@@ -115,6 +115,12 @@ asss_status mrs_multi_solve(const Ctx& c, const MrsOperator& op, bool fp32, doub
                             const double* B, long long ldb, double* X64, float* X32, long long ldx, double tol,
                             int maxit, int* its, double* ratio);
 
+// matching.cu: maximum-product matching (auction, epsilon-scaling) and the dual
+// scalings of Eq. mc64; perm, dr, dc: device arrays of n entries (row i of Abar is
+// row perm[i] of D_r A D_c)
+asss_status matching_scaling(const Ctx& c, const DCsr& A, int* perm, double* dr, double* dc, int* rounds,
+                             double* eps);
+
 // lls.cu
 struct LlsResult {
     int its = 0;

@@ -226,6 +226,7 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
     // 0 sign*nu, 1 sign, 2 beta_{j-1} nu_{j-1}, 3 nu_p, 4 delta_pp, 5 1/theta_p, 6 xcoef_p,
     // 7..10 the final pass: nu, delta, 1/theta, xcoef
     __shared__ T s_cf[12];
+    __shared__ int s_next;   // SELL: next slice of this block for the warp that asks (see next_slice)
     if constexpr (FMT == 1) {
         for (int d = threadIdx.x; d < p.ndiag; d += MRS_THREADS) s_off[d] = p.off[d];
     }
@@ -362,6 +363,17 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
     T tacc[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) tacc[v] = (T)0;
+    // The slices of a SELL operator carry very different amounts of work (heavy-tailed
+    // rows), so in the step passes the warps of a block take them one at a time from a
+    // shared counter instead of in a fixed stride; the other storages keep the stride.
+    auto next_slice = [&](int sl) -> int {
+        if constexpr (FMT == 0) {
+            int nx = 0;
+            if (lane == 0) nx = atomicAdd(&s_next, 1);
+            return __shfl_sync(0xffffffffu, nx, 0);
+        }
+        return sl + MRS_WARPS;
+    };
     // the row held by lane `lane` of slice sl (SELL-C-sigma permutes rows within windows)
     auto row_of = [&](int sl) -> int {
         if constexpr (FMT == 0) {
@@ -413,6 +425,7 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
             sc.its = 0;
             sc.stop = r0 > zero ? 0 : 1;
             set_coefs();
+            s_next = s0 + MRS_WARPS;
         }
         __syncwarp();
         if (!sc.stop) make_u_warp0(sc.nu);
@@ -446,7 +459,7 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
         const T tnp = s_cf[3], tdpp = s_cf[4], tthp = s_cf[5], txp = s_cf[6];
 #pragma unroll
         for (int v = 0; v < NV; ++v) tacc[v] = (T)0;
-        for (int sl = s0 + warp; sl < s1; sl += MRS_WARPS) {
+        for (int sl = s0 + warp; sl < s1; sl = next_slice(sl)) {
             const int i = row_of(sl);
             const bool live = i < n;
             // this row's own data first (independent of the operator loop below)
@@ -559,6 +572,7 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
                     sc.G = Gn;
                 }
                 set_coefs();
+                s_next = s0 + MRS_WARPS;
             }
             __syncwarp();
             if (!sc.stop) make_u_warp0(sc.nu);

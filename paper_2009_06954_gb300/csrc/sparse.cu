@@ -541,7 +541,7 @@ constexpr int PAT_WARPS = 4;
 
 __global__ void k_pattern_rows(int n, const int* arp, const int* aci, const int* srp, const int* sci,
                                const int* strp, const int* stci, const int* atrp, const int* atci,
-                               int cap, const int* cand, const int* prp, int* counts, int* pci) {
+                               int cap, const int* cand, const int* prp, int* counts, int* pci, int* chk) {
     extern __shared__ int smem[];
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int* buf = smem + warp * cap;
@@ -582,15 +582,22 @@ __global__ void k_pattern_rows(int n, const int* arp, const int* aci, const int*
             }
         }
         int base = prp ? prp[i] : 0;
+        const int end = prp ? prp[i + 1] : 0;
         int written = 0;
         for (int t0 = 0; t0 < pos; t0 += 32) {
             int t = t0 + lane;
             bool u = (t < pos) && (t == 0 || buf[t] != buf[t - 1]);
             unsigned m = __ballot_sync(0xffffffffu, u);
-            if (pci && u) pci[base + written + __popc(m & ((1u << lane) - 1u))] = buf[t];
+            if (pci && u) {
+                // checked write: a row never writes past its own range
+                const int at = base + written + __popc(m & ((1u << lane) - 1u));
+                if (at < end) pci[at] = buf[t];
+                else atomicOr(chk, 1);
+            }
             written += __popc(m);
         }
         if (counts && lane == 0) counts[i] = written;
+        if (pci && lane == 0 && base + written != end) atomicOr(chk, 8);
         __syncwarp();
     }
 }
@@ -603,7 +610,7 @@ constexpr int PATH_THREADS = 512;
 __global__ void __launch_bounds__(PATH_THREADS) k_pattern_heavy(
     int n, const int* heavy, int nheavy, const int* arp, const int* aci, const int* srp, const int* sci,
     const int* strp, const int* stci, const int* atrp, const int* atci, unsigned* bitmaps, int words,
-    const int* prp, int* counts, int* pci) {
+    const int* prp, int* counts, int* pci, int* chk) {
     __shared__ int s_warp[PATH_THREADS / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = PATH_THREADS / 32;
     unsigned* bm = bitmaps + (size_t)blockIdx.x * words;
@@ -653,11 +660,14 @@ __global__ void __launch_bounds__(PATH_THREADS) k_pattern_heavy(
             if (threadIdx.x == PATH_THREADS - 1) counts[i] = before + cnt;
         } else {
             int pos = prp[i] + before;
+            const int end = prp[i + 1];
             for (int w = w0; w < w1; ++w) {
                 unsigned bits = bm[w];
                 while (bits) {
                     const int t = __ffs(bits) - 1;
-                    pci[pos++] = w * 32 + t;
+                    if (pos < end) pci[pos] = w * 32 + t;   // checked write
+                    else atomicOr(chk, 2);
+                    ++pos;
                     bits &= bits - 1u;
                 }
             }
@@ -666,11 +676,16 @@ __global__ void __launch_bounds__(PATH_THREADS) k_pattern_heavy(
     }
 }
 
-__global__ void k_mirror(int n, const int* prp, const int* pci, int* mirror, int* diagpos) {
+__global__ void k_mirror(int n, const int* prp, const int* pci, int* mirror, int* diagpos, int* chk) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     for (int k = prp[i]; k < prp[i + 1]; ++k) {
         int j = pci[k];
+        if (j < 0 || j >= n) {   // checked read: a column outside the matrix is recorded, not followed
+            atomicOr(chk, 4);
+            mirror[k] = -1;
+            continue;
+        }
         int lo = prp[j], hi = prp[j + 1] - 1, f = -1;
         while (lo <= hi) {
             int mid = (lo + hi) >> 1;
@@ -715,8 +730,10 @@ asss_status build_pattern(const DCsr& Abar, const DCsr& AbarT, const DCsr& S, co
         for (int i = 0; i < n; ++i)
             if (hc[i] > cap) heavy.push_back(i);
     }
-    DBuf<int> cand, hrows;
+    DBuf<int> cand, hrows, chk;
     DBuf<unsigned> bitmaps;
+    ASSS_TRY(chk.alloc(1));
+    ASSS_CUDA(cudaMemsetAsync(chk.p, 0, sizeof(int), s));
     const int words = (n + 31) / 32;
     int hblk = 0;
     ASSS_TRY(cand.alloc(n));
@@ -732,12 +749,12 @@ asss_status build_pattern(const DCsr& Abar, const DCsr& AbarT, const DCsr& S, co
     if (grid > 65535 * 8) grid = 65535 * 8;
     k_pattern_rows<<<grid, PAT_WARPS * 32, smem, s>>>(n, Abar.rp.p, Abar.ci.p, S.rp.p, S.ci.p, ST.rp.p,
                                                       ST.ci.p, AbarT.rp.p, AbarT.ci.p, cap, cand.p, nullptr,
-                                                      cnt.p, nullptr);
+                                                      cnt.p, nullptr, chk.p);
     ASSS_CHECK_LAUNCH();
     if (hblk) {
         k_pattern_heavy<<<hblk, PATH_THREADS, 0, s>>>(n, hrows.p, (int)heavy.size(), Abar.rp.p, Abar.ci.p, S.rp.p,
                                                       S.ci.p, ST.rp.p, ST.ci.p, AbarT.rp.p, AbarT.ci.p, bitmaps.p,
-                                                      words, nullptr, cnt.p, nullptr);
+                                                      words, nullptr, cnt.p, nullptr, chk.p);
         ASSS_CHECK_LAUNCH();
     }
     P.n = n;
@@ -752,18 +769,31 @@ asss_status build_pattern(const DCsr& Abar, const DCsr& AbarT, const DCsr& S, co
     ASSS_TRY(P.ci.alloc(tot));
     k_pattern_rows<<<grid, PAT_WARPS * 32, smem, s>>>(n, Abar.rp.p, Abar.ci.p, S.rp.p, S.ci.p, ST.rp.p,
                                                       ST.ci.p, AbarT.rp.p, AbarT.ci.p, cap, cand.p, P.rp.p,
-                                                      nullptr, P.ci.p);
+                                                      nullptr, P.ci.p, chk.p);
     ASSS_CHECK_LAUNCH();
     if (hblk) {
         k_pattern_heavy<<<hblk, PATH_THREADS, 0, s>>>(n, hrows.p, (int)heavy.size(), Abar.rp.p, Abar.ci.p, S.rp.p,
                                                       S.ci.p, ST.rp.p, ST.ci.p, AbarT.rp.p, AbarT.ci.p, bitmaps.p,
-                                                      words, P.rp.p, nullptr, P.ci.p);
+                                                      words, P.rp.p, nullptr, P.ci.p, chk.p);
         ASSS_CHECK_LAUNCH();
+    }
+    int hchk = 0;
+    ASSS_CUDA(cudaMemcpyAsync(&hchk, chk.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ASSS_CUDA(cudaStreamSynchronize(s));
+    if (hchk) {
+        set_error("pattern of Abar*S: a row's entries disagree with its count (check bits %d)", hchk);
+        return ASSS_ERR_CUDA;
     }
     ASSS_TRY(mirror.alloc(tot));
     ASSS_TRY(diagpos.alloc(n));
-    k_mirror<<<cdiv(n, 256), 256, 0, s>>>(n, P.rp.p, P.ci.p, mirror.p, diagpos.p);
+    k_mirror<<<cdiv(n, 256), 256, 0, s>>>(n, P.rp.p, P.ci.p, mirror.p, diagpos.p, chk.p);
     ASSS_CHECK_LAUNCH();
+    ASSS_CUDA(cudaMemcpyAsync(&hchk, chk.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ASSS_CUDA(cudaStreamSynchronize(s));
+    if (hchk) {
+        set_error("pattern of Abar*S: a column index outside the matrix (check bits %d)", hchk);
+        return ASSS_ERR_CUDA;
+    }
     return ASSS_OK;
 }
 
@@ -786,37 +816,45 @@ __global__ void k_sell_rowlen(int n, const int* rp, const int* ci, int skip_diag
 }
 
 // SELL-C-sigma: one block per window of SELL_SIGMA rows sorts (length desc, row asc)
-// with a bitonic network in shared memory and writes slot -> row and row -> slot;
-// slots past the last row map to row n
-__global__ void __launch_bounds__(SELL_SIGMA) k_sell_sort_window(int n, int nslots, const int* len, int* rowmap,
-                                                                   int* rowpos) {
+// with a bitonic network in shared memory (each of the 1024 threads holds
+// SELL_SIGMA / 1024 keys) and writes slot -> row and row -> slot; slots past the last
+// row map to row n
+constexpr int SELL_SORT_THREADS = 1024;
+__global__ void __launch_bounds__(SELL_SORT_THREADS) k_sell_sort_window(int n, int nslots, const int* len,
+                                                                          int* rowmap, int* rowpos) {
     __shared__ long long key[SELL_SIGMA];
     const int w0 = blockIdx.x * SELL_SIGMA;
-    const int t = threadIdx.x;
-    const int r = w0 + t;
-    // key: length in the high word (complemented for descending order), row in the low word
-    key[t] = r < n ? ((long long)(0x7fffffff - len[r]) << 32) | (unsigned)r : ((long long)0x7fffffff << 32) | 0x7fffffffu;
+    for (int t = threadIdx.x; t < SELL_SIGMA; t += SELL_SORT_THREADS) {
+        const int r = w0 + t;
+        // length in the high word (complemented: descending), row in the low word
+        key[t] = r < n ? ((long long)(0x7fffffff - len[r]) << 32) | (unsigned)r
+                       : ((long long)0x7fffffff << 32) | 0x7fffffffu;
+    }
     __syncthreads();
     for (int k = 2; k <= SELL_SIGMA; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
-            const int ixj = t ^ j;
-            if (ixj > t) {
-                const long long a = key[t], b = key[ixj];
-                const bool up = (t & k) == 0;
-                if ((a > b) == up) {
-                    key[t] = b;
-                    key[ixj] = a;
+            for (int t = threadIdx.x; t < SELL_SIGMA; t += SELL_SORT_THREADS) {
+                const int ixj = t ^ j;
+                if (ixj > t) {
+                    const long long a = key[t], b = key[ixj];
+                    const bool up = (t & k) == 0;
+                    if ((a > b) == up) {
+                        key[t] = b;
+                        key[ixj] = a;
+                    }
                 }
             }
             __syncthreads();
         }
     }
-    const int slot = w0 + t;
-    if (slot < nslots) {
-        const int row = (int)(key[t] & 0xffffffffLL);
-        const bool real = row < n;   // the padding key's row word is 0x7fffffff >= n
-        rowmap[slot] = real ? row : n;
-        if (real) rowpos[row] = slot;
+    for (int t = threadIdx.x; t < SELL_SIGMA; t += SELL_SORT_THREADS) {
+        const int slot = w0 + t;
+        if (slot < nslots) {
+            const int row = (int)(key[t] & 0xffffffffLL);
+            const bool real = row < n;   // the padding key's row word is 0x7fffffff >= n
+            rowmap[slot] = real ? row : n;
+            if (real) rowpos[row] = slot;
+        }
     }
 }
 
@@ -891,8 +929,8 @@ asss_status build_sell(const DCsr& A, bool skip_diag, DSell<T>& out, cudaStream_
         const int nslots = ns * 32;
         ASSS_TRY(out.rowmap.alloc(nslots));
         ASSS_TRY(out.rowpos.alloc(n));
-        k_sell_sort_window<<<cdiv(nslots, SELL_SIGMA), SELL_SIGMA, 0, s>>>(n, nslots, len.p, out.rowmap.p,
-                                                                           out.rowpos.p);
+        k_sell_sort_window<<<cdiv(nslots, SELL_SIGMA), SELL_SORT_THREADS, 0, s>>>(n, nslots, len.p, out.rowmap.p,
+                                                                                  out.rowpos.p);
         ASSS_CHECK_LAUNCH();
     }
     out.nnz = (int64_t)hn;

@@ -252,6 +252,26 @@ def pattern_of(A):
     return _pattern(sp.csr_matrix(A))
 
 
+def indefinite_zero_diagonal(n: int, seed: int = 0):
+    """Sparse indefinite matrix whose diagonal is zero: random N(0,1) entries (about 4
+    per row) plus one large entry of random sign per row at a random permuted
+    position (|a| in [3, 4)), so that a row permutation exists that puts large
+    entries on the diagonal - the situation the matching of §2 (Eq. mc64) is for."""
+    rng = np.random.default_rng(seed)
+    K = sp.random(n, n, density=4.0 / n, random_state=rng, data_rvs=rng.standard_normal).tolil()
+    perm = rng.permutation(n)
+    for i in range(n):
+        K[i, perm[i]] = (3.0 + rng.random()) * rng.choice([-1.0, 1.0])
+    for i in np.flatnonzero(perm == np.arange(n)):   # keep the diagonal zero
+        K[i, i] = 0.0
+        K[i, (i + 1) % n] = 5.0
+    K = K.tocsr()
+    K.setdiag(0.0)
+    K.eliminate_zeros()
+    K.sort_indices()
+    return K
+
+
 def pattern_symmetrized(A):
     """Pattern of A + A^T (unit values)."""
     P = (abs(sp.csr_matrix(A)) + abs(sp.csr_matrix(A)).T).tocsr()
