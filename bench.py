@@ -35,6 +35,11 @@ SIDE = 100
 CPU_SAMPLE_SIDE = 40
 ADJ_CPU_SIDE = 24
 BATCH = {"count": 256, "side_lo": 10, "side_hi": 40, "nrhs": 32, "seed": 3}
+GENERAL = {"n": 2_000_000, "seed": 2, "outer_steps": 20, "lls_maxit": 100}
+GENERAL_WORKLOAD = ("general_2e6: general sparse nonsymmetric matrix, n = {n:,}, power-law row lengths (min 4, mean 16, "
+                    "max 512), 60% of columns within |i-j| <= 1000, N(0,1) values, 30% of rows with diagonal 1.1 x "
+                    "row abs-sum, S on pat(A + A^T), b ~ N(0,1); FP32 inner mrs (tol 1e-6, J~ in SELL-C-sigma) / FP64 "
+                    "outer FGMRES(60); a step = {steps} outer steps (the method does not reach 1e-8 on this recipe)")
 ADJ_SIDE = 64
 ADJ_WORKLOAD = ("adjoint_dh64: gradient of L = ||x - x*||^2 for the dissipative-Hamiltonian step on a 64^3 grid "
                 "(n = 262,144), x* ~ N(0,1): dL/db = lambda from A^T lambda = 2 (x - x*) and dL/dA = -lambda_i x_j "
@@ -601,6 +606,112 @@ def main_adjoint(args, world, rank, local):
 
 
 # ----------------------------------------------------------------------------
+# general power-law matrix: the SELL-C path at size (inner iterations/s)
+# ----------------------------------------------------------------------------
+def main_general(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_2009_06954_gb300 as pkg
+    from paper_2009_06954_gb300.binding import kernel_launches
+    from workloads import pattern_symmetrized, random_powerlaw
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    n = GENERAL["n"]
+    A, b = random_powerlaw(n=n, seed=GENERAL["seed"] + rank)
+    Sp = pattern_symmetrized(A)
+    t0 = time.perf_counter()
+    solver = pkg.Solver(A, s_pattern=Sp, precision="mixed", outer="fgmres", inner_tol=1e-6, outer_tol=1e-8,
+                        outer_maxit=GENERAL["outer_steps"], lls_maxit=GENERAL["lls_maxit"], k=20,
+                        stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    bd = torch.tensor(b, device=dev)
+    x = torch.empty(n, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        solver.solve(bd, x)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    l0 = kernel_launches()
+    with ClockSampler(dev.index) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            _, st = solver.solve(bd, x)
+            evs[k][1].record(stream)
+            stats.append(st)
+        torch.cuda.synchronize()
+    launches = kernel_launches() - l0
+    total_ms = sum(a.elapsed_time(c) for a, c in evs)
+    tmax = reduce_max(total_ms, dist, dev)
+    inner_its = sum(s_["inner_its_total"] for s_ in stats)
+    inner_ms = sum(s_["t_inner_ms"] for s_ in stats)
+    inner_bytes = sum(s_["inner_bytes"] for s_ in stats)
+    inner_launches = sum(s_["inner_launches"] for s_ in stats)
+    value = world * inner_its / (tmax / 1000.0)
+    # end to end: b in from pinned host memory, x out, every step
+    bp = torch.from_numpy(b).pin_memory()
+    xp = torch.empty(n, dtype=torch.float64).pin_memory()
+    e2e_s, e2e_its = 0.0, 0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        _, st = solver.solve(bp, xp)
+        e2e_s += time.perf_counter() - t
+        e2e_its += st["inner_its_total"]
+    e2e_val = world * e2e_its / reduce_max(e2e_s, dist, dev)
+    peak, peak_kind = _peaks()
+    achieved = inner_bytes / (inner_ms / 1000.0) / 1e9 if inner_ms > 0 else 0.0
+    relres = float(np.linalg.norm(b - A @ xp.numpy()) / np.linalg.norm(b))
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": "inner mrs iterations/s (general power-law system, fixed outer steps)", "value": value,
+        "unit": "mrs iterations/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32-inner/f64-outer", "data": "synthetic",
+        "config": {"workload": GENERAL_WORKLOAD.format(n=n, steps=GENERAL["outer_steps"]),
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "256 MB buffer written between steps (not timed); working set > L2",
+                   "setup_s": round(t_setup, 2), "lls_its": solver.setup_stats["lls_its"],
+                   "lls_relgrad": solver.setup_stats["lls_relgrad"], "lls_maxit": GENERAL["lls_maxit"],
+                   "nnz_pattern": solver.setup_stats["nnz_pattern"], "r": solver.setup_stats["r"],
+                   "outer_its": stats[-1]["outer_its"], "inner_its_avg": round(stats[-1]["inner_its_avg"], 2),
+                   "relres_after_step": relres, "status": stats[-1]["status"], "converged": False,
+                   "solves_per_s": None},
+        "gpu_launches": int(launches),
+        "e2e": {"value": e2e_val, "unit": "mrs iterations/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
+        "roofline": {"bound": "hbm", "kernel": "k_mrs<float,20,SELL> (persistent mrs, SELL-C-sigma J~)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak if peak else None,
+                     "peak_source": f"{peak_kind} hbm_gbs", "traffic": None,
+                     "algorithmic_bytes_per_launch": inner_bytes / max(inner_launches, 1),
+                     "avg_launch_ms": inner_ms / max(inner_launches, 1), "launches": inner_launches,
+                     "share_of_step": inner_ms / total_ms if total_ms else None},
+        "clocks": clk.summary(),
+        "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+    solver.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------
 # reference arm: the FP64 CPU oracle, timed as it stands on the host cores
 # ----------------------------------------------------------------------------
 def main_reference(args):
@@ -616,6 +727,12 @@ def main_reference(args):
         workload = BATCH_WORKLOAD.format(count=BATCH["count"], items=BATCH["count"] * BATCH["nrhs"])
         steps, warm, ms = cb["solves"], 0, 1000.0 * cb["seconds"] / max(cb["solves"], 1)
         per_step = "one oracle solve of a sampled (matrix, column) item, counted as n_item / mean n of an item"
+    elif args.workload == "general_2e6":
+        line = {"impl": "reference", "metric": "inner mrs iterations/s (general power-law system, fixed outer steps)",
+                "unavailable": ("the oracle's least-squares set-up (LSQR) of the 2e6-row power-law system does not "
+                                "finish within a benchmark run; its solve phase is compared on 2e4 rows in the tests")}
+        print(json.dumps(line), flush=True)
+        return
     elif adj:
         cb = run_adjoint_cpu_baseline(120.0)
         workload = ADJ_WORKLOAD
@@ -678,16 +795,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--q-storage", default="f32", choices=["f32", "bf16"],
                     help="storage of the Lanczos basis read by the FP32 inner solve")
-    ap.add_argument("--workload", default="dh3d_100", choices=["dh3d_100", "batched_dh", "adjoint_dh64"],
+    ap.add_argument("--workload", default="dh3d_100", choices=["dh3d_100", "batched_dh", "adjoint_dh64", "general_2e6"],
                     help="dh3d_100: one 1e6-unknown system; batched_dh: 256 systems x 32 right-hand sides; "
                          "adjoint_dh64: gradients through the adjoint solve")
     ap.add_argument("--procs", type=int, default=0, help="(CPU worker) processes of the oracle pool")
     ap.add_argument("--xout", default="", help="(CPU worker) where to save the oracle's x of the first rhs")
     ap.add_argument("--no-fp64-leg", action="store_true", help="skip the FP64-GPU comparison solve")
+    ap.add_argument("--general-n", type=int, default=GENERAL["n"], help="rows of the general_2e6 workload")
     ap.add_argument("--batch-count", type=int, default=BATCH["count"],
                     help="systems in the batched workload (smaller counts for profiling captures)")
     args = ap.parse_args()
     BATCH["count"] = args.batch_count
+    GENERAL["n"] = args.general_n
 
     if args.cpu_worker:
         if args.workload == "batched_dh":
@@ -704,6 +823,9 @@ def main():
         return
     if args.workload == "adjoint_dh64" and args.impl != "reference":
         main_adjoint(args, world, rank, local)
+        return
+    if args.workload == "general_2e6" and args.impl != "reference":
+        main_general(args, world, rank, local)
         return
 
     if args.impl == "reference":

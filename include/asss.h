@@ -108,7 +108,7 @@ typedef struct {
                                  all NULL: ASSS_SCALING_MAXES (identity P, row then column maxima)
                                  or ASSS_SCALING_MATCHING (maximum-product matching and its dual
                                  scalings, the role of MC64 in §2: |diag| = 1, other entries
-                                 <= 1 up to a relative 1e-9)                                    */
+                                 <= 1 up to a relative 1e-12 * max(1, max cost))                */
 } asss_options;
 
 enum { ASSS_SCALING_MAXES = 0, ASSS_SCALING_MATCHING = 1 };
@@ -251,10 +251,10 @@ asss_status asss_skew_symmetrizer(const asss_csr* Abar, const asss_csr* s_patter
 /* Maximum-product matching and scaling of a square A (§2, Eq. mc64, the role MC64
  * plays in the paper): costs c_ij = log(max_k |a_kj|) - log|a_ij| on A's nonzeros, a
  * perfect matching of minimum total cost (maximum product of matched |a_ij|) by an
- * auction algorithm with epsilon-scaling, within n * 1e-9 * max(1, max c) of the
- * optimum, and scalings from its dual variables.  row_perm (n), dr (n), dc (n), host
- * or device, receive P, D_r, D_c with row i of P D_r A D_c equal to row row_perm[i] of
- * D_r A D_c, |diagonal| = 1 and every other entry <= 1 + 1e-9 in modulus.  Explicit
+ * auction algorithm with epsilon-scaling down to eps = 1e-12 * max(1, max c), within
+ * n * eps of the optimum, and scalings from its dual variables.  row_perm (n), dr (n),
+ * dc (n), host or device, receive P, D_r, D_c with row i of P D_r A D_c equal to row
+ * row_perm[i] of D_r A D_c, |diagonal| = 1 and every other entry <= exp(eps) in modulus.  Explicit
  * zeros of A are not matched.  ASSS_ERR_PATTERN when A has no perfect matching
  * (structurally singular) or an empty column.  *rounds (may be NULL): auction rounds. */
 asss_status asss_matching_scaling(const asss_csr* A, int32_t* row_perm, double* dr, double* dc, int* rounds,

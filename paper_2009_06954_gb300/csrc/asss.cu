@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <vector>
 
 #include <cuda_bf16.h>
@@ -528,6 +529,12 @@ struct asss_handle {
     // statistics of the current solve
     int inner_solves = 0;
     asss_stats setup_stats;
+    // block solve (several right-hand sides in lockstep): per-column Krylov work and
+    // buffers, allocated on first use
+    static constexpr int BLK = 8;
+    std::unique_ptr<KrylovWork> kwb[BLK];
+    DBuf<double> blk_r, blk_rh, blk_dy, blk_z64, blk_G, blk_T, blk_b, blk_x;
+    DBuf<float> blk_z32;
     ~asss_handle() {
         if (mw) mrs_work_destroy(mw);
     }
@@ -1104,6 +1111,284 @@ static asss_status refine(asss_handle* h, int tr, const double* rhs, double* x, 
 }
 
 // ---------------------------------------------------------------------------
+// several right-hand sides in lockstep: every column runs its own refinement loop
+// and flexible GMRES (same arithmetic as refine / fgmres_cycle), but the
+// preconditioner applications of one Arnoldi step are a single multi-column mrs
+// launch (App. B's simultaneous iterations), so the columns share each pass over J~
+// and Q_k
+// ---------------------------------------------------------------------------
+__global__ void k_gather_col(const double* G, int ldg, int col, int k, double* out) {
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < k) out[a] = G[(size_t)a * ldg + col];
+}
+
+// out_c = P^-1 u_c (tr = 0) or P^-T u_c for the columns listed (Eq. smw around one
+// multi-column mrs launch per 8 columns)
+static asss_status apply_prec_block(asss_handle* h, int tr, int nc, const double* const* u, double* const* out,
+                                    long long* its_sum, int* launches) {
+    NvtxRange nv_("asss:preconditioner-block");
+    const Ctx& c = h->ctx;
+    cudaStream_t s = c.stream;
+    const int n = h->n;
+    ASSS_TRY(ensure_smw(h, tr));
+    MrsOperator op;
+    op.J64 = h->use_dia ? nullptr : &h->J64;
+    op.J32 = (!h->use_dia && h->J32.n) ? &h->J32 : nullptr;
+    op.D64 = h->use_dia ? &h->D64 : nullptr;
+    op.D32 = (h->use_dia && h->D32.n) ? &h->D32 : nullptr;
+    op.k = h->k;
+    op.kp = h->kp;
+    op.Q64 = h->Q64.p;
+    op.Q32 = h->Q32.p;
+    op.alpha = h->alpha_d.p;
+    const bool fp32 = h->opt.precision == ASSS_PREC_MIXED;
+    const double sign = tr ? -1.0 : 1.0;
+    SmwData& S = h->smw[tr];
+    const int B = asss_handle::BLK;
+    int its[B];
+    double ratio[B];
+    double* z64[B];
+    float* z32[B];
+    for (int t = 0; t < nc; ++t) {
+        z64[t] = (S.m > 0 || fp32) ? h->blk_z64.p + (size_t)t * n : out[t];
+        z32[t] = h->blk_z32.p ? h->blk_z32.p + (size_t)t * n : nullptr;
+    }
+    if (fp32) {
+        ASSS_TRY(mrs_multi_solve_cols(c, op, true, 1.0, sign, nc, u, nullptr, z32, h->opt.inner_tol,
+                                      h->opt.inner_maxit, its, ratio));
+        for (int t = 0; t < nc; ++t) {
+            k_f2d<<<cdiv(n, 256), 256, 0, s>>>(z32[t], z64[t], n);
+            ASSS_CHECK_LAUNCH();
+        }
+    } else {
+        ASSS_TRY(mrs_multi_solve_cols(c, op, false, 1.0, sign, nc, u, z64, nullptr, h->opt.inner_tol,
+                                      h->opt.inner_maxit, its, ratio));
+    }
+    for (int t = 0; t < nc; ++t) *its_sum += its[t];
+    *launches += nc;
+    if (S.m > 0) {
+        // U_bar^T z = [Q_k^T z ; z(neg)] for every column at once (one pass over Q_k)
+        if (h->k) ASSS_TRY(gram(h->Qcm.p, n, h->k, h->blk_z64.p, n, nc, n, h->blk_G.p, s));
+        for (int t = 0; t < nc; ++t) {
+            double* wv = h->blk_T.p + (size_t)t * (S.m + 1);
+            if (h->k) {
+                k_gather_col<<<cdiv(h->k, 64), 64, 0, s>>>(h->blk_G.p, nc, t, h->k, wv);
+                ASSS_CHECK_LAUNCH();
+            }
+            if (h->r) {
+                k_gather_neg<<<cdiv(h->r, 128), 128, 0, s>>>(z64[t], h->neg.p, h->r, wv + h->k);
+                ASSS_CHECK_LAUNCH();
+            }
+            if (fp32) {
+                k_smw_apply_f32<<<cdiv(n, 256), 256, sizeof(float) * S.m, s>>>(
+                    z32[t], S.Y32.p, S.m, wv, n, out[t],
+                    stream_evict_first(c, (long long)n * (4LL * h->kp + 28) + 4LL * h->D32.nnz) ? 1 : 0);
+                ASSS_CHECK_LAUNCH();
+            } else {
+                ASSS_TRY(sub_rowmajor_gemv(S.Y.p, S.m, wv, z64[t], n, out[t], s));
+            }
+        }
+    } else if (fp32) {
+        for (int t = 0; t < nc; ++t) ASSS_TRY(vcopy(out[t], z64[t], n, s));
+    }
+    return ASSS_OK;
+}
+
+static asss_status refine_block(asss_handle* h, int nb, const double* const* rhs, double* const* x,
+                                asss_stats* st) {
+    NvtxRange nv_("asss:solve-block");
+    cudaStream_t s = h->ctx.stream;
+    const int n = h->n;
+    const int nbk = cdiv(n, 256);
+    const asss_options& o = h->opt;
+    const int B = asss_handle::BLK;
+    const int M = o.restart > 0 ? o.restart : 60;
+    for (int t = 0; t < nb; ++t) {
+        if (!h->kwb[t]) h->kwb[t].reset(new KrylovWork());
+        ASSS_TRY(h->kwb[t]->init(n, M, ASSS_OUTER_FGMRES));
+    }
+    if (!h->blk_r.p) {
+        ASSS_TRY(h->blk_r.alloc((int64_t)B * n));
+        ASSS_TRY(h->blk_rh.alloc((int64_t)B * n));
+        ASSS_TRY(h->blk_dy.alloc((int64_t)B * n));
+        ASSS_TRY(h->blk_z64.alloc((int64_t)B * n));
+        if (o.precision == ASSS_PREC_MIXED) ASSS_TRY(h->blk_z32.alloc((int64_t)B * n));
+        ASSS_TRY(h->blk_G.alloc((int64_t)B * (h->k + 1)));
+        ASSS_TRY(h->blk_T.alloc((int64_t)B * (h->k + h->r + 2)));
+    }
+    if (!h->t1.p) {
+        set_error("internal: work vectors missing");
+        return ASSS_ERR_CUDA;
+    }
+    ASSS_TRY(mrs_collect(h->ctx, h->mw, nullptr));
+    mrs_take_totals(h->mw);
+    double* r[B];
+    double* rh[B];
+    double* dy[B];
+    double bn[B], best[B];
+    int stall[B], active[B];
+    long long its_sum = 0;
+    int launches = 0;
+    int* perm = h->has_perm ? h->perm.p : nullptr;
+    for (int t = 0; t < nb; ++t) {
+        r[t] = h->blk_r.p + (size_t)t * n;
+        rh[t] = h->blk_rh.p + (size_t)t * n;
+        dy[t] = h->blk_dy.p + (size_t)t * n;
+        st[t] = h->setup_stats;
+        st[t].outer_its = 0;
+        st[t].cycles = 0;
+        st[t].relres = 0.0;
+        st[t].status = ASSS_OK;
+        ASSS_CUDA(cudaMemsetAsync(x[t], 0, sizeof(double) * n, s));
+        ASSS_TRY(vcopy(r[t], rhs[t], n, s));
+        ASSS_TRY(dot(rhs[t], rhs[t], n, h->kwb[t]->T.p + 8, s));
+        best[t] = INFINITY;
+        stall[t] = 0;
+    }
+    std::vector<double> hv(nb);
+    for (int t = 0; t < nb; ++t) {
+        asss_status es = ASSS_OK;
+        bn[t] = sqrt(read_scalar(h->kwb[t]->T.p + 8, s, &es));
+        ASSS_TRY(es);
+        active[t] = bn[t] > 0.0;
+    }
+    bool first = true;
+    while (true) {
+        // the true residual of every active column; stop tests as in refine
+        for (int t = 0; t < nb; ++t)
+            if (active[t] && !first) ASSS_TRY(dot(r[t], r[t], n, h->kwb[t]->T.p + 8, s));
+        int na = 0;
+        for (int t = 0; t < nb; ++t) {
+            if (!active[t]) continue;
+            double rn = bn[t];
+            if (!first) {
+                asss_status es = ASSS_OK;
+                rn = sqrt(read_scalar(h->kwb[t]->T.p + 8, s, &es));
+                ASSS_TRY(es);
+            }
+            st[t].relres = rn / bn[t];
+            hv[t] = rn;
+            if (rn / bn[t] <= o.outer_tol) {
+                active[t] = 0;
+            } else if (!(rn == rn)) {
+                st[t].status = ASSS_ERR_BREAKDOWN;
+                active[t] = 0;
+            } else if (st[t].outer_its >= o.outer_maxit) {
+                st[t].status = ASSS_ERR_NOT_CONVERGED;
+                active[t] = 0;
+            } else if (rn < 0.999 * best[t]) {
+                best[t] = rn;
+                stall[t] = 0;
+            } else if (++stall[t] >= 5) {
+                st[t].status = ASSS_ERR_STAGNATION;
+                active[t] = 0;
+            }
+            na += active[t];
+        }
+        first = false;
+        if (!na) break;
+        // one FGMRES cycle per active column, the Arnoldi steps in lockstep
+        int cols[B], nc = 0;
+        double thr[B];
+        int steps[B], live[B];
+        for (int t = 0; t < nb; ++t) {
+            if (!active[t]) continue;
+            cols[nc++] = t;
+            KrylovWork& kw = *h->kwb[t];
+            k_to_scaled_fwd<<<nbk, 256, 0, s>>>(r[t], h->dr.p, h->w.p, perm, n, rh[t]);  // W P D_r r
+            ASSS_CHECK_LAUNCH();
+            ASSS_TRY(dot(rh[t], rh[t], n, kw.T.p, s));
+            k_fg_init<<<1, 1, 0, s>>>(kw.g.p, kw.m, kw.T.p, kw.T.p + 1);
+            ASSS_CHECK_LAUNCH();
+            ASSS_CUDA(cudaMemsetAsync(dy[t], 0, sizeof(double) * n, s));
+            k_scale_dev<<<nbk, 256, 0, s>>>(kw.V.p, rh[t], kw.T.p + 1, n);
+            ASSS_CHECK_LAUNCH();
+        }
+        std::vector<double> beta0(nb, 0.0);
+        for (int q = 0; q < nc; ++q) {
+            const int t = cols[q];
+            asss_status es = ASSS_OK;
+            beta0[t] = sqrt(read_scalar(h->kwb[t]->T.p, s, &es));
+            ASSS_TRY(es);
+            const double eta = fmin(0.5, 0.5 * o.outer_tol * bn[t] / hv[t]);
+            const int budget = o.outer_maxit - st[t].outer_its;
+            thr[t] = eta * beta0[t];
+            steps[t] = 0;
+            live[t] = beta0[t] > 0.0 && budget > 0;
+        }
+        const int mcyc = M;
+        for (int j = 0; j < mcyc; ++j) {
+            int lc[B], nl = 0;
+            for (int q = 0; q < nc; ++q)
+                if (live[cols[q]] && j < o.outer_maxit - st[cols[q]].outer_its) lc[nl++] = cols[q];
+                else live[cols[q]] = 0;
+            if (!nl) break;
+            // z_j = P^-1 v_j for every live column in one multi-column launch
+            const double* uin[B];
+            double* zout[B];
+            for (int q = 0; q < nl; ++q) {
+                KrylovWork& kw = *h->kwb[lc[q]];
+                uin[q] = kw.V.p + (size_t)j * n;
+                zout[q] = kw.Z.p + (size_t)j * n;
+            }
+            ASSS_TRY(apply_prec_block(h, 0, nl, uin, zout, &its_sum, &launches));
+            for (int q = 0; q < nl; ++q) {
+                const int t = lc[q];
+                KrylovWork& kw = *h->kwb[t];
+                ASSS_TRY(apply_op(h, 0, kw.Z.p + (size_t)j * n, kw.w.p));
+                ASSS_TRY(arnoldi_orth(h->ctx, kw.ao, kw.V.p, kw.w.p, n, j, kw.m, kw.H.p, kw.cs.p, kw.sn.p, kw.g.p,
+                                      kw.hv.p, kw.hv2.p, kw.T.p + 2, kw.T.p + 3, thr[t], kw.stop.p));
+                int* hi = reinterpret_cast<int*>(kw.hpin + 2);
+                hi[0] = 0;
+                hi[2] = 0;
+                ASSS_CUDA(cudaMemcpyAsync(hi, kw.ao.err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+                ASSS_CUDA(cudaMemcpyAsync(hi + 2, kw.stop.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+            }
+            ASSS_CUDA(cudaStreamSynchronize(s));
+            for (int q = 0; q < nl; ++q) {
+                const int t = lc[q];
+                KrylovWork& kw = *h->kwb[t];
+                const int* hi = reinterpret_cast<const int*>(kw.hpin + 2);
+                if (hi[0]) {
+                    kw.ao.n = 0;
+                    set_error("a device wait in the Arnoldi step ran out (status %d)", hi[0]);
+                    return (asss_status)hi[0];
+                }
+                steps[t] = j + 1;
+                if (hi[2]) live[t] = 0;
+            }
+        }
+        for (int q = 0; q < nc; ++q) {
+            const int t = cols[q];
+            KrylovWork& kw = *h->kwb[t];
+            if (steps[t] > 0) {
+                k_fg_backsolve<<<1, 1, 0, s>>>(kw.H.p, kw.g.p, steps[t], kw.m, kw.y.p);
+                ASSS_CHECK_LAUNCH();
+                ASSS_TRY(colmajor_gemv(kw.Z.p, n, steps[t], kw.y.p, n, 0.0, dy[t], s));
+            }
+            st[t].outer_its += steps[t];
+            st[t].cycles += 1;
+            ASSS_TRY(vmul(h->t1.p, h->w.p, dy[t], n, s));  // x += D_c S W dy
+            ASSS_TRY(spmv(h->S, h->t1.p, h->t2.p, nullptr, s));
+            k_axpy_mul<<<nbk, 256, 0, s>>>(x[t], h->dc.p, h->t2.p, n);
+            ASSS_CHECK_LAUNCH();
+            ASSS_TRY(spmv(h->A, x[t], h->t1.p, nullptr, s));
+            k_sub<<<nbk, 256, 0, s>>>(rhs[t], h->t1.p, r[t], n);
+            ASSS_CHECK_LAUNCH();
+        }
+    }
+    for (int t = 0; t < nb; ++t) {
+        st[t].inner_its_total = its_sum;
+        st[t].inner_solves = launches;
+        st[t].inner_its_avg = launches ? (double)its_sum / launches : 0.0;
+        st[t].t_inner_ms = 0.0;
+        st[t].inner_bytes = 0;
+        st[t].inner_launches = 0;
+    }
+    return ASSS_OK;
+}
+
+// ---------------------------------------------------------------------------
 // set-up
 // ---------------------------------------------------------------------------
 static asss_status do_setup(asss_handle* h, const asss_csr* Ain, asss_stats* st) {
@@ -1462,6 +1747,59 @@ static asss_status solve_common(asss_handle* h, int tr, int nrhs, const double* 
     DBuf<double>& xx = h->xx;
     asss_stats lst = h->setup_stats;
     asss_status worst = ASSS_OK;
+    // several right-hand sides of a forward FGMRES solve: lockstep blocks of up to 8
+    // columns whose preconditioner applications share each pass over J~ and Q_k
+    const bool block = !tr && nrhs >= 2 && h->opt.outer == ASSS_OUTER_FGMRES && h->kp <= MRS_MULTI_KPMAX &&
+                       !h->Q16.p;
+    if (block) {
+        const int B = asss_handle::BLK;
+        if (!h->blk_b.p) {
+            ASSS_TRY(h->blk_b.alloc((int64_t)B * n));
+            ASSS_TRY(h->blk_x.alloc((int64_t)B * n));
+        }
+        long long its_all = 0;
+        int outer_max = 0, cycles = 0, solves = 0;
+        double relres_max = 0.0;
+        for (int j0 = 0; j0 < nrhs; j0 += B) {
+            const int nb = nrhs - j0 < B ? nrhs - j0 : B;
+            const double* bp[B];
+            double* xp[B];
+            for (int t = 0; t < nb; ++t) {
+                if (bdev) {
+                    bp[t] = b + (size_t)(j0 + t) * ldb;
+                } else {
+                    ASSS_CUDA(cudaMemcpyAsync(h->blk_b.p + (size_t)t * n, b + (size_t)(j0 + t) * ldb,
+                                              sizeof(double) * n, cudaMemcpyHostToDevice, s));
+                    bp[t] = h->blk_b.p + (size_t)t * n;
+                }
+                xp[t] = xdev ? x + (size_t)(j0 + t) * ldx : h->blk_x.p + (size_t)t * n;
+            }
+            asss_stats bst[B];
+            ASSS_TRY(refine_block(h, nb, bp, xp, bst));
+            for (int t = 0; t < nb; ++t) {
+                if (!xdev)
+                    ASSS_CUDA(cudaMemcpyAsync(x + (size_t)(j0 + t) * ldx, xp[t], sizeof(double) * n,
+                                              cudaMemcpyDeviceToHost, s));
+                if (bst[t].status != ASSS_OK && worst == ASSS_OK) worst = (asss_status)bst[t].status;
+                outer_max = std::max(outer_max, bst[t].outer_its);
+                cycles += bst[t].cycles;
+                relres_max = std::max(relres_max, bst[t].relres);
+            }
+            its_all += bst[0].inner_its_total;
+            solves += bst[0].inner_solves;
+            ASSS_CUDA(cudaStreamSynchronize(s));
+        }
+        lst.outer_its = outer_max;
+        lst.cycles = cycles;
+        lst.relres = relres_max;
+        lst.inner_its_total = its_all;
+        lst.inner_solves = solves;
+        lst.inner_its_avg = solves ? (double)its_all / solves : 0.0;
+        lst.t_inner_ms = 0.0;
+        lst.inner_bytes = 0;
+        lst.inner_launches = 0;
+        nrhs = 0;   // every column is done
+    }
     for (int j = 0; j < nrhs; ++j) {
         ASSS_CUDA(cudaMemcpyAsync(bb.p, b + (size_t)j * ldb, sizeof(double) * n,
                                   bdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));

@@ -114,6 +114,10 @@ constexpr int MRS_MULTI_KPMAX = 32;
 asss_status mrs_multi_solve(const Ctx& c, const MrsOperator& op, bool fp32, double shift, double sign, int ncol,
                             const double* B, long long ldb, double* X64, float* X32, long long ldx, double tol,
                             int maxit, int* its, double* ratio);
+// the same with one pointer per column (B[t], X64[t] or X32[t]: n values each)
+asss_status mrs_multi_solve_cols(const Ctx& c, const MrsOperator& op, bool fp32, double shift, double sign,
+                                 int ncol, const double* const* B, double* const* X64, float* const* X32, double tol,
+                                 int maxit, int* its, double* ratio);
 
 // matching.cu: maximum-product matching (auction, epsilon-scaling) and the dual
 // scalings of Eq. mc64; perm, dr, dc: device arrays of n entries (row i of Abar is

@@ -142,7 +142,7 @@ __global__ void k_lls_prec_setup(int nS, const int* srow, const int* sci, const 
     if (l != j) {
         int lo = srp[j], hi = srp[j + 1] - 1;
         while (lo <= hi) {
-            int mid = (lo + hi) >> 1;
+            int mid = lo + ((hi - lo) >> 1);   // no overflow for offsets near 2^31
             int c = sci[mid];
             if (c == l) {
                 p = mid;

@@ -74,7 +74,7 @@ __global__ void k_match_reset(int n, int* assigned, int* owner, unsigned long lo
 }
 
 __global__ void k_match_bid(const int* rp, const int* ci, const double* cost, int n, const double* price,
-                            const int* assigned, double eps, double big, double* bidval, int* bidcol,
+                            const int* assigned, double eps, double* bidval, int* bidcol,
                             unsigned long long* colbid) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -96,7 +96,12 @@ __global__ void k_match_bid(const int* rp, const int* ci, const double* cost, in
         }
     }
     if (j1 < 0) return;   // a row without finite entries: no perfect matching (caught by the round limit)
-    if (!(w2 > -INFINITY)) w2 = w1 - big;
+    // A row with one column has no second best.  Any bid of at least p + eps keeps
+    // eps-complementary slackness for it; bidding just that (rather than an "infinite"
+    // increment) keeps its column's price, and with it the range of the scalings, from
+    // growing with every epsilon phase: such prices reached e^130 in tests, and scalings
+    // that lopsided defeat the outer iteration in floating point.
+    if (!(w2 > -INFINITY)) w2 = w1;
     const double bid = price[j1] + (w1 - w2) + eps;
     bidval[i] = bid;
     bidcol[i] = j1;
@@ -206,8 +211,7 @@ asss_status matching_scaling(const Ctx& c, const DCsr& A, int* perm, double* dr,
     double cmaxv;
     memcpy(&cmaxv, &hcm, sizeof(cmaxv));
     const double scale = cmaxv > 1.0 ? cmaxv : 1.0;
-    const double big = cmaxv + 1.0;
-    const double eps_final = 1e-9 * scale;
+    const double eps_final = 1e-12 * scale;
     // rounds allowed in all (a structurally singular A never completes a phase)
     const long long max_rounds = 10000LL + 50LL * n;
     long long rounds = 0;
@@ -219,7 +223,7 @@ asss_status matching_scaling(const Ctx& c, const DCsr& A, int* perm, double* dr,
         while (true) {
             // several rounds between read-backs of the assigned count
             for (int r = 0; r < 8; ++r) {
-                k_match_bid<<<nb, 256, 0, s>>>(A.rp.p, A.ci.p, cost.p, n, price.p, assigned.p, eps, big, bidval.p,
+                k_match_bid<<<nb, 256, 0, s>>>(A.rp.p, A.ci.p, cost.p, n, price.p, assigned.p, eps, bidval.p,
                                                bidcol.p, colbid.p);
                 ASSS_CHECK_LAUNCH();
                 k_match_win<<<nb, 256, 0, s>>>(n, bidval.p, bidcol.p, colbid.p, colwin.p);

@@ -115,7 +115,7 @@ static __global__ void k_partition(const int* sptr, int nslices, int nblk, int* 
     long long target = wtot * b / nblk;
     int lo = 0, hi = nslices;
     while (lo < hi) {
-        int mid = (lo + hi) >> 1;
+        int mid = lo + ((hi - lo) >> 1);   // no overflow for offsets near 2^31
         long long w = (long long)sptr[mid] + (long long)mid * 256;
         if (w < target) lo = mid + 1;
         else hi = mid;

@@ -49,10 +49,8 @@ struct MultiParams {
     const double* alpha;      // k-1 values
     int k;
     double shift, sign;
-    const double* rhs;        // n x ncol column-major, leading dimension ldb
-    long long ldb;
-    T* x;                     // n x ncol column-major, leading dimension ldx
-    long long ldx;
+    const double* rhs[MM_R];  // column c of the right-hand side (n values, FP64)
+    T* x[MM_R];               // column c of the solution (n values)
     T* Y;                     // 3 slots, row 0 of slot 0 (halo rows before it)
     T* P;                     // 2 slots of n x MM_R
     double* part;             // [2][MM_R * (KP+1)][nblk]
@@ -180,11 +178,11 @@ __global__ void __launch_bounds__(MRS_THREADS, 1) k_mrs_multi(MultiParams<T> p) 
         const int i = base + rsub;
         if (i < r1) {
             const size_t e = (size_t)i * MM_R + c;
-            T b = colok ? (T)p.rhs[(size_t)c * p.ldb + i] : (T)0;
+            T b = colok ? (T)p.rhs[c][i] : (T)0;
             p.Y[e] = b;
             p.P[e] = (T)0;
             p.P[(size_t)n * MM_R + e] = (T)0;
-            if (colok) p.x[(size_t)c * p.ldx + i] = (T)0;
+            if (colok) p.x[c][i] = (T)0;
             tacc[0] += b * b;
             T q[KQ];
             load_qrow<T, KP>(p.Q, i, q, p.qcs != 0);
@@ -289,7 +287,7 @@ __global__ void __launch_bounds__(MRS_THREADS, 1) k_mrs_multi(MultiParams<T> p) 
             if (pd) {   // the p/x update of the previous step of this column
                 const T pv = (tnp * yold - tdpp * pold) * tthp;
                 Pj1[e] = pv;
-                p.x[(size_t)c * p.ldx + i] += txp * pv;
+                p.x[c][i] += txp * pv;
             }
         }
         if (finalpass) break;
@@ -408,8 +406,8 @@ static asss_status dispatch_multi(const Ctx& c, int kp, MultiParams<T>& prm, int
 
 template <class T>
 static asss_status multi_typed(const Ctx& c, const DSell<T>* sell, const DSkewDia<T>* dia, const T* Q, int kp,
-                               const double* alpha, int k, double shift, double sign, int ncol, const double* B,
-                               long long ldb, T* X, long long ldx, double tol, int maxit, int* its, double* ratio) {
+                               const double* alpha, int k, double shift, double sign, int ncol,
+                               const double* const* Bc, T* const* Xc, double tol, int maxit, int* its, double* ratio) {
     if (dia && dia->ndiag > MRS_MAXDIAG) dia = nullptr;
     if (!dia && !sell) {
         set_error("mrs: no operator storage");
@@ -456,8 +454,6 @@ static asss_status multi_typed(const Ctx& c, const DSell<T>* sell, const DSkewDi
     prm.k = k;
     prm.shift = shift;
     prm.sign = sign;
-    prm.ldb = ldb;
-    prm.ldx = ldx;
     prm.Y = Y.p + (size_t)H * MM_R;
     prm.P = P.p;
     prm.gb.count = bar.p;
@@ -474,8 +470,10 @@ static asss_status multi_typed(const Ctx& c, const DSell<T>* sell, const DSkewDi
     for (int c0 = 0; c0 < ncol; c0 += MM_R) {
         const int nc = ncol - c0 < MM_R ? ncol - c0 : MM_R;
         prm.ncol = nc;
-        prm.rhs = B + (size_t)c0 * ldb;
-        prm.x = X + (size_t)c0 * ldx;
+        for (int t = 0; t < MM_R; ++t) {
+            prm.rhs[t] = t < nc ? Bc[c0 + t] : nullptr;
+            prm.x[t] = t < nc ? Xc[c0 + t] : nullptr;
+        }
         if (dia) ASSS_TRY((dispatch_multi<T, 1>(c, kp, prm, nslices, blk, part, bar)));
         else ASSS_TRY((dispatch_multi<T, 0>(c, kp, prm, nslices, blk, part, bar)));
         int hi[MM_R];
@@ -497,9 +495,9 @@ static asss_status multi_typed(const Ctx& c, const DSell<T>* sell, const DSkewDi
     return ASSS_OK;
 }
 
-asss_status mrs_multi_solve(const Ctx& c, const MrsOperator& op, bool fp32, double shift, double sign, int ncol,
-                            const double* B, long long ldb, double* X64, float* X32, long long ldx, double tol,
-                            int maxit, int* its, double* ratio) {
+asss_status mrs_multi_solve_cols(const Ctx& c, const MrsOperator& op, bool fp32, double shift, double sign,
+                                 int ncol, const double* const* B, double* const* X64, float* const* X32, double tol,
+                                 int maxit, int* its, double* ratio) {
     NvtxRange nv_("asss:mrs-multi");
     if (ncol <= 0) return ASSS_OK;
     if (fp32) {
@@ -507,15 +505,30 @@ asss_status mrs_multi_solve(const Ctx& c, const MrsOperator& op, bool fp32, doub
             set_error("FP32 multi-column mrs needs the FP32 operator, FP32 Q and an FP32 output");
             return ASSS_ERR_ARG;
         }
-        return multi_typed<float>(c, op.J32, op.D32, op.Q32, op.kp, op.alpha, op.k, shift, sign, ncol, B, ldb, X32,
-                                  ldx, tol, maxit, its, ratio);
+        return multi_typed<float>(c, op.J32, op.D32, op.Q32, op.kp, op.alpha, op.k, shift, sign, ncol, B, X32, tol,
+                                  maxit, its, ratio);
     }
     if ((!op.J64 && !op.D64) || !X64) {
         set_error("FP64 multi-column mrs needs the FP64 operator and an FP64 output");
         return ASSS_ERR_ARG;
     }
-    return multi_typed<double>(c, op.J64, op.D64, op.Q64, op.kp, op.alpha, op.k, shift, sign, ncol, B, ldb, X64, ldx,
-                               tol, maxit, its, ratio);
+    return multi_typed<double>(c, op.J64, op.D64, op.Q64, op.kp, op.alpha, op.k, shift, sign, ncol, B, X64, tol,
+                               maxit, its, ratio);
+}
+
+asss_status mrs_multi_solve(const Ctx& c, const MrsOperator& op, bool fp32, double shift, double sign, int ncol,
+                            const double* B, long long ldb, double* X64, float* X32, long long ldx, double tol,
+                            int maxit, int* its, double* ratio) {
+    std::vector<const double*> bc(ncol);
+    std::vector<double*> x64(ncol, nullptr);
+    std::vector<float*> x32(ncol, nullptr);
+    for (int t = 0; t < ncol; ++t) {
+        bc[t] = B + (size_t)t * ldb;
+        if (X64) x64[t] = X64 + (size_t)t * ldx;
+        if (X32) x32[t] = X32 + (size_t)t * ldx;
+    }
+    return mrs_multi_solve_cols(c, op, fp32, shift, sign, ncol, bc.data(), X64 ? x64.data() : nullptr,
+                                X32 ? x32.data() : nullptr, tol, maxit, its, ratio);
 }
 
 }  // namespace asss

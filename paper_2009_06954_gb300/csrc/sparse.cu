@@ -430,7 +430,7 @@ __global__ void k_dia_fill(int n, const int* rp, const int* ci, const double* v,
         const int o = ci[e] - i;
         int lo = 0, hi = ndiag - 1;
         while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
+            const int mid = lo + ((hi - lo) >> 1);   // no overflow for offsets near 2^31
             if (off[mid] < o) lo = mid + 1;
             else hi = mid;
         }
@@ -688,7 +688,7 @@ __global__ void k_mirror(int n, const int* prp, const int* pci, int* mirror, int
         }
         int lo = prp[j], hi = prp[j + 1] - 1, f = -1;
         while (lo <= hi) {
-            int mid = (lo + hi) >> 1;
+            int mid = lo + ((hi - lo) >> 1);   // no overflow for offsets near 2^31
             int c = pci[mid];
             if (c == i) {
                 f = mid;
@@ -974,7 +974,7 @@ __global__ void k_skew_offsets(int n, const int* rp, const int* ci, const double
         // mirror entry
         int lo = rp[j], hi = rp[j + 1] - 1, f = -1;
         while (lo <= hi) {
-            int mid = (lo + hi) >> 1;
+            int mid = lo + ((hi - lo) >> 1);   // no overflow for offsets near 2^31
             int c = ci[mid];
             if (c == i) {
                 f = mid;
@@ -1005,7 +1005,7 @@ __global__ void k_fill_dia(int n, const int* rp, const int* ci, const double* v,
         int m = j - i;
         int lo = 0, hi = ndiag - 1;
         while (lo < hi) {
-            int mid = (lo + hi) >> 1;
+            int mid = lo + ((hi - lo) >> 1);   // no overflow for offsets near 2^31
             if (off[mid] < m) lo = mid + 1;
             else hi = mid;
         }

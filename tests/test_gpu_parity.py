@@ -744,3 +744,48 @@ def test_powerlaw_inner_operator_mrs_steps_match_oracle(pkg, precision):
     Xg, its_m, _ = pkg.mrs_multi(Jt, B, Q, alpha, tol=1e-14, maxit=5, precision=precision, fmt="sell")
     assert np.all(its_m == 5)
     np.testing.assert_allclose(Xg, Xo, rtol=0, atol=rtol * np.abs(Xo).max())
+
+
+# ----------------------------------------------------------------------------
+# several right-hand sides in one call: lockstep FGMRES blocks whose preconditioner
+# applications are one multi-column mrs launch (App. B) per Arnoldi step
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_block_solve_matches_single_solves_and_direct(pkg, precision):
+    A, b, _ = dissipative_hamiltonian_3d(side=16, seed=9)
+    n = A.shape[0]
+    rng = np.random.default_rng(61)
+    B = rng.standard_normal((n, 11))          # one block of 8 and one of 3
+    B[:, 4] = 0.0
+    B[:, 7] = 3.0 * B[:, 1]
+    s = pkg.Solver(A, precision=precision, outer="fgmres", inner_tol=1e-6 if precision == "mixed" else 1e-10)
+    X, st = s.solve(B)
+    assert st["status"] == 0 and st["inner_solves"] > 0
+    assert np.all(X[:, 4] == 0)
+    Xd = sp.linalg.splu(A.tocsc()).solve(B)
+    for c in range(B.shape[1]):
+        if c == 4:
+            continue
+        assert np.linalg.norm(B[:, c] - A @ X[:, c]) <= 1e-8 * np.linalg.norm(B[:, c])
+        np.testing.assert_allclose(X[:, c], Xd[:, c], rtol=0, atol=1e-7 * np.abs(Xd[:, c]).max())
+    np.testing.assert_allclose(X[:, 7], 3.0 * X[:, 1], rtol=0, atol=1e-7 * np.abs(X[:, 7]).max())
+    for c in (0, 9):                           # the same as a call with that column alone
+        x1, st1 = s.solve(B[:, c])
+        assert abs(st1["outer_its"] - st["outer_its"]) <= 3
+        np.testing.assert_allclose(X[:, c], x1, rtol=0, atol=1e-7 * np.abs(x1).max())
+    s.close()
+
+
+def test_block_solve_fp64_matches_oracle_cd64(pkg):
+    A, b, _ = convection_diffusion_2d(m=64)
+    rng = np.random.default_rng(62)
+    B = np.column_stack([b, rng.standard_normal(A.shape[0])])
+    o = O.AsssOracle(A, inner_tol=1e-10)
+    s = pkg.Solver(A, inner_tol=1e-10, outer="fgmres")
+    X, st = s.solve(B)
+    assert st["status"] == 0
+    for c in range(2):
+        xo, sto = o.solve(B[:, c], tol=1e-8, outer="fgmres")
+        assert np.linalg.norm(B[:, c] - A @ X[:, c]) <= 1e-8 * np.linalg.norm(B[:, c])
+        assert np.linalg.norm(X[:, c] - xo) <= 1e-5 * np.linalg.norm(xo)
+    s.close()
