@@ -355,6 +355,15 @@ def _traffic_record():
 # ----------------------------------------------------------------------------
 # multi-rank helpers (replicas: one independent solve stream per GPU)
 # ----------------------------------------------------------------------------
+def prof_range(args, start):
+    """cudaProfilerStart/Stop around the timed steps when asked (profilers that capture
+    only that range see exactly the benchmark's kernels)."""
+    if getattr(args, "cuda_profiler_range", False):
+        import torch
+        torch.cuda.synchronize()
+        (torch.cuda.profiler.start if start else torch.cuda.profiler.stop)()
+
+
 def rank_env():
     """(world, rank, local_rank) from the torchrun environment."""
     return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
@@ -416,6 +425,7 @@ def main_batched(args, world, rank, local):
     torch.cuda.synchronize()
     l0 = kernel_launches()
     stats = []
+    prof_range(args, True)
     with ClockSampler(dev.index) as clk:
         for _ in range(args.steps):
             flush.zero_()
@@ -423,6 +433,7 @@ def main_batched(args, world, rank, local):
             stats.append(st)
         torch.cuda.synchronize()
     launches = kernel_launches() - l0
+    prof_range(args, False)
     if dist:
         dist.barrier()
     total_ms = sum(s_["t_inner_ms"] for s_ in stats)
@@ -532,6 +543,7 @@ def main_adjoint(args, world, rank, local):
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     stats = []
     l0 = kernel_launches()
+    prof_range(args, True)
     with ClockSampler(dev.index) as clk:
         for k in range(args.steps):
             flush.zero_()
@@ -541,6 +553,7 @@ def main_adjoint(args, world, rank, local):
             stats.append(st)
         torch.cuda.synchronize()
     launches = kernel_launches() - l0
+    prof_range(args, False)
     if dist:
         dist.barrier()
     total_ms = sum(a.elapsed_time(c) for a, c in evs)
@@ -606,6 +619,133 @@ def main_adjoint(args, world, rank, local):
 
 
 # ----------------------------------------------------------------------------
+# many right-hand sides of the 100^3 system in one call (lockstep FGMRES blocks,
+# multi-column mrs): the SpMM form of the inner solve
+# ----------------------------------------------------------------------------
+MULTI_NRHS = 8
+
+
+def main_multi_rhs(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_2009_06954_gb300 as pkg
+    from paper_2009_06954_gb300.binding import kernel_launches
+    from workloads import dissipative_hamiltonian_3d
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    A, _, parts = dissipative_hamiltonian_3d(side=SIDE, seed=1)
+    n = A.shape[0]
+    t0 = time.perf_counter()
+    solver = pkg.Solver(A, precision="mixed", outer="fgmres", inner_tol=1e-6, outer_tol=1e-8, k=20,
+                        stream=stream.cuda_stream, rhs_block=True)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    R = MULTI_NRHS
+    Bh = np.asfortranarray(np.column_stack(_make_rhs(parts, n, 1 + rank, R)))
+    Bd = torch.tensor(Bh.T.copy(), device=dev).T          # n x R column-major on the device
+    Xd = torch.empty((R, n), dtype=torch.float64, device=dev).T
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        solver.solve(Bd, Xd)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    l0 = kernel_launches()
+    prof_range(args, True)
+    with ClockSampler(dev.index) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            _, st = solver.solve(Bd, Xd)
+            evs[k][1].record(stream)
+            stats.append(st)
+        torch.cuda.synchronize()
+    launches = kernel_launches() - l0
+    prof_range(args, False)
+    total_ms = sum(a.elapsed_time(c) for a, c in evs)
+    tmax = reduce_max(total_ms, dist, dev)
+    value = world * R * args.steps / (tmax / 1000.0)
+    X = Xd.cpu().numpy()
+    relres = max(float(np.linalg.norm(Bh[:, c] - A @ X[:, c]) / np.linalg.norm(Bh[:, c])) for c in range(R))
+    ok = all(s_["status"] == 0 for s_ in stats) and relres <= 1e-8
+    Bp = torch.from_numpy(Bh.T.copy()).pin_memory()
+    Xp = torch.empty((R, n), dtype=torch.float64).pin_memory()
+    e2e_s = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        solver.solve(Bp.T, Xp.T)
+        e2e_s += time.perf_counter() - t
+    e2e_val = world * R * args.steps / reduce_max(e2e_s, dist, dev)
+    # the same right-hand sides solved one after another (the default path), timed alike
+    solver.close()
+    s1 = pkg.Solver(A, precision="mixed", outer="fgmres", inner_tol=1e-6, outer_tol=1e-8, k=20,
+                    stream=stream.cuda_stream)
+    for _ in range(args.warmup):
+        s1.solve(Bd, Xd)
+    torch.cuda.synchronize()
+    e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    seq_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e_a.record(stream)
+        s1.solve(Bd, Xd)
+        e_b.record(stream)
+        torch.cuda.synchronize()
+        seq_ms += e_a.elapsed_time(e_b)
+    s1.close()
+    seq_val = world * R * args.steps / (reduce_max(seq_ms, dist, dev) / 1000.0)
+    inner_ms = sum(s_["t_inner_ms"] for s_ in stats)
+    inner_bytes = sum(s_["inner_bytes"] for s_ in stats)
+    inner_launches = sum(s_["inner_launches"] for s_ in stats)
+    peak, peak_kind = _peaks()
+    achieved = inner_bytes / (inner_ms / 1000.0) / 1e9 if inner_ms > 0 else 0.0
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32-inner/f64-outer", "data": "synthetic",
+        "config": {"workload": (f"dh3d_100_rhs{R}: the dh3d_100 system with {R} right-hand sides per call "
+                                f"(lockstep FGMRES, one multi-column FP32 mrs launch per Arnoldi step)"),
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "256 MB buffer written between steps (not timed); working set > L2",
+                   "setup_s": round(t_setup, 3), "rhs_per_call": R, "outer_its_max": stats[-1]["outer_its"],
+                   "inner_its_avg": round(stats[-1]["inner_its_avg"], 2), "max_relres": relres, "converged": ok,
+                   "one_after_another_solves_per_s": seq_val},
+        "gpu_launches": int(launches),
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 8 * n * R, "d2h_bytes_per_step": 8 * n * R},
+        "roofline": {"bound": "hbm", "kernel": "k_mrs_multi<float,20> (8 right-hand sides per launch)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak if peak else None,
+                     "peak_source": f"{peak_kind} hbm_gbs", "traffic": None,
+                     "algorithmic_bytes_per_launch": inner_bytes / max(inner_launches, 1),
+                     "bytes_model": "matrix and Q rows once per step for all columns, 28 B per live column",
+                     "avg_launch_ms": inner_ms / max(inner_launches, 1), "launches": inner_launches,
+                     "share_of_step": inner_ms / total_ms if total_ms else None},
+        "clocks": clk.summary(),
+        "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+    solver.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------
 # general power-law matrix: the SELL-C path at size (inner iterations/s)
 # ----------------------------------------------------------------------------
 def main_general(args, world, rank, local):
@@ -645,6 +785,7 @@ def main_general(args, world, rank, local):
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     stats = []
     l0 = kernel_launches()
+    prof_range(args, True)
     with ClockSampler(dev.index) as clk:
         for k in range(args.steps):
             flush.zero_()
@@ -654,6 +795,7 @@ def main_general(args, world, rank, local):
             stats.append(st)
         torch.cuda.synchronize()
     launches = kernel_launches() - l0
+    prof_range(args, False)
     total_ms = sum(a.elapsed_time(c) for a, c in evs)
     tmax = reduce_max(total_ms, dist, dev)
     inner_its = sum(s_["inner_its_total"] for s_ in stats)
@@ -795,12 +937,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--q-storage", default="f32", choices=["f32", "bf16"],
                     help="storage of the Lanczos basis read by the FP32 inner solve")
-    ap.add_argument("--workload", default="dh3d_100", choices=["dh3d_100", "batched_dh", "adjoint_dh64", "general_2e6"],
+    ap.add_argument("--workload", default="dh3d_100", choices=["dh3d_100", "batched_dh", "adjoint_dh64", "general_2e6", "dh3d_100_rhs8"],
                     help="dh3d_100: one 1e6-unknown system; batched_dh: 256 systems x 32 right-hand sides; "
                          "adjoint_dh64: gradients through the adjoint solve")
     ap.add_argument("--procs", type=int, default=0, help="(CPU worker) processes of the oracle pool")
     ap.add_argument("--xout", default="", help="(CPU worker) where to save the oracle's x of the first rhs")
     ap.add_argument("--no-fp64-leg", action="store_true", help="skip the FP64-GPU comparison solve")
+    ap.add_argument("--cuda-profiler-range", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--general-n", type=int, default=GENERAL["n"], help="rows of the general_2e6 workload")
     ap.add_argument("--batch-count", type=int, default=BATCH["count"],
                     help="systems in the batched workload (smaller counts for profiling captures)")
@@ -826,6 +970,9 @@ def main():
         return
     if args.workload == "general_2e6" and args.impl != "reference":
         main_general(args, world, rank, local)
+        return
+    if args.workload == "dh3d_100_rhs8" and args.impl != "reference":
+        main_multi_rhs(args, world, rank, local)
         return
 
     if args.impl == "reference":
@@ -874,6 +1021,7 @@ def main():
     torch.cuda.synchronize()
     l0 = kernel_launches()
     print(f"[bench] kernel launches before the timed region: {l0}", file=sys.stderr, flush=True)
+    prof_range(args, True)
     with ClockSampler(dev.index) as clk:
         for s in range(args.steps):
             flush.zero_()
@@ -883,6 +1031,7 @@ def main():
             stats.append(st)
         torch.cuda.synchronize()
     launches = kernel_launches() - l0
+    prof_range(args, False)
     if dist:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in evs]

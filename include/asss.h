@@ -109,6 +109,10 @@ typedef struct {
                                  or ASSS_SCALING_MATCHING (maximum-product matching and its dual
                                  scalings, the role of MC64 in §2: |diag| = 1, other entries
                                  <= 1 up to a relative 1e-12 * max(1, max cost))                */
+    int    rhs_block;         /* 1: asss_solve with several right-hand sides (FGMRES, k <= 32, FP32 Q)
+                                 runs them in lockstep blocks of up to 8 whose preconditioner
+                                 applications are one multi-column mrs launch per Arnoldi step
+                                 (App. B's simultaneous iterations); 0: one column after another */
 } asss_options;
 
 enum { ASSS_SCALING_MAXES = 0, ASSS_SCALING_MATCHING = 1 };

@@ -48,7 +48,7 @@ class Options(C.Structure):
                 ("seed", C.c_uint64), ("lls_tol", C.c_double), ("lls_maxit", C.c_int),
                 ("zero_tol", C.c_double), ("wait_timeout_ms", C.c_double), ("stream", C.c_void_p),
                 ("inner_format", C.c_int), ("q_bf16", C.c_int), ("s_values", C.c_void_p),
-                ("scaling", C.c_int)]
+                ("scaling", C.c_int), ("rhs_block", C.c_int)]
 
 FORMATS = {"auto": 0, "sell": 1, "diag": 2}
 SCALINGS = {"maxes": 0, "matching": 1}
@@ -235,7 +235,7 @@ def _options(keep, **kw):
     for key, val in kw.items():
         if val is None:
             continue
-        if key in ("reorth", "q_bf16"):
+        if key in ("reorth", "q_bf16", "rhs_block"):
             val = int(bool(val))
         setattr(o, key, val)
     return o
@@ -251,7 +251,8 @@ class Solver:
     ('fp64' | 'mixed'), outer ('tfqmr' | 'fgmres'), gamma, k, reorth, s_pattern,
     inner_tol, setup_tol, outer_tol, inner_maxit, outer_maxit, restart, r_max,
     seed, lls_tol, lls_maxit, zero_tol, wait_timeout_ms, row_perm, dr, dc, stream, s_values,
-    scaling ('maxes' | 'matching': how Eq. mc64's P, D_r, D_c are found when none is given)
+    scaling ('maxes' | 'matching': how Eq. mc64's P, D_r, D_c are found when none is given),
+    rhs_block (several right-hand sides in lockstep blocks sharing multi-column mrs launches)
     (saved S values to resume the set-up from, e.g. ``export(nnz)["s_val"]`` of an
     earlier solver for the same matrix).
     """

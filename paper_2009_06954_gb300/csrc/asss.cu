@@ -564,6 +564,7 @@ static void fill_defaults(asss_options* o) {
     o->q_bf16 = 0;
     o->s_values = nullptr;
     o->scaling = ASSS_SCALING_MAXES;
+    o->rhs_block = 0;
 }
 
 static int pick_kp(int k) {
@@ -1125,7 +1126,7 @@ __global__ void k_gather_col(const double* G, int ldg, int col, int k, double* o
 // out_c = P^-1 u_c (tr = 0) or P^-T u_c for the columns listed (Eq. smw around one
 // multi-column mrs launch per 8 columns)
 static asss_status apply_prec_block(asss_handle* h, int tr, int nc, const double* const* u, double* const* out,
-                                    long long* its_sum, int* launches) {
+                                    long long* its_sum, int* launches, MrsTotals* tot) {
     NvtxRange nv_("asss:preconditioner-block");
     const Ctx& c = h->ctx;
     cudaStream_t s = c.stream;
@@ -1155,14 +1156,14 @@ static asss_status apply_prec_block(asss_handle* h, int tr, int nc, const double
     }
     if (fp32) {
         ASSS_TRY(mrs_multi_solve_cols(c, op, true, 1.0, sign, nc, u, nullptr, z32, h->opt.inner_tol,
-                                      h->opt.inner_maxit, its, ratio));
+                                      h->opt.inner_maxit, its, ratio, tot));
         for (int t = 0; t < nc; ++t) {
             k_f2d<<<cdiv(n, 256), 256, 0, s>>>(z32[t], z64[t], n);
             ASSS_CHECK_LAUNCH();
         }
     } else {
         ASSS_TRY(mrs_multi_solve_cols(c, op, false, 1.0, sign, nc, u, z64, nullptr, h->opt.inner_tol,
-                                      h->opt.inner_maxit, its, ratio));
+                                      h->opt.inner_maxit, its, ratio, tot));
     }
     for (int t = 0; t < nc; ++t) *its_sum += its[t];
     *launches += nc;
@@ -1229,6 +1230,7 @@ static asss_status refine_block(asss_handle* h, int nb, const double* const* rhs
     int stall[B], active[B];
     long long its_sum = 0;
     int launches = 0;
+    MrsTotals mt;
     int* perm = h->has_perm ? h->perm.p : nullptr;
     for (int t = 0; t < nb; ++t) {
         r[t] = h->blk_r.p + (size_t)t * n;
@@ -1331,7 +1333,7 @@ static asss_status refine_block(asss_handle* h, int nb, const double* const* rhs
                 uin[q] = kw.V.p + (size_t)j * n;
                 zout[q] = kw.Z.p + (size_t)j * n;
             }
-            ASSS_TRY(apply_prec_block(h, 0, nl, uin, zout, &its_sum, &launches));
+            ASSS_TRY(apply_prec_block(h, 0, nl, uin, zout, &its_sum, &launches, &mt));
             for (int q = 0; q < nl; ++q) {
                 const int t = lc[q];
                 KrylovWork& kw = *h->kwb[t];
@@ -1381,9 +1383,9 @@ static asss_status refine_block(asss_handle* h, int nb, const double* const* rhs
         st[t].inner_its_total = its_sum;
         st[t].inner_solves = launches;
         st[t].inner_its_avg = launches ? (double)its_sum / launches : 0.0;
-        st[t].t_inner_ms = 0.0;
-        st[t].inner_bytes = 0;
-        st[t].inner_launches = 0;
+        st[t].t_inner_ms = mt.ms;
+        st[t].inner_bytes = mt.bytes;
+        st[t].inner_launches = mt.launches;
     }
     return ASSS_OK;
 }
@@ -1749,16 +1751,17 @@ static asss_status solve_common(asss_handle* h, int tr, int nrhs, const double* 
     asss_status worst = ASSS_OK;
     // several right-hand sides of a forward FGMRES solve: lockstep blocks of up to 8
     // columns whose preconditioner applications share each pass over J~ and Q_k
-    const bool block = !tr && nrhs >= 2 && h->opt.outer == ASSS_OUTER_FGMRES && h->kp <= MRS_MULTI_KPMAX &&
-                       !h->Q16.p;
+    const bool block = h->opt.rhs_block && !tr && nrhs >= 2 && h->opt.outer == ASSS_OUTER_FGMRES &&
+                       h->kp <= MRS_MULTI_KPMAX && !h->Q16.p;
     if (block) {
         const int B = asss_handle::BLK;
         if (!h->blk_b.p) {
             ASSS_TRY(h->blk_b.alloc((int64_t)B * n));
             ASSS_TRY(h->blk_x.alloc((int64_t)B * n));
         }
-        long long its_all = 0;
-        int outer_max = 0, cycles = 0, solves = 0;
+        long long its_all = 0, bytes_all = 0;
+        int outer_max = 0, cycles = 0, solves = 0, mlaunch = 0;
+        double ms_all = 0.0;
         double relres_max = 0.0;
         for (int j0 = 0; j0 < nrhs; j0 += B) {
             const int nb = nrhs - j0 < B ? nrhs - j0 : B;
@@ -1787,6 +1790,9 @@ static asss_status solve_common(asss_handle* h, int tr, int nrhs, const double* 
             }
             its_all += bst[0].inner_its_total;
             solves += bst[0].inner_solves;
+            ms_all += bst[0].t_inner_ms;
+            bytes_all += bst[0].inner_bytes;
+            mlaunch += bst[0].inner_launches;
             ASSS_CUDA(cudaStreamSynchronize(s));
         }
         lst.outer_its = outer_max;
@@ -1795,9 +1801,9 @@ static asss_status solve_common(asss_handle* h, int tr, int nrhs, const double* 
         lst.inner_its_total = its_all;
         lst.inner_solves = solves;
         lst.inner_its_avg = solves ? (double)its_all / solves : 0.0;
-        lst.t_inner_ms = 0.0;
-        lst.inner_bytes = 0;
-        lst.inner_launches = 0;
+        lst.t_inner_ms = ms_all;          // the multi-column mrs launches
+        lst.inner_bytes = bytes_all;
+        lst.inner_launches = mlaunch;
         nrhs = 0;   // every column is done
     }
     for (int j = 0; j < nrhs; ++j) {

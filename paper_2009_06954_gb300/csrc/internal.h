@@ -117,7 +117,7 @@ asss_status mrs_multi_solve(const Ctx& c, const MrsOperator& op, bool fp32, doub
 // the same with one pointer per column (B[t], X64[t] or X32[t]: n values each)
 asss_status mrs_multi_solve_cols(const Ctx& c, const MrsOperator& op, bool fp32, double shift, double sign,
                                  int ncol, const double* const* B, double* const* X64, float* const* X32, double tol,
-                                 int maxit, int* its, double* ratio);
+                                 int maxit, int* its, double* ratio, MrsTotals* tot = nullptr);
 
 // matching.cu: maximum-product matching (auction, epsilon-scaling) and the dual
 // scalings of Eq. mc64; perm, dr, dc: device arrays of n entries (row i of Abar is

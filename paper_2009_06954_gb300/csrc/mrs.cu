@@ -18,6 +18,7 @@
 // iteration, which keeps the method's one-synchronisation-per-step property (§3.1).
 // Vectors produced by other blocks are read through L2 (ld.global.cg); the grid
 // barrier has a bounded wait.
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -358,7 +359,6 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
         }
     };
     unsigned phase = 0;  // grid barriers passed in this launch
-
     // ---- phase 0: y_1 = b, x = 0, p = 0, ||b||^2 and Q^T b ----
     T tacc[NV];
 #pragma unroll
@@ -484,8 +484,39 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
                 const int width = (__ldg(&p.sptr[sl + 1]) - base) >> 5;
                 const int* cp = p.col + base + lane;
                 const T* vp = p.val + base + lane;
-#pragma unroll 4
-                for (int kk = 0; kk < width; ++kk) acc += __ldg(vp + kk * 32) * Ycur[__ldg(cp + kk * 32)];
+                // Sixteen entries in flight per lane (the gathers depend on the column
+                // loads, so the depth of the batch is the latency hiding); when the
+                // matrix exceeds L2 its entries are loaded evict-first, so the gathered
+                // vector stays in L2 while the matrix streams past it.
+                constexpr int UB = 16;
+                int kk = 0;
+                if (p.qcs) {
+                    for (; kk + UB <= width; kk += UB) {
+                        int cc[UB];
+                        T vv[UB];
+#pragma unroll
+                        for (int u = 0; u < UB; ++u) {
+                            cc[u] = __ldcs(cp + (kk + u) * 32);
+                            vv[u] = __ldcs(vp + (kk + u) * 32);
+                        }
+#pragma unroll
+                        for (int u = 0; u < UB; ++u) acc += vv[u] * Ycur[cc[u]];
+                    }
+                    for (; kk < width; ++kk) acc += __ldcs(vp + kk * 32) * Ycur[__ldcs(cp + kk * 32)];
+                } else {
+                    for (; kk + UB <= width; kk += UB) {
+                        int cc[UB];
+                        T vv[UB];
+#pragma unroll
+                        for (int u = 0; u < UB; ++u) {
+                            cc[u] = __ldg(cp + (kk + u) * 32);
+                            vv[u] = __ldg(vp + (kk + u) * 32);
+                        }
+#pragma unroll
+                        for (int u = 0; u < UB; ++u) acc += vv[u] * Ycur[cc[u]];
+                    }
+                    for (; kk < width; ++kk) acc += __ldg(vp + kk * 32) * Ycur[__ldg(cp + kk * 32)];
+                }
             } else {
                 // (J~ y)_i = sum_d U_d[i] y[i + m_d] - U_d[i - m_d] y[i - m_d]; zero halos on
                 // both U (front) and y (both ends) make the loop branch-free

@@ -407,7 +407,8 @@ static asss_status dispatch_multi(const Ctx& c, int kp, MultiParams<T>& prm, int
 template <class T>
 static asss_status multi_typed(const Ctx& c, const DSell<T>* sell, const DSkewDia<T>* dia, const T* Q, int kp,
                                const double* alpha, int k, double shift, double sign, int ncol,
-                               const double* const* Bc, T* const* Xc, double tol, int maxit, int* its, double* ratio) {
+                               const double* const* Bc, T* const* Xc, double tol, int maxit, int* its, double* ratio,
+                               MrsTotals* tot) {
     if (dia && dia->ndiag > MRS_MAXDIAG) dia = nullptr;
     if (!dia && !sell) {
         set_error("mrs: no operator storage");
@@ -467,6 +468,23 @@ static asss_status multi_typed(const Ctx& c, const DSell<T>* sell, const DSkewDi
     prm.qcs = stream_evict_first(c, nnz * (long long)sizeof(T) + (long long)n * (qrow + 7LL * sizeof(T) * MM_R)) ? 1
                                                                                                                   : 0;
     const int nslices = cdiv(n, 32);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (tot) {
+        ASSS_CUDA(cudaEventCreate(&e0));
+        ASSS_CUDA(cudaEventCreate(&e1));
+    }
+    struct EvGuard {
+        cudaEvent_t a, b;
+        ~EvGuard() {
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+        }
+    } evg{e0, e1};
+    // algorithmic bytes: the matrix entries (with their column index in SELL) and the Q
+    // row are read once per step for all columns; each live column reads and writes its
+    // own vectors (gathered y, y_old, y_new, p r/w, x r/w); set-up and final passes
+    const long long Tb = (long long)sizeof(T);
+    const long long per_entry = dia ? Tb : Tb + 4;
     for (int c0 = 0; c0 < ncol; c0 += MM_R) {
         const int nc = ncol - c0 < MM_R ? ncol - c0 : MM_R;
         prm.ncol = nc;
@@ -474,8 +492,10 @@ static asss_status multi_typed(const Ctx& c, const DSell<T>* sell, const DSkewDi
             prm.rhs[t] = t < nc ? Bc[c0 + t] : nullptr;
             prm.x[t] = t < nc ? Xc[c0 + t] : nullptr;
         }
+        if (tot) ASSS_CUDA(cudaEventRecord(e0, s));
         if (dia) ASSS_TRY((dispatch_multi<T, 1>(c, kp, prm, nslices, blk, part, bar)));
         else ASSS_TRY((dispatch_multi<T, 0>(c, kp, prm, nslices, blk, part, bar)));
+        if (tot) ASSS_CUDA(cudaEventRecord(e1, s));
         int hi[MM_R];
         double hr[MM_R];
         int herr = 0;
@@ -491,13 +511,29 @@ static asss_status multi_typed(const Ctx& c, const DSell<T>* sell, const DSkewDi
             if (its) its[c0 + t] = hi[t];
             if (ratio) ratio[c0 + t] = hr[t];
         }
+        if (tot) {
+            float ms = 0.f;
+            ASSS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            long long sum_its = 0, max_its = 0;
+            for (int t = 0; t < nc; ++t) {
+                sum_its += hi[t];
+                max_its = hi[t] > max_its ? hi[t] : max_its;
+            }
+            tot->ms += ms;
+            tot->launches += 1;
+            tot->its += sum_its;
+            tot->bytes += (long long)n * (qrow + nc * (8 + 4 * Tb)) +                 // set-up pass
+                          max_its * (nnz * per_entry + (long long)n * qrow) +         // shared per step
+                          sum_its * (long long)n * 7 * Tb +                           // per column and step
+                          (long long)n * nc * 4 * Tb;                                 // final updates
+        }
     }
     return ASSS_OK;
 }
 
 asss_status mrs_multi_solve_cols(const Ctx& c, const MrsOperator& op, bool fp32, double shift, double sign,
                                  int ncol, const double* const* B, double* const* X64, float* const* X32, double tol,
-                                 int maxit, int* its, double* ratio) {
+                                 int maxit, int* its, double* ratio, MrsTotals* tot) {
     NvtxRange nv_("asss:mrs-multi");
     if (ncol <= 0) return ASSS_OK;
     if (fp32) {
@@ -506,14 +542,14 @@ asss_status mrs_multi_solve_cols(const Ctx& c, const MrsOperator& op, bool fp32,
             return ASSS_ERR_ARG;
         }
         return multi_typed<float>(c, op.J32, op.D32, op.Q32, op.kp, op.alpha, op.k, shift, sign, ncol, B, X32, tol,
-                                  maxit, its, ratio);
+                                  maxit, its, ratio, tot);
     }
     if ((!op.J64 && !op.D64) || !X64) {
         set_error("FP64 multi-column mrs needs the FP64 operator and an FP64 output");
         return ASSS_ERR_ARG;
     }
     return multi_typed<double>(c, op.J64, op.D64, op.Q64, op.kp, op.alpha, op.k, shift, sign, ncol, B, X64, tol,
-                               maxit, its, ratio);
+                               maxit, its, ratio, tot);
 }
 
 asss_status mrs_multi_solve(const Ctx& c, const MrsOperator& op, bool fp32, double shift, double sign, int ncol,
@@ -528,7 +564,7 @@ asss_status mrs_multi_solve(const Ctx& c, const MrsOperator& op, bool fp32, doub
         if (X32) x32[t] = X32 + (size_t)t * ldx;
     }
     return mrs_multi_solve_cols(c, op, fp32, shift, sign, ncol, bc.data(), X64 ? x64.data() : nullptr,
-                                X32 ? x32.data() : nullptr, tol, maxit, its, ratio);
+                                X32 ? x32.data() : nullptr, tol, maxit, its, ratio, nullptr);
 }
 
 }  // namespace asss

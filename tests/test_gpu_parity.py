@@ -758,7 +758,8 @@ def test_block_solve_matches_single_solves_and_direct(pkg, precision):
     B = rng.standard_normal((n, 11))          # one block of 8 and one of 3
     B[:, 4] = 0.0
     B[:, 7] = 3.0 * B[:, 1]
-    s = pkg.Solver(A, precision=precision, outer="fgmres", inner_tol=1e-6 if precision == "mixed" else 1e-10)
+    s = pkg.Solver(A, precision=precision, outer="fgmres", inner_tol=1e-6 if precision == "mixed" else 1e-10,
+                   rhs_block=True)
     X, st = s.solve(B)
     assert st["status"] == 0 and st["inner_solves"] > 0
     assert np.all(X[:, 4] == 0)
@@ -781,7 +782,7 @@ def test_block_solve_fp64_matches_oracle_cd64(pkg):
     rng = np.random.default_rng(62)
     B = np.column_stack([b, rng.standard_normal(A.shape[0])])
     o = O.AsssOracle(A, inner_tol=1e-10)
-    s = pkg.Solver(A, inner_tol=1e-10, outer="fgmres")
+    s = pkg.Solver(A, inner_tol=1e-10, outer="fgmres", rhs_block=True)
     X, st = s.solve(B)
     assert st["status"] == 0
     for c in range(2):
