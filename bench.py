@@ -71,67 +71,102 @@ def _make_rhs(A_parts, n, seed, count):
 # ----------------------------------------------------------------------------
 # CPU oracle baseline (subprocess, one thread)
 # ----------------------------------------------------------------------------
-def batched_worker(budget_s):
-    """Oracle solves of a bounded sample of the batched workload's items."""
-    import numpy as np
+def _barrier_pool(procs, target, args_of):
+    """Run target(rank, barrier, queue, *args_of(rank)) in `procs` forked processes
+    (CPU only; this process never touches the GPU).  Every process does its untimed
+    set-up, waits at the barrier, then does its timed work; returns the results and the
+    wall time from the barrier's release until the last process finished."""
+    import multiprocessing as mp
+    ctx = mp.get_context("fork")
+    barrier = ctx.Barrier(procs + 1)
+    q = ctx.Queue()
+    ps = [ctx.Process(target=target, args=(r, barrier, q) + tuple(args_of(r))) for r in range(procs)]
+    for p_ in ps:
+        p_.start()
+    barrier.wait()
+    t0 = time.perf_counter()
+    res = [q.get() for _ in range(procs)]
+    wall = time.perf_counter() - t0
+    for p_ in ps:
+        p_.join()
+    return res, wall
 
+
+def _batched_proc(rank, barrier, q, mats, budget_s):
     import oracle
-    from workloads import batched_dissipative_hamiltonian
-    batch = batched_dissipative_hamiltonian(**BATCH)
-    order = np.argsort([A.shape[0] for A, _ in batch])
-    solves, secs, rows, t_setup, relres = 0, 0.0, 0, 0.0, 0.0
-    t_start = time.perf_counter()
-    for m in order[::max(1, len(order) // 16)]:
-        A, B = batch[m]
-        t0 = time.perf_counter()
+    setups = []
+    for A, B in mats:
         o = oracle.AsssOracle(A, inner_tol=1e-6)
         o._smw(False)   # the SMW data the oracle would otherwise build inside the first solve
-        t_setup += time.perf_counter() - t0
+        setups.append((o, A, B))
+    barrier.wait()
+    solves, rows, relres = 0, 0, 0.0
+    t0 = time.perf_counter()
+    for o, A, B in setups:
         for c in range(2):
-            t = time.perf_counter()
             _, st = o.solve(B[:, c], tol=1e-8, outer="fgmres")
-            secs += time.perf_counter() - t
             solves += 1
             rows += A.shape[0]
             relres = max(relres, st["relres"])
-        if time.perf_counter() - t_start > budget_s:
+        if time.perf_counter() - t0 > budget_s:
             break
-    print(json.dumps({"solves": solves, "seconds": secs, "rows": rows, "t_setup_s": t_setup,
-                      "max_relres": relres}))
+    q.put((solves, rows, relres, time.perf_counter() - t0))
 
 
-def adjoint_worker(budget_s):
-    """Oracle gradients (forward solve untimed, adjoint solve timed) at 24^3."""
+def batched_worker(budget_s, procs):
+    """Oracle solves of a bounded sample of the batched workload's items, on all host
+    cores: the sampled matrices (every 8th by size) are dealt to the processes, each
+    sets its share up (untimed), then all solve two columns per matrix at once."""
+    import numpy as np
+
+    from workloads import batched_dissipative_hamiltonian
+    batch = batched_dissipative_hamiltonian(**BATCH)
+    order = np.argsort([A.shape[0] for A, _ in batch])
+    sample = [batch[m] for m in order[::max(1, len(order) // 32)]]
+    res, wall = _barrier_pool(procs, _batched_proc, lambda r: (sample[r::procs], budget_s))
+    solves = sum(r[0] for r in res)
+    rows = sum(r[1] for r in res)
+    print(json.dumps({"solves": solves, "seconds": wall, "rows": rows, "procs": procs,
+                      "matrices": len(sample), "max_relres": max(r[2] for r in res)}))
+
+
+def _adjoint_proc(rank, barrier, q, budget_s):
     import numpy as np
 
     import oracle
     from workloads import dissipative_hamiltonian_3d
     A, b, _ = dissipative_hamiltonian_3d(side=ADJ_CPU_SIDE, seed=4)
     n = A.shape[0]
-    t0 = time.perf_counter()
     o = oracle.AsssOracle(A, inner_tol=1e-6)
-    t_setup = time.perf_counter() - t0
     x, _ = o.solve(b, tol=1e-8, outer="fgmres")
     o._smw(True)        # the transposed SMW data (set-up of the adjoint), outside the timed solves
-    xs = np.random.default_rng(44).standard_normal(n)
-    g = 2.0 * (x - xs)
-    times = []
-    t_start = time.perf_counter()
+    g = 2.0 * (x - np.random.default_rng(44).standard_normal(n))
+    barrier.wait()
+    cnt = 0
+    t0 = time.perf_counter()
     while True:
-        t = time.perf_counter()
-        lam, dA, st = o.solve_adjoint(g, x, tol=1e-8, outer="fgmres")
-        times.append(time.perf_counter() - t)
-        if time.perf_counter() - t_start > budget_s or len(times) >= 50:
+        o.solve_adjoint(g, x, tol=1e-8, outer="fgmres")
+        cnt += 1
+        if time.perf_counter() - t0 > budget_s or cnt >= 50:
             break
-    print(json.dumps({"n": n, "solves": len(times), "seconds": sum(times), "t_setup_s": t_setup}))
+    q.put((cnt, n))
+
+
+def adjoint_worker(budget_s, procs):
+    """Oracle gradients at ADJ_CPU_SIDE^3 (forward solve untimed, adjoint solve + dL/dA
+    timed), one oracle per host core, all at once."""
+    res, wall = _barrier_pool(procs, _adjoint_proc, lambda r: (budget_s,))
+    print(json.dumps({"n": res[0][1], "solves": sum(r[0] for r in res), "seconds": wall, "procs": procs,
+                      "t_setup_s": 0.0}))
 
 
 def run_adjoint_cpu_baseline(budget_s):
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[v] = "1"
+    procs = host_cores()
     cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", "--workload", "adjoint_dh64", "--budget",
-           str(budget_s)]
+           str(budget_s), "--procs", str(procs)]
     p = subprocess.run(cmd, capture_output=True, text=True, env=env, cwd=ROOT)
     if p.returncode != 0:
         raise RuntimeError("CPU baseline worker failed:\n" + p.stdout + p.stderr)
@@ -139,9 +174,10 @@ def run_adjoint_cpu_baseline(budget_s):
     n_full = ADJ_SIDE ** 3
     per_s = r["solves"] / r["seconds"]
     return {
-        "value": per_s * r["n"] / n_full, "unit": "gradients/s", "cores": 1, "kind": "oracle",
+        "value": per_s * r["n"] / n_full, "unit": "gradients/s", "cores": r["procs"], "kind": "oracle",
         "sample": (f"FP64 numpy/scipy oracle, adjoint solve + dL/dA at {ADJ_CPU_SIDE}^3 (n = {r['n']}), "
-                   f"{r['solves']} in {r['seconds']:.2f} s ({per_s:.3f}/s), scaled to n = {n_full} by unknowns; "
+                   f"{r['solves']} on {r['procs']} processes (one per host core, BLAS 1 thread) in "
+                   f"{r['seconds']:.2f} s wall ({per_s:.3f}/s), each counted as n_sample/n of a 64^3 gradient; "
                    f"set-up and the forward solve untimed"),
         "solves": r["solves"], "seconds": r["seconds"],
     }
@@ -159,8 +195,9 @@ def run_batched_cpu_baseline(budget_s, mean_n):
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[v] = "1"
+    procs = host_cores()
     cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", "--workload", "batched_dh", "--budget",
-           str(budget_s), "--batch-count", str(BATCH["count"])]
+           str(budget_s), "--batch-count", str(BATCH["count"]), "--procs", str(procs)]
     p = subprocess.run(cmd, capture_output=True, text=True, env=env, cwd=ROOT)
     if p.returncode != 0:
         raise RuntimeError("CPU baseline worker failed:\n" + p.stdout + p.stderr)
@@ -168,11 +205,11 @@ def run_batched_cpu_baseline(budget_s, mean_n):
     per_s = r["solves"] / r["seconds"]
     sample_n = r["rows"] / r["solves"]
     return {
-        "value": per_s * sample_n / mean_n, "unit": UNIT, "cores": 1, "kind": "oracle",
-        "sample": (f"FP64 numpy/scipy oracle, {r['solves']} solves (2 columns each of every 16th matrix of the "
-                   f"batch by size, mean n = {sample_n:.0f}) in {r['seconds']:.2f} s ({per_s:.3f} solves/s), "
-                   f"scaled to the batch's mean n = {mean_n:.0f} by unknowns; set-up {r['t_setup_s']:.1f} s "
-                   f"untimed"),
+        "value": per_s * sample_n / mean_n, "unit": UNIT, "cores": r["procs"], "kind": "oracle",
+        "sample": (f"FP64 numpy/scipy oracle, {r['solves']} solves (2 columns each of {r['matrices']} matrices, "
+                   f"every 8th of the batch by size, mean n = {sample_n:.0f}) on {r['procs']} processes (one per "
+                   f"host core, BLAS 1 thread) in {r['seconds']:.2f} s wall ({per_s:.3f} solves/s), each counted "
+                   f"as n_item / mean n = {mean_n:.0f} of an item; set-up untimed"),
         "max_relres": r["max_relres"], "solves": r["solves"], "seconds": r["seconds"],
     }
 
@@ -954,9 +991,9 @@ def main():
 
     if args.cpu_worker:
         if args.workload == "batched_dh":
-            batched_worker(args.budget)
+            batched_worker(args.budget, max(1, args.procs))
         elif args.workload == "adjoint_dh64":
-            adjoint_worker(args.budget)
+            adjoint_worker(args.budget, max(1, args.procs))
         else:
             cpu_worker(CPU_SAMPLE_SIDE, args.steps, args.warmup, args.budget, max(1, args.procs), args.xout)
         return

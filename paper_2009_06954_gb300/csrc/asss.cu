@@ -2235,12 +2235,13 @@ struct asss_batch {
 };
 
 static asss_status batch_view(asss_handle* h, BatchMat* v) {
-    if (!h->use_dia || !h->D32.n || h->opt.precision != ASSS_PREC_MIXED) {
-        set_error("batched solves need the mixed-precision path and skew-diagonal storage of J~");
+    const bool dia = h->use_dia && h->D32.n;
+    if (h->opt.precision != ASSS_PREC_MIXED || (!dia && !h->J32.n)) {
+        set_error("batched solves need the mixed-precision path (FP32 storage of J~)");
         return ASSS_ERR_UNSUPPORTED;
     }
     SmwData& S = h->smw[0];
-    if (!S.ready || (S.m > 0 && !S.Y32.p) || S.m > 320 || h->k > 32 || h->D32.ndiag > 64) {
+    if (!S.ready || (S.m > 0 && !S.Y32.p) || S.m > 320 || h->k > 32 || (dia && h->D32.ndiag > 64)) {
         set_error("batched solves support k <= 32, k + r <= 320 and at most 64 diagonals");
         return ASSS_ERR_UNSUPPORTED;
     }
@@ -2249,11 +2250,21 @@ static asss_status batch_view(asss_handle* h, BatchMat* v) {
     v->k = h->k;
     v->m = S.m;
     v->r = h->r;
-    v->ndiag = h->D32.ndiag;
-    v->halo = h->D32.halo;
-    v->ustride = h->D32.ustride;
-    v->off = h->D32.off.p;
-    v->U = h->D32.U.p + h->D32.halo;
+    if (dia) {
+        v->ndiag = h->D32.ndiag;
+        v->halo = h->D32.halo;
+        v->ustride = h->D32.ustride;
+        v->off = h->D32.off.p;
+        v->U = h->D32.U.p + h->D32.halo;
+    } else {   // general pattern: SELL-C-sigma
+        v->ndiag = 0;
+        v->halo = 0;
+        v->nslots = h->J32.nslices * 32;
+        v->sptr = h->J32.sptr.p;
+        v->scol = h->J32.col.p;
+        v->sval = h->J32.val.p;
+        v->rowmap = h->J32.rowmap.p;
+    }
     v->Q32 = h->Q32.p;
     v->Q16 = h->Q16.p;
     v->alpha = h->alpha_d.p;
@@ -2419,12 +2430,8 @@ asss_status asss_setup_batched(int nmat, const asss_csr* const* A, const asss_op
     else fill_defaults(&B->opt);
     B->opt.precision = ASSS_PREC_MIXED;
     B->opt.outer = ASSS_OUTER_FGMRES;
-    if (B->opt.inner_format == ASSS_FORMAT_SELL) {
-        delete B;
-        set_error("batched solves use the skew-diagonal storage");
-        return ASSS_ERR_UNSUPPORTED;
-    }
-    B->opt.inner_format = ASSS_FORMAT_DIAG;
+    // J~ of each matrix: skew diagonals when its pattern fits them, SELL-C-sigma otherwise
+    // (ASSS_FORMAT_AUTO), or as the options force
     B->restart = B->opt.restart > 0 ? (B->opt.restart < BATCH_RMAX ? B->opt.restart : BATCH_RMAX) : 20;
     asss_status s = make_ctx(B->ctx, B->opt.stream, B->opt.wait_timeout_ms);
     if (s == ASSS_OK && cudaStreamCreateWithFlags(&B->own, cudaStreamNonBlocking) != cudaSuccess) s = ASSS_ERR_CUDA;
@@ -2457,14 +2464,15 @@ asss_status asss_setup_batched(int nmat, const asss_csr* const* A, const asss_op
         // p and z read and written; per call the set-up and final passes
         {
             double nn = h->n, qrow = h->Q16.p ? 2.0 * h->kp16 : 4.0 * h->kp;
-            B->step_bytes.push_back(4.0 * (double)h->D32.nnz + nn * (28.0 + qrow));
+            const double mat = h->use_dia ? 4.0 * (double)h->D32.nnz : 8.0 * (double)h->J32.nnz;
+            B->step_bytes.push_back(mat + nn * (28.0 + qrow));
             B->call_bytes.push_back(nn * (8.0 + 16.0 + qrow) + nn * 16.0 + (h->k ? nn * qrow : 0.0));
         }
         B->n_of.push_back(h->n);
         B->off_h.push_back(rows);
         rows += h->n;
         if (h->n > B->n_max) B->n_max = h->n;
-        if (h->D32.halo > B->halo_max) B->halo_max = h->D32.halo;
+        if (h->use_dia && h->D32.halo > B->halo_max) B->halo_max = h->D32.halo;
     }
     if (s == ASSS_OK) {
         B->total_rows = rows;

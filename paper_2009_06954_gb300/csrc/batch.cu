@@ -318,15 +318,31 @@ __device__ int bmrs(const double* u, float* z, float* Y, long long ys, float* P,
                     txp = sh.cf[6];
 #pragma unroll
         for (int v = 0; v <= KP; ++v) tacc[v] = 0.f;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        // skew diagonals: one row per thread in natural order; SELL-C-sigma: one slot
+        // per thread (coalesced matrix reads), its row from the slot map
+        const bool sell = nd == 0;
+        const int nrun = sell ? M.nslots : n;
+        for (int s_ = threadIdx.x; s_ < nrun; s_ += blockDim.x) {
+            const int i = (sell && M.rowmap) ? M.rowmap[s_] : s_;
+            if (i >= n) continue;
             const float yold = j >= 2 ? Yold[i] : 0.f;
             const float pold = j >= 2 ? Pj1[i] : 0.f;
             float acc = 0.f;
-            const float* Ud = Ubase + i;
-            const float* yi = Ycur + i;
-            for (int d = 0; d < nd; ++d, Ud += ust) {
-                const int m = soff[d];
-                acc += __ldg(Ud) * yi[m] - __ldg(Ud - m) * yi[-m];
+            if (sell) {
+                const int sl = s_ >> 5, t = s_ & 31;
+                const int b0 = __ldg(&M.sptr[sl]);
+                const int width = (__ldg(&M.sptr[sl + 1]) - b0) >> 5;
+                const int* cp = M.scol + b0 + t;
+                const float* vp = M.sval + b0 + t;
+#pragma unroll 4
+                for (int kk = 0; kk < width; ++kk) acc += __ldg(vp + kk * 32) * Ycur[__ldg(cp + kk * 32)];
+            } else {
+                const float* Ud = Ubase + i;
+                const float* yi = Ycur + i;
+                for (int d = 0; d < nd; ++d, Ud += ust) {
+                    const int m = soff[d];
+                    acc += __ldg(Ud) * yi[m] - __ldg(Ud - m) * yi[-m];
+                }
             }
             float q[KP > 0 ? KP : 1];
             bq_row<KP, QB>(M, i, q);

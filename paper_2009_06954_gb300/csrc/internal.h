@@ -150,6 +150,12 @@ struct BatchMat {
     long long ustride;
     const int* off;  // ndiag offsets
     const float* U;  // J~ diagonals (FP32), diagonal d at U + d*ustride, entries [-halo, n)
+    // J~ in SELL-C-sigma (FP32) when it does not fit the diagonals (ndiag = 0 then)
+    int nslots;           // 32 * slices
+    const int* sptr;      // slice offsets
+    const int* scol;
+    const float* sval;
+    const int* rowmap;    // slot -> row (n for padding), or null for the identity
     const float* Q32;               // n x kp row-major (or null)
     const void* Q16;                // BF16 n x kp row-major (or null)
     const double* alpha;            // k-1

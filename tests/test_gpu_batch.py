@@ -156,3 +156,42 @@ def test_batched_bf16_basis_and_a_tiny_system(pkg, batch):
     assert st["status"] == 0
     assert np.linalg.norm(b - A @ x) <= 1e-8 * np.linalg.norm(b)
     bs.close()
+
+
+def test_batched_general_patterns_use_sell(pkg):
+    """Matrices whose J~ does not fit skew diagonals (general sparse patterns, power-law
+    rows) join the batch in SELL-C-sigma storage, next to stencil matrices in skew
+    diagonals; every item meets the tolerance and the exact solution."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(71)
+    mats = []
+    for n in (700, 1300, 2111):
+        K = sp.random(n, n, density=6.0 / n, random_state=rng, data_rvs=rng.standard_normal)
+        A = (K + sp.diags(4.0 + rng.random(n))).tocsr()
+        A.sum_duplicates()
+        A.sort_indices()
+        mats.append(A)
+    # a few long rows (heavy tail, so the SELL slices are sorted by length)
+    n = 1500
+    K = sp.random(n, n, density=5.0 / n, random_state=rng, data_rvs=rng.standard_normal).tolil()
+    for i in rng.choice(n, 12, replace=False):
+        cols = rng.choice(n, 300, replace=False)
+        K[i, cols] = 0.01 * rng.standard_normal(300)
+    A = (K.tocsr() + sp.diags(4.0 + rng.random(n))).tocsr()
+    A.sum_duplicates()
+    A.sort_indices()
+    mats.append(A)
+    mats.append(dissipative_hamiltonian_3d(side=9, seed=3)[0])
+    nrhs = 2
+    Bs = [rng.standard_normal((A.shape[0], nrhs)) for A in mats]
+    bs = pkg.BatchSolver(mats, inner_tol=1e-6, restart=24, outer_maxit=400)
+    x, st = bs.solve(bs.pack(Bs), nrhs=nrhs)
+    X = bs.unpack(x, nrhs)
+    for A, Xm, Bm in zip(mats, X, Bs):
+        xs = spla.splu(A.tocsc()).solve(Bm)
+        for c in range(nrhs):
+            r = np.linalg.norm(Bm[:, c] - A @ Xm[:, c]) / np.linalg.norm(Bm[:, c])
+            assert r <= 1e-8, r
+        assert np.linalg.norm(Xm - xs) <= 1e-6 * np.linalg.norm(xs)
+    assert st["status"] == 0
+    bs.close()
