@@ -118,7 +118,18 @@ struct DSell {
     DBuf<T> val;
     DBuf<int> rowmap; // 32 * nslices slots -> row (empty: identity)
     DBuf<int> rowpos; // n rows -> slot (empty: identity)
+    // Work units of a pass: a slice, or one part of SELL_SPLIT entries of a long slice
+    // (x slice, y part, z parts of that slice, w its accumulator or -1); uoff[s] is the
+    // first unit of slice s.  The parts of a long slice add their lanes' partial sums
+    // into hacc (32 values per long slice) and the last one to finish carries on.
+    int nunits = 0;
+    int nheavy = 0;
+    DBuf<int4> units;
+    DBuf<int> uoff;
+    DBuf<T> hacc;
+    DBuf<unsigned> hcnt;
 };
+constexpr int SELL_SPLIT = 1024;
 
 // Skew half-diagonal storage of an exactly skew matrix J whose entries lie on a
 // few diagonals (stencil-like patterns): only the diagonals with positive offset

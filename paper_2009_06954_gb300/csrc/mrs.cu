@@ -125,6 +125,10 @@ struct MrsParams {
     const int* col;
     const T* val;
     const int* rowmap;
+    const int4* units;   // SELL work units (slice, part, parts, accumulator) and their offsets per slice
+    const int* uoff;
+    T* hacc;             // partial sums of the parts of long slices (32 per long slice, left at 0)
+    unsigned* hcnt;      // parts finished per long slice (left at 0)
     // skew half-diagonal operator: U points at U_0[0]; diagonal d starts ustride later
     int ndiag;
     const int* off;
@@ -227,7 +231,7 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
     // 0 sign*nu, 1 sign, 2 beta_{j-1} nu_{j-1}, 3 nu_p, 4 delta_pp, 5 1/theta_p, 6 xcoef_p,
     // 7..10 the final pass: nu, delta, 1/theta, xcoef
     __shared__ T s_cf[12];
-    __shared__ int s_next;   // SELL: next slice of this block for the warp that asks (see next_slice)
+    __shared__ int s_next;   // SELL: next work unit of this block for the warp that asks (see next_slice)
     if constexpr (FMT == 1) {
         for (int d = threadIdx.x; d < p.ndiag; d += MRS_THREADS) s_off[d] = p.off[d];
     }
@@ -374,6 +378,9 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
         }
         return sl + MRS_WARPS;
     };
+    // SELL: the block's work units (its slices, long ones cut into parts)
+    const int u0 = FMT == 0 ? __ldg(&p.uoff[s0]) : s0;
+    const int u1 = FMT == 0 ? __ldg(&p.uoff[s1]) : s1;
     // the row held by lane `lane` of slice sl (SELL-C-sigma permutes rows within windows)
     auto row_of = [&](int sl) -> int {
         if constexpr (FMT == 0) {
@@ -425,7 +432,7 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
             sc.its = 0;
             sc.stop = r0 > zero ? 0 : 1;
             set_coefs();
-            s_next = s0 + MRS_WARPS;
+            s_next = u0 + MRS_WARPS;
         }
         __syncwarp();
         if (!sc.stop) make_u_warp0(sc.nu);
@@ -459,7 +466,15 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
         const T tnp = s_cf[3], tdpp = s_cf[4], tthp = s_cf[5], txp = s_cf[6];
 #pragma unroll
         for (int v = 0; v < NV; ++v) tacc[v] = (T)0;
-        for (int sl = s0 + warp; sl < s1; sl = next_slice(sl)) {
+        for (int uu = u0 + warp; uu < u1; uu = next_slice(uu)) {
+            int sl = uu, part = 0, nparts = 1, hix = -1;
+            if constexpr (FMT == 0) {
+                const int4 U = __ldg(&p.units[uu]);
+                sl = U.x;
+                part = U.y;
+                nparts = U.z;
+                hix = U.w;
+            }
             const int i = row_of(sl);
             const bool live = i < n;
             // this row's own data first (independent of the operator loop below)
@@ -481,9 +496,12 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
                 }
             } else if constexpr (FMT == 0) {
                 const int base = __ldg(&p.sptr[sl]);
-                const int width = (__ldg(&p.sptr[sl + 1]) - base) >> 5;
-                const int* cp = p.col + base + lane;
-                const T* vp = p.val + base + lane;
+                const int wfull = (__ldg(&p.sptr[sl + 1]) - base) >> 5;
+                // this unit's part of the slice: entries [part * SELL_SPLIT, ...) of every lane
+                const int kbeg = part * SELL_SPLIT;
+                const int width = min(wfull, kbeg + SELL_SPLIT) - kbeg;
+                const int* cp = p.col + base + lane + kbeg * 32;
+                const T* vp = p.val + base + lane + kbeg * 32;
                 // Sixteen entries in flight per lane (the gathers depend on the column
                 // loads, so the depth of the batch is the latency hiding); when the
                 // matrix exceeds L2 its entries are loaded evict-first, so the gathered
@@ -516,6 +534,24 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
                         for (int u = 0; u < UB; ++u) acc += vv[u] * Ycur[cc[u]];
                     }
                     for (; kk < width; ++kk) acc += __ldg(vp + kk * 32) * Ycur[__ldg(cp + kk * 32)];
+                }
+                if (nparts > 1) {
+                    // a part of a long slice: add the lanes' partial sums; the warp that
+                    // finishes the slice's last part reads the totals (resetting them for
+                    // the next pass) and carries on with the rows, the others are done
+                    atomicAdd(&p.hacc[(size_t)hix * 32 + lane], acc);
+                    __threadfence();
+                    __syncwarp();
+                    int last = 0;
+                    if (lane == 0) last = atomicAdd(&p.hcnt[hix], 1u) == (unsigned)(nparts - 1);
+                    last = __shfl_sync(0xffffffffu, last, 0);
+                    if (!last) continue;
+                    __threadfence();
+                    // every other part's adds completed before its count (fenced), and no
+                    // one touches this slice's accumulators again before the next pass
+                    acc = __ldcg(&p.hacc[(size_t)hix * 32 + lane]);
+                    p.hacc[(size_t)hix * 32 + lane] = (T)0;
+                    if (lane == 0) p.hcnt[hix] = 0u;
                 }
             } else {
                 // (J~ y)_i = sum_d U_d[i] y[i + m_d] - U_d[i - m_d] y[i - m_d]; zero halos on
@@ -603,7 +639,7 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
                     sc.G = Gn;
                 }
                 set_coefs();
-                s_next = s0 + MRS_WARPS;
+                s_next = u0 + MRS_WARPS;
             }
             __syncwarp();
             if (!sc.stop) make_u_warp0(sc.nu);
@@ -654,6 +690,11 @@ struct OpView {
     const int* col = nullptr;
     const T* val = nullptr;
     const int* rowmap = nullptr;
+    const int4* units = nullptr;
+    const int* uoff = nullptr;
+    T* hacc = nullptr;
+    unsigned* hcnt = nullptr;
+    int nheavy = 0;
     int ndiag = 0;
     const int* off = nullptr;
     const T* U = nullptr;
@@ -691,12 +732,22 @@ static asss_status launch_mrs(const Ctx& c, MrsWork* w, const OpView<T>& J, cons
         w->part_nblk = nblk;
     }
     ASSS_CUDA(cudaMemsetAsync(w->bar.p, 0, 2 * sizeof(unsigned), c.stream));
+    if (FMT == 0 && J.nheavy > 0) {
+        // the long slices' accumulators start at zero (a launch that gave up at a barrier
+        // may have left partial sums behind)
+        ASSS_CUDA(cudaMemsetAsync(J.hacc, 0, sizeof(T) * 32 * (size_t)J.nheavy, c.stream));
+        ASSS_CUDA(cudaMemsetAsync(J.hcnt, 0, sizeof(unsigned) * (size_t)J.nheavy, c.stream));
+    }
     MrsParams<T> prm;
     prm.n = J.n;
     prm.sptr = J.sptr;
     prm.col = J.col;
     prm.val = J.val;
     prm.rowmap = J.rowmap;
+    prm.units = J.units;
+    prm.uoff = J.uoff;
+    prm.hacc = J.hacc;
+    prm.hcnt = J.hcnt;
     prm.ndiag = J.ndiag;
     prm.off = J.off;
     prm.U = J.U;
@@ -846,6 +897,11 @@ static asss_status dispatch_mrs(const Ctx& c, MrsWork* w, const DSell<T>* sell, 
     v.col = sell->col.p;
     v.val = sell->val.p;
     v.rowmap = sell->rowmap.p;
+    v.units = sell->units.p;
+    v.uoff = sell->uoff.p;
+    v.hacc = const_cast<T*>(sell->hacc.p);
+    v.hcnt = const_cast<unsigned*>(sell->hcnt.p);
+    v.nheavy = sell->nheavy;
     v.key = sell;
     v.nnz = sell->nnz;
     *nnz_read = v.nnz;

@@ -946,6 +946,33 @@ asss_status build_sell(const DCsr& A, bool skip_diag, DSell<T>& out, cudaStream_
     k_sell_fill<T><<<cdiv((int64_t)ns * 32, 256), 256, 0, s>>>(n, ns, A.rp.p, A.ci.p, A.v.p, skip_diag ? 1 : 0,
                                                                out.rowmap.p, out.sptr.p, out.col.p, out.val.p);
     ASSS_CHECK_LAUNCH();
+    // work units: slices longer than SELL_SPLIT entries per lane are cut into parts
+    std::vector<int> hsp(ns + 1);
+    ASSS_CUDA(cudaMemcpyAsync(hsp.data(), out.sptr.p, sizeof(int) * (ns + 1), cudaMemcpyDeviceToHost, s));
+    ASSS_CUDA(cudaStreamSynchronize(s));
+    std::vector<int4> units;
+    std::vector<int> uoff(ns + 1);
+    int nheavy = 0;
+    units.reserve(ns + 64);
+    for (int sl = 0; sl < ns; ++sl) {
+        uoff[sl] = (int)units.size();
+        const int width = (hsp[sl + 1] - hsp[sl]) >> 5;
+        const int np = width > SELL_SPLIT ? (width + SELL_SPLIT - 1) / SELL_SPLIT : 1;
+        const int hidx = np > 1 ? nheavy++ : -1;
+        for (int pt = 0; pt < np; ++pt) units.push_back(make_int4(sl, pt, np, hidx));
+    }
+    uoff[ns] = (int)units.size();
+    out.nunits = (int)units.size();
+    out.nheavy = nheavy;
+    ASSS_TRY(to_device(out.units, units.data(), (int64_t)units.size(), s));
+    ASSS_TRY(to_device(out.uoff, uoff.data(), (int64_t)ns + 1, s));
+    if (nheavy) {
+        ASSS_TRY(out.hacc.alloc((int64_t)nheavy * 32));
+        ASSS_TRY(out.hcnt.alloc(nheavy));
+        ASSS_CUDA(cudaMemsetAsync(out.hacc.p, 0, sizeof(T) * 32 * (size_t)nheavy, s));
+        ASSS_CUDA(cudaMemsetAsync(out.hcnt.p, 0, sizeof(unsigned) * (size_t)nheavy, s));
+    }
+    ASSS_CUDA(cudaStreamSynchronize(s));
     return ASSS_OK;
 }
 
