@@ -2,9 +2,13 @@
 // the FGMRES cycle): given w = A_cal z_j, two classical Gram-Schmidt passes
 // against v_0..v_j, the norm of what is left, the Givens update of the Hessenberg
 // column and of the residual vector g, and v_{j+1} = w / ||w||, all in one
-// cooperative launch with three grid barriers (the passes over V are the only
-// HBM traffic; the dot products of a pass are reduced deterministically, every
-// block adding the block partials in the same order).
+// cooperative launch with two grid barriers (the passes over V are the only HBM
+// traffic; the dot products of a pass are reduced deterministically, every block
+// adding the block partials in the same order).  The norm after the second pass
+// comes from the one before it: with w1 = w - V h1 and h2 = V^T w1,
+// ||w1 - V h2||^2 = ||w1||^2 - ||h2||^2 up to the (re-orthogonalised) departure of V
+// from orthonormality, so the second correction and the new basis vector share one
+// sweep.
 #include <type_traits>
 
 #include "common.cuh"
@@ -97,6 +101,25 @@ __global__ void __launch_bounds__(AO_THREADS, 2) k_arnoldi_orth(AoParams p) {
         }
         __syncthreads();
     };
+    // block partials of NVC dot products (slots 0..NVC-1) and one squared norm (last
+    // accumulator, slot AO_MAXV - 1)
+    auto put_partials_n = [&](auto& acc, int nvc) {
+        constexpr int NA = sizeof(acc) / sizeof(double);
+#pragma unroll
+        for (int t = 0; t < NA; ++t) {
+            const double v = warp_sum(acc[t]);
+            if (lane == 0) s_w[warp][t] = v;
+        }
+        __syncthreads();
+        if ((int)threadIdx.x <= nvc) {
+            double s = 0.0;
+#pragma unroll
+            for (int q = 0; q < AO_WARPS; ++q) s += s_w[q][threadIdx.x];
+            const int slot = (int)threadIdx.x < nvc ? (int)threadIdx.x : AO_MAXV - 1;
+            part[(size_t)slot * nblk + blockIdx.x] = s;
+        }
+        __syncthreads();
+    };
     // dots V_a^T w over this block's rows, a < nv, AO_CH vectors per sweep
     auto dots = [&]() {
         for (int c0 = 0; c0 < nv; c0 += AO_CH) {
@@ -134,11 +157,13 @@ __global__ void __launch_bounds__(AO_THREADS, 2) k_arnoldi_orth(AoParams p) {
     // ---- pass 2: w -= V h1, then h2 = V^T w (one sweep when all of V fits the accumulators;
     // the vector count is a template argument there, so no FP64 operation is spent on padding) ----
     part = p.part + (size_t)AO_MAXV * nblk;
+    // the dot products h2 (slots 0..nv-1) and ||w1||^2 (slot AO_MAXV - 1 of the
+    // partials, never a vector slot: nv <= AO_MAXV - 1)
     auto fused2 = [&](auto nvc) {
         constexpr int NVC = decltype(nvc)::value;
-        double acc[NVC];
+        double acc[NVC + 1];
 #pragma unroll
-        for (int t = 0; t < NVC; ++t) acc[t] = 0.0;
+        for (int t = 0; t <= NVC; ++t) acc[t] = 0.0;
         for (long long i = r0 + threadIdx.x; i < r1; i += AO_THREADS) {
             double vi[NVC];
             double s = 0.0;
@@ -151,8 +176,9 @@ __global__ void __launch_bounds__(AO_THREADS, 2) k_arnoldi_orth(AoParams p) {
             w[i] = wi;
 #pragma unroll
             for (int t = 0; t < NVC; ++t) acc[t] += vi[t] * wi;
+            acc[NVC] += wi * wi;
         }
-        put_partials(acc, 0, NVC);
+        put_partials_n(acc, NVC);
     };
     if (nv <= 6) {
         switch (nv) {
@@ -164,50 +190,55 @@ __global__ void __launch_bounds__(AO_THREADS, 2) k_arnoldi_orth(AoParams p) {
             default: fused2(std::integral_constant<int, 6>{}); break;
         }
     } else {
+        double accn[1] = {0.0};
         for (long long i = r0 + threadIdx.x; i < r1; i += AO_THREADS) {
             double s = 0.0;
             for (int a = 0; a < nv; ++a) s += V[(size_t)a * n + i] * s_h1[a];
-            w[i] -= s;
+            const double wi = w[i] - s;
+            w[i] = wi;
+            accn[0] += wi * wi;
         }
+        put_partials_n(accn, 0);
         dots();
     }
     grid_sync_phase(p.gb, nblk, p.phase0 + 1, p.budget);
     if (*err) return;
     reduce(nv, s_h2);
+    {
+        // ||w1||^2 from its slot
+        double t = 0.0;
+        if (warp == 0) {
+            for (int b = lane; b < nblk; b += 32) t += __ldcg(&part[(size_t)(AO_MAXV - 1) * nblk + b]);
+            t = warp_sum(t);
+            if (lane == 0) s_n = t;
+        }
+        __syncthreads();
+    }
     if (blockIdx.x == 0)
         for (int a = threadIdx.x; a < nv; a += AO_THREADS) p.hv2[a] = s_h2[a];
 
-    // ---- pass 3: w -= V h2 and ||w||^2 ----
-    part = p.part;
-    {
-        double acc[1] = {0.0};
-        for (long long i = r0 + threadIdx.x; i < r1; i += AO_THREADS) {
-            double s = 0.0;
-            for (int a = 0; a < nv; ++a) s += V[(size_t)a * n + i] * s_h2[a];
-            const double wi = w[i] - s;
-            w[i] = wi;
-            acc[0] += wi * wi;
-        }
-        put_partials(acc, 0, 1);  // slot 0 holds this block's part of ||w||^2
-    }
-    grid_sync_phase(p.gb, nblk, p.phase0 + 2, p.budget);
-    if (*err) return;
-    reduce(1, &s_n);
-    const double hn2 = s_n;
+    // ---- pass 3: hn2 = ||w1||^2 - ||h2||^2; w2 = w1 - V h2 and v_{j+1} = w2 / ||w2|| in one sweep ----
+    double h2n = 0.0;
+    for (int a = 0; a < nv; ++a) h2n += s_h2[a] * s_h2[a];
+    const double hn2 = fmax(s_n - h2n, 0.0);
     if (blockIdx.x == 0 && threadIdx.x == 0) ao_fg_column(p, s_h1, s_h2, hn2);
-
-    // ---- v_{j+1} = w / ||w|| (unused when the cycle stops here) ----
     const double hn = sqrt(hn2);
     const double inv = (hn > 0.0) ? 1.0 / hn : 0.0;
     double* vn = const_cast<double*>(V) + (size_t)nv * n;
-    for (long long i = r0 + threadIdx.x; i < r1; i += AO_THREADS) vn[i] = w[i] * inv;
+    for (long long i = r0 + threadIdx.x; i < r1; i += AO_THREADS) {
+        double s = 0.0;
+        for (int a = 0; a < nv; ++a) s += V[(size_t)a * n + i] * s_h2[a];
+        const double wi = w[i] - s;
+        w[i] = wi;
+        vn[i] = wi * inv;
+    }
 }
 
 asss_status arnoldi_orth(const Ctx& c, ArnoldiWork& aw, const double* V, double* w, int n, int j, int m, double* H,
                          double* cs, double* sn, double* g, double* hv, double* hv2, double* hn2, double* inv_hn,
                          double thr, int* stop) {
-    if (j + 1 > AO_MAXV) {
-        set_error("Arnoldi step %d exceeds the fused kernel's %d vectors", j, AO_MAXV);
+    if (j + 1 > AO_MAXV - 1) {   // one partial slot is kept for the norm
+        set_error("Arnoldi step %d exceeds the fused kernel's %d vectors", j, AO_MAXV - 1);
         return ASSS_ERR_UNSUPPORTED;
     }
     if (aw.n != n || !aw.part.p) {
@@ -258,7 +289,7 @@ asss_status arnoldi_orth(const Ctx& c, ArnoldiWork& aw, const double* V, double*
     ASSS_CUDA(cudaLaunchCooperativeKernel((const void*)k_arnoldi_orth, dim3(aw.nblk), dim3(AO_THREADS), args, 0,
                                           c.stream));
     count_launch();
-    aw.phase += 3;
+    aw.phase += 2;
     return ASSS_OK;
 }
 

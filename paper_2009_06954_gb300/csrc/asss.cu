@@ -931,7 +931,7 @@ static asss_status fgmres_cycle(asss_handle* h, KrylovWork& kw, int tr, const do
         h->tr.mark(s, Tracer::OP);
         ASSS_TRY(apply_op(h, tr, zj, kw.w.p));
         h->tr.mark(s, Tracer::ORTH);
-        const bool fused = j + 1 <= AO_MAXV;
+        const bool fused = j + 1 < AO_MAXV;
         if (fused) {
             // CGS2, ||w||, the Givens update, v_{j+1} and the stop test in one launch
             ASSS_TRY(arnoldi_orth(h->ctx, kw.ao, kw.V.p, kw.w.p, n, j, M, kw.H.p, kw.cs.p, kw.sn.p, kw.g.p,
