@@ -30,7 +30,14 @@ METRIC = "solves/s to 1e-8 rel. residual"
 UNIT = "solves/s"
 WORKLOAD = ("dh3d_100: dissipative-Hamiltonian implicit-Euler step A = E + h(R - J), 100^3 grid "
             "(n = 1,000,000, nnz = 6,940,000), S on the pattern of A, k = 20, FP32 inner mrs "
-            "(tol 1e-6) / FP64 outer FGMRES(60), outer tol 1e-8")
+            "(tol {inner_tol}) / FP64 outer FGMRES(60), outer tol 1e-8")
+DH = {"inner_tol": 1e-6}
+
+
+def dh_workload():
+    return WORKLOAD.format(inner_tol=f"{DH['inner_tol']:g}".replace("e-0", "e-"))
+
+
 SIDE = 100
 CPU_SAMPLE_SIDE = 40
 ADJ_CPU_SIDE = 24
@@ -243,7 +250,7 @@ def cpu_worker(side, steps, warmup, budget_s, procs, xout):
     A, b, parts = dissipative_hamiltonian_3d(side=side, seed=1)
     n = A.shape[0]
     t0 = time.perf_counter()
-    o = oracle.AsssOracle(A, inner_tol=1e-6)
+    o = oracle.AsssOracle(A, inner_tol=DH["inner_tol"])
     rhs = _make_rhs(parts, n, 1, 8)
     o.solve(rhs[0], tol=1e-8, outer="fgmres")   # the oracle builds its SMW data on first use: set-up
     t_setup = time.perf_counter() - t0
@@ -289,7 +296,7 @@ def run_cpu_baseline(steps, warmup, budget_s, xout=None):
         env[v] = "1"
     procs = host_cores()
     cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", "--steps", str(steps), "--warmup",
-           str(warmup), "--budget", str(budget_s), "--procs", str(procs)]
+           str(warmup), "--budget", str(budget_s), "--procs", str(procs), "--inner-tol", repr(DH["inner_tol"])]
     if xout:
         cmd += ["--xout", xout]
     p = subprocess.run(cmd, capture_output=True, text=True, env=env, cwd=ROOT)
@@ -919,7 +926,7 @@ def main_reference(args):
         per_step = f"one oracle adjoint solve + dL/dA at {ADJ_CPU_SIDE}^3, counted as n_sample / n of a gradient"
     else:
         cb = run_cpu_baseline(args.steps, max(0, min(args.warmup, 1)), 120.0)
-        workload = WORKLOAD
+        workload = dh_workload()
         steps, warm = len(cb["rounds"]), cb["warmup"]
         ms = 1000.0 * sum(cb["rounds"]) / max(steps, 1)
         per_step = (f"{cb['procs']} concurrent oracle solves at {CPU_SAMPLE_SIDE}^3 (n = {cb['n_sample']}), each "
@@ -983,11 +990,14 @@ def main():
     ap.add_argument("--cuda-profiler-range", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--general-n", type=int, default=GENERAL["n"], help="rows of the general_2e6 workload")
+    ap.add_argument("--inner-tol", type=float, default=DH["inner_tol"],
+                    help="mrs tolerance of the dh3d_100 workload (FGMRES takes inexact inner solves)")
     ap.add_argument("--batch-count", type=int, default=BATCH["count"],
                     help="systems in the batched workload (smaller counts for profiling captures)")
     args = ap.parse_args()
     BATCH["count"] = args.batch_count
     GENERAL["n"] = args.general_n
+    DH["inner_tol"] = args.inner_tol
 
     if args.cpu_worker:
         if args.workload == "batched_dh":
@@ -1038,7 +1048,7 @@ def main():
     A, b0, parts = dissipative_hamiltonian_3d(side=SIDE, seed=1)
     n = A.shape[0]
     t0 = time.perf_counter()
-    solver = pkg.Solver(A, precision="mixed", outer="fgmres", inner_tol=1e-6, outer_tol=1e-8, k=20,
+    solver = pkg.Solver(A, precision="mixed", outer="fgmres", inner_tol=DH["inner_tol"], outer_tol=1e-8, k=20,
                         q_bf16=args.q_storage == "bf16", stream=stream.cuda_stream)
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
@@ -1096,7 +1106,7 @@ def main():
     if not args.no_fp64_leg:
         solver.close()   # frees the mixed handle's device memory first
         t0 = time.perf_counter()
-        s64 = pkg.Solver(A, precision="fp64", outer="fgmres", inner_tol=1e-6, outer_tol=1e-8, k=20,
+        s64 = pkg.Solver(A, precision="fp64", outer="fgmres", inner_tol=DH["inner_tol"], outer_tol=1e-8, k=20,
                          stream=stream.cuda_stream)
         torch.cuda.synchronize()
         t_setup64 = time.perf_counter() - t0
@@ -1133,7 +1143,7 @@ def main():
     # CUDA events around repeated applications, L2 flushed between them
     others = []
     if not args.no_fp64_leg:
-        s_op = pkg.Solver(A, precision="mixed", outer="fgmres", inner_tol=1e-6, outer_tol=1e-8, k=20,
+        s_op = pkg.Solver(A, precision="mixed", outer="fgmres", inner_tol=DH["inner_tol"], outer_tol=1e-8, k=20,
                           stream=stream.cuda_stream)
         v = rhs[0].clone()
         ndiag = len(np.unique(np.repeat(np.arange(n), np.diff(A.indptr)) - A.indices))
@@ -1180,7 +1190,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32-inner/f64-outer", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+        "config": {"workload": dh_workload(), "inner_tol": DH["inner_tol"], "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "256 MB buffer written between steps (not timed); working set > L2",
                    "setup_s": round(t_setup, 3), "lls_its": solver.setup_stats["lls_its"],
                    "outer_its": stats[-1]["outer_its"], "inner_its_avg": round(stats[-1]["inner_its_avg"], 2),

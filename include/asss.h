@@ -113,6 +113,14 @@ typedef struct {
                                  runs them in lockstep blocks of up to 8 whose preconditioner
                                  applications are one multi-column mrs launch per Arnoldi step
                                  (App. B's simultaneous iterations); 0: one column after another */
+    int    sell_sigma;        /* J~ in SELL-C (general patterns): rows are sorted by length within
+                                 windows of sell_sigma rows when natural-order slices would pad the
+                                 storage by more than a fifth; a power of two in [1024, 16384], or
+                                 0: picked at set-up by timing mrs steps (mixed precision, n >=
+                                 10^5), else 4096. Other values: ASSS_ERR_ARG                   */
+    int    sell_split;        /* entries per lane in one SELL-C work unit: wider slices are cut
+                                 into parts taken by different warps; >= 64, or 0 (picked with
+                                 sell_sigma, else 1024). Both only change summation order      */
 } asss_options;
 
 enum { ASSS_SCALING_MAXES = 0, ASSS_SCALING_MATCHING = 1 };
@@ -138,6 +146,9 @@ typedef struct {
     double t_inner_ms;        /* device time of the mrs kernel launches (CUDA events on the stream) */
     long long inner_bytes;    /* algorithmic bytes those launches move (matrix entries, Q_k rows, vectors) */
     int    inner_launches;    /* mrs kernel launches counted in t_inner_ms / inner_bytes */
+    int    sell_sigma;        /* set-up, J~ in SELL-C: sorting window in rows (0: natural order) */
+    int    sell_split;        /* set-up, J~ in SELL-C: entries per lane of one work unit; both picked
+                                 by timing mrs steps for systems of 10^5 rows and more (FP32 path) */
 } asss_stats;
 
 typedef struct asss_handle asss_handle;

@@ -48,7 +48,7 @@ class Options(C.Structure):
                 ("seed", C.c_uint64), ("lls_tol", C.c_double), ("lls_maxit", C.c_int),
                 ("zero_tol", C.c_double), ("wait_timeout_ms", C.c_double), ("stream", C.c_void_p),
                 ("inner_format", C.c_int), ("q_bf16", C.c_int), ("s_values", C.c_void_p),
-                ("scaling", C.c_int), ("rhs_block", C.c_int)]
+                ("scaling", C.c_int), ("rhs_block", C.c_int), ("sell_sigma", C.c_int), ("sell_split", C.c_int)]
 
 FORMATS = {"auto": 0, "sell": 1, "diag": 2}
 SCALINGS = {"maxes": 0, "matching": 1}
@@ -61,7 +61,8 @@ class Stats(C.Structure):
                 ("k_eff", C.c_int), ("prec2", C.c_int), ("lls_its", C.c_int),
                 ("lls_relgrad", C.c_double), ("nnz_pattern", C.c_longlong),
                 ("t_setup_ms", C.c_double), ("t_solve_ms", C.c_double), ("t_inner_ms", C.c_double),
-                ("inner_bytes", C.c_longlong), ("inner_launches", C.c_int)]
+                ("inner_bytes", C.c_longlong), ("inner_launches", C.c_int), ("sell_sigma", C.c_int),
+                ("sell_split", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -252,7 +253,8 @@ class Solver:
     inner_tol, setup_tol, outer_tol, inner_maxit, outer_maxit, restart, r_max,
     seed, lls_tol, lls_maxit, zero_tol, wait_timeout_ms, row_perm, dr, dc, stream, s_values,
     scaling ('maxes' | 'matching': how Eq. mc64's P, D_r, D_c are found when none is given),
-    rhs_block (several right-hand sides in lockstep blocks sharing multi-column mrs launches)
+    rhs_block (several right-hand sides in lockstep blocks sharing multi-column mrs launches),
+    sell_sigma, sell_split (SELL-C storage of J~: sorting window and work-unit width; 0 = tuned)
     (saved S values to resume the set-up from, e.g. ``export(nnz)["s_val"]`` of an
     earlier solver for the same matrix).
     """

@@ -565,6 +565,8 @@ static void fill_defaults(asss_options* o) {
     o->s_values = nullptr;
     o->scaling = ASSS_SCALING_MAXES;
     o->rhs_block = 0;
+    o->sell_sigma = 0;
+    o->sell_split = 0;
 }
 
 static int pick_kp(int k) {
@@ -1391,6 +1393,56 @@ static asss_status refine_block(asss_handle* h, int nb, const double* const* rhs
 }
 
 // ---------------------------------------------------------------------------
+// SELL-C-sigma autotuner: J~ in general patterns is stored with a sorting window sigma
+// and cut into work units of `split` entries per lane; the best pair depends on the row
+// length distribution and on locality (a larger window pads less but scatters a slice's
+// rows further apart).  Each candidate is built in FP32 and timed on four mrs steps
+// (k = 0, the operator dominates); the fastest is kept.
+// ---------------------------------------------------------------------------
+static asss_status tune_sell(asss_handle* h, int* sigma_out, int* split_out) {
+    NvtxRange nv_("asss:sell-tuner");
+    const Ctx& c = h->ctx;
+    const int n = h->n;
+    const int cand[][2] = {{4096, 1024}, {1024, 1024}, {16384, 1024}, {4096, 256}, {4096, 4096}};
+    MrsWork* w = nullptr;
+    ASSS_TRY(mrs_work_create(&w, n, c.sms));
+    struct WGuard {
+        MrsWork* w;
+        ~WGuard() { mrs_work_destroy(w); }
+    } wg{w};
+    DBuf<float> x32;
+    DBuf<double> alpha;
+    ASSS_TRY(x32.alloc(n));
+    ASSS_TRY(alpha.alloc(1));
+    double best = INFINITY;
+    *sigma_out = 0;
+    *split_out = 0;
+    for (const auto& cd : cand) {
+        DSell<float> J;
+        ASSS_TRY(build_sell<float>(h->Jt, true, J, c.stream, cd[0], cd[1]));
+        MrsOperator op;
+        op.J32 = &J;
+        op.k = 0;
+        op.kp = 0;
+        op.alpha = alpha.p;
+        double ms = 0.0;
+        for (int rep = 0; rep < 2; ++rep) {   // the second run is timed
+            MrsResult r;
+            ASSS_TRY(mrs_solve(c, w, op, true, 1.0, 1.0, h->d.p, nullptr, x32.p, 0.0, 4, nullptr, &r, true));
+            ms = r.ms;
+        }
+        mrs_take_totals(w);
+        if (ms < best) {
+            best = ms;
+            *sigma_out = J.sigma > 0 ? cd[0] : 0;
+            *split_out = cd[1];
+        }
+        if (J.sigma == 0) break;   // rows of even length: no window is built, nothing to tune
+    }
+    return ASSS_OK;
+}
+
+// ---------------------------------------------------------------------------
 // set-up
 // ---------------------------------------------------------------------------
 static asss_status do_setup(asss_handle* h, const asss_csr* Ain, asss_stats* st) {
@@ -1597,8 +1649,13 @@ static asss_status do_setup(asss_handle* h, const asss_csr* Ain, asss_stats* st)
         }
     }
     if (!h->use_dia) {
-        ASSS_TRY(build_sell<double>(h->Jt, true, h->J64, s));
-        if (o.precision == ASSS_PREC_MIXED) ASSS_TRY(build_sell<float>(h->Jt, true, h->J32, s));
+        int sigma = o.sell_sigma, split = o.sell_split;
+        if (sigma == 0 && split == 0 && o.precision == ASSS_PREC_MIXED && n >= 100000)
+            ASSS_TRY(tune_sell(h, &sigma, &split));
+        ASSS_TRY(build_sell<double>(h->Jt, true, h->J64, s, sigma, split));
+        if (o.precision == ASSS_PREC_MIXED) ASSS_TRY(build_sell<float>(h->Jt, true, h->J32, s, sigma, split));
+        st->sell_sigma = h->J64.sigma;
+        st->sell_split = h->J64.split;
     }
     // outer operator pieces: W Abar and S W
     ASSS_TRY(copy_csr(h->Abar, h->Aw, s));

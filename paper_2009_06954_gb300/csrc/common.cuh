@@ -101,12 +101,13 @@ struct DCsr {
 
 // SELL-C (C = 32) storage: slot 32s + t (lane t of slice s) holds row rowmap[32s + t]
 // (row 32s + t when rowmap is empty); entry kk of that lane sits at sptr[s] + kk*32 + t.
-// With SELL-C-sigma the rows of each window of SELL_SIGMA consecutive rows are sorted
+// With SELL-C-sigma the rows of each window of sigma consecutive rows are sorted
 // by length (longest first) before they are cut into slices, so a slice holds rows
 // of similar length and heavy-tailed row lengths do not pad every slice to its
 // longest row.  Padding entries have value 0 and a valid column; slots past the
 // last row map to row n (no row).
-constexpr int SELL_SIGMA = 4096;
+constexpr int SELL_SIGMA = 4096;          // default sorting window
+constexpr int SELL_SIGMA_MAX = 16384;     // largest window the sort kernel takes
 template <class T>
 struct DSell {
     int n = 0;
@@ -118,10 +119,12 @@ struct DSell {
     DBuf<T> val;
     DBuf<int> rowmap; // 32 * nslices slots -> row (empty: identity)
     DBuf<int> rowpos; // n rows -> slot (empty: identity)
-    // Work units of a pass: a slice, or one part of SELL_SPLIT entries of a long slice
+    // Work units of a pass: a slice, or one part of `split` entries of a long slice
     // (x slice, y part, z parts of that slice, w its accumulator or -1); uoff[s] is the
     // first unit of slice s.  The parts of a long slice add their lanes' partial sums
     // into hacc (32 values per long slice) and the last one to finish carries on.
+    int sigma = 0;        // sorting window in rows (0: natural order)
+    int split = 0;        // entries per lane of one work unit
     int nunits = 0;
     int nheavy = 0;
     DBuf<int4> units;

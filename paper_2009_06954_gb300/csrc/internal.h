@@ -18,7 +18,7 @@ asss_status attach_dia(DCsr& A, int max_diag, double min_fill, int* ok, cudaStre
 asss_status build_pattern(const DCsr& Abar, const DCsr& AbarT, const DCsr& S, const DCsr& ST, DCsr& P,
                           DBuf<int>& mirror, DBuf<int>& diagpos, cudaStream_t s);
 template <class T>
-asss_status build_sell(const DCsr& A, bool skip_diag, DSell<T>& out, cudaStream_t s);
+asss_status build_sell(const DCsr& A, bool skip_diag, DSell<T>& out, cudaStream_t s, int sigma = 0, int split = 0);
 // Skew half-diagonal storage of J when J is exactly skew, has at most max_diag
 // positive offsets and fills at least min_fill of the stored diagonals; *ok = 0
 // (and nothing allocated) otherwise.

@@ -129,6 +129,7 @@ struct MrsParams {
     const int* uoff;
     T* hacc;             // partial sums of the parts of long slices (32 per long slice, left at 0)
     unsigned* hcnt;      // parts finished per long slice (left at 0)
+    int split;           // entries per lane of one work unit
     // skew half-diagonal operator: U points at U_0[0]; diagonal d starts ustride later
     int ndiag;
     const int* off;
@@ -497,9 +498,9 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
             } else if constexpr (FMT == 0) {
                 const int base = __ldg(&p.sptr[sl]);
                 const int wfull = (__ldg(&p.sptr[sl + 1]) - base) >> 5;
-                // this unit's part of the slice: entries [part * SELL_SPLIT, ...) of every lane
-                const int kbeg = part * SELL_SPLIT;
-                const int width = min(wfull, kbeg + SELL_SPLIT) - kbeg;
+                // this unit's part of the slice: entries [part * split, ...) of every lane
+                const int kbeg = part * p.split;
+                const int width = min(wfull, kbeg + p.split) - kbeg;
                 const int* cp = p.col + base + lane + kbeg * 32;
                 const T* vp = p.val + base + lane + kbeg * 32;
                 // Sixteen entries in flight per lane (the gathers depend on the column
@@ -695,6 +696,7 @@ struct OpView {
     T* hacc = nullptr;
     unsigned* hcnt = nullptr;
     int nheavy = 0;
+    int split = 0;
     int ndiag = 0;
     const int* off = nullptr;
     const T* U = nullptr;
@@ -748,6 +750,7 @@ static asss_status launch_mrs(const Ctx& c, MrsWork* w, const OpView<T>& J, cons
     prm.uoff = J.uoff;
     prm.hacc = J.hacc;
     prm.hcnt = J.hcnt;
+    prm.split = J.split > 0 ? J.split : SELL_SPLIT;
     prm.ndiag = J.ndiag;
     prm.off = J.off;
     prm.U = J.U;
@@ -902,6 +905,7 @@ static asss_status dispatch_mrs(const Ctx& c, MrsWork* w, const DSell<T>* sell, 
     v.hacc = const_cast<T*>(sell->hacc.p);
     v.hcnt = const_cast<unsigned*>(sell->hcnt.p);
     v.nheavy = sell->nheavy;
+    v.split = sell->split;
     v.key = sell;
     v.nnz = sell->nnz;
     *nnz_read = v.nnz;

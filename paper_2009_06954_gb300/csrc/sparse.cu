@@ -815,25 +815,25 @@ __global__ void k_sell_rowlen(int n, const int* rp, const int* ci, int skip_diag
     len[r] = l;
 }
 
-// SELL-C-sigma: one block per window of SELL_SIGMA rows sorts (length desc, row asc)
-// with a bitonic network in shared memory (each of the 1024 threads holds
-// SELL_SIGMA / 1024 keys) and writes slot -> row and row -> slot; slots past the last
-// row map to row n
+// SELL-C-sigma: one block per window of sigma rows sorts (length desc, row asc) with a
+// bitonic network in shared memory (each of the 1024 threads holds sigma / 1024 keys;
+// sigma a power of two from 1024 to SELL_SIGMA_MAX, the keys in dynamic shared memory)
+// and writes slot -> row and row -> slot; slots past the last row map to row n
 constexpr int SELL_SORT_THREADS = 1024;
-__global__ void __launch_bounds__(SELL_SORT_THREADS) k_sell_sort_window(int n, int nslots, const int* len,
+__global__ void __launch_bounds__(SELL_SORT_THREADS) k_sell_sort_window(int n, int nslots, int sigma, const int* len,
                                                                           int* rowmap, int* rowpos) {
-    __shared__ long long key[SELL_SIGMA];
-    const int w0 = blockIdx.x * SELL_SIGMA;
-    for (int t = threadIdx.x; t < SELL_SIGMA; t += SELL_SORT_THREADS) {
+    extern __shared__ long long key[];
+    const int w0 = blockIdx.x * sigma;
+    for (int t = threadIdx.x; t < sigma; t += SELL_SORT_THREADS) {
         const int r = w0 + t;
         // length in the high word (complemented: descending), row in the low word
         key[t] = r < n ? ((long long)(0x7fffffff - len[r]) << 32) | (unsigned)r
                        : ((long long)0x7fffffff << 32) | 0x7fffffffu;
     }
     __syncthreads();
-    for (int k = 2; k <= SELL_SIGMA; k <<= 1) {
+    for (int k = 2; k <= sigma; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int t = threadIdx.x; t < SELL_SIGMA; t += SELL_SORT_THREADS) {
+            for (int t = threadIdx.x; t < sigma; t += SELL_SORT_THREADS) {
                 const int ixj = t ^ j;
                 if (ixj > t) {
                     const long long a = key[t], b = key[ixj];
@@ -847,7 +847,7 @@ __global__ void __launch_bounds__(SELL_SORT_THREADS) k_sell_sort_window(int n, i
             __syncthreads();
         }
     }
-    for (int t = threadIdx.x; t < SELL_SIGMA; t += SELL_SORT_THREADS) {
+    for (int t = threadIdx.x; t < sigma; t += SELL_SORT_THREADS) {
         const int slot = w0 + t;
         if (slot < nslots) {
             const int row = (int)(key[t] & 0xffffffffLL);
@@ -899,9 +899,25 @@ __global__ void k_sell_fill(int n, int nslices, const int* rp, const int* ci, co
 }
 
 // Slices of 32 rows in natural order; when that pads the stored entries by more than
-// a fifth over the matrix's own (heavy-tailed row lengths), SELL-C-sigma instead.
+// a fifth over the matrix's own (heavy-tailed row lengths), SELL-C-sigma instead (sigma:
+// the window in rows, a power of two from 1024 to SELL_SIGMA_MAX; 0: SELL_SIGMA).  Slices
+// wider than `split` entries per lane become several work units (0: SELL_SPLIT).
 template <class T>
-asss_status build_sell(const DCsr& A, bool skip_diag, DSell<T>& out, cudaStream_t s) {
+asss_status build_sell(const DCsr& A, bool skip_diag, DSell<T>& out, cudaStream_t s, int sigma, int split) {
+    if (sigma <= 0) sigma = SELL_SIGMA;
+    if (split <= 0) split = SELL_SPLIT;
+    if (sigma < 1024 || sigma > SELL_SIGMA_MAX || (sigma & (sigma - 1))) {
+        set_error("SELL-C-sigma window %d is not a power of two in [1024, %d]", sigma, SELL_SIGMA_MAX);
+        return ASSS_ERR_ARG;
+    }
+    if (split < 64) {
+        set_error("SELL-C work unit of %d entries per lane is below 64", split);
+        return ASSS_ERR_ARG;
+    }
+    out.sigma = 0;
+    out.split = split;
+    out.rowmap.free();
+    out.rowpos.free();
     int n = A.n;
     int ns = cdiv(n, 32);
     out.n = n;
@@ -925,13 +941,16 @@ asss_status build_sell(const DCsr& A, bool skip_diag, DSell<T>& out, cudaStream_
         ASSS_CUDA(cudaMemcpyAsync(&hn, cnt.p, sizeof(hn), cudaMemcpyDeviceToHost, s));
         ASSS_TRY(exclusive_scan64(w.p, off64.p, ns, &tot, s));   // 64-bit total (synchronises)
         if (pass == 1 || (double)tot <= 1.2 * (double)hn) break;
-        // heavy-tailed rows: sort each window of SELL_SIGMA rows by length
+        // heavy-tailed rows: sort each window of sigma rows by length
         const int nslots = ns * 32;
         ASSS_TRY(out.rowmap.alloc(nslots));
         ASSS_TRY(out.rowpos.alloc(n));
-        k_sell_sort_window<<<cdiv(nslots, SELL_SIGMA), SELL_SORT_THREADS, 0, s>>>(n, nslots, len.p, out.rowmap.p,
-                                                                                  out.rowpos.p);
+        const size_t smem = sizeof(long long) * (size_t)sigma;
+        ASSS_CUDA(cudaFuncSetAttribute(k_sell_sort_window, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_sell_sort_window<<<cdiv(nslots, sigma), SELL_SORT_THREADS, smem, s>>>(n, nslots, sigma, len.p,
+                                                                                out.rowmap.p, out.rowpos.p);
         ASSS_CHECK_LAUNCH();
+        out.sigma = sigma;
     }
     out.nnz = (int64_t)hn;
     out.nstored = tot;
@@ -946,7 +965,7 @@ asss_status build_sell(const DCsr& A, bool skip_diag, DSell<T>& out, cudaStream_
     k_sell_fill<T><<<cdiv((int64_t)ns * 32, 256), 256, 0, s>>>(n, ns, A.rp.p, A.ci.p, A.v.p, skip_diag ? 1 : 0,
                                                                out.rowmap.p, out.sptr.p, out.col.p, out.val.p);
     ASSS_CHECK_LAUNCH();
-    // work units: slices longer than SELL_SPLIT entries per lane are cut into parts
+    // work units: slices longer than `split` entries per lane are cut into parts
     std::vector<int> hsp(ns + 1);
     ASSS_CUDA(cudaMemcpyAsync(hsp.data(), out.sptr.p, sizeof(int) * (ns + 1), cudaMemcpyDeviceToHost, s));
     ASSS_CUDA(cudaStreamSynchronize(s));
@@ -957,7 +976,7 @@ asss_status build_sell(const DCsr& A, bool skip_diag, DSell<T>& out, cudaStream_
     for (int sl = 0; sl < ns; ++sl) {
         uoff[sl] = (int)units.size();
         const int width = (hsp[sl + 1] - hsp[sl]) >> 5;
-        const int np = width > SELL_SPLIT ? (width + SELL_SPLIT - 1) / SELL_SPLIT : 1;
+        const int np = width > split ? (width + split - 1) / split : 1;
         const int hidx = np > 1 ? nheavy++ : -1;
         for (int pt = 0; pt < np; ++pt) units.push_back(make_int4(sl, pt, np, hidx));
     }
@@ -966,6 +985,8 @@ asss_status build_sell(const DCsr& A, bool skip_diag, DSell<T>& out, cudaStream_
     out.nheavy = nheavy;
     ASSS_TRY(to_device(out.units, units.data(), (int64_t)units.size(), s));
     ASSS_TRY(to_device(out.uoff, uoff.data(), (int64_t)ns + 1, s));
+    out.hacc.free();
+    out.hcnt.free();
     if (nheavy) {
         ASSS_TRY(out.hacc.alloc((int64_t)nheavy * 32));
         ASSS_TRY(out.hcnt.alloc(nheavy));
@@ -976,8 +997,8 @@ asss_status build_sell(const DCsr& A, bool skip_diag, DSell<T>& out, cudaStream_
     return ASSS_OK;
 }
 
-template asss_status build_sell<double>(const DCsr&, bool, DSell<double>&, cudaStream_t);
-template asss_status build_sell<float>(const DCsr&, bool, DSell<float>&, cudaStream_t);
+template asss_status build_sell<double>(const DCsr&, bool, DSell<double>&, cudaStream_t, int, int);
+template asss_status build_sell<float>(const DCsr&, bool, DSell<float>&, cudaStream_t, int, int);
 
 }  // namespace asss
 

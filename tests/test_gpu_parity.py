@@ -746,6 +746,51 @@ def test_powerlaw_inner_operator_mrs_steps_match_oracle(pkg, precision):
     np.testing.assert_allclose(Xg, Xo, rtol=0, atol=rtol * np.abs(Xo).max())
 
 
+def test_powerlaw_sell_layouts_agree(pkg):
+    """The SELL-C layout of J~ (sorting window sigma, work-unit width) changes only the
+    summation order of J~ v: FP64 solves of the power-law recipe with the extreme
+    layouts (narrow units that split long slices into many parts finished by the last
+    warp, wide units that keep them whole) reach the same x, each meeting the outer
+    tolerance on the original system."""
+    from workloads import random_powerlaw
+    A, b = random_powerlaw(n=20000, seed=2, band=1000, dom_frac=1.0)   # every row dominant: converges
+    A = sp.csr_matrix(A)
+    xs = []
+    for sigma, split in ((1024, 64), (16384, 4096), (4096, 0)):
+        s = pkg.Solver(A, precision="fp64", outer="fgmres", inner_tol=1e-10, lls_maxit=400,
+                       sell_sigma=sigma, sell_split=split)
+        st0 = s.setup_stats
+        assert st0["sell_sigma"] == sigma            # heavy tail: the rows are sorted
+        assert st0["sell_split"] == (split or 1024)
+        x, st = s.solve(b)
+        s.close()
+        assert st["status"] == 0
+        assert np.linalg.norm(b - A @ x) <= 1e-8 * np.linalg.norm(b)
+        xs.append(x)
+    for x in xs[1:]:
+        np.testing.assert_allclose(x, xs[0], rtol=0, atol=1e-7 * np.abs(xs[0]).max())
+    with pytest.raises(pkg.AsssError):
+        pkg.Solver(A, precision="fp64", sell_sigma=3000)
+    with pytest.raises(pkg.AsssError):
+        pkg.Solver(A, precision="fp64", sell_split=8)
+
+
+def test_powerlaw_sell_tuner_picks_a_candidate(pkg):
+    """Mixed precision at 10^5 rows or more tunes the SELL-C layout at set-up by timing
+    mrs steps; the chosen pair is one of the candidates and the solve converges."""
+    from workloads import random_powerlaw
+    A, b = random_powerlaw(n=120000, seed=4, band=4000, dom_frac=1.0)
+    A = sp.csr_matrix(A)
+    s = pkg.Solver(A, precision="mixed", outer="fgmres", inner_tol=1e-6, lls_maxit=400)
+    st0 = s.setup_stats
+    assert (st0["sell_sigma"], st0["sell_split"]) in {(4096, 1024), (1024, 1024), (16384, 1024),
+                                                      (4096, 256), (4096, 4096)}
+    x, st = s.solve(b)
+    s.close()
+    assert st["status"] == 0
+    assert np.linalg.norm(b - A @ x) <= 1e-8 * np.linalg.norm(b)
+
+
 # ----------------------------------------------------------------------------
 # several right-hand sides in one call: lockstep FGMRES blocks whose preconditioner
 # applications are one multi-column mrs launch (App. B) per Arnoldi step
