@@ -31,7 +31,7 @@ UNIT = "solves/s"
 WORKLOAD = ("dh3d_100: dissipative-Hamiltonian implicit-Euler step A = E + h(R - J), 100^3 grid "
             "(n = 1,000,000, nnz = 6,940,000), S on the pattern of A, k = 20, FP32 inner mrs "
             "(tol {inner_tol}) / FP64 outer FGMRES(60), outer tol 1e-8")
-DH = {"inner_tol": 1e-6}
+DH = {"inner_tol": 1e-3}
 
 
 def dh_workload():
@@ -877,6 +877,7 @@ def main_general(args, world, rank, local):
                    "setup_s": round(t_setup, 2), "lls_its": solver.setup_stats["lls_its"],
                    "lls_relgrad": solver.setup_stats["lls_relgrad"], "lls_maxit": GENERAL["lls_maxit"],
                    "nnz_pattern": solver.setup_stats["nnz_pattern"], "r": solver.setup_stats["r"],
+                   "sell_sigma": solver.setup_stats["sell_sigma"], "sell_split": solver.setup_stats["sell_split"],
                    "outer_its": stats[-1]["outer_its"], "inner_its_avg": round(stats[-1]["inner_its_avg"], 2),
                    "relres_after_step": relres, "status": stats[-1]["status"], "converged": False,
                    "solves_per_s": None},
