@@ -27,4 +27,14 @@ from .asss import (  # noqa: F401
     tfqmr_cycle,
     fgmres_cycle,
 )
+from .ildl import (  # noqa: F401
+    FactoredSkew,
+    colour_order,
+    colouring_priorities,
+    ildl0,
+    jp_colouring,
+    splitmix64_u64,
+    structural_pattern,
+    values_on_pattern,
+)
 from .matching import matching_costs, matching_scaling, max_product_matching  # noqa: F401

@@ -8,7 +8,8 @@ Readings of the paper taken where it is silent or ambiguous (listed in full in t
 design notes of the repository):
   R1 scaling: identity permutation, D_r = 1/row-max|a|, then D_c = 1/col-max|D_r a|.
   R3 the LLS minimiser itself is the result (solver-independent).
-  R5 incomplete LDL^T restricted to 1x1 pivots without fill: L~ = |diag(A^)|^(1/2).
+  R5 incomplete LDL^T restricted to 1x1 pivots without fill: L~ = |diag(A^)|^(1/2);
+     factor="ildl0": the no-fill incomplete L D L^T in a multicolour order (ildl.py).
   R7 Lanczos start vector from a counter-based splitmix64 stream; optional full
      re-orthogonalisation (two classical Gram-Schmidt passes).
   R8 SMW written in the inverse-free form  S^-1 - X Sig (I + U^T X Sig)^-1 U^T S^-1.
@@ -223,7 +224,8 @@ def skew_lanczos(J, q1, k: int, reorth: bool = True, breakdown_tol: float = 1e-1
     Gram-Schmidt passes before its norm is taken (reading R7).  The process stops
     early when alpha_i <= breakdown_tol * alpha_1 (or alpha_1 == 0).
     Returns (Q n x k_eff, alpha (k_eff-1,))."""
-    J = sp.csr_matrix(J)
+    if sp.issparse(J) or isinstance(J, np.ndarray):
+        J = sp.csr_matrix(J)
     n = J.shape[0]
     k = int(min(k, n))
     if k <= 0:
@@ -458,12 +460,17 @@ class AsssOracle:
     combined rank-(r+k) SMW data of Eq. (preconditioner)/(smw): X = S_bar^-1 U_bar
     by multi-RHS mrs and K = I + U_bar^T X Sig_bar.
     Solve: outer Krylov on  A_cal y = W P D_r b,  A_cal = W Abar S W, with
-    preconditioner P^-1 applied via mrs + SMW; x = D_c S W y (§3, Eq. modified)."""
+    preconditioner P^-1 applied via mrs + SMW; x = D_c S W y (§3, Eq. modified).
+
+    factor="ildl0" replaces the diagonal factor by the no-fill incomplete L D L^T of M^
+    (§3 after Eq. absfac, §4.1 ~ildl(0); ildl.py): L~^-1 and L~^-T are applied by
+    triangular solves (F and G of FactoredSkew), A_cal = F Abar S G, J~ = F J^ G, the
+    right-hand side F P D_r b and x = D_c S G y; M~_r = sign(D) - I."""
 
     def __init__(self, A, S_pattern=None, gamma=1.0, k=20, reorth=True, seed=0x5eed,
                  inner_tol=1e-10, inner_maxit=1000, setup_tol=None, r_max=256,
                  row_perm=None, dr=None, dc=None, q1=None, lls_method="auto",
-                 zero_tol=1e-14):
+                 zero_tol=1e-14, factor="diag"):
         A = sp.csr_matrix(A, dtype=np.float64)
         A.sort_indices()
         self.A = A
@@ -474,11 +481,28 @@ class AsssOracle:
             Ab = self.Abar
             S_pattern = sp.csr_matrix((np.ones(Ab.nnz), Ab.indices, Ab.indptr), shape=Ab.shape)
         self.S = skew_symmetrizer(self.Abar, S_pattern, gamma, lls_method)
-        self.d, self.w, neg = shift_and_lowrank(self.Abar, self.S, zero_tol)
+        self.factor = factor
+        self.fac = None
+        if factor == "ildl0":
+            from . import ildl
+            C = (sp.csr_matrix(self.Abar) @ sp.csr_matrix(self.S)).tocsr()
+            P = ildl.structural_pattern(self.Abar, self.S)
+            MP = ildl.values_on_pattern(0.5 * (C + C.T), P)
+            self.colour, self.jp_rounds = ildl.jp_colouring(P, ildl.colouring_priorities(seed, n))
+            self.order = ildl.colour_order(self.colour)
+            self.L, self.d = ildl.ildl0(MP, self.order, zero_tol)
+            neg = np.flatnonzero(self.d < 0)
+            self.w = np.ones(n)                 # L~ enters through F and G instead
+            self.fac = ildl.FactoredSkew(self.L, self.d, self.order,
+                                         inner_skew_operator(self.Abar, self.S, self.w))
+        elif factor == "diag":
+            self.d, self.w, neg = shift_and_lowrank(self.Abar, self.S, zero_tol)
+        else:
+            raise ValueError(f"unknown factor {factor!r}")
         self.prec2 = neg.size > r_max          # Eq. (preconditioner2) fallback
         self.neg = np.zeros(0, dtype=np.int64) if self.prec2 else neg
         self.r = self.neg.size
-        self.Jt = inner_skew_operator(self.Abar, self.S, self.w)
+        self.Jt = self.fac if self.fac is not None else inner_skew_operator(self.Abar, self.S, self.w)
         if q1 is None:
             q1 = splitmix64_uniform(seed, n)
         self.Q, self.alpha = skew_lanczos(self.Jt, q1, k, reorth)
@@ -512,7 +536,7 @@ class AsssOracle:
 
     def prec_dense(self):
         """P = M~_r + I + J~ as a dense matrix (tiny problems, tests only)."""
-        P = self.Jt.toarray() + np.eye(self.n)
+        P = (self.fac.dense() if self.fac is not None else self.Jt.toarray()) + np.eye(self.n)
         P[self.neg, self.neg] -= 2.0
         return P
 
@@ -552,7 +576,13 @@ class AsssOracle:
         return z - X @ (SigT @ sla.lu_solve(lu, wv))
 
     def apply_op(self, v, transpose=False):
-        """A_cal v = W Abar S W v, or A_cal^T v = W S^T Abar^T W v."""
+        """A_cal v = W Abar S W v, or A_cal^T v = W S^T Abar^T W v (with the incomplete
+        factor: F Abar S G v, or F S^T Abar^T G v)."""
+        f = self.fac
+        if f is not None:
+            if transpose:
+                return f.F(self.Sw.T @ (self.Aw.T @ f.G(v)))
+            return f.F(self.Aw @ (self.Sw @ f.G(v)))
         if transpose:
             return self.Sw.T @ (self.Aw.T @ v)
         return self.Aw @ (self.Sw @ v)
@@ -611,11 +641,14 @@ class AsssOracle:
         b = np.asarray(b, dtype=np.float64)
         A = self.A
 
-        def to_scaled(r):          # W P D_r r
-            return self.w * (self.dr * r)[self.perm]
+        f = self.fac
 
-        def from_scaled(dy):       # D_c S W dy
-            return self.dc * (self.S @ (self.w * dy))
+        def to_scaled(r):          # W P D_r r  (F P D_r r)
+            t = self.w * (self.dr * r)[self.perm]
+            return f.F(t) if f is not None else t
+
+        def from_scaled(dy):       # D_c S W dy  (D_c S G dy)
+            return self.dc * (self.S @ (f.G(dy) if f is not None else self.w * dy))
 
         return self._refine(b, lambda x: A @ x, to_scaled, from_scaled, False, tol,
                             maxit, outer, restart)
@@ -629,12 +662,15 @@ class AsssOracle:
         AT = A.T.tocsr()
         n = self.n
 
-        def to_scaled(r):          # W S^T D_c r
-            return self.w * (self.S.T @ (self.dc * r))
+        f = self.fac
 
-        def from_scaled(dmu):      # D_r P^T W dmu
+        def to_scaled(r):          # W S^T D_c r  (F S^T D_c r)
+            t = self.w * (self.S.T @ (self.dc * r))
+            return f.F(t) if f is not None else t
+
+        def from_scaled(dmu):      # D_r P^T W dmu  (D_r P^T G dmu)
             t = np.zeros(n)
-            t[self.perm] = self.w * dmu
+            t[self.perm] = f.G(dmu) if f is not None else self.w * dmu
             return self.dr * t
 
         lam, st = self._refine(g, lambda v: AT @ v, to_scaled, from_scaled, True, tol,
