@@ -121,11 +121,21 @@ typedef struct {
     int    sell_split;        /* entries per lane in one SELL-C work unit: wider slices are cut
                                  into parts taken by different warps; >= 64, or 0 (picked with
                                  sell_sigma, else 1024). Both only change summation order      */
+    int    factor;            /* the factor L~ of M^ = (A^ + A^T)/2 (§3 after Eq. absfac):
+                                 ASSS_FACTOR_DIAG: 1x1 pivots without fill, L~ = |diag(A^)|^1/2;
+                                 ASSS_FACTOR_ILDL0: the no-fill incomplete L D L^T (§4.1's
+                                 ~ildl(0); 1x1 pivots, factored in a multicolour order from
+                                 Jones-Plassmann rounds seeded by `seed`), J~ = L~^-1 J^ L~^-T
+                                 applied by triangular solves (one parallel step per colour).
+                                 Not with q_bf16 (ASSS_ERR_UNSUPPORTED) nor in asss_setup_batched;
+                                 rhs_block is ignored                                           */
 } asss_options;
 
 enum { ASSS_SCALING_MAXES = 0, ASSS_SCALING_MATCHING = 1 };
 
 enum { ASSS_FORMAT_AUTO = 0, ASSS_FORMAT_SELL = 1, ASSS_FORMAT_DIAG = 2 };
+
+enum { ASSS_FACTOR_DIAG = 0, ASSS_FACTOR_ILDL0 = 1 };
 
 typedef struct {
     int    status;            /* asss_status of the call                                        */
@@ -149,6 +159,7 @@ typedef struct {
     int    sell_sigma;        /* set-up, J~ in SELL-C: sorting window in rows (0: natural order) */
     int    sell_split;        /* set-up, J~ in SELL-C: entries per lane of one work unit; both picked
                                  by timing mrs steps for systems of 10^5 rows and more (FP32 path) */
+    int    factor_colours;    /* set-up, ASSS_FACTOR_ILDL0: colours of the factorization order  */
 } asss_stats;
 
 typedef struct asss_handle asss_handle;
@@ -201,6 +212,16 @@ asss_status asss_export(asss_handle* h, double* dr, double* dc, double* w, doubl
 /* The row permutation of Eq. mc64 used by the handle: row i of Abar is row
  * row_perm[i] of D_r A D_c (n entries; the identity unless given or matched). */
 asss_status asss_export_permutation(asss_handle* h, int32_t* row_perm);
+
+/* The incomplete factor of a handle set up with ASSS_FACTOR_ILDL0 (host or device
+ * pointers, each may be NULL): colour (n) of every row in the factorization order,
+ * and L, strictly lower in that order, in the original indexing as CSR: l_row_ptr
+ * (n+1), l_col / l_val (l_cap >= the entry count, which *l_nnz receives; the columns
+ * of a row ascend).  (I + L) D (I + L)^T equals M^ on M^'s pattern; D is the `d` of
+ * asss_export (which exports w = 1 for such a handle).  ASSS_ERR_ARG without a
+ * factor or with l_cap too small. */
+asss_status asss_export_factor(asss_handle* h, int32_t* colour, int64_t* l_row_ptr, int32_t* l_col, double* l_val,
+                               int64_t l_cap, int64_t* l_nnz);
 
 void asss_destroy(asss_handle* h);
 

@@ -48,10 +48,12 @@ class Options(C.Structure):
                 ("seed", C.c_uint64), ("lls_tol", C.c_double), ("lls_maxit", C.c_int),
                 ("zero_tol", C.c_double), ("wait_timeout_ms", C.c_double), ("stream", C.c_void_p),
                 ("inner_format", C.c_int), ("q_bf16", C.c_int), ("s_values", C.c_void_p),
-                ("scaling", C.c_int), ("rhs_block", C.c_int), ("sell_sigma", C.c_int), ("sell_split", C.c_int)]
+                ("scaling", C.c_int), ("rhs_block", C.c_int), ("sell_sigma", C.c_int), ("sell_split", C.c_int),
+                ("factor", C.c_int)]
 
 FORMATS = {"auto": 0, "sell": 1, "diag": 2}
 SCALINGS = {"maxes": 0, "matching": 1}
+FACTORS = {"diag": 0, "ildl0": 1}
 
 
 class Stats(C.Structure):
@@ -62,7 +64,7 @@ class Stats(C.Structure):
                 ("lls_relgrad", C.c_double), ("nnz_pattern", C.c_longlong),
                 ("t_setup_ms", C.c_double), ("t_solve_ms", C.c_double), ("t_inner_ms", C.c_double),
                 ("inner_bytes", C.c_longlong), ("inner_launches", C.c_int), ("sell_sigma", C.c_int),
-                ("sell_split", C.c_int)]
+                ("sell_split", C.c_int), ("factor_colours", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -72,7 +74,7 @@ EXPORTED = ["asss_default_options", "asss_setup", "asss_solve", "asss_solve_adjo
             "asss_apply_operator", "asss_apply_preconditioner", "asss_export", "asss_destroy",
             "asss_status_str", "asss_last_error", "asss_skew_symmetrizer", "asss_skew_lanczos",
             "asss_mrs", "asss_mrs_multi", "asss_kernel_launches", "asss_mrs_noalloc", "asss_export_permutation",
-            "asss_matching_scaling", "asss_setup_batched",
+            "asss_matching_scaling", "asss_export_factor", "asss_setup_batched",
             "asss_solve_batched", "asss_destroy_batched", "asss_batch_cta_threads"]
 
 _lib = None
@@ -120,6 +122,7 @@ def lib():
     L.asss_mrs.argtypes = [pCSR, C.c_int, P, P, C.c_double, C.c_double, P, P, C.c_double, C.c_int,
                            C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double), P]
     L.asss_export_permutation.argtypes = [P, P]
+    L.asss_export_factor.argtypes = [P, P, P, P, P, C.c_int64, C.POINTER(C.c_int64)]
     L.asss_matching_scaling.argtypes = [pCSR, P, P, P, C.POINTER(C.c_int), P]
     L.asss_mrs_multi.argtypes = [pCSR, C.c_int, P, P, C.c_double, C.c_double, C.c_int, P, C.c_int64, P, C.c_int64,
                                  C.c_double, C.c_int, C.c_int, C.c_int, P, P, P]
@@ -138,7 +141,7 @@ def lib():
     for f in ("asss_setup", "asss_solve", "asss_solve_adjoint", "asss_apply_operator",
               "asss_apply_preconditioner", "asss_export", "asss_skew_symmetrizer",
               "asss_skew_lanczos", "asss_mrs", "asss_mrs_multi", "asss_setup_batched", "asss_solve_batched",
-              "asss_export_permutation", "asss_matching_scaling"):
+              "asss_export_permutation", "asss_matching_scaling", "asss_export_factor"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -228,6 +231,9 @@ def _options(keep, **kw):
     scl = kw.pop("scaling", None)
     if scl is not None:
         o.scaling = SCALINGS.get(scl, scl)
+    fac = kw.pop("factor", None)
+    if fac is not None:
+        o.factor = FACTORS.get(fac, fac)
     stream = kw.pop("stream", None)
     if stream is not None:
         o.stream = stream if isinstance(stream, int) else stream.cuda_stream
@@ -254,6 +260,7 @@ class Solver:
     seed, lls_tol, lls_maxit, zero_tol, wait_timeout_ms, row_perm, dr, dc, stream, s_values,
     scaling ('maxes' | 'matching': how Eq. mc64's P, D_r, D_c are found when none is given),
     rhs_block (several right-hand sides in lockstep blocks sharing multi-column mrs launches),
+    factor ('diag' | 'ildl0': the no-fill incomplete L D L^T of M^, §3 / §4.1 ~ildl(0)),
     sell_sigma, sell_split (SELL-C storage of J~: sorting window and work-unit width; 0 = tuned)
     (saved S values to resume the set-up from, e.g. ``export(nnz)["s_val"]`` of an
     earlier solver for the same matrix).
@@ -349,6 +356,23 @@ class Solver:
         out = np.empty(self.n, dtype=np.int32)
         _check("asss_export_permutation", lib().asss_export_permutation(self._h, out.ctypes.data))
         return out
+
+    def export_factor(self):
+        """The incomplete factor (factor='ildl0'): colour of each row and L (strictly
+        lower in the (colour, index) order, original indexing) as scipy CSR."""
+        import scipy.sparse as sp
+        n = self.n
+        nl = C.c_int64(0)
+        _check("asss_export_factor", lib().asss_export_factor(self._h, None, None, None, None, 0, C.byref(nl)))
+        colour = np.empty(n, dtype=np.int32)
+        rp = np.empty(n + 1, dtype=np.int64)
+        ci = np.empty(max(nl.value, 1), dtype=np.int32)
+        lv = np.empty(max(nl.value, 1))
+        _check("asss_export_factor", lib().asss_export_factor(self._h, colour.ctypes.data, rp.ctypes.data,
+                                                              ci.ctypes.data, lv.ctypes.data, nl.value,
+                                                              C.byref(nl)))
+        L = sp.csr_matrix((lv[:nl.value], ci[:nl.value], rp), shape=(n, n))
+        return colour, L
 
     def export(self, s_nnz):
         n = self.n

@@ -503,6 +503,11 @@ struct asss_handle {
     DSkewDia<double> D64;
     DSkewDia<float> D32;
     bool use_dia = false;
+    // incomplete L D L^T (options.factor = ASSS_FACTOR_ILDL0): J~ in factored form, W = 1
+    // in the operators above and L~ applied by triangular solves instead
+    bool factored = false;
+    IldlFactor fac;
+    DBuf<double> fa, fb;
     DBuf<double> dr, dc, w, d;
     DBuf<int> perm;
     bool has_perm = false;
@@ -567,6 +572,7 @@ static void fill_defaults(asss_options* o) {
     o->rhs_block = 0;
     o->sell_sigma = 0;
     o->sell_split = 0;
+    o->factor = ASSS_FACTOR_DIAG;
 }
 
 static int pick_kp(int k) {
@@ -579,8 +585,17 @@ static int pick_kp(int k) {
 // ---------------------------------------------------------------------------
 // skew-Lanczos (Fig. 2) with optional two-pass classical Gram-Schmidt
 // ---------------------------------------------------------------------------
+// J~ v in factored form: F (J^ (G v)), ta and tb n-vectors of scratch
+static asss_status apply_jt_factored(const Ctx& c, IldlFactor& F, const DCsr& Jh, const double* v, double* out,
+                                     double* ta, double* tb) {
+    ASSS_TRY(ildl_G(c, F, v, ta));
+    ASSS_TRY(spmv(Jh, ta, tb, nullptr, c.stream));
+    return ildl_F(c, F, tb, out);
+}
+
 static asss_status lanczos(const Ctx& c, const DCsr& J, const double* q1, int n, int k, int reorth,
-                           DBuf<double>& Qcm, std::vector<double>& alpha, int* k_eff) {
+                           DBuf<double>& Qcm, std::vector<double>& alpha, int* k_eff, IldlFactor* F = nullptr,
+                           double* ta = nullptr, double* tb = nullptr) {
     cudaStream_t s = c.stream;
     if (k > n) k = n;
     alpha.assign(k > 1 ? k - 1 : 0, 0.0);
@@ -603,7 +618,8 @@ static asss_status lanczos(const Ctx& c, const DCsr& J, const double* q1, int n,
     ASSS_TRY(vscale(Qcm.p, q1, 1.0 / sqrt(nn), n, s));
     int kk = 1;
     for (int i = 1; i < k; ++i) {
-        ASSS_TRY(spmv(J, Qcm.p + (size_t)(i - 1) * n, z.p, nullptr, s));
+        if (F) ASSS_TRY(apply_jt_factored(c, *F, J, Qcm.p + (size_t)(i - 1) * n, z.p, ta, tb));
+        else ASSS_TRY(spmv(J, Qcm.p + (size_t)(i - 1) * n, z.p, nullptr, s));
         if (i >= 2) ASSS_TRY(vaxpy(z.p, Qcm.p + (size_t)(i - 2) * n, -alpha[i - 2], n, s));
         if (reorth) {
             for (int pass = 0; pass < 2; ++pass) {
@@ -646,6 +662,7 @@ static asss_status ensure_smw(asss_handle* h, int tr) {
     MrsOperator op;
     op.J64 = h->use_dia ? nullptr : &h->J64;
     op.D64 = h->use_dia ? &h->D64 : nullptr;
+    op.F = h->factored ? &h->fac : nullptr;
     op.k = h->k;
     op.kp = h->kp;
     op.Q64 = h->Q64.p;
@@ -654,7 +671,7 @@ static asss_status ensure_smw(asss_handle* h, int tr) {
     double sign = tr ? -1.0 : 1.0;
     std::vector<int> negh(r);
     if (r) ASSS_CUDA(cudaMemcpy(negh.data(), h->neg.p, sizeof(int) * r, cudaMemcpyDeviceToHost));
-    if (h->kp <= MRS_MULTI_KPMAX) {
+    if (h->kp <= MRS_MULTI_KPMAX && !h->factored) {
         // S_bar X = U_bar as App. B's simultaneous iterations: the k + r columns share
         // every pass over J~ and Q_k (groups of up to 8 per launch)
         DBuf<double> Ub;
@@ -731,6 +748,7 @@ static asss_status apply_prec(asss_handle* h, int tr, const double* u, double* o
     op.J32 = (!h->use_dia && h->J32.n) ? &h->J32 : nullptr;
     op.D64 = h->use_dia ? &h->D64 : nullptr;
     op.D32 = (h->use_dia && h->D32.n) ? &h->D32 : nullptr;
+    op.F = h->factored ? &h->fac : nullptr;
     op.k = h->k;
     op.kp = h->kp;
     op.Q64 = h->Q64.p;
@@ -784,6 +802,19 @@ static asss_status ensure_adjoint_ops(asss_handle* h) {
 // out = A_cal v or A_cal^T v
 static asss_status apply_op(asss_handle* h, int tr, const double* v, double* out) {
     cudaStream_t s = h->ctx.stream;
+    if (h->factored) {
+        // F A^ G v or F A^T G v (Eq. preconditioner with the incomplete factor)
+        ASSS_TRY(ildl_G(h->ctx, h->fac, v, h->fa.p));
+        if (!tr) {
+            ASSS_TRY(spmv(h->Sw, h->fa.p, h->t3.p, nullptr, s));
+            ASSS_TRY(spmv(h->Aw, h->t3.p, h->fb.p, nullptr, s));
+        } else {
+            ASSS_TRY(ensure_adjoint_ops(h));
+            ASSS_TRY(spmv(h->AwT, h->fa.p, h->t3.p, nullptr, s));
+            ASSS_TRY(spmv(h->SwT, h->t3.p, h->fb.p, nullptr, s));
+        }
+        return ildl_F(h->ctx, h->fac, h->fb.p, out);
+    }
     if (!tr) {
         ASSS_TRY(spmv(h->Sw, v, h->t3.p, nullptr, s));
         ASSS_TRY(spmv(h->Aw, h->t3.p, out, nullptr, s));
@@ -1067,12 +1098,15 @@ static asss_status refine(asss_handle* h, int tr, const double* rhs, double* x, 
             break;
         }
         if (!tr) {
-            k_to_scaled_fwd<<<nb, 256, 0, s>>>(r.p, h->dr.p, h->w.p, perm, n, rh.p);  // W P D_r r
+            // W P D_r r  (F P D_r r with the incomplete factor, W = 1 there)
+            k_to_scaled_fwd<<<nb, 256, 0, s>>>(r.p, h->dr.p, h->w.p, perm, n, h->factored ? h->fa.p : rh.p);
             ASSS_CHECK_LAUNCH();
+            if (h->factored) ASSS_TRY(ildl_F(h->ctx, h->fac, h->fa.p, rh.p));
         } else {
-            ASSS_TRY(vmul(h->t1.p, h->dc.p, r.p, n, s));  // W S^T D_c r
+            ASSS_TRY(vmul(h->t1.p, h->dc.p, r.p, n, s));  // W S^T D_c r  (F S^T D_c r)
             ASSS_TRY(spmv(h->ST, h->t1.p, h->t2.p, nullptr, s));
-            ASSS_TRY(vmul(rh.p, h->w.p, h->t2.p, n, s));
+            if (h->factored) ASSS_TRY(ildl_F(h->ctx, h->fac, h->t2.p, rh.p));
+            else ASSS_TRY(vmul(rh.p, h->w.p, h->t2.p, n, s));
         }
         double eta = fmin(0.5, 0.5 * o.outer_tol * bn / rn);
         int budget = o.outer_maxit - st->outer_its;
@@ -1087,13 +1121,17 @@ static asss_status refine(asss_handle* h, int tr, const double* rhs, double* x, 
         st->cycles += 1;
         h->tr.mark(s, Tracer::REFINE);
         if (!tr) {
-            ASSS_TRY(vmul(h->t1.p, h->w.p, dy.p, n, s));  // x += D_c S W dy
+            // x += D_c S W dy  (D_c S G dy)
+            if (h->factored) ASSS_TRY(ildl_G(h->ctx, h->fac, dy.p, h->t1.p));
+            else ASSS_TRY(vmul(h->t1.p, h->w.p, dy.p, n, s));
             ASSS_TRY(spmv(h->S, h->t1.p, h->t2.p, nullptr, s));
             k_axpy_mul<<<nb, 256, 0, s>>>(x, h->dc.p, h->t2.p, n);
             ASSS_CHECK_LAUNCH();
             ASSS_TRY(spmv(h->A, x, h->t1.p, nullptr, s));
         } else {
-            k_from_scaled_adj<<<nb, 256, 0, s>>>(dy.p, h->dr.p, h->w.p, perm, n, x);  // lambda += D_r P^T W dmu
+            // lambda += D_r P^T W dmu  (D_r P^T G dmu)
+            if (h->factored) ASSS_TRY(ildl_G(h->ctx, h->fac, dy.p, h->fa.p));
+            k_from_scaled_adj<<<nb, 256, 0, s>>>(h->factored ? h->fa.p : dy.p, h->dr.p, h->w.p, perm, n, x);
             ASSS_CHECK_LAUNCH();
             ASSS_TRY(spmv(h->AT, x, h->t1.p, nullptr, s));
         }
@@ -1139,6 +1177,7 @@ static asss_status apply_prec_block(asss_handle* h, int tr, int nc, const double
     op.J32 = (!h->use_dia && h->J32.n) ? &h->J32 : nullptr;
     op.D64 = h->use_dia ? &h->D64 : nullptr;
     op.D32 = (h->use_dia && h->D32.n) ? &h->D32 : nullptr;
+    op.F = h->factored ? &h->fac : nullptr;
     op.k = h->k;
     op.kp = h->kp;
     op.Q64 = h->Q64.p;
@@ -1454,9 +1493,14 @@ static asss_status do_setup(asss_handle* h, const asss_csr* Ain, asss_stats* st)
         (o.precision != ASSS_PREC_FP64 && o.precision != ASSS_PREC_MIXED) ||
         (o.outer != ASSS_OUTER_TFQMR && o.outer != ASSS_OUTER_FGMRES) || (o.outer == ASSS_OUTER_FGMRES && o.restart < 1) ||
         o.inner_format < ASSS_FORMAT_AUTO || o.inner_format > ASSS_FORMAT_DIAG ||
-        (o.scaling != ASSS_SCALING_MAXES && o.scaling != ASSS_SCALING_MATCHING)) {
+        (o.scaling != ASSS_SCALING_MAXES && o.scaling != ASSS_SCALING_MATCHING) ||
+        (o.factor != ASSS_FACTOR_DIAG && o.factor != ASSS_FACTOR_ILDL0)) {
         set_error("invalid option");
         return ASSS_ERR_ARG;
+    }
+    if (o.factor == ASSS_FACTOR_ILDL0 && o.q_bf16) {
+        set_error("the incomplete factor reads Q_k in FP32 or FP64 only (q_bf16 unsupported)");
+        return ASSS_ERR_UNSUPPORTED;
     }
     ASSS_TRY(upload_csr(Ain, h->A, true, s));
     int n = h->A.n;
@@ -1585,7 +1629,20 @@ static asss_status do_setup(asss_handle* h, const asss_csr* Ain, asss_stats* st)
     ASSS_TRY(h->w.alloc(n));
     k_diag_w<<<cdiv(n, 256), 256, 0, s>>>(Cval.p, diagpos.p, n, h->d.p, h->w.p);
     ASSS_CHECK_LAUNCH();
-    {
+    h->factored = o.factor == ASSS_FACTOR_ILDL0;
+    if (h->factored) {
+        // the no-fill incomplete L D L^T of M^ (§3 after Eq. absfac, §4.1 ~ildl(0)):
+        // d becomes the pivots D, W = 1 (L~ = (I + L)|D|^1/2 is applied by triangular solves)
+        ASSS_TRY(vfill(h->w.p, 1.0, n, s));
+        int nzero = 0;
+        ASSS_TRY(ildl_build(c, P, mirror.p, Cval.p, h->d.p, o.seed, o.zero_tol, o.precision == ASSS_PREC_MIXED,
+                            h->fac, &nzero));
+        if (nzero) {
+            set_error("%d zero pivot(s) in the incomplete L D L^T", nzero);
+            return ASSS_ERR_ZERO_DIAG;
+        }
+        st->factor_colours = h->fac.ncol;
+    } else {
         DBuf<unsigned long long> mx;
         ASSS_TRY(mx.alloc(1));
         ASSS_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(unsigned long long), s));
@@ -1638,7 +1695,12 @@ static asss_status do_setup(asss_handle* h, const asss_csr* Ain, asss_stats* st)
     ASSS_TRY(h->Jt.v.alloc(h->Jt.nnz));
     k_assemble_jt<<<cdiv(n, 256), 256, 0, s>>>(n, h->Jt.rp.p, h->Jt.ci.p, mirror.p, Cval.p, h->w.p, h->Jt.v.p);
     ASSS_CHECK_LAUNCH();
-    if (o.inner_format != ASSS_FORMAT_SELL) {
+    if (h->factored) {
+        // Jt holds J^ itself (W = 1); the inner kernel applies L~^-1 J^ L~^-T
+        ASSS_TRY(ildl_set_skew(c, h->fac, h->Jt, o.precision == ASSS_PREC_MIXED));
+        ASSS_TRY(h->fa.alloc(n));
+        ASSS_TRY(h->fb.alloc(n));
+    } else if (o.inner_format != ASSS_FORMAT_SELL) {
         int ok = 0;
         ASSS_TRY(build_skew_dia<double>(h->Jt, 64, 0.5, h->D64, &ok, s));
         if (ok && o.precision == ASSS_PREC_MIXED) ASSS_TRY(build_skew_dia<float>(h->Jt, 64, 0.5, h->D32, &ok, s));
@@ -1648,7 +1710,7 @@ static asss_status do_setup(asss_handle* h, const asss_csr* Ain, asss_stats* st)
             return ASSS_ERR_UNSUPPORTED;
         }
     }
-    if (!h->use_dia) {
+    if (!h->use_dia && !h->factored) {
         int sigma = o.sell_sigma, split = o.sell_split;
         if (sigma == 0 && split == 0 && o.precision == ASSS_PREC_MIXED && n >= 100000)
             ASSS_TRY(tune_sell(h, &sigma, &split));
@@ -1674,7 +1736,8 @@ static asss_status do_setup(asss_handle* h, const asss_csr* Ain, asss_stats* st)
         DBuf<double> q1;
         ASSS_TRY(q1.alloc(n));
         ASSS_TRY(splitmix64_fill(o.seed, n, q1.p, s));
-        ASSS_TRY(lanczos(c, h->Jt, q1.p, n, o.k_lanczos, o.reorth, h->Qcm, h->alpha_h, &h->k));
+        ASSS_TRY(lanczos(c, h->Jt, q1.p, n, o.k_lanczos, o.reorth, h->Qcm, h->alpha_h, &h->k,
+                         h->factored ? &h->fac : nullptr, h->fa.p, h->fb.p));
     }
     h->kp = pick_kp(h->k);
     if (h->kp < 0) {
@@ -1809,7 +1872,7 @@ static asss_status solve_common(asss_handle* h, int tr, int nrhs, const double* 
     // several right-hand sides of a forward FGMRES solve: lockstep blocks of up to 8
     // columns whose preconditioner applications share each pass over J~ and Q_k
     const bool block = h->opt.rhs_block && !tr && nrhs >= 2 && h->opt.outer == ASSS_OUTER_FGMRES &&
-                       h->kp <= MRS_MULTI_KPMAX && !h->Q16.p;
+                       h->kp <= MRS_MULTI_KPMAX && !h->Q16.p && !h->factored;
     if (block) {
         const int B = asss_handle::BLK;
         if (!h->blk_b.p) {
@@ -1976,6 +2039,37 @@ asss_status asss_export(asss_handle* h, double* dr, double* dc, double* w, doubl
     if (alpha && h->k > 1)
         ASSS_CUDA(cudaMemcpyAsync(alpha, h->alpha_d.p, sizeof(double) * (h->k - 1), cudaMemcpyDefault, s));
     if (neg && h->r) ASSS_CUDA(cudaMemcpyAsync(neg, h->neg.p, sizeof(int) * h->r, cudaMemcpyDefault, s));
+    ASSS_CUDA(cudaStreamSynchronize(s));
+    return ASSS_OK;
+}
+
+asss_status asss_export_factor(asss_handle* h, int32_t* colour, int64_t* l_row_ptr, int32_t* l_col, double* l_val,
+                               int64_t l_cap, int64_t* l_nnz) {
+    if (!h) {
+        set_error("handle is NULL");
+        return ASSS_ERR_ARG;
+    }
+    if (!h->factored) {
+        set_error("the handle has no incomplete factor (options.factor)");
+        return ASSS_ERR_ARG;
+    }
+    IldlFactor& F = h->fac;
+    const int n = h->n;
+    if (l_nnz) *l_nnz = F.nl;
+    if ((l_col || l_val) && l_cap < F.nl) {
+        set_error("l_cap %lld below the %lld entries of L", (long long)l_cap, (long long)F.nl);
+        return ASSS_ERR_ARG;
+    }
+    cudaStream_t s = h->ctx.stream;
+    if (colour) ASSS_CUDA(cudaMemcpyAsync(colour, F.colour.p, sizeof(int) * n, cudaMemcpyDefault, s));
+    if (l_row_ptr) {
+        std::vector<int> rp(n + 1);
+        ASSS_CUDA(cudaMemcpyAsync(rp.data(), F.lrp.p, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost, s));
+        ASSS_CUDA(cudaStreamSynchronize(s));
+        for (int i = 0; i <= n; ++i) l_row_ptr[i] = rp[i];
+    }
+    if (l_col && F.nl) ASSS_CUDA(cudaMemcpyAsync(l_col, F.lci.p, sizeof(int) * F.nl, cudaMemcpyDefault, s));
+    if (l_val && F.nl) ASSS_CUDA(cudaMemcpyAsync(l_val, F.lv.p, sizeof(double) * F.nl, cudaMemcpyDefault, s));
     ASSS_CUDA(cudaStreamSynchronize(s));
     return ASSS_OK;
 }
@@ -2481,6 +2575,10 @@ asss_status asss_setup_batched(int nmat, const asss_csr* const* A, const asss_op
         return ASSS_ERR_ARG;
     }
     *out = nullptr;
+    if (opt && opt->factor != ASSS_FACTOR_DIAG) {
+        set_error("the batched form runs with the diagonal factor only");
+        return ASSS_ERR_UNSUPPORTED;
+    }
     auto t0 = std::chrono::steady_clock::now();
     asss_batch* B = new asss_batch();
     if (opt) B->opt = *opt;

@@ -51,6 +51,8 @@ asss_status vmul(double* y, const double* a, const double* b, int n, cudaStream_
 asss_status vcopy(double* y, const double* x, int n, cudaStream_t s);
 asss_status vfill(double* y, double v, int n, cudaStream_t s);
 
+struct IldlFactor;
+
 // mrs.cu
 struct MrsOperator {
     // J~ (exactly skew) in SELL-C, FP64 and/or FP32 copies
@@ -65,6 +67,8 @@ struct MrsOperator {
     const void* Q16 = nullptr;   // BF16 n x kp16 row-major (FP32 solve only); used instead of Q32 when set
     int kp16 = 0;
     const double* alpha = nullptr;  // device, k-1 values (S_k superdiagonal)
+    // factored J~ = L~^-1 J^ L~^-T (incomplete L D L^T); used instead of the storages above
+    const IldlFactor* F = nullptr;
 };
 
 struct MrsTotals {
@@ -118,6 +122,33 @@ asss_status mrs_multi_solve(const Ctx& c, const MrsOperator& op, bool fp32, doub
 asss_status mrs_multi_solve_cols(const Ctx& c, const MrsOperator& op, bool fp32, double shift, double sign,
                                  int ncol, const double* const* B, double* const* X64, float* const* X32, double tol,
                                  int maxit, int* its, double* ratio, MrsTotals* tot = nullptr);
+
+// ildl.cu: no-fill incomplete L D L^T of M^ in a multicolour order (§3 after Eq.
+// absfac, §4.1 ~ildl(0)); original indexing, "lower" = of a smaller colour.
+constexpr int ILDL_MAXCOL = 256;
+struct IldlFactor {
+    int n = 0, ncol = 0, rounds = 0;
+    int64_t nl = 0, nu = 0, nj = 0;
+    std::vector<int> hls;            // ncol + 1 level offsets (host)
+    DBuf<int> ls;                    // the same on the device
+    DBuf<int> colour, lvl;           // colour of each vertex; vertices by (colour, index)
+    DBuf<int> lrp, lci, urp, uci;    // L: entries of smaller colour; U: of larger colour
+    DBuf<double> lv, uv, wd;         // l_ij; the mirrored l_ji; |D|^-1/2
+    DBuf<float> lv32, uv32, wd32, jv32;
+    DBuf<double> ft, fw;             // scratch of one application
+    DBuf<float> ft32, fw32;
+    const int* jrp = nullptr;        // J^ (exactly skew) on the pattern, not owned
+    const int* jci = nullptr;
+    const double* jv = nullptr;
+};
+// P: symmetric pattern of A^ (diagonal included), mirror[e] = position of the transposed
+// entry, Cval = A^ on P; d: diag(A^) on entry, the pivots D on return; *nzero: pivots
+// below zero_tol * max|diag|
+asss_status ildl_build(const Ctx& c, const DCsr& P, const int* mirror, const double* Cval, double* d,
+                       uint64_t seed, double zero_tol, bool fp32, IldlFactor& F, int* nzero);
+asss_status ildl_set_skew(const Ctx& c, IldlFactor& F, const DCsr& Jh, bool fp32);
+asss_status ildl_F(const Ctx& c, IldlFactor& F, const double* v, double* out);  // |D|^-1/2 (I + L)^-1 v
+asss_status ildl_G(const Ctx& c, IldlFactor& F, const double* v, double* out);  // (I + L)^-T |D|^-1/2 v
 
 // matching.cu: maximum-product matching (auction, epsilon-scaling) and the dual
 // scalings of Eq. mc64; perm, dr, dc: device arrays of n entries (row i of Abar is

@@ -1,8 +1,10 @@
 // Persistent single-kernel mrs solve (paper §3.1, App. B) of
 //     (shift I + sign * (J~ - Q_k S_k Q_k^T)) x = b
 // with J~ exactly skew - stored as skew half-diagonals (stencil-like patterns), in
-// SELL-C, or read in place as CSR - and Q_k, S_k the skew-Lanczos data of
-// §3.2 (Fig. 2).  One cooperative launch runs the whole iteration:
+// SELL-C, read in place as CSR, or applied in factored form L~^-1 J^ L~^-T through the
+// incomplete L D L^T (one grid barrier per colour of each triangular solve) - and
+// Q_k, S_k the skew-Lanczos data of §3.2 (Fig. 2).  One cooperative launch runs the
+// whole iteration:
 //
 //   per iteration j (one pass over the rows owned by each block):
 //     y_{j+1} = sign*(nu_j J~ y_j - Q (S_k h_j)) + beta_{j-1} nu_{j-1} y_{j-1}
@@ -139,6 +141,14 @@ struct MrsParams {
     const long long* crp;
     const int* cci;
     const T* cval;
+    // factored operator: z = wd .* (I + L)^-1 J^ (I + L)^-T (wd .* y), colour by colour
+    int ncol;
+    const int* fls;      // ncol + 1 level offsets into flvl
+    const int* flvl;     // vertices by (colour, index)
+    const int *flrp, *flci, *furp, *fuci, *fjrp, *fjci;
+    const T *flv, *fuv, *fjv, *fwd;
+    T* ft;               // (I + L)^-T (wd .* y)
+    T* fw;               // (I + L)^-1 J^ ft
     long long ystride;  // distance between the three Y slots (n + 2 halo)
     const T* Q;
     const __nv_bfloat16* Q16;  // BF16 copy of Q (row stride KP) when the kernel reads Q in BF16
@@ -211,7 +221,8 @@ __device__ __forceinline__ void qtz_reduce(const MrsParams<T>& p, T (&tacc)[KP +
     }
 }
 
-// FMT 0: SELL-C storage of J~; FMT 1: skew half-diagonal storage; FMT 2: plain CSR
+// FMT 0: SELL-C storage of J~; FMT 1: skew half-diagonal storage; FMT 2: plain CSR;
+// FMT 3: factored J~ = L~^-1 J^ L~^-T (incomplete L D L^T in a multicolour order)
 template <class T, int KP, int FMT, bool QB = false>
 __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsParams<T> p) {
     constexpr int NV = KP + 1;
@@ -226,6 +237,7 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
     __shared__ T s_red[NV];
     __shared__ T s_u[KP > 0 ? KP : 1];
     __shared__ int s_off[FMT == 1 ? MRS_MAXDIAG : 1];
+    __shared__ int s_ls[FMT == 3 ? ILDL_MAXCOL + 1 : 1];
     __shared__ MrsScalars<T> sc;
     __shared__ T s_alpha[MRS_KPMAX];
     // per-step coefficients in T, set by one thread (the others only read them):
@@ -235,6 +247,10 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
     __shared__ int s_next;   // SELL: next work unit of this block for the warp that asks (see next_slice)
     if constexpr (FMT == 1) {
         for (int d = threadIdx.x; d < p.ndiag; d += MRS_THREADS) s_off[d] = p.off[d];
+    }
+    if constexpr (FMT == 3) {
+        for (int c = threadIdx.x; c <= p.ncol; c += MRS_THREADS) s_ls[c] = p.fls[c];
+        __syncthreads();
     }
     for (int m = threadIdx.x; m + 1 < p.k && m < MRS_KPMAX; m += MRS_THREADS) s_alpha[m] = (T)p.alpha[m];
     auto set_coefs = [&]() {  // thread 0 only
@@ -465,6 +481,39 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
         const T* __restrict__ Qr = p.Q;
         const T tnu = s_cf[0], tsg = s_cf[1], tco = s_cf[2];
         const T tnp = s_cf[3], tdpp = s_cf[4], tthp = s_cf[5], txp = s_cf[6];
+        if constexpr (FMT == 3) {
+            // J~ y_j in factored form: the back solve (I + L)^T t = wd .* y_j from the
+            // largest colour down, then w = (I + L)^-1 J^ t from the smallest colour up
+            // (J^ t is formed row by row inside the forward solve); the rows of one
+            // colour are spread over the whole grid, one grid barrier per colour
+            const int gt = blockIdx.x * MRS_THREADS + threadIdx.x, gs = nblk * MRS_THREADS;
+            bool ok = true;
+            for (int cc = p.ncol - 1; cc >= 0 && ok; --cc) {
+                for (int e = s_ls[cc] + gt; e < s_ls[cc + 1]; e += gs) {
+                    const int i = __ldg(&p.flvl[e]);
+                    T a = __ldg(&p.fwd[i]) * Ycur[i];
+                    const int q1 = __ldg(&p.furp[i + 1]);
+                    for (int q = __ldg(&p.furp[i]); q < q1; ++q) a -= __ldg(&p.fuv[q]) * p.ft[__ldg(&p.fuci[q])];
+                    p.ft[i] = a;
+                }
+                grid_sync_phase(p.gb, nblk, phase++, p.budget);
+                if (*err) ok = false;
+            }
+            for (int cc = 0; cc < p.ncol && ok; ++cc) {
+                for (int e = s_ls[cc] + gt; e < s_ls[cc + 1]; e += gs) {
+                    const int i = __ldg(&p.flvl[e]);
+                    T a = (T)0;
+                    const int j1 = __ldg(&p.fjrp[i + 1]);
+                    for (int q = __ldg(&p.fjrp[i]); q < j1; ++q) a += __ldg(&p.fjv[q]) * p.ft[__ldg(&p.fjci[q])];
+                    const int l1 = __ldg(&p.flrp[i + 1]);
+                    for (int q = __ldg(&p.flrp[i]); q < l1; ++q) a -= __ldg(&p.flv[q]) * p.fw[__ldg(&p.flci[q])];
+                    p.fw[i] = a;
+                }
+                grid_sync_phase(p.gb, nblk, phase++, p.budget);
+                if (*err) ok = false;
+            }
+            if (!ok) break;
+        }
 #pragma unroll
         for (int v = 0; v < NV; ++v) tacc[v] = (T)0;
         for (int uu = u0 + warp; uu < u1; uu = next_slice(uu)) {
@@ -490,7 +539,9 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
                 }
             }
             T acc = (T)0;
-            if constexpr (FMT == 2) {
+            if constexpr (FMT == 3) {
+                if (live) acc = __ldg(&p.fwd[i]) * p.fw[i];
+            } else if constexpr (FMT == 2) {
                 if (i < n) {
                     const long long e1 = __ldg(&p.crp[i + 1]);
                     for (long long e = __ldg(&p.crp[i]); e < e1; ++e) acc += __ldg(&p.cval[e]) * Ycur[__ldg(&p.cci[e])];
@@ -704,6 +755,7 @@ struct OpView {
     int halo = 0;
     const void* key = nullptr;
     long long nnz = 0;  // matrix entries one application reads
+    const IldlFactor* fac = nullptr;  // FMT 3
 };
 
 struct LaunchOut {
@@ -758,6 +810,37 @@ static asss_status launch_mrs(const Ctx& c, MrsWork* w, const OpView<T>& J, cons
     prm.crp = nullptr;
     prm.cci = nullptr;
     prm.cval = nullptr;
+    prm.ncol = 0;
+    prm.fls = prm.flvl = prm.flrp = prm.flci = prm.furp = prm.fuci = prm.fjrp = prm.fjci = nullptr;
+    prm.flv = prm.fuv = prm.fjv = prm.fwd = nullptr;
+    prm.ft = prm.fw = nullptr;
+    if constexpr (FMT == 3) {
+        const IldlFactor& F = *J.fac;
+        prm.ncol = F.ncol;
+        prm.fls = F.ls.p;
+        prm.flvl = F.lvl.p;
+        prm.flrp = F.lrp.p;
+        prm.flci = F.lci.p;
+        prm.furp = F.urp.p;
+        prm.fuci = F.uci.p;
+        prm.fjrp = F.jrp;
+        prm.fjci = F.jci;
+        if constexpr (sizeof(T) == 4) {
+            prm.flv = F.lv32.p;
+            prm.fuv = F.uv32.p;
+            prm.fjv = F.jv32.p;
+            prm.fwd = F.wd32.p;
+            prm.ft = F.ft32.p;
+            prm.fw = F.fw32.p;
+        } else {
+            prm.flv = F.lv.p;
+            prm.fuv = F.uv.p;
+            prm.fjv = F.jv;
+            prm.fwd = F.wd.p;
+            prm.ft = F.ft.p;
+            prm.fw = F.fw.p;
+        }
+    }
     prm.ystride = ystride;
     prm.Q = Q;
     prm.Q16 = Q16;
@@ -865,12 +948,27 @@ template <class T>
 static asss_status dispatch_mrs(const Ctx& c, MrsWork* w, const DSell<T>* sell, const DSkewDia<T>* dia, const T* Q,
                                 const double* alpha, int k, int kp, double shift, double sign, const double* rhs,
                                 T* x, DBuf<T>& Ybuf, int& ylay, T* P, double tol, int maxit, long long* nnz_read,
-                                LaunchOut lo, const __nv_bfloat16* Q16 = nullptr, int kp16 = 0) {
+                                LaunchOut lo, const __nv_bfloat16* Q16 = nullptr, int kp16 = 0,
+                                const IldlFactor* fac = nullptr) {
     OpView<T> v;
     if (dia && dia->ndiag > MRS_MAXDIAG) dia = nullptr;
     T* Y = nullptr;
     long long ystride = 0;
-    ASSS_TRY(y_layout<T>(w, Ybuf, ylay, dia ? dia->halo : 0, c.stream, &Y, &ystride));
+    ASSS_TRY(y_layout<T>(w, Ybuf, ylay, (dia && !fac) ? dia->halo : 0, c.stream, &Y, &ystride));
+    if (fac) {
+        if (Q16) {
+            set_error("the factored inner operator reads Q_k in FP32 or FP64 only");
+            return ASSS_ERR_UNSUPPORTED;
+        }
+        v.n = fac->n;
+        v.fmt = 3;
+        v.nslices = cdiv(fac->n, 32);
+        v.key = fac;
+        v.fac = fac;
+        v.nnz = fac->nl + fac->nu + fac->nj;
+        *nnz_read = v.nnz;
+        return dispatch_kp<T, 3>(c, w, v, Q, alpha, k, kp, shift, sign, rhs, x, Y, ystride, P, tol, maxit, lo);
+    }
     if (dia) {
         v.n = dia->n;
         v.fmt = 1;
@@ -930,22 +1028,22 @@ asss_status mrs_solve(const Ctx& c, MrsWork* w, const MrsOperator& op, bool fp32
     }
     long long nnz_read = 0;
     if (fp32) {
-        if ((!op.J32 && !op.D32) || !x32) {
+        if ((!op.J32 && !op.D32 && !op.F) || !x32) {
             set_error("FP32 mrs needs the FP32 operator and an FP32 output");
             return ASSS_ERR_ARG;
         }
         if (!w->P32.p) ASSS_TRY(w->P32.alloc((int64_t)2 * n));
         ASSS_TRY(dispatch_mrs<float>(c, w, op.J32, op.D32, op.Q32, op.alpha, op.k, op.kp, shift, sign, rhs, x32,
                                      w->Y32, w->halo32, w->P32.p, tol, maxit, &nnz_read, lo,
-                                     (const __nv_bfloat16*)op.Q16, op.kp16));
+                                     (const __nv_bfloat16*)op.Q16, op.kp16, op.F));
     } else {
-        if ((!op.J64 && !op.D64) || !x64) {
+        if ((!op.J64 && !op.D64 && !op.F) || !x64) {
             set_error("FP64 mrs needs the FP64 operator and an FP64 output");
             return ASSS_ERR_ARG;
         }
         if (!w->P64.p) ASSS_TRY(w->P64.alloc((int64_t)2 * n));
         ASSS_TRY(dispatch_mrs<double>(c, w, op.J64, op.D64, op.Q64, op.alpha, op.k, op.kp, shift, sign, rhs, x64,
-                                      w->Y64, w->halo64, w->P64.p, tol, maxit, &nnz_read, lo));
+                                      w->Y64, w->halo64, w->P64.p, tol, maxit, &nnz_read, lo, nullptr, 0, op.F));
     }
     // algorithmic bytes: set-up pass (rhs in FP64, Y/x/P written, Q row), per step
     // (matrix entries - SELL ones with a 4-byte index -, Q row, gathered/own y,
@@ -953,13 +1051,14 @@ asss_status mrs_solve(const Ctx& c, MrsWork* w, const MrsOperator& op, bool fp32
     long long T = fp32 ? 4 : 8;
     long long nn = n, kp = op.kp;
     long long qrow = (fp32 && op.Q16) ? 2LL * op.kp16 : kp * T;  // bytes of one Q row as read
-    long long per_entry = (fp32 ? (op.D32 != nullptr) : (op.D64 != nullptr)) ? T : T + 4;
+    long long per_entry = (!op.F && (fp32 ? (op.D32 != nullptr) : (op.D64 != nullptr))) ? T : T + 4;
     if ((int)w->log_nnz.size() <= lo.slot) {
         w->log_nnz.resize(lo.slot + 1);
         w->log_per_row.resize(lo.slot + 1);
     }
     w->log_nnz[lo.slot] = nn * (8 + 4 * T + qrow) + nn * 4 * T + ((qtz && op.k) ? nn * qrow : 0);
-    w->log_per_row[lo.slot] = nnz_read * per_entry + nn * (7 * T + qrow);
+    // factored operator: + wd, t written and gathered, w written and gathered, per step
+    w->log_per_row[lo.slot] = nnz_read * per_entry + nn * (7 * T + qrow) + (op.F ? nn * 5 * T : 0);
     w->log_n++;
     if (sync_result) {
         std::vector<MrsResult> v;
