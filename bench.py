@@ -31,11 +31,14 @@ UNIT = "solves/s"
 WORKLOAD = ("dh3d_100: dissipative-Hamiltonian implicit-Euler step A = E + h(R - J), 100^3 grid "
             "(n = 1,000,000, nnz = 6,940,000), S on the pattern of A, k = 20, FP32 inner mrs "
             "(tol {inner_tol}) / FP64 outer FGMRES(60), outer tol 1e-8")
-DH = {"inner_tol": 1e-3}
+DH = {"inner_tol": 1e-3, "factor": "diag"}
 
 
 def dh_workload():
-    return WORKLOAD.format(inner_tol=f"{DH['inner_tol']:g}".replace("e-0", "e-"))
+    w = WORKLOAD.format(inner_tol=f"{DH['inner_tol']:g}".replace("e-0", "e-"))
+    if DH["factor"] == "ildl0":
+        w += "; L~ = the no-fill incomplete L D L^T of M^ (~ildl(0), multicolour order)"
+    return w
 
 
 SIDE = 100
@@ -250,7 +253,7 @@ def cpu_worker(side, steps, warmup, budget_s, procs, xout):
     A, b, parts = dissipative_hamiltonian_3d(side=side, seed=1)
     n = A.shape[0]
     t0 = time.perf_counter()
-    o = oracle.AsssOracle(A, inner_tol=DH["inner_tol"])
+    o = oracle.AsssOracle(A, inner_tol=DH["inner_tol"], factor=DH["factor"])
     rhs = _make_rhs(parts, n, 1, 8)
     o.solve(rhs[0], tol=1e-8, outer="fgmres")   # the oracle builds its SMW data on first use: set-up
     t_setup = time.perf_counter() - t0
@@ -296,7 +299,8 @@ def run_cpu_baseline(steps, warmup, budget_s, xout=None):
         env[v] = "1"
     procs = host_cores()
     cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", "--steps", str(steps), "--warmup",
-           str(warmup), "--budget", str(budget_s), "--procs", str(procs), "--inner-tol", repr(DH["inner_tol"])]
+           str(warmup), "--budget", str(budget_s), "--procs", str(procs), "--inner-tol", repr(DH["inner_tol"]),
+           "--factor", DH["factor"]]
     if xout:
         cmd += ["--xout", xout]
     p = subprocess.run(cmd, capture_output=True, text=True, env=env, cwd=ROOT)
@@ -956,8 +960,8 @@ def rel_error_legs(pkg, dev, stream, xo_path, legs):
     b = _make_rhs(parts, A.shape[0], 1, 1)[0]
     out = {}
     for name, prec in legs:
-        s = pkg.Solver(A, precision=prec, outer="fgmres", inner_tol=1e-6, outer_tol=1e-8, k=20,
-                       stream=stream.cuda_stream)
+        s = pkg.Solver(A, precision=prec, outer="fgmres", inner_tol=DH["inner_tol"], outer_tol=1e-8, k=20,
+                       stream=stream.cuda_stream, factor=DH["factor"])
         x, st = s.solve(torch.tensor(b, device=dev))
         xh = x.cpu().numpy()
         out[name] = {"rel_error": float(np.linalg.norm(xh - xo) / np.linalg.norm(xo)),
@@ -991,6 +995,8 @@ def main():
     ap.add_argument("--cuda-profiler-range", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--general-n", type=int, default=GENERAL["n"], help="rows of the general_2e6 workload")
+    ap.add_argument("--factor", default=DH["factor"], choices=["diag", "ildl0"],
+                    help="L~ of the dh3d_100 workload: 1x1 diagonal, or the no-fill incomplete L D L^T")
     ap.add_argument("--inner-tol", type=float, default=DH["inner_tol"],
                     help="mrs tolerance of the dh3d_100 workload (FGMRES takes inexact inner solves)")
     ap.add_argument("--batch-count", type=int, default=BATCH["count"],
@@ -999,6 +1005,7 @@ def main():
     BATCH["count"] = args.batch_count
     GENERAL["n"] = args.general_n
     DH["inner_tol"] = args.inner_tol
+    DH["factor"] = args.factor
 
     if args.cpu_worker:
         if args.workload == "batched_dh":
@@ -1050,7 +1057,7 @@ def main():
     n = A.shape[0]
     t0 = time.perf_counter()
     solver = pkg.Solver(A, precision="mixed", outer="fgmres", inner_tol=DH["inner_tol"], outer_tol=1e-8, k=20,
-                        q_bf16=args.q_storage == "bf16", stream=stream.cuda_stream)
+                        q_bf16=args.q_storage == "bf16", stream=stream.cuda_stream, factor=DH["factor"])
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
     rhs_h = _make_rhs(parts, n, 1 + rank, 4)
@@ -1108,7 +1115,7 @@ def main():
         solver.close()   # frees the mixed handle's device memory first
         t0 = time.perf_counter()
         s64 = pkg.Solver(A, precision="fp64", outer="fgmres", inner_tol=DH["inner_tol"], outer_tol=1e-8, k=20,
-                         stream=stream.cuda_stream)
+                         stream=stream.cuda_stream, factor=DH["factor"])
         torch.cuda.synchronize()
         t_setup64 = time.perf_counter() - t0
         for w in range(args.warmup):
@@ -1143,9 +1150,9 @@ def main():
     # the outer operator on its own (two diagonal-storage SpMVs, W Abar (S W v)):
     # CUDA events around repeated applications, L2 flushed between them
     others = []
-    if not args.no_fp64_leg:
+    if not args.no_fp64_leg and DH["factor"] == "diag":
         s_op = pkg.Solver(A, precision="mixed", outer="fgmres", inner_tol=DH["inner_tol"], outer_tol=1e-8, k=20,
-                          stream=stream.cuda_stream)
+                          stream=stream.cuda_stream, factor=DH["factor"])
         v = rhs[0].clone()
         ndiag = len(np.unique(np.repeat(np.arange(n), np.diff(A.indptr)) - A.indices))
         op_bytes = 2 * (ndiag * 8 + 16) * n                 # values, x and y of each product
@@ -1165,7 +1172,7 @@ def main():
                        "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak if peak else None,
                        "bytes_per_call": op_bytes, "ms_per_call": t_op,
                        "note": "asss_apply_operator timed alone (includes its host call overhead)"})
-    tr = _traffic_record()
+    tr = _traffic_record() if DH["factor"] == "diag" else None
     traffic = tr.get("dram_bytes_per_launch") if tr is not None else None
 
     if rank != 0:
@@ -1191,7 +1198,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32-inner/f64-outer", "data": "synthetic",
-        "config": {"workload": dh_workload(), "inner_tol": DH["inner_tol"], "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+        "config": {"workload": dh_workload(), "inner_tol": DH["inner_tol"], "factor": DH["factor"],
+                   "factor_colours": solver.setup_stats["factor_colours"], "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "256 MB buffer written between steps (not timed); working set > L2",
                    "setup_s": round(t_setup, 3), "lls_its": solver.setup_stats["lls_its"],
                    "outer_its": stats[-1]["outer_its"], "inner_its_avg": round(stats[-1]["inner_its_avg"], 2),
@@ -1201,7 +1209,8 @@ def main():
                    "fp64_gpu": fp64, "rel_error_vs_oracle": rel_err},
         "gpu_launches": int(launches),
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
-        "roofline": {"bound": "hbm", "kernel": "k_mrs<float,20> (persistent mrs)", "achieved": achieved,
+        "roofline": {"bound": "hbm", "kernel": "k_mrs<float,20> (persistent mrs)" if DH["factor"] == "diag" else
+                     "k_mrs<float,20,factored> (persistent mrs, J~ by triangular solves per colour)", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak if peak else None,
                      "peak_source": f"{peak_kind} hbm_gbs", "traffic": traffic,
                      "algorithmic_bytes_per_launch": inner_bytes / max(inner_launches, 1),

@@ -196,9 +196,23 @@ __global__ void k_tri_level(const int* __restrict__ lvl, int cnt, const int* __r
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= cnt) return;
     const int i = lvl[t];
-    double s = in[i];
-    for (int q = rp[i]; q < rp[i + 1]; ++q) s -= v[q] * out[ci[q]];
-    out[i] = s;
+    const int q1 = rp[i + 1];
+    double s = 0.0;
+    for (int q = rp[i]; q < q1; q += 8) {  // the batch's loads first, then its gathers
+        int cc[8];
+        double vv[8], g[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const bool inb = q + u < q1;
+            cc[u] = inb ? ci[q + u] : 0;
+            vv[u] = inb ? v[q + u] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) g[u] = (q + u < q1) ? out[cc[u]] : 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += vv[u] * g[u];
+    }
+    out[i] = in[i] - s;
 }
 
 __global__ void k_absmax_bits(const double* a, int n, unsigned long long* out) {

@@ -221,6 +221,32 @@ __device__ __forceinline__ void qtz_reduce(const MrsParams<T>& p, T (&tacc)[KP +
     }
 }
 
+// sum over q in [q0, q1) of v[q] * x[ci[q]], eight entries at a time: the indices
+// and values of a batch are loaded first, then all its gathers, so a row costs a
+// few memory latencies instead of two per entry (x is written by other blocks of
+// the launch: plain loads after the grid barrier, not the read-only path)
+template <class T>
+__device__ __forceinline__ T row_dot8(const int* __restrict__ ci, const T* __restrict__ v, const T* x, int q0,
+                                      int q1) {
+    T a = (T)0;
+    for (int q = q0; q < q1; q += 8) {
+        int cc[8];
+        T vv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const bool in = q + u < q1;
+            cc[u] = in ? __ldg(ci + q + u) : 0;
+            vv[u] = in ? __ldg(v + q + u) : (T)0;
+        }
+        T g[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) g[u] = (q + u < q1) ? x[cc[u]] : (T)0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a += vv[u] * g[u];
+    }
+    return a;
+}
+
 // FMT 0: SELL-C storage of J~; FMT 1: skew half-diagonal storage; FMT 2: plain CSR;
 // FMT 3: factored J~ = L~^-1 J^ L~^-T (incomplete L D L^T in a multicolour order)
 template <class T, int KP, int FMT, bool QB = false>
@@ -491,10 +517,8 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
             for (int cc = p.ncol - 1; cc >= 0 && ok; --cc) {
                 for (int e = s_ls[cc] + gt; e < s_ls[cc + 1]; e += gs) {
                     const int i = __ldg(&p.flvl[e]);
-                    T a = __ldg(&p.fwd[i]) * Ycur[i];
-                    const int q1 = __ldg(&p.furp[i + 1]);
-                    for (int q = __ldg(&p.furp[i]); q < q1; ++q) a -= __ldg(&p.fuv[q]) * p.ft[__ldg(&p.fuci[q])];
-                    p.ft[i] = a;
+                    const T a = __ldg(&p.fwd[i]) * Ycur[i];
+                    p.ft[i] = a - row_dot8<T>(p.fuci, p.fuv, p.ft, __ldg(&p.furp[i]), __ldg(&p.furp[i + 1]));
                 }
                 grid_sync_phase(p.gb, nblk, phase++, p.budget);
                 if (*err) ok = false;
@@ -502,12 +526,8 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
             for (int cc = 0; cc < p.ncol && ok; ++cc) {
                 for (int e = s_ls[cc] + gt; e < s_ls[cc + 1]; e += gs) {
                     const int i = __ldg(&p.flvl[e]);
-                    T a = (T)0;
-                    const int j1 = __ldg(&p.fjrp[i + 1]);
-                    for (int q = __ldg(&p.fjrp[i]); q < j1; ++q) a += __ldg(&p.fjv[q]) * p.ft[__ldg(&p.fjci[q])];
-                    const int l1 = __ldg(&p.flrp[i + 1]);
-                    for (int q = __ldg(&p.flrp[i]); q < l1; ++q) a -= __ldg(&p.flv[q]) * p.fw[__ldg(&p.flci[q])];
-                    p.fw[i] = a;
+                    const T a = row_dot8<T>(p.fjci, p.fjv, p.ft, __ldg(&p.fjrp[i]), __ldg(&p.fjrp[i + 1]));
+                    p.fw[i] = a - row_dot8<T>(p.flci, p.flv, p.fw, __ldg(&p.flrp[i]), __ldg(&p.flrp[i + 1]));
                 }
                 grid_sync_phase(p.gb, nblk, phase++, p.budget);
                 if (*err) ok = false;

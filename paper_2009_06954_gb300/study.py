@@ -6,7 +6,9 @@ one markdown row per choice:
 
 * the pattern of S: diagonal (S_d), tridiagonal (S_t) or the pattern of A (§2, Table 3),
 * the weight gamma of the diagonal equations (§2, Eq. regularized),
-* the number k of skew-Lanczos vectors used for deflation (§3.2).
+* the number k of skew-Lanczos vectors used for deflation (§3.2),
+* the factor L~ of M^: 1x1 pivots without fill ("diag") or the no-fill incomplete
+  L D L^T ("ildl0", §3 after Eq. absfac, §4.1's ~ildl(0)).
 
 Columns: the least-squares fit (iterations of the GPU solver), how skew-symmetric the
 off-diagonal part of Abar S is (||(C - C^T)/2||_F / ||C - diag C||_F, C = Abar S), how far
@@ -52,10 +54,10 @@ def skew_measures(Abar, S):
     return frac, float(np.linalg.norm(d - 1.0) / np.sqrt(len(d)))
 
 
-def measure_case(A, b, S_pat, gamma, k, precision, outer, inner_tol):
+def measure_case(A, b, S_pat, gamma, k, precision, outer, inner_tol, factor="diag"):
     """Set up and solve once with one choice; returns the study's measures as a dict."""
     s = Solver(A, s_pattern=S_pat, gamma=gamma, k=k, precision=precision, outer=outer,
-               inner_tol=inner_tol)
+               inner_tol=inner_tol, factor=factor)
     st0 = s.setup_stats
     ex = s.export(S_pat.nnz)
     S = sp.csr_matrix((ex["s_val"], S_pat.indices.copy(), S_pat.indptr.copy()), shape=A.shape)
@@ -68,9 +70,9 @@ def measure_case(A, b, S_pat, gamma, k, precision, outer, inner_tol):
             "relres": relres, "status": st["status"]}
 
 
-def run_case(A, b, pattern_name, S_pat, gamma, k, precision, outer, inner_tol):
-    m = measure_case(A, b, S_pat, gamma, k, precision, outer, inner_tol)
-    return (f"| {pattern_name} | {gamma:g} | {k} | {m['lls_its']} | {m['skew_fraction']:.4f} | "
+def run_case(A, b, pattern_name, S_pat, gamma, k, precision, outer, inner_tol, factor="diag"):
+    m = measure_case(A, b, S_pat, gamma, k, precision, outer, inner_tol, factor)
+    return (f"| {factor} | {pattern_name} | {gamma:g} | {k} | {m['lls_its']} | {m['skew_fraction']:.4f} | "
             f"{m['diag_dev']:.2e} | {m['r']} | {m['outer_its']} | {m['inner_its_avg']:.1f} | "
             f"{m['solve_ms']:.1f} | {m['relres']:.1e} |")
 
@@ -92,14 +94,16 @@ def main(argv=None):
     outer = "fgmres" if args.precision == "mixed" else "tfqmr"
     pats = {"S_d": pattern_diagonal(n), "S_t": pattern_tridiagonal(n), "pat(A)": pattern_of(A)}
     print(f"{title}, {args.precision}, outer {outer}, inner tol {inner_tol:g}\n")
-    print("| S pattern | gamma | k | LLS its | skew fraction | diag dev | r | outer its | inner its | "
+    print("| L~ | S pattern | gamma | k | LLS its | skew fraction | diag dev | r | outer its | inner its | "
           "solve ms | relres |")
-    print("|---|---|---|---|---|---|---|---|---|---|---|")
+    print("|---|---|---|---|---|---|---|---|---|---|---|---|")
     for name, P in pats.items():
         for gamma in (0.1, 1.0, 10.0):
             print(run_case(A, b, name, P, gamma, 20, args.precision, outer, inner_tol), flush=True)
     for k in (0, 10, 50):
         print(run_case(A, b, "pat(A)", pats["pat(A)"], 1.0, k, args.precision, outer, inner_tol), flush=True)
+    for name in ("S_t", "pat(A)"):
+        print(run_case(A, b, name, pats[name], 1.0, 20, args.precision, outer, inner_tol, "ildl0"), flush=True)
 
 
 if __name__ == "__main__":
