@@ -656,7 +656,8 @@ def main_adjoint(args, world, rank, local):
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak if peak else None,
                      "peak_source": f"{peak_kind} hbm_gbs", "traffic": None,
                      "algorithmic_bytes_per_launch": inner_bytes / max(inner_launches, 1),
-                     "avg_launch_ms": inner_ms / max(inner_launches, 1), "launches": inner_launches},
+                     "avg_launch_ms": inner_ms / max(inner_launches, 1), "launches": inner_launches,
+                     "others": phase_rooflines(stats, peak)},
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
     }
@@ -892,7 +893,8 @@ def main_general(args, world, rank, local):
                      "peak_source": f"{peak_kind} hbm_gbs", "traffic": None,
                      "algorithmic_bytes_per_launch": inner_bytes / max(inner_launches, 1),
                      "avg_launch_ms": inner_ms / max(inner_launches, 1), "launches": inner_launches,
-                     "share_of_step": inner_ms / total_ms if total_ms else None},
+                     "share_of_step": inner_ms / total_ms if total_ms else None,
+                     "others": phase_rooflines(stats, peak)},
         "clocks": clk.summary(),
         "cpu_baseline": None,
     }
@@ -946,6 +948,42 @@ def main_reference(args):
     if "one_thread_value" in cb:
         line["cpu_baseline"]["one_thread_value"] = cb["one_thread_value"]
     print(json.dumps(line), flush=True)
+
+
+FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12   # SMs x max SM clock x FP64 flops per clock per SM (2 FMA)
+
+
+def phase_rooflines(stats, peak):
+    """Roofline entries of the outer operator and the fused Arnoldi step, from the CUDA
+    events the library records around them inside the timed solves."""
+    out = []
+    t_op = sum(s_["t_op_ms"] for s_ in stats)
+    if t_op > 0:
+        b = sum(s_["op_bytes"] for s_ in stats)
+        f = sum(s_["op_flops"] for s_ in stats)
+        calls = sum(s_["op_calls"] for s_ in stats)
+        ach = b / (t_op / 1000.0) / 1e9
+        tf = f / (t_op / 1000.0) / 1e12
+        out.append({"kernel": "k_dia_spmv x2 (outer operator W Abar S W v)" if DH["factor"] == "diag" else
+                    "outer operator with triangular solves per colour", "bound": "hbm", "achieved": ach,
+                    "peak": peak, "unit": "GB/s", "frac": ach / peak if peak else None, "calls": calls,
+                    "bytes_per_call": b / max(calls, 1), "ms_per_call": t_op / max(calls, 1),
+                    "fp64_tflops": tf, "fp64_frac": tf / FP64_PEAK_TFLOPS,
+                    "note": "CUDA events around each application inside the timed solves; one FP64 FMA per "
+                            "stored value, so the FP64 pipe (fp64_frac) bounds it about as much as HBM"})
+    t_or = sum(s_["t_orth_ms"] for s_ in stats)
+    if t_or > 0:
+        f = sum(s_["orth_flops"] for s_ in stats)
+        b = sum(s_["orth_bytes"] for s_ in stats)
+        calls = sum(s_["orth_calls"] for s_ in stats)
+        tf = f / (t_or / 1000.0) / 1e12
+        gb = b / (t_or / 1000.0) / 1e9
+        out.append({"kernel": "k_arnoldi_orth (fused CGS2 Arnoldi step, FP64)", "bound": "alu", "achieved": tf,
+                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS, "calls": calls,
+                    "ms_per_call": t_or / max(calls, 1), "hbm_achieved_gbs": gb,
+                    "hbm_frac": gb / peak if peak else None,
+                    "note": "FP64 pipe: 4(j+1) FMAs per row at step j; peak = 152 SMs x 2.07 GHz x 4 flops"})
+    return out
 
 
 def rel_error_legs(pkg, dev, stream, xo_path, legs):
@@ -1147,31 +1185,7 @@ def main():
     inner_launches = sum(s_["inner_launches"] for s_ in stats)
     peak, peak_kind = _peaks()
     achieved = inner_bytes / (inner_ms / 1000.0) / 1e9 if inner_ms > 0 else 0.0
-    # the outer operator on its own (two diagonal-storage SpMVs, W Abar (S W v)):
-    # CUDA events around repeated applications, L2 flushed between them
-    others = []
-    if not args.no_fp64_leg and DH["factor"] == "diag":
-        s_op = pkg.Solver(A, precision="mixed", outer="fgmres", inner_tol=DH["inner_tol"], outer_tol=1e-8, k=20,
-                          stream=stream.cuda_stream, factor=DH["factor"])
-        v = rhs[0].clone()
-        ndiag = len(np.unique(np.repeat(np.arange(n), np.diff(A.indptr)) - A.indices))
-        op_bytes = 2 * (ndiag * 8 + 16) * n                 # values, x and y of each product
-        op_ms = []
-        for _ in range(10):
-            flush.zero_()
-            e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e_a.record(stream)
-            s_op.apply_operator(v)
-            e_b.record(stream)
-            torch.cuda.synchronize()
-            op_ms.append(e_a.elapsed_time(e_b))
-        s_op.close()
-        t_op = statistics.median(op_ms[2:])
-        ach = op_bytes / (t_op / 1000.0) / 1e9
-        others.append({"kernel": "k_dia_spmv x2 (outer operator W Abar S W v)", "bound": "hbm",
-                       "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak if peak else None,
-                       "bytes_per_call": op_bytes, "ms_per_call": t_op,
-                       "note": "asss_apply_operator timed alone (includes its host call overhead)"})
+    others = phase_rooflines(stats, peak)
     tr = _traffic_record() if DH["factor"] == "diag" else None
     traffic = tr.get("dram_bytes_per_launch") if tr is not None else None
 

@@ -160,6 +160,14 @@ typedef struct {
     int    sell_split;        /* set-up, J~ in SELL-C: entries per lane of one work unit; both picked
                                  by timing mrs steps for systems of 10^5 rows and more (FP32 path) */
     int    factor_colours;    /* set-up, ASSS_FACTOR_ILDL0: colours of the factorization order  */
+    double t_op_ms;           /* solve: CUDA-event time of the outer operator applications      */
+    int    op_calls;
+    long long op_bytes;       /* their algorithmic bytes (stored values, x and y per product)   */
+    long long op_flops;       /* and FP64 flops (one FMA per stored value)                      */
+    double t_orth_ms;         /* solve: CUDA-event time of the fused Arnoldi steps (FGMRES)     */
+    int    orth_calls;
+    long long orth_bytes;     /* their algorithmic bytes (basis read twice, w r/w, v_{j+1} out) */
+    long long orth_flops;     /* and FP64 flops (4(j+1) FMAs a row)                             */
 } asss_stats;
 
 typedef struct asss_handle asss_handle;

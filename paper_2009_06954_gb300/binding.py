@@ -64,7 +64,9 @@ class Stats(C.Structure):
                 ("lls_relgrad", C.c_double), ("nnz_pattern", C.c_longlong),
                 ("t_setup_ms", C.c_double), ("t_solve_ms", C.c_double), ("t_inner_ms", C.c_double),
                 ("inner_bytes", C.c_longlong), ("inner_launches", C.c_int), ("sell_sigma", C.c_int),
-                ("sell_split", C.c_int), ("factor_colours", C.c_int)]
+                ("sell_split", C.c_int), ("factor_colours", C.c_int), ("t_op_ms", C.c_double),
+                ("op_calls", C.c_int), ("op_bytes", C.c_longlong), ("op_flops", C.c_longlong), ("t_orth_ms", C.c_double),
+                ("orth_calls", C.c_int), ("orth_bytes", C.c_longlong), ("orth_flops", C.c_longlong)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

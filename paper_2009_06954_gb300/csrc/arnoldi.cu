@@ -67,7 +67,10 @@ __device__ void ao_fg_column(const AoParams& p, const double* h1, const double* 
     *p.stop = (hn2 == 0.0 || fabs(p.g[j + 1]) <= p.thr) ? 1 : 0;
 }
 
-__global__ void __launch_bounds__(AO_THREADS, 2) k_arnoldi_orth(AoParams p) {
+// one 512-thread block per SM: the kernel is bound by GB300's FP64 pipe, and every
+// block spends FP64 adds on its partial sums, so fewer, fuller blocks leave more of the
+// pipe to the rows (and 128 registers a thread, no spills)
+__global__ void __launch_bounds__(AO_THREADS, 1) k_arnoldi_orth(AoParams p) {
     __shared__ double s_w[AO_WARPS][AO_CH];
     __shared__ double s_h1[AO_MAXV];
     __shared__ double s_h2[AO_MAXV];
@@ -120,19 +123,34 @@ __global__ void __launch_bounds__(AO_THREADS, 2) k_arnoldi_orth(AoParams p) {
         }
         __syncthreads();
     };
-    // dots V_a^T w over this block's rows, a < nv, AO_CH vectors per sweep
+    // dots V_a^T w over this block's rows for a in [c0, c0 + CNT): the count is a
+    // template argument, so no FP64 instruction is issued for a vector that is not
+    // there (the FP64 pipe is what bounds this kernel on GB300)
+    auto dots_n = [&](auto cnt, int c0) {
+        constexpr int CNT = decltype(cnt)::value;
+        double acc[CNT];
+#pragma unroll
+        for (int t = 0; t < CNT; ++t) acc[t] = 0.0;
+        for (long long i = r0 + threadIdx.x; i < r1; i += AO_THREADS) {
+            const double wi = w[i];
+#pragma unroll
+            for (int t = 0; t < CNT; ++t) acc[t] += V[(size_t)(c0 + t) * n + i] * wi;
+        }
+        put_partials(acc, c0, CNT);
+    };
+    // all nv dots, AO_CH vectors per sweep
     auto dots = [&]() {
         for (int c0 = 0; c0 < nv; c0 += AO_CH) {
-            double acc[AO_CH];
-#pragma unroll
-            for (int t = 0; t < AO_CH; ++t) acc[t] = 0.0;
-            for (long long i = r0 + threadIdx.x; i < r1; i += AO_THREADS) {
-                const double wi = w[i];
-#pragma unroll
-                for (int t = 0; t < AO_CH; ++t)
-                    if (c0 + t < nv) acc[t] += V[(size_t)(c0 + t) * n + i] * wi;
+            switch (nv - c0 < AO_CH ? nv - c0 : AO_CH) {
+                case 1: dots_n(std::integral_constant<int, 1>{}, c0); break;
+                case 2: dots_n(std::integral_constant<int, 2>{}, c0); break;
+                case 3: dots_n(std::integral_constant<int, 3>{}, c0); break;
+                case 4: dots_n(std::integral_constant<int, 4>{}, c0); break;
+                case 5: dots_n(std::integral_constant<int, 5>{}, c0); break;
+                case 6: dots_n(std::integral_constant<int, 6>{}, c0); break;
+                case 7: dots_n(std::integral_constant<int, 7>{}, c0); break;
+                default: dots_n(std::integral_constant<int, AO_CH>{}, c0); break;
             }
-            put_partials(acc, c0, AO_CH);
         }
     };
     // every block adds the nblk partials of each vector in block order
@@ -248,7 +266,7 @@ asss_status arnoldi_orth(const Ctx& c, ArnoldiWork& aw, const double* V, double*
             set_error("Arnoldi kernel cannot be resident");
             return ASSS_ERR_CUDA;
         }
-        if (occ > 2) occ = 2;
+        if (occ > 1) occ = 1;
         int nblk = c.sms * occ;
         int need = cdiv(n, 64);
         if (need < 1) need = 1;

@@ -479,6 +479,60 @@ struct Tracer {
     }
 };
 
+// CUDA events around the outer operator and the fused Arnoldi step of a solve, with
+// the work each launch does; summed into the solve's statistics after its last
+// synchronisation (the pairs are reused from one solve to the next)
+struct PhaseClock {
+    enum { OP = 0, ORTH = 1 };
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> cat;
+    std::vector<double> bytes, flops;
+    int used = 0;
+    void start(cudaStream_t s) {
+        while ((int)ev.size() < 2 * (used + 1)) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return;
+            ev.push_back(e);
+        }
+        cudaEventRecord(ev[2 * used], s);
+    }
+    void stop(cudaStream_t s, int c, double b, double f) {
+        if ((int)ev.size() < 2 * (used + 1)) return;
+        cudaEventRecord(ev[2 * used + 1], s);
+        if ((int)cat.size() <= used) {
+            cat.resize(used + 1);
+            bytes.resize(used + 1);
+            flops.resize(used + 1);
+        }
+        cat[used] = c;
+        bytes[used] = b;
+        flops[used] = f;
+        ++used;
+    }
+    // the stream has been synchronised
+    void collect(asss_stats* st) {
+        for (int i = 0; i < used; ++i) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]) != cudaSuccess) continue;
+            if (cat[i] == OP) {
+                st->t_op_ms += ms;
+                st->op_calls += 1;
+                st->op_bytes += (long long)bytes[i];
+                st->op_flops += (long long)flops[i];
+            } else {
+                st->t_orth_ms += ms;
+                st->orth_calls += 1;
+                st->orth_bytes += (long long)bytes[i];
+                st->orth_flops += (long long)flops[i];
+            }
+        }
+        used = 0;
+    }
+    ~PhaseClock() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+};
+
 struct SmwData {
     bool ready = false;
     int m = 0;
@@ -530,6 +584,7 @@ struct asss_handle {
     // per-solve work buffers, allocated once
     KrylovWork kw;
     Tracer tr;
+    PhaseClock pc;
     DBuf<double> rr, rh, dy, rscal, bb, xx;
     // statistics of the current solve
     int inner_solves = 0;
@@ -799,8 +854,37 @@ static asss_status ensure_adjoint_ops(asss_handle* h) {
     return ASSS_OK;
 }
 
-// out = A_cal v or A_cal^T v
+// algorithmic bytes of one product: the stored values (a diagonal copy has no column
+// indices) and x, y once each; its FP64 flops: one FMA per stored value
+static long long spmv_bytes(const DCsr& A) {
+    const long long n = A.n;
+    if (A.dia.ndiag > 0) return (long long)A.dia.ndiag * n * 8 + 16 * n;
+    return (long long)A.nnz * 12 + 4 * (n + 1) + 16 * n;
+}
+static long long spmv_flops(const DCsr& A) {
+    return 2LL * (A.dia.ndiag > 0 ? (long long)A.dia.ndiag * A.n : (long long)A.nnz);
+}
+
+static asss_status apply_op_impl(asss_handle* h, int tr, const double* v, double* out);
+
+// out = A_cal v or A_cal^T v, timed into the solve's statistics
 static asss_status apply_op(asss_handle* h, int tr, const double* v, double* out) {
+    cudaStream_t s = h->ctx.stream;
+    h->pc.start(s);
+    ASSS_TRY(apply_op_impl(h, tr, v, out));
+    const DCsr& a = tr ? h->AwT : h->Aw;
+    const DCsr& b = tr ? h->SwT : h->Sw;
+    double bytes = (double)(spmv_bytes(a) + spmv_bytes(b));
+    double flops = (double)(spmv_flops(a) + spmv_flops(b));
+    if (h->factored) {
+        bytes += (double)(h->fac.nl + h->fac.nu) * 12 + 6.0 * 8 * h->n;
+        flops += 2.0 * (double)(h->fac.nl + h->fac.nu) + 2.0 * h->n;
+    }
+    h->pc.stop(s, PhaseClock::OP, bytes, flops);
+    return ASSS_OK;
+}
+
+static asss_status apply_op_impl(asss_handle* h, int tr, const double* v, double* out) {
     cudaStream_t s = h->ctx.stream;
     if (h->factored) {
         // F A^ G v or F A^T G v (Eq. preconditioner with the incomplete factor)
@@ -966,9 +1050,12 @@ static asss_status fgmres_cycle(asss_handle* h, KrylovWork& kw, int tr, const do
         h->tr.mark(s, Tracer::ORTH);
         const bool fused = j + 1 < AO_MAXV;
         if (fused) {
-            // CGS2, ||w||, the Givens update, v_{j+1} and the stop test in one launch
+            // CGS2, ||w||, the Givens update, v_{j+1} and the stop test in one launch;
+            // work: V read twice, w three times, w and v_{j+1} written; 4(j+1) FP64 FMAs a row
+            h->pc.start(s);
             ASSS_TRY(arnoldi_orth(h->ctx, kw.ao, kw.V.p, kw.w.p, n, j, M, kw.H.p, kw.cs.p, kw.sn.p, kw.g.p,
                                   kw.hv.p, kw.hv2.p, T + 2, T + 3, thr, kw.stop.p));
+            h->pc.stop(s, PhaseClock::ORTH, 8.0 * n * (2.0 * (j + 1) + 5.0), 8.0 * n * (j + 1));
             h->tr.mark(s, Tracer::SCALAR);
         } else {
             ASSS_TRY(gram(kw.V.p, n, j + 1, kw.w.p, n, 1, n, kw.hv.p, s));
@@ -1054,6 +1141,10 @@ static asss_status refine(asss_handle* h, int tr, const double* rhs, double* x, 
     h->inner_solves = 0;
     ASSS_TRY(mrs_collect(h->ctx, h->mw, nullptr));
     mrs_take_totals(h->mw);
+    h->pc.used = 0;   // pairs recorded outside a solve (single operator applications) are dropped
+    st->t_op_ms = st->t_orth_ms = 0.0;
+    st->op_calls = st->orth_calls = 0;
+    st->op_bytes = st->op_flops = st->orth_bytes = st->orth_flops = 0;
     ASSS_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
     ASSS_TRY(vcopy(r.p, rhs, n, s));
     ASSS_TRY(dot(rhs, rhs, n, scal.p, s));
@@ -1142,6 +1233,7 @@ static asss_status refine(asss_handle* h, int tr, const double* rhs, double* x, 
     ASSS_TRY(mrs_collect(h->ctx, h->mw, nullptr));
     MrsTotals t = mrs_take_totals(h->mw);
     h->tr.report(s, st->outer_its, t.its);
+    h->pc.collect(st);   // mrs_collect synchronised the stream
     st->inner_its_total = t.its;
     st->inner_solves = t.launches;
     st->inner_its_avg = t.launches ? (double)t.its / t.launches : 0.0;
