@@ -509,6 +509,12 @@ def main_batched(args, world, rank, local):
     peak, peak_kind = _peaks()
     inner_bytes = sum(s_["inner_bytes"] for s_ in stats)
     achieved = inner_bytes / (total_ms / 1000.0) / 1e9 if total_ms > 0 else 0.0
+    # the precision form's comparison: the same systems and right-hand sides through the
+    # one-system path (asss_solve, one column after another), in FP64 throughout and in
+    # mixed precision, on a sample of every 16th matrix by size (timed with CUDA events)
+    one_sys = None
+    if not args.no_fp64_leg and rank == 0:
+        one_sys = batched_one_system_legs(pkg, torch, batch, nrhs, dev, stream, flush, bs.total / len(batch))
 
     if rank != 0:
         if dist:
@@ -529,10 +535,13 @@ def main_batched(args, world, rank, local):
         "config": {"workload": BATCH_WORKLOAD.format(count=len(batch), items=items),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "256 MB buffer written between steps (not timed); working set > L2",
-                   "setup_s": round(t_setup, 3), "cta_threads": bs.cta_threads, "items_per_step": items,
+                   "setup_s": round(t_setup, 3), "cta_threads": bs.cta_threads,
+                   "cta_registers": bs.cta_registers, "items_per_step": items,
                    "total_rows": bs.total, "max_relres": relres, "host_checked_max_relres": worst,
                    "converged": ok and worst <= 1e-8, "outer_its_max": stats[-1]["outer_its"],
-                   "inner_its_total": stats[-1]["inner_its_total"], "q_storage": args.q_storage},
+                   "inner_its_total": stats[-1]["inner_its_total"], "q_storage": args.q_storage,
+                   "fp64_gpu": one_sys["fp64"] if one_sys else None,
+                   "one_system_mixed": one_sys["mixed"] if one_sys else None},
         "gpu_launches": int(launches),
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 8 * bs.total * nrhs,
                 "d2h_bytes_per_step": 8 * bs.total * nrhs},
@@ -549,6 +558,56 @@ def main_batched(args, world, rank, local):
     bs.close()
     if dist:
         dist.destroy_process_group()
+
+
+def batched_one_system_legs(pkg, torch, batch, nrhs, dev, stream, flush, mean_n):
+    """Solves/s of the one-system path (asss_solve per matrix, its nrhs columns one after
+    another) on every 16th matrix of the batch by size, FP64 throughout and mixed; each
+    solve counted as n_m / mean n of a batch item, so the rate is comparable with the
+    batched line's."""
+    import numpy as np
+    order = np.argsort([A.shape[0] for A, _ in batch])
+    pick = [int(i) for i in order[8::16]]
+    out = {}
+    for prec in ("fp64", "mixed"):
+        ms = 0.0
+        units = 0.0
+        solves = 0
+        worst = 0.0
+        its = []
+        setup = 0.0
+        for m in pick:
+            A, B = batch[m]
+            t0 = time.perf_counter()
+            s = pkg.Solver(A, precision=prec, outer="fgmres", inner_tol=1e-6, outer_tol=1e-8, k=20, restart=24,
+                           stream=stream.cuda_stream)
+            torch.cuda.synchronize()
+            setup += time.perf_counter() - t0
+            Bd = torch.tensor(np.asfortranarray(B), device=dev)
+            s.solve(Bd[:, 0].contiguous())   # warm-up
+            for c in range(nrhs):
+                bc = Bd[:, c].contiguous()
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                x, st = s.solve(bc)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms += e0.elapsed_time(e1)
+                units += A.shape[0] / mean_n
+                solves += 1
+                its.append(st["outer_its"])
+                if c == 0:
+                    xh = x.cpu().numpy()
+                    worst = max(worst, float(np.linalg.norm(B[:, 0] - A @ xh) / np.linalg.norm(B[:, 0])))
+            s.close()
+        out[prec] = {"value": units / (ms / 1000.0), "unit": UNIT, "solves_timed": solves,
+                     "matrices": len(pick), "mean_outer_its": float(np.mean(its)),
+                     "host_checked_max_relres": worst, "setup_s": round(setup, 3),
+                     "sample": (f"asss_solve (one system, columns one after another), {prec}, every 16th of the "
+                                f"{len(batch)} matrices by size x {nrhs} columns, each solve counted as n_m / mean n "
+                                f"of a batch item; L2 flushed between solves")}
+    return out
 
 
 # ----------------------------------------------------------------------------

@@ -263,15 +263,20 @@ asss_status asss_setup_batched(int nmat, const asss_csr* const* A, const asss_op
  * the algorithmic bytes of the inner mrs steps (the one-system byte model summed
  * over items).  Returns the
  * first non-OK item status (x then holds every item's last iterate).  The first
- * call for a given nrhs tunes the CTA size: it solves the batch once at each of
- * 128, 256, 512 and 1024 threads per CTA (64 registers a thread, as many CTAs
- * per SM as fit, at most one CTA per item) and keeps the fastest for later calls;
- * that call takes about five times as long. */
+ * call for a given nrhs tunes the CTA shape: it solves the batch once at each of
+ * 128, 256, 512 and 1024 threads per CTA with 64 registers a thread, and at 512
+ * threads with 128 registers a thread (as many CTAs per SM as fit, at most one CTA
+ * per item), and keeps the fastest for later calls; that call takes about six
+ * times as long. */
 asss_status asss_solve_batched(asss_batch* b, int nrhs, const double* rhs, double* x,
                                asss_stats* st);
 
 /* CTA size chosen by the tuner (0 before the first solve). */
 int asss_batch_cta_threads(const asss_batch* b);
+
+/* Registers a thread of the CTA shape chosen by the tuner (64 or 128; 0 before the
+ * first solve). */
+int asss_batch_cta_registers(const asss_batch* b);
 
 void asss_destroy_batched(asss_batch* b);
 

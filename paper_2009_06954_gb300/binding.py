@@ -77,7 +77,7 @@ EXPORTED = ["asss_default_options", "asss_setup", "asss_solve", "asss_solve_adjo
             "asss_status_str", "asss_last_error", "asss_skew_symmetrizer", "asss_skew_lanczos",
             "asss_mrs", "asss_mrs_multi", "asss_kernel_launches", "asss_mrs_noalloc", "asss_export_permutation",
             "asss_matching_scaling", "asss_export_factor", "asss_setup_batched",
-            "asss_solve_batched", "asss_destroy_batched", "asss_batch_cta_threads"]
+            "asss_solve_batched", "asss_destroy_batched", "asss_batch_cta_threads", "asss_batch_cta_registers"]
 
 _lib = None
 _live = weakref.WeakSet()   # open handles, closed at exit while CUDA is still up
@@ -138,6 +138,8 @@ def lib():
     L.asss_destroy_batched.restype = None
     L.asss_batch_cta_threads.argtypes = [P]
     L.asss_batch_cta_threads.restype = C.c_int
+    L.asss_batch_cta_registers.argtypes = [P]
+    L.asss_batch_cta_registers.restype = C.c_int
     L.asss_kernel_launches.argtypes = []
     L.asss_kernel_launches.restype = C.c_ulonglong
     for f in ("asss_setup", "asss_solve", "asss_solve_adjoint", "asss_apply_operator",
@@ -421,6 +423,11 @@ class BatchSolver:
     def cta_threads(self):
         """CTA size picked by the tuner on the first solve (0 before it)."""
         return int(lib().asss_batch_cta_threads(self._h)) if getattr(self, "_h", None) else 0
+
+    @property
+    def cta_registers(self):
+        """Registers a thread of the CTA shape picked by the tuner (64 or 128; 0 before it)."""
+        return int(lib().asss_batch_cta_registers(self._h)) if getattr(self, "_h", None) else 0
 
     def close(self):
         if getattr(self, "_h", None):

@@ -243,12 +243,38 @@ __global__ void __launch_bounds__(AO_THREADS, 1) k_arnoldi_orth(AoParams p) {
     const double hn = sqrt(hn2);
     const double inv = (hn > 0.0) ? 1.0 / hn : 0.0;
     double* vn = const_cast<double*>(V) + (size_t)nv * n;
-    for (long long i = r0 + threadIdx.x; i < r1; i += AO_THREADS) {
-        double s = 0.0;
-        for (int a = 0; a < nv; ++a) s += V[(size_t)a * n + i] * s_h2[a];
-        const double wi = w[i] - s;
-        w[i] = wi;
-        vn[i] = wi * inv;
+    // the vector count as a template argument where it is small (the loads of a row are
+    // then issued together and no FP64 operation is spent on a loop counter)
+    auto pass3 = [&](auto nvc) {
+        constexpr int NVC = decltype(nvc)::value;
+        for (long long i = r0 + threadIdx.x; i < r1; i += AO_THREADS) {
+            double vi[NVC];
+#pragma unroll
+            for (int t = 0; t < NVC; ++t) vi[t] = V[(size_t)t * n + i];
+            double s = 0.0;
+#pragma unroll
+            for (int t = 0; t < NVC; ++t) s += vi[t] * s_h2[t];
+            const double wi = w[i] - s;
+            w[i] = wi;
+            vn[i] = wi * inv;
+        }
+    };
+    switch (nv) {
+        case 1: pass3(std::integral_constant<int, 1>{}); break;
+        case 2: pass3(std::integral_constant<int, 2>{}); break;
+        case 3: pass3(std::integral_constant<int, 3>{}); break;
+        case 4: pass3(std::integral_constant<int, 4>{}); break;
+        case 5: pass3(std::integral_constant<int, 5>{}); break;
+        case 6: pass3(std::integral_constant<int, 6>{}); break;
+        default:
+            for (long long i = r0 + threadIdx.x; i < r1; i += AO_THREADS) {
+                double s = 0.0;
+                for (int a = 0; a < nv; ++a) s += V[(size_t)a * n + i] * s_h2[a];
+                const double wi = w[i] - s;
+                w[i] = wi;
+                vn[i] = wi * inv;
+            }
+            break;
     }
 }
 

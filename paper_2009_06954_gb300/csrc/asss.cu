@@ -401,10 +401,12 @@ struct KrylovWork {
     DBuf<int> stop;   // set by the fused step when the cycle ends
     double* hpin = nullptr;        // pinned read-back slots
     cudaEvent_t ev_rb = nullptr;   // marks the read-back in the stream
+    cudaEvent_t ev_bn = nullptr;   // marks the read-back of ||b||^2 (slot 6)
     int outer = -1;
     ~KrylovWork() {
         if (hpin) cudaFreeHost(hpin);
         if (ev_rb) cudaEventDestroy(ev_rb);
+        if (ev_bn) cudaEventDestroy(ev_bn);
     }
     // allocates on first use or when the size changes; kept by the handle across solves
     asss_status init(int n_, int m_, int outer_) {
@@ -413,6 +415,7 @@ struct KrylovWork {
         ASSS_TRY(T.alloc(32));
         if (!hpin) ASSS_CUDA(cudaMallocHost((void**)&hpin, 8 * sizeof(double)));
         if (!ev_rb) ASSS_CUDA(cudaEventCreateWithFlags(&ev_rb, cudaEventDisableTiming));
+        if (!ev_bn) ASSS_CUDA(cudaEventCreateWithFlags(&ev_bn, cudaEventDisableTiming));
         if (!stop.p) ASSS_TRY(stop.alloc(1));
         if (outer_ == ASSS_OUTER_TFQMR) {
             ASSS_TRY(w.alloc(n_));
@@ -1031,7 +1034,7 @@ static asss_status fgmres_cycle(asss_handle* h, KrylovWork& kw, int tr, const do
     bool have_z = true;  // Z[:, j] is already enqueued
     ASSS_CUDA(cudaEventSynchronize(kw.ev_rb));
     const double rr = hp[0];
-    if (rr == 0.0) return ASSS_OK;
+    if (rr == 0.0 || !(rr == rr) || rr == INFINITY) return ASSS_OK;  // nothing to do, or a NaN the caller reports
     *napp_out = 1;
     const double beta0 = sqrt(rr);
     const double thr = eta * beta0;
@@ -1148,8 +1151,18 @@ static asss_status refine(asss_handle* h, int tr, const double* rhs, double* x, 
     ASSS_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
     ASSS_TRY(vcopy(r.p, rhs, n, s));
     ASSS_TRY(dot(rhs, rhs, n, scal.p, s));
-    double bn = sqrt(read_scalar(scal.p, s, &es));
-    ASSS_TRY(es);
+    // FGMRES: the first cycle needs ||b|| only through ||r|| / ||b|| = 1, so its read-back
+    // is left in flight and the cycle is enqueued at once (b = 0 and a NaN in b come back
+    // through the cycle's own ||r^|| and are decided after it); TFQMR waits for it here
+    const bool defer_bn = o.outer == ASSS_OUTER_FGMRES && o.outer_tol < 1.0 && o.outer_maxit > 0;
+    double bn = -1.0;
+    if (defer_bn) {
+        ASSS_CUDA(cudaMemcpyAsync(kw.hpin + 6, scal.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+        ASSS_CUDA(cudaEventRecord(kw.ev_bn, s));
+    } else {
+        bn = sqrt(read_scalar(scal.p, s, &es));
+        ASSS_TRY(es);
+    }
     st->outer_its = 0;
     st->cycles = 0;
     st->relres = 0.0;
@@ -1170,6 +1183,10 @@ static asss_status refine(asss_handle* h, int tr, const double* rhs, double* x, 
             ASSS_TRY(es);
         }
         first = false;
+        if (bn < 0.0) {  // ||b|| still in flight: r = b, so ||r|| / ||b|| = 1 (not below tol < 1)
+            rn = 1.0;
+            bn = 1.0;
+        }
         st->relres = rn / bn;
         if (rn / bn <= o.outer_tol) break;
         if (!(rn == rn)) {
@@ -1207,6 +1224,22 @@ static asss_status refine(asss_handle* h, int tr, const double* rhs, double* x, 
         } else {
             int m = o.restart < budget ? o.restart : budget;
             ASSS_TRY(fgmres_cycle(h, kw, tr, rh.p, eta, m, dy.p, &steps, &napp));
+        }
+        if (defer_bn && st->cycles == 0) {
+            // the true ||b|| (its read-back finished long ago); the first cycle ran with
+            // the ratio 1, which is what r = b gives for any non-zero finite b
+            ASSS_CUDA(cudaEventSynchronize(kw.ev_bn));
+            bn = sqrt(kw.hpin[6]);
+            if (bn == 0.0) {  // the cycle saw r^ = 0 and added nothing: x = 0
+                st->relres = 0.0;
+                break;
+            }
+            if (!(bn == bn) || bn == INFINITY) {
+                st->status = ASSS_ERR_BREAKDOWN;
+                set_error("right-hand side has a NaN or infinite entry");
+                break;
+            }
+            best = bn;  // the first pass's ||r|| in its true scale
         }
         st->outer_its += steps;
         st->cycles += 1;
@@ -2455,9 +2488,10 @@ struct asss_batch {
     DBuf<long long> row_off;
     DBuf<double> work;
     long long work_stride = 0;
-    int nblk = 0, nthreads = 0, tuned_nrhs = -1;
+    int nblk = 0, nthreads = 0, wide = 0, tuned_nrhs = -1;
     DBuf<unsigned> counter;
     DBuf<BatchItemStat> stats;
+    DBuf<unsigned long long> prof;  // ASSS_BATCH_PROFILE: phase times
     DBuf<int2> items;
     std::vector<int2> items_h;
     std::vector<double> step_bytes, call_bytes;   // mrs byte model per matrix
@@ -2466,7 +2500,7 @@ struct asss_batch {
     cudaGraphExec_t gexec = nullptr;
     const void* g_b = nullptr;
     const void* g_x = nullptr;
-    int g_nrhs = -1, g_nt = -1;
+    int g_nrhs = -1, g_nt = -1, g_wide = -1;
     ~asss_batch() {
         if (gexec) cudaGraphExecDestroy(gexec);
         for (asss_handle* h : hs) delete h;
@@ -2554,8 +2588,8 @@ static asss_status batch_items(asss_batch* B, int nrhs) {
     return ASSS_OK;
 }
 
-static asss_status batch_run(asss_batch* B, int nrhs, const double* bd, double* xd, int nthreads, bool use_graph,
-                             float* ms) {
+static asss_status batch_run(asss_batch* B, int nrhs, const double* bd, double* xd, int nthreads, int wide,
+                             bool use_graph, float* ms) {
     ASSS_TRY(batch_items(B, nrhs));
     BatchLaunch L;
     L.mats = B->mats.p;
@@ -2578,11 +2612,22 @@ static asss_status batch_run(asss_batch* B, int nrhs, const double* bd, double* 
     L.inner_maxit = B->opt.inner_maxit;
     L.next_item = B->counter.p;
     L.stats = B->stats.p;
+    L.prof = nullptr;
+    // ASSS_BATCH_PROFILE=1: per-phase device time of the CTAs (the plain launch, not the
+    // graph), printed to stderr; for analysis only
+    const bool prof = getenv("ASSS_BATCH_PROFILE") != nullptr;
+    if (prof) {
+        if (!B->prof.p) ASSS_TRY(B->prof.alloc(BATCH_NPROF));
+        ASSS_CUDA(cudaMemsetAsync(B->prof.p, 0, sizeof(unsigned long long) * BATCH_NPROF, B->own));
+        L.prof = B->prof.p;
+        use_graph = false;
+    }
     int nblk = B->nblk < L.nitems ? B->nblk : L.nitems;
     if (nblk < 1) nblk = 1;
     cudaStream_t s = B->own;
     if (use_graph) {
-        if (!B->gexec || B->g_b != bd || B->g_x != xd || B->g_nrhs != nrhs || B->g_nt != nthreads) {
+        if (!B->gexec || B->g_b != bd || B->g_x != xd || B->g_nrhs != nrhs || B->g_nt != nthreads ||
+            B->g_wide != wide) {
             if (B->gexec) {
                 cudaGraphExecDestroy(B->gexec);
                 B->gexec = nullptr;
@@ -2591,7 +2636,7 @@ static asss_status batch_run(asss_batch* B, int nrhs, const double* bd, double* 
             ASSS_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
             asss_status st = ASSS_OK;
             if (cudaMemsetAsync(B->counter.p, 0, sizeof(unsigned), s) != cudaSuccess) st = ASSS_ERR_CUDA;
-            if (st == ASSS_OK) st = batch_launch(L, nthreads, nblk, s);
+            if (st == ASSS_OK) st = batch_launch(L, nthreads, wide, nblk, s);
             cudaError_t e = cudaStreamEndCapture(s, &g);
             if (st != ASSS_OK) return st;
             if (e != cudaSuccess) {
@@ -2608,6 +2653,7 @@ static asss_status batch_run(asss_batch* B, int nrhs, const double* bd, double* 
             B->g_x = xd;
             B->g_nrhs = nrhs;
             B->g_nt = nthreads;
+            B->g_wide = wide;
         }
         ASSS_CUDA(cudaEventRecord(B->ev_t0, s));
         ASSS_CUDA(cudaGraphLaunch(B->gexec, s));
@@ -2616,34 +2662,54 @@ static asss_status batch_run(asss_batch* B, int nrhs, const double* bd, double* 
     } else {
         ASSS_CUDA(cudaEventRecord(B->ev_t0, s));
         ASSS_CUDA(cudaMemsetAsync(B->counter.p, 0, sizeof(unsigned), s));
-        ASSS_TRY(batch_launch(L, nthreads, nblk, s));
+        ASSS_TRY(batch_launch(L, nthreads, wide, nblk, s));
         ASSS_CUDA(cudaEventRecord(B->ev_t1, s));
     }
     ASSS_CUDA(cudaStreamSynchronize(s));
     if (ms) ASSS_CUDA(cudaEventElapsedTime(ms, B->ev_t0, B->ev_t1));
+    if (prof) {
+        unsigned long long t[BATCH_NPROF];
+        ASSS_CUDA(cudaMemcpy(t, B->prof.p, sizeof(t), cudaMemcpyDeviceToHost));
+        const double per = 1e-6 / (nblk > 0 ? nblk : 1);
+        fprintf(stderr,
+                "asss batch profile (%d threads%s, %d CTAs, launch %.2f ms; ms per CTA): mrs %.2f | smw %.2f | "
+                "operator %.2f | gram-schmidt %.2f | update+residual %.2f | rest %.2f\n",
+                nthreads, wide ? ", 128 registers" : "", nblk, ms ? *ms : 0.f, t[0] * per, t[1] * per, t[2] * per,
+                t[3] * per, t[4] * per, t[5] * per);
+    }
     return ASSS_OK;
 }
 
-// CTA size for a number of right-hand sides: each candidate (128 / 256 / 512 /
-// 1024 threads, as many CTAs as fit on the GPU, at most one per item) solves the
-// caller's batch once, timed with CUDA events; the fastest is kept for later calls
+// CTA shape for a number of right-hand sides: each candidate (128 / 256 / 512 / 1024
+// threads at 64 registers, or 512 threads at 128 registers; as many CTAs as fit on the
+// GPU, at most one per item) solves the caller's batch once, timed with CUDA events;
+// the fastest is kept for later calls
 static asss_status batch_tune(asss_batch* B, int nrhs, const double* bd, double* xd) {
-    const int cand[4] = {128, 256, 512, 1024};
+    const int cand[5][2] = {{128, 0}, {256, 0}, {512, 0}, {1024, 0}, {512, 1}};
     const long long nitems = (long long)B->hs.size() * nrhs;
-    int best_nt = 0, best_nb = 0;
+    int best_nt = 0, best_wide = 0, best_nb = 0;
     float best_ms = 0.f;
-    for (int c = 0; c < 4; ++c) {
+    // ASSS_BATCH_CTA = "<threads>" or "<threads>w" (128 registers) restricts the tuner
+    // to that one shape (tests run every shape this way)
+    int force_nt = 0, force_wide = 0;
+    if (const char* f = getenv("ASSS_BATCH_CTA")) {
+        force_nt = atoi(f);
+        force_wide = strchr(f, 'w') != nullptr;
+    }
+    for (int c = 0; c < 5; ++c) {
+        if (force_nt && (cand[c][0] != force_nt || cand[c][1] != force_wide)) continue;
         int occ = 0;
-        ASSS_TRY(batch_occupancy(B->kp, B->qbf16, cand[c], &occ));
+        ASSS_TRY(batch_occupancy(B->kp, B->qbf16, cand[c][0], cand[c][1], &occ));
         if (occ < 1) continue;
         long long nb = (long long)B->ctx.sms * occ;
         if (nb > nitems) nb = nitems;
         if (B->work.n < B->work_stride * nb) ASSS_TRY(B->work.alloc(B->work_stride * nb));
         B->nblk = (int)nb;
         float ms = 0.f;
-        ASSS_TRY(batch_run(B, nrhs, bd, xd, cand[c], false, &ms));
+        ASSS_TRY(batch_run(B, nrhs, bd, xd, cand[c][0], cand[c][1], false, &ms));
         if (!best_nt || ms < best_ms) {
-            best_nt = cand[c];
+            best_nt = cand[c][0];
+            best_wide = cand[c][1];
             best_nb = (int)nb;
             best_ms = ms;
         }
@@ -2653,6 +2719,7 @@ static asss_status batch_tune(asss_batch* B, int nrhs, const double* bd, double*
         return ASSS_ERR_UNSUPPORTED;
     }
     B->nthreads = best_nt;
+    B->wide = best_wide;
     B->nblk = best_nb;
     B->tuned_nrhs = nrhs;
     return ASSS_OK;
@@ -2708,12 +2775,13 @@ asss_status asss_setup_batched(int nmat, const asss_csr* const* A, const asss_op
         }
         // algorithmic bytes of the inner solve (same model as the one-system mrs):
         // per step the stored diagonal entries once, the Q row, y (own, old, new),
-        // p and z read and written; per call the set-up and final passes
+        // p and z read and written; per call the set-up pass and the final pass (no Q
+        // there: Q^T z follows from the reduced Q^T y of the steps)
         {
             double nn = h->n, qrow = h->Q16.p ? 2.0 * h->kp16 : 4.0 * h->kp;
             const double mat = h->use_dia ? 4.0 * (double)h->D32.nnz : 8.0 * (double)h->J32.nnz;
             B->step_bytes.push_back(mat + nn * (28.0 + qrow));
-            B->call_bytes.push_back(nn * (8.0 + 16.0 + qrow) + nn * 16.0 + (h->k ? nn * qrow : 0.0));
+            B->call_bytes.push_back(nn * (8.0 + 16.0 + qrow) + nn * 16.0);
         }
         B->n_of.push_back(h->n);
         B->off_h.push_back(rows);
@@ -2771,7 +2839,7 @@ asss_status asss_solve_batched(asss_batch* B, int nrhs, const double* b, double*
     }
     if (B->tuned_nrhs != nrhs) ASSS_TRY(batch_tune(B, nrhs, bd, xd));
     float ms = 0.f;
-    ASSS_TRY(batch_run(B, nrhs, bd, xd, B->nthreads, true, &ms));
+    ASSS_TRY(batch_run(B, nrhs, bd, xd, B->nthreads, B->wide, true, &ms));
     if (!xdv) ASSS_CUDA(cudaMemcpyAsync(x, xd, sizeof(double) * total, cudaMemcpyDeviceToHost, B->own));
     std::vector<BatchItemStat> hs(B->items.n);
     ASSS_CUDA(cudaMemcpyAsync(hs.data(), B->stats.p, sizeof(BatchItemStat) * hs.size(), cudaMemcpyDeviceToHost,
@@ -2805,6 +2873,8 @@ asss_status asss_solve_batched(asss_batch* B, int nrhs, const double* b, double*
 }
 
 int asss_batch_cta_threads(const asss_batch* B) { return B ? B->nthreads : 0; }
+
+int asss_batch_cta_registers(const asss_batch* B) { return (B && B->nthreads) ? (B->wide ? 128 : 64) : 0; }
 
 void asss_destroy_batched(asss_batch* B) {
     if (!B) return;

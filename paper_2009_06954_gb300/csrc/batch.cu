@@ -12,6 +12,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "mrs_dev.cuh"
 
 namespace asss {
 
@@ -49,7 +50,11 @@ struct BatchShared {
     double cs[BATCH_RMAX + 1], sn[BATCH_RMAX + 1], g[BATCH_RMAX + 2], hv[BATCH_RMAX + 1], hv2[BATCH_RMAX + 1],
         yv[BATCH_RMAX + 1];
     float wv[BMMAX];  // U^T z for the SMW correction (FP32, like the inner solve)
+    // Q^T z of the final iterate from the reduced Q^T y_j (no pass over Q): Q^T y_j,
+    // Q^T p of the last two directions, Q^T z, and step j's nu, delta, 1/theta, xcoef
+    float qty[BKPMAX], qtp[2][BKPMAX], qtx[BKPMAX], pq[4];
     BScalars sc;
+    unsigned long long prof[BATCH_NPROF + 1];  // phase times of this CTA (thread 0), last stamp
     int item;
     int steps;
     int brk;
@@ -110,12 +115,34 @@ __device__ __forceinline__ void bdots(const double* __restrict__ V, long long ld
 // y = A x for a CSR matrix, one row per thread (rows strided over the block); the
 // diagonal copies of the one-system path measured slower here, where a CTA's rows are
 // few and the gathers hit L1
+// (WIDE: 128 registers a thread, so a row's indices and values are loaded eight at a
+// time ahead of their gathers)
+template <bool WIDE>
 __device__ __forceinline__ void bspmv(const int* __restrict__ rp, const int* __restrict__ ci,
                                       const double* __restrict__ v, const double* __restrict__ x,
                                       double* __restrict__ y, int n) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         double s = 0.0;
-        for (int e = rp[i]; e < rp[i + 1]; ++e) s += v[e] * x[ci[e]];
+        if constexpr (WIDE) {
+            const int e1 = rp[i + 1];
+            for (int e = rp[i]; e < e1; e += 8) {
+                int cc[8];
+                double vv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const bool in = e + u < e1;
+                    cc[u] = in ? ci[e + u] : 0;
+                    vv[u] = in ? v[e + u] : 0.0;
+                }
+                double g[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) g[u] = e + u < e1 ? x[cc[u]] : 0.0;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) s += vv[u] * g[u];
+            }
+        } else {
+            for (int e = rp[i]; e < rp[i + 1]; ++e) s += v[e] * x[ci[e]];
+        }
         y[i] = s;
     }
     __syncthreads();
@@ -164,26 +191,9 @@ __device__ __forceinline__ float2 bdf_add(float2 a, float2 b) {
 }
 
 // block reduction of the KP+1 per-thread sums of an mrs step into sh.red: warp sums
-// in FP32, then the warps added in a fixed order in float pairs
-template <int KP>
-__device__ __forceinline__ void bred(float (&tacc)[KP + 1], BatchShared& sh) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int v = 0; v <= KP; ++v) {
-        float d = warp_sum(tacc[v]);
-        if (lane == 0) sh.wsum[warp][v] = d;
-    }
-    __syncthreads();
-    for (int v = threadIdx.x; v <= KP; v += blockDim.x) {
-        float2 t = make_float2(0.f, 0.f);
-        for (int w = 0; w < nw; ++w) t = bdf_add(t, make_float2(sh.wsum[w][v], 0.f));
-        sh.red[v] = t.x + t.y;
-    }
-    __syncthreads();
-}
-
-// as bred, but only warp 0 adds the warps' sums and holds sh.red afterwards (the
-// scalar update that reads it runs in warp 0 too, so one block barrier is saved)
+// in FP32, then warp 0 adds the warps' sums in a fixed order in float pairs and holds
+// sh.red afterwards (the scalar update that reads it runs in warp 0 too, so one block
+// barrier is saved)
 template <int KP>
 __device__ __forceinline__ void bred_w0(float (&tacc)[KP + 1], BatchShared& sh) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -235,7 +245,7 @@ __device__ __forceinline__ void bset_coefs(BatchShared& sh) {
 
 // mrs (App. B) in block scope on (I + J_bar) z = u, J_bar = J~ - Q S_k Q^T, FP32 vectors;
 // z in FP32, Q^T z of the final iterate into sh.wv[0..k); returns the step count.
-template <int KP, bool QB>
+template <int KP, bool QB, bool WIDE>
 __device__ int bmrs(const double* u, float* z, float* Y, long long ys, float* P, double tol, int maxit,
                     BatchShared& sh) {
     const BatchMat& M = sh.M;
@@ -247,6 +257,22 @@ __device__ int bmrs(const double* u, float* z, float* Y, long long ys, float* P,
         int idx = e < h ? -h + e : n + (e - h);
         Y[slot * ys + idx] = 0.f;
     }
+    for (int m = threadIdx.x; m < KP; m += blockDim.x) {
+        sh.qtp[0][m] = 0.f;
+        sh.qtp[1][m] = 0.f;
+        sh.qtx[m] = 0.f;
+    }
+    // warp 1: fold direction p_jj into Q^T z (p_jj = (nu y_jj - delta p_{jj-2}) / theta,
+    // z = sum xcoef_jj p_jj)
+    auto qtx_fold = [&](int jj) {
+        const int ln = threadIdx.x & 31;
+        if (ln < M.k) {
+            float* pp = sh.qtp[jj & 1];
+            const float v = (sh.pq[0] * sh.qty[ln] - sh.pq[1] * pp[ln]) * sh.pq[2];
+            pp[ln] = v;
+            sh.qtx[ln] += sh.pq[3] * v;
+        }
+    };
     float tacc[KP + 1];
 #pragma unroll
     for (int v = 0; v <= KP; ++v) tacc[v] = 0.f;
@@ -309,6 +335,11 @@ __device__ int bmrs(const double* u, float* z, float* Y, long long ys, float* P,
     const int nd = M.ndiag;
     const int* __restrict__ soff = sh.off;
     for (int j = 1; j <= maxit; ++j) {
+        if (KP > 0 && warp0 == 1) {
+            // off the step's synchronisation chain: step j-1's direction, then Q^T y_j
+            if (j >= 2) qtx_fold(j - 1);
+            if (lane0 < M.k) sh.qty[lane0] = sh.red[1 + lane0];
+        }
         const float* __restrict__ Ycur = Y + (size_t)((j - 1) % 3) * ys;
         const float* __restrict__ Yold = Y + (size_t)((j + 1) % 3) * ys;
         float* __restrict__ Ynew = Y + (size_t)(j % 3) * ys;
@@ -339,9 +370,18 @@ __device__ int bmrs(const double* u, float* z, float* Y, long long ys, float* P,
             } else {
                 const float* Ud = Ubase + i;
                 const float* yi = Ycur + i;
-                for (int d = 0; d < nd; ++d, Ud += ust) {
-                    const int m = soff[d];
-                    acc += __ldg(Ud) * yi[m] - __ldg(Ud - m) * yi[-m];
+                if constexpr (WIDE) {
+                    // 128 registers: the loads of all diagonals of the row in flight together
+#pragma unroll 12
+                    for (int d = 0; d < nd; ++d, Ud += ust) {
+                        const int m = soff[d];
+                        acc += __ldg(Ud) * yi[m] - __ldg(Ud - m) * yi[-m];
+                    }
+                } else {
+                    for (int d = 0; d < nd; ++d, Ud += ust) {
+                        const int m = soff[d];
+                        acc += __ldg(Ud) * yi[m] - __ldg(Ud - m) * yi[-m];
+                    }
                 }
             }
             float q[KP > 0 ? KP : 1];
@@ -371,6 +411,10 @@ __device__ int bmrs(const double* u, float* z, float* Y, long long ys, float* P,
             const float theta_t_next = c.c_prev * theta;
             const float xcoef = c.G * cc;
             const float Gn = -c.G * s;
+            sh.pq[0] = c.nu;
+            sh.pq[1] = c.delta_prev;
+            sh.pq[2] = rth;
+            sh.pq[3] = xcoef;
             c.ratio = fabsf(Gn) * c.rr0;
             c.its = j;
             if (c.ratio < tol || j == maxit) {
@@ -402,19 +446,14 @@ __device__ int bmrs(const double* u, float* z, float* Y, long long ys, float* P,
         if (sh.sc.stop) {
             const float* __restrict__ Pj = P + (size_t)(j & 1) * n;
             const float tn = sh.cf[7], td = sh.cf[8], tth = sh.cf[9], tx = sh.cf[10];
-#pragma unroll
-            for (int v = 0; v <= KP; ++v) tacc[v] = 0.f;
             for (int i = threadIdx.x; i < n; i += blockDim.x) {
                 float pv = (tn * Ycur[i] - td * Pj[i]) * tth;
-                float xi = zz[i] + tx * pv;
-                zz[i] = xi;
-                float q[KP > 0 ? KP : 1];
-                bq_row<KP, QB>(M, i, q);
-#pragma unroll
-                for (int m = 0; m < KP; ++m) tacc[1 + m] += q[m] * xi;
+                zz[i] = zz[i] + tx * pv;
             }
-            bred<KP>(tacc, sh);
-            for (int v = threadIdx.x; v < M.k; v += blockDim.x) sh.wv[v] = sh.red[1 + v];
+            if (warp0 == 1) {
+                if (KP > 0) qtx_fold(j);
+                if (lane0 < M.k) sh.wv[lane0] = KP > 0 ? sh.qtx[lane0] : 0.f;
+            }
             __syncthreads();
             return sh.sc.its;
         }
@@ -422,11 +461,12 @@ __device__ int bmrs(const double* u, float* z, float* Y, long long ys, float* P,
     return sh.sc.its;
 }
 
-// 64 registers a thread at every CTA size: 1024 threads per SM in 1024 / NT
-// resident CTAs, so that while one CTA waits in a block reduction the others
-// keep loads in flight
-template <int KP, bool QB, int NT>
-__global__ void __launch_bounds__(NT, 1024 / NT) k_batch(BatchLaunch L) {
+// Two register budgets: 64 registers a thread (1024 threads per SM in 1024 / NT
+// resident CTAs, so that while one CTA waits in a block reduction the others keep
+// loads in flight), or WIDE: 128 registers (512 threads per SM), which lets a row's
+// loads - all diagonals of J~, a CSR row's entries - be in flight together
+template <int KP, bool QB, int NT, bool WIDE>
+__global__ void __launch_bounds__(NT, (WIDE ? 512 : 1024) / NT) k_batch(BatchLaunch L) {
     __shared__ BatchShared sh;
     const int R = L.restart;
     const long long nm = L.n_max;
@@ -443,6 +483,19 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_batch(BatchLaunch L) {
     float* Y = fb + L.halo_max;
     float* P = fb + 3 * ys;
     float* z32 = P + 2 * nm;
+    // optional phase timing (thread 0 stamps %globaltimer at block-synchronous points)
+    const bool prof = L.prof != nullptr;
+    auto mark = [&](int slot) {
+        if (prof && threadIdx.x == 0) {
+            const unsigned long long t = gtimer();
+            sh.prof[slot] += t - sh.prof[BATCH_NPROF];
+            sh.prof[BATCH_NPROF] = t;
+        }
+    };
+    if (prof && threadIdx.x == 0) {
+        for (int q = 0; q < BATCH_NPROF; ++q) sh.prof[q] = 0ull;
+        sh.prof[BATCH_NPROF] = gtimer();
+    }
 
     while (true) {
         if (threadIdx.x == 0) sh.item = (int)atomicAdd(L.next_item, 1u);
@@ -510,7 +563,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_batch(BatchLaunch L) {
                 double* vj = V + j * nm;
                 double* zj = Z + j * nm;
                 // z_j = P^-1 v_j: mrs, then z - Y (U^T z)
-                inner += bmrs<KP, QB>(vj, z32, Y, ys, P, L.inner_tol, L.inner_maxit, sh);
+                mark(5);
+                inner += bmrs<KP, QB, WIDE>(vj, z32, Y, ys, P, L.inner_tol, L.inner_maxit, sh);
+                mark(0);
                 for (int a = threadIdx.x; a < M.r; a += blockDim.x) sh.wv[M.k + a] = z32[M.neg[a]];
                 __syncthreads();
                 // FP32 correction (no per-row FP64 operation); rows of Y as float4 when possible
@@ -534,9 +589,11 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_batch(BatchLaunch L) {
                     zjr[i] = (double)(z32r[i] - acc);
                 }
                 __syncthreads();
+                mark(1);
                 // w = A_cal z_j = (W Abar) (S W) z_j, into t2
-                bspmv(M.swrp, M.swci, M.swv, zj, t1, n);
-                bspmv(M.awrp, M.awci, M.awv, t1, t2, n);
+                bspmv<WIDE>(M.swrp, M.swci, M.swv, zj, t1, n);
+                bspmv<WIDE>(M.awrp, M.awci, M.awv, t1, t2, n);
+                mark(2);
                 // two classical Gram-Schmidt passes
                 for (int pass = 0; pass < 2; ++pass) {
                     bdots(V, nm, j + 1, t2, n, pass == 0 ? sh.hv : sh.hv2, sh.wd);
@@ -573,9 +630,13 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_batch(BatchLaunch L) {
                     sh.brk = (hn == 0.0 || fabs(sh.g[j + 1]) <= eta * beta0) ? 1 : 0;
                 }
                 __syncthreads();
-                if (sh.brk) break;
+                if (sh.brk) {
+                    mark(3);
+                    break;
+                }
                 for (int i = threadIdx.x; i < n; i += blockDim.x) V[(j + 1) * nm + i] = t2[i] / hn;
                 __syncthreads();
+                mark(3);
             }
             const int steps = sh.steps;
             if (threadIdx.x == 0) {
@@ -594,14 +655,15 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_batch(BatchLaunch L) {
                 t1[i] = M.w[i] * acc;
             }
             __syncthreads();
-            bspmv(M.srp, M.sci, M.sv, t1, t2, n);
+            bspmv<WIDE>(M.srp, M.sci, M.sv, t1, t2, n);
             for (int i = threadIdx.x; i < n; i += blockDim.x) xcol[i] += M.dc[i] * t2[i];
             __syncthreads();
-            bspmv(M.arp, M.aci, M.av, xcol, t1, n);
+            bspmv<WIDE>(M.arp, M.aci, M.av, xcol, t1, n);
             for (int i = threadIdx.x; i < n; i += blockDim.x) r[i] = bcol[i] - t1[i];
             __syncthreads();
             outer += steps;
             ++cycles;
+            mark(4);
         }
         if (threadIdx.x == 0) {
             BatchItemStat st;
@@ -614,25 +676,32 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_batch(BatchLaunch L) {
         }
         __syncthreads();
     }
+    if (prof && threadIdx.x == 0) {
+        mark(5);
+        for (int q = 0; q < BATCH_NPROF; ++q) atomicAdd(&L.prof[q], sh.prof[q]);
+    }
 }
 
 template <int KP, bool QB>
-static asss_status launch_nt(const BatchLaunch& L, int nthreads, int nblk, cudaStream_t s) {
-    switch (nthreads) {
-        case 128:
-            k_batch<KP, QB, 128><<<nblk, 128, 0, s>>>(L);
+static asss_status launch_nt(const BatchLaunch& L, int nthreads, int wide, int nblk, cudaStream_t s) {
+    switch (nthreads * 2 + (wide ? 1 : 0)) {
+        case 128 * 2:
+            k_batch<KP, QB, 128, false><<<nblk, 128, 0, s>>>(L);
             break;
-        case 256:
-            k_batch<KP, QB, 256><<<nblk, 256, 0, s>>>(L);
+        case 256 * 2:
+            k_batch<KP, QB, 256, false><<<nblk, 256, 0, s>>>(L);
             break;
-        case 512:
-            k_batch<KP, QB, 512><<<nblk, 512, 0, s>>>(L);
+        case 512 * 2:
+            k_batch<KP, QB, 512, false><<<nblk, 512, 0, s>>>(L);
             break;
-        case 1024:
-            k_batch<KP, QB, 1024><<<nblk, 1024, 0, s>>>(L);
+        case 1024 * 2:
+            k_batch<KP, QB, 1024, false><<<nblk, 1024, 0, s>>>(L);
+            break;
+        case 512 * 2 + 1:
+            k_batch<KP, QB, 512, true><<<nblk, 512, 0, s>>>(L);
             break;
         default:
-            set_error("batched solver: unsupported CTA size %d", nthreads);
+            set_error("batched solver: unsupported CTA shape %d (wide %d)", nthreads, wide);
             return ASSS_ERR_ARG;
     }
     ASSS_CHECK_LAUNCH();
@@ -640,22 +709,25 @@ static asss_status launch_nt(const BatchLaunch& L, int nthreads, int nblk, cudaS
 }
 
 template <int KP, bool QB>
-static asss_status occ_nt(int nthreads, int* occ) {
-    switch (nthreads) {
-        case 128:
-            ASSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_batch<KP, QB, 128>, 128, 0));
+static asss_status occ_nt(int nthreads, int wide, int* occ) {
+    switch (nthreads * 2 + (wide ? 1 : 0)) {
+        case 128 * 2:
+            ASSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_batch<KP, QB, 128, false>, 128, 0));
             return ASSS_OK;
-        case 256:
-            ASSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_batch<KP, QB, 256>, 256, 0));
+        case 256 * 2:
+            ASSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_batch<KP, QB, 256, false>, 256, 0));
             return ASSS_OK;
-        case 512:
-            ASSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_batch<KP, QB, 512>, 512, 0));
+        case 512 * 2:
+            ASSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_batch<KP, QB, 512, false>, 512, 0));
             return ASSS_OK;
-        case 1024:
-            ASSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_batch<KP, QB, 1024>, 1024, 0));
+        case 1024 * 2:
+            ASSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_batch<KP, QB, 1024, false>, 1024, 0));
+            return ASSS_OK;
+        case 512 * 2 + 1:
+            ASSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_batch<KP, QB, 512, true>, 512, 0));
             return ASSS_OK;
     }
-    set_error("batched solver: unsupported CTA size %d", nthreads);
+    set_error("batched solver: unsupported CTA shape %d (wide %d)", nthreads, wide);
     return ASSS_ERR_ARG;
 }
 
@@ -676,13 +748,13 @@ static asss_status occ_nt(int nthreads, int* occ) {
             return ASSS_ERR_UNSUPPORTED;                                                 \
     }
 
-asss_status batch_launch(const BatchLaunch& L, int nthreads, int nblk, cudaStream_t s) {
+asss_status batch_launch(const BatchLaunch& L, int nthreads, int wide, int nblk, cudaStream_t s) {
     const int kp = L.kp, qbf16 = L.qbf16;
-    ASSS_BATCH_DISPATCH(launch_nt, L, nthreads, nblk, s)
+    ASSS_BATCH_DISPATCH(launch_nt, L, nthreads, wide, nblk, s)
 }
 
-asss_status batch_occupancy(int kp, int qbf16, int nthreads, int* occ) {
-    ASSS_BATCH_DISPATCH(occ_nt, nthreads, occ)
+asss_status batch_occupancy(int kp, int qbf16, int nthreads, int wide, int* occ) {
+    ASSS_BATCH_DISPATCH(occ_nt, nthreads, wide, occ)
 }
 
 }  // namespace asss

@@ -231,12 +231,15 @@ struct BatchLaunch {
     int inner_maxit;
     unsigned* next_item;
     BatchItemStat* stats;
+    unsigned long long* prof;   // optional (may be null): nanoseconds per phase summed over CTAs
 };
+constexpr int BATCH_NPROF = 6;  // mrs, SMW correction, operator, Gram-Schmidt, x update + residual, rest
 
 // launches the persistent batched solver on stream s with nthreads per CTA and nblk CTAs
-asss_status batch_launch(const BatchLaunch& L, int nthreads, int nblk, cudaStream_t s);
-// resident CTAs per SM of the batched solver for a CTA size
-asss_status batch_occupancy(int kp, int qbf16, int nthreads, int* occ);
+// (wide: the 128-register build, 512 threads per SM)
+asss_status batch_launch(const BatchLaunch& L, int nthreads, int wide, int nblk, cudaStream_t s);
+// resident CTAs per SM of the batched solver for a CTA size and register budget
+asss_status batch_occupancy(int kp, int qbf16, int nthreads, int wide, int* occ);
 constexpr int BATCH_RMAX = 24;
 
 // fused Arnoldi step of FGMRES (arnoldi.cu): CGS2 + norm + Givens + next basis vector

@@ -69,8 +69,6 @@ struct MrsWork {
     std::vector<long long> log_nnz, log_per_row;  // bytes model per launch
     int log_n = 0;
     MrsTotals tot;
-    DBuf<double> qtz_part;   // [KPMAX][maxblk] partials of the fused Q^T x
-    DBuf<unsigned> qtz_done; // last-block counter
     DBuf<unsigned long long> trace;  // ASSS_TRACE_MRS=1: timeline of block 0
     ~MrsWork() {
         if (ev0) cudaEventDestroy(ev0);
@@ -102,13 +100,11 @@ asss_status mrs_work_create(MrsWork** w, int n, int sms) {
         return st;
     }
     if ((st = m->its_log.alloc(MrsWork::LOG_CAP)) != ASSS_OK ||
-        (st = m->ratio_log.alloc(MrsWork::LOG_CAP)) != ASSS_OK ||
-        (st = m->qtz_part.alloc((int64_t)MRS_KPMAX * maxblk)) != ASSS_OK || (st = m->qtz_done.alloc(1)) != ASSS_OK) {
+        (st = m->ratio_log.alloc(MrsWork::LOG_CAP)) != ASSS_OK) {
         delete m;
         return st;
     }
-    if (cudaMemset(m->qtz_done.p, 0, sizeof(unsigned)) != cudaSuccess ||
-        cudaMemset(m->err.p, 0, sizeof(int)) != cudaSuccess) {
+    if (cudaMemset(m->err.p, 0, sizeof(int)) != cudaSuccess) {
         delete m;
         set_error("cudaMemset failed");
         return ASSS_ERR_CUDA;
@@ -170,56 +166,8 @@ struct MrsParams {
     unsigned long long* trace;  // optional timeline (block 0): %globaltimer at phase boundaries
     const int* skip;     // optional: when *skip != 0 at launch the kernel only logs its = -1
     int qcs;             // load Q rows evict-first (the step's data exceed L2)
-    double* qtz;         // optional: Q^T x (k values) computed in the final pass
-    double* qtz_part;    // [KP][nblk] block partials for it
-    unsigned* qtz_done;  // last-block counter (left at 0)
+    double* qtz;         // optional: Q^T x (k values) of the final iterate
 };
-
-// Q^T x of the final iterate: block partials, then the last block to finish adds
-// them in block order and writes p.qtz (no block waits for another).
-template <class T, int KP>
-__device__ __forceinline__ void qtz_reduce(const MrsParams<T>& p, T (&tacc)[KP + 1], T (&s_wsum)[MRS_WARPS][KP + 1],
-                                           int warp, int lane) {
-    __shared__ int s_last;
-    const int nblk = gridDim.x;
-#pragma unroll
-    for (int v = 1; v <= KP; ++v) {
-        T d = warp_sum(tacc[v]);
-        if (lane == 0) s_wsum[warp][v] = d;
-    }
-    __syncthreads();
-    for (int v = threadIdx.x; v < p.k; v += MRS_THREADS) {
-        double t;
-        if constexpr (sizeof(T) == 4) {
-            float2 a = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int w = 0; w < MRS_WARPS; ++w) a = df_add(a, make_float2(s_wsum[w][1 + v], 0.f));
-            t = (double)a.x + (double)a.y;
-        } else {
-            t = 0.0;
-#pragma unroll
-            for (int w = 0; w < MRS_WARPS; ++w) t += s_wsum[w][1 + v];
-        }
-        p.qtz_part[v * nblk + blockIdx.x] = t;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        unsigned t = atomicAdd(p.qtz_done, 1u);
-        s_last = (t == (unsigned)nblk - 1);
-    }
-    __syncthreads();
-    if (s_last) {
-        __threadfence();
-        for (int v = warp; v < p.k; v += MRS_WARPS) {
-            double t = 0.0;
-            for (int b = lane; b < nblk; b += 32) t += __ldcg(&p.qtz_part[v * nblk + b]);
-            t = warp_sum(t);
-            if (lane == 0) p.qtz[v] = t;
-        }
-        if (threadIdx.x == 0) atomicExch(p.qtz_done, 0u);
-    }
-}
 
 // sum over q in [q0, q1) of v[q] * x[ci[q]], eight entries at a time: the indices
 // and values of a batch are loaded first, then all its gathers, so a row costs a
@@ -271,8 +219,20 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
     // 7..10 the final pass: nu, delta, 1/theta, xcoef
     __shared__ T s_cf[12];
     __shared__ int s_next;   // SELL: next work unit of this block for the warp that asks (see next_slice)
+    // Q^T x of the final iterate without a pass over Q: the directions obey
+    // p_j = (nu_j y_j - delta_j p_{j-2}) / theta_j and x = sum_j xcoef_j p_j, so Q^T p_j and
+    // Q^T x follow from the Q^T y_j that every step reduces anyway (warp 1 keeps them)
+    __shared__ T s_qty[KP > 0 ? KP : 1];     // Q^T y_j of the step in progress
+    __shared__ T s_qtp[2][KP > 0 ? KP : 1];  // Q^T p of the last two directions (slot j & 1)
+    __shared__ T s_qtx[KP > 0 ? KP : 1];     // Q^T x
+    __shared__ T s_pq[4];                    // step j: nu_j, delta, 1/theta_j, xcoef_j
     if constexpr (FMT == 1) {
         for (int d = threadIdx.x; d < p.ndiag; d += MRS_THREADS) s_off[d] = p.off[d];
+    }
+    for (int m = threadIdx.x; m < KP; m += MRS_THREADS) {
+        s_qtp[0][m] = (T)0;
+        s_qtp[1][m] = (T)0;
+        s_qtx[m] = (T)0;
     }
     if constexpr (FMT == 3) {
         for (int c = threadIdx.x; c <= p.ncol; c += MRS_THREADS) s_ls[c] = p.fls[c];
@@ -405,6 +365,18 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
             }
         }
     };
+    // warp 1: fold direction p_jj into Q^T x (s_pq holds step jj's scalars, s_qty Q^T y_jj)
+    auto qtx_fold = [&](int jj) {
+        if constexpr (KP > 0) {
+            if (lane < p.k) {
+                T* pp = s_qtp[jj & 1];
+                const T v = (s_pq[0] * s_qty[lane] - s_pq[1] * pp[lane]) * s_pq[2];
+                pp[lane] = v;
+                s_qtx[lane] += s_pq[3] * v;
+            }
+        }
+    };
+    const bool want_qtx = KP > 0 && p.qtz != nullptr;
     unsigned phase = 0;  // grid barriers passed in this launch
     // ---- phase 0: y_1 = b, x = 0, p = 0, ||b||^2 and Q^T b ----
     T tacc[NV];
@@ -496,6 +468,12 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
 
     for (int j = 1; j <= p.maxit; ++j) {
         const int tb = 4 + 5 * (j - 1);
+        if (want_qtx && warp == 1) {
+            // off the synchronisation chain: step j-1's direction, then Q^T y_j from the
+            // last reduction (s_red is next written after this pass's block barrier)
+            if (j >= 2) qtx_fold(j - 1);
+            if (lane < p.k) s_qty[lane] = s_red[1 + lane];
+        }
         // the step's vectors do not overlap: restrict lets later rows' loads be scheduled
         // ahead of this row's stores
         const T* __restrict__ Ycur = p.Y + (size_t)((j - 1) % 3) * ys;
@@ -689,6 +667,10 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
                 const T theta_t_next = sc.c_prev * theta;
                 const T xcoef = sc.G * c;
                 const T Gn = -sc.G * s;
+                s_pq[0] = sc.nu;
+                s_pq[1] = sc.delta_prev;
+                s_pq[2] = rth;
+                s_pq[3] = xcoef;
                 sc.ratio = fabs(Gn) * sc.rr0;
                 sc.its = j;
                 if (sc.ratio < p.tol || j == p.maxit) {
@@ -726,21 +708,12 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
                 int i = row_of(sl);
                 if (i < n) {
                     T pv = (tn * Ycur[i] - td * Pj[i]) * tth;
-                    T xi = p.x[i] + tx * pv;
-                    p.x[i] = xi;
-                    if constexpr (KP > 0) {
-                        if (p.qtz) {
-                            T q[KP];
-                            if constexpr (QB) load_qrow16<T, KP>(p.Q16, i, q);
-                            else load_qrow<T, KP>(p.Q, i, q, p.qcs != 0);
-#pragma unroll
-                            for (int m = 0; m < KP; ++m) tacc[1 + m] += q[m] * xi;
-                        }
-                    }
+                    p.x[i] = p.x[i] + tx * pv;
                 }
             }
-            if constexpr (KP > 0) {
-                if (p.qtz) qtz_reduce<T, KP>(p, tacc, s_wsum, warp, lane);
+            if (want_qtx && warp == 1) {
+                qtx_fold(j);
+                if (blockIdx.x == 0 && lane < p.k) p.qtz[lane] = (double)s_qtx[lane];
             }
             break;
         }
@@ -889,8 +862,6 @@ static asss_status launch_mrs(const Ctx& c, MrsWork* w, const OpView<T>& J, cons
         const long long qrow = QB ? 2LL * KP : (long long)sizeof(T) * KP;
         prm.qcs = stream_evict_first(c, J.nnz * (long long)sizeof(T) + (long long)J.n * (7LL * sizeof(T) + qrow)) ? 1 : 0;
     }
-    prm.qtz_part = w->qtz_part.p;
-    prm.qtz_done = w->qtz_done.p;
     void* args[] = {&prm};
     ASSS_CUDA(cudaEventRecord(w->evs[2 * lo.slot], c.stream));
     ASSS_CUDA(cudaLaunchCooperativeKernel((const void*)k_mrs<T, KP, FMT, QB>, dim3(nblk), dim3(MRS_THREADS), args,
@@ -1067,7 +1038,7 @@ asss_status mrs_solve(const Ctx& c, MrsWork* w, const MrsOperator& op, bool fp32
     }
     // algorithmic bytes: set-up pass (rhs in FP64, Y/x/P written, Q row), per step
     // (matrix entries - SELL ones with a 4-byte index -, Q row, gathered/own y,
-    // y_old, y_new, p r/w, x r/w), final pass (y, p, x r/w, and the Q row for Q^T x)
+    // y_old, y_new, p r/w, x r/w), final pass (y, p, x r/w; Q^T x needs no pass over Q)
     long long T = fp32 ? 4 : 8;
     long long nn = n, kp = op.kp;
     long long qrow = (fp32 && op.Q16) ? 2LL * op.kp16 : kp * T;  // bytes of one Q row as read
@@ -1076,7 +1047,7 @@ asss_status mrs_solve(const Ctx& c, MrsWork* w, const MrsOperator& op, bool fp32
         w->log_nnz.resize(lo.slot + 1);
         w->log_per_row.resize(lo.slot + 1);
     }
-    w->log_nnz[lo.slot] = nn * (8 + 4 * T + qrow) + nn * 4 * T + ((qtz && op.k) ? nn * qrow : 0);
+    w->log_nnz[lo.slot] = nn * (8 + 4 * T + qrow) + nn * 4 * T;
     // factored operator: + wd, t written and gathered, w written and gathered, per step
     w->log_per_row[lo.slot] = nnz_read * per_entry + nn * (7 * T + qrow) + (op.F ? nn * 5 * T : 0);
     w->log_n++;

@@ -42,7 +42,7 @@ def test_batched_matches_exact_solutions(pkg, batch):
     assert bs.cta_threads == 0
     nrhs = Bs[0].shape[1]
     x, st = bs.solve(bs.pack(Bs), nrhs=nrhs)
-    assert bs.cta_threads in (128, 256, 512, 1024)
+    assert (bs.cta_threads, bs.cta_registers) in {(128, 64), (256, 64), (512, 64), (1024, 64), (512, 128)}
     assert st["status"] == 0
     assert st["inner_solves"] == len(As) * nrhs
     assert st["relres"] <= 1e-8
@@ -194,4 +194,26 @@ def test_batched_general_patterns_use_sell(pkg):
             assert r <= 1e-8, r
         assert np.linalg.norm(Xm - xs) <= 1e-6 * np.linalg.norm(xs)
     assert st["status"] == 0
+    bs.close()
+
+
+@pytest.mark.parametrize("shape", ["128", "256", "512", "1024", "512w"])
+def test_batched_every_cta_shape_meets_the_tolerance(pkg, batch, shape, monkeypatch):
+    """Each CTA shape the tuner may pick (64 registers a thread at 128..1024 threads,
+    or 128 registers at 512 threads with a row's loads unrolled) solves every item to
+    the outer tolerance and agrees with the exact solution."""
+    monkeypatch.setenv("ASSS_BATCH_CTA", shape)
+    As = [A for A, _ in batch]
+    Bs = [B for _, B in batch]
+    bs = pkg.BatchSolver(As, inner_tol=1e-6, restart=24)
+    nrhs = Bs[0].shape[1]
+    x, st = bs.solve(bs.pack(Bs), nrhs=nrhs)
+    assert bs.cta_threads == int(shape.rstrip("w"))
+    assert bs.cta_registers == (128 if shape.endswith("w") else 64)
+    assert st["status"] == 0 and st["relres"] <= 1e-8
+    X = bs.unpack(x, nrhs)
+    _check_columns(batch, X, Bs)
+    for (A, _), xm, b in zip(batch, X, Bs):
+        xe = spla.spsolve(A.tocsc(), b)
+        assert np.linalg.norm(xm - xe) <= 1e-6 * np.linalg.norm(xe)
     bs.close()
