@@ -549,7 +549,8 @@ def main_batched(args, world, rank, local):
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak if peak else None,
                      "peak_source": f"{peak_kind} hbm_gbs", "traffic": None,
                      "algorithmic_bytes_per_launch": inner_bytes / max(len(stats), 1),
-                     "bytes_model": "inner mrs steps only (a lower bound on the launch's bytes)",
+                     "bytes_model": ("inner mrs steps only: each column's vectors, and J~ and Q of its matrix "
+                                     "once per step for all its columns (the SpMM form's unique bytes)"),
                      "avg_launch_ms": total_ms / max(len(stats), 1), "launches": len(stats)},
         "clocks": clk.summary(),
         "cpu_baseline": cpu,

@@ -260,13 +260,13 @@ asss_status asss_setup_batched(int nmat, const asss_csr* const* A, const asss_op
  * n_m x nrhs inside.  x is overwritten.  st (may be NULL): outer_its = the largest
  * over items, inner_its_total and cycles summed, relres = the largest, inner_solves
  * = number of items, t_inner_ms = device time of the batched launch, inner_bytes =
- * the algorithmic bytes of the inner mrs steps (the one-system byte model summed
- * over items).  Returns the
+ * the algorithmic bytes of the inner mrs steps (each column's vectors, plus J~ and
+ * Q of its matrix divided among the nrhs columns that share them).  Returns the
  * first non-OK item status (x then holds every item's last iterate).  The first
- * call for a given nrhs tunes the CTA shape: it solves the batch once at each of
- * 128, 256, 512 and 1024 threads per CTA with 64 registers a thread, and at 512
- * threads with 128 registers a thread (as many CTAs per SM as fit, at most one CTA
- * per item), and keeps the fastest for later calls; that call takes about six
+ * call for a given nrhs tunes the CTA shape: it solves the batch once with each of
+ * six shapes - 256 and 512 threads per CTA at 64 registers a thread, 256 and 384
+ * threads at 80, 256 and 512 threads at 128 (as many CTAs per SM as fit, at most one
+ * CTA per item) - and keeps the fastest for later calls; that call takes about seven
  * times as long. */
 asss_status asss_solve_batched(asss_batch* b, int nrhs, const double* rhs, double* x,
                                asss_stats* st);
@@ -274,8 +274,8 @@ asss_status asss_solve_batched(asss_batch* b, int nrhs, const double* rhs, doubl
 /* CTA size chosen by the tuner (0 before the first solve). */
 int asss_batch_cta_threads(const asss_batch* b);
 
-/* Registers a thread of the CTA shape chosen by the tuner (64 or 128; 0 before the
- * first solve). */
+/* Registers a thread of the CTA shape chosen by the tuner (64, 80 or 128; 0 before
+ * the first solve). */
 int asss_batch_cta_registers(const asss_batch* b);
 
 void asss_destroy_batched(asss_batch* b);

@@ -426,7 +426,7 @@ class BatchSolver:
 
     @property
     def cta_registers(self):
-        """Registers a thread of the CTA shape picked by the tuner (64 or 128; 0 before it)."""
+        """Registers a thread of the CTA shape picked by the tuner (64, 80 or 128; 0 before it)."""
         return int(lib().asss_batch_cta_registers(self._h)) if getattr(self, "_h", None) else 0
 
     def close(self):

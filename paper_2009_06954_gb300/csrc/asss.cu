@@ -2488,19 +2488,22 @@ struct asss_batch {
     DBuf<long long> row_off;
     DBuf<double> work;
     long long work_stride = 0;
-    int nblk = 0, nthreads = 0, wide = 0, tuned_nrhs = -1;
+    int nblk = 0, nthreads = 0, minb = 0, tuned_nrhs = -1;
     DBuf<unsigned> counter;
     DBuf<BatchItemStat> stats;
     DBuf<unsigned long long> prof;  // ASSS_BATCH_PROFILE: phase times
     DBuf<int2> items;
     std::vector<int2> items_h;
-    std::vector<double> step_bytes, call_bytes;   // mrs byte model per matrix
+    // mrs byte model per matrix: per step, the bytes of one column (vectors) and the bytes
+    // its columns share (J~ and Q: an SpMM reads them once per step for all columns);
+    // per call, the set-up and final passes of one column and the Q row they share
+    std::vector<double> step_col_bytes, step_shared_bytes, call_col_bytes, call_shared_bytes;
     int items_nrhs = -1;
     DBuf<double> bdev, xdev;
     cudaGraphExec_t gexec = nullptr;
     const void* g_b = nullptr;
     const void* g_x = nullptr;
-    int g_nrhs = -1, g_nt = -1, g_wide = -1;
+    int g_nrhs = -1, g_nt = -1, g_minb = -1;
     ~asss_batch() {
         if (gexec) cudaGraphExecDestroy(gexec);
         for (asss_handle* h : hs) delete h;
@@ -2588,7 +2591,7 @@ static asss_status batch_items(asss_batch* B, int nrhs) {
     return ASSS_OK;
 }
 
-static asss_status batch_run(asss_batch* B, int nrhs, const double* bd, double* xd, int nthreads, int wide,
+static asss_status batch_run(asss_batch* B, int nrhs, const double* bd, double* xd, int nthreads, int minb,
                              bool use_graph, float* ms) {
     ASSS_TRY(batch_items(B, nrhs));
     BatchLaunch L;
@@ -2627,7 +2630,7 @@ static asss_status batch_run(asss_batch* B, int nrhs, const double* bd, double* 
     cudaStream_t s = B->own;
     if (use_graph) {
         if (!B->gexec || B->g_b != bd || B->g_x != xd || B->g_nrhs != nrhs || B->g_nt != nthreads ||
-            B->g_wide != wide) {
+            B->g_minb != minb) {
             if (B->gexec) {
                 cudaGraphExecDestroy(B->gexec);
                 B->gexec = nullptr;
@@ -2636,7 +2639,7 @@ static asss_status batch_run(asss_batch* B, int nrhs, const double* bd, double* 
             ASSS_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
             asss_status st = ASSS_OK;
             if (cudaMemsetAsync(B->counter.p, 0, sizeof(unsigned), s) != cudaSuccess) st = ASSS_ERR_CUDA;
-            if (st == ASSS_OK) st = batch_launch(L, nthreads, wide, nblk, s);
+            if (st == ASSS_OK) st = batch_launch(L, nthreads, minb, nblk, s);
             cudaError_t e = cudaStreamEndCapture(s, &g);
             if (st != ASSS_OK) return st;
             if (e != cudaSuccess) {
@@ -2653,7 +2656,7 @@ static asss_status batch_run(asss_batch* B, int nrhs, const double* bd, double* 
             B->g_x = xd;
             B->g_nrhs = nrhs;
             B->g_nt = nthreads;
-            B->g_wide = wide;
+            B->g_minb = minb;
         }
         ASSS_CUDA(cudaEventRecord(B->ev_t0, s));
         ASSS_CUDA(cudaGraphLaunch(B->gexec, s));
@@ -2662,7 +2665,7 @@ static asss_status batch_run(asss_batch* B, int nrhs, const double* bd, double* 
     } else {
         ASSS_CUDA(cudaEventRecord(B->ev_t0, s));
         ASSS_CUDA(cudaMemsetAsync(B->counter.p, 0, sizeof(unsigned), s));
-        ASSS_TRY(batch_launch(L, nthreads, wide, nblk, s));
+        ASSS_TRY(batch_launch(L, nthreads, minb, nblk, s));
         ASSS_CUDA(cudaEventRecord(B->ev_t1, s));
     }
     ASSS_CUDA(cudaStreamSynchronize(s));
@@ -2672,32 +2675,35 @@ static asss_status batch_run(asss_batch* B, int nrhs, const double* bd, double* 
         ASSS_CUDA(cudaMemcpy(t, B->prof.p, sizeof(t), cudaMemcpyDeviceToHost));
         const double per = 1e-6 / (nblk > 0 ? nblk : 1);
         fprintf(stderr,
-                "asss batch profile (%d threads%s, %d CTAs, launch %.2f ms; ms per CTA): mrs %.2f | smw %.2f | "
+                "asss batch profile (%d threads x %d per SM, %d CTAs, launch %.2f ms; ms per CTA): mrs %.2f | smw %.2f | "
                 "operator %.2f | gram-schmidt %.2f | update+residual %.2f | rest %.2f\n",
-                nthreads, wide ? ", 128 registers" : "", nblk, ms ? *ms : 0.f, t[0] * per, t[1] * per, t[2] * per,
+                nthreads, minb, nblk, ms ? *ms : 0.f, t[0] * per, t[1] * per, t[2] * per,
                 t[3] * per, t[4] * per, t[5] * per);
     }
     return ASSS_OK;
 }
 
-// CTA shape for a number of right-hand sides: each candidate (128 / 256 / 512 / 1024
-// threads at 64 registers, or 512 threads at 128 registers; as many CTAs as fit on the
-// GPU, at most one per item) solves the caller's batch once, timed with CUDA events;
-// the fastest is kept for later calls
+// CTA shape for a number of right-hand sides: each candidate (threads per CTA and the
+// resident CTAs per SM it is built for, which set the registers a thread may use: 64 at
+// 1024 threads per SM, 80 at 768, 128 at 512; as many CTAs as fit on the GPU, at most one
+// per item) solves the caller's batch once, timed with CUDA events; the fastest is kept
+// for later calls
 static asss_status batch_tune(asss_batch* B, int nrhs, const double* bd, double* xd) {
-    const int cand[5][2] = {{128, 0}, {256, 0}, {512, 0}, {1024, 0}, {512, 1}};
+    constexpr int NC = 6;
+    const int cand[NC][2] = {{256, 4}, {512, 2}, {256, 3}, {384, 2}, {256, 2}, {512, 1}};
     const long long nitems = (long long)B->hs.size() * nrhs;
-    int best_nt = 0, best_wide = 0, best_nb = 0;
+    int best_nt = 0, best_minb = 0, best_nb = 0;
     float best_ms = 0.f;
-    // ASSS_BATCH_CTA = "<threads>" or "<threads>w" (128 registers) restricts the tuner
-    // to that one shape (tests run every shape this way)
-    int force_nt = 0, force_wide = 0;
+    // ASSS_BATCH_CTA = "<threads>x<CTAs per SM>" restricts the tuner to that one shape
+    // (tests run every shape this way)
+    int force_nt = 0, force_minb = 0;
     if (const char* f = getenv("ASSS_BATCH_CTA")) {
         force_nt = atoi(f);
-        force_wide = strchr(f, 'w') != nullptr;
+        const char* xpos = strchr(f, 'x');
+        force_minb = xpos ? atoi(xpos + 1) : 0;
     }
-    for (int c = 0; c < 5; ++c) {
-        if (force_nt && (cand[c][0] != force_nt || cand[c][1] != force_wide)) continue;
+    for (int c = 0; c < NC; ++c) {
+        if (force_nt && (cand[c][0] != force_nt || cand[c][1] != force_minb)) continue;
         int occ = 0;
         ASSS_TRY(batch_occupancy(B->kp, B->qbf16, cand[c][0], cand[c][1], &occ));
         if (occ < 1) continue;
@@ -2709,17 +2715,17 @@ static asss_status batch_tune(asss_batch* B, int nrhs, const double* bd, double*
         ASSS_TRY(batch_run(B, nrhs, bd, xd, cand[c][0], cand[c][1], false, &ms));
         if (!best_nt || ms < best_ms) {
             best_nt = cand[c][0];
-            best_wide = cand[c][1];
+            best_minb = cand[c][1];
             best_nb = (int)nb;
             best_ms = ms;
         }
     }
     if (!best_nt) {
-        set_error("batched solver: no CTA size fits on this device");
+        set_error("batched solver: no CTA shape fits on this device");
         return ASSS_ERR_UNSUPPORTED;
     }
     B->nthreads = best_nt;
-    B->wide = best_wide;
+    B->minb = best_minb;
     B->nblk = best_nb;
     B->tuned_nrhs = nrhs;
     return ASSS_OK;
@@ -2773,15 +2779,18 @@ asss_status asss_setup_batched(int nmat, const asss_csr* const* A, const asss_op
             s = ASSS_ERR_UNSUPPORTED;
             break;
         }
-        // algorithmic bytes of the inner solve (same model as the one-system mrs):
-        // per step the stored diagonal entries once, the Q row, y (own, old, new),
-        // p and z read and written; per call the set-up pass and the final pass (no Q
-        // there: Q^T z follows from the reduced Q^T y of the steps)
+        // algorithmic bytes of the inner solve: per step the stored entries of J~ and the
+        // Q rows - shared by all columns of the matrix, as the SpMM form of the step reads
+        // them once per step - and per column y (own, old, new), p and z read and
+        // written; per call the set-up pass (b in FP64, y, z, p written; Q shared) and the
+        // final pass (no Q there: Q^T z follows from the reduced Q^T y of the steps)
         {
             double nn = h->n, qrow = h->Q16.p ? 2.0 * h->kp16 : 4.0 * h->kp;
             const double mat = h->use_dia ? 4.0 * (double)h->D32.nnz : 8.0 * (double)h->J32.nnz;
-            B->step_bytes.push_back(mat + nn * (28.0 + qrow));
-            B->call_bytes.push_back(nn * (8.0 + 16.0 + qrow) + nn * 16.0);
+            B->step_col_bytes.push_back(nn * 28.0);
+            B->step_shared_bytes.push_back(mat + nn * qrow);
+            B->call_col_bytes.push_back(nn * (8.0 + 16.0) + nn * 16.0);
+            B->call_shared_bytes.push_back(nn * qrow);
         }
         B->n_of.push_back(h->n);
         B->off_h.push_back(rows);
@@ -2839,7 +2848,7 @@ asss_status asss_solve_batched(asss_batch* B, int nrhs, const double* b, double*
     }
     if (B->tuned_nrhs != nrhs) ASSS_TRY(batch_tune(B, nrhs, bd, xd));
     float ms = 0.f;
-    ASSS_TRY(batch_run(B, nrhs, bd, xd, B->nthreads, B->wide, true, &ms));
+    ASSS_TRY(batch_run(B, nrhs, bd, xd, B->nthreads, B->minb, true, &ms));
     if (!xdv) ASSS_CUDA(cudaMemcpyAsync(x, xd, sizeof(double) * total, cudaMemcpyDeviceToHost, B->own));
     std::vector<BatchItemStat> hs(B->items.n);
     ASSS_CUDA(cudaMemcpyAsync(hs.data(), B->stats.p, sizeof(BatchItemStat) * hs.size(), cudaMemcpyDeviceToHost,
@@ -2852,7 +2861,8 @@ asss_status asss_solve_batched(asss_batch* B, int nrhs, const double* b, double*
     for (size_t q = 0; q < hs.size(); ++q) {
         const BatchItemStat& t = hs[q];
         const int m = B->items_h[q].x;
-        bytes += t.inner_its * B->step_bytes[m] + t.outer_its * B->call_bytes[m];
+        bytes += t.inner_its * (B->step_col_bytes[m] + B->step_shared_bytes[m] / nrhs) +
+                 t.outer_its * (B->call_col_bytes[m] + B->call_shared_bytes[m] / nrhs);
         if (t.outer_its > a.outer_its) a.outer_its = t.outer_its;
         a.inner_its_total += t.inner_its;
         a.cycles += t.cycles;
@@ -2874,7 +2884,11 @@ asss_status asss_solve_batched(asss_batch* B, int nrhs, const double* b, double*
 
 int asss_batch_cta_threads(const asss_batch* B) { return B ? B->nthreads : 0; }
 
-int asss_batch_cta_registers(const asss_batch* B) { return (B && B->nthreads) ? (B->wide ? 128 : 64) : 0; }
+int asss_batch_cta_registers(const asss_batch* B) {
+    if (!B || !B->nthreads || !B->minb) return 0;
+    const int r = 65536 / (B->nthreads * B->minb);
+    return (r > 255 ? 255 : r) & ~7;
+}
 
 void asss_destroy_batched(asss_batch* B) {
     if (!B) return;

@@ -235,11 +235,11 @@ struct BatchLaunch {
 };
 constexpr int BATCH_NPROF = 6;  // mrs, SMW correction, operator, Gram-Schmidt, x update + residual, rest
 
-// launches the persistent batched solver on stream s with nthreads per CTA and nblk CTAs
-// (wide: the 128-register build, 512 threads per SM)
-asss_status batch_launch(const BatchLaunch& L, int nthreads, int wide, int nblk, cudaStream_t s);
-// resident CTAs per SM of the batched solver for a CTA size and register budget
-asss_status batch_occupancy(int kp, int qbf16, int nthreads, int wide, int* occ);
+// launches the persistent batched solver on stream s with nthreads per CTA and nblk CTAs,
+// built for minb resident CTAs per SM (which sets the registers a thread may use)
+asss_status batch_launch(const BatchLaunch& L, int nthreads, int minb, int nblk, cudaStream_t s);
+// resident CTAs per SM of the batched solver for a CTA shape
+asss_status batch_occupancy(int kp, int qbf16, int nthreads, int minb, int* occ);
 constexpr int BATCH_RMAX = 24;
 
 // fused Arnoldi step of FGMRES (arnoldi.cu): CGS2 + norm + Givens + next basis vector

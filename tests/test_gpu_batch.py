@@ -42,7 +42,8 @@ def test_batched_matches_exact_solutions(pkg, batch):
     assert bs.cta_threads == 0
     nrhs = Bs[0].shape[1]
     x, st = bs.solve(bs.pack(Bs), nrhs=nrhs)
-    assert (bs.cta_threads, bs.cta_registers) in {(128, 64), (256, 64), (512, 64), (1024, 64), (512, 128)}
+    assert (bs.cta_threads, bs.cta_registers) in {(256, 64), (512, 64), (256, 80), (384, 80), (256, 128),
+                                                  (512, 128)}
     assert st["status"] == 0
     assert st["inner_solves"] == len(As) * nrhs
     assert st["relres"] <= 1e-8
@@ -197,19 +198,20 @@ def test_batched_general_patterns_use_sell(pkg):
     bs.close()
 
 
-@pytest.mark.parametrize("shape", ["128", "256", "512", "1024", "512w"])
-def test_batched_every_cta_shape_meets_the_tolerance(pkg, batch, shape, monkeypatch):
-    """Each CTA shape the tuner may pick (64 registers a thread at 128..1024 threads,
-    or 128 registers at 512 threads with a row's loads unrolled) solves every item to
-    the outer tolerance and agrees with the exact solution."""
+@pytest.mark.parametrize("shape,regs", [("256x4", 64), ("512x2", 64), ("256x3", 80), ("384x2", 80), ("256x2", 128),
+                                        ("512x1", 128)])
+def test_batched_every_cta_shape_meets_the_tolerance(pkg, batch, shape, regs, monkeypatch):
+    """Each CTA shape the tuner may pick (threads per CTA x resident CTAs per SM, which
+    sets the registers a thread may use; at 128 registers a row's loads are unrolled)
+    solves every item to the outer tolerance and agrees with the exact solution."""
     monkeypatch.setenv("ASSS_BATCH_CTA", shape)
     As = [A for A, _ in batch]
     Bs = [B for _, B in batch]
     bs = pkg.BatchSolver(As, inner_tol=1e-6, restart=24)
     nrhs = Bs[0].shape[1]
     x, st = bs.solve(bs.pack(Bs), nrhs=nrhs)
-    assert bs.cta_threads == int(shape.rstrip("w"))
-    assert bs.cta_registers == (128 if shape.endswith("w") else 64)
+    assert bs.cta_threads == int(shape.split("x")[0])
+    assert bs.cta_registers == regs
     assert st["status"] == 0 and st["relres"] <= 1e-8
     X = bs.unpack(x, nrhs)
     _check_columns(batch, X, Bs)
