@@ -2,12 +2,16 @@
 // Host code here only orders kernel launches and reads back the scalars that
 // decide control flow (convergence, breakdown); all arithmetic runs on the GPU.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include <cuda_bf16.h>
@@ -2504,9 +2508,12 @@ struct asss_batch {
     const void* g_b = nullptr;
     const void* g_x = nullptr;
     int g_nrhs = -1, g_nt = -1, g_minb = -1;
+    std::vector<cudaStream_t> setup_streams;   // streams of the concurrent set-ups (the handles keep them)
     ~asss_batch() {
         if (gexec) cudaGraphExecDestroy(gexec);
         for (asss_handle* h : hs) delete h;
+        for (cudaStream_t w : setup_streams)
+            if (w) cudaStreamDestroy(w);
         if (ev_in) cudaEventDestroy(ev_in);
         if (ev_t0) cudaEventDestroy(ev_t0);
         if (ev_t1) cudaEventDestroy(ev_t1);
@@ -2758,18 +2765,72 @@ asss_status asss_setup_batched(int nmat, const asss_csr* const* A, const asss_op
     if (s == ASSS_OK && (cudaEventCreate(&B->ev_in) != cudaSuccess || cudaEventCreate(&B->ev_t0) != cudaSuccess ||
                          cudaEventCreate(&B->ev_t1) != cudaSuccess))
         s = ASSS_ERR_CUDA;
-    asss_options o = B->opt;
-    o.stream = B->own;
     std::vector<BatchMat> views(nmat);
     long long rows = 0;
+    // The set-ups of small systems are bound by launch latency and host round trips, so
+    // they run concurrently: a few host threads, each with a stream of its own, take the
+    // matrices one at a time (every handle keeps the stream it was set up on).
+    if (s == ASSS_OK) {
+        const int nw = nmat < 8 ? nmat : 8;
+        B->hs.assign(nmat, nullptr);
+        B->setup_streams.assign(nw, nullptr);
+        for (int w = 0; w < nw && s == ASSS_OK; ++w)
+            if (cudaStreamCreateWithFlags(&B->setup_streams[w], cudaStreamNonBlocking) != cudaSuccess) {
+                set_error("cudaStreamCreate failed");
+                s = ASSS_ERR_CUDA;
+            }
+        std::atomic<int> next{0};
+        std::atomic<int> failed{0};
+        std::mutex mu;
+        asss_status first = ASSS_OK;
+        std::string first_text;
+        auto worker = [&](int w) {
+            if (cudaSetDevice(B->ctx.device) != cudaSuccess) {
+                std::lock_guard<std::mutex> lk(mu);
+                if (first == ASSS_OK) {
+                    first = ASSS_ERR_CUDA;
+                    first_text = "cudaSetDevice failed in a set-up thread";
+                }
+                failed = 1;
+                return;
+            }
+            asss_options ow = B->opt;
+            ow.stream = B->setup_streams[w];
+            for (;;) {
+                const int m = next.fetch_add(1);
+                if (m >= nmat || failed.load()) break;
+                asss_handle* h = nullptr;
+                asss_stats hst;
+                asss_status r = asss_setup(A[m], &ow, &h, &hst);
+                if (r == ASSS_OK) {
+                    B->hs[m] = h;
+                    r = batch_view(h, &views[m]);
+                }
+                if (r != ASSS_OK) {
+                    std::lock_guard<std::mutex> lk(mu);
+                    if (first == ASSS_OK) {
+                        first = r;
+                        first_text = get_error();
+                    }
+                    failed = 1;
+                    break;
+                }
+            }
+            cudaStreamSynchronize(B->setup_streams[w]);
+            release_thread_scratch();
+        };
+        if (s == ASSS_OK) {
+            std::vector<std::thread> th;
+            for (int w = 0; w < nw; ++w) th.emplace_back(worker, w);
+            for (std::thread& t : th) t.join();
+            if (first != ASSS_OK) {
+                set_error("%s", first_text.c_str());
+                s = first;
+            }
+        }
+    }
     for (int m = 0; m < nmat && s == ASSS_OK; ++m) {
-        asss_handle* h = nullptr;
-        asss_stats hs;
-        s = asss_setup(A[m], &o, &h, &hs);
-        if (s != ASSS_OK) break;
-        B->hs.push_back(h);
-        s = batch_view(h, &views[m]);
-        if (s != ASSS_OK) break;
+        asss_handle* h = B->hs[m];
         int kpm = h->Q16.p ? h->kp16 : h->kp;
         if (m == 0) {
             B->kp = kpm;

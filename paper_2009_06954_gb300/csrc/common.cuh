@@ -77,8 +77,11 @@ struct DBuf {
 };
 
 // Reduction scratch that lives as long as the process, one buffer per device and
-// thread.  It is never freed, so no CUDA call runs during process teardown.
+// thread.  It is never freed by the library's own threads, so no CUDA call runs during
+// process teardown; worker threads the library starts free theirs before they end
+// (release_thread_scratch, after their streams are idle).
 asss_status process_scratch(int slot, int64_t count, double** out);
+void release_thread_scratch();
 
 // CSR with 32-bit row pointers (nnz < 2^31 is checked on entry).
 // Optional diagonal copy of a CSR matrix whose entries sit on a few diagonals

@@ -26,10 +26,24 @@ static unsigned long long g_launches = 0;
 void count_launch() { __atomic_add_fetch(&g_launches, 1ull, __ATOMIC_RELAXED); }
 unsigned long long launches() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
+constexpr int SCRATCH_MAXDEV = 64, SCRATCH_SLOTS = 4;
+static thread_local double* g_scratch[SCRATCH_MAXDEV][SCRATCH_SLOTS] = {};
+static thread_local int64_t g_scratch_cap[SCRATCH_MAXDEV][SCRATCH_SLOTS] = {};
+
+void release_thread_scratch() {
+    for (int d = 0; d < SCRATCH_MAXDEV; ++d)
+        for (int s = 0; s < SCRATCH_SLOTS; ++s)
+            if (g_scratch[d][s]) {
+                cudaFree(g_scratch[d][s]);
+                g_scratch[d][s] = nullptr;
+                g_scratch_cap[d][s] = 0;
+            }
+}
+
 asss_status process_scratch(int slot, int64_t count, double** out) {
-    constexpr int MAXDEV = 64, SLOTS = 4;
-    static thread_local double* buf[MAXDEV][SLOTS] = {};
-    static thread_local int64_t cap[MAXDEV][SLOTS] = {};
+    constexpr int MAXDEV = SCRATCH_MAXDEV, SLOTS = SCRATCH_SLOTS;
+    auto& buf = g_scratch;
+    auto& cap = g_scratch_cap;
     int dev = 0;
     ASSS_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= MAXDEV || slot < 0 || slot >= SLOTS) {
