@@ -217,3 +217,200 @@ class FactoredSkew:
 
     def dense(self):
         return self @ np.eye(self.n)
+
+
+# ----------------------------------------------------------------------------
+# 2x2 pivot blocks (reading R20): a static Bunch-Kaufman choice, the block pattern,
+# the colouring of the quotient graph and the block factor
+# ----------------------------------------------------------------------------
+BK_ALPHA = (1.0 + np.sqrt(17.0)) / 8.0   # Bunch-Kaufman's growth-optimal threshold
+
+
+def bk_pairs(MP, alpha: float = BK_ALPHA):
+    """Static 2x2 pivot choice on the symmetric matrix MP (values on its pattern).
+    For every i: gamma_i = max_{j != i} |m_ij| over the stored entries, r_i its column
+    (the smallest j on ties); i asks for a 2x2 pivot when |m_ii| < alpha gamma_i (the
+    first Bunch-Kaufman test).  i and r_i form a pair when each asks and each is the
+    other's r.  Returns partner (int64, -1 for a 1x1 pivot)."""
+    M = sp.csr_matrix(MP)
+    n = M.shape[0]
+    partner = np.full(n, -1, dtype=np.int64)
+    r = np.full(n, -1, dtype=np.int64)
+    need = np.zeros(n, dtype=bool)
+    diag = M.diagonal()
+    for i in range(n):
+        cols = M.indices[M.indptr[i]:M.indptr[i + 1]]
+        vals = np.abs(M.data[M.indptr[i]:M.indptr[i + 1]])
+        off = cols != i
+        if not np.any(off):
+            continue
+        c, v = cols[off], vals[off]
+        g = v.max()
+        r[i] = int(c[v == g].min())
+        need[i] = abs(diag[i]) < alpha * g
+    for i in range(n):
+        j = r[i]
+        if need[i] and j >= 0 and need[j] and r[j] == i:
+            partner[i] = j
+    return partner
+
+
+def block_pattern(P, partner):
+    """The pattern the block factor keeps: P plus what makes every block between two
+    pivots full, i.e. the pattern of (I + E) P (I + E) with E linking the members of
+    each pair.  Unit values, sorted indices."""
+    n = P.shape[0]
+    p = np.asarray(partner)
+    rows = np.flatnonzero(p >= 0)
+    E = sp.csr_matrix((np.ones(rows.size), (rows, p[rows])), shape=(n, n))
+    B = (sp.identity(n, format="csr") + E).tocsr()
+    P1 = sp.csr_matrix((np.ones(P.nnz), P.indices, P.indptr), shape=P.shape)
+    Q = (B @ P1 @ B).tocsr()
+    Q.data[:] = 1.0
+    Q.sort_indices()
+    return Q
+
+
+def jp_colouring_blocks(P, prio, partner):
+    """Jones-Plassmann colouring of the quotient graph in which each pair is one vertex
+    (its leader: the smaller index, whose priority it takes); both members get the
+    leader's colour.  Returns (colour (int64, n), rounds)."""
+    n = P.shape[0]
+    p = np.asarray(partner)
+    lead = np.where(p >= 0, np.minimum(np.arange(n), p), np.arange(n))
+    leaders = np.flatnonzero(lead == np.arange(n))
+    slot = np.full(n, -1, dtype=np.int64)
+    slot[leaders] = np.arange(leaders.size)
+    R = sp.csr_matrix((np.ones(n), (np.arange(n), slot[lead])), shape=(n, leaders.size))
+    P1 = sp.csr_matrix((np.ones(P.nnz), P.indices, P.indptr), shape=P.shape)
+    Gq = (R.T @ P1 @ R).tocsr()
+    Gq.sort_indices()
+    cq, rounds = jp_colouring(Gq, np.asarray(prio)[leaders])
+    return cq[slot[lead]], rounds
+
+
+def ildl0_blocks(MP, colour, partner, zero_tol: float = 1e-14):
+    """No-fill incomplete block L D L^T of the symmetric matrix MP (values on its block
+    pattern, see block_pattern) with 1x1 and 2x2 pivots, in the order of the pivot
+    blocks by (colour, leader index).  For each block I in that order and each lower
+    block K adjacent to it, in order:
+        L_IK = (M_IK - sum_{K' < K adjacent to I and K} L_IK' D_K' L_KK'^T) D_K^-1,
+    then D_I = M_II - sum_{K < I} L_IK D_K L_IK^T.  A zero (or tiny) 1x1 pivot, or a 2x2
+    pivot with a zero (or tiny) determinant, is an error.
+    Returns (L, D): L strictly block-lower (n x n CSR, original indexing), D the block
+    diagonal (n x n CSR: the pivots, and m_{i,partner(i)} updated for pairs)."""
+    M = sp.csr_matrix(MP)
+    n = M.shape[0]
+    p = np.asarray(partner)
+    lead = np.where(p >= 0, np.minimum(np.arange(n), p), np.arange(n))
+    leaders = np.flatnonzero(lead == np.arange(n))
+    order = leaders[np.lexsort((leaders, np.asarray(colour)[leaders]))]
+    rank = np.full(n, -1, dtype=np.int64)
+    rank[order] = np.arange(order.size)
+    members = {int(i): ([int(i)] if p[i] < 0 else sorted([int(i), int(p[i])])) for i in leaders}
+    Md = M.toarray() if n <= 2000 else None
+
+    def mblock(I, K):
+        if Md is not None:
+            return Md[np.ix_(members[I], members[K])]
+        return M[members[I]][:, members[K]].toarray()
+
+    dmax = np.abs(M.diagonal()).max() if n else 0.0
+    Lb = {}      # block I -> {K: L_IK}
+    Db = {}
+    for I in order:
+        I = int(I)
+        rows = members[I]
+        nb = set()
+        for r_ in rows:
+            for c in M.indices[M.indptr[r_]:M.indptr[r_ + 1]]:
+                K = int(lead[c])
+                if rank[K] < rank[I]:
+                    nb.add(K)
+        LI = {}
+        for K in sorted(nb, key=lambda k: rank[k]):
+            S = mblock(I, K).copy()
+            for K2, LK2 in Lb[K].items():
+                if K2 in LI:
+                    S -= LI[K2] @ Db[K2] @ LK2.T
+            LI[K] = S @ np.linalg.inv(Db[K])
+        DI = mblock(I, I).copy()
+        for K, LIK in LI.items():
+            DI -= LIK @ Db[K] @ LIK.T
+        if DI.shape[0] == 1:
+            if DI[0, 0] == 0.0 or abs(DI[0, 0]) < zero_tol * dmax:
+                raise ZeroDivisionError(f"zero pivot in the incomplete block LDL^T at {rows}")
+        else:
+            det = DI[0, 0] * DI[1, 1] - DI[0, 1] * DI[1, 0]
+            if det == 0.0 or abs(det) < zero_tol * dmax * dmax:
+                raise ZeroDivisionError(f"singular 2x2 pivot in the incomplete block LDL^T at {rows}")
+            DI = 0.5 * (DI + DI.T)
+        Db[I] = DI
+        Lb[I] = LI
+    r_, c_, v_ = [], [], []
+    for I, LI in Lb.items():
+        for K, LIK in LI.items():
+            for a, ra in enumerate(members[I]):
+                for b, cb in enumerate(members[K]):
+                    r_.append(ra)
+                    c_.append(cb)
+                    v_.append(LIK[a, b])
+    L = sp.csr_matrix((np.array(v_, dtype=np.float64), (np.array(r_, dtype=np.int64), np.array(c_, dtype=np.int64))),
+                      shape=(n, n))
+    L.sort_indices()
+    dr, dc, dv = [], [], []
+    for I, DI in Db.items():
+        for a, ra in enumerate(members[I]):
+            for b, cb in enumerate(members[I]):
+                dr.append(ra)
+                dc.append(cb)
+                dv.append(DI[a, b])
+    D = sp.csr_matrix((np.array(dv), (np.array(dr, dtype=np.int64), np.array(dc, dtype=np.int64))), shape=(n, n))
+    D.sort_indices()
+    return L, D
+
+
+def block_pivot_split(D, partner):
+    """For the block diagonal D of 1x1 and 2x2 pivots: W = |D|^(-1/2) (block by block:
+    V |Lambda|^(-1/2) V^T of each symmetric 2x2 block) and M~_r = sign(D) - I as
+    U_r Sigma_r U_r^T (Fig. 1: a 1x1 negative pivot gives e_i with -2; a 2x2 block with
+    eigenpairs (lambda, v) gives v with -2 for each negative lambda).
+    Returns (W (n x n CSR), U_r (n x r dense), sigma_r (r,))."""
+    n = D.shape[0]
+    p = np.asarray(partner)
+    Dd = sp.csr_matrix(D)
+    wr, wc, wv = [], [], []
+    cols, sig = [], []
+    for i in range(n):
+        j = int(p[i])
+        if j >= 0 and j < i:
+            continue
+        if j < 0:
+            d = Dd[i, i]
+            wr.append(i)
+            wc.append(i)
+            wv.append(1.0 / np.sqrt(abs(d)))
+            if d < 0:
+                u = np.zeros(n)
+                u[i] = 1.0
+                cols.append(u)
+                sig.append(-2.0)
+            continue
+        idx = [i, j]
+        B = np.array([[Dd[i, i], Dd[i, j]], [Dd[j, i], Dd[j, j]]])
+        lam, V = np.linalg.eigh(0.5 * (B + B.T))
+        Wb = V @ np.diag(1.0 / np.sqrt(np.abs(lam))) @ V.T
+        for a in range(2):
+            for b in range(2):
+                wr.append(idx[a])
+                wc.append(idx[b])
+                wv.append(Wb[a, b])
+        for t in range(2):
+            if lam[t] < 0:
+                u = np.zeros(n)
+                u[idx] = V[:, t]
+                cols.append(u)
+                sig.append(-2.0)
+    W = sp.csr_matrix((np.array(wv), (np.array(wr, dtype=np.int64), np.array(wc, dtype=np.int64))), shape=(n, n))
+    U = np.array(cols).T if cols else np.zeros((n, 0))
+    return W, U, np.array(sig)

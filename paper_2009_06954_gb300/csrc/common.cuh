@@ -82,6 +82,8 @@ struct DBuf {
 // (release_thread_scratch, after their streams are idle).
 asss_status process_scratch(int slot, int64_t count, double** out);
 void release_thread_scratch();
+// raises a kernel's dynamic shared-memory limit to at least bytes (never lowers it)
+asss_status raise_dynamic_smem(const void* func, int bytes);
 
 // CSR with 32-bit row pointers (nnz < 2^31 is checked on entry).
 // Optional diagonal copy of a CSR matrix whose entries sit on a few diagonals

@@ -3,6 +3,9 @@
 #include <cstdarg>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
+#include <tuple>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -21,6 +24,28 @@ void set_error(const char* fmt, ...) {
     va_end(ap);
 }
 const char* get_error() { return g_err; }
+
+// The dynamic shared-memory limit is an attribute of the kernel for the whole process, and
+// set-ups may run on several host threads at once: the limit only ever grows (under a
+// lock), so a launch sized for it never finds it lowered by another thread.
+asss_status raise_dynamic_smem(const void* func, int bytes) {
+    static std::mutex mu;
+    static std::vector<std::tuple<const void*, int, int>> set;   // (kernel, device, limit)
+    std::lock_guard<std::mutex> lk(mu);
+    int dev = 0;
+    ASSS_CUDA(cudaGetDevice(&dev));
+    for (auto& f : set) {
+        if (std::get<0>(f) == func && std::get<1>(f) == dev) {
+            if (std::get<2>(f) >= bytes) return ASSS_OK;
+            ASSS_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+            std::get<2>(f) = bytes;
+            return ASSS_OK;
+        }
+    }
+    ASSS_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    set.emplace_back(func, dev, bytes);
+    return ASSS_OK;
+}
 
 static unsigned long long g_launches = 0;
 void count_launch() { __atomic_add_fetch(&g_launches, 1ull, __ATOMIC_RELAXED); }
@@ -779,7 +804,7 @@ asss_status build_pattern(const DCsr& Abar, const DCsr& AbarT, const DCsr& S, co
         ASSS_TRY(bitmaps.alloc((int64_t)hblk * words));
     }
     size_t smem = (size_t)cap * PAT_WARPS * sizeof(int);
-    ASSS_CUDA(cudaFuncSetAttribute(k_pattern_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ASSS_TRY(raise_dynamic_smem((const void*)k_pattern_rows, (int)smem));
     int grid = cdiv(n, PAT_WARPS);
     if (grid > 65535 * 8) grid = 65535 * 8;
     k_pattern_rows<<<grid, PAT_WARPS * 32, smem, s>>>(n, Abar.rp.p, Abar.ci.p, S.rp.p, S.ci.p, ST.rp.p,
@@ -981,7 +1006,7 @@ asss_status build_sell(const DCsr& A, bool skip_diag, DSell<T>& out, cudaStream_
         ASSS_TRY(out.rowmap.alloc(nslots));
         ASSS_TRY(out.rowpos.alloc(n));
         const size_t smem = sizeof(long long) * (size_t)sigma;
-        ASSS_CUDA(cudaFuncSetAttribute(k_sell_sort_window, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        ASSS_TRY(raise_dynamic_smem((const void*)k_sell_sort_window, (int)smem));
         k_sell_sort_window<<<cdiv(nslots, sigma), SELL_SORT_THREADS, smem, s>>>(n, nslots, sigma, len.p,
                                                                                 out.rowmap.p, out.rowpos.p);
         ASSS_CHECK_LAUNCH();
