@@ -465,12 +465,15 @@ class AsssOracle:
     factor="ildl0" replaces the diagonal factor by the no-fill incomplete L D L^T of M^
     (§3 after Eq. absfac, §4.1 ~ildl(0); ildl.py): L~^-1 and L~^-T are applied by
     triangular solves (F and G of FactoredSkew), A_cal = F Abar S G, J~ = F J^ G, the
-    right-hand side F P D_r b and x = D_c S G y; M~_r = sign(D) - I."""
+    right-hand side F P D_r b and x = D_c S G y; M~_r = sign(D) - I.  factor="ildl0_bk"
+    also takes 2x2 pivot blocks where the first Bunch-Kaufman test asks for them (reading
+    R20): |D|^(-1/2) and M~_r = sign(D) - I = U_r Sigma_r U_r^T block by block (Fig. 1).
+    S (optional) is used as given instead of the least-squares fit of §2."""
 
     def __init__(self, A, S_pattern=None, gamma=1.0, k=20, reorth=True, seed=0x5eed,
                  inner_tol=1e-10, inner_maxit=1000, setup_tol=None, r_max=256,
                  row_perm=None, dr=None, dc=None, q1=None, lls_method="auto",
-                 zero_tol=1e-14, factor="diag"):
+                 zero_tol=1e-14, factor="diag", S=None):
         A = sp.csr_matrix(A, dtype=np.float64)
         A.sort_indices()
         self.A = A
@@ -480,7 +483,9 @@ class AsssOracle:
         if S_pattern is None:           # "having the sparsity of Abar" (§2)
             Ab = self.Abar
             S_pattern = sp.csr_matrix((np.ones(Ab.nnz), Ab.indices, Ab.indptr), shape=Ab.shape)
-        self.S = skew_symmetrizer(self.Abar, S_pattern, gamma, lls_method)
+        # S given (values already fitted, or chosen by a test) or fitted here (§2)
+        self.S = sp.csr_matrix(S, dtype=np.float64) if S is not None else \
+            skew_symmetrizer(self.Abar, S_pattern, gamma, lls_method)
         self.factor = factor
         self.fac = None
         if factor == "ildl0":
@@ -495,6 +500,25 @@ class AsssOracle:
             self.w = np.ones(n)                 # L~ enters through F and G instead
             self.fac = ildl.FactoredSkew(self.L, self.d, self.order,
                                          inner_skew_operator(self.Abar, self.S, self.w))
+        elif factor == "ildl0_bk":
+            # 2x2 pivot blocks where the first Bunch-Kaufman test asks for them (R20)
+            from . import ildl
+            C = (sp.csr_matrix(self.Abar) @ sp.csr_matrix(self.S)).tocsr()
+            Mh = 0.5 * (C + C.T)
+            P = ildl.structural_pattern(self.Abar, self.S)
+            self.partner = ildl.bk_pairs(ildl.values_on_pattern(Mh, P))
+            Pb = ildl.block_pattern(P, self.partner)
+            MP = ildl.values_on_pattern(Mh, Pb)
+            self.colour, self.jp_rounds = ildl.jp_colouring_blocks(Pb, ildl.colouring_priorities(seed, n),
+                                                                   self.partner)
+            self.order = ildl.block_order(self.colour, self.partner)
+            self.L, self.D = ildl.ildl0_blocks(MP, self.colour, self.partner, zero_tol)
+            self.d = self.D.diagonal()
+            W, self.Ur, self.sig_r = ildl.block_pivot_split(self.D, self.partner)
+            self.w = np.ones(n)
+            self.fac = ildl.FactoredSkew(self.L, None, self.order,
+                                         inner_skew_operator(self.Abar, self.S, self.w), W=W)
+            neg = np.arange(self.Ur.shape[1])       # r columns (counted; U_r set below)
         elif factor == "diag":
             self.d, self.w, neg = shift_and_lowrank(self.Abar, self.S, zero_tol)
         else:
@@ -511,7 +535,13 @@ class AsssOracle:
         self.inner_tol = inner_tol
         self.inner_maxit = inner_maxit
         self.setup_tol = inner_tol if setup_tol is None else setup_tol
-        self.set_lowrank(self.neg)
+        if factor == "ildl0_bk":
+            if self.prec2:
+                self.set_lowrank_columns(np.zeros((n, 0)), np.zeros(0))
+            else:
+                self.set_lowrank_columns(self.Ur, self.sig_r)
+        else:
+            self.set_lowrank(self.neg)
         self.inner_its = []
         # outer operator pieces: A_cal = (W Abar)(S W)
         self.Aw = (sp.diags(self.w) @ self.Abar).tocsr()
@@ -521,15 +551,28 @@ class AsssOracle:
         """U_bar = [Q_k, U_r], Sig_bar = blkdiag(S_k, -2 I_r)  (Eq. preconditioner);
         U_r = [e_i : i in neg] (Fig. 1 with 1x1 blocks).  Drops cached SMW data."""
         n = self.n
-        self.neg = np.asarray(neg, dtype=np.int64)
-        self.r = self.neg.size
+        neg = np.asarray(neg, dtype=np.int64)
+        Ur = np.zeros((n, neg.size))
+        Ur[neg, np.arange(neg.size)] = 1.0
+        self.set_lowrank_columns(Ur, -2.0 * np.ones(neg.size))
+        self.neg = neg
+
+    def set_lowrank_columns(self, Ur, sig):
+        """U_bar = [Q_k, U_r], Sig_bar = blkdiag(S_k, diag(sig)) for any U_r (Fig. 1: the
+        eigenvectors of 2x2 pivot blocks, unit vectors of 1x1 ones).  Drops cached SMW
+        data."""
+        n = self.n
+        Ur = np.asarray(Ur, dtype=np.float64).reshape(n, -1)
+        self.Ur_cols, self.sig_cols = Ur, np.asarray(sig, dtype=np.float64)
+        self.r = Ur.shape[1]
+        self.neg = np.arange(self.r)
         m = self.k + self.r
         Ub = np.zeros((n, m))
         Ub[:, :self.k] = self.Q
-        Ub[self.neg, self.k + np.arange(self.r)] = 1.0
+        Ub[:, self.k:] = Ur
         Sig = np.zeros((m, m))
         Sig[:self.k, :self.k] = self.Sk
-        Sig[self.k:, self.k:] = -2.0 * np.eye(self.r)
+        Sig[self.k:, self.k:] = np.diag(self.sig_cols)
         self.Ub, self.Sig = Ub, Sig
         self._X = {}
         self._K = {}
@@ -537,7 +580,7 @@ class AsssOracle:
     def prec_dense(self):
         """P = M~_r + I + J~ as a dense matrix (tiny problems, tests only)."""
         P = (self.fac.dense() if self.fac is not None else self.Jt.toarray()) + np.eye(self.n)
-        P[self.neg, self.neg] -= 2.0
+        P += self.Ur_cols @ np.diag(self.sig_cols) @ self.Ur_cols.T
         return P
 
     # -- deflated inner operator  J_bar = J~ - Q S_k Q^T  (§3.2) ------------------

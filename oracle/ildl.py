@@ -7,7 +7,12 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
 large systems, replaces it by an incomplete factorization; §4.1's ~ildl(0) keeps no
 more entries than M^ has.  Readings taken here (the paper names sym-ildl and stops):
   * pattern: exactly the structural pattern of A^ + A^T (no fill at all);
-  * pivots: 1x1 only (no 2x2 Bunch-Kaufman blocks), a tiny |d_i| is an error;
+  * pivots: 1x1 (ildl0), or 1x1 and 2x2 blocks (ildl0_blocks, reading R20): a row whose
+    diagonal fails the first Bunch-Kaufman test |m_ii| >= alpha max_j |m_ij| pairs with
+    the column of that maximum when that row fails it too and points back (a static,
+    parallel choice made before the ordering); the pattern is then closed so that every
+    block between two pivots is full, and the pairs are coloured as single vertices;
+    a tiny |d_i| or 2x2 determinant is an error;
   * order: the factorization runs in a multicolour order - vertices sorted by
     (colour, index) - where the colours come from Jones-Plassmann rounds with
     first-fit colours and splitmix64 priorities (a published, deterministic rule), so
@@ -175,11 +180,14 @@ class FactoredSkew:
     lower triangular in the factorization order: the triangular solves run on the
     permuted matrices."""
 
-    def __init__(self, L, d, order, Jh):
-        n = d.size
+    def __init__(self, L, d, order, Jh, W=None):
+        """W (optional): the block-diagonal |D|^(-1/2) of a factor with 2x2 pivots, used
+        in place of the diagonal weights |d|^(-1/2)."""
+        n = L.shape[0]
         self.n = n
         self.order = np.asarray(order)
-        self.wd = 1.0 / np.sqrt(np.abs(d))
+        self.W = None if W is None else sp.csr_matrix(W)
+        self.wd = None if W is not None else 1.0 / np.sqrt(np.abs(d))
         Lc = sp.csr_matrix(L)[self.order][:, self.order].tocsr()
         self.L1c = (Lc + sp.identity(n, format="csr")).tocsr()
         self.L1cT = self.L1c.T.tocsr()
@@ -199,17 +207,20 @@ class FactoredSkew:
         out[o] = spla.spsolve_triangular(self.L1cT, v[o], lower=False, unit_diagonal=True)
         return out
 
+    def _weight(self, v):
+        return self.W @ v if self.W is not None else self.wd * v
+
     def F(self, v):
         v = np.asarray(v, dtype=np.float64)
         if v.ndim == 2:
             return np.column_stack([self.F(v[:, c]) for c in range(v.shape[1])]) if v.shape[1] else v.copy()
-        return self.wd * self._lower_solve(v)
+        return self._weight(self._lower_solve(v))
 
     def G(self, v):
         v = np.asarray(v, dtype=np.float64)
         if v.ndim == 2:
             return np.column_stack([self.G(v[:, c]) for c in range(v.shape[1])]) if v.shape[1] else v.copy()
-        return self._upper_solve(self.wd * v)
+        return self._upper_solve(self._weight(v))
 
     def __matmul__(self, v):
         """J~ v = F (J^ (G v))."""
@@ -414,3 +425,19 @@ def block_pivot_split(D, partner):
     W = sp.csr_matrix((np.array(wv), (np.array(wr, dtype=np.int64), np.array(wc, dtype=np.int64))), shape=(n, n))
     U = np.array(cols).T if cols else np.zeros((n, 0))
     return W, U, np.array(sig)
+
+
+def block_order(colour, partner):
+    """Vertex order of the block factor: pivot blocks by (colour, leader index), the two
+    members of a pair next to each other (smaller index first)."""
+    n = len(colour)
+    p = np.asarray(partner)
+    lead = np.where(p >= 0, np.minimum(np.arange(n), p), np.arange(n))
+    leaders = np.flatnonzero(lead == np.arange(n))
+    ordl = leaders[np.lexsort((leaders, np.asarray(colour)[leaders]))]
+    out = []
+    for i in ordl:
+        out.append(int(i))
+        if p[i] >= 0:
+            out.append(int(p[i]))
+    return np.array(out, dtype=np.int64)

@@ -272,6 +272,42 @@ def indefinite_zero_diagonal(n: int, seed: int = 0):
     return K
 
 
+def saddle_pairs(n: int, seed: int = 0, singles: int = 0):
+    """Nonsymmetric sparse matrix whose symmetric part has zero diagonal entries coupled in
+    pairs: rows pi(2t), pi(2t+1) (pi a seeded permutation) have a zero diagonal and a
+    symmetric coupling of modulus in [1, 2) between them, the last `singles` rows a
+    diagonal in [2, 3); about 3 random symmetric couplings N(0, 0.1^2) per row connect
+    everything, and a skew part N(0, 0.3^2) on a random pattern is added.  No 1x1 pivot
+    order factors the symmetric part of the pairs (zero diagonal); 2x2 pivots do."""
+    rng = np.random.default_rng(seed)
+    pi = rng.permutation(n)
+    npair = (n - singles) // 2
+    rows, cols, vals = [], [], []
+    for t in range(npair):
+        i, j = int(pi[2 * t]), int(pi[2 * t + 1])
+        v = (1.0 + rng.random()) * rng.choice([-1.0, 1.0])
+        rows += [i, j]
+        cols += [j, i]
+        vals += [v, v]
+    for t in range(2 * npair, n):
+        i = int(pi[t])
+        rows.append(i)
+        cols.append(i)
+        vals.append(2.0 + rng.random())
+    M = sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+    R = sp.random(n, n, density=1.5 / n, random_state=rng, data_rvs=lambda k: 0.1 * rng.standard_normal(k))
+    R = sp.csr_matrix(R)
+    R.setdiag(0.0)
+    K = sp.random(n, n, density=2.0 / n, random_state=rng, data_rvs=lambda k: 0.3 * rng.standard_normal(k))
+    K = sp.csr_matrix(K)
+    K.setdiag(0.0)
+    A = (M + R + R.T + K - K.T).tocsr()
+    A.sum_duplicates()
+    A.eliminate_zeros()
+    A.sort_indices()
+    return A
+
+
 def pattern_symmetrized(A):
     """Pattern of A + A^T (unit values)."""
     P = (abs(sp.csr_matrix(A)) + abs(sp.csr_matrix(A)).T).tocsr()
