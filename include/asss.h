@@ -127,6 +127,14 @@ typedef struct {
                                  ~ildl(0); 1x1 pivots, factored in a multicolour order from
                                  Jones-Plassmann rounds seeded by `seed`), J~ = L~^-1 J^ L~^-T
                                  applied by triangular solves (one parallel step per colour).
+                                 ASSS_FACTOR_ILDL0_BK: the same with 2x2 pivot blocks where the
+                                 first Bunch-Kaufman test |m_ii| >= alpha max_j |m_ij| (alpha =
+                                 (1 + 17^1/2)/8) fails for a row and for the column of that
+                                 maximum, which points back (a static pairing made before the
+                                 ordering; the pattern is closed so that every block between two
+                                 pivots is full, pairs are coloured as one vertex); |D|^-1/2 and
+                                 M~_r = sign(D) - I are taken block by block (Fig. 1: a 2x2 block
+                                 with one negative eigenvalue adds its eigenvector to U_r).
                                  Not with q_bf16 (ASSS_ERR_UNSUPPORTED) nor in asss_setup_batched;
                                  rhs_block is ignored                                           */
 } asss_options;
@@ -135,7 +143,7 @@ enum { ASSS_SCALING_MAXES = 0, ASSS_SCALING_MATCHING = 1 };
 
 enum { ASSS_FORMAT_AUTO = 0, ASSS_FORMAT_SELL = 1, ASSS_FORMAT_DIAG = 2 };
 
-enum { ASSS_FACTOR_DIAG = 0, ASSS_FACTOR_ILDL0 = 1 };
+enum { ASSS_FACTOR_DIAG = 0, ASSS_FACTOR_ILDL0 = 1, ASSS_FACTOR_ILDL0_BK = 2 };
 
 typedef struct {
     int    status;            /* asss_status of the call                                        */
@@ -145,7 +153,8 @@ typedef struct {
     int    inner_solves;      /* number of inner solves (preconditioner applications)           */
     double inner_its_avg;
     double relres;            /* final ||b - A x|| / ||b|| in FP64 (original system)            */
-    int    r;                 /* rank of M~_r (number of negative d_i kept)                     */
+    int    r;                 /* rank of M~_r (negative d_i kept; with 2x2 pivots, the negative
+                                 eigenvalues of the pivot blocks)                               */
     int    k_eff;             /* Lanczos vectors kept after breakdown checks                    */
     int    prec2;             /* 1 if Eq. (preconditioner2) was used because r > r_max          */
     int    lls_its;           /* iterations of the LLS solve                                    */
@@ -168,6 +177,7 @@ typedef struct {
     int    orth_calls;
     long long orth_bytes;     /* their algorithmic bytes (basis read twice, w r/w, v_{j+1} out) */
     long long orth_flops;     /* and FP64 flops (4(j+1) FMAs a row)                             */
+    int    factor_pairs;      /* set-up, ASSS_FACTOR_ILDL0_BK: 2x2 pivot blocks formed          */
 } asss_stats;
 
 typedef struct asss_handle asss_handle;
@@ -230,6 +240,19 @@ asss_status asss_export_permutation(asss_handle* h, int32_t* row_perm);
  * factor or with l_cap too small. */
 asss_status asss_export_factor(asss_handle* h, int32_t* colour, int64_t* l_row_ptr, int32_t* l_col, double* l_val,
                                int64_t l_cap, int64_t* l_nnz);
+
+/* The 2x2 pivots of a handle set up with ASSS_FACTOR_ILDL0_BK (§3 Eq. absfac with
+ * Bunch-Kaufman blocks, Fig. 1; host or device pointers, each may be NULL):
+ * partner (n; -1 for a 1x1 pivot), d_off (n; D_{i,partner(i)}, 0 for a 1x1 pivot;
+ * the diagonal of D is asss_export's d), and the r columns of U_r (r from the
+ * set-up statistics) - column a holds ur_c1[a] at row ur_i1[a] and ur_c2[a] at row
+ * ur_i2[a] (ur_i2[a] = -1: a unit column), M~_r = -2 U_r U_r^T.  L of
+ * asss_export_factor is then block-lower: (I + L) D (I + L)^T equals M^ on the block
+ * closure of M^'s pattern.  *npairs receives the number of 2x2 blocks (0: the factor
+ * has 1x1 pivots only, and the other outputs are left untouched).  ASSS_ERR_ARG
+ * without an incomplete factor. */
+asss_status asss_export_pivots(asss_handle* h, int32_t* partner, double* d_off, int32_t* ur_i1, int32_t* ur_i2,
+                               double* ur_c1, double* ur_c2, int* npairs);
 
 void asss_destroy(asss_handle* h);
 

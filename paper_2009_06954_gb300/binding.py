@@ -53,7 +53,7 @@ class Options(C.Structure):
 
 FORMATS = {"auto": 0, "sell": 1, "diag": 2}
 SCALINGS = {"maxes": 0, "matching": 1}
-FACTORS = {"diag": 0, "ildl0": 1}
+FACTORS = {"diag": 0, "ildl0": 1, "ildl0_bk": 2}
 
 
 class Stats(C.Structure):
@@ -66,7 +66,8 @@ class Stats(C.Structure):
                 ("inner_bytes", C.c_longlong), ("inner_launches", C.c_int), ("sell_sigma", C.c_int),
                 ("sell_split", C.c_int), ("factor_colours", C.c_int), ("t_op_ms", C.c_double),
                 ("op_calls", C.c_int), ("op_bytes", C.c_longlong), ("op_flops", C.c_longlong), ("t_orth_ms", C.c_double),
-                ("orth_calls", C.c_int), ("orth_bytes", C.c_longlong), ("orth_flops", C.c_longlong)]
+                ("orth_calls", C.c_int), ("orth_bytes", C.c_longlong), ("orth_flops", C.c_longlong),
+                ("factor_pairs", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -76,7 +77,7 @@ EXPORTED = ["asss_default_options", "asss_setup", "asss_solve", "asss_solve_adjo
             "asss_apply_operator", "asss_apply_preconditioner", "asss_export", "asss_destroy",
             "asss_status_str", "asss_last_error", "asss_skew_symmetrizer", "asss_skew_lanczos",
             "asss_mrs", "asss_mrs_multi", "asss_kernel_launches", "asss_mrs_noalloc", "asss_export_permutation",
-            "asss_matching_scaling", "asss_export_factor", "asss_setup_batched",
+            "asss_matching_scaling", "asss_export_factor", "asss_export_pivots", "asss_setup_batched",
             "asss_solve_batched", "asss_destroy_batched", "asss_batch_cta_threads", "asss_batch_cta_registers"]
 
 _lib = None
@@ -125,6 +126,7 @@ def lib():
                            C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double), P]
     L.asss_export_permutation.argtypes = [P, P]
     L.asss_export_factor.argtypes = [P, P, P, P, P, C.c_int64, C.POINTER(C.c_int64)]
+    L.asss_export_pivots.argtypes = [P, P, P, P, P, P, P, C.POINTER(C.c_int)]
     L.asss_matching_scaling.argtypes = [pCSR, P, P, P, C.POINTER(C.c_int), P]
     L.asss_mrs_multi.argtypes = [pCSR, C.c_int, P, P, C.c_double, C.c_double, C.c_int, P, C.c_int64, P, C.c_int64,
                                  C.c_double, C.c_int, C.c_int, C.c_int, P, P, P]
@@ -145,7 +147,7 @@ def lib():
     for f in ("asss_setup", "asss_solve", "asss_solve_adjoint", "asss_apply_operator",
               "asss_apply_preconditioner", "asss_export", "asss_skew_symmetrizer",
               "asss_skew_lanczos", "asss_mrs", "asss_mrs_multi", "asss_setup_batched", "asss_solve_batched",
-              "asss_export_permutation", "asss_matching_scaling", "asss_export_factor"):
+              "asss_export_permutation", "asss_matching_scaling", "asss_export_factor", "asss_export_pivots"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -377,6 +379,31 @@ class Solver:
                                                               C.byref(nl)))
         L = sp.csr_matrix((lv[:nl.value], ci[:nl.value], rp), shape=(n, n))
         return colour, L
+
+    def export_pivots(self):
+        """The 2x2 pivots (factor='ildl0_bk'): partner of each row (-1: 1x1), the
+        off-diagonal D entries, and U_r (n x r dense) of M~_r = -2 U_r U_r^T; None when
+        no 2x2 block was formed."""
+        n = self.n
+        r = int(self.setup_stats["r"])
+        npairs = C.c_int(0)
+        part = np.empty(n, dtype=np.int32)
+        doff = np.empty(n)
+        i1 = np.empty(max(r, 1), dtype=np.int32)
+        i2 = np.empty(max(r, 1), dtype=np.int32)
+        c1 = np.empty(max(r, 1))
+        c2 = np.empty(max(r, 1))
+        _check("asss_export_pivots", lib().asss_export_pivots(self._h, part.ctypes.data, doff.ctypes.data,
+                                                              i1.ctypes.data, i2.ctypes.data, c1.ctypes.data,
+                                                              c2.ctypes.data, C.byref(npairs)))
+        if npairs.value == 0:
+            return None
+        U = np.zeros((n, r))
+        for a in range(r):
+            U[i1[a], a] += c1[a]
+            if i2[a] >= 0:
+                U[i2[a], a] += c2[a]
+        return {"npairs": npairs.value, "partner": part.astype(np.int64), "d_off": doff, "Ur": U}
 
     def export(self, s_nnz):
         n = self.n

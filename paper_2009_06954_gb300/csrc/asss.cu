@@ -146,9 +146,25 @@ __global__ void k_to_rowmajor_bf16(const double* A, int lda, int p, int n, int k
     int i = (int)(t / kp), a = (int)(t % kp);
     out[t] = __double2bfloat16(a < p ? A[(size_t)a * lda + i] : 0.0);
 }
-__global__ void k_gather_neg_f(const float* z, const int* neg, int r, double* out) {
+// U_r^T z: column a of U_r is e_{neg[a]}, or (with 2x2 pivots, neg2 != null) c1[a] at
+// neg[a] plus c2[a] at neg2[a] (neg2[a] = -1 for a unit column)
+struct UrCols {
+    const int* neg = nullptr;
+    const int* neg2 = nullptr;
+    const double* c1 = nullptr;
+    const double* c2 = nullptr;
+};
+template <class T>
+__device__ __forceinline__ double ur_dot(const UrCols& U, int a, const T* z) {
+    if (!U.neg2) return (double)z[U.neg[a]];
+    double v = U.c1[a] * (double)z[U.neg[a]];
+    const int j = U.neg2[a];
+    if (j >= 0) v += U.c2[a] * (double)z[j];
+    return v;
+}
+__global__ void k_gather_neg_f(const float* z, UrCols U, int r, double* out) {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a < r) out[a] = (double)z[neg[a]];
+    if (a < r) out[a] = ur_dot(U, a, z);
 }
 __global__ void k_d2f(const double* a, int64_t n, float* b) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -180,20 +196,29 @@ __global__ void k_smw_apply_f32(const float* __restrict__ z, const float* __rest
     }
     out[i] = (double)(z[i] - a);
 }
-__global__ void k_gather_neg(const double* z, const int* neg, int r, double* out) {
+__global__ void k_gather_neg(const double* z, UrCols U, int r, double* out) {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a < r) out[a] = z[neg[a]];
+    if (a < r) out[a] = ur_dot(U, a, z);
 }
-__global__ void k_unit(double* y, int n, int idx) {
+// y = column a of U_r
+__global__ void k_ur_column(double* y, int n, UrCols U, int a) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) y[i] = (i == idx) ? 1.0 : 0.0;
+    if (i >= n) return;
+    double v = 0.0;
+    if (!U.neg2) {
+        v = (i == U.neg[a]) ? 1.0 : 0.0;
+    } else {
+        if (i == U.neg[a]) v += U.c1[a];
+        if (i == U.neg2[a]) v += U.c2[a];
+    }
+    y[i] = v;
 }
-// rows k..m-1 of G = U_bar^T X are rows neg[a] of X
-__global__ void k_gram_neg_rows(const double* X, int n, int m, const int* neg, int k, int r, double* G) {
+// rows k..m-1 of G = U_bar^T X: U_r^T X (rows neg[a] of X, or their combinations)
+__global__ void k_gram_neg_rows(const double* X, int n, int m, UrCols U, int k, int r, double* G) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= r * m) return;
     int a = t / m, c = t % m;
-    G[(size_t)(k + a) * m + c] = X[(size_t)c * n + neg[a]];
+    G[(size_t)(k + a) * m + c] = ur_dot(U, a, X + (size_t)c * n);
 }
 // Sig_bar (m x m row-major) = blkdiag(S_k, -2 I_r), transposed if tr
 __global__ void k_sigma(const double* alpha, int k, int m, int tr, double* Sig) {
@@ -573,6 +598,11 @@ struct asss_handle {
     DBuf<int> perm;
     bool has_perm = false;
     DBuf<int> neg;
+    // 2x2 pivots: the second index and both coefficients of each U_r column (owned by
+    // fac; null when every column is a unit vector)
+    const int* neg2 = nullptr;
+    const double* negc1 = nullptr;
+    const double* negc2 = nullptr;
     int r = 0;
     int prec2 = 0;
     int k = 0, kp = 0;
@@ -606,6 +636,15 @@ struct asss_handle {
         if (mw) mrs_work_destroy(mw);
     }
 };
+
+static UrCols ur_cols(const asss_handle* h) {
+    UrCols U;
+    U.neg = h->neg.p;
+    U.neg2 = h->neg2;
+    U.c1 = h->negc1;
+    U.c2 = h->negc2;
+    return U;
+}
 
 static void fill_defaults(asss_options* o) {
     memset(o, 0, sizeof(*o));
@@ -731,8 +770,7 @@ static asss_status ensure_smw(asss_handle* h, int tr) {
     op.alpha = h->alpha_d.p;
     double tol = h->opt.setup_tol > 0 ? h->opt.setup_tol : h->opt.inner_tol;
     double sign = tr ? -1.0 : 1.0;
-    std::vector<int> negh(r);
-    if (r) ASSS_CUDA(cudaMemcpy(negh.data(), h->neg.p, sizeof(int) * r, cudaMemcpyDeviceToHost));
+    const UrCols U = ur_cols(h);
     if (h->kp <= MRS_MULTI_KPMAX && !h->factored) {
         // S_bar X = U_bar as App. B's simultaneous iterations: the k + r columns share
         // every pass over J~ and Q_k (groups of up to 8 per launch)
@@ -740,7 +778,7 @@ static asss_status ensure_smw(asss_handle* h, int tr) {
         ASSS_TRY(Ub.alloc((int64_t)n * m));
         if (k) ASSS_CUDA(cudaMemcpyAsync(Ub.p, h->Qcm.p, sizeof(double) * (size_t)n * k, cudaMemcpyDeviceToDevice, s));
         for (int t = 0; t < r; ++t) {
-            k_unit<<<cdiv(n, 256), 256, 0, s>>>(Ub.p + (size_t)(k + t) * n, n, negh[t]);
+            k_ur_column<<<cdiv(n, 256), 256, 0, s>>>(Ub.p + (size_t)(k + t) * n, n, U, t);
             ASSS_CHECK_LAUNCH();
         }
         ASSS_TRY(mrs_multi_solve(c, op, false, 1.0, sign, m, Ub.p, n, X.p, nullptr, n, tol, h->opt.inner_maxit,
@@ -751,7 +789,7 @@ static asss_status ensure_smw(asss_handle* h, int tr) {
             if (col < k) {
                 b = h->Qcm.p + (size_t)col * n;
             } else {
-                k_unit<<<cdiv(n, 256), 256, 0, s>>>(rhs.p, n, negh[col - k]);
+                k_ur_column<<<cdiv(n, 256), 256, 0, s>>>(rhs.p, n, U, col - k);
                 ASSS_CHECK_LAUNCH();
                 b = rhs.p;
             }
@@ -765,7 +803,7 @@ static asss_status ensure_smw(asss_handle* h, int tr) {
     ASSS_TRY(Z.alloc((int64_t)m * m));
     if (k) ASSS_TRY(gram(h->Qcm.p, n, k, X.p, n, m, n, G.p, s));
     if (r) {
-        k_gram_neg_rows<<<cdiv(r * m, 256), 256, 0, s>>>(X.p, n, m, h->neg.p, k, r, G.p);
+        k_gram_neg_rows<<<cdiv(r * m, 256), 256, 0, s>>>(X.p, n, m, U, k, r, G.p);
         ASSS_CHECK_LAUNCH();
     }
     k_sigma<<<cdiv(m * m, 256), 256, 0, s>>>(h->alpha_d.p, k, m, tr, Sig.p);
@@ -826,7 +864,7 @@ static asss_status apply_prec(asss_handle* h, int tr, const double* u, double* o
         ASSS_TRY(mrs_solve(c, h->mw, op, true, 1.0, sign, u, nullptr, h->z32.p, h->opt.inner_tol,
                            h->opt.inner_maxit, qtz, nullptr, false));
         if (h->r && S.m > 0) {
-            k_gather_neg_f<<<cdiv(h->r, 128), 128, 0, s>>>(h->z32.p, h->neg.p, h->r, h->wv.p + h->k);
+            k_gather_neg_f<<<cdiv(h->r, 128), 128, 0, s>>>(h->z32.p, ur_cols(h), h->r, h->wv.p + h->k);
             ASSS_CHECK_LAUNCH();
         }
         k_smw_apply_f32<<<cdiv(n, 256), 256, sizeof(float) * (S.m > 0 ? S.m : 1), s>>>(
@@ -839,7 +877,7 @@ static asss_status apply_prec(asss_handle* h, int tr, const double* u, double* o
                            qtz, nullptr, false));
         if (S.m > 0) {
             if (h->r) {
-                k_gather_neg<<<cdiv(h->r, 128), 128, 0, s>>>(z, h->neg.p, h->r, h->wv.p + h->k);
+                k_gather_neg<<<cdiv(h->r, 128), 128, 0, s>>>(z, ur_cols(h), h->r, h->wv.p + h->k);
                 ASSS_CHECK_LAUNCH();
             }
             ASSS_TRY(sub_rowmajor_gemv(S.Y.p, S.m, h->wv.p, z, n, out, s));
@@ -1347,7 +1385,7 @@ static asss_status apply_prec_block(asss_handle* h, int tr, int nc, const double
                 ASSS_CHECK_LAUNCH();
             }
             if (h->r) {
-                k_gather_neg<<<cdiv(h->r, 128), 128, 0, s>>>(z64[t], h->neg.p, h->r, wv + h->k);
+                k_gather_neg<<<cdiv(h->r, 128), 128, 0, s>>>(z64[t], ur_cols(h), h->r, wv + h->k);
                 ASSS_CHECK_LAUNCH();
             }
             if (fp32) {
@@ -1623,11 +1661,11 @@ static asss_status do_setup(asss_handle* h, const asss_csr* Ain, asss_stats* st)
         (o.outer != ASSS_OUTER_TFQMR && o.outer != ASSS_OUTER_FGMRES) || (o.outer == ASSS_OUTER_FGMRES && o.restart < 1) ||
         o.inner_format < ASSS_FORMAT_AUTO || o.inner_format > ASSS_FORMAT_DIAG ||
         (o.scaling != ASSS_SCALING_MAXES && o.scaling != ASSS_SCALING_MATCHING) ||
-        (o.factor != ASSS_FACTOR_DIAG && o.factor != ASSS_FACTOR_ILDL0)) {
+        (o.factor != ASSS_FACTOR_DIAG && o.factor != ASSS_FACTOR_ILDL0 && o.factor != ASSS_FACTOR_ILDL0_BK)) {
         set_error("invalid option");
         return ASSS_ERR_ARG;
     }
-    if (o.factor == ASSS_FACTOR_ILDL0 && o.q_bf16) {
+    if (o.factor != ASSS_FACTOR_DIAG && o.q_bf16) {
         set_error("the incomplete factor reads Q_k in FP32 or FP64 only (q_bf16 unsupported)");
         return ASSS_ERR_UNSUPPORTED;
     }
@@ -1758,18 +1796,19 @@ static asss_status do_setup(asss_handle* h, const asss_csr* Ain, asss_stats* st)
     ASSS_TRY(h->w.alloc(n));
     k_diag_w<<<cdiv(n, 256), 256, 0, s>>>(Cval.p, diagpos.p, n, h->d.p, h->w.p);
     ASSS_CHECK_LAUNCH();
-    h->factored = o.factor == ASSS_FACTOR_ILDL0;
+    h->factored = o.factor == ASSS_FACTOR_ILDL0 || o.factor == ASSS_FACTOR_ILDL0_BK;
     if (h->factored) {
         // the no-fill incomplete L D L^T of M^ (§3 after Eq. absfac, §4.1 ~ildl(0)):
         // d becomes the pivots D, W = 1 (L~ = (I + L)|D|^1/2 is applied by triangular solves)
         ASSS_TRY(vfill(h->w.p, 1.0, n, s));
         int nzero = 0;
         ASSS_TRY(ildl_build(c, P, mirror.p, Cval.p, h->d.p, o.seed, o.zero_tol, o.precision == ASSS_PREC_MIXED,
-                            h->fac, &nzero));
+                            h->fac, &nzero, o.factor == ASSS_FACTOR_ILDL0_BK));
         if (nzero) {
             set_error("%d zero pivot(s) in the incomplete L D L^T", nzero);
             return ASSS_ERR_ZERO_DIAG;
         }
+        st->factor_pairs = h->fac.npairs;
         st->factor_colours = h->fac.ncol;
     } else {
         DBuf<unsigned long long> mx;
@@ -1792,7 +1831,23 @@ static asss_status do_setup(asss_handle* h, const asss_csr* Ain, asss_stats* st)
             return ASSS_ERR_ZERO_DIAG;
         }
     }
-    {
+    if (h->factored && h->fac.npairs > 0) {
+        // M~_r = sign(D) - I block by block (Fig. 1): the factor's U_r columns
+        if (h->fac.nur > o.r_max) {
+            h->prec2 = 1;
+            h->r = 0;
+        } else {
+            h->r = h->fac.nur;
+            if (h->r) {
+                ASSS_TRY(h->neg.alloc(h->r));
+                ASSS_CUDA(cudaMemcpyAsync(h->neg.p, h->fac.ur_i1.p, sizeof(int) * (size_t)h->r,
+                                          cudaMemcpyDeviceToDevice, s));
+                h->neg2 = h->fac.ur_i2.p;
+                h->negc1 = h->fac.ur_c1.p;
+                h->negc2 = h->fac.ur_c2.p;
+            }
+        }
+    } else {
         DBuf<int> nf, npos;
         ASSS_TRY(nf.alloc(n));
         ASSS_TRY(npos.alloc(n + 1));
@@ -2199,6 +2254,33 @@ asss_status asss_export_factor(asss_handle* h, int32_t* colour, int64_t* l_row_p
     }
     if (l_col && F.nl) ASSS_CUDA(cudaMemcpyAsync(l_col, F.lci.p, sizeof(int) * F.nl, cudaMemcpyDefault, s));
     if (l_val && F.nl) ASSS_CUDA(cudaMemcpyAsync(l_val, F.lv.p, sizeof(double) * F.nl, cudaMemcpyDefault, s));
+    ASSS_CUDA(cudaStreamSynchronize(s));
+    return ASSS_OK;
+}
+
+asss_status asss_export_pivots(asss_handle* h, int32_t* partner, double* d_off, int32_t* ur_i1, int32_t* ur_i2,
+                               double* ur_c1, double* ur_c2, int* npairs) {
+    if (!h) {
+        set_error("handle is NULL");
+        return ASSS_ERR_ARG;
+    }
+    if (!h->factored) {
+        set_error("the handle has no incomplete factor (options.factor)");
+        return ASSS_ERR_ARG;
+    }
+    IldlFactor& F = h->fac;
+    if (npairs) *npairs = F.npairs;
+    if (F.npairs == 0) return ASSS_OK;
+    const int n = h->n, r = h->r;
+    cudaStream_t s = h->ctx.stream;
+    if (partner) ASSS_CUDA(cudaMemcpyAsync(partner, F.part.p, sizeof(int) * n, cudaMemcpyDefault, s));
+    if (d_off) ASSS_CUDA(cudaMemcpyAsync(d_off, F.doff.p, sizeof(double) * n, cudaMemcpyDefault, s));
+    if (r > 0) {
+        if (ur_i1) ASSS_CUDA(cudaMemcpyAsync(ur_i1, F.ur_i1.p, sizeof(int) * r, cudaMemcpyDefault, s));
+        if (ur_i2) ASSS_CUDA(cudaMemcpyAsync(ur_i2, F.ur_i2.p, sizeof(int) * r, cudaMemcpyDefault, s));
+        if (ur_c1) ASSS_CUDA(cudaMemcpyAsync(ur_c1, F.ur_c1.p, sizeof(double) * r, cudaMemcpyDefault, s));
+        if (ur_c2) ASSS_CUDA(cudaMemcpyAsync(ur_c2, F.ur_c2.p, sizeof(double) * r, cudaMemcpyDefault, s));
+    }
     ASSS_CUDA(cudaStreamSynchronize(s));
     return ASSS_OK;
 }

@@ -140,12 +140,26 @@ struct IldlFactor {
     const int* jrp = nullptr;        // J^ (exactly skew) on the pattern, not owned
     const int* jci = nullptr;
     const double* jv = nullptr;
+    // 2x2 pivots (factor ASSS_FACTOR_ILDL0_BK; all empty when no pair was formed):
+    // partner of each vertex (-1: 1x1 pivot), the off-diagonal D_{i,partner(i)}, the
+    // off-diagonal of |D|^-1/2, and U_r of M~_r = sign(D) - I column by column: entries
+    // ur_c1 at ur_i1 and ur_c2 at ur_i2 (ur_i2 = -1 for a unit vector), Sigma_r = -2 I
+    int npairs = 0;
+    DBuf<int> part;
+    DBuf<double> doff, wo;
+    DBuf<float> wo32;
+    int nur = 0;
+    DBuf<int> ur_i1, ur_i2;
+    DBuf<double> ur_c1, ur_c2;
 };
 // P: symmetric pattern of A^ (diagonal included), mirror[e] = position of the transposed
 // entry, Cval = A^ on P; d: diag(A^) on entry, the pivots D on return; *nzero: pivots
 // below zero_tol * max|diag|
+// pivots2: also 2x2 pivot blocks where the first Bunch-Kaufman test asks for them (the
+// factor then works on the block closure of P; U_r comes back in F.ur_*)
 asss_status ildl_build(const Ctx& c, const DCsr& P, const int* mirror, const double* Cval, double* d,
-                       uint64_t seed, double zero_tol, bool fp32, IldlFactor& F, int* nzero);
+                       uint64_t seed, double zero_tol, bool fp32, IldlFactor& F, int* nzero,
+                       bool pivots2 = false);
 asss_status ildl_set_skew(const Ctx& c, IldlFactor& F, const DCsr& Jh, bool fp32);
 asss_status ildl_F(const Ctx& c, IldlFactor& F, const double* v, double* out);  // |D|^-1/2 (I + L)^-1 v
 asss_status ildl_G(const Ctx& c, IldlFactor& F, const double* v, double* out);  // (I + L)^-T |D|^-1/2 v

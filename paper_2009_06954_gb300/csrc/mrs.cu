@@ -143,6 +143,8 @@ struct MrsParams {
     const int* flvl;     // vertices by (colour, index)
     const int *flrp, *flci, *furp, *fuci, *fjrp, *fjci;
     const T *flv, *fuv, *fjv, *fwd;
+    const int* fpart;    // 2x2 pivots: partner of each vertex (null: 1x1 pivots only)
+    const T* fwo;        // off-diagonal of |D|^-1/2 between the members of a pair
     T* ft;               // (I + L)^-T (wd .* y)
     T* fw;               // (I + L)^-1 J^ ft
     long long ystride;  // distance between the three Y slots (n + 2 halo)
@@ -495,7 +497,11 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
             for (int cc = p.ncol - 1; cc >= 0 && ok; --cc) {
                 for (int e = s_ls[cc] + gt; e < s_ls[cc + 1]; e += gs) {
                     const int i = __ldg(&p.flvl[e]);
-                    const T a = __ldg(&p.fwd[i]) * Ycur[i];
+                    T a = __ldg(&p.fwd[i]) * Ycur[i];
+                    if (p.fpart) {
+                        const int m = __ldg(&p.fpart[i]);
+                        if (m >= 0) a += __ldg(&p.fwo[i]) * Ycur[m];
+                    }
                     p.ft[i] = a - row_dot8<T>(p.fuci, p.fuv, p.ft, __ldg(&p.furp[i]), __ldg(&p.furp[i + 1]));
                 }
                 grid_sync_phase(p.gb, nblk, phase++, p.budget);
@@ -538,7 +544,13 @@ __global__ void __launch_bounds__(MRS_THREADS, mrs_min_blocks<T>()) k_mrs(MrsPar
             }
             T acc = (T)0;
             if constexpr (FMT == 3) {
-                if (live) acc = __ldg(&p.fwd[i]) * p.fw[i];
+                if (live) {
+                    acc = __ldg(&p.fwd[i]) * p.fw[i];
+                    if (p.fpart) {
+                        const int m = __ldg(&p.fpart[i]);
+                        if (m >= 0) acc += __ldg(&p.fwo[i]) * p.fw[m];
+                    }
+                }
             } else if constexpr (FMT == 2) {
                 if (i < n) {
                     const long long e1 = __ldg(&p.crp[i + 1]);
@@ -806,10 +818,13 @@ static asss_status launch_mrs(const Ctx& c, MrsWork* w, const OpView<T>& J, cons
     prm.ncol = 0;
     prm.fls = prm.flvl = prm.flrp = prm.flci = prm.furp = prm.fuci = prm.fjrp = prm.fjci = nullptr;
     prm.flv = prm.fuv = prm.fjv = prm.fwd = nullptr;
+    prm.fpart = nullptr;
+    prm.fwo = nullptr;
     prm.ft = prm.fw = nullptr;
     if constexpr (FMT == 3) {
         const IldlFactor& F = *J.fac;
         prm.ncol = F.ncol;
+        prm.fpart = F.npairs > 0 ? F.part.p : nullptr;
         prm.fls = F.ls.p;
         prm.flvl = F.lvl.p;
         prm.flrp = F.lrp.p;
@@ -823,6 +838,7 @@ static asss_status launch_mrs(const Ctx& c, MrsWork* w, const OpView<T>& J, cons
             prm.fuv = F.uv32.p;
             prm.fjv = F.jv32.p;
             prm.fwd = F.wd32.p;
+            prm.fwo = F.wo32.p;
             prm.ft = F.ft32.p;
             prm.fw = F.fw32.p;
         } else {
@@ -830,6 +846,7 @@ static asss_status launch_mrs(const Ctx& c, MrsWork* w, const OpView<T>& J, cons
             prm.fuv = F.uv.p;
             prm.fjv = F.jv;
             prm.fwd = F.wd.p;
+            prm.fwo = F.wo.p;
             prm.ft = F.ft.p;
             prm.fw = F.fw.p;
         }
