@@ -175,8 +175,10 @@ __global__ void k_d2f(const double* a, int64_t n, float* b) {
 // FP64 pipe, which is narrow on this part; rows of Y are read as float4 when m
 // is a multiple of 4)
 __global__ void k_smw_apply_f32(const float* __restrict__ z, const float* __restrict__ Y, int m,
-                                const double* __restrict__ w, int n, double* __restrict__ out, int evict_first) {
+                                const double* __restrict__ w, int n, double* __restrict__ out, int evict_first,
+                                const int* skip) {
     extern __shared__ float sw_f[];
+    if (skip && *skip) return;   // the speculative application the outer method did not need
     for (int t = threadIdx.x; t < m; t += blockDim.x) sw_f[t] = (float)w[t];
     __syncthreads();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -869,7 +871,8 @@ static asss_status apply_prec(asss_handle* h, int tr, const double* u, double* o
         }
         k_smw_apply_f32<<<cdiv(n, 256), 256, sizeof(float) * (S.m > 0 ? S.m : 1), s>>>(
             h->z32.p, S.m > 0 ? S.Y32.p : nullptr, S.m, h->wv.p, n, out,
-            stream_evict_first(c, (long long)n * (4LL * h->kp + 28) + 4LL * h->D32.nnz) ? 1 : 0);
+            stream_evict_first(c, (long long)n * (4LL * h->kp + 28) + 4LL * h->D32.nnz) ? 1 : 0,
+            mrs_get_skip(h->mw));
         ASSS_CHECK_LAUNCH();
     } else {
         double* z = (S.m > 0) ? h->zt.p : out;
@@ -1391,7 +1394,7 @@ static asss_status apply_prec_block(asss_handle* h, int tr, int nc, const double
             if (fp32) {
                 k_smw_apply_f32<<<cdiv(n, 256), 256, sizeof(float) * S.m, s>>>(
                     z32[t], S.Y32.p, S.m, wv, n, out[t],
-                    stream_evict_first(c, (long long)n * (4LL * h->kp + 28) + 4LL * h->D32.nnz) ? 1 : 0);
+                    stream_evict_first(c, (long long)n * (4LL * h->kp + 28) + 4LL * h->D32.nnz) ? 1 : 0, nullptr);
                 ASSS_CHECK_LAUNCH();
             } else {
                 ASSS_TRY(sub_rowmajor_gemv(S.Y.p, S.m, wv, z64[t], n, out[t], s));

@@ -108,6 +108,7 @@ MrsTotals mrs_take_totals(MrsWork* w);
 // launches enqueued while flag is set (non-null) read *flag on the device first and
 // do nothing if it is non-zero (speculative work enqueued ahead of a host decision)
 void mrs_set_skip(MrsWork* w, const int* flag);
+const int* mrs_get_skip(const MrsWork* w);
 
 // mrs_multi.cu: App. B's simultaneous iterations for ncol right-hand sides (B, X
 // column-major with leading dimensions ldb, ldx; X in FP64 or FP32 as fp32 says), in

@@ -1130,6 +1130,7 @@ asss_status mrs_collect(const Ctx& c, MrsWork* w, std::vector<MrsResult>* out) {
 }
 
 void mrs_set_skip(MrsWork* w, const int* flag) { w->skip = flag; }
+const int* mrs_get_skip(const MrsWork* w) { return w->skip; }
 
 MrsTotals mrs_take_totals(MrsWork* w) {
     MrsTotals t = w->tot;
