@@ -883,7 +883,7 @@ static asss_status apply_prec(asss_handle* h, int tr, const double* u, double* o
                 k_gather_neg<<<cdiv(h->r, 128), 128, 0, s>>>(z, ur_cols(h), h->r, h->wv.p + h->k);
                 ASSS_CHECK_LAUNCH();
             }
-            ASSS_TRY(sub_rowmajor_gemv(S.Y.p, S.m, h->wv.p, z, n, out, s));
+            ASSS_TRY(sub_rowmajor_gemv(S.Y.p, S.m, h->wv.p, z, n, out, s, mrs_get_skip(h->mw)));
         }
     }
     h->inner_solves += 1;

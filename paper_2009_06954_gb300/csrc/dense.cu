@@ -111,8 +111,9 @@ asss_status gram(const double* A, int lda, int p, const double* B, int ldb, int 
 
 // out = z - Y w  (Y n x m row-major)
 __global__ void k_sub_rowmajor_gemv(const double* __restrict__ Y, int m, const double* __restrict__ w,
-                                    const double* z, int n, double* out) {
+                                    const double* z, int n, double* out, const int* skip) {
     extern __shared__ double sw_[];
+    if (skip && *skip) return;   // a speculative application the outer method did not need
     for (int t = threadIdx.x; t < m; t += blockDim.x) sw_[t] = w[t];
     __syncthreads();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -124,8 +125,8 @@ __global__ void k_sub_rowmajor_gemv(const double* __restrict__ Y, int m, const d
 }
 
 asss_status sub_rowmajor_gemv(const double* Y, int m, const double* w, const double* z, int n, double* out,
-                              cudaStream_t s) {
-    k_sub_rowmajor_gemv<<<cdiv(n, 256), 256, sizeof(double) * (m > 0 ? m : 1), s>>>(Y, m, w, z, n, out);
+                              cudaStream_t s, const int* skip) {
+    k_sub_rowmajor_gemv<<<cdiv(n, 256), 256, sizeof(double) * (m > 0 ? m : 1), s>>>(Y, m, w, z, n, out, skip);
     ASSS_CHECK_LAUNCH();
     return ASSS_OK;
 }

@@ -33,7 +33,7 @@ asss_status gram(const double* A, int lda, int p, const double* B, int ldb, int 
                  cudaStream_t s);
 // out = z - Y w, Y n x m row-major; w on device (m)
 asss_status sub_rowmajor_gemv(const double* Y, int m, const double* w, const double* z, int n, double* out,
-                              cudaStream_t s);
+                              cudaStream_t s, const int* skip = nullptr);
 // out (n) = A (n x p col-major) c  (+ beta*out)
 asss_status colmajor_gemv(const double* A, int lda, int p, const double* c, int n, double beta, double* out,
                           cudaStream_t s);
