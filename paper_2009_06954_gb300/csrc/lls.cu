@@ -114,6 +114,136 @@ __global__ void k_lls_BT(int nS, const int* __restrict__ srow, const int* __rest
     g[u] = acc;
 }
 
+// ---------------------------------------------------------------------------
+// B and B^T stored explicitly (when they fit a memory budget): the entries each merge
+// above would visit, in the same order, so the products are bit for bit those of the
+// merge kernels while each iteration streams two sparse matrices instead of redoing
+// the intersections.  B row k: the C_ij terms (unknown, abar_il) then - off the
+// diagonal - the C_ji terms from position bsplit[k]; B^T row u: (P position, abar_lj),
+// a position stored as ~pos where the diagonal weight sqrt(gamma) applies.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int merge_list(const int* __restrict__ ac, const double* __restrict__ av, int alen,
+                                          const int* __restrict__ bc, const int* __restrict__ bu, int blen,
+                                          int* oc, double* ov) {
+    int x = 0, y = 0, k = 0;
+    while (x < alen && y < blen) {
+        int ca = ac[x], cb = bc[y];
+        if (ca == cb) {
+            if (oc) {
+                oc[k] = bu[y];
+                ov[k] = av[x];
+            }
+            ++k;
+            ++x;
+            ++y;
+        } else if (ca < cb) {
+            ++x;
+        } else {
+            ++y;
+        }
+    }
+    return k;
+}
+
+// count (bcol == nullptr) or fill row k of B
+__global__ void k_bx_rows(int nP, const int* __restrict__ prow, const int* __restrict__ pci,
+                          const int* __restrict__ arp, const int* __restrict__ aci, const double* __restrict__ av,
+                          const int* __restrict__ strp, const int* __restrict__ stci, const int* __restrict__ stsrc,
+                          const int* brp, int* bcnt, int* bsplit, int* bcol, double* bval) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nP) return;
+    int i = prow[k], j = pci[k];
+    if (j < i) {
+        if (!bcol) bcnt[k] = 0;
+        else bsplit[k] = 0;
+        return;
+    }
+    int* oc = bcol ? bcol + brp[k] : nullptr;
+    double* ov = bcol ? bval + brp[k] : nullptr;
+    int a = merge_list(aci + arp[i], av + arp[i], arp[i + 1] - arp[i], stci + strp[j], stsrc + strp[j],
+                       strp[j + 1] - strp[j], oc, ov);
+    int b = 0;
+    if (j != i)
+        b = merge_list(aci + arp[j], av + arp[j], arp[j + 1] - arp[j], stci + strp[i], stsrc + strp[i],
+                       strp[i + 1] - strp[i], oc ? oc + a : nullptr, ov ? ov + a : nullptr);
+    if (!bcol) bcnt[k] = a + b;
+    else bsplit[k] = a;
+}
+
+// q = B s, summed as the merge kernel does: C_ij and C_ji separately, then added
+__global__ void k_bx_apply(int nP, const int* __restrict__ prow, const int* __restrict__ pci,
+                           const int* __restrict__ brp, const int* __restrict__ bsplit,
+                           const int* __restrict__ bcol, const double* __restrict__ bval,
+                           const double* __restrict__ s, double sg, double* q) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nP) return;
+    const int i = prow[k], j = pci[k];
+    if (j < i) {
+        q[k] = 0.0;
+        return;
+    }
+    const int e0 = brp[k], e1 = brp[k + 1], em = e0 + bsplit[k];
+    double cij = 0.0;
+    for (int e = e0; e < em; ++e) cij += bval[e] * s[bcol[e]];
+    if (j == i) {
+        q[k] = sg * cij;
+        return;
+    }
+    double cji = 0.0;
+    for (int e = em; e < e1; ++e) cji += bval[e] * s[bcol[e]];
+    q[k] = cij + cji;
+}
+
+// count (tcol == nullptr) or fill row u of B^T (same walk as k_lls_BT)
+__global__ void k_btx_rows(int nS, const int* __restrict__ srow, const int* __restrict__ sci,
+                           const int* __restrict__ atrp, const int* __restrict__ atci, const double* __restrict__ atv,
+                           const int* __restrict__ prp, const int* __restrict__ pci, const int* __restrict__ mirror,
+                           const int* trp, int* tcnt, int* tcol, double* tval) {
+    int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= nS) return;
+    int l = srow[u], j = sci[u];
+    int x = atrp[l], xe = atrp[l + 1];
+    int y = prp[j], ye = prp[j + 1];
+    int o = tcol ? trp[u] : 0;
+    int k = 0;
+    while (x < xe && y < ye) {
+        int ia = atci[x], ib = pci[y];
+        if (ia == ib) {
+            int pos;
+            if (ia > j) pos = y;
+            else if (ia < j) pos = mirror[y] >= 0 ? mirror[y] : -1;   // none: a zero term, left out
+            else pos = ~y;                                           // the diagonal: weight sqrt(gamma)
+            if (ia == j || pos >= 0) {
+                if (tcol) {
+                    tcol[o + k] = pos;
+                    tval[o + k] = atv[x];
+                }
+                ++k;
+            }
+            ++x;
+            ++y;
+        } else if (ia < ib) {
+            ++x;
+        } else {
+            ++y;
+        }
+    }
+    if (!tcol) tcnt[u] = k;
+}
+
+__global__ void k_btx_apply(int nS, const int* __restrict__ trp, const int* __restrict__ tcol,
+                            const double* __restrict__ tval, const double* __restrict__ t, double sg, double* g) {
+    int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= nS) return;
+    double acc = 0.0;
+    for (int e = trp[u]; e < trp[u + 1]; ++e) {
+        const int c = tcol[e];
+        const double G = c >= 0 ? t[c] : sg * t[~c];
+        acc += tval[e] * G;
+    }
+    g[u] = acc;
+}
+
 __global__ void k_diag_values(const int* rp, const int* ci, const double* v, int n, double* dv) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -197,6 +327,27 @@ __global__ void k_cg_newp(double* p, const double* z, int nS, const double* rz_n
     if (u < nS) p[u] = z[u] + b * p[u];
 }
 
+__global__ void k_sum_counts(const int* cnt, int n, unsigned long long* total) {
+    unsigned long long a = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a += (unsigned)cnt[i];
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(total, a);
+}
+
+// the sum of n counts in 64 bits (integer: the same whatever the order)
+static asss_status sum_counts(const int* cnt, int n, int64_t* total, cudaStream_t s) {
+    DBuf<unsigned long long> t;
+    ASSS_TRY(t.alloc(1));
+    ASSS_CUDA(cudaMemsetAsync(t.p, 0, sizeof(unsigned long long), s));
+    k_sum_counts<<<256, 256, 0, s>>>(cnt, n, t.p);
+    ASSS_CHECK_LAUNCH();
+    unsigned long long h = 0;
+    ASSS_CUDA(cudaMemcpyAsync(&h, t.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+    ASSS_CUDA(cudaStreamSynchronize(s));
+    *total = (int64_t)h;
+    return ASSS_OK;
+}
+
 asss_status lls_product_on_pattern(const Ctx& c, const DCsr& Abar, const DCsr& ST, const int* st_src,
                                    const double* s_val, const DCsr& P, const int* prow, double* Cval) {
     k_lls_C<<<cdiv(P.nnz, 256), 256, 0, c.stream>>>(P.nnz, prow, P.ci.p, Abar.rp.p, Abar.ci.p, Abar.v.p, ST.rp.p,
@@ -254,15 +405,63 @@ asss_status lls_fit(const Ctx& c, const DCsr& Abar, const DCsr& AbarT, const DCs
     ASSS_CUDA(cudaMemsetAsync(s_val.p, 0, sizeof(double) * nS, s));
     k_lls_init_rho<<<cdiv(nP, 256), 256, 0, s>>>(nP, prow.p, P.ci.p, sg, rho.p);
     ASSS_CHECK_LAUNCH();
+    // B and B^T stored explicitly when they fit min(8 GiB, a quarter of the free device
+    // memory): the same products, bit for bit, streamed instead of re-intersected each
+    // iteration; otherwise the merge kernels apply them matrix-free
+    DBuf<int> bcnt, brp, bsplit, bcol, tcnt, trp, tcol;
+    DBuf<double> bval, tval;
+    bool explicit_b = false;
+    {
+        ASSS_TRY(bcnt.alloc(nP > 0 ? nP : 1));
+        ASSS_TRY(tcnt.alloc(nS > 0 ? nS : 1));
+        ASSS_TRY(brp.alloc(nP + 1));
+        ASSS_TRY(trp.alloc(nS + 1));
+        k_bx_rows<<<cdiv(nP, 256), 256, 0, s>>>(nP, prow.p, P.ci.p, Abar.rp.p, Abar.ci.p, Abar.v.p, ST.rp.p, ST.ci.p,
+                                                 st_src.p, nullptr, bcnt.p, nullptr, nullptr, nullptr);
+        ASSS_CHECK_LAUNCH();
+        k_btx_rows<<<cdiv(nS, 256), 256, 0, s>>>(nS, srow.p, Spat.ci.p, AbarT.rp.p, AbarT.ci.p, AbarT.v.p, P.rp.p,
+                                                  P.ci.p, mirror.p, nullptr, tcnt.p, nullptr, nullptr);
+        ASSS_CHECK_LAUNCH();
+        int64_t nb = 0, nt = 0;
+        ASSS_TRY(sum_counts(bcnt.p, nP, &nb, s));
+        ASSS_TRY(sum_counts(tcnt.p, nS, &nt, s));
+        size_t fr = 0, tot = 0;
+        ASSS_CUDA(cudaMemGetInfo(&fr, &tot));
+        const double need = 12.0 * (double)(nb + nt) + 8.0 * (double)(nP + nS);
+        const double budget = fmin(8.0 * 1024 * 1024 * 1024, 0.25 * (double)fr);
+        explicit_b = nb < 0x7fffffffLL && nt < 0x7fffffffLL && need <= budget;
+        if (explicit_b) {
+            ASSS_TRY(exclusive_scan(bcnt.p, brp.p, nP, nullptr, s));
+            ASSS_TRY(exclusive_scan(tcnt.p, trp.p, nS, nullptr, s));
+            ASSS_TRY(bsplit.alloc(nP > 0 ? nP : 1));
+            ASSS_TRY(bcol.alloc(nb > 0 ? nb : 1));
+            ASSS_TRY(bval.alloc(nb > 0 ? nb : 1));
+            ASSS_TRY(tcol.alloc(nt > 0 ? nt : 1));
+            ASSS_TRY(tval.alloc(nt > 0 ? nt : 1));
+            k_bx_rows<<<cdiv(nP, 256), 256, 0, s>>>(nP, prow.p, P.ci.p, Abar.rp.p, Abar.ci.p, Abar.v.p, ST.rp.p,
+                                                     ST.ci.p, st_src.p, brp.p, nullptr, bsplit.p, bcol.p, bval.p);
+            ASSS_CHECK_LAUNCH();
+            k_btx_rows<<<cdiv(nS, 256), 256, 0, s>>>(nS, srow.p, Spat.ci.p, AbarT.rp.p, AbarT.ci.p, AbarT.v.p,
+                                                      P.rp.p, P.ci.p, mirror.p, trp.p, nullptr, tcol.p, tval.p);
+            ASSS_CHECK_LAUNCH();
+        }
+    }
     auto applyBT = [&](const double* t, double* g) -> asss_status {
-        k_lls_BT<<<cdiv(nS, 256), 256, 0, s>>>(nS, srow.p, Spat.ci.p, AbarT.rp.p, AbarT.ci.p, AbarT.v.p, P.rp.p,
-                                                P.ci.p, mirror.p, t, sg, g);
+        if (explicit_b)
+            k_btx_apply<<<cdiv(nS, 256), 256, 0, s>>>(nS, trp.p, tcol.p, tval.p, t, sg, g);
+        else
+            k_lls_BT<<<cdiv(nS, 256), 256, 0, s>>>(nS, srow.p, Spat.ci.p, AbarT.rp.p, AbarT.ci.p, AbarT.v.p, P.rp.p,
+                                                    P.ci.p, mirror.p, t, sg, g);
         ASSS_CHECK_LAUNCH();
         return ASSS_OK;
     };
     auto applyB = [&](const double* sv, double* out) -> asss_status {
-        k_lls_B<<<cdiv(nP, 256), 256, 0, s>>>(nP, prow.p, P.ci.p, Abar.rp.p, Abar.ci.p, Abar.v.p, ST.rp.p, ST.ci.p,
-                                               st_src.p, sv, sg, out);
+        if (explicit_b)
+            k_bx_apply<<<cdiv(nP, 256), 256, 0, s>>>(nP, prow.p, P.ci.p, brp.p, bsplit.p, bcol.p, bval.p, sv, sg,
+                                                      out);
+        else
+            k_lls_B<<<cdiv(nP, 256), 256, 0, s>>>(nP, prow.p, P.ci.p, Abar.rp.p, Abar.ci.p, Abar.v.p, ST.rp.p,
+                                                   ST.ci.p, st_src.p, sv, sg, out);
         ASSS_CHECK_LAUNCH();
         return ASSS_OK;
     };
