@@ -414,8 +414,6 @@ asss_status lls_fit(const Ctx& c, const DCsr& Abar, const DCsr& AbarT, const DCs
     {
         ASSS_TRY(bcnt.alloc(nP > 0 ? nP : 1));
         ASSS_TRY(tcnt.alloc(nS > 0 ? nS : 1));
-        ASSS_TRY(brp.alloc(nP + 1));
-        ASSS_TRY(trp.alloc(nS + 1));
         k_bx_rows<<<cdiv(nP, 256), 256, 0, s>>>(nP, prow.p, P.ci.p, Abar.rp.p, Abar.ci.p, Abar.v.p, ST.rp.p, ST.ci.p,
                                                  st_src.p, nullptr, bcnt.p, nullptr, nullptr, nullptr);
         ASSS_CHECK_LAUNCH();
@@ -431,6 +429,8 @@ asss_status lls_fit(const Ctx& c, const DCsr& Abar, const DCsr& AbarT, const DCs
         const double budget = fmin(8.0 * 1024 * 1024 * 1024, 0.25 * (double)fr);
         explicit_b = nb < 0x7fffffffLL && nt < 0x7fffffffLL && need <= budget;
         if (explicit_b) {
+            ASSS_TRY(brp.alloc(nP + 1));
+            ASSS_TRY(trp.alloc(nS + 1));
             ASSS_TRY(exclusive_scan(bcnt.p, brp.p, nP, nullptr, s));
             ASSS_TRY(exclusive_scan(tcnt.p, trp.p, nS, nullptr, s));
             ASSS_TRY(bsplit.alloc(nP > 0 ? nP : 1));

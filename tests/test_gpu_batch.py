@@ -219,3 +219,24 @@ def test_batched_every_cta_shape_meets_the_tolerance(pkg, batch, shape, regs, mo
         xe = spla.spsolve(A.tocsc(), b)
         assert np.linalg.norm(xm - xe) <= 1e-6 * np.linalg.norm(xe)
     bs.close()
+
+
+def test_batched_setup_reports_a_bad_matrix_and_recovers(pkg, batch):
+    """The matrices are set up concurrently (host threads with streams of their own): a
+    malformed matrix among them (an empty row, rejected on the host) makes the whole
+    set-up return its status with the error text, and a valid batch sets up and solves
+    afterwards."""
+    As = [A for A, _ in batch]
+    bad = As[3].tolil()
+    bad[5, :] = 0.0
+    bad = bad.tocsr()
+    bad.eliminate_zeros()
+    with pytest.raises(pkg.AsssError) as ei:
+        pkg.BatchSolver(As[:3] + [bad] + As[4:], inner_tol=1e-3, restart=24)
+    assert "asss_setup_batched" in str(ei.value)
+    bs = pkg.BatchSolver(As, inner_tol=1e-3, restart=24)
+    Bs = [B for _, B in batch]
+    x, st = bs.solve(bs.pack(Bs), nrhs=Bs[0].shape[1])
+    assert st["status"] == 0
+    _check_columns(batch, bs.unpack(x, Bs[0].shape[1]), Bs)
+    bs.close()
