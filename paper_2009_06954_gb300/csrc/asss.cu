@@ -599,6 +599,7 @@ struct asss_handle {
     DBuf<double> dr, dc, w, d;
     DBuf<int> perm;
     bool has_perm = false;
+    DBuf<double> xf_stage, dA_stage;   // adjoint gradient with host x / dA (allocated on first use)
     DBuf<int> neg;
     // 2x2 pivots: the second index and both coefficients of each U_r column (owned by
     // fac; null when every column is a unit vector)
@@ -2047,7 +2048,8 @@ static asss_status solve_common(asss_handle* h, int tr, int nrhs, const double* 
     int n = h->n;
     auto t0 = std::chrono::steady_clock::now();
     bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
-    DBuf<double> xf, dAd;
+    DBuf<double>& xf = h->xf_stage;    // staging of host x / dA for the gradient, kept by the handle
+    DBuf<double>& dAd = h->dA_stage;
     if (!h->bb.p) {
         ASSS_TRY(h->bb.alloc(n));
         ASSS_TRY(h->xx.alloc(n));
@@ -2125,13 +2127,13 @@ static asss_status solve_common(asss_handle* h, int tr, int nrhs, const double* 
             bool fdev = is_device_ptr(xfwd), adev = is_device_ptr(dA);
             const double* xf_p = xfwd + (size_t)j * ldxf;
             if (!fdev) {
-                ASSS_TRY(xf.alloc(n));
+                if (xf.n < n) ASSS_TRY(xf.alloc(n));
                 ASSS_CUDA(cudaMemcpyAsync(xf.p, xf_p, sizeof(double) * n, cudaMemcpyHostToDevice, s));
                 xf_p = xf.p;
             }
             double* dA_p = dA + (size_t)j * h->A.nnz;
             if (!adev) {
-                ASSS_TRY(dAd.alloc(h->A.nnz));
+                if (dAd.n < h->A.nnz) ASSS_TRY(dAd.alloc(h->A.nnz));
                 dA_p = dAd.p;
             }
             k_grad_A<<<cdiv(n, 256), 256, 0, s>>>(h->A.rp.p, h->A.ci.p, xt, xf_p, n, dA_p);
