@@ -7,8 +7,9 @@ one markdown row per choice:
 * the pattern of S: diagonal (S_d), tridiagonal (S_t) or the pattern of A (§2, Table 3),
 * the weight gamma of the diagonal equations (§2, Eq. regularized),
 * the number k of skew-Lanczos vectors used for deflation (§3.2),
-* the factor L~ of M^: 1x1 pivots without fill ("diag") or the no-fill incomplete
-  L D L^T ("ildl0", §3 after Eq. absfac, §4.1's ~ildl(0)).
+* the factor L~ of M^: 1x1 pivots without fill ("diag"), the no-fill incomplete
+  L D L^T ("ildl0", §3 after Eq. absfac, §4.1's ~ildl(0)), or the same with 2x2 pivot
+  blocks ("ildl0_bk", Fig. 1; --matrix saddle).
 
 Columns: the least-squares fit (iterations of the GPU solver), how skew-symmetric the
 off-diagonal part of Abar S is (||(C - C^T)/2||_F / ||C - diag C||_F, C = Abar S), how far
@@ -16,7 +17,7 @@ its diagonal is from the identity (||diag C - 1||_F / sqrt(n)), the number r of 
 diagonal entries, and the solve: outer iterations, average inner (mrs) iterations per
 preconditioner application, device solve time and the final relative residual.
 
-    python -m paper_2009_06954_gb300.study [--side 48] [--matrix dh|cd]
+    python -m paper_2009_06954_gb300.study [--side 48] [--matrix dh|cd|saddle]
 """
 from __future__ import annotations
 
@@ -54,10 +55,11 @@ def skew_measures(Abar, S):
     return frac, float(np.linalg.norm(d - 1.0) / np.sqrt(len(d)))
 
 
-def measure_case(A, b, S_pat, gamma, k, precision, outer, inner_tol, factor="diag"):
-    """Set up and solve once with one choice; returns the study's measures as a dict."""
+def measure_case(A, b, S_pat, gamma, k, precision, outer, inner_tol, factor="diag", **extra):
+    """Set up and solve once with one choice; returns the study's measures as a dict
+    (extra: further Solver options, e.g. given S values)."""
     s = Solver(A, s_pattern=S_pat, gamma=gamma, k=k, precision=precision, outer=outer,
-               inner_tol=inner_tol, factor=factor)
+               inner_tol=inner_tol, factor=factor, **extra)
     st0 = s.setup_stats
     ex = s.export(S_pat.nnz)
     S = sp.csr_matrix((ex["s_val"], S_pat.indices.copy(), S_pat.indptr.copy()), shape=A.shape)
@@ -66,8 +68,8 @@ def measure_case(A, b, S_pat, gamma, k, precision, outer, inner_tol, factor="dia
     s.close()
     relres = float(np.linalg.norm(b - A @ x) / np.linalg.norm(b))
     return {"lls_its": st0["lls_its"], "skew_fraction": frac, "diag_dev": ddev, "r": st0["r"],
-            "outer_its": st["outer_its"], "inner_its_avg": st["inner_its_avg"], "solve_ms": st["t_solve_ms"],
-            "relres": relres, "status": st["status"]}
+            "pairs": st0["factor_pairs"], "outer_its": st["outer_its"], "inner_its_avg": st["inner_its_avg"],
+            "solve_ms": st["t_solve_ms"], "relres": relres, "status": st["status"]}
 
 
 def run_case(A, b, pattern_name, S_pat, gamma, k, precision, outer, inner_tol, factor="diag"):
@@ -77,12 +79,44 @@ def run_case(A, b, pattern_name, S_pat, gamma, k, precision, outer, inner_tol, f
             f"{m['solve_ms']:.1f} | {m['relres']:.1e} |")
 
 
+def saddle_rows(n=4000, seed=1):
+    """2x2 pivots (Fig. 1, reading R20): on saddle_pairs, whose symmetric part has
+    zero-diagonal pairs, with S = I taken as given (M^ = the symmetric part of A: no 1x1
+    pivot order factors it) and with S fitted on pat(A) (§2: the fit pulls diag(Abar S)
+    towards 1)."""
+    from paper_2009_06954_gb300 import AsssError
+    from workloads import saddle_pairs
+    A = saddle_pairs(n, seed=seed, singles=n // 10)
+    b = np.random.default_rng(seed).standard_normal(n)
+    I = sp.identity(n, format="csr")
+    given = dict(s_values=np.ones(n), lls_maxit=0, dr=np.ones(n), dc=np.ones(n),
+                 row_perm=np.arange(n, dtype=np.int32))
+    rows = []
+    for S_name, S_pat, extra in (("I (given)", I, given), ("pat(A) (fitted)", pattern_of(A), {})):
+        for factor in ("diag", "ildl0", "ildl0_bk"):
+            try:
+                m = measure_case(A, b, S_pat, 1.0, 20, "fp64", "fgmres", 1e-10, factor, **extra)
+                rows.append(f"| {factor} | {S_name} | {m['pairs']} | {m['r']} | {m['outer_its']} | "
+                            f"{m['inner_its_avg']:.1f} | {m['solve_ms']:.1f} | {m['relres']:.1e} |")
+            except AsssError as e:
+                rows.append(f"| {factor} | {S_name} | - | - | set-up fails: {str(e).split(':')[1].strip()} | | | |")
+    return rows
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--matrix", default="dh", choices=["dh", "cd"])
+    ap.add_argument("--matrix", default="dh", choices=["dh", "cd", "saddle"])
     ap.add_argument("--side", type=int, default=48)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     args = ap.parse_args(argv)
+    if args.matrix == "saddle":
+        print("saddle_pairs n = 4000 (400 rows with a diagonal, 1800 zero-diagonal pairs), FP64, FGMRES, "
+              "inner tol 1e-10\n")
+        print("| L~ | S | 2x2 pivots | r | outer its | inner its | solve ms | relres |")
+        print("|---|---|---|---|---|---|---|---|")
+        for row in saddle_rows():
+            print(row, flush=True)
+        return
     if args.matrix == "dh":
         A, b, _ = dissipative_hamiltonian_3d(side=args.side, seed=1)
         title = f"dissipative Hamiltonian {args.side}^3 (n = {A.shape[0]})"

@@ -58,3 +58,25 @@ def test_incomplete_factor_lowers_outer_iterations_cd(study):
     il = study.measure_case(A, b, P, 1.0, 20, "fp64", "tfqmr", 1e-10, factor="ildl0")
     assert il["outer_its"] < dg["outer_its"]
     assert il["status"] == 0 and il["relres"] <= 1e-8 and dg["relres"] <= 1e-8
+
+
+def test_two_by_two_pivots_factor_a_saddle_matrix(study):
+    """Fig. 1 / reading R20: with M^ the symmetric part of saddle_pairs (S = I given), no
+    1x1 factor exists (the diagonal factor and ~ildl(0) meet zero pivots), the factor
+    with 2x2 pivot blocks does, and its solve reaches the tolerance with M~_r of rank r > 0
+    from the blocks' negative eigenvalues."""
+    import scipy.sparse as sp
+    from paper_2009_06954_gb300 import AsssError
+    from workloads import saddle_pairs
+    n = 600
+    A = saddle_pairs(n, seed=3, singles=60)
+    b = np.random.default_rng(3).standard_normal(n)
+    I = sp.identity(n, format="csr")
+    given = dict(s_values=np.ones(n), lls_maxit=0, dr=np.ones(n), dc=np.ones(n),
+                 row_perm=np.arange(n, dtype=np.int32))
+    for factor in ("diag", "ildl0"):
+        with pytest.raises(AsssError):
+            study.measure_case(A, b, I, 1.0, 20, "fp64", "fgmres", 1e-10, factor, **given)
+    m = study.measure_case(A, b, I, 1.0, 20, "fp64", "fgmres", 1e-10, "ildl0_bk", **given)
+    assert m["status"] == 0 and m["relres"] <= 1e-8
+    assert m["pairs"] == 270 and m["r"] > 0
