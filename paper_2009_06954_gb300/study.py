@@ -79,7 +79,7 @@ def run_case(A, b, pattern_name, S_pat, gamma, k, precision, outer, inner_tol, f
             f"{m['solve_ms']:.1f} | {m['relres']:.1e} |")
 
 
-def saddle_rows(n=4000, seed=1):
+def saddle_rows(n=1200, seed=1):
     """2x2 pivots (Fig. 1, reading R20): on saddle_pairs, whose symmetric part has
     zero-diagonal pairs, with S = I taken as given (M^ = the symmetric part of A: no 1x1
     pivot order factors it) and with S fitted on pat(A) (§2: the fit pulls diag(Abar S)
@@ -90,9 +90,9 @@ def saddle_rows(n=4000, seed=1):
     b = np.random.default_rng(seed).standard_normal(n)
     I = sp.identity(n, format="csr")
     given = dict(s_values=np.ones(n), lls_maxit=0, dr=np.ones(n), dc=np.ones(n),
-                 row_perm=np.arange(n, dtype=np.int32))
+                 row_perm=np.arange(n, dtype=np.int32), r_max=n)
     rows = []
-    for S_name, S_pat, extra in (("I (given)", I, given), ("pat(A) (fitted)", pattern_of(A), {})):
+    for S_name, S_pat, extra in (("I (given)", I, given), ("pat(A) (fitted)", pattern_of(A), {"r_max": n})):
         for factor in ("diag", "ildl0", "ildl0_bk"):
             try:
                 m = measure_case(A, b, S_pat, 1.0, 20, "fp64", "fgmres", 1e-10, factor, **extra)
@@ -110,8 +110,8 @@ def main(argv=None):
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     args = ap.parse_args(argv)
     if args.matrix == "saddle":
-        print("saddle_pairs n = 4000 (400 rows with a diagonal, 1800 zero-diagonal pairs), FP64, FGMRES, "
-              "inner tol 1e-10\n")
+        print("saddle_pairs n = 1200 (120 rows with a diagonal, 540 zero-diagonal pairs), r_max = n, FP64, "
+              "FGMRES, inner tol 1e-10\n")
         print("| L~ | S | 2x2 pivots | r | outer its | inner its | solve ms | relres |")
         print("|---|---|---|---|---|---|---|---|")
         for row in saddle_rows():

@@ -72,11 +72,12 @@ def test_two_by_two_pivots_factor_a_saddle_matrix(study):
     A = saddle_pairs(n, seed=3, singles=60)
     b = np.random.default_rng(3).standard_normal(n)
     I = sp.identity(n, format="csr")
+    # r_max above the 270 pairs, so M~_r is kept (above r_max Eq. preconditioner2 drops it)
     given = dict(s_values=np.ones(n), lls_maxit=0, dr=np.ones(n), dc=np.ones(n),
-                 row_perm=np.arange(n, dtype=np.int32))
+                 row_perm=np.arange(n, dtype=np.int32), r_max=1000)
     for factor in ("diag", "ildl0"):
         with pytest.raises(AsssError):
             study.measure_case(A, b, I, 1.0, 20, "fp64", "fgmres", 1e-10, factor, **given)
     m = study.measure_case(A, b, I, 1.0, 20, "fp64", "fgmres", 1e-10, "ildl0_bk", **given)
     assert m["status"] == 0 and m["relres"] <= 1e-8
-    assert m["pairs"] == 270 and m["r"] > 0
+    assert m["pairs"] == 270 and m["r"] == 270   # one negative eigenvalue in each pair's block
