@@ -686,12 +686,14 @@ def main_adjoint(args, world, rank, local):
     # end to end from pinned host buffers (g and x in, lambda and dA out)
     gp = g.cpu().pin_memory()
     xp = x.cpu().pin_memory()
+    lam_p = torch.empty(n, dtype=torch.float64).pin_memory()
+    dA_p = torch.empty(s.nnz, dtype=torch.float64).pin_memory()
     e2e_s = 0.0
     for _ in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         t = time.perf_counter()
-        s.solve_adjoint(gp, xp)
+        s.solve_adjoint(gp, xp, lam=lam_p, dA=dA_p)
         e2e_s += time.perf_counter() - t
     e2e_val = aggregate_rate(world, args.steps, reduce_max(e2e_s, dist, dev))
     inner_ms = sum(st_["t_inner_ms"] for st_ in stats)

@@ -322,19 +322,26 @@ class Solver:
         _check("asss_solve", status, soft_ok=True)
         return x, st.as_dict()
 
-    def solve_adjoint(self, g, x=None):
-        """lambda with A^T lambda = g; with x also dA_e = -lambda_i x_j on A's nonzeros."""
+    def solve_adjoint(self, g, x=None, lam=None, dA=None):
+        """lambda with A^T lambda = g; with x also dA_e = -lambda_i x_j on A's nonzeros.
+        lam (n) and dA (nnz), when given, receive the results (host or device, e.g.
+        pinned host buffers kept across calls); otherwise they are allocated like g."""
         keep = []
-        lam = self._out_like(g, 1)
-        dA = None
+        if lam is None:
+            lam = self._out_like(g, 1)
+        _check_out("lam", lam, self.n)
         xp = None
         if x is not None:
-            if _is_torch(g):
-                import torch
-                dA = torch.empty(self.nnz, dtype=torch.float64, device=g.device)
-            else:
-                dA = np.empty(self.nnz)
+            if dA is None:
+                if _is_torch(g):
+                    import torch
+                    dA = torch.empty(self.nnz, dtype=torch.float64, device=g.device)
+                else:
+                    dA = np.empty(self.nnz)
+            _check_out("dA", dA, self.nnz)
             xp = _ptr_f(x, keep)
+        else:
+            dA = None
         st = Stats()
         status = lib().asss_solve_adjoint(self._h, 1, _ptr_f(g, keep), self.n, _ptr_f(lam, keep),
                                           self.n, xp, self.n, _ptr_f(dA, keep), C.byref(st))
@@ -496,6 +503,16 @@ class BatchSolver:
         status = lib().asss_solve_batched(self._h, int(nrhs), _ptr_f(b, keep), _ptr_f(x, keep), C.byref(st))
         _check("asss_solve_batched", status, soft_ok=True)
         return x, st.as_dict()
+
+
+def _check_out(name, a, size):
+    """An output buffer: float64, contiguous, size entries."""
+    if _is_torch(a):
+        ok = a.dtype.is_floating_point and a.element_size() == 8 and a.is_contiguous() and a.numel() == size
+    else:
+        ok = a.dtype == np.float64 and a.flags.c_contiguous and a.size == size
+    if not ok:
+        raise ValueError(f"{name} must be a contiguous float64 buffer of {size} entries")
 
 
 def _ptr_f(a, keep):

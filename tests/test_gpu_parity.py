@@ -274,6 +274,22 @@ def test_adjoint_matches_dense(pkg):
     assert np.linalg.norm(lam - lam_d) <= 1e-9 * np.linalg.norm(lam_d)
     rows = np.repeat(np.arange(n), np.diff(A.indptr))
     np.testing.assert_allclose(dA, -lam[rows] * x[A.indices], rtol=1e-14)
+    # the same gradient into caller-owned pinned host buffers, and into device buffers
+    import torch
+    lam_p = torch.empty(n, dtype=torch.float64).pin_memory()
+    dA_p = torch.empty(A.nnz, dtype=torch.float64).pin_memory()
+    r = s.solve_adjoint(torch.tensor(g).pin_memory(), torch.tensor(x).pin_memory(), lam=lam_p, dA=dA_p)
+    assert r[0] is lam_p and r[1] is dA_p
+    # (same path; tolerance rather than bit equality, as a SELL inner operator sums in a
+    # dynamic slice order)
+    close = lambda u, v: np.linalg.norm(u - v) <= 1e-9 * np.linalg.norm(v)
+    assert close(lam_p.numpy(), lam) and close(dA_p.numpy(), dA)
+    lam_d2 = torch.empty(n, dtype=torch.float64, device="cuda")
+    dA_d2 = torch.empty(A.nnz, dtype=torch.float64, device="cuda")
+    s.solve_adjoint(torch.tensor(g, device="cuda"), torch.tensor(x, device="cuda"), lam=lam_d2, dA=dA_d2)
+    assert close(lam_d2.cpu().numpy(), lam) and close(dA_d2.cpu().numpy(), dA)
+    with pytest.raises(ValueError):
+        s.solve_adjoint(g, x, dA=np.empty(A.nnz - 1))
 
 
 def test_torch_autograd(pkg):
