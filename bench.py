@@ -503,6 +503,7 @@ def main_batched(args, world, rank, local):
     # end to end: pinned host b and x, copies inside the timed region
     bp = torch.from_numpy(bh).pin_memory()
     xp = torch.empty_like(bp).pin_memory()
+    bs.solve(bp, nrhs=nrhs, x=xp)   # untimed: allocates the device copies of host b and x once
     e2e_s = 0.0
     for _ in range(args.steps):
         flush.zero_()
@@ -688,6 +689,7 @@ def main_adjoint(args, world, rank, local):
     xp = x.cpu().pin_memory()
     lam_p = torch.empty(n, dtype=torch.float64).pin_memory()
     dA_p = torch.empty(s.nnz, dtype=torch.float64).pin_memory()
+    s.solve_adjoint(gp, xp, lam=lam_p, dA=dA_p)   # untimed: allocates the staging of host x and dA once
     e2e_s = 0.0
     for _ in range(args.steps):
         flush.zero_()
@@ -803,6 +805,7 @@ def main_multi_rhs(args, world, rank, local):
     ok = all(s_["status"] == 0 for s_ in stats) and relres <= 1e-8
     Bp = torch.from_numpy(Bh.T.copy()).pin_memory()
     Xp = torch.empty((R, n), dtype=torch.float64).pin_memory()
+    solver.solve(Bp.T, Xp.T)   # untimed: allocates the device copies of host B and X once
     e2e_s = 0.0
     for _ in range(args.steps):
         flush.zero_()
@@ -928,6 +931,7 @@ def main_general(args, world, rank, local):
     # end to end: b in from pinned host memory, x out, every step
     bp = torch.from_numpy(b).pin_memory()
     xp = torch.empty(n, dtype=torch.float64).pin_memory()
+    solver.solve(bp, xp)   # untimed: allocates the device copies of host b and x once
     e2e_s, e2e_its = 0.0, 0
     for _ in range(args.steps):
         flush.zero_()
@@ -1210,6 +1214,7 @@ def main():
     # end to end through the C ABI with pinned host buffers (copies in the timed region)
     bh = [torch.tensor(r).pin_memory() for r in rhs_h]
     xh = torch.empty(n, dtype=torch.float64).pin_memory()
+    solver.solve(bh[0], xh)   # untimed: allocates the device copies of host b and x once
     e2e_s = 0.0
     for s in range(args.steps):
         flush.zero_()
