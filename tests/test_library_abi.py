@@ -98,3 +98,17 @@ def test_batched_packing_follows_the_abi_layout():
             np.testing.assert_array_equal(v[o * nrhs + c * n: o * nrhs + (c + 1) * n], blocks[m][:, c])
     for a, b in zip(bs.unpack(v, nrhs), blocks):
         np.testing.assert_array_equal(a, b)
+
+
+def test_output_buffers_are_checked_on_the_host():
+    """solve_adjoint's caller-owned outputs: float64, contiguous, the right length
+    (checked before any call into the library)."""
+    import numpy as np
+    import torch
+    from paper_2009_06954_gb300.binding import _check_out
+    _check_out("lam", np.empty(10), 10)
+    _check_out("dA", torch.empty(7, dtype=torch.float64), 7)
+    for bad in (np.empty(9), np.empty(10, dtype=np.float32), np.empty((10, 2))[:, 0],
+                torch.empty(10, dtype=torch.float32), torch.empty(20, dtype=torch.float64)[::2]):
+        with pytest.raises(ValueError):
+            _check_out("lam", bad, 10)
